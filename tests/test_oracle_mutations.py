@@ -1,0 +1,110 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that the
+pins in test_oracle.py catch every one of them: a dropped term, a wrong
+sign, a transposed operand, an off-by-one diagonal, a missing pivot search,
+a missing square root."""
+import glob
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import tests.test_oracle as T
+
+PINS = [
+    lambda o: [T.test_golden_expression(o, p) for p in sorted(glob.glob(os.path.join(T.GOLDEN, "*.json")))
+               if not p.endswith("chain_e6.json")],
+    lambda o: T.test_elementwise_vs_numpy(o, 37, 53),
+    T.test_small_integer_brute_force, T.test_accu_vs_fsum_and_dot, T.test_norm_fro,
+    T.test_matmul_vs_numpy_and_transpose_identity, T.test_trace_invariants, T.test_diagmat,
+    T.test_inverse, T.test_solve_literal_and_backward_error, T.test_exact_fraction_inverse,
+]
+
+
+def _mut_matmul_transposed(a, b):
+    a, b = oracle.f64(a), oracle.f64(b)
+    if b.shape[0] == b.shape[1]:
+        b = np.asfortranarray(b.T)
+    return np.asfortranarray(a @ b)
+
+
+def _mut_matmul_dropped_term(a, b):
+    a, b = oracle.f64(a), oracle.f64(b)
+    if a.shape[1] <= 1:
+        return np.asfortranarray(a @ b)
+    return np.asfortranarray(a[:, :-1] @ b[:-1, :])
+
+
+def _mut_sub_sign(a, b):
+    return oracle.f64(b) - oracle.f64(a)
+
+
+def _mut_accu_dropped(a):
+    a = oracle.f64(a)
+    return float(np.sum(a.ravel(order="F")[:-1])) if a.size > 1 else float(a.sum())
+
+
+def _mut_trace_offset(a):
+    a = oracle.f64(a)
+    d = min(a.shape)
+    return float(sum(a[i, (i + 1) % a.shape[1]] for i in range(d)))
+
+
+def _mut_diagmat_cols(a):
+    a = oracle.f64(a)
+    if a.shape[0] == 1 or a.shape[1] == 1:
+        v = a.reshape(-1, order="F")
+        return np.asfortranarray(np.diag(v[::-1]))
+    return np.asfortranarray(np.eye(*a.shape) * a)
+
+
+def _mut_inv_no_pivot(a):
+    a = oracle.f64(a).copy()
+    n = a.shape[0]
+    t = np.hstack([a, np.eye(n)])
+    for c in range(n):
+        if t[c, c] == 0.0:
+            raise oracle.SingularMatrix("zero pivot without row search")
+        t[c] /= t[c, c]
+        for r in range(n):
+            if r != c:
+                t[r] -= t[r, c] * t[c]
+    return np.asfortranarray(t[:, n:])
+
+
+def _mut_norm_no_sqrt(a):
+    a = oracle.f64(a)
+    return float(np.sum(a * a))
+
+
+def _mut_schur_as_add(a, b):
+    return oracle.f64(a) + oracle.f64(b)
+
+
+MUTANTS = {
+    "matmul_transposed_operand": ("matmul", _mut_matmul_transposed),
+    "matmul_dropped_term": ("matmul", _mut_matmul_dropped_term),
+    "sub_wrong_sign": ("sub", _mut_sub_sign),
+    "accu_dropped_element": ("accu", _mut_accu_dropped),
+    "trace_off_diagonal": ("trace", _mut_trace_offset),
+    "diagmat_wrong_placement": ("diagmat", _mut_diagmat_cols),
+    "inv_without_pivoting": ("inv", _mut_inv_no_pivot),
+    "norm_without_sqrt": ("norm_fro", _mut_norm_no_sqrt),
+    "schur_as_sum": ("schur", _mut_schur_as_add),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(orc, monkeypatch, name):
+    attr, fn = MUTANTS[name]
+    monkeypatch.setattr(oracle, attr, fn)
+    for table in (oracle._BIN, oracle._SCAL, oracle._RED):
+        if attr in table:
+            monkeypatch.setitem(table, attr, fn)
+    caught = 0
+    for pin in PINS:
+        try:
+            pin(oracle)
+        except (AssertionError, ValueError, oracle.SingularMatrix, IndexError):
+            caught += 1
+    assert caught > 0, f"no pin caught the planted mistake {name}"
