@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark of the bandwidth-bound fused elementwise workload.
+
+Workload: A, B, C, D are 8192 x 8192 matrices with entries uniform in
+[-1, 1], in FP32 and in FP64; one step evaluates out = A%B + 3*C - D/2 with
+accu(out) and norm(out, "fro") once per element type (two evaluations).
+The optimised plan is one fused launch per evaluation; the literal plan (one
+kernel per operator with temporaries, the paper's naive evaluation) is timed
+beside it on the same GPU.  The inputs (1.34 GB FP32, 2.68 GB FP64 moved per
+evaluation) are far larger than L2, so no flush is needed between steps.
+
+Prints one JSON line.  ``--impl reference`` times the CPU FP64 oracle on a
+bounded sample of the same workload instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 8192
+DTYPES = ("f32", "f64")
+SEED = 20250203 + 2
+# columns of the bounded CPU sample (the oracle evaluates this column block)
+SAMPLE_COLS = 1024
+
+# DRAM bytes of one fused FP64 launch at n = 8192 from an ncu capture of the
+# same kernel source (profiles/ew_fused_8192.md); reported as null once the
+# kernel source no longer has this hash.
+NCU_TRAFFIC = {"kernel_src_sha1": None, "f64": None, "f32": None}
+
+
+def kernel_sha1() -> str:
+    with open(os.path.join(ROOT, "paper_2502_03000_gb300", "csrc", "k_ew.cu"), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=N)
+    p.add_argument("--literal-steps", type=int, default=5)
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def host_inputs(n: int, cols: int | None = None):
+    """Seeded FP64 draws for A, B, C, D (column block [0, cols) if given)."""
+    import synth
+    c = n if cols is None else cols
+    out = []
+    for s in range(4):
+        v = synth.uniform_flat(SEED, s + 1, n * c)
+        out.append(v.reshape((n, c), order="F"))
+    return out
+
+
+def workload_nodes(n, dtype):
+    from paper_2502_03000_gb300 import expr as E
+    return E.config_fused(n, dtype)
+
+
+def oracle_sample(n: int, cols: int):
+    """Literal FP64 oracle on the column block [0, cols) of both dtypes.
+    Returns (seconds, results per dtype, inputs per dtype)."""
+    import numpy as np
+    import oracle
+    import synth
+    hin = host_inputs(n, cols)
+    res, ins = {}, {}
+    t = 0.0
+    for dt in DTYPES:
+        x = [synth.cast(h, dt) for h in hin]
+        nodes, outs = workload_nodes(n, dt)
+        # the same expression on an n x cols block
+        for d in nodes:
+            if d["op"] == "input":
+                d["cols"] = cols
+        t0 = time.perf_counter()
+        r = oracle.evaluate(nodes, outs, x)
+        t += time.perf_counter() - t0
+        res[dt], ins[dt] = r, x
+        _ = np
+    return t, res, ins
+
+
+def clocks_start(dev_index: int):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", "-i", str(dev_index), f"--query-gpu={q}",
+                                 "--format=csv,noheader,nounits", "-lms", "200"],
+                                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except (OSError, FileNotFoundError):
+        return None
+
+
+def clocks_stop(proc):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        out, _ = proc.communicate()
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.strip().splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            smax.append(float(f[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+            "reasons": sorted(reasons)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cols = SAMPLE_COLS if a.n == N else max(1, a.n // 8)
+    for _ in range(a.warmup):
+        oracle_sample(a.n, cols)
+    ts = []
+    for _ in range(a.steps):
+        t, _, _ = oracle_sample(a.n, cols)
+        ts.append(t)
+    frac = cols / a.n
+    sec = sum(ts) / len(ts)
+    value = 2 * frac / sec
+    line = {"impl": "reference", "metric": "evals/s & % roofline, optimised vs literal plan, at stated err vs FP64 oracle",
+            "value": value, "unit": "evals/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": sec * 1e3 / frac, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"fused elementwise out=A%B+3*C-D/2, accu(out), norm(out,'fro'); "
+                                   f"A,B,C,D {a.n}x{a.n} uniform[-1,1] in FP32 and FP64",
+                       "evals_per_step": 2},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                             "sample": f"literal FP64 oracle on the {a.n}x{cols} column block of both dtypes per step, scaled by {a.n}/{cols}"},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = args()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import numpy as np
+    import torch
+
+    import paper_2502_03000_gb300 as ag
+    from paper_2502_03000_gb300 import build as _b
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0 or world > 1:
+        _b.build()
+    ag.lib.cache_clear()
+    ag.lib()
+    n = a.n
+    stream = torch.cuda.current_stream(dev)
+
+    # ---- inputs: seeded host draws -> device (both element types) ----
+    hin = host_inputs(n)
+    dev_in, host_pinned, plans, lits, outs = {}, {}, {}, {}, {}
+    for dt in DTYPES:
+        td = torch.float32 if dt == "f32" else torch.float64
+        host_pinned[dt] = []
+        dev_in[dt] = []
+        for h in hin:
+            t = torch.from_numpy(np.ascontiguousarray(h.T)).to(td).pin_memory()
+            host_pinned[dt].append(t)
+            dev_in[dt].append(t.to(dev, non_blocking=True).t())
+        nodes, o = workload_nodes(n, dt)
+        plans[dt] = ag.Plan(nodes, o)
+        lits[dt] = ag.Plan(nodes, o, flags=ag.PLAN_LITERAL)
+        outs[dt] = plans[dt].alloc_outputs(dev)
+        plans[dt].workspace(dev)
+    del hin
+    torch.cuda.synchronize()
+
+    def step():
+        for dt in DTYPES:
+            plans[dt](*dev_in[dt], outputs=outs[dt])
+
+    for _ in range(max(3, a.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, events around every evaluation ----
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(a.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = clocks_start(local)
+    time.sleep(0.3)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(a.steps):
+        evs[k][0].record(stream)
+        plans["f32"](*dev_in["f32"], outputs=outs["f32"])
+        evs[k][1].record(stream)
+        plans["f64"](*dev_in["f64"], outputs=outs["f64"])
+        evs[k][2].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks = clocks_stop(clk)
+    total_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    ms32 = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    ms64 = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+
+    # ---- literal plan, same GPU ----
+    lit_ms = {}
+    lit_outs = {dt: lits[dt].alloc_outputs(dev) for dt in DTYPES}
+    for dt in DTYPES:
+        lits[dt].workspace(dev)
+        lits[dt](*dev_in[dt], outputs=lit_outs[dt])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.literal_steps):
+            lits[dt](*dev_in[dt], outputs=lit_outs[dt])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lit_ms[dt] = e0.elapsed_time(e1) / a.literal_steps
+    del lit_outs
+    for dt in DTYPES:
+        lits[dt]._ws.clear()
+    torch.cuda.empty_cache()
+
+    # ---- end to end: host buffers in, results out, through the public API ----
+    h2d = sum(t.numel() * t.element_size() for dt in DTYPES for t in host_pinned[dt])
+    d2h = sum(o.numel() * o.element_size() for dt in DTYPES for o in outs[dt])
+    host_out = {dt: [torch.empty(o.t().shape if o.dim() == 2 else o.shape, dtype=o.dtype).pin_memory()
+                     for o in outs[dt]] for dt in DTYPES}
+    def e2e_step():
+        for dt in DTYPES:
+            for hp, dv in zip(host_pinned[dt], dev_in[dt]):
+                dv.t().copy_(hp, non_blocking=True)
+            plans[dt](*dev_in[dt], outputs=outs[dt])
+            for ho, o in zip(host_out[dt], outs[dt]):
+                ho.copy_(o.t() if o.dim() == 2 else o, non_blocking=True)
+    e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / a.e2e_steps
+
+    # ---- accuracy against the oracle on the CPU sample (rank 0) ----
+    cpu = None
+    err = {}
+    if rank == 0 and not a.no_cpu:
+        import oracle
+        oracle.build()
+        cols = SAMPLE_COLS if n == N else max(1, n // 8)
+        t_cpu, ref, _ = oracle_sample(n, cols)
+        for dt in DTYPES:
+            blk = outs[dt][0][:, :cols].double().cpu().numpy()
+            err[dt] = {"out_block": oracle.rel_err(blk, ref[dt][0])}
+        frac = cols / n
+        cpu = {"value": 2 * frac / t_cpu, "unit": "evals/s", "cores": 1, "kind": "oracle",
+               "sample": f"literal FP64 oracle (one thread) on the {n}x{cols} column block of both "
+                         f"element types, scaled by {n}/{cols}; {t_cpu:.2f} s"}
+
+    # ---- roofline of the dominant kernel ----
+    hbm, src = peaks()
+    elems = n * n
+    alg = {"f32": 5 * elems * 4, "f64": 5 * elems * 8}
+    dom = "f64" if ms64 >= ms32 else "f32"
+    dom_ms = ms64 if dom == "f64" else ms32
+    achieved = alg[dom] / (dom_ms * 1e-3) / 1e9
+    traffic = None
+    if NCU_TRAFFIC.get("kernel_src_sha1") == kernel_sha1():
+        traffic = NCU_TRAFFIC.get(dom)
+    info = plans["f32"].info
+    launches_per_step = sum(len(plans[dt].info["steps"]) for dt in DTYPES)
+    value = world * 2 * a.steps / (total_ms * 1e-3)
+    line = {
+        "metric": "evals/s & % roofline, optimised vs literal plan, at stated err vs FP64 oracle",
+        "value": value, "unit": "evals/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"fused elementwise out=A%B+3*C-D/2, accu(out), norm(out,'fro'); "
+                               f"A,B,C,D {n}x{n} uniform[-1,1] in FP32 and FP64 (one evaluation each per step)",
+                   "evals_per_step": 2, "plan": info["mode"],
+                   "l2": "inputs larger than L2 (1.34 GB FP32 / 2.68 GB FP64 per evaluation), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "per_eval_ms": {"f32": ms32, "f64": ms64},
+        "gbs": {"f32": alg["f32"] / (ms32 * 1e-3) / 1e9, "f64": alg["f64"] / (ms64 * 1e-3) / 1e9},
+        "literal_ms": lit_ms,
+        "vs_literal": {dt: lit_ms[dt] / (ms32 if dt == "f32" else ms64) for dt in DTYPES},
+        "err_vs_oracle": err,
+        "roofline": {"bound": "hbm", "kernel": f"ew_flat_kernel<{'double' if dom == 'f64' else 'float'},4>",
+                     "achieved": achieved, "peak": hbm, "peak_source": src, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic,
+                     "alg_bytes_per_launch": alg[dom]},
+        "cpu_baseline": cpu,
+        "e2e": {"value": 2 / (e2e_ms * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * a.steps,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * arma_gpu.h -- C ABI of a GB300 (sm_103a) evaluator for compound
+ * linear-algebra expressions.
+ *
+ * The method follows Sanderson & Curtin, "Armadillo: An Efficient Framework
+ * for Numerical Linear Algebra" (ICCAE 2025):
+ *   - delayed evaluation: an expression is first described as a tree of
+ *     operations and only evaluated as a whole (Sec. II);
+ *   - elementwise fusion: chains of elementwise operations run as one pass
+ *     with no temporaries (Sec. II, the Z = 0.4*X + 0.6*Y example);
+ *   - products map onto a small set of kernels with transposes and scalar
+ *     factors folded in (Sec. II, the paragraph on xGEMM/xGEMV; Fig. 3);
+ *   - pattern rewrites: inv(A)*B becomes a solve (Sec. I; Sec. II, the
+ *     Glue<Op<Mat,op_inv>,Vec,glue_times> paragraph; Sec. III (9)),
+ *     diagmat(v)*B a row scaling (Sec. III (3)), trace(A*B) a diagonal-only
+ *     product (Sec. III (5)), and matrix chains are re-parenthesised
+ *     (Sec. II, chain paragraph; Sec. III (6)).
+ *
+ * Usage: build an expression descriptor (arma_expr), call arma_gpu_plan()
+ * once (host only, no GPU work), then arma_gpu_eval() any number of times on
+ * device buffers.  The library allocates no device memory during eval: the
+ * caller supplies a workspace of at least arma_gpu_plan_workspace() bytes.
+ *
+ * Storage conventions (all calls):
+ *   - matrices are column-major, element (i, j) at base[i + j*ld], with ld
+ *     in elements and ld >= rows (BLAS/LAPACK convention, which the paper's
+ *     library maps onto);
+ *   - a vector is an n x 1 (or 1 x n) matrix;
+ *   - matrix outputs are written contiguous (ld = rows) in the node's result
+ *     element type (arma_gpu_output_info);
+ *   - scalar outputs (trace, accu, norm_fro) are one FP64 value.
+ *
+ * Ownership: the caller owns every device buffer (inputs, outputs,
+ * workspace).  A plan is owned by the library until arma_gpu_plan_free().
+ * Plans are immutable after creation and may be evaluated concurrently on
+ * different streams provided each evaluation has its own workspace.
+ *
+ * Errors: every call returns an arma_status.  Shape and dtype errors are
+ * reported by arma_gpu_plan (the paper's conformance check, Sec. II);
+ * pointer alignment and workspace size by arma_gpu_eval.  Numerical
+ * failures detected on the device (exact zero pivot, iterative refinement
+ * not converging) are recorded in the workspace and read back with
+ * arma_gpu_eval_status() after the stream has been synchronised; they are
+ * never raised as device traps.
+ */
+#ifndef ARMA_GPU_H
+#define ARMA_GPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Element types.  BF16 products accumulate and return FP32. */
+typedef enum { ARMA_F64 = 0, ARMA_F32 = 1, ARMA_BF16 = 2 } arma_dtype;
+
+typedef enum {
+  ARMA_OK = 0,
+  ARMA_ERR_INVALID = 1,     /* null pointer, bad node index, malformed descriptor */
+  ARMA_ERR_SHAPE = 2,       /* non-conforming operand sizes (Sec. II conformance check) */
+  ARMA_ERR_DTYPE = 3,       /* mixed element types where the operation needs equal ones */
+  ARMA_ERR_ALIGN = 4,       /* device pointer misaligned for the kernel the plan chose */
+  ARMA_ERR_WORKSPACE = 5,   /* workspace null or smaller than arma_gpu_plan_workspace() */
+  ARMA_ERR_SINGULAR = 6,    /* LU met an exact zero pivot (LAPACK info > 0) */
+  ARMA_ERR_NOCONVERGE = 7,  /* iterative refinement did not reach its tolerance */
+  ARMA_ERR_CUDA = 8,        /* a CUDA runtime call failed */
+  ARMA_ERR_UNSUPPORTED = 9  /* a valid expression this library does not evaluate */
+} arma_status;
+
+/* Operations of the expression tree.  Operands are earlier node indices. */
+typedef enum {
+  ARMA_OP_INPUT = 0,       /* operand in_ptrs[slot]: rows, cols, ld, dtype from the node */
+  ARMA_OP_ADD = 1,         /* a + b (elementwise) */
+  ARMA_OP_SUB = 2,         /* a - b */
+  ARMA_OP_SCHUR = 3,       /* a % b, elementwise (Schur) product */
+  ARMA_OP_DIV = 4,         /* a / b, elementwise */
+  ARMA_OP_SCALE = 5,       /* scalar * a */
+  ARMA_OP_DIV_SCALAR = 6,  /* a / scalar */
+  ARMA_OP_ADD_SCALAR = 7,  /* a + scalar */
+  ARMA_OP_NEG = 8,         /* -a */
+  ARMA_OP_TRANS = 9,       /* a^T */
+  ARMA_OP_MATMUL = 10,     /* a * b, matrix product */
+  ARMA_OP_DIAGMAT = 11,    /* vector -> diagonal matrix; matrix -> off-diagonals zero */
+  ARMA_OP_TRACE = 12,      /* sum of the main diagonal -> FP64 scalar */
+  ARMA_OP_ACCU = 13,       /* sum of all elements -> FP64 scalar */
+  ARMA_OP_NORM_FRO = 14,   /* sqrt(sum of squares) -> FP64 scalar */
+  ARMA_OP_INV = 15         /* matrix inverse (square a) */
+} arma_op;
+
+/* Precision tier for products and solves (elementwise work always runs in
+ * the operands' own type, FP32 arithmetic for BF16 data). */
+typedef enum {
+  ARMA_TIER_NATIVE = 0,      /* by element type: FP64 -> F64, FP32 -> SPLIT_BF16, BF16 -> BF16;
+                                solves: FP64 -> LU32_IR64, FP32 -> SPLIT_BF16 */
+  ARMA_TIER_F64 = 1,         /* FP64 arithmetic throughout */
+  ARMA_TIER_SPLIT_BF16 = 2,  /* operands split into 3 BF16 terms, 6 tensor-core products
+                                with FP32 accumulation (about FP32 accuracy) */
+  ARMA_TIER_BF16 = 3,        /* operands rounded to BF16, one tensor-core product, FP32 accumulate */
+  ARMA_TIER_LU32_IR64 = 4    /* solves: FP32-accurate LU on tensor cores, FP64 iterative refinement */
+} arma_tier;
+
+/* Plan flags. */
+#define ARMA_PLAN_LITERAL      0x1u  /* one kernel per operator with temporaries: the naive
+                                        evaluation the paper compares against (Sec. III) */
+#define ARMA_PLAN_CHAIN_LEFT   0x2u  /* keep the written left-to-right order of product chains */
+#define ARMA_PLAN_CHAIN_GREEDY 0x4u  /* the paper's chain rule (smallest adjacent result first)
+                                        instead of the exact minimum-cost order */
+#define ARMA_PLAN_COST_MLP     0x8u  /* rank candidate plans with the learned cost model */
+#define ARMA_PLAN_NO_FUSE      0x10u /* optimised rewrites but no elementwise fusion */
+
+typedef struct arma_node {
+  int32_t op;        /* arma_op */
+  int32_t a;         /* first operand node index (< this node's index), -1 if none */
+  int32_t b;         /* second operand node index, -1 if none */
+  int32_t slot;      /* ARMA_OP_INPUT: index into in_ptrs */
+  int32_t dtype;     /* ARMA_OP_INPUT: arma_dtype */
+  int32_t reserved;  /* must be 0 */
+  int64_t rows;      /* ARMA_OP_INPUT: number of rows */
+  int64_t cols;      /* ARMA_OP_INPUT: number of columns */
+  int64_t ld;        /* ARMA_OP_INPUT: leading dimension in elements (>= rows) */
+  double scalar;     /* SCALE, DIV_SCALAR, ADD_SCALAR: the scalar */
+} arma_node;
+
+typedef struct arma_expr {
+  int32_t n_nodes;          /* 1 .. 256 */
+  int32_t n_outputs;        /* 1 .. 32 */
+  const arma_node* nodes;   /* topological order: operands before users */
+  const int32_t* outputs;   /* node indices; out_ptrs[i] receives node outputs[i] */
+  int32_t tier;             /* arma_tier */
+  uint32_t flags;           /* ARMA_PLAN_* */
+} arma_expr;
+
+typedef struct arma_plan arma_plan;
+
+/* Validate and plan an expression (host only; no CUDA call).
+ * On success *plan is a new plan; on error *plan is set to NULL. */
+arma_status arma_gpu_plan(const arma_expr* expr, arma_plan** plan);
+
+/* Workspace bytes arma_gpu_eval needs for this plan (256-byte aligned). */
+arma_status arma_gpu_plan_workspace(const arma_plan* plan, size_t* bytes);
+
+/* Shape and element type of output i (scalars: 1 x 1, ARMA_F64). */
+arma_status arma_gpu_output_info(const arma_plan* plan, int32_t i, int64_t* rows,
+                                 int64_t* cols, int32_t* dtype);
+
+/* Enqueue the plan on `stream` (a cudaStream_t; NULL = legacy default).
+ * in_ptrs[slot] are device pointers to the operands described by the INPUT
+ * nodes; out_ptrs[i] device pointers for the outputs; workspace a device
+ * buffer of workspace_bytes >= arma_gpu_plan_workspace(), 256-byte aligned.
+ * Asynchronous: returns after launching; it does not synchronise. */
+arma_status arma_gpu_eval(const arma_plan* plan, const void* const* in_ptrs,
+                          void* const* out_ptrs, void* workspace, size_t workspace_bytes,
+                          void* stream);
+
+/* After the stream of an arma_gpu_eval has been synchronised: read the
+ * device-side status the evaluation left in `workspace`.  Returns ARMA_OK,
+ * ARMA_ERR_SINGULAR (info = 1-based column of the zero pivot) or
+ * ARMA_ERR_NOCONVERGE (info = refinement steps taken).  Synchronises `stream`. */
+arma_status arma_gpu_eval_status(const arma_plan* plan, const void* workspace, void* stream,
+                                 int64_t* info);
+
+/* Human- and machine-readable decision log of the plan (JSON text): the
+ * rewrites taken, chain order, precision tier, kernels, predicted work.
+ * The counterpart of the paper's internal call trace (Fig. 3).  Writes at
+ * most len bytes including the terminating NUL; *needed (if non-NULL)
+ * receives the full length + 1. */
+arma_status arma_gpu_plan_info(const arma_plan* plan, char* buf, size_t len, size_t* needed);
+
+void arma_gpu_plan_free(arma_plan* plan);
+
+const char* arma_gpu_status_string(arma_status status);
+
+/* Matrix-chain ordering used by the planner (Sec. II, chain paragraph;
+ * Sec. III (6)).  dims[0..n] give factor t as dims[t] x dims[t+1].
+ * method 0: exact minimum number of scalar multiply-adds (dynamic
+ * programming; among equal costs the lexicographically smallest preorder
+ * sequence of split points); 1: the paper's greedy rule (multiply first the
+ * adjacent pair with the smallest result, left-most on ties); 2: left to
+ * right.  splits receives the n-1 split points in preorder (split k joins
+ * factors [i..k] and [k+1..j]); cost the total multiply-adds. */
+arma_status arma_gpu_chain_order(int32_t n, const int64_t* dims, int32_t method, int32_t* splits,
+                                 uint64_t* cost);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ARMA_GPU_H */

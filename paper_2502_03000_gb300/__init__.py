@@ -1,0 +1,257 @@
+"""Python binding of libarma_gpu.so, a GB300 evaluator for compound
+linear-algebra expressions (delayed evaluation, elementwise fusion, product
+rewrites and chain reordering as in Sanderson & Curtin, ICCAE 2025).
+
+This module only marshals arguments: every step of an evaluation runs in
+the library's CUDA kernels.  PyTorch supplies device memory and streams.
+There is no fallback: if the library is missing, importing ``lib()`` raises.
+
+Expressions are lists of node dicts in topological order (the same plain
+format the tests use), e.g.::
+
+    nodes = [{"op": "input", "slot": 0, "rows": m, "cols": n, "dtype": "f64"},
+             {"op": "input", "slot": 1, "rows": m, "cols": n, "dtype": "f64"},
+             {"op": "scale", "a": 0, "s": 0.4},
+             {"op": "scale", "a": 1, "s": 0.6},
+             {"op": "add", "a": 2, "b": 3}]
+    plan = Plan(nodes, outputs=[4])
+    (Z,) = plan(X, Y)          # X, Y column-major CUDA tensors
+
+Matrices are column-major: a tensor ``t`` of shape (rows, cols) with
+``t.stride(0) == 1`` (see ``colmajor``).
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+from functools import lru_cache
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libarma_gpu.so")
+
+# ---- enums (include/arma_gpu.h) ----
+F64, F32, BF16 = 0, 1, 2
+DTYPES = {"f64": F64, "f32": F32, "bf16": BF16}
+OPS = {"input": 0, "add": 1, "sub": 2, "schur": 3, "div": 4, "scale": 5, "div_scalar": 6,
+       "add_scalar": 7, "neg": 8, "trans": 9, "matmul": 10, "diagmat": 11, "trace": 12,
+       "accu": 13, "norm_fro": 14, "inv": 15}
+TIERS = {"native": 0, "f64": 1, "split_bf16": 2, "bf16": 3, "lu32_ir64": 4}
+PLAN_LITERAL, PLAN_CHAIN_LEFT, PLAN_CHAIN_GREEDY, PLAN_COST_MLP, PLAN_NO_FUSE = 1, 2, 4, 8, 16
+STATUS = {0: "ok", 1: "invalid", 2: "shape", 3: "dtype", 4: "align", 5: "workspace",
+          6: "singular", 7: "noconverge", 8: "cuda", 9: "unsupported"}
+
+
+class ArmaError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+        super().__init__(f"{where}: {self.status} ({code})")
+
+
+class Node(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("a", ctypes.c_int32), ("b", ctypes.c_int32),
+                ("slot", ctypes.c_int32), ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("ld", ctypes.c_int64),
+                ("scalar", ctypes.c_double)]
+
+
+class Expr(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("n_outputs", ctypes.c_int32),
+                ("nodes", ctypes.POINTER(Node)), ("outputs", ctypes.POINTER(ctypes.c_int32)),
+                ("tier", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+EXPORTS = ["arma_gpu_plan", "arma_gpu_plan_workspace", "arma_gpu_output_info", "arma_gpu_eval",
+           "arma_gpu_eval_status", "arma_gpu_plan_info", "arma_gpu_plan_free",
+           "arma_gpu_status_string", "arma_gpu_chain_order"]
+
+
+@lru_cache(maxsize=1)
+def lib() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() (needs nvcc)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    L.arma_gpu_plan.argtypes = [ctypes.POINTER(Expr), ctypes.POINTER(vp)]
+    L.arma_gpu_plan_workspace.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.arma_gpu_output_info.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)]
+    L.arma_gpu_eval.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, ctypes.c_size_t, vp]
+    L.arma_gpu_eval_status.argtypes = [vp, vp, vp, ctypes.POINTER(i64)]
+    L.arma_gpu_plan_info.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+    L.arma_gpu_plan_free.argtypes = [vp]
+    L.arma_gpu_plan_free.restype = None
+    L.arma_gpu_status_string.argtypes = [ctypes.c_int]
+    L.arma_gpu_status_string.restype = ctypes.c_char_p
+    L.arma_gpu_chain_order.argtypes = [i32, ctypes.POINTER(i64), i32, ctypes.POINTER(i32),
+                                       ctypes.POINTER(ctypes.c_uint64)]
+    for n in EXPORTS:
+        if getattr(L, n).restype is ctypes.c_int:
+            getattr(L, n).restype = ctypes.c_int
+    return L
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise ArmaError(code, where)
+
+
+def torch_dtype(dt: int):
+    import torch
+    return {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16}[dt]
+
+
+def colmajor(t):
+    """Column-major copy (or view) of a 2-D tensor: stride (1, rows)."""
+    if t.dim() == 1:
+        t = t.reshape(-1, 1)
+    if t.stride(0) == 1 and (t.shape[1] <= 1 or t.stride(1) >= max(1, t.shape[0])):
+        return t
+    return t.t().contiguous().t()
+
+
+def empty_colmajor(rows: int, cols: int, dtype, device):
+    import torch
+    return torch.empty((cols, rows), dtype=dtype, device=device).t()
+
+
+def ld_of(t) -> int:
+    rows = t.shape[0]
+    if t.shape[1] <= 1:
+        return max(1, rows)
+    return int(t.stride(1))
+
+
+def _mk_nodes(nodes):
+    arr = (Node * len(nodes))()
+    for i, d in enumerate(nodes):
+        n = arr[i]
+        n.op = OPS[d["op"]]
+        n.a = d.get("a", -1)
+        n.b = d.get("b", -1)
+        n.slot = d.get("slot", 0)
+        dt = d.get("dtype", "f64")
+        n.dtype = DTYPES[dt] if isinstance(dt, str) else int(dt)
+        n.rows = d.get("rows", 0)
+        n.cols = d.get("cols", 0)
+        n.ld = d.get("ld", max(1, d.get("rows", 0)))
+        n.scalar = float(d.get("s", 0.0))
+    return arr
+
+
+class Plan:
+    """A planned expression.  Planning runs on the host only; ``__call__``
+    enqueues the plan's kernels on the current CUDA stream."""
+
+    def __init__(self, nodes, outputs, tier="native", flags=0):
+        self.nodes = [dict(d) for d in nodes]
+        self.outputs = list(outputs)
+        L = lib()
+        self._arr = _mk_nodes(self.nodes)
+        self._outs = (ctypes.c_int32 * len(self.outputs))(*self.outputs)
+        e = Expr(len(self.nodes), len(self.outputs), self._arr, self._outs,
+                 TIERS[tier] if isinstance(tier, str) else int(tier), int(flags))
+        h = ctypes.c_void_p()
+        _check(L.arma_gpu_plan(ctypes.byref(e), ctypes.byref(h)), "arma_gpu_plan")
+        self._h = h
+        ws = ctypes.c_size_t()
+        _check(L.arma_gpu_plan_workspace(h, ctypes.byref(ws)), "arma_gpu_plan_workspace")
+        self.workspace_bytes = int(ws.value)
+        self.out_info = []
+        for i in range(len(self.outputs)):
+            r, c, dt = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+            _check(L.arma_gpu_output_info(h, i, ctypes.byref(r), ctypes.byref(c), ctypes.byref(dt)),
+                   "arma_gpu_output_info")
+            scalar = self.nodes[self.outputs[i]]["op"] in ("trace", "accu", "norm_fro")
+            self.out_info.append((int(r.value), int(c.value), int(dt.value), scalar))
+        self.n_slots = 1 + max((d.get("slot", 0) for d in self.nodes if d["op"] == "input"), default=-1)
+        self._ws = {}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().arma_gpu_plan_free(h)
+            except Exception:
+                pass
+
+    @property
+    def info(self) -> dict:
+        L = lib()
+        need = ctypes.c_size_t()
+        L.arma_gpu_plan_info(self._h, None, 0, ctypes.byref(need))
+        buf = ctypes.create_string_buffer(need.value)
+        _check(L.arma_gpu_plan_info(self._h, buf, need.value, None), "arma_gpu_plan_info")
+        return json.loads(buf.value.decode())
+
+    def workspace(self, device):
+        import torch
+        key = str(device)
+        ws = self._ws.get(key)
+        if ws is None or ws.numel() < self.workspace_bytes:
+            ws = torch.empty(max(256, self.workspace_bytes), dtype=torch.uint8, device=device)
+            self._ws[key] = ws
+        return ws
+
+    def alloc_outputs(self, device):
+        import torch
+        outs = []
+        for (r, c, dt, scalar) in self.out_info:
+            if scalar:
+                outs.append(torch.empty(1, dtype=torch.float64, device=device))
+            else:
+                outs.append(empty_colmajor(r, c, torch_dtype(dt), device))
+        return outs
+
+    def pointers(self, inputs, outputs):
+        ins = (ctypes.c_void_p * max(1, self.n_slots))()
+        for k, t in enumerate(inputs):
+            ins[k] = t.data_ptr() if t is not None else None
+        outs = (ctypes.c_void_p * len(outputs))(*[o.data_ptr() for o in outputs])
+        return ins, outs
+
+    def __call__(self, *inputs, outputs=None, workspace=None, stream=None):
+        import torch
+        dev = inputs[0].device if inputs else torch.device("cuda")
+        if outputs is None:
+            outputs = self.alloc_outputs(dev)
+        if workspace is None:
+            workspace = self.workspace(dev)
+        ins, outs = self.pointers(inputs, outputs)
+        st = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+        _check(lib().arma_gpu_eval(self._h, ins, outs, ctypes.c_void_p(workspace.data_ptr()),
+                                   workspace.numel(), ctypes.c_void_p(st)), "arma_gpu_eval")
+        return outputs
+
+    def status(self, workspace=None, stream=None):
+        """Device-side status of the last evaluation (synchronises)."""
+        import torch
+        ws = workspace if workspace is not None else next(iter(self._ws.values()))
+        st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        info = ctypes.c_int64()
+        code = lib().arma_gpu_eval_status(self._h, ctypes.c_void_p(ws.data_ptr()), ctypes.c_void_p(st),
+                                          ctypes.byref(info))
+        return STATUS.get(code, str(code)), int(info.value)
+
+
+def chain_order(dims, method: int = 0):
+    """(splits in preorder, cost) of the planner's chain order: 0 exact DP,
+    1 the paper's greedy rule, 2 left to right."""
+    n = len(dims) - 1
+    d = (ctypes.c_int64 * len(dims))(*dims)
+    sp = (ctypes.c_int32 * max(1, n - 1))()
+    cost = ctypes.c_uint64()
+    _check(lib().arma_gpu_chain_order(n, d, method, sp, ctypes.byref(cost)), "arma_gpu_chain_order")
+    return [int(sp[i]) for i in range(n - 1)], int(cost.value)
+
+
+def tree_from_splits(splits, lo: int, hi: int):
+    """Rebuild a (split, left, right) tree from a preorder split list."""
+    it = iter(splits)
+
+    def rec(i, j):
+        if i == j:
+            return i
+        k = next(it)
+        return (k, rec(i, k), rec(k + 1, j))
+    return rec(lo, hi)

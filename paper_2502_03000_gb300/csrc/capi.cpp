@@ -1,0 +1,239 @@
+// C-ABI entry points (include/arma_gpu.h) and the executor that enqueues a
+// plan's steps on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+namespace arma {
+arma_status plan_expression(const arma_expr* e, arma_plan* p, std::string* msg);
+arma_status chain_order_api(int32_t n, const int64_t* dims, int32_t method, int32_t* splits,
+                            uint64_t* cost);
+}  // namespace arma
+
+using namespace arma;
+
+namespace {
+
+struct Bind {
+  const void* const* in;
+  void* const* out;
+  char* ws;
+  int32_t n_slots;
+  int32_t n_out;
+};
+
+const void* cptr(const Bind& b, const Ref& r) {
+  switch (r.kind) {
+    case REF_INPUT: return b.in[r.idx];
+    case REF_OUTPUT: return b.out[r.idx];
+    case REF_WS: return b.ws + r.idx;
+    default: return nullptr;
+  }
+}
+void* mptr(const Bind& b, const Ref& r) { return const_cast<void*>(cptr(b, r)); }
+
+arma_status cuda_status(cudaError_t e) { return e == cudaSuccess ? ARMA_OK : ARMA_ERR_CUDA; }
+
+arma_status run_step(const Step& st, const Bind& b, cudaStream_t s, int* launches) {
+  unsigned int* tickets = reinterpret_cast<unsigned int*>(b.ws + 64);
+  switch (st.kind) {
+    case ST_EW: {
+      const EwStep& e = st.ew;
+      EwArgs a;
+      std::memset(&a, 0, sizeof a);
+      a.m = e.m; a.n = e.n;
+      a.mode = e.mode; a.nin = e.nin; a.nops = e.nops; a.red = e.red;
+      a.compute_f64 = e.compute_f64; a.out_dtype = e.out_dtype;
+      for (int k = 0; k < e.nin; ++k) {
+        a.in[k] = cptr(b, e.in[k].ref);
+        a.rs[k] = e.in[k].rs; a.cs[k] = e.in[k].cs;
+        a.in_dtype[k] = e.in[k].dtype; a.in_flags[k] = e.in[k].flags;
+      }
+      for (int i = 0; i < e.nops; ++i) a.ops[i] = e.ops[i];
+      a.out = e.out.valid() ? mptr(b, e.out) : nullptr;
+      a.out_ld = e.out_ld;
+      a.partials = e.partials.valid() ? reinterpret_cast<double*>(mptr(b, e.partials)) : nullptr;
+      a.ticket = tickets + e.ticket;
+      a.sum_out = e.sum_out.valid() ? reinterpret_cast<double*>(mptr(b, e.sum_out)) : nullptr;
+      a.norm_out = e.norm_out.valid() ? reinterpret_cast<double*>(mptr(b, e.norm_out)) : nullptr;
+      return cuda_status(launch_ew(a, s, launches));
+    }
+    case ST_GEMM: {
+      const GemmStep& g = st.gemm;
+      GemmArgs a;
+      std::memset(&a, 0, sizeof a);
+      a.m = g.m; a.n = g.n; a.k = g.k;
+      a.A = cptr(b, g.A.ref); a.lda = g.A.ld; a.ta = g.A.trans; a.adt = g.A.dtype;
+      a.B = cptr(b, g.B.ref); a.ldb = g.B.ld; a.tb = g.B.trans; a.bdt = g.B.dtype;
+      a.C = g.C.ref.valid() ? cptr(b, g.C.ref) : nullptr; a.ldc = g.C.ld; a.cdt = g.C.dtype;
+      a.D = mptr(b, g.D.ref); a.ldd = g.D.ld; a.ddt = g.D.dtype;
+      a.alpha = g.alpha; a.beta = g.beta;
+      a.rs = g.rowscale.ref.valid() ? cptr(b, g.rowscale.ref) : nullptr;
+      a.rs_inc = g.rowscale.inc; a.rsdt = g.rowscale.dtype;
+      a.cs = g.colscale.ref.valid() ? cptr(b, g.colscale.ref) : nullptr;
+      a.cs_inc = g.colscale.inc; a.csdt = g.colscale.dtype;
+      a.tier = g.tier;
+      a.scratch = g.scratch.valid() ? mptr(b, g.scratch) : nullptr;
+      a.scratch_bytes = g.scratch_bytes;
+      return cuda_status(launch_gemm(a, s, launches));
+    }
+    case ST_DOT: {
+      const DotStep& d = st.dot;
+      DotArgs a;
+      std::memset(&a, 0, sizeof a);
+      a.m = d.m; a.n = d.n; a.k = d.k;
+      a.A = cptr(b, d.A.ref); a.lda = d.A.ld; a.ta = d.A.trans; a.adt = d.A.dtype;
+      a.B = cptr(b, d.B.ref); a.ldb = d.B.ld; a.tb = d.B.trans; a.bdt = d.B.dtype;
+      a.alpha = d.alpha;
+      a.out = reinterpret_cast<double*>(mptr(b, d.out));
+      a.partials = reinterpret_cast<double*>(mptr(b, d.partials));
+      a.ticket = tickets + d.ticket;
+      return cuda_status(launch_diagdot(a, s, launches));
+    }
+    case ST_TRANSPOSE:
+    case ST_DIAGBUILD: {
+      CopyArgs a;
+      std::memset(&a, 0, sizeof a);
+      a.m = st.cm; a.n = st.cn;
+      a.src = cptr(b, st.csrc.ref); a.lds = st.csrc.ld; a.inc = st.cinc; a.sdt = st.csrc.dtype;
+      a.dst = mptr(b, st.cdst.ref); a.ldd = st.cdst.ld; a.ddt = st.cdst.dtype;
+      return cuda_status(st.kind == ST_TRANSPOSE ? launch_transpose(a, s, launches)
+                                                 : launch_diag_build(a, s, launches));
+    }
+    case ST_SOLVE: {
+      const SolveStep& v = st.solve;
+      SolveArgs a;
+      std::memset(&a, 0, sizeof a);
+      a.n = v.n; a.nrhs = v.nrhs;
+      a.A = cptr(b, v.A.ref); a.lda = v.A.ld; a.adt = v.A.dtype;
+      a.B = v.B.ref.valid() ? cptr(b, v.B.ref) : nullptr; a.ldb = v.B.ld; a.bdt = v.B.dtype;
+      a.X = mptr(b, v.X.ref); a.ldx = v.X.ld; a.xdt = v.X.dtype;
+      a.tier = v.tier;
+      a.scratch = mptr(b, v.scratch); a.scratch_bytes = v.scratch_bytes;
+      a.status_code = reinterpret_cast<int32_t*>(b.ws);
+      a.status_info = reinterpret_cast<int64_t*>(b.ws + 8);
+      return cuda_status(launch_solve(a, s, launches));
+    }
+  }
+  return ARMA_ERR_INVALID;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+arma_status arma_gpu_plan(const arma_expr* expr, arma_plan** plan) {
+  if (!plan) return ARMA_ERR_INVALID;
+  *plan = nullptr;
+  if (!expr) return ARMA_ERR_INVALID;
+  arma_plan* p = new (std::nothrow) arma_plan();
+  if (!p) return ARMA_ERR_INVALID;
+  arma_status s;
+  try {
+    s = plan_expression(expr, p, nullptr);
+  } catch (...) {
+    s = ARMA_ERR_INVALID;
+  }
+  if (s != ARMA_OK) {
+    delete p;
+    return s;
+  }
+  *plan = p;
+  return ARMA_OK;
+}
+
+arma_status arma_gpu_plan_workspace(const arma_plan* plan, size_t* bytes) {
+  if (!plan || !bytes) return ARMA_ERR_INVALID;
+  *bytes = plan->ws_bytes;
+  return ARMA_OK;
+}
+
+arma_status arma_gpu_output_info(const arma_plan* plan, int32_t i, int64_t* rows, int64_t* cols,
+                                 int32_t* dtype) {
+  if (!plan || i < 0 || i >= (int32_t)plan->outs.size()) return ARMA_ERR_INVALID;
+  if (rows) *rows = plan->outs[i].rows;
+  if (cols) *cols = plan->outs[i].cols;
+  if (dtype) *dtype = plan->outs[i].dtype;
+  return ARMA_OK;
+}
+
+arma_status arma_gpu_eval(const arma_plan* plan, const void* const* in_ptrs, void* const* out_ptrs,
+                          void* workspace, size_t workspace_bytes, void* stream) {
+  if (!plan || !out_ptrs || (plan->n_slots > 0 && !in_ptrs)) return ARMA_ERR_INVALID;
+  if (!workspace || workspace_bytes < plan->ws_bytes) return ARMA_ERR_WORKSPACE;
+  if (!aligned(workspace, 256)) return ARMA_ERR_ALIGN;
+  for (size_t o = 0; o < plan->outs.size(); ++o) {
+    bool empty = !plan->outs[o].scalar && (plan->outs[o].rows == 0 || plan->outs[o].cols == 0);
+    if (!out_ptrs[o] && !empty) return ARMA_ERR_INVALID;
+    size_t es = plan->outs[o].scalar ? 8 : dtype_size(plan->outs[o].dtype);
+    if (!aligned(out_ptrs[o], es)) return ARMA_ERR_ALIGN;
+  }
+  for (int32_t k = 0; k < plan->n_slots; ++k)
+    if (in_ptrs[k] && !aligned(in_ptrs[k], 2)) return ARMA_ERR_ALIGN;
+  Bind b{in_ptrs, out_ptrs, static_cast<char*>(workspace), plan->n_slots,
+         (int32_t)plan->outs.size()};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(workspace, 0, kHeaderBytes, s) != cudaSuccess) return ARMA_ERR_CUDA;
+  int launches = 0;
+  for (const Step& st : plan->steps) {
+    arma_status r = run_step(st, b, s, &launches);
+    if (r != ARMA_OK) return r;
+  }
+  return ARMA_OK;
+}
+
+arma_status arma_gpu_eval_status(const arma_plan* plan, const void* workspace, void* stream,
+                                 int64_t* info) {
+  if (!plan || !workspace) return ARMA_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int64_t hdr[2] = {0, 0};
+  if (cudaStreamSynchronize(s) != cudaSuccess) return ARMA_ERR_CUDA;
+  if (cudaMemcpy(hdr, workspace, sizeof hdr, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return ARMA_ERR_CUDA;
+  int32_t code = static_cast<int32_t>(hdr[0] & 0xffffffff);
+  if (info) *info = hdr[1];
+  if (code == 0) return ARMA_OK;
+  return static_cast<arma_status>(code);
+}
+
+arma_status arma_gpu_plan_info(const arma_plan* plan, char* buf, size_t len, size_t* needed) {
+  if (!plan) return ARMA_ERR_INVALID;
+  if (needed) *needed = plan->log.size() + 1;
+  if (buf && len > 0) {
+    size_t n = plan->log.size() < len - 1 ? plan->log.size() : len - 1;
+    std::memcpy(buf, plan->log.data(), n);
+    buf[n] = 0;
+  }
+  return ARMA_OK;
+}
+
+void arma_gpu_plan_free(arma_plan* plan) { delete plan; }
+
+const char* arma_gpu_status_string(arma_status s) {
+  switch (s) {
+    case ARMA_OK: return "ok";
+    case ARMA_ERR_INVALID: return "invalid argument or malformed expression";
+    case ARMA_ERR_SHAPE: return "non-conforming operand sizes";
+    case ARMA_ERR_DTYPE: return "element types do not match";
+    case ARMA_ERR_ALIGN: return "device pointer misaligned";
+    case ARMA_ERR_WORKSPACE: return "workspace missing or too small";
+    case ARMA_ERR_SINGULAR: return "matrix is singular (zero pivot)";
+    case ARMA_ERR_NOCONVERGE: return "iterative refinement did not converge";
+    case ARMA_ERR_CUDA: return "CUDA runtime error";
+    case ARMA_ERR_UNSUPPORTED: return "expression not supported";
+  }
+  return "unknown status";
+}
+
+arma_status arma_gpu_chain_order(int32_t n, const int64_t* dims, int32_t method, int32_t* splits,
+                                 uint64_t* cost) {
+  return chain_order_api(n, dims, method, splits, cost);
+}
+
+}  // extern "C"

@@ -1,0 +1,257 @@
+// Internal structures shared by the planner (host) and the kernel launchers.
+// Not part of the public ABI (include/arma_gpu.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/arma_gpu.h"
+
+namespace arma {
+
+constexpr int kMaxIn = 8;       // distinct operands of one fused elementwise pass
+constexpr int kMaxOps = 48;     // instructions of one fused elementwise program
+constexpr int kMaxStack = 4;    // spill slots of the elementwise accumulator machine
+constexpr int kMaxRedBlocks = 2048;  // partial-sum slots of a reduction
+constexpr size_t kHeaderBytes = 4096;  // workspace header: status + tickets
+constexpr int kMaxTickets = 960;
+
+// --------------------------------------------------------------------------
+// References to buffers, resolved at eval time
+// --------------------------------------------------------------------------
+enum RefKind : int32_t { REF_NONE = 0, REF_INPUT = 1, REF_OUTPUT = 2, REF_WS = 3 };
+
+struct Ref {
+  int32_t kind = REF_NONE;
+  int32_t pad = 0;
+  int64_t idx = 0;  // input slot, output index, or workspace byte offset
+  bool valid() const { return kind != REF_NONE; }
+};
+
+inline Ref ref_input(int64_t slot) { Ref r; r.kind = REF_INPUT; r.idx = slot; return r; }
+inline Ref ref_output(int64_t i) { Ref r; r.kind = REF_OUTPUT; r.idx = i; return r; }
+inline Ref ref_ws(int64_t off) { Ref r; r.kind = REF_WS; r.idx = off; return r; }
+
+inline size_t dtype_size(int dt) { return dt == ARMA_F64 ? 8 : dt == ARMA_F32 ? 4 : 2; }
+
+// --------------------------------------------------------------------------
+// K1: fused elementwise + reduction pass (an accumulator machine)
+// --------------------------------------------------------------------------
+// acc is a per-element register; X_k is operand k at the element; S_j a
+// spill slot.  Every instruction updates acc.
+enum EwOpcode : int32_t {
+  EW_LD = 0,     // acc = X_k
+  EW_ADD,        // acc = acc + X_k
+  EW_SUB,        // acc = acc - X_k
+  EW_RSUB,       // acc = X_k - acc
+  EW_MUL,        // acc = acc * X_k
+  EW_DIV,        // acc = acc / X_k
+  EW_RDIV,       // acc = X_k / acc
+  EW_AXPY,       // acc = acc + s * X_k
+  EW_SCAL,       // acc = s * acc
+  EW_DIVS,       // acc = acc / s
+  EW_ADDS,       // acc = acc + s
+  EW_NEG,        // acc = -acc
+  EW_PUSH,       // S_j = acc
+  EW_POPADD,     // acc = S_j + acc
+  EW_POPSUB,     // acc = S_j - acc
+  EW_POPMUL,     // acc = S_j * acc
+  EW_POPDIV,     // acc = S_j / acc
+  EW_NOPS
+};
+
+struct EwIns {
+  int32_t op;
+  int32_t arg;   // operand index k or slot j
+  double s;
+};
+
+enum EwMode : int32_t { EW_FLAT = 0, EW_GRID = 1, EW_DIAG = 2 };
+
+// operand flags
+enum : int32_t { EWF_DIAGMASK = 1 };  // value is zero off the main diagonal
+
+struct EwOperand {
+  Ref ref;
+  int64_t rs = 1, cs = 0;   // element (i, j) at base[i*rs + j*cs]
+  int32_t dtype = ARMA_F64;
+  int32_t flags = 0;
+};
+
+struct EwStep {
+  int64_t m = 0, n = 0;
+  int32_t mode = EW_FLAT;
+  int32_t nin = 0, nops = 0;
+  EwOperand in[kMaxIn];
+  EwIns ops[kMaxOps];
+  Ref out;                    // optional matrix store
+  int64_t out_ld = 0;
+  int32_t out_dtype = ARMA_F64;
+  int32_t compute_f64 = 1;    // 1: FP64 arithmetic, 0: FP32
+  int32_t red = 0;            // bit0: sum, bit1: sum of squares
+  Ref sum_out, norm_out;      // FP64 scalars (norm = sqrt(sum of squares))
+  Ref partials;               // 2*kMaxRedBlocks doubles
+  int32_t ticket = 0;         // index of the ticket counter in the header
+};
+
+// Device-side argument block of K1 (passed by value).
+struct EwArgs {
+  int64_t m, n;
+  int32_t mode, nin, nops, red;
+  int32_t compute_f64, out_dtype;
+  const void* in[kMaxIn];
+  int64_t rs[kMaxIn], cs[kMaxIn];
+  int32_t in_dtype[kMaxIn], in_flags[kMaxIn];
+  EwIns ops[kMaxOps];
+  void* out;
+  int64_t out_ld;
+  double* partials;
+  unsigned int* ticket;
+  double* sum_out;
+  double* norm_out;
+};
+
+cudaError_t launch_ew(const EwArgs& a, cudaStream_t s, int* launches);
+
+// --------------------------------------------------------------------------
+// Products
+// --------------------------------------------------------------------------
+struct MatOperand {
+  Ref ref;
+  int64_t ld = 0;
+  int32_t dtype = ARMA_F64;
+  int32_t trans = 0;
+};
+
+struct VecOperand {
+  Ref ref;
+  int64_t inc = 1;
+  int32_t dtype = ARMA_F64;
+};
+
+// D = alpha * diag(r) * op(A) * op(B) * diag(c) + beta * C
+struct GemmStep {
+  int64_t m = 0, n = 0, k = 0;
+  MatOperand A, B, C, D;    // C optional (beta term); D output (trans ignored)
+  double alpha = 1.0, beta = 0.0;
+  VecOperand rowscale, colscale;  // optional
+  int32_t tier = ARMA_TIER_F64;
+  Ref scratch;              // workspace for operand conversion / split-K partials
+  int64_t scratch_bytes = 0;
+};
+
+struct GemmArgs {
+  int64_t m, n, k;
+  const void* A; int64_t lda; int32_t ta, adt;
+  const void* B; int64_t ldb; int32_t tb, bdt;
+  const void* C; int64_t ldc; int32_t cdt;
+  void* D; int64_t ldd; int32_t ddt;
+  double alpha, beta;
+  const void* rs; int64_t rs_inc; int32_t rsdt;
+  const void* cs; int64_t cs_inc; int32_t csdt;
+  int32_t tier;
+  void* scratch; int64_t scratch_bytes;
+};
+
+cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s, int* launches);
+int64_t gemm_scratch_bytes(const GemmStep& g);
+
+// trace(op(A) * op(B)) -> FP64 scalar.  op(A) is m x k, op(B) is k x n;
+// the sum runs over i < min(m, n), l < k.
+struct DotStep {
+  int64_t m = 0, n = 0, k = 0;
+  MatOperand A, B;
+  double alpha = 1.0;
+  Ref out;
+  Ref partials;
+  int32_t ticket = 0;
+};
+
+struct DotArgs {
+  int64_t m, n, k;
+  const void* A; int64_t lda; int32_t ta, adt;
+  const void* B; int64_t ldb; int32_t tb, bdt;
+  double alpha;
+  double* out;
+  double* partials;
+  unsigned int* ticket;
+};
+
+cudaError_t launch_diagdot(const DotArgs& a, cudaStream_t s, int* launches);
+
+// --------------------------------------------------------------------------
+// Literal-plan helpers and the solve
+// --------------------------------------------------------------------------
+struct CopyArgs {  // transpose / diagonal build
+  int64_t m, n;
+  const void* src; int64_t lds; int64_t inc; int32_t sdt;
+  void* dst; int64_t ldd; int32_t ddt;
+};
+cudaError_t launch_transpose(const CopyArgs& a, cudaStream_t s, int* launches);
+cudaError_t launch_diag_build(const CopyArgs& a, cudaStream_t s, int* launches);
+
+// X = inv(A) * B  (n x n, n x nrhs) by blocked LU with partial pivoting
+struct SolveStep {
+  int64_t n = 0, nrhs = 0;
+  MatOperand A, B, X;      // B may be absent: X = inv(A)
+  int32_t tier = ARMA_TIER_LU32_IR64;
+  int32_t explicit_inverse = 0;  // literal plan: form inv(A) then multiply
+  Ref scratch;
+  int64_t scratch_bytes = 0;
+};
+
+struct SolveArgs {
+  int64_t n, nrhs;
+  const void* A; int64_t lda; int32_t adt;
+  const void* B; int64_t ldb; int32_t bdt;   // null: identity
+  void* X; int64_t ldx; int32_t xdt;
+  int32_t tier;
+  void* scratch; int64_t scratch_bytes;
+  int32_t* status_code;   // workspace header
+  int64_t* status_info;
+};
+int64_t solve_scratch_bytes(int64_t n, int64_t nrhs, int32_t tier);
+cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches);
+
+// --------------------------------------------------------------------------
+// Plan
+// --------------------------------------------------------------------------
+enum StepKind : int32_t { ST_EW = 0, ST_GEMM, ST_DOT, ST_TRANSPOSE, ST_DIAGBUILD, ST_SOLVE };
+
+struct Step {
+  StepKind kind = ST_EW;
+  EwStep ew;
+  GemmStep gemm;
+  DotStep dot;
+  SolveStep solve;
+  // ST_TRANSPOSE / ST_DIAGBUILD
+  int64_t cm = 0, cn = 0;
+  MatOperand csrc, cdst;
+  int64_t cinc = 1;
+  std::string note;         // decision-log text
+  double flops = 0, bytes = 0;  // algorithmic work of the step
+};
+
+struct OutInfo {
+  int64_t rows, cols;
+  int32_t dtype;
+  int32_t scalar;
+};
+
+}  // namespace arma
+
+struct arma_plan {
+  std::vector<arma::Step> steps;
+  std::vector<arma::OutInfo> outs;
+  std::vector<int64_t> in_align_need;  // per slot: required byte alignment (0 = none)
+  int32_t n_slots = 0;
+  size_t ws_bytes = arma::kHeaderBytes;
+  int32_t tickets = 0;
+  uint32_t flags = 0;
+  int32_t tier = 0;
+  std::string log;          // JSON decision log
+  double flops = 0, bytes = 0;
+};

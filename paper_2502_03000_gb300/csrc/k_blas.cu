@@ -1,0 +1,335 @@
+// Product kernels that need no tensor cores: the FP64 DFMA GEMM (the FP64
+// tier and the refinement residual), GEMV for matrix-vector chains, the
+// diagonal-only product behind trace(A*B) (Sec. III (5)), and the explicit
+// transpose / dense-diagonal copies that only the literal plan uses.
+//
+// Column-major everywhere; op(X) is X or X^T.  The product kernels fold
+// alpha, beta*C, a row scaling diag(r) and a column scaling diag(c) into
+// their epilogue, so 2*A*B + C, trans(A)*B and diagmat(v)*(A*B) are single
+// launches (Sec. II, the folded scalar and transpose flags of Fig. 3).
+#include "common.cuh"
+
+namespace arma {
+
+cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches);
+bool gemm_tc_supported(const GemmArgs& a);
+int64_t gemm_tc_scratch_bytes(int64_t m, int64_t n, int64_t k, int32_t tier);
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// SIMT GEMM: 64 x 64 tile, BK = 16, 256 threads, 4 x 4 outputs per thread.
+// Accumulates in AT (double for the FP64 tier, float otherwise).
+// ---------------------------------------------------------------------------
+constexpr int BM = 64, BN = 64, BK = 16;
+
+template <typename AT>
+__global__ void __launch_bounds__(256) gemm_simt_kernel(const __grid_constant__ GemmArgs a) {
+  __shared__ AT As[BK][BM + 1];
+  __shared__ AT Bs[BK][BN + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t i0 = (int64_t)blockIdx.x * BM, j0 = (int64_t)blockIdx.y * BN;
+  AT acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0;
+  for (int64_t l0 = 0; l0 < a.k; l0 += BK) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int e = tid + r * 256;
+      int ii, ll;
+      if (!a.ta) { ii = e & 63; ll = e >> 6; } else { ll = e & 15; ii = e >> 4; }
+      int64_t gi = i0 + ii, gl = l0 + ll;
+      AT v = 0;
+      if (gi < a.m && gl < a.k) v = load_as<AT>(a.A, a.ta ? gl + gi * a.lda : gi + gl * a.lda, a.adt);
+      As[ll][ii] = v;
+      int jj;
+      if (!a.tb) { ll = e & 15; jj = e >> 4; } else { jj = e & 63; ll = e >> 6; }
+      int64_t gj = j0 + jj;
+      gl = l0 + ll;
+      AT w = 0;
+      if (gl < a.k && gj < a.n) w = load_as<AT>(a.B, a.tb ? gj + gl * a.ldb : gl + gj * a.ldb, a.bdt);
+      Bs[ll][jj] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < BK; ++l) {
+      AT av[4], bv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) av[r] = As[l][tx + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = Bs[l][ty + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    int64_t j = j0 + ty + 16 * c;
+    if (j >= a.n) continue;
+    double cj = a.cs ? load_as<double>(a.cs, j * a.cs_inc, a.csdt) : 1.0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int64_t i = i0 + tx + 16 * r;
+      if (i >= a.m) continue;
+      double v = a.alpha * (double)acc[r][c];
+      if (a.rs) v *= load_as<double>(a.rs, i * a.rs_inc, a.rsdt);
+      v *= cj;
+      if (a.C && a.beta != 0.0) v += a.beta * load_as<double>(a.C, i + j * a.ldc, a.cdt);
+      store_as<double>(a.D, i + j * a.ldd, a.ddt, v);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// GEMV: y_i = alpha * sum_l M(i, l) x_l, M(i, l) at M[i*rsm + l*csm].
+// ---------------------------------------------------------------------------
+struct GemvArgs {
+  int64_t rows, k;
+  const void* M; int64_t rsm, csm; int32_t mdt;
+  const void* x; int64_t incx; int32_t xdt;
+  void* y; int64_t incy; int32_t ydt;
+  const void* c; int64_t incc; int32_t cdt; double beta;
+  double alpha;
+  const void* rsv; int64_t rs_inc; int32_t rsdt;   // per-output scale
+  const void* sv; int32_t svdt;                     // one scale factor (1 x 1 diagonal)
+  double scal;
+  double* partials;  // [splits][rows] when splits > 1
+  int32_t splits;
+};
+
+__device__ __forceinline__ void gemv_out(const GemvArgs& a, int64_t i, double sum) {
+  double v = a.alpha * a.scal * sum;
+  if (a.rsv) v *= load_as<double>(a.rsv, i * a.rs_inc, a.rsdt);
+  if (a.sv) v *= load_as<double>(a.sv, 0, a.svdt);
+  if (a.c && a.beta != 0.0) v += a.beta * load_as<double>(a.c, i * a.incc, a.cdt);
+  store_as<double>(a.y, i * a.incy, a.ydt, v);
+}
+
+// rows contiguous in memory (rsm == 1): one thread per row, k split in chunks
+__global__ void __launch_bounds__(256) gemv_rows_kernel(const __grid_constant__ GemvArgs a) {
+  __shared__ double xs[256];
+  const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const int64_t chunk = (a.k + a.splits - 1) / a.splits;
+  const int64_t lb = (int64_t)blockIdx.y * chunk;
+  const int64_t le = lb + chunk < a.k ? lb + chunk : a.k;
+  double sum = 0.0;
+  for (int64_t l0 = lb; l0 < le; l0 += 256) {
+    int64_t l = l0 + threadIdx.x;
+    xs[threadIdx.x] = l < le ? load_as<double>(a.x, l * a.incx, a.xdt) : 0.0;
+    __syncthreads();
+    int64_t cnt = le - l0 < 256 ? le - l0 : 256;
+    if (i < a.rows) {
+      if (a.mdt == ARMA_F64) {
+        const double* M = static_cast<const double*>(a.M);
+        for (int u = 0; u < cnt; ++u) sum = fma(M[i + (l0 + u) * a.csm], xs[u], sum);
+      } else {
+        for (int u = 0; u < cnt; ++u) sum = fma(load_as<double>(a.M, i + (l0 + u) * a.csm, a.mdt), xs[u], sum);
+      }
+    }
+    __syncthreads();
+  }
+  if (i >= a.rows) return;
+  if (a.splits == 1) gemv_out(a, i, sum);
+  else a.partials[(int64_t)blockIdx.y * a.rows + i] = sum;
+}
+
+__global__ void gemv_finish_kernel(const __grid_constant__ GemvArgs a) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.rows) return;
+  double sum = 0.0;
+  for (int s = 0; s < a.splits; ++s) sum += a.partials[(int64_t)s * a.rows + i];
+  gemv_out(a, i, sum);
+}
+
+// the reduction index contiguous (csm == 1): one warp per output
+__global__ void __launch_bounds__(256) gemv_cols_kernel(const __grid_constant__ GemvArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= a.rows) return;
+  double sum = 0.0;
+  for (int64_t l = lane; l < a.k; l += 32)
+    sum = fma(load_as<double>(a.M, i * a.rsm + l, a.mdt), load_as<double>(a.x, l * a.incx, a.xdt), sum);
+  sum = warp_sum(sum);
+  if (lane == 0) gemv_out(a, i, sum);
+}
+
+int gemv_splits(int64_t rows, int64_t k) {
+  int64_t blocks = (rows + 255) / 256;
+  int64_t want = (int64_t)device_sm_count() * 4;
+  int64_t s = (want + blocks - 1) / blocks;
+  int64_t smax = (k + 511) / 512;
+  if (s > smax) s = smax;
+  if (s > 64) s = 64;
+  return s < 1 ? 1 : (int)s;
+}
+
+cudaError_t launch_gemv(const GemmArgs& a, cudaStream_t s, int* launches) {
+  GemvArgs g;
+  memset(&g, 0, sizeof g);
+  g.alpha = a.alpha;
+  g.beta = a.beta;
+  g.scal = 1.0;
+  if (a.n == 1) {
+    // y (m) = op(A) (m x k) * op(B)(:, 0)
+    g.rows = a.m; g.k = a.k;
+    g.M = a.A; g.mdt = a.adt;
+    if (a.ta) { g.rsm = a.lda; g.csm = 1; } else { g.rsm = 1; g.csm = a.lda; }
+    g.x = a.B; g.xdt = a.bdt; g.incx = a.tb ? a.ldb : 1;
+    g.y = a.D; g.incy = 1; g.ydt = a.ddt;
+    g.c = a.C; g.incc = 1; g.cdt = a.cdt;
+    g.rsv = a.rs; g.rs_inc = a.rs_inc; g.rsdt = a.rsdt;
+    g.sv = a.cs; g.svdt = a.csdt;
+  } else {
+    // y^T (n) = op(A)(0, :) (1 x k) * op(B) (k x n)  ->  y_j = sum_l op(B)(l, j) x_l
+    g.rows = a.n; g.k = a.k;
+    g.M = a.B; g.mdt = a.bdt;
+    if (a.tb) { g.rsm = 1; g.csm = a.ldb; } else { g.rsm = a.ldb; g.csm = 1; }
+    g.x = a.A; g.xdt = a.adt; g.incx = a.ta ? 1 : a.lda;
+    g.y = a.D; g.incy = a.ldd; g.ydt = a.ddt;
+    g.c = a.C; g.incc = a.ldc; g.cdt = a.cdt;
+    g.rsv = a.cs; g.rs_inc = a.cs_inc; g.rsdt = a.csdt;
+    g.sv = a.rs; g.svdt = a.rsdt;
+  }
+  cudaError_t e;
+  if (g.rsm == 1 || g.k == 0) {
+    g.splits = g.k == 0 ? 1 : gemv_splits(g.rows, g.k);
+    if (g.splits > 1 && (!a.scratch || a.scratch_bytes < (int64_t)g.splits * g.rows * 8)) g.splits = 1;
+    g.partials = static_cast<double*>(a.scratch);
+    dim3 grid((unsigned)((g.rows + 255) / 256), (unsigned)g.splits);
+    gemv_rows_kernel<<<grid, 256, 0, s>>>(g);
+    if (launches) ++*launches;
+    if (g.splits > 1) {
+      gemv_finish_kernel<<<(unsigned)((g.rows + 255) / 256), 256, 0, s>>>(g);
+      if (launches) ++*launches;
+    }
+  } else {
+    gemv_cols_kernel<<<(unsigned)((g.rows + 7) / 8), 256, 0, s>>>(g);
+    if (launches) ++*launches;
+  }
+  e = cudaGetLastError();
+  return e;
+}
+
+// ---------------------------------------------------------------------------
+// trace(op(A) op(B)) = sum_{i < min(m,n)} sum_l op(A)(i,l) op(B)(l,i).
+// 32 x 32 tiles over (i, l); each operand is loaded along its contiguous
+// index and met in shared memory, so both reads are coalesced.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) diagdot_kernel(const __grid_constant__ DotArgs a) {
+  __shared__ double As[32][33];
+  __shared__ double Bs[32][33];
+  const int64_t d = a.m < a.n ? a.m : a.n;
+  const int64_t ti = (d + 31) / 32, tl = (a.k + 31) / 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  double sum = 0.0;
+  for (int64_t t = blockIdx.x; t < ti * tl; t += gridDim.x) {
+    int64_t i0 = (t % ti) * 32, l0 = (t / ti) * 32;
+    // op(A)(i, l): contiguous along i when A is not transposed
+    for (int r = ty; r < 32; r += 8) {
+      int ii = a.ta ? r : tx, ll = a.ta ? tx : r;
+      int64_t gi = i0 + ii, gl = l0 + ll;
+      double v = 0.0;
+      if (gi < d && gl < a.k) v = load_as<double>(a.A, a.ta ? gl + gi * a.lda : gi + gl * a.lda, a.adt);
+      As[ii][ll] = v;
+      // op(B)(l, i): contiguous along l when B is not transposed
+      ll = a.tb ? r : tx;
+      ii = a.tb ? tx : r;
+      gi = i0 + ii; gl = l0 + ll;
+      double w = 0.0;
+      if (gi < d && gl < a.k) w = load_as<double>(a.B, a.tb ? gi + gl * a.ldb : gl + gi * a.ldb, a.bdt);
+      Bs[ii][ll] = w;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) sum = fma(As[r][tx], Bs[r][tx], sum);
+    __syncthreads();
+  }
+  reduce_finish(sum, 0.0, a.partials, a.ticket, a.out, nullptr, a.alpha);
+}
+
+// ---------------------------------------------------------------------------
+// literal-plan copies
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) transpose_kernel(const __grid_constant__ CopyArgs a) {
+  __shared__ double t[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+  for (int r = ty; r < 32; r += 8) {
+    int64_t i = i0 + tx, j = j0 + r;
+    if (i < a.m && j < a.n) t[r][tx] = load_as<double>(a.src, i + j * a.lds, a.sdt);
+  }
+  __syncthreads();
+  // dst (n x m): dst[j + i*ldd] = src(i, j)
+  for (int r = ty; r < 32; r += 8) {
+    int64_t j = j0 + tx, i = i0 + r;
+    if (i < a.m && j < a.n) store_as<double>(a.dst, j + i * a.ldd, a.ddt, t[tx][r]);
+  }
+}
+
+__global__ void __launch_bounds__(256) diag_build_kernel(const __grid_constant__ CopyArgs a) {
+  int64_t total = a.m * a.n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j = t / a.m, i = t - j * a.m;
+    double v = (i == j) ? load_as<double>(a.src, i * a.inc, a.sdt) : 0.0;
+    store_as<double>(a.dst, i + j * a.ldd, a.ddt, v);
+  }
+}
+
+}  // namespace
+
+int64_t gemm_scratch_bytes(const GemmStep& g) {
+  if (g.n == 1 || g.m == 1) {
+    int64_t rows = g.n == 1 ? g.m : g.n;
+    return 64 * rows * 8;
+  }
+  return gemm_tc_scratch_bytes(g.m, g.n, g.k, g.tier);
+}
+
+cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s, int* launches) {
+  if (a.m == 0 || a.n == 0) return cudaSuccess;
+  if (a.n == 1 || a.m == 1) return launch_gemv(a, s, launches);
+  if (a.tier != ARMA_TIER_F64 && gemm_tc_supported(a)) return launch_gemm_tc(a, s, launches);
+  dim3 grid((unsigned)((a.m + BM - 1) / BM), (unsigned)((a.n + BN - 1) / BN));
+  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+  if (a.tier == ARMA_TIER_F64 || a.adt == ARMA_F64 || a.bdt == ARMA_F64)
+    gemm_simt_kernel<double><<<grid, 256, 0, s>>>(a);
+  else
+    gemm_simt_kernel<float><<<grid, 256, 0, s>>>(a);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diagdot(const DotArgs& a, cudaStream_t s, int* launches) {
+  int64_t d = a.m < a.n ? a.m : a.n;
+  int64_t tiles = ((d + 31) / 32) * ((a.k + 31) / 32);
+  int64_t cap = (int64_t)device_sm_count() * 8;
+  if (cap > kMaxRedBlocks) cap = kMaxRedBlocks;
+  int grid = (int)(tiles < 1 ? 1 : tiles > cap ? cap : tiles);
+  diagdot_kernel<<<grid, 256, 0, s>>>(a);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(const CopyArgs& a, cudaStream_t s, int* launches) {
+  if (a.m == 0 || a.n == 0) return cudaSuccess;
+  dim3 grid((unsigned)((a.m + 31) / 32), (unsigned)((a.n + 31) / 32));
+  transpose_kernel<<<grid, 256, 0, s>>>(a);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_build(const CopyArgs& a, cudaStream_t s, int* launches) {
+  int64_t total = a.m * a.n;
+  if (total == 0) return cudaSuccess;
+  int64_t need = (total + 255) / 256, cap = (int64_t)device_sm_count() * 8;
+  diag_build_kernel<<<(unsigned)(need < cap ? need : cap), 256, 0, s>>>(a);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+}  // namespace arma

@@ -1,0 +1,291 @@
+// K1: fused elementwise pass with optional sum / sum-of-squares reduction.
+//
+// The paper's delayed evaluation turns an elementwise expression into one
+// loop that reads every operand once and writes the result once, with no
+// temporaries (Sec. II, the Z = 0.4*X + 0.6*Y example), vectorised with
+// SIMD (Sec. II, last paragraphs; Sec. III (1)).  Here the expression is a
+// short program for an accumulator machine (EwIns), interpreted per element
+// by every thread; the program is uniform across the grid, so dispatch never
+// diverges.  The flat path loads each operand with two 128-bit loads per
+// thread and iteration (all operands of a chunk are in flight together),
+// runs the program on registers, stores with 128-bit stores and folds
+// accu / norm into the same pass.  A strided path serves transposed views,
+// row/column broadcasts (diagmat(v)*B), diagonal masks and the diagonal-only
+// mode of trace().
+#include <cuda_bf16.h>
+
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace arma {
+
+int device_sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cached[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = n > 0 ? n : 1;
+  }
+  return cached[dev];
+}
+
+namespace {
+
+template <typename CT>
+__device__ __forceinline__ CT ew_in(int op, CT acc, CT x, double s) {
+  switch (op) {
+    case EW_LD: return x;
+    case EW_ADD: return acc + x;
+    case EW_SUB: return acc - x;
+    case EW_RSUB: return x - acc;
+    case EW_MUL: return acc * x;
+    case EW_DIV: return acc / x;
+    case EW_RDIV: return x / acc;
+    case EW_AXPY: return fma((CT)s, x, acc);
+    default: return acc;
+  }
+}
+
+template <typename CT>
+__device__ __forceinline__ CT ew_pop(int op, CT st, CT acc) {
+  switch (op) {
+    case EW_POPADD: return st + acc;
+    case EW_POPSUB: return st - acc;
+    case EW_POPMUL: return st * acc;
+    default: return st / acc;
+  }
+}
+
+template <typename CT>
+__device__ __forceinline__ CT ew_self(int op, CT acc, double s) {
+  switch (op) {
+    case EW_SCAL: return (CT)s * acc;
+    case EW_DIVS: return acc / (CT)s;
+    case EW_ADDS: return acc + (CT)s;
+    default: return -acc;  // EW_NEG
+  }
+}
+
+__device__ __forceinline__ bool uses_operand(int op) { return op <= EW_AXPY; }
+__device__ __forceinline__ bool is_pop(int op) { return op >= EW_POPADD; }
+
+// ---- strided path: one element per step, any operand layout ----
+template <typename CT>
+__global__ void __launch_bounds__(256) ew_strided_kernel(const __grid_constant__ EwArgs a) {
+  int64_t total = a.mode == EW_DIAG ? (a.m < a.n ? a.m : a.n) : a.m * a.n;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  double rs = 0.0, rq = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+    int64_t i, j;
+    if (a.mode == EW_DIAG) { i = t; j = t; }
+    else { j = t / a.m; i = t - j * a.m; }
+    CT acc = 0, s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    for (int pc = 0; pc < a.nops; ++pc) {
+      const int op = a.ops[pc].op, arg = a.ops[pc].arg;
+      const double s = a.ops[pc].s;
+      if (uses_operand(op)) {
+        CT x;
+        if ((a.in_flags[arg] & EWF_DIAGMASK) && i != j) x = 0;
+        else x = load_as<CT>(a.in[arg], i * a.rs[arg] + j * a.cs[arg], a.in_dtype[arg]);
+        acc = ew_in<CT>(op, acc, x, s);
+      } else if (op == EW_PUSH) {
+        if (arg == 0) s0 = acc; else if (arg == 1) s1 = acc; else if (arg == 2) s2 = acc; else s3 = acc;
+      } else if (is_pop(op)) {
+        CT st = arg == 0 ? s0 : arg == 1 ? s1 : arg == 2 ? s2 : s3;
+        acc = ew_pop<CT>(op, st, acc);
+      } else {
+        acc = ew_self<CT>(op, acc, s);
+      }
+    }
+    if (a.out) store_as<CT>(a.out, i + j * a.out_ld, a.out_dtype, acc);
+    if (a.red) {
+      double v = (double)acc;
+      rs += v;
+      rq = fma(v, v, rq);
+    }
+  }
+  if (a.red)
+    reduce_finish(rs, rq, a.partials, a.ticket, (a.red & 1) ? a.sum_out : nullptr,
+                  (a.red & 2) ? a.norm_out : nullptr, 1.0);
+}
+
+// ---- flat path: contiguous operands of one storage type T ----
+template <typename T> struct VecTraits;
+template <> struct VecTraits<double> { static constexpr int V = 4; typedef double CT; };
+template <> struct VecTraits<float> { static constexpr int V = 8; typedef float CT; };
+template <> struct VecTraits<__nv_bfloat16> { static constexpr int V = 8; typedef float CT; };
+
+template <typename T, int V, typename CT>
+__device__ __forceinline__ void load_chunk(const T* __restrict__ p, int64_t c, CT (&x)[V]) {
+  const uint4* q = reinterpret_cast<const uint4*>(p + c * V);
+  constexpr int NV = (V * (int)sizeof(T)) / 16;
+  uint4 r[NV];
+#pragma unroll
+  for (int u = 0; u < NV; ++u) r[u] = __ldcs(q + u);   // streamed: read once
+  const T* e = reinterpret_cast<const T*>(r);
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) x[v] = __bfloat162float(e[v]);
+    else x[v] = (CT)e[v];
+  }
+}
+
+template <typename T, int V, typename CT>
+__device__ __forceinline__ void store_chunk(T* __restrict__ p, int64_t c, const CT (&x)[V]) {
+  constexpr int NV = (V * (int)sizeof(T)) / 16;
+  uint4 r[NV];
+  T* e = reinterpret_cast<T*>(r);
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) e[v] = __float2bfloat16_rn(x[v]);
+    else e[v] = (T)x[v];
+  }
+  uint4* q = reinterpret_cast<uint4*>(p + c * V);
+#pragma unroll
+  for (int u = 0; u < NV; ++u) __stcs(q + u, r[u]);
+}
+
+template <typename T, int NIN>
+__global__ void __launch_bounds__(256) ew_flat_kernel(const __grid_constant__ EwArgs a) {
+  constexpr int V = VecTraits<T>::V;
+  typedef typename VecTraits<T>::CT CT;
+  const int64_t total = a.m * a.n;
+  const int64_t nchunk = total / V;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  double rs = 0.0, rq = 0.0;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunk; c += stride) {
+    CT x[NIN][V];
+#pragma unroll
+    for (int k = 0; k < NIN; ++k) load_chunk<T, V, CT>(static_cast<const T*>(a.in[k]), c, x[k]);
+    CT acc[V], st[kMaxStack][V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0;
+    for (int pc = 0; pc < a.nops; ++pc) {
+      const int op = a.ops[pc].op, arg = a.ops[pc].arg;
+      const double s = a.ops[pc].s;
+      if (uses_operand(op)) {
+#pragma unroll
+        for (int k = 0; k < NIN; ++k)
+          if (k == arg) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = ew_in<CT>(op, acc[v], x[k][v], s);
+          }
+      } else if (op == EW_PUSH) {
+#pragma unroll
+        for (int q = 0; q < kMaxStack; ++q)
+          if (q == arg) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) st[q][v] = acc[v];
+          }
+      } else if (is_pop(op)) {
+#pragma unroll
+        for (int q = 0; q < kMaxStack; ++q)
+          if (q == arg) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = ew_pop<CT>(op, st[q][v], acc[v]);
+          }
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = ew_self<CT>(op, acc[v], s);
+      }
+    }
+    if (a.out) store_chunk<T, V, CT>(static_cast<T*>(a.out), c, acc);
+    if (a.red) {
+      CT ps = 0, pq = 0;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        ps += acc[v];
+        pq = fma(acc[v], acc[v], pq);
+      }
+      rs += (double)ps;
+      rq += (double)pq;
+    }
+  }
+  // ragged tail: the last total % V elements, one per thread
+  for (int64_t t = nchunk * V + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+    CT acc = 0, s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    for (int pc = 0; pc < a.nops; ++pc) {
+      const int op = a.ops[pc].op, arg = a.ops[pc].arg;
+      const double s = a.ops[pc].s;
+      if (uses_operand(op)) {
+        CT x = load_as<CT>(a.in[arg], t, a.in_dtype[arg]);
+        acc = ew_in<CT>(op, acc, x, s);
+      } else if (op == EW_PUSH) {
+        if (arg == 0) s0 = acc; else if (arg == 1) s1 = acc; else if (arg == 2) s2 = acc; else s3 = acc;
+      } else if (is_pop(op)) {
+        CT stv = arg == 0 ? s0 : arg == 1 ? s1 : arg == 2 ? s2 : s3;
+        acc = ew_pop<CT>(op, stv, acc);
+      } else {
+        acc = ew_self<CT>(op, acc, s);
+      }
+    }
+    if (a.out) store_as<CT>(a.out, t, a.out_dtype, acc);
+    if (a.red) {
+      double v = (double)acc;
+      rs += v;
+      rq = fma(v, v, rq);
+    }
+  }
+  if (a.red)
+    reduce_finish(rs, rq, a.partials, a.ticket, (a.red & 1) ? a.sum_out : nullptr,
+                  (a.red & 2) ? a.norm_out : nullptr, 1.0);
+}
+
+template <typename T>
+cudaError_t launch_flat_t(const EwArgs& a, int grid, cudaStream_t s) {
+  switch (a.nin) {
+#define ARMA_EW_CASE(N) \
+  case N: ew_flat_kernel<T, N><<<grid, 256, 0, s>>>(a); break;
+    ARMA_EW_CASE(1) ARMA_EW_CASE(2) ARMA_EW_CASE(3) ARMA_EW_CASE(4)
+    ARMA_EW_CASE(5) ARMA_EW_CASE(6) ARMA_EW_CASE(7) ARMA_EW_CASE(8)
+#undef ARMA_EW_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+}  // namespace
+
+cudaError_t launch_ew(const EwArgs& a, cudaStream_t s, int* launches) {
+  const int64_t total = a.mode == EW_DIAG ? (a.m < a.n ? a.m : a.n) : a.m * a.n;
+  if (total == 0 && !a.red) return cudaSuccess;
+  if (a.nin < 1 || a.nin > kMaxIn) return cudaErrorInvalidValue;
+  const int sms = device_sm_count();
+  // flat fast path: one storage type, 16-byte aligned, contiguous
+  bool flat = a.mode == EW_FLAT;
+  int dt = a.in_dtype[0];
+  if (flat) {
+    for (int k = 0; k < a.nin; ++k) flat &= a.in_dtype[k] == dt && al16(a.in[k]) && a.in_flags[k] == 0;
+    if (a.out) flat &= a.out_dtype == dt && al16(a.out);
+    flat &= (a.compute_f64 != 0) == (dt == ARMA_F64);
+  }
+  const int per_sm = 8;  // 256-thread blocks resident per SM at full occupancy
+  int64_t work = total;
+  if (flat) work = total / (dt == ARMA_F64 ? 4 : 8) + 1;
+  int64_t need = (work + 255) / 256;
+  int64_t cap = (int64_t)sms * per_sm;
+  if (cap > kMaxRedBlocks) cap = kMaxRedBlocks;
+  int grid = (int)(need < 1 ? 1 : need > cap ? cap : need);
+  cudaError_t e;
+  if (flat) {
+    e = dt == ARMA_F64 ? launch_flat_t<double>(a, grid, s)
+        : dt == ARMA_F32 ? launch_flat_t<float>(a, grid, s)
+                         : launch_flat_t<__nv_bfloat16>(a, grid, s);
+  } else if (a.compute_f64) {
+    ew_strided_kernel<double><<<grid, 256, 0, s>>>(a);
+    e = cudaGetLastError();
+  } else {
+    ew_strided_kernel<float><<<grid, 256, 0, s>>>(a);
+    e = cudaGetLastError();
+  }
+  if (launches) ++*launches;
+  return e;
+}
+
+}  // namespace arma

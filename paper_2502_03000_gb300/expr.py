@@ -1,0 +1,154 @@
+"""Build expression descriptors with Armadillo-like operators.
+
+    g = Graph()
+    A = g.input(0, m, n); B = g.input(1, m, n)
+    Z = 0.4 * A + 0.6 * B              # elementwise (Sec. II example)
+    k = trace(A @ B.t())                 # '@' is the matrix product, '%' Schur
+    nodes, outputs = g.build(Z, k)
+
+The result is the plain node-dict list that ``Plan`` (and the tests'
+oracle) consume.  Nothing is evaluated here: this is the delayed-evaluation
+tree of Sec. II written down as data.
+"""
+from __future__ import annotations
+
+
+class Graph:
+    def __init__(self):
+        self.nodes: list[dict] = []
+
+    def _add(self, d: dict) -> "X":
+        self.nodes.append(d)
+        return X(self, len(self.nodes) - 1)
+
+    def input(self, slot: int, rows: int, cols: int, dtype: str = "f64", ld: int | None = None) -> "X":
+        return self._add({"op": "input", "slot": slot, "rows": rows, "cols": cols, "dtype": dtype,
+                          "ld": ld if ld is not None else max(1, rows)})
+
+    def build(self, *outs: "X"):
+        return [dict(d) for d in self.nodes], [o.i for o in outs]
+
+
+class X:
+    __array_priority__ = 1000
+
+    def __init__(self, g: Graph, i: int):
+        self.g, self.i = g, i
+
+    def _bin(self, op, other):
+        return self.g._add({"op": op, "a": self.i, "b": other.i})
+
+    def __add__(self, o):
+        if isinstance(o, X):
+            return self._bin("add", o)
+        return self.g._add({"op": "add_scalar", "a": self.i, "s": float(o)})
+
+    __radd__ = __add__
+
+    def __sub__(self, o):
+        if isinstance(o, X):
+            return self._bin("sub", o)
+        return self.g._add({"op": "add_scalar", "a": self.i, "s": -float(o)})
+
+    def __neg__(self):
+        return self.g._add({"op": "neg", "a": self.i})
+
+    def __mul__(self, o):
+        if isinstance(o, X):
+            return self._bin("matmul", o)   # Armadillo: '*' between matrices is the product
+        return self.g._add({"op": "scale", "a": self.i, "s": float(o)})
+
+    def __rmul__(self, s):
+        return self.g._add({"op": "scale", "a": self.i, "s": float(s)})
+
+    def __matmul__(self, o):
+        return self._bin("matmul", o)
+
+    def __mod__(self, o):
+        return self._bin("schur", o)
+
+    def __truediv__(self, o):
+        if isinstance(o, X):
+            return self._bin("div", o)
+        return self.g._add({"op": "div_scalar", "a": self.i, "s": float(o)})
+
+    def t(self):
+        return self.g._add({"op": "trans", "a": self.i})
+
+
+def trans(x: X) -> X:
+    return x.t()
+
+
+def diagmat(x: X) -> X:
+    return x.g._add({"op": "diagmat", "a": x.i})
+
+
+def trace(x: X) -> X:
+    return x.g._add({"op": "trace", "a": x.i})
+
+
+def accu(x: X) -> X:
+    return x.g._add({"op": "accu", "a": x.i})
+
+
+def norm_fro(x: X) -> X:
+    return x.g._add({"op": "norm_fro", "a": x.i})
+
+
+def inv(x: X) -> X:
+    return x.g._add({"op": "inv", "a": x.i})
+
+
+# ---- the benchmark expressions (seeded shapes; names follow the paper) ----
+
+def config_plain(n: int = 256, dtype: str = "f64"):
+    """The six expressions over A, B, C, D (n x n) and v (n): C+A-2*D+B%D,
+    trans(A)*B, 2*A*B+C, trace(A*B), diagmat(v)*B, accu(A%B).  Slots:
+    A=0, B=1, C=2, D=3, v=4."""
+    out = {}
+    for name in ("ew", "transAB", "2AB+C", "traceAB", "diagvB", "accuAoB"):
+        g = Graph()
+        A, B, C, D = (g.input(s, n, n, dtype) for s in range(4))
+        v = g.input(4, n, 1, dtype)
+        e = {"ew": lambda: C + A - 2 * D + B % D,
+             "transAB": lambda: A.t() * B,
+             "2AB+C": lambda: 2 * A * B + C,
+             "traceAB": lambda: trace(A * B),
+             "diagvB": lambda: diagmat(v) * B,
+             "accuAoB": lambda: accu(A % B)}[name]()
+        out[name] = g.build(e)
+    return out
+
+
+def config_fused(n: int = 8192, dtype: str = "f32"):
+    """out = A%B + 3*C - D/2 with accu(out) and norm(out,'fro'); slots A..D = 0..3."""
+    g = Graph()
+    A, B, C, D = (g.input(s, n, n, dtype) for s in range(4))
+    out = A % B + 3 * C - D / 2
+    return g.build(out, accu(out), norm_fro(out))
+
+
+def config_products(n: int = 8192, dtype: str = "f64"):
+    """2*trans(A)*B + C (slots A=0, B=1, C=2)."""
+    g = Graph()
+    A, B, C = (g.input(s, n, n, dtype) for s in range(3))
+    return g.build(2 * A.t() * B + C)
+
+
+def config_chain(dims=(4096, 8192, 512, 4096, 1), dtype: str = "f64"):
+    """A*B*C*v with A dims[0]xdims[1], ... (slots 0..3)."""
+    g = Graph()
+    Ms = [g.input(s, dims[s], dims[s + 1], dtype) for s in range(len(dims) - 1)]
+    e = Ms[0]
+    for M in Ms[1:]:
+        e = e * M
+    return g.build(e)
+
+
+def config_solve(n: int = 4096, nrhs: int = 64, dtype: str = "f64"):
+    """inv(A)*B (slots A=0, B=1)."""
+    g = Graph()
+    A = g.input(0, n, n, dtype)
+    B = g.input(1, n, nrhs, dtype)
+    return g.build(inv(A) * B)

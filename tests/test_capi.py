@@ -1,0 +1,161 @@
+"""Host-side tests of the C-ABI library (no GPU): it loads, exports every
+symbol the header declares, validates descriptors (the paper's conformance
+checks, Sec. II), orders matrix chains exactly like exhaustive search, and
+plans the paper's rewrites onto the expected kernels."""
+import ctypes
+import os
+import random
+import re
+
+import pytest
+
+import paper_2502_03000_gb300 as ag
+from paper_2502_03000_gb300 import expr as E
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2502_03000_gb300 import build
+    build.build()
+    ag.lib.cache_clear()
+
+
+def test_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "arma_gpu.h")).read()
+    declared = set(re.findall(r"\b(arma_gpu_\w+)\s*\(", hdr))
+    assert declared, "no declarations found"
+    L = ag.lib()
+    for name in sorted(declared):
+        assert hasattr(L, name), name
+    assert set(ag.EXPORTS) <= declared
+
+
+def test_status_strings():
+    L = ag.lib()
+    for code in range(10):
+        assert L.arma_gpu_status_string(code)
+
+
+def _plan_err(nodes, outputs, **kw):
+    with pytest.raises(ag.ArmaError) as ei:
+        ag.Plan(nodes, outputs, **kw)
+    return ei.value.status
+
+
+def test_conformance_errors():
+    g = E.Graph()
+    A = g.input(0, 4, 5); B = g.input(1, 5, 4)
+    assert _plan_err(*g.build(A + B)) == "shape"
+    g = E.Graph()
+    A = g.input(0, 4, 5); B = g.input(1, 4, 5)
+    assert _plan_err(*g.build(A * B)) == "shape"
+    g = E.Graph()
+    A = g.input(0, 4, 4, "f64"); B = g.input(1, 4, 4, "f32")
+    assert _plan_err(*g.build(A % B)) == "dtype"
+    g = E.Graph()
+    A = g.input(0, 3, 4)
+    assert _plan_err(*g.build(E.inv(A))) == "shape"
+    # operand indices must point backwards
+    assert _plan_err([{"op": "add", "a": 0, "b": 1}], [0]) == "invalid"
+    assert _plan_err([{"op": "input", "slot": 0, "rows": 4, "cols": 4, "ld": 2}], [0]) == "shape"
+    # a scalar cannot feed another operation
+    g = E.Graph()
+    A = g.input(0, 3, 3)
+    t = E.trace(A)
+    nodes, _ = g.build(t)
+    nodes.append({"op": "neg", "a": len(nodes) - 1})
+    assert _plan_err(nodes, [len(nodes) - 1]) == "unsupported"
+
+
+def test_workspace_and_outputs():
+    nodes, outs = E.config_fused(64, "f32")
+    p = ag.Plan(nodes, outs)
+    assert p.workspace_bytes >= 4096 and p.workspace_bytes % 256 == 0
+    assert p.out_info[0][:3] == (64, 64, ag.F32)
+    assert p.out_info[1][3] and p.out_info[2][3]
+
+
+# ---------------------------------------------------------------- chains
+
+def _splits_to_tree(splits, n):
+    return ag.tree_from_splits(splits, 0, n - 1)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_chain_dp_equals_exhaustive(orc, seed):
+    rnd = random.Random(seed)
+    n = rnd.randint(1, 9)
+    dims = [rnd.choice([1, 2, 3, 5, 8, 13, 64, 100, 512, 4096]) for _ in range(n + 1)]
+    splits, cost = ag.chain_order(dims, 0)
+    if n == 1:
+        assert cost == 0
+        return
+    best_cost, best_tree = orc.chain_exhaustive(dims)
+    assert cost == best_cost
+    assert _splits_to_tree(splits, n) == best_tree
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_chain_greedy_and_left_match_oracle(orc, seed):
+    rnd = random.Random(100 + seed)
+    n = rnd.randint(2, 8)
+    dims = [rnd.randint(1, 300) for _ in range(n + 1)]
+    s1, c1 = ag.chain_order(dims, 1)
+    t1 = orc.chain_paper_greedy(dims)
+    assert _splits_to_tree(s1, n) == t1 and c1 == orc.tree_cost(t1, dims)
+    s2, c2 = ag.chain_order(dims, 2)
+    t2 = orc.chain_left_to_right(n)
+    assert _splits_to_tree(s2, n) == t2 and c2 == orc.tree_cost(t2, dims)
+
+
+def test_chain_benchmark_dims():
+    splits, cost = ag.chain_order([4096, 8192, 512, 4096, 1], 0)
+    assert cost == 39845888 and _splits_to_tree(splits, 4) == (0, 0, (1, 1, (2, 2, 3)))
+    _, left = ag.chain_order([4096, 8192, 512, 4096, 1], 2)
+    assert left == 25786580992
+
+
+# ---------------------------------------------------------------- rewrites
+
+def kernels(p):
+    return [s["kernel"] for s in p.info["steps"]]
+
+
+def test_rewrites_config_plain():
+    ex = E.config_plain(256)
+    k = {name: kernels(ag.Plan(*ex[name])) for name in ex}
+    assert k["ew"] == ["ew"]                       # one fused pass, no temporaries
+    assert k["transAB"] == ["gemm"]                # transpose folded into the product
+    assert k["2AB+C"] == ["gemm"]                  # alpha and beta*C in the epilogue
+    assert k["traceAB"] == ["diagdot"]             # diagonal-only product
+    assert k["diagvB"] == ["ew"]                   # row scaling, no dense diagonal
+    assert k["accuAoB"] == ["ew"]                  # product and sum in one pass, no store
+    lit = {name: kernels(ag.Plan(*ex[name], flags=ag.PLAN_LITERAL)) for name in ex}
+    assert lit["ew"] == ["ew"] * 5
+    assert lit["transAB"] == ["transpose", "gemm"]
+    assert lit["2AB+C"] == ["ew", "gemm", "ew"]
+    assert lit["traceAB"] == ["gemm", "ew"]
+    assert lit["diagvB"] == ["diagbuild", "gemm"]
+    assert lit["accuAoB"] == ["ew", "ew"]
+
+
+def test_rewrites_fused_and_chain_and_solve():
+    p = ag.Plan(*E.config_fused(128))
+    assert kernels(p) == ["ew"]
+    assert "+sum" in p.info["steps"][0]["note"] and "+sumsq" in p.info["steps"][0]["note"]
+    assert kernels(ag.Plan(*E.config_fused(128), flags=ag.PLAN_LITERAL)) == ["ew"] * 7
+    p = ag.Plan(*E.config_chain((40, 80, 5, 40, 1)))
+    notes = [s["note"] for s in p.info["steps"]]
+    assert kernels(p) == ["gemm"] * 3 and all(n.startswith("gemv") for n in notes)
+    assert p.info["flops"] == 2 * (5 * 40 + 80 * 5 + 40 * 80)
+    p = ag.Plan(*E.config_solve(64, 3))
+    assert kernels(p) == ["solve"]
+    assert kernels(ag.Plan(*E.config_solve(64, 3), flags=ag.PLAN_LITERAL)) == ["solve", "gemm"]
+
+
+def test_plan_info_is_json():
+    p = ag.Plan(*E.config_products(256))
+    info = p.info
+    assert info["mode"] == "optimised" and info["steps"][0]["flops"] == 2 * 256 ** 3

@@ -1,0 +1,185 @@
+"""Parity of the CUDA path with the CPU FP64 oracle, element by element, on
+seeded inputs: the paper's expressions (Sec. III), the fused benchmark
+expression, folded transposes / scalars / diagonals, chains, and the edge
+cases (empty, 1 x 1, ragged, padded leading dimensions, misaligned
+pointers).  Every call goes through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2502_03000_gb300 as ag
+import synth
+from paper_2502_03000_gb300 import expr as E
+from tests.gpu_util import TOL, check, inputs, need_gpu, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return need_gpu()
+
+
+def run(nodes, outs, host, dtype, flags=0, tier="native", **kw):
+    plan = ag.Plan(nodes, outs, tier=tier, flags=flags)
+    ins = [to_dev(h, dtype, **kw) for h in host]
+    got = plan(*ins)
+    import torch as T
+    T.cuda.synchronize()
+    return got
+
+
+def plain_inputs(seed, n, dtype):
+    return inputs(seed, [(n, n)] * 4 + [(n, 1)], dtype)
+
+
+@pytest.mark.parametrize("n", [1, 2, 37, 130, 256])
+@pytest.mark.parametrize("flags", [0, ag.PLAN_LITERAL, ag.PLAN_NO_FUSE])
+def test_plain_expressions_f64(torch, n, flags):
+    host = plain_inputs(11 + n, n, "f64")
+    for name, (nodes, outs) in E.config_plain(n, "f64").items():
+        got = run(nodes, outs, host, "f64", flags)
+        check(got, oracle.evaluate(nodes, outs, host), TOL["f64"], f"{name} n={n} flags={flags}")
+
+
+@pytest.mark.parametrize("n", [33, 256])
+def test_plain_expressions_f32(torch, n):
+    host = plain_inputs(21, n, "f32")
+    for name, (nodes, outs) in E.config_plain(n, "f32").items():
+        for flags in (0, ag.PLAN_LITERAL):
+            got = run(nodes, outs, host, "f32", flags)
+            check(got, oracle.evaluate(nodes, outs, host), TOL["f32"], f"{name} f32 flags={flags}")
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("shape", [(257, 263), (1, 1), (8, 8), (1000, 3), (3, 1000)])
+@pytest.mark.parametrize("flags", [0, ag.PLAN_LITERAL])
+def test_fused_expression(torch, dtype, shape, flags):
+    m, n = shape
+    g = E.Graph()
+    A, B, C, D = (g.input(s, m, n, dtype) for s in range(4))
+    out = A % B + 3 * C - D / 2
+    nodes, outs = g.build(out, E.accu(out), E.norm_fro(out))
+    host = inputs(31, [shape] * 4, dtype)
+    got = run(nodes, outs, host, dtype, flags)
+    ref = oracle.evaluate(nodes, outs, host)
+    tol = TOL[dtype]
+    check(got[:1], ref[:1], tol, f"out {dtype} {shape}")
+    # the reductions of a BF16-stored result are computed from the
+    # unrounded values when fused; BF16-rounded temporaries in the literal plan
+    tol_red = TOL["f32"] if (dtype == "bf16" and flags == 0) else tol
+    check(got[1:], ref[1:], tol_red, f"reductions {dtype} {shape}")
+
+
+@pytest.mark.parametrize("layout", [dict(pad=3), dict(offset=1), dict(pad=5, offset=3)])
+def test_fused_padded_and_misaligned(torch, layout):
+    m, n = 129, 67
+    g = E.Graph()
+    ld = m + layout.get("pad", 0)
+    A, B, C, D = (g.input(s, m, n, "f64", ld=ld) for s in range(4))
+    out = A % B + 3 * C - D / 2
+    nodes, outs = g.build(out, E.accu(out))
+    host = inputs(41, [(m, n)] * 4, "f64")
+    got = run(nodes, outs, host, "f64", **layout)
+    check(got, oracle.evaluate(nodes, outs, host), TOL["f64"], str(layout))
+
+
+def test_empty_inputs(torch):
+    g = E.Graph()
+    A, B = g.input(0, 0, 5), g.input(1, 0, 5)
+    out = A + B
+    nodes, outs = g.build(out, E.accu(out), E.norm_fro(out))
+    host = [np.zeros((0, 5)), np.zeros((0, 5))]
+    plan = ag.Plan(nodes, outs)
+    import torch as T
+    ins = [T.zeros((5, 1), dtype=T.float64, device="cuda").t()[:0, :] for _ in range(2)]
+    got = plan(*ins)
+    T.cuda.synchronize()
+    assert got[0].shape == (0, 5)
+    assert to_host(got[1]) == 0.0 and to_host(got[2]) == 0.0
+
+
+def test_elementwise_views(torch):
+    """transposed operands, diagonal masks, broadcasts and trace of an
+    elementwise expression (the strided and diagonal modes of the fused pass)"""
+    m = 45
+    g = E.Graph()
+    A, B = g.input(0, m, m), g.input(1, m, m)
+    v = g.input(2, m, 1)
+    e1 = A + B.t()
+    e2 = E.diagmat(A) + 2 * B
+    e3 = E.trace(A % B - 3 * A)
+    e4 = E.diagmat(v) - A
+    nodes, outs = g.build(e1, e2, e3, e4)
+    host = inputs(51, [(m, m), (m, m), (m, 1)], "f64")
+    for flags in (0, ag.PLAN_LITERAL):
+        got = run(nodes, outs, host, "f64", flags)
+        check(got, oracle.evaluate(nodes, outs, host), TOL["f64"], f"views flags={flags}")
+
+
+@pytest.mark.parametrize("ta,tb", [(0, 0), (1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("mnk", [(64, 64, 64), (70, 33, 129), (1, 40, 17), (40, 1, 17), (3, 5, 1)])
+def test_products_folded(torch, ta, tb, mnk):
+    m, n, k = mnk
+    g = E.Graph()
+    A = g.input(0, k, m) if ta else g.input(0, m, k)
+    B = g.input(1, n, k) if tb else g.input(1, k, n)
+    C = g.input(2, m, n)
+    r, c = g.input(3, m, 1), g.input(4, n, 1)
+    opA = A.t() if ta else A
+    opB = B.t() if tb else B
+    e1 = 2 * opA * opB + C
+    e2 = E.diagmat(r) * (opA * opB) * E.diagmat(c)
+    e3 = -(opA * opB) / 4 - C
+    e4 = E.trace(opA * opB * E.trans(C))
+    nodes, outs = g.build(e1, e2, e3, e4)
+    shapes = [(k, m) if ta else (m, k), (n, k) if tb else (k, n), (m, n), (m, 1), (n, 1)]
+    host = inputs(61 + m + n + k, shapes, "f64")
+    for flags in (0, ag.PLAN_LITERAL):
+        got = run(nodes, outs, host, "f64", flags)
+        check(got, oracle.evaluate(nodes, outs, host), TOL["f64"], f"products {ta}{tb} {mnk} {flags}")
+
+
+@pytest.mark.parametrize("ta,tb", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_trace_of_product(torch, ta, tb):
+    for (m, k, n) in [(50, 70, 50), (33, 7, 40), (1, 9, 1), (129, 257, 100)]:
+        g = E.Graph()
+        A = g.input(0, k, m) if ta else g.input(0, m, k)
+        B = g.input(1, n, k) if tb else g.input(1, k, n)
+        e = E.trace(0.5 * (A.t() if ta else A) * (B.t() if tb else B))
+        nodes, outs = g.build(e)
+        shapes = [(k, m) if ta else (m, k), (n, k) if tb else (k, n)]
+        host = inputs(71 + m, shapes, "f64")
+        got = run(nodes, outs, host, "f64")
+        check(got, oracle.evaluate(nodes, outs, host), TOL["f64"], f"trace {ta}{tb} {(m, k, n)}")
+
+
+@pytest.mark.parametrize("dims", [(40, 80, 5, 40, 1), (12, 12, 6, 4, 3), (7, 1, 9, 2)])
+@pytest.mark.parametrize("flags", [0, ag.PLAN_CHAIN_LEFT, ag.PLAN_CHAIN_GREEDY, ag.PLAN_LITERAL])
+def test_chains(torch, dims, flags):
+    nodes, outs = E.config_chain(dims, "f64")
+    host = inputs(81, [(dims[i], dims[i + 1]) for i in range(len(dims) - 1)], "f64")
+    got = run(nodes, outs, host, "f64", flags)
+    check(got, oracle.evaluate(nodes, outs, host), TOL["f64"], f"chain {dims} {flags}")
+
+
+def test_deterministic(torch):
+    nodes, outs = E.config_fused(1031, "f32")
+    host = inputs(91, [(1031, 1031)] * 4, "f32")
+    a = run(nodes, outs, host, "f32")
+    b = run(nodes, outs, host, "f32")
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_fused_full_size(torch, dtype):
+    """The benchmark workload at its full size (8192 x 8192), in the launch
+    configuration the benchmark times, against the oracle's literal
+    evaluation of the same inputs."""
+    n = 8192
+    nodes, outs = E.config_fused(n, dtype)
+    host = inputs(20250203 + 2, [(n, n)] * 4, dtype)
+    got = run(nodes, outs, host, dtype)
+    ref = oracle.evaluate(nodes, outs, host)
+    check(got, ref, TOL[dtype], f"full size {dtype}")
