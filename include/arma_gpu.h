@@ -172,6 +172,29 @@ void arma_gpu_plan_free(arma_plan* plan);
 
 const char* arma_gpu_status_string(arma_status status);
 
+/* Size of the library-owned scratch array used by arma_gpu_eval_fused_static. */
+#define ARMA_STATIC_SCRATCH_BYTES 131072
+
+/* Evaluate a plan without any caller workspace, for callers that cannot
+ * allocate device memory (a plug-in that receives only raw input and
+ * output pointers, code inside another framework's memory pool, loops that
+ * cannot afford cudaMalloc's implicit synchronisation).  The paper has no
+ * counterpart to this call.
+ *
+ * Only plans made entirely of fused elementwise passes (elementwise
+ * expressions, with accu / norm_fro / trace of them) are accepted, and only
+ * if arma_gpu_plan_workspace() <= ARMA_STATIC_SCRATCH_BYTES; otherwise the
+ * call returns ARMA_ERR_UNSUPPORTED or ARMA_ERR_WORKSPACE and launches
+ * nothing.  The scratch lives in one file-scope device array of
+ * ARMA_STATIC_SCRATCH_BYTES per GPU, held until the process exits.  The
+ * first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  The
+ * call allocates nothing.  Every call shares the array: calls whose kernels
+ * overlap on the GPU (different streams, or other threads) race on it.
+ * in_ptrs, out_ptrs and stream mean the same as in arma_gpu_eval. */
+arma_status arma_gpu_eval_fused_static(const arma_plan* plan, const void* const* in_ptrs,
+                                       void* const* out_ptrs, void* stream);
+
 /* Matrix-chain ordering used by the planner (Sec. II, chain paragraph;
  * Sec. III (6)).  dims[0..n] give factor t as dims[t] x dims[t+1].
  * method 0: exact minimum number of scalar multiply-adds (dynamic

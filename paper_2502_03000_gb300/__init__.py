@@ -64,7 +64,8 @@ class Expr(ctypes.Structure):
 
 EXPORTS = ["arma_gpu_plan", "arma_gpu_plan_workspace", "arma_gpu_output_info", "arma_gpu_eval",
            "arma_gpu_eval_status", "arma_gpu_plan_info", "arma_gpu_plan_free",
-           "arma_gpu_status_string", "arma_gpu_chain_order"]
+           "arma_gpu_status_string", "arma_gpu_chain_order", "arma_gpu_eval_fused_static"]
+STATIC_SCRATCH_BYTES = 131072
 
 
 @lru_cache(maxsize=1)
@@ -85,9 +86,7 @@ def lib() -> ctypes.CDLL:
     L.arma_gpu_status_string.restype = ctypes.c_char_p
     L.arma_gpu_chain_order.argtypes = [i32, ctypes.POINTER(i64), i32, ctypes.POINTER(i32),
                                        ctypes.POINTER(ctypes.c_uint64)]
-    for n in EXPORTS:
-        if getattr(L, n).restype is ctypes.c_int:
-            getattr(L, n).restype = ctypes.c_int
+    L.arma_gpu_eval_fused_static.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
     return L
 
 
@@ -221,6 +220,19 @@ class Plan:
         st = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
         _check(lib().arma_gpu_eval(self._h, ins, outs, ctypes.c_void_p(workspace.data_ptr()),
                                    workspace.numel(), ctypes.c_void_p(st)), "arma_gpu_eval")
+        return outputs
+
+    def call_static(self, *inputs, outputs=None, stream=None):
+        """Evaluate with the library's own static scratch instead of a
+        workspace (fused elementwise plans only; see arma_gpu_eval_fused_static)."""
+        import torch
+        dev = inputs[0].device if inputs else torch.device("cuda")
+        if outputs is None:
+            outputs = self.alloc_outputs(dev)
+        ins, outs = self.pointers(inputs, outputs)
+        st = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+        _check(lib().arma_gpu_eval_fused_static(self._h, ins, outs, ctypes.c_void_p(st)),
+               "arma_gpu_eval_fused_static")
         return outputs
 
     def status(self, workspace=None, stream=None):
