@@ -113,6 +113,56 @@ __global__ void __launch_bounds__(256) ew_strided_kernel(const __grid_constant__
                   (a.red & 2) ? a.norm_out : nullptr, 1.0);
 }
 
+// ---- exact float-float accumulation for FP64 reductions ----
+// GB300 issues FP64 at a small fraction of its FP32 rate, so the two
+// running sums of an FP64 pass (sum, sum of squares) are kept as unevaluated
+// float pairs (hi + lo, about 48 significant bits) on the FP32 pipes: Knuth's
+// two-sum for additions, an FMA-exact product for squares.  The double is
+// split into its pair with integer operations only.  Values outside the
+// pair's exponent range take the FP64 route.
+__device__ __forceinline__ bool split_ff(double x, float& hi, float& lo) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned int e = (unsigned int)(u >> 52) & 0x7ffu;
+  if (e == 0u && (u << 1) == 0ull) { hi = 0.f; lo = 0.f; return true; }  // +-0
+  if (e < 949u || e > 1150u) return false;            // hi or the lo scale would leave float range
+  const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
+  const unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
+  hi = __uint_as_float(sign | ((e - 896u) << 23) | (unsigned int)(mant >> 29));
+  const float rf = __uint2float_rn((unsigned int)(mant & 0x1FFFFFFFull));  // low 29 bits
+  const float scale = __uint_as_float((e - 948u) << 23);                  // 2^(e-1075)
+  lo = __fmul_rn(sign ? -rf : rf, scale);
+  return true;
+}
+
+__device__ __forceinline__ void ff_add(float& sh, float& sl, float xh, float xl) {
+  const float s = __fadd_rn(sh, xh);
+  const float bb = __fsub_rn(s, sh);
+  float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(xh, bb));
+  e = __fadd_rn(e, __fadd_rn(sl, xl));
+  sh = __fadd_rn(s, e);
+  sl = __fsub_rn(e, __fsub_rn(sh, s));
+}
+
+struct FFAcc {
+  float sh = 0.f, sl = 0.f, qh = 0.f, ql = 0.f;
+  double s64 = 0.0, q64 = 0.0;  // values outside the pair's range
+  __device__ __forceinline__ void add(double x) {
+    float hi, lo;
+    if (split_ff(x, hi, lo)) {
+      ff_add(sh, sl, hi, lo);
+      const float p = __fmul_rn(hi, hi);
+      float pe = __fmaf_rn(hi, hi, -p);
+      pe = __fmaf_rn(__fmul_rn(2.f, hi), lo, pe);
+      ff_add(qh, ql, p, pe);
+    } else {
+      s64 += x;
+      q64 = fma(x, x, q64);
+    }
+  }
+  __device__ __forceinline__ double sum() const { return ((double)sh + (double)sl) + s64; }
+  __device__ __forceinline__ double sumsq() const { return ((double)qh + (double)ql) + q64; }
+};
+
 // ---- flat path: contiguous operands of one storage type T ----
 template <typename T> struct VecTraits;
 template <> struct VecTraits<double> { static constexpr int V = 4; typedef double CT; };
@@ -149,19 +199,23 @@ __device__ __forceinline__ void store_chunk(T* __restrict__ p, int64_t c, const 
   for (int u = 0; u < NV; ++u) __stcs(q + u, r[u]);
 }
 
-template <typename T, int NIN>
-__global__ void __launch_bounds__(256) ew_flat_kernel(const __grid_constant__ EwArgs a) {
+// STK: spill slots the program may use (0 when it never pushes), so that
+// programs without spills do not hold dead registers.
+template <typename T, int NIN, int STK>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) ew_flat_kernel(const __grid_constant__ EwArgs a) {
   constexpr int V = VecTraits<T>::V;
   typedef typename VecTraits<T>::CT CT;
+  constexpr bool kFF = std::is_same<T, double>::value;
   const int64_t total = a.m * a.n;
   const int64_t nchunk = total / V;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   double rs = 0.0, rq = 0.0;
+  FFAcc ff;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunk; c += stride) {
     CT x[NIN][V];
 #pragma unroll
     for (int k = 0; k < NIN; ++k) load_chunk<T, V, CT>(static_cast<const T*>(a.in[k]), c, x[k]);
-    CT acc[V], st[kMaxStack][V];
+    CT acc[V], st[STK > 0 ? STK : 1][V];
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = 0;
     for (int pc = 0; pc < a.nops; ++pc) {
@@ -176,14 +230,14 @@ __global__ void __launch_bounds__(256) ew_flat_kernel(const __grid_constant__ Ew
           }
       } else if (op == EW_PUSH) {
 #pragma unroll
-        for (int q = 0; q < kMaxStack; ++q)
+        for (int q = 0; q < STK; ++q)
           if (q == arg) {
 #pragma unroll
             for (int v = 0; v < V; ++v) st[q][v] = acc[v];
           }
       } else if (is_pop(op)) {
 #pragma unroll
-        for (int q = 0; q < kMaxStack; ++q)
+        for (int q = 0; q < STK; ++q)
           if (q == arg) {
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] = ew_pop<CT>(op, st[q][v], acc[v]);
@@ -195,15 +249,24 @@ __global__ void __launch_bounds__(256) ew_flat_kernel(const __grid_constant__ Ew
     }
     if (a.out) store_chunk<T, V, CT>(static_cast<T*>(a.out), c, acc);
     if (a.red) {
-      CT ps = 0, pq = 0;
+      if constexpr (kFF) {
 #pragma unroll
-      for (int v = 0; v < V; ++v) {
-        ps += acc[v];
-        pq = fma(acc[v], acc[v], pq);
+        for (int v = 0; v < V; ++v) ff.add((double)acc[v]);
+      } else {
+        CT ps = 0, pq = 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          ps += acc[v];
+          pq = fma(acc[v], acc[v], pq);
+        }
+        rs += (double)ps;
+        rq += (double)pq;
       }
-      rs += (double)ps;
-      rq += (double)pq;
     }
+  }
+  if constexpr (kFF) {
+    rs += ff.sum();
+    rq += ff.sumsq();
   }
   // ragged tail: the last total % V elements, one per thread
   for (int64_t t = nchunk * V + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
@@ -235,17 +298,42 @@ __global__ void __launch_bounds__(256) ew_flat_kernel(const __grid_constant__ Ew
                   (a.red & 2) ? a.norm_out : nullptr, 1.0);
 }
 
-template <typename T>
-cudaError_t launch_flat_t(const EwArgs& a, int grid, cudaStream_t s) {
-  switch (a.nin) {
-#define ARMA_EW_CASE(N) \
-  case N: ew_flat_kernel<T, N><<<grid, 256, 0, s>>>(a); break;
-    ARMA_EW_CASE(1) ARMA_EW_CASE(2) ARMA_EW_CASE(3) ARMA_EW_CASE(4)
-    ARMA_EW_CASE(5) ARMA_EW_CASE(6) ARMA_EW_CASE(7) ARMA_EW_CASE(8)
-#undef ARMA_EW_CASE
-    default: return cudaErrorInvalidValue;
+typedef void (*EwKernel)(EwArgs);
+
+// Resident 256-thread blocks per SM for a kernel (cached): the streaming
+// passes launch exactly one wave and stride through the data.
+int resident_blocks(const void* k) {
+  static const void* keys[128];
+  static int vals[128];
+  static int n = 0;
+  for (int i = 0; i < n; ++i)
+    if (keys[i] == k) return vals[i];
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 256, 0) != cudaSuccess || occ < 1) occ = 1;
+  if (n < 128) { keys[n] = k; vals[n] = occ; ++n; }
+  return occ;
+}
+
+template <typename T, int STK>
+EwKernel pick_flat(int nin) {
+  switch (nin) {
+    case 1: return ew_flat_kernel<T, 1, STK>;
+    case 2: return ew_flat_kernel<T, 2, STK>;
+    case 3: return ew_flat_kernel<T, 3, STK>;
+    case 4: return ew_flat_kernel<T, 4, STK>;
+    case 5: return ew_flat_kernel<T, 5, STK>;
+    case 6: return ew_flat_kernel<T, 6, STK>;
+    case 7: return ew_flat_kernel<T, 7, STK>;
+    case 8: return ew_flat_kernel<T, 8, STK>;
+    default: return nullptr;
   }
-  return cudaGetLastError();
+}
+
+template <typename T>
+EwKernel pick_flat_t(const EwArgs& a) {
+  bool stack = false;
+  for (int i = 0; i < a.nops; ++i) stack |= a.ops[i].op == EW_PUSH;
+  return stack ? pick_flat<T, kMaxStack>(a.nin) : pick_flat<T, 0>(a.nin);
 }
 
 bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
@@ -265,25 +353,19 @@ cudaError_t launch_ew(const EwArgs& a, cudaStream_t s, int* launches) {
     if (a.out) flat &= a.out_dtype == dt && al16(a.out);
     flat &= (a.compute_f64 != 0) == (dt == ARMA_F64);
   }
-  const int per_sm = 8;  // 256-thread blocks resident per SM at full occupancy
+  EwKernel k;
+  if (flat) k = dt == ARMA_F64 ? pick_flat_t<double>(a) : dt == ARMA_F32 ? pick_flat_t<float>(a)
+                                                                 : pick_flat_t<__nv_bfloat16>(a);
+  else k = a.compute_f64 ? ew_strided_kernel<double> : ew_strided_kernel<float>;
+  if (!k) return cudaErrorInvalidValue;
   int64_t work = total;
   if (flat) work = total / (dt == ARMA_F64 ? 4 : 8) + 1;
   int64_t need = (work + 255) / 256;
-  int64_t cap = (int64_t)sms * per_sm;
+  int64_t cap = (int64_t)sms * resident_blocks(reinterpret_cast<const void*>(k));
   if (cap > kMaxRedBlocks) cap = kMaxRedBlocks;
   int grid = (int)(need < 1 ? 1 : need > cap ? cap : need);
-  cudaError_t e;
-  if (flat) {
-    e = dt == ARMA_F64 ? launch_flat_t<double>(a, grid, s)
-        : dt == ARMA_F32 ? launch_flat_t<float>(a, grid, s)
-                         : launch_flat_t<__nv_bfloat16>(a, grid, s);
-  } else if (a.compute_f64) {
-    ew_strided_kernel<double><<<grid, 256, 0, s>>>(a);
-    e = cudaGetLastError();
-  } else {
-    ew_strided_kernel<float><<<grid, 256, 0, s>>>(a);
-    e = cudaGetLastError();
-  }
+  k<<<grid, 256, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
   if (launches) ++*launches;
   return e;
 }

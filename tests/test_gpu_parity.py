@@ -183,3 +183,20 @@ def test_fused_full_size(torch, dtype):
     got = run(nodes, outs, host, dtype)
     ref = oracle.evaluate(nodes, outs, host)
     check(got, ref, TOL[dtype], f"full size {dtype}")
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1e-20, 1.0, 1e20, 1e36])
+def test_fused_f64_reductions_any_magnitude(torch, scale):
+    """FP64 sums and sums of squares are carried as float pairs when the
+    values fit a float's exponent range and in FP64 otherwise; both routes
+    (and a mix of them in one pass) must meet the FP64 tolerance."""
+    m, n = 300, 211
+    g = E.Graph()
+    A, B, C, D = (g.input(s, m, n, "f64") for s in range(4))
+    out = A % B + 3 * C - D / 2
+    nodes, outs = g.build(out, E.accu(out), E.norm_fro(out))
+    host = inputs(97, [(m, n)] * 4, "f64")
+    host = [h * scale for h in host]
+    host[2][:, : n // 2] *= 1e-12          # a spread of magnitudes inside one pass
+    got = run(nodes, outs, host, "f64")
+    check(got, oracle.evaluate(nodes, outs, host), TOL["f64"], f"scale {scale}")
