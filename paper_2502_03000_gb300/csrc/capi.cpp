@@ -53,7 +53,10 @@ arma_status run_step(const Step& st, const Bind& b, cudaStream_t s, int* launche
         a.rs[k] = e.in[k].rs; a.cs[k] = e.in[k].cs;
         a.in_dtype[k] = e.in[k].dtype; a.in_flags[k] = e.in[k].flags;
       }
-      for (int i = 0; i < e.nops; ++i) a.ops[i] = e.ops[i];
+      for (int i = 0; i < e.nops; ++i) {
+        a.ops[i] = e.ops[i];
+        a.ops[i].sf = static_cast<float>(e.ops[i].s);
+      }
       a.out = e.out.valid() ? mptr(b, e.out) : nullptr;
       a.out_ld = e.out_ld;
       a.partials = e.partials.valid() ? reinterpret_cast<double*>(mptr(b, e.partials)) : nullptr;

@@ -124,7 +124,9 @@ __device__ __forceinline__ bool split_ff(double x, float& hi, float& lo) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const unsigned int e = (unsigned int)(u >> 52) & 0x7ffu;
   if (e == 0u && (u << 1) == 0ull) { hi = 0.f; lo = 0.f; return true; }  // +-0
-  if (e < 949u || e > 1150u) return false;            // hi or the lo scale would leave float range
+  // |x| in [2^-51, 2^51): hi, lo, hi^2 and its rounding error all stay
+  // normal floats, and per-thread sums of squares cannot overflow
+  if (e < 972u || e > 1073u) return false;
   const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
   const unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
   hi = __uint_as_float(sign | ((e - 896u) << 23) | (unsigned int)(mant >> 29));
@@ -148,7 +150,7 @@ struct FFAcc {
   double s64 = 0.0, q64 = 0.0;  // values outside the pair's range
   __device__ __forceinline__ void add(double x) {
     float hi, lo;
-    if (split_ff(x, hi, lo)) {
+    if (__builtin_expect(split_ff(x, hi, lo), 1)) {
       ff_add(sh, sl, hi, lo);
       const float p = __fmul_rn(hi, hi);
       float pe = __fmaf_rn(hi, hi, -p);
@@ -158,6 +160,11 @@ struct FFAcc {
       s64 += x;
       q64 = fma(x, x, q64);
     }
+  }
+  // FP32 chunk sums (already float): plain two-sums, no FP64 instruction
+  __device__ __forceinline__ void add_f32(float ps, float pq) {
+    ff_add(sh, sl, ps, 0.f);
+    ff_add(qh, ql, pq, 0.f);
   }
   __device__ __forceinline__ double sum() const { return ((double)sh + (double)sl) + s64; }
   __device__ __forceinline__ double sumsq() const { return ((double)qh + (double)ql) + q64; }
@@ -218,34 +225,56 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) ew_flat_kernel(co
     CT acc[V], st[STK > 0 ? STK : 1][V];
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = 0;
+    // one uniform branch per instruction; the element loops inside each
+    // case are branch-free (no if-conversion of the whole instruction set)
     for (int pc = 0; pc < a.nops; ++pc) {
       const int op = a.ops[pc].op, arg = a.ops[pc].arg;
-      const double s = a.ops[pc].s;
-      if (uses_operand(op)) {
+      CT sc;
+      if constexpr (kFF) sc = a.ops[pc].s; else sc = a.ops[pc].sf;
+#define ARMA_EW_SEL(BODY)                        \
+  _Pragma("unroll") for (int k = 0; k < NIN; ++k) \
+    if (k == arg) {                              \
+      _Pragma("unroll") for (int v = 0; v < V; ++v) { BODY; } \
+    }
+#define ARMA_EW_STK(BODY)                        \
+  _Pragma("unroll") for (int q = 0; q < STK; ++q) \
+    if (q == arg) {                              \
+      _Pragma("unroll") for (int v = 0; v < V; ++v) { BODY; } \
+    }
+      switch (op) {
+        case EW_LD: ARMA_EW_SEL(acc[v] = x[k][v]) break;
+        case EW_ADD: ARMA_EW_SEL(acc[v] = acc[v] + x[k][v]) break;
+        case EW_SUB: ARMA_EW_SEL(acc[v] = acc[v] - x[k][v]) break;
+        case EW_RSUB: ARMA_EW_SEL(acc[v] = x[k][v] - acc[v]) break;
+        case EW_MUL: ARMA_EW_SEL(acc[v] = acc[v] * x[k][v]) break;
+        case EW_DIV: ARMA_EW_SEL(acc[v] = acc[v] / x[k][v]) break;
+        case EW_RDIV: ARMA_EW_SEL(acc[v] = x[k][v] / acc[v]) break;
+        case EW_AXPY: ARMA_EW_SEL(acc[v] = fma(sc, x[k][v], acc[v])) break;
+        case EW_SCAL:
 #pragma unroll
-        for (int k = 0; k < NIN; ++k)
-          if (k == arg) {
+          for (int v = 0; v < V; ++v) acc[v] = sc * acc[v];
+          break;
+        case EW_DIVS:
 #pragma unroll
-            for (int v = 0; v < V; ++v) acc[v] = ew_in<CT>(op, acc[v], x[k][v], s);
-          }
-      } else if (op == EW_PUSH) {
+          for (int v = 0; v < V; ++v) acc[v] = acc[v] / sc;
+          break;
+        case EW_ADDS:
 #pragma unroll
-        for (int q = 0; q < STK; ++q)
-          if (q == arg) {
+          for (int v = 0; v < V; ++v) acc[v] = acc[v] + sc;
+          break;
+        case EW_NEG:
 #pragma unroll
-            for (int v = 0; v < V; ++v) st[q][v] = acc[v];
-          }
-      } else if (is_pop(op)) {
-#pragma unroll
-        for (int q = 0; q < STK; ++q)
-          if (q == arg) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) acc[v] = ew_pop<CT>(op, st[q][v], acc[v]);
-          }
-      } else {
-#pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] = ew_self<CT>(op, acc[v], s);
+          for (int v = 0; v < V; ++v) acc[v] = -acc[v];
+          break;
+        case EW_PUSH: ARMA_EW_STK(st[q][v] = acc[v]) break;
+        case EW_POPADD: ARMA_EW_STK(acc[v] = st[q][v] + acc[v]) break;
+        case EW_POPSUB: ARMA_EW_STK(acc[v] = st[q][v] - acc[v]) break;
+        case EW_POPMUL: ARMA_EW_STK(acc[v] = st[q][v] * acc[v]) break;
+        case EW_POPDIV: ARMA_EW_STK(acc[v] = st[q][v] / acc[v]) break;
+        default: break;
       }
+#undef ARMA_EW_SEL
+#undef ARMA_EW_STK
     }
     if (a.out) store_chunk<T, V, CT>(static_cast<T*>(a.out), c, acc);
     if (a.red) {
@@ -253,21 +282,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) ew_flat_kernel(co
 #pragma unroll
         for (int v = 0; v < V; ++v) ff.add((double)acc[v]);
       } else {
-        CT ps = 0, pq = 0;
+        float ps = 0.f, pq = 0.f;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-          ps += acc[v];
-          pq = fma(acc[v], acc[v], pq);
+          ps += (float)acc[v];
+          pq = fmaf((float)acc[v], (float)acc[v], pq);
         }
-        rs += (double)ps;
-        rq += (double)pq;
+        ff.add_f32(ps, pq);
       }
     }
   }
-  if constexpr (kFF) {
-    rs += ff.sum();
-    rq += ff.sumsq();
-  }
+  rs += ff.sum();
+  rq += ff.sumsq();
   // ragged tail: the last total % V elements, one per thread
   for (int64_t t = nchunk * V + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
     CT acc = 0, s0 = 0, s1 = 0, s2 = 0, s3 = 0;
