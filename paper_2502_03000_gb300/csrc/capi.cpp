@@ -82,6 +82,7 @@ arma_status run_step(const Step& st, const Bind& b, cudaStream_t s, int* launche
       a.tier = g.tier;
       a.scratch = g.scratch.valid() ? mptr(b, g.scratch) : nullptr;
       a.scratch_bytes = g.scratch_bytes;
+      a.status = reinterpret_cast<int32_t*>(b.ws);
       return cuda_status(launch_gemm(a, s, launches));
     }
     case ST_DOT: {

@@ -156,6 +156,7 @@ struct GemmArgs {
   const void* cs; int64_t cs_inc; int32_t csdt;
   int32_t tier;
   void* scratch; int64_t scratch_bytes;
+  int32_t* status;   // workspace status word (device-side failures)
 };
 
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s, int* launches);

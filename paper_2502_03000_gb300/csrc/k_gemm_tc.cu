@@ -1,8 +1,635 @@
-// tcgen05 GEMM (placeholder until the tensor-core path lands).
+// Tensor-core products on sm_103a: tcgen05.mma (kind::f16, BF16 operands,
+// FP32 accumulation in TMEM) fed by TMA into 128-byte-swizzled shared
+// memory, with the paper's folded scalars, transposes and diagonal scalings
+// (Sec. II, glue_times carrying alpha and the transpose flags, Fig. 3)
+// applied in the operand preparation and in the epilogue.
+//
+// Pipeline (one CTA per SM, persistent over output tiles):
+//   warp 0      TMA producer: A and B tiles into a 4-stage smem ring
+//   warp 1      owns TMEM (512 columns = two 128 x 256 FP32 accumulators)
+//               and issues tcgen05.mma from one elected lane
+//   warps 2..5  epilogue: tcgen05.ld from TMEM, scale, store (overlaps the
+//               next tile's main loop through the second accumulator)
+//
+// Precision tiers.  BF16: one product of BF16-rounded operands.  Split-BF16:
+// each operand is split exactly into three BF16 slices x = x0 + x1 + x2
+// (its leading 24 significand bits) and the six slice products whose order
+// is at most 2 (x0y0, x0y1, x1y0, x0y2, x1y1, x2y0) are accumulated, which
+// gives about FP32 accuracy from BF16 tensor cores (Henry et al. 2019, the
+// BF16 work the paper cites for future element types).  Slice products run
+// smallest first, and long K is split into chunks whose FP32 partials are
+// combined in FP64, to keep the FP32 accumulation error small.
+//
+// Every mbarrier wait is bounded: on timeout the kernel records an error in
+// the workspace status word, drains its own copies and MMAs (again with
+// bounded waits), frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "common.cuh"
 
 namespace arma {
-bool gemm_tc_supported(const GemmArgs&) { return false; }
-int64_t gemm_tc_scratch_bytes(int64_t, int64_t, int64_t, int32_t) { return 0; }
-cudaError_t launch_gemm_tc(const GemmArgs&, cudaStream_t, int*) { return cudaErrorNotSupported; }
+
+namespace tc {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_TILE = BM * BK * 2;           // 16 KiB
+constexpr int B_TILE = BN * BK * 2;           // 32 KiB
+constexpr int STAGE_BYTES = A_TILE + B_TILE;  // 48 KiB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int TMEM_COLS = 512;
+constexpr int THREADS = 192;
+constexpr uint32_t WAIT_LIMIT = 1u << 22;     // try_wait iterations before giving up
+
+// slice pairs (a, b) of the split tier, smallest contribution first
+__constant__ int kTermA[6] = {2, 1, 0, 1, 0, 0};
+__constant__ int kTermB[6] = {0, 1, 2, 0, 1, 0};
+
+struct Params {
+  int64_t m, n, k;          // logical problem
+  int64_t mpad, npad, kp;   // padded slice extents (rows per slice, row stride in elements)
+  int32_t terms;            // 1 (BF16) or 6 (split-BF16)
+  int32_t splits;           // K chunks
+  int32_t kb_per_split;     // k-blocks of BK per chunk
+  int32_t tiles_m, tiles_n;
+  // epilogue
+  int32_t partial;          // 1: write FP32 partial P[split] (ld = m); 0: final D
+  float* P;
+  void* D; int64_t ldd; int32_t ddt;
+  const void* C; int64_t ldc; int32_t cdt;
+  double alpha, beta;
+  const void* rs; int64_t rs_inc; int32_t rsdt;
+  const void* cs; int64_t cs_inc; int32_t csdt;
+  int32_t* status;          // workspace status word (0 = ok)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; returns false (and raises the CTA abort flag) on timeout or
+// when another role already aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 255u) == 255u && *abort) return false;
+  }
+  *abort = 1;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int32_t x,
+                                            int32_t y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+// K-major, 128-byte swizzle: 8-row groups of 1024 bytes (SBO), version 1
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;              // descriptor version
+  d |= (uint64_t)2 << 61;              // SWIZZLE_128B
+  return d;
+}
+
+// kind::f16 instruction descriptor: D=F32, A=B=BF16, both K-major, N, M
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct WorkItem {
+  int32_t tm, tn, split;
+};
+
+__device__ __forceinline__ WorkItem work_item(const Params& p, int32_t w) {
+  // split outermost; inside a split, groups of 16 tile rows sweep the tile
+  // columns so that concurrently running CTAs share A and B panels in L2
+  const int32_t per_split = p.tiles_m * p.tiles_n;
+  WorkItem it;
+  it.split = w / per_split;
+  int32_t r = w - it.split * per_split;
+  const int32_t G = 16;
+  int32_t group = r / (G * p.tiles_n);
+  int32_t first = group * G;
+  int32_t gsize = min(G, p.tiles_m - first);
+  int32_t q = r - group * G * p.tiles_n;
+  it.tm = first + q % gsize;
+  it.tn = q / gsize;
+  return it;
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ Params p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], done
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+  const uint32_t tfull0 = smem_u32(bars + 2 * STAGES), tempty0 = smem_u32(bars + 2 * STAGES + 2);
+  const uint32_t done_bar = smem_u32(bars + 2 * STAGES + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t kb_total = p.kb_per_split;
+  const int32_t total_work = p.tiles_m * p.tiles_n * p.splits;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull0 + 8 * a, 1);
+      mbar_init(tempty0 + 8 * a, 128);
+    }
+    mbar_init(done_bar, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      int32_t inflight[STAGES];
+      for (int s = 0; s < STAGES; ++s) inflight[s] = -1;
+      for (int32_t w = blockIdx.x; w < total_work && ok; w += gridDim.x) {
+        WorkItem it = work_item(p, w);
+        const int32_t kb0 = it.split * kb_total;
+        for (int t = 0; t < p.terms && ok; ++t) {
+          const int sa = p.terms == 1 ? 0 : kTermA[t], sb = p.terms == 1 ? 0 : kTermB[t];
+          for (int32_t kb = 0; kb < kb_total; ++kb) {
+            if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, abort)) { ok = false; break; }
+            const uint32_t fb = full0 + 8 * stage;
+            mbar_expect_tx(fb, STAGE_BYTES);
+            const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
+            const int32_t x = (kb0 + kb) * BK;
+            tma_load_2d(sA, &tmA, fb, x, (int32_t)(sa * p.mpad + (int64_t)it.tm * BM));
+            tma_load_2d(sA + A_TILE, &tmB, fb, x, (int32_t)(sb * p.npad + (int64_t)it.tn * BN));
+            inflight[stage] = (int32_t)phase;
+            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+          }
+        }
+      }
+      if (!ok) {
+        // drain copies already issued (bounded) before the CTA can exit
+        for (int s = 0; s < STAGES; ++s) {
+          if (inflight[s] < 0) continue;
+          for (uint32_t i = 0; i < WAIT_LIMIT && !mbar_try(full0 + 8 * s, (uint32_t)inflight[s]); ++i) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(BM, BN);
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t aphase = 0;
+      bool ok = true;
+      bool issued = false;
+      for (int32_t w = blockIdx.x; w < total_work && ok; w += gridDim.x) {
+        if (!mbar_wait(tempty0 + 8 * acc, aphase ^ 1u, abort)) { ok = false; break; }
+        fence_after();
+        const uint32_t dcol = tmem_base + (uint32_t)(acc * BN);
+        uint32_t accumulate = 0;
+        const int32_t nkb = p.terms * kb_total;
+        for (int32_t j = 0; j < nkb; ++j) {
+          if (!mbar_wait(full0 + 8 * stage, phase, abort)) { ok = false; break; }
+          fence_after();
+          const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
+          const uint32_t sB = sA + A_TILE;
+          const uint64_t ad = sw128_desc(sA), bd = sw128_desc(sB);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            // advance 16 BF16 (32 bytes) along K inside the swizzle atom
+            mma_bf16(dcol, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, accumulate);
+            accumulate = 1;
+          }
+          mma_commit(empty0 + 8 * stage);  // frees the smem stage when these MMAs finish
+          issued = true;
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+        mma_commit(tfull0 + 8 * acc);      // accumulator ready for the epilogue
+        if (++acc == 2) { acc = 0; aphase ^= 1u; }
+      }
+      if (issued) {
+        // all MMAs of this CTA complete before TMEM is released
+        mma_commit(done_bar);
+        for (uint32_t i = 0; i < WAIT_LIMIT && !mbar_try(done_bar, 0); ++i) {
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int quarter = warp & 3;   // TMEM lanes 32*quarter .. +31
+    int acc = 0;
+    uint32_t aphase = 0;
+    const bool f64_out = p.ddt == ARMA_F64;
+    const float alpha_f = (float)p.alpha, beta_f = (float)p.beta;
+    for (int32_t w = blockIdx.x; w < total_work; w += gridDim.x) {
+      WorkItem it = work_item(p, w);
+      // warp-uniform decision: tcgen05.ld below is .sync.aligned
+      bool ok = mbar_wait(tfull0 + 8 * acc, aphase, abort);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      fence_after();
+      const int64_t row = (int64_t)it.tm * BM + quarter * 32 + lane;
+      const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
+      const bool row_ok = row < p.m;
+      double rsv = 1.0;
+      if (!p.partial && p.rs && row_ok) rsv = load_as<double>(p.rs, row * p.rs_inc, p.rsdt);
+      const float rsf = (float)rsv;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(tbase + (uint32_t)c0, v);
+        if (!row_ok) continue;
+        const int64_t col0 = (int64_t)it.tn * BN + c0;
+        if (p.partial) {
+          float* dst = p.P + (int64_t)it.split * p.m * p.n + row;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (col0 + j < p.n) dst[(col0 + j) * p.m] = v[j];
+        } else if (f64_out) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int64_t col = col0 + j;
+            if (col >= p.n) break;
+            double r = p.alpha * (double)v[j] * rsv;
+            if (p.cs) r *= load_as<double>(p.cs, col * p.cs_inc, p.csdt);
+            if (p.C && p.beta != 0.0) r += p.beta * load_as<double>(p.C, row + col * p.ldc, p.cdt);
+            static_cast<double*>(p.D)[row + col * p.ldd] = r;
+          }
+        } else {
+          // FP32 / BF16 results: FP32 epilogue arithmetic (no FP64 pipe)
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int64_t col = col0 + j;
+            if (col >= p.n) break;
+            float r = alpha_f * v[j] * rsf;
+            if (p.cs) r *= load_as<float>(p.cs, col * p.cs_inc, p.csdt);
+            if (p.C && p.beta != 0.0) r = fmaf(beta_f, load_as<float>(p.C, row + col * p.ldc, p.cdt), r);
+            store_as<float>(p.D, row + col * p.ldd, p.ddt, r);
+          }
+        }
+      }
+      fence_before();
+      mbar_arrive(tempty0 + 8 * acc);
+      if (++acc == 2) { acc = 0; aphase ^= 1u; }
+    }
+  }
+
+  fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort && p.status) atomicCAS(p.status, 0, (int32_t)ARMA_ERR_CUDA);
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// operand preparation: op(X) (R x K, any storage type, either orientation)
+// -> T BF16 slices, K-major, rows padded to rpad, row stride kp (>= K, zero fill)
+// ---------------------------------------------------------------------------
+// The slices come from the binary expansion: slice 0 holds the leading 8
+// significand bits, slice 1 the next 8, slice 2 the next 8 (integer
+// operations only; each slice is exactly a BF16).  For one slice the value
+// is rounded to nearest BF16.
+__device__ __forceinline__ uint16_t bf16_bits_of_window(uint32_t sign, int32_t exp2_lsb, uint32_t win) {
+  // value = win * 2^exp2_lsb with win < 256; returns exact BF16 bits (0 if win == 0)
+  if (win == 0u) return 0;
+  const int lz = __clz(win) - 24;          // leading zeros inside the 8-bit window
+  const uint32_t norm = win << lz;         // bit 7 set
+  const int32_t e = exp2_lsb + 7 - lz;     // exponent of the leading bit
+  const int32_t be = e + 127;
+  if (be <= 0 || be >= 255) return 0;      // outside BF16's normal range: dropped
+  return (uint16_t)((sign >> 16) | ((uint32_t)be << 7) | (norm & 0x7Fu));
+}
+
+__device__ __forceinline__ void split3(double x, int dt, uint16_t (&s)[3]) {
+  if (dt == ARMA_F64) {
+    const uint64_t u = (uint64_t)__double_as_longlong(x);
+    const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
+    const int32_t e = (int32_t)((u >> 52) & 0x7FF);
+    if (e == 0 || e == 0x7FF) { s[0] = s[1] = s[2] = 0; return; }
+    const uint64_t m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // 53 bits
+    const int32_t E = e - 1023;   // value = m * 2^(E - 52)
+    s[0] = bf16_bits_of_window(sign, E - 7, (uint32_t)(m >> 45) & 0xFFu);
+    s[1] = bf16_bits_of_window(sign, E - 15, (uint32_t)(m >> 37) & 0xFFu);
+    s[2] = bf16_bits_of_window(sign, E - 23, (uint32_t)(m >> 29) & 0xFFu);
+  } else {
+    const float f = (float)x;   // exact for FP32 / BF16 storage
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t sign = u & 0x80000000u;
+    const int32_t e = (int32_t)((u >> 23) & 0xFF);
+    if (e == 0 || e == 0xFF) { s[0] = s[1] = s[2] = 0; return; }
+    const uint32_t m = (u & 0x7FFFFFu) | (1u << 23);   // 24 bits
+    const int32_t E = e - 127;
+    s[0] = bf16_bits_of_window(sign, E - 7, (m >> 16) & 0xFFu);
+    s[1] = bf16_bits_of_window(sign, E - 15, (m >> 8) & 0xFFu);
+    s[2] = bf16_bits_of_window(sign, E - 23, m & 0xFFu);
+  }
+}
+
+struct PrepArgs {
+  const void* X; int64_t ldx; int32_t xdt, trans;  // op(X)(r, l) = trans ? X[l + r*ldx] : X[r + l*ldx]
+  int64_t R, K, rpad, kp;
+  int32_t terms;
+  __nv_bfloat16* out;    // [terms][rpad][kp]
+};
+
+// 32 x 32 tiles through shared memory: read along X's contiguous index,
+// write along K
+__global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepArgs a) {
+  __shared__ uint16_t t[3][32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t r0 = (int64_t)blockIdx.x * 32, l0 = (int64_t)blockIdx.y * 32;
+  for (int q = ty; q < 32; q += 8) {
+    int64_t r, l;
+    if (a.trans) { l = l0 + tx; r = r0 + q; } else { r = r0 + tx; l = l0 + q; }
+    uint16_t s[3] = {0, 0, 0};
+    if (r < a.R && l < a.K) {
+      const int64_t idx = a.trans ? l + r * a.ldx : r + l * a.ldx;
+      const double x = load_as<double>(a.X, idx, a.xdt);
+      if (a.terms == 1) {
+        s[0] = __bfloat16_as_ushort(__float2bfloat16_rn((float)x));
+      } else {
+        split3(x, a.xdt, s);
+      }
+    }
+    const int rr = (int)(r - r0), ll = (int)(l - l0);
+    for (int u = 0; u < a.terms; ++u) t[u][rr][ll] = s[u];
+  }
+  __syncthreads();
+  for (int q = ty; q < 32; q += 8) {
+    const int64_t r = r0 + q, l = l0 + tx;
+    if (r < a.rpad && l < a.kp) {
+      for (int u = 0; u < a.terms; ++u) {
+        uint16_t v = (r < a.R && l < a.K) ? t[u][q][tx] : (uint16_t)0;
+        reinterpret_cast<uint16_t*>(a.out)[((int64_t)u * a.rpad + r) * a.kp + l] = v;
+      }
+    }
+  }
+}
+
+// D = alpha * diag(r) * (sum_s P_s) * diag(c) + beta * C, partials summed in FP64
+struct CombineArgs {
+  int64_t m, n;
+  int32_t splits;
+  const float* P;
+  void* D; int64_t ldd; int32_t ddt;
+  const void* C; int64_t ldc; int32_t cdt;
+  double alpha, beta;
+  const void* rs; int64_t rs_inc; int32_t rsdt;
+  const void* cs; int64_t cs_inc; int32_t csdt;
+};
+
+__global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ CombineArgs a) {
+  const int64_t total = a.m * a.n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t col = t / a.m, row = t - col * a.m;
+    double s = 0.0;
+    for (int k = 0; k < a.splits; ++k) s += (double)a.P[(int64_t)k * total + t];
+    double r = a.alpha * s;
+    if (a.rs) r *= load_as<double>(a.rs, row * a.rs_inc, a.rsdt);
+    if (a.cs) r *= load_as<double>(a.cs, col * a.cs_inc, a.csdt);
+    if (a.C && a.beta != 0.0) r += a.beta * load_as<double>(a.C, row + col * a.ldc, a.cdt);
+    store_as<double>(a.D, row + col * a.ldd, a.ddt, r);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct Geometry {
+  int32_t terms, splits, kb_per_split, tiles_m, tiles_n;
+  int64_t mpad, npad, kp;
+  int64_t a_bytes, b_bytes, p_bytes;
+};
+
+Geometry geometry(int64_t m, int64_t n, int64_t k, int32_t tier) {
+  Geometry g;
+  g.terms = tier == ARMA_TIER_SPLIT_BF16 ? 6 : 1;
+  g.kp = (k + 7) / 8 * 8;
+  g.mpad = (m + BM - 1) / BM * BM;
+  g.npad = (n + BN - 1) / BN * BN;
+  g.tiles_m = (int32_t)(g.mpad / BM);
+  g.tiles_n = (int32_t)(g.npad / BN);
+  const int64_t kb = (k + BK - 1) / BK;
+  // K chunks: at most 2048 of K per FP32 accumulator for the split tier,
+  // and enough work items to fill the GPU when the output is small
+  int64_t max_chunk_kb = g.terms > 1 ? 2048 / BK : kb;
+  int64_t splits = (kb + max_chunk_kb - 1) / max_chunk_kb;
+  const int64_t tiles = (int64_t)g.tiles_m * g.tiles_n;
+  while (tiles * splits < 148 && kb / (splits * 2) >= 4) splits *= 2;
+  if (splits > kb) splits = kb > 0 ? kb : 1;
+  g.splits = (int32_t)(splits < 1 ? 1 : splits);
+  g.kb_per_split = (int32_t)((kb + g.splits - 1) / g.splits);
+  g.a_bytes = (int64_t)g.terms * g.mpad * g.kp * 2;
+  g.b_bytes = (int64_t)g.terms * g.npad * g.kp * 2;
+  g.p_bytes = g.splits > 1 ? (int64_t)g.splits * m * n * 4 : 0;
+  return g;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const void* base, int64_t kp, int64_t rows, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(kp * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace tc
+
+bool gemm_tc_supported(const GemmArgs& a) {
+  if (a.tier != ARMA_TIER_SPLIT_BF16 && a.tier != ARMA_TIER_BF16) return false;
+  if (a.m < 1 || a.n < 1 || a.k < 1) return false;
+  if (a.m > (1ll << 30) || a.n > (1ll << 30) || a.k > (1ll << 30)) return false;
+  if (!a.scratch) return false;
+  tc::Geometry g = tc::geometry(a.m, a.n, a.k, a.tier);
+  return a.scratch_bytes >= g.a_bytes + g.b_bytes + g.p_bytes + 1024;
+}
+
+int64_t gemm_tc_scratch_bytes(int64_t m, int64_t n, int64_t k, int32_t tier) {
+  if (tier != ARMA_TIER_SPLIT_BF16 && tier != ARMA_TIER_BF16) return 0;
+  if (m < 1 || n < 1 || k < 1) return 0;
+  tc::Geometry g = tc::geometry(m, n, k, tier);
+  return g.a_bytes + g.b_bytes + g.p_bytes + 1024;
+}
+
+cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
+  using namespace tc;
+  Geometry g = geometry(a.m, a.n, a.k, a.tier);
+  char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(a.scratch) + 255) & ~uintptr_t(255));
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(base);
+  __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(base + ((g.a_bytes + 255) / 256) * 256);
+  float* P = reinterpret_cast<float*>(base + ((g.a_bytes + 255) / 256) * 256 + ((g.b_bytes + 255) / 256) * 256);
+  // operand preparation: op(A) rows = m, op(B)^T rows = n, both K-major
+  PrepArgs pa;
+  pa.X = a.A; pa.ldx = a.lda; pa.xdt = a.adt; pa.trans = a.ta;
+  pa.R = a.m; pa.K = a.k; pa.rpad = g.mpad; pa.kp = g.kp; pa.terms = g.terms; pa.out = As;
+  dim3 ga((unsigned)((g.mpad + 31) / 32), (unsigned)((g.kp + 31) / 32));
+  prep_kernel<<<ga, 256, 0, s>>>(pa);
+  // op(B)^T (n x k): element (j, l) = op(B)(l, j) = tb ? B[j + l*ldb] : B[l + j*ldb]
+  PrepArgs pb;
+  pb.X = a.B; pb.ldx = a.ldb; pb.xdt = a.bdt; pb.trans = a.tb ? 0 : 1;
+  pb.R = a.n; pb.K = a.k; pb.rpad = g.npad; pb.kp = g.kp; pb.terms = g.terms; pb.out = Bs;
+  dim3 gb((unsigned)((g.npad + 31) / 32), (unsigned)((g.kp + 31) / 32));
+  prep_kernel<<<gb, 256, 0, s>>>(pb);
+  if (launches) *launches += 2;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+
+  CUtensorMap mapA, mapB;
+  if (!make_map(&mapA, As, g.kp, (int64_t)g.terms * g.mpad, BM)) return cudaErrorInvalidValue;
+  if (!make_map(&mapB, Bs, g.kp, (int64_t)g.terms * g.npad, BN)) return cudaErrorInvalidValue;
+
+  Params p;
+  memset(&p, 0, sizeof p);
+  p.m = a.m; p.n = a.n; p.k = a.k;
+  p.mpad = g.mpad; p.npad = g.npad; p.kp = g.kp;
+  p.terms = g.terms; p.splits = g.splits; p.kb_per_split = g.kb_per_split;
+  p.tiles_m = g.tiles_m; p.tiles_n = g.tiles_n;
+  p.partial = g.splits > 1 ? 1 : 0;
+  p.P = P;
+  p.D = a.D; p.ldd = a.ldd; p.ddt = a.ddt;
+  p.C = a.C; p.ldc = a.ldc; p.cdt = a.cdt;
+  p.alpha = a.alpha; p.beta = a.beta;
+  p.rs = a.rs; p.rs_inc = a.rs_inc; p.rsdt = a.rsdt;
+  p.cs = a.cs; p.cs_inc = a.cs_inc; p.csdt = a.csdt;
+  p.status = a.status;
+
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!attr_set[dev]) {
+    e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  const int64_t work = (int64_t)g.tiles_m * g.tiles_n * g.splits;
+  const int sms = device_sm_count();
+  const int grid = (int)(work < sms ? work : sms);
+  gemm_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(mapA, mapB, p);
+  if (launches) ++*launches;
+  e = cudaGetLastError();
+  if (e != cudaSuccess || g.splits == 1) return e;
+
+  CombineArgs c;
+  c.m = a.m; c.n = a.n; c.splits = g.splits; c.P = P;
+  c.D = a.D; c.ldd = a.ldd; c.ddt = a.ddt;
+  c.C = a.C; c.ldc = a.ldc; c.cdt = a.cdt;
+  c.alpha = a.alpha; c.beta = a.beta;
+  c.rs = a.rs; c.rs_inc = a.rs_inc; c.rsdt = a.rsdt;
+  c.cs = a.cs; c.cs_inc = a.cs_inc; c.csdt = a.csdt;
+  const int64_t total = a.m * a.n;
+  int64_t blocks = (total + 255) / 256, cap = (int64_t)sms * 8;
+  combine_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(c);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
 }  // namespace arma

@@ -1,0 +1,110 @@
+"""Tensor-core products (tcgen05, BF16 and split-BF16 tiers) against the FP64
+oracle: folded transposes, alpha / beta*C, diagonal scalings, ragged tiles,
+split-K, every input element type, and the benchmark size on sampled
+entries.  Smallest cases first."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2502_03000_gb300 as ag
+import synth
+from paper_2502_03000_gb300 import expr as E
+from tests.gpu_util import TOL, check, inputs, need_gpu, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return need_gpu()
+
+
+def product_case(m, n, k, ta, tb, dtype, extra=False):
+    g = E.Graph()
+    A = g.input(0, k, m, dtype) if ta else g.input(0, m, k, dtype)
+    B = g.input(1, n, k, dtype) if tb else g.input(1, k, n, dtype)
+    opA = A.t() if ta else A
+    opB = B.t() if tb else B
+    outs = [opA * opB]
+    shapes = [(k, m) if ta else (m, k), (n, k) if tb else (k, n)]
+    if extra:
+        cdt = "f32" if dtype == "bf16" else dtype
+        C = g.input(2, m, n, cdt)
+        r, c = g.input(3, m, 1, cdt), g.input(4, n, 1, cdt)
+        outs += [2 * opA * opB + C, E.diagmat(r) * (opA * opB) * E.diagmat(c)]
+        shapes += [(m, n), (m, 1), (n, 1)]
+    nodes, o = g.build(*outs)
+    return nodes, o, shapes
+
+
+def run_case(torch, nodes, outs, shapes, dtype, tier, seed=1, cdt=None):
+    host = [synth.matrix(seed, s + 1, r, c, dtype if s < 2 else (cdt or dtype)) for s, (r, c) in enumerate(shapes)]
+    plan = ag.Plan(nodes, outs, tier=tier)
+    assert any(st["kernel"] == "gemm" for st in plan.info["steps"])
+    ins = [to_dev(h, dtype if s < 2 else (cdt or dtype)) for s, h in enumerate(host)]
+    got = plan(*ins)
+    torch.cuda.synchronize()
+    st, info = plan.status()
+    assert st == "ok", (st, info)
+    return got, oracle.evaluate(nodes, outs, host)
+
+
+@pytest.mark.parametrize("tier", ["bf16", "split_bf16"])
+def test_gemm_tile_exact(torch, tier):
+    nodes, outs, shapes = product_case(128, 256, 64, 1, 0, "f64")
+    got, ref = run_case(torch, nodes, outs, shapes, "f64", tier)
+    check(got, ref, TOL[tier], f"128x256x64 {tier}")
+
+
+@pytest.mark.parametrize("tier", ["bf16", "split_bf16"])
+@pytest.mark.parametrize("ta,tb", [(1, 0), (0, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("mnk", [(129, 300, 77), (257, 513, 200), (64, 1000, 2000), (300, 2, 129)])
+def test_gemm_folded(torch, tier, ta, tb, mnk):
+    m, n, k = mnk
+    nodes, outs, shapes = product_case(m, n, k, ta, tb, "f64", extra=True)
+    got, ref = run_case(torch, nodes, outs, shapes, "f64", tier, seed=m + n + k)
+    check(got, ref, TOL[tier], f"{mnk} {ta}{tb} {tier}")
+
+
+@pytest.mark.parametrize("dtype,tier,tol", [("f32", "native", TOL["split_bf16"]), ("f32", "bf16", TOL["bf16"]),
+                                            ("bf16", "native", TOL["bf16"]), ("bf16", "split_bf16", 1e-6)])
+def test_gemm_input_types(torch, dtype, tier, tol):
+    nodes, outs, shapes = product_case(200, 330, 520, 1, 0, dtype, extra=True)
+    got, ref = run_case(torch, nodes, outs, shapes, dtype, tier, cdt="f32" if dtype == "bf16" else dtype)
+    check(got, ref, tol, f"{dtype} {tier}")
+
+
+@pytest.mark.parametrize("k", [1, 8, 4096, 9000])
+def test_gemm_split_k(torch, k):
+    nodes, outs, shapes = product_case(256, 256, k, 1, 0, "f64")
+    got, ref = run_case(torch, nodes, outs, shapes, "f64", "split_bf16", seed=k)
+    check(got, ref, TOL["split_bf16"], f"k={k}")
+
+
+def test_gemm_repeatable(torch):
+    nodes, outs, shapes = product_case(384, 512, 1024, 1, 0, "f32")
+    a, _ = run_case(torch, nodes, outs, shapes, "f32", "split_bf16")
+    b, _ = run_case(torch, nodes, outs, shapes, "f32", "split_bf16")
+    assert torch.equal(a[0], b[0])
+
+
+@pytest.mark.parametrize("tier", ["split_bf16", "bf16"])
+def test_gemm_benchmark_size_sampled(torch, tier):
+    """2*trans(A)*B + C at 8192^3 with FP64 inputs, in the launch
+    configuration the benchmark times; sampled entries against the oracle's
+    own increasing-l sums."""
+    n = 8192
+    nodes, outs = E.config_products(n, "f64")
+    host = [synth.matrix(20250203 + 3, s + 1, n, n, "f64") for s in range(3)]
+    plan = ag.Plan(nodes, outs, tier=tier)
+    ins = [to_dev(h) for h in host]
+    (D,) = plan(*ins)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(3)
+    ii = rng.integers(0, n, 256)
+    jj = rng.integers(0, n, 256)
+    At = np.asfortranarray(host[0].T)   # trans(A) as stored values
+    ref = 2.0 * oracle.matmul_entries(At, host[1], ii, jj) + host[2][ii, jj]
+    got = D[torch.as_tensor(ii), torch.as_tensor(jj)].double().cpu().numpy()
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= TOL[tier], err
