@@ -416,14 +416,15 @@ __device__ __forceinline__ void split3(double x, int dt, uint16_t (&s)[3]) {
 struct PrepArgs {
   const void* X; int64_t ldx; int32_t xdt, trans;  // op(X)(r, l) = trans ? X[l + r*ldx] : X[r + l*ldx]
   int64_t R, K, rpad, kp;
-  int32_t terms;
-  __nv_bfloat16* out;    // [terms][rpad][kp]
+  int32_t slices;        // 1 or 3
+  __nv_bfloat16* out;    // [slices][rpad][kp]
 };
 
 // 32 x 32 tiles through shared memory: read along X's contiguous index,
 // write along K
 __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepArgs a) {
   __shared__ uint16_t t[3][32][33];
+  if (a.slices != 1 && a.slices != 3) return;   // the tile above holds at most 3 slices
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t r0 = (int64_t)blockIdx.x * 32, l0 = (int64_t)blockIdx.y * 32;
   for (int q = ty; q < 32; q += 8) {
@@ -433,20 +434,20 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepA
     if (r < a.R && l < a.K) {
       const int64_t idx = a.trans ? l + r * a.ldx : r + l * a.ldx;
       const double x = load_as<double>(a.X, idx, a.xdt);
-      if (a.terms == 1) {
+      if (a.slices == 1) {
         s[0] = __bfloat16_as_ushort(__float2bfloat16_rn((float)x));
       } else {
         split3(x, a.xdt, s);
       }
     }
     const int rr = (int)(r - r0), ll = (int)(l - l0);
-    for (int u = 0; u < a.terms; ++u) t[u][rr][ll] = s[u];
+    for (int u = 0; u < a.slices; ++u) t[u][rr][ll] = s[u];
   }
   __syncthreads();
   for (int q = ty; q < 32; q += 8) {
     const int64_t r = r0 + q, l = l0 + tx;
     if (r < a.rpad && l < a.kp) {
-      for (int u = 0; u < a.terms; ++u) {
+      for (int u = 0; u < a.slices; ++u) {
         uint16_t v = (r < a.R && l < a.K) ? t[u][q][tx] : (uint16_t)0;
         reinterpret_cast<uint16_t*>(a.out)[((int64_t)u * a.rpad + r) * a.kp + l] = v;
       }
@@ -485,7 +486,9 @@ __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ Co
 // host side
 // ---------------------------------------------------------------------------
 struct Geometry {
-  int32_t terms, splits, kb_per_split, tiles_m, tiles_n;
+  int32_t terms;    // slice products accumulated (1 or 6)
+  int32_t slices;   // BF16 slices stored per operand (1 or 3)
+  int32_t splits, kb_per_split, tiles_m, tiles_n;
   int64_t mpad, npad, kp;
   int64_t a_bytes, b_bytes, p_bytes;
 };
@@ -493,6 +496,7 @@ struct Geometry {
 Geometry geometry(int64_t m, int64_t n, int64_t k, int32_t tier) {
   Geometry g;
   g.terms = tier == ARMA_TIER_SPLIT_BF16 ? 6 : 1;
+  g.slices = tier == ARMA_TIER_SPLIT_BF16 ? 3 : 1;
   g.kp = (k + 7) / 8 * 8;
   g.mpad = (m + BM - 1) / BM * BM;
   g.npad = (n + BN - 1) / BN * BN;
@@ -508,8 +512,8 @@ Geometry geometry(int64_t m, int64_t n, int64_t k, int32_t tier) {
   if (splits > kb) splits = kb > 0 ? kb : 1;
   g.splits = (int32_t)(splits < 1 ? 1 : splits);
   g.kb_per_split = (int32_t)((kb + g.splits - 1) / g.splits);
-  g.a_bytes = (int64_t)g.terms * g.mpad * g.kp * 2;
-  g.b_bytes = (int64_t)g.terms * g.npad * g.kp * 2;
+  g.a_bytes = (int64_t)g.slices * g.mpad * g.kp * 2;
+  g.b_bytes = (int64_t)g.slices * g.npad * g.kp * 2;
   g.p_bytes = g.splits > 1 ? (int64_t)g.splits * m * n * 4 : 0;
   return g;
 }
@@ -566,16 +570,17 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(base);
   __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(base + ((g.a_bytes + 255) / 256) * 256);
   float* P = reinterpret_cast<float*>(base + ((g.a_bytes + 255) / 256) * 256 + ((g.b_bytes + 255) / 256) * 256);
+  if (g.slices != 1 && g.slices != 3) return cudaErrorInvalidValue;
   // operand preparation: op(A) rows = m, op(B)^T rows = n, both K-major
   PrepArgs pa;
   pa.X = a.A; pa.ldx = a.lda; pa.xdt = a.adt; pa.trans = a.ta;
-  pa.R = a.m; pa.K = a.k; pa.rpad = g.mpad; pa.kp = g.kp; pa.terms = g.terms; pa.out = As;
+  pa.R = a.m; pa.K = a.k; pa.rpad = g.mpad; pa.kp = g.kp; pa.slices = g.slices; pa.out = As;
   dim3 ga((unsigned)((g.mpad + 31) / 32), (unsigned)((g.kp + 31) / 32));
   prep_kernel<<<ga, 256, 0, s>>>(pa);
   // op(B)^T (n x k): element (j, l) = op(B)(l, j) = tb ? B[j + l*ldb] : B[l + j*ldb]
   PrepArgs pb;
   pb.X = a.B; pb.ldx = a.ldb; pb.xdt = a.bdt; pb.trans = a.tb ? 0 : 1;
-  pb.R = a.n; pb.K = a.k; pb.rpad = g.npad; pb.kp = g.kp; pb.terms = g.terms; pb.out = Bs;
+  pb.R = a.n; pb.K = a.k; pb.rpad = g.npad; pb.kp = g.kp; pb.slices = g.slices; pb.out = Bs;
   dim3 gb((unsigned)((g.npad + 31) / 32), (unsigned)((g.kp + 31) / 32));
   prep_kernel<<<gb, 256, 0, s>>>(pb);
   if (launches) *launches += 2;
@@ -583,8 +588,8 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   if (e != cudaSuccess) return e;
 
   CUtensorMap mapA, mapB;
-  if (!make_map(&mapA, As, g.kp, (int64_t)g.terms * g.mpad, BM)) return cudaErrorInvalidValue;
-  if (!make_map(&mapB, Bs, g.kp, (int64_t)g.terms * g.npad, BN)) return cudaErrorInvalidValue;
+  if (!make_map(&mapA, As, g.kp, (int64_t)g.slices * g.mpad, BM)) return cudaErrorInvalidValue;
+  if (!make_map(&mapB, Bs, g.kp, (int64_t)g.slices * g.npad, BN)) return cudaErrorInvalidValue;
 
   Params p;
   memset(&p, 0, sizeof p);
