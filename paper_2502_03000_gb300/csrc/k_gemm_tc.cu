@@ -8,8 +8,9 @@
 //   warp 0      TMA producer: A and B tiles into a 4-stage smem ring
 //   warp 1      owns TMEM (512 columns = two 128 x 256 FP32 accumulators)
 //               and issues tcgen05.mma from one elected lane
-//   warps 2..5  epilogue: tcgen05.ld from TMEM, scale, store (overlaps the
-//               next tile's main loop through the second accumulator)
+//   warps 2..9  epilogue: drain each finished TMEM accumulator chunk into
+//               FP32 register sums, then scale and store (overlaps the MMA
+//               through the second accumulator)
 //
 // Precision tiers.  BF16: one product of BF16-rounded operands.  Split-BF16:
 // each operand is split exactly into three BF16 slices x = x0 + x1 + x2
@@ -17,8 +18,11 @@
 // is at most 2 (x0y0, x0y1, x1y0, x0y2, x1y1, x2y0) are accumulated, which
 // gives about FP32 accuracy from BF16 tensor cores (Henry et al. 2019, the
 // BF16 work the paper cites for future element types).  Slice products run
-// smallest first, and long K is split into chunks whose FP32 partials are
-// combined in FP64, to keep the FP32 accumulation error small.
+// smallest first.  The tensor core's own FP32 accumulation loses accuracy
+// over long K, so the split tier accumulates in TMEM for 256 of K at a time
+// and the epilogue adds each chunk into correctly rounded FP32 registers;
+// split-K over CTAs (FP32 partials, combined in FP64) is used only to fill
+// the GPU when the output has few tiles.
 //
 // Every mbarrier wait is bounded: on timeout the kernel records an error in
 // the workspace status word, drains its own copies and MMAs (again with
@@ -41,7 +45,8 @@ constexpr int B_TILE = BN * BK * 2;           // 32 KiB
 constexpr int STAGE_BYTES = A_TILE + B_TILE;  // 48 KiB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr int TMEM_COLS = 512;
-constexpr int THREADS = 192;
+constexpr int THREADS = 320;          // producer, MMA, 8 epilogue warps
+constexpr int EPI_THREADS = 256;
 constexpr uint32_t WAIT_LIMIT = 1u << 22;     // try_wait iterations before giving up
 
 // slice pairs (a, b) of the split tier, smallest contribution first
@@ -53,7 +58,9 @@ struct Params {
   int64_t mpad, npad, kp;   // padded slice extents (rows per slice, row stride in elements)
   int32_t terms;            // 1 (BF16) or 6 (split-BF16)
   int32_t splits;           // K chunks
-  int32_t kb_per_split;     // k-blocks of BK per chunk
+  int32_t kb_per_split;     // k-blocks of BK per work item
+  int32_t chunk_kb;         // k-blocks per TMEM accumulation chunk
+  int32_t nchunks;          // chunks per work item
   int32_t tiles_m, tiles_n;
   // epilogue
   int32_t partial;          // 1: write FP32 partial P[split] (ld = m); 0: final D
@@ -202,7 +209,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull0 + 8 * a, 1);
-      mbar_init(tempty0 + 8 * a, 128);
+      mbar_init(tempty0 + 8 * a, EPI_THREADS);
     }
     mbar_init(done_bar, 1);
     *abort = 0;
@@ -232,18 +239,22 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int32_t w = blockIdx.x; w < total_work && ok; w += gridDim.x) {
         WorkItem it = work_item(p, w);
         const int32_t kb0 = it.split * kb_total;
-        for (int t = 0; t < p.terms && ok; ++t) {
-          const int sa = p.terms == 1 ? 0 : kTermA[t], sb = p.terms == 1 ? 0 : kTermB[t];
-          for (int32_t kb = 0; kb < kb_total; ++kb) {
-            if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, abort)) { ok = false; break; }
-            const uint32_t fb = full0 + 8 * stage;
-            mbar_expect_tx(fb, STAGE_BYTES);
-            const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
-            const int32_t x = (kb0 + kb) * BK;
-            tma_load_2d(sA, &tmA, fb, x, (int32_t)(sa * p.mpad + (int64_t)it.tm * BM));
-            tma_load_2d(sA + A_TILE, &tmB, fb, x, (int32_t)(sb * p.npad + (int64_t)it.tn * BN));
-            inflight[stage] = (int32_t)phase;
-            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        for (int32_t c = 0; c < p.nchunks && ok; ++c) {
+          const int32_t cb = c * p.chunk_kb;
+          const int32_t ce = min(cb + p.chunk_kb, kb_total);
+          for (int t = 0; t < p.terms && ok; ++t) {
+            const int sa = p.terms == 1 ? 0 : kTermA[t], sb = p.terms == 1 ? 0 : kTermB[t];
+            for (int32_t kb = cb; kb < ce; ++kb) {
+              if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, abort)) { ok = false; break; }
+              const uint32_t fb = full0 + 8 * stage;
+              mbar_expect_tx(fb, STAGE_BYTES);
+              const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
+              const int32_t x = (kb0 + kb) * BK;
+              tma_load_2d(sA, &tmA, fb, x, (int32_t)(sa * p.mpad + (int64_t)it.tm * BM));
+              tma_load_2d(sA + A_TILE, &tmB, fb, x, (int32_t)(sb * p.npad + (int64_t)it.tn * BN));
+              inflight[stage] = (int32_t)phase;
+              if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            }
           }
         }
       }
@@ -267,30 +278,33 @@ __global__ void __launch_bounds__(THREADS, 1)
       bool ok = true;
       bool issued = false;
       for (int32_t w = blockIdx.x; w < total_work && ok; w += gridDim.x) {
-        if (!mbar_wait(tempty0 + 8 * acc, aphase ^ 1u, abort)) { ok = false; break; }
-        fence_after();
-        const uint32_t dcol = tmem_base + (uint32_t)(acc * BN);
-        uint32_t accumulate = 0;
-        const int32_t nkb = p.terms * kb_total;
-        for (int32_t j = 0; j < nkb; ++j) {
-          if (!mbar_wait(full0 + 8 * stage, phase, abort)) { ok = false; break; }
+        for (int32_t c = 0; c < p.nchunks && ok; ++c) {
+          if (!mbar_wait(tempty0 + 8 * acc, aphase ^ 1u, abort)) { ok = false; break; }
           fence_after();
-          const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
-          const uint32_t sB = sA + A_TILE;
-          const uint64_t ad = sw128_desc(sA), bd = sw128_desc(sB);
+          const uint32_t dcol = tmem_base + (uint32_t)(acc * BN);
+          uint32_t accumulate = 0;
+          const int32_t cb = c * p.chunk_kb;
+          const int32_t nkb = p.terms * (min(cb + p.chunk_kb, kb_total) - cb);
+          for (int32_t j = 0; j < nkb; ++j) {
+            if (!mbar_wait(full0 + 8 * stage, phase, abort)) { ok = false; break; }
+            fence_after();
+            const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
+            const uint32_t sB = sA + A_TILE;
+            const uint64_t ad = sw128_desc(sA), bd = sw128_desc(sB);
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            // advance 16 BF16 (32 bytes) along K inside the swizzle atom
-            mma_bf16(dcol, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, accumulate);
-            accumulate = 1;
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              // advance 16 BF16 (32 bytes) along K inside the swizzle atom
+              mma_bf16(dcol, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, accumulate);
+              accumulate = 1;
+            }
+            mma_commit(empty0 + 8 * stage);  // frees the smem stage when these MMAs finish
+            issued = true;
+            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
           }
-          mma_commit(empty0 + 8 * stage);  // frees the smem stage when these MMAs finish
-          issued = true;
-          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+          if (!ok) break;
+          mma_commit(tfull0 + 8 * acc);      // chunk accumulator ready for the epilogue
+          if (++acc == 2) { acc = 0; aphase ^= 1u; }
         }
-        if (!ok) break;
-        mma_commit(tfull0 + 8 * acc);      // accumulator ready for the epilogue
-        if (++acc == 2) { acc = 0; aphase ^= 1u; }
       }
       if (issued) {
         // all MMAs of this CTA complete before TMEM is released
@@ -302,60 +316,70 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
-    const int quarter = warp & 3;   // TMEM lanes 32*quarter .. +31
-    int acc = 0;
-    uint32_t aphase = 0;
+    // warp w: TMEM lane quarter w % 4, column half (w - 2) / 4; each thread
+    // owns one output row and 128 consecutive columns of the tile
+    const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
     const bool f64_out = p.ddt == ARMA_F64;
     const float alpha_f = (float)p.alpha, beta_f = (float)p.beta;
+    int acc = 0;
+    uint32_t aphase = 0;
     for (int32_t w = blockIdx.x; w < total_work; w += gridDim.x) {
       WorkItem it = work_item(p, w);
-      // warp-uniform decision: tcgen05.ld below is .sync.aligned
-      bool ok = mbar_wait(tfull0 + 8 * acc, aphase, abort);
-      if (!__all_sync(0xffffffffu, ok)) break;
-      fence_after();
+      float sum[BN / 2];
+#pragma unroll
+      for (int j = 0; j < BN / 2; ++j) sum[j] = 0.f;
+      bool ok = true;
+      for (int32_t c = 0; c < p.nchunks; ++c) {
+        // warp-uniform decision: tcgen05.ld below is .sync.aligned
+        ok = __all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * acc, aphase, abort));
+        if (!ok) break;
+        fence_after();
+        const uint32_t tb = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN + half * (BN / 2));
+#pragma unroll
+        for (int c0 = 0; c0 < BN / 2; c0 += 16) {
+          float v[16];
+          tmem_ld16(tb + (uint32_t)c0, v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) sum[c0 + j] += v[j];
+        }
+        fence_before();
+        mbar_arrive(tempty0 + 8 * acc);
+        if (++acc == 2) { acc = 0; aphase ^= 1u; }
+      }
+      if (!ok) break;
       const int64_t row = (int64_t)it.tm * BM + quarter * 32 + lane;
-      const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
-      const bool row_ok = row < p.m;
-      double rsv = 1.0;
-      if (!p.partial && p.rs && row_ok) rsv = load_as<double>(p.rs, row * p.rs_inc, p.rsdt);
-      const float rsf = (float)rsv;
-#pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        float v[16];
-        tmem_ld16(tbase + (uint32_t)c0, v);
-        if (!row_ok) continue;
-        const int64_t col0 = (int64_t)it.tn * BN + c0;
-        if (p.partial) {
-          float* dst = p.P + (int64_t)it.split * p.m * p.n + row;
+      if (row >= p.m) continue;
+      const int64_t col0 = (int64_t)it.tn * BN + half * (BN / 2);
+      if (p.partial) {
+        float* dst = p.P + (int64_t)it.split * p.m * p.n + row;
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (col0 + j < p.n) dst[(col0 + j) * p.m] = v[j];
-        } else if (f64_out) {
+        for (int j = 0; j < BN / 2; ++j)
+          if (col0 + j < p.n) dst[(col0 + j) * p.m] = sum[j];
+      } else if (f64_out) {
+        const double rsv = p.rs ? load_as<double>(p.rs, row * p.rs_inc, p.rsdt) : 1.0;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int64_t col = col0 + j;
-            if (col >= p.n) break;
-            double r = p.alpha * (double)v[j] * rsv;
-            if (p.cs) r *= load_as<double>(p.cs, col * p.cs_inc, p.csdt);
-            if (p.C && p.beta != 0.0) r += p.beta * load_as<double>(p.C, row + col * p.ldc, p.cdt);
-            static_cast<double*>(p.D)[row + col * p.ldd] = r;
-          }
-        } else {
-          // FP32 / BF16 results: FP32 epilogue arithmetic (no FP64 pipe)
+        for (int j = 0; j < BN / 2; ++j) {
+          const int64_t col = col0 + j;
+          if (col >= p.n) break;
+          double r = p.alpha * (double)sum[j] * rsv;
+          if (p.cs) r *= load_as<double>(p.cs, col * p.cs_inc, p.csdt);
+          if (p.C && p.beta != 0.0) r += p.beta * load_as<double>(p.C, row + col * p.ldc, p.cdt);
+          static_cast<double*>(p.D)[row + col * p.ldd] = r;
+        }
+      } else {
+        // FP32 / BF16 results: FP32 epilogue arithmetic (no FP64 pipe)
+        const float rsf = p.rs ? load_as<float>(p.rs, row * p.rs_inc, p.rsdt) : 1.f;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int64_t col = col0 + j;
-            if (col >= p.n) break;
-            float r = alpha_f * v[j] * rsf;
-            if (p.cs) r *= load_as<float>(p.cs, col * p.cs_inc, p.csdt);
-            if (p.C && p.beta != 0.0) r = fmaf(beta_f, load_as<float>(p.C, row + col * p.ldc, p.cdt), r);
-            store_as<float>(p.D, row + col * p.ldd, p.ddt, r);
-          }
+        for (int j = 0; j < BN / 2; ++j) {
+          const int64_t col = col0 + j;
+          if (col >= p.n) break;
+          float r = alpha_f * sum[j] * rsf;
+          if (p.cs) r *= load_as<float>(p.cs, col * p.cs_inc, p.csdt);
+          if (p.C && p.beta != 0.0) r = fmaf(beta_f, load_as<float>(p.C, row + col * p.ldc, p.cdt), r);
+          store_as<float>(p.D, row + col * p.ldd, p.ddt, r);
         }
       }
-      fence_before();
-      mbar_arrive(tempty0 + 8 * acc);
-      if (++acc == 2) { acc = 0; aphase ^= 1u; }
     }
   }
 
@@ -488,7 +512,7 @@ __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ Co
 struct Geometry {
   int32_t terms;    // slice products accumulated (1 or 6)
   int32_t slices;   // BF16 slices stored per operand (1 or 3)
-  int32_t splits, kb_per_split, tiles_m, tiles_n;
+  int32_t splits, kb_per_split, chunk_kb, nchunks, tiles_m, tiles_n;
   int64_t mpad, npad, kp;
   int64_t a_bytes, b_bytes, p_bytes;
 };
@@ -503,15 +527,17 @@ Geometry geometry(int64_t m, int64_t n, int64_t k, int32_t tier) {
   g.tiles_m = (int32_t)(g.mpad / BM);
   g.tiles_n = (int32_t)(g.npad / BN);
   const int64_t kb = (k + BK - 1) / BK;
-  // K chunks: at most 2048 of K per FP32 accumulator for the split tier,
-  // and enough work items to fill the GPU when the output is small
-  int64_t max_chunk_kb = g.terms > 1 ? 2048 / BK : kb;
-  int64_t splits = (kb + max_chunk_kb - 1) / max_chunk_kb;
+  // split K over CTAs only when the output has too few tiles to fill the GPU
+  int64_t splits = 1;
   const int64_t tiles = (int64_t)g.tiles_m * g.tiles_n;
   while (tiles * splits < 148 && kb / (splits * 2) >= 4) splits *= 2;
   if (splits > kb) splits = kb > 0 ? kb : 1;
   g.splits = (int32_t)(splits < 1 ? 1 : splits);
   g.kb_per_split = (int32_t)((kb + g.splits - 1) / g.splits);
+  // accumulate at most 256 of K per TMEM chunk for the split tier
+  g.chunk_kb = g.terms > 1 ? 256 / BK : g.kb_per_split;
+  if (g.chunk_kb < 1) g.chunk_kb = 1;
+  g.nchunks = (g.kb_per_split + g.chunk_kb - 1) / g.chunk_kb;
   g.a_bytes = (int64_t)g.slices * g.mpad * g.kp * 2;
   g.b_bytes = (int64_t)g.slices * g.npad * g.kp * 2;
   g.p_bytes = g.splits > 1 ? (int64_t)g.splits * m * n * 4 : 0;
@@ -596,6 +622,7 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   p.m = a.m; p.n = a.n; p.k = a.k;
   p.mpad = g.mpad; p.npad = g.npad; p.kp = g.kp;
   p.terms = g.terms; p.splits = g.splits; p.kb_per_split = g.kb_per_split;
+  p.chunk_kb = g.chunk_kb; p.nchunks = g.nchunks;
   p.tiles_m = g.tiles_m; p.tiles_n = g.tiles_n;
   p.partial = g.splits > 1 ? 1 : 0;
   p.P = P;
