@@ -53,6 +53,11 @@ def args():
     p.add_argument("--literal-steps", type=int, default=5)
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--workload", default="fused",
+                   choices=["fused", "products", "chain", "solve", "plain", "batched", "planner"],
+                   help="fused (default) is the benchmark line; the others measure the remaining "
+                        "expression families and print one JSON line each")
+    p.add_argument("--tiers", default="bf16,split_bf16")
     return p.parse_args()
 
 
@@ -175,10 +180,94 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def time_ms(fn, steps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def tensor_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["bf16_tflops"]), float(p["bf16_tflops_sustained"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, 1700.0, "fallback"
+
+
+def dev_matrix(seed, stream, rows, cols, dtype, dev):
+    import numpy as np
+    import torch
+    import synth
+    h = synth.matrix(seed, stream, rows, cols, "f64")
+    td = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[dtype]
+    return h, torch.from_numpy(np.ascontiguousarray(h.T)).to(dev).to(td).t()
+
+
+def bench_products(a):
+    """2*trans(A)*B + C, A, B, C n x n FP64, per precision tier."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_2502_03000_gb300 as ag
+    from paper_2502_03000_gb300 import expr as E
+    dev = torch.device("cuda", 0)
+    n = a.n
+    host, ins = [], []
+    for s in range(3):
+        h, d = dev_matrix(20250203 + 3, s + 1, n, n, "f64", dev)
+        host.append(h)
+        ins.append(d)
+    nodes, outs = E.config_products(n, "f64")
+    peak, peak_sus, src = tensor_peak()
+    stream = torch.cuda.current_stream(dev)
+    rng = np.random.default_rng(3)
+    ii, jj = rng.integers(0, n, 128), rng.integers(0, n, 128)
+    At = np.asfortranarray(host[0].T)
+    ref = 2.0 * oracle.matmul_entries(At, host[1], ii, jj) + host[2][ii, jj]
+    flops = 2.0 * n ** 3
+    res = {}
+    for tier in a.tiers.split(","):
+        plan = ag.Plan(nodes, outs, tier=tier)
+        out = plan.alloc_outputs(dev)
+        plan(*ins, outputs=out)
+        torch.cuda.synchronize()
+        steps = a.steps if tier != "f64" else 1
+        ms = time_ms(lambda: plan(*ins, outputs=out), steps, stream)
+        got = out[0][torch.as_tensor(ii), torch.as_tensor(jj)].double().cpu().numpy()
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        lit = ag.Plan(nodes, outs, tier=tier, flags=ag.PLAN_LITERAL)
+        lout = lit.alloc_outputs(dev)
+        lit(*ins, outputs=lout)
+        torch.cuda.synchronize()
+        lms = time_ms(lambda: lit(*ins, outputs=lout), max(1, steps // 4), stream)
+        del lout
+        lit._ws.clear()
+        terms = 6 if tier == "split_bf16" else 1
+        r = {"ms": ms, "useful_tflops": flops / ms / 1e9, "err_vs_oracle": err, "literal_ms": lms,
+             "vs_literal": lms / ms, "kernels": [st["kernel"] for st in plan.info["steps"]]}
+        if tier != "f64":
+            r["issued_tflops"] = terms * flops / ms / 1e9
+            r["frac_of_bf16_peak"] = r["issued_tflops"] / peak
+        res[tier] = r
+        plan._ws.clear()
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": f"2*trans(A)*B+C, A,B,C {n}x{n} FP64 uniform[-1,1]", "n": n,
+                      "bf16_peak_tflops": peak, "peak_source": src, "tiers": res}), flush=True)
+
+
 def main():
     a = args()
     if a.impl == "reference":
         run_reference(a)
+        return
+    if a.workload == "products":
+        bench_products(a)
         return
     import numpy as np
     import torch
