@@ -157,10 +157,13 @@ struct GemmArgs {
   int32_t tier;
   void* scratch; int64_t scratch_bytes;
   int32_t* status;   // workspace status word (device-side failures)
+  const int* skip;   // optional: the kernels return at once when *skip != 0
 };
 
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s, int* launches);
 int64_t gemm_scratch_bytes(const GemmStep& g);
+int64_t gemm_tc_scratch_bytes(int64_t m, int64_t n, int64_t k, int32_t tier);
+int64_t gemm_simt_scratch_bytes(int64_t m, int64_t n, int64_t k);
 
 // trace(op(A) * op(B)) -> FP64 scalar.  op(A) is m x k, op(B) is k x n;
 // the sum runs over i < min(m, n), l < k.

@@ -13,7 +13,6 @@ namespace arma {
 
 cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches);
 bool gemm_tc_supported(const GemmArgs& a);
-int64_t gemm_tc_scratch_bytes(int64_t m, int64_t n, int64_t k, int32_t tier);
 
 namespace {
 
@@ -23,18 +22,25 @@ namespace {
 // ---------------------------------------------------------------------------
 constexpr int BM = 64, BN = 64, BK = 16;
 
+// blockIdx.z selects a K range when the output has too few tiles to fill
+// the GPU; those partial sums go to scratch (FP64) and a second kernel
+// combines them in a fixed order.
 template <typename AT>
 __global__ void __launch_bounds__(256) gemm_simt_kernel(const __grid_constant__ GemmArgs a) {
+  if (a.skip && *a.skip) return;
   __shared__ AT As[BK][BM + 1];
   __shared__ AT Bs[BK][BN + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t i0 = (int64_t)blockIdx.x * BM, j0 = (int64_t)blockIdx.y * BN;
+  const int64_t kchunk = (a.k + gridDim.z - 1) / gridDim.z;
+  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+  const int64_t kend = kbeg + kchunk < a.k ? kbeg + kchunk : a.k;
   AT acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = 0;
-  for (int64_t l0 = 0; l0 < a.k; l0 += BK) {
+  for (int64_t l0 = kbeg; l0 < kend; l0 += BK) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       int e = tid + r * 256;
@@ -42,14 +48,14 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const __grid_constant__ 
       if (!a.ta) { ii = e & 63; ll = e >> 6; } else { ll = e & 15; ii = e >> 4; }
       int64_t gi = i0 + ii, gl = l0 + ll;
       AT v = 0;
-      if (gi < a.m && gl < a.k) v = load_as<AT>(a.A, a.ta ? gl + gi * a.lda : gi + gl * a.lda, a.adt);
+      if (gi < a.m && gl < kend) v = load_as<AT>(a.A, a.ta ? gl + gi * a.lda : gi + gl * a.lda, a.adt);
       As[ll][ii] = v;
       int jj;
       if (!a.tb) { ll = e & 15; jj = e >> 4; } else { jj = e & 63; ll = e >> 6; }
       int64_t gj = j0 + jj;
       gl = l0 + ll;
       AT w = 0;
-      if (gl < a.k && gj < a.n) w = load_as<AT>(a.B, a.tb ? gj + gl * a.ldb : gl + gj * a.ldb, a.bdt);
+      if (gl < kend && gj < a.n) w = load_as<AT>(a.B, a.tb ? gj + gl * a.ldb : gl + gj * a.ldb, a.bdt);
       Bs[ll][jj] = w;
     }
     __syncthreads();
@@ -66,6 +72,20 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const __grid_constant__ 
         for (int c = 0; c < 4; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
     }
     __syncthreads();
+  }
+  if (gridDim.z > 1) {
+    double* P = static_cast<double*>(a.scratch) + (int64_t)blockIdx.z * a.m * a.n;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int64_t j = j0 + ty + 16 * c;
+      if (j >= a.n) continue;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        int64_t i = i0 + tx + 16 * r;
+        if (i < a.m) P[i + j * a.m] = (double)acc[r][c];
+      }
+    }
+    return;
   }
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
@@ -85,6 +105,30 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const __grid_constant__ 
   }
 }
 
+__global__ void __launch_bounds__(256) gemm_simt_combine_kernel(const __grid_constant__ GemmArgs a, int splits) {
+  if (a.skip && *a.skip) return;
+  const int64_t total = a.m * a.n;
+  const double* P = static_cast<const double*>(a.scratch);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = t / a.m, i = t - j * a.m;
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z) s += P[(int64_t)z * total + t];
+    double v = a.alpha * s;
+    if (a.rs) v *= load_as<double>(a.rs, i * a.rs_inc, a.rsdt);
+    if (a.cs) v *= load_as<double>(a.cs, j * a.cs_inc, a.csdt);
+    if (a.C && a.beta != 0.0) v += a.beta * load_as<double>(a.C, i + j * a.ldc, a.cdt);
+    store_as<double>(a.D, i + j * a.ldd, a.ddt, v);
+  }
+}
+
+int simt_splits(int64_t m, int64_t n, int64_t k) {
+  const int64_t tiles = ((m + BM - 1) / BM) * ((n + BN - 1) / BN);
+  const int64_t want = 2 * (int64_t)152;
+  int64_t s = 1;
+  while (tiles * s < want && k / (s * 2) >= 4 * BK && s < 32) s *= 2;
+  return (int)s;
+}
+
 // ---------------------------------------------------------------------------
 // GEMV: y_i = alpha * sum_l M(i, l) x_l, M(i, l) at M[i*rsm + l*csm].
 // ---------------------------------------------------------------------------
@@ -100,6 +144,7 @@ struct GemvArgs {
   double scal;
   double* partials;  // [splits][rows] when splits > 1
   int32_t splits;
+  const int* skip;
 };
 
 __device__ __forceinline__ void gemv_out(const GemvArgs& a, int64_t i, double sum) {
@@ -112,6 +157,7 @@ __device__ __forceinline__ void gemv_out(const GemvArgs& a, int64_t i, double su
 
 // rows contiguous in memory (rsm == 1): one thread per row, k split in chunks
 __global__ void __launch_bounds__(256) gemv_rows_kernel(const __grid_constant__ GemvArgs a) {
+  if (a.skip && *a.skip) return;
   __shared__ double xs[256];
   const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
   const int64_t chunk = (a.k + a.splits - 1) / a.splits;
@@ -139,6 +185,7 @@ __global__ void __launch_bounds__(256) gemv_rows_kernel(const __grid_constant__ 
 }
 
 __global__ void gemv_finish_kernel(const __grid_constant__ GemvArgs a) {
+  if (a.skip && *a.skip) return;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.rows) return;
   double sum = 0.0;
@@ -148,6 +195,7 @@ __global__ void gemv_finish_kernel(const __grid_constant__ GemvArgs a) {
 
 // the reduction index contiguous (csm == 1): one warp per output
 __global__ void __launch_bounds__(256) gemv_cols_kernel(const __grid_constant__ GemvArgs a) {
+  if (a.skip && *a.skip) return;
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (i >= a.rows) return;
@@ -174,6 +222,7 @@ cudaError_t launch_gemv(const GemmArgs& a, cudaStream_t s, int* launches) {
   g.alpha = a.alpha;
   g.beta = a.beta;
   g.scal = 1.0;
+  g.skip = a.skip;
   if (a.n == 1) {
     // y (m) = op(A) (m x k) * op(B)(:, 0)
     g.rows = a.m; g.k = a.k;
@@ -282,25 +331,40 @@ __global__ void __launch_bounds__(256) diag_build_kernel(const __grid_constant__
 
 }  // namespace
 
+int64_t gemm_simt_scratch_bytes(int64_t m, int64_t n, int64_t k) {
+  const int s = simt_splits(m, n, k);
+  return s > 1 ? (int64_t)s * m * n * 8 : 0;
+}
+
 int64_t gemm_scratch_bytes(const GemmStep& g) {
   if (g.n == 1 || g.m == 1) {
     int64_t rows = g.n == 1 ? g.m : g.n;
     return 64 * rows * 8;
   }
-  return gemm_tc_scratch_bytes(g.m, g.n, g.k, g.tier);
+  const int64_t tc = gemm_tc_scratch_bytes(g.m, g.n, g.k, g.tier);
+  const int64_t simt = gemm_simt_scratch_bytes(g.m, g.n, g.k);
+  return tc > simt ? tc : simt;
 }
 
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s, int* launches) {
   if (a.m == 0 || a.n == 0) return cudaSuccess;
   if (a.n == 1 || a.m == 1) return launch_gemv(a, s, launches);
   if (a.tier != ARMA_TIER_F64 && gemm_tc_supported(a)) return launch_gemm_tc(a, s, launches);
-  dim3 grid((unsigned)((a.m + BM - 1) / BM), (unsigned)((a.n + BN - 1) / BN));
+  int splits = simt_splits(a.m, a.n, a.k);
+  if (splits > 1 && (!a.scratch || a.scratch_bytes < (int64_t)splits * a.m * a.n * 8)) splits = 1;
+  dim3 grid((unsigned)((a.m + BM - 1) / BM), (unsigned)((a.n + BN - 1) / BN), (unsigned)splits);
   if (grid.y > 65535) return cudaErrorInvalidConfiguration;
   if (a.tier == ARMA_TIER_F64 || a.adt == ARMA_F64 || a.bdt == ARMA_F64)
     gemm_simt_kernel<double><<<grid, 256, 0, s>>>(a);
   else
     gemm_simt_kernel<float><<<grid, 256, 0, s>>>(a);
   if (launches) ++*launches;
+  if (splits > 1) {
+    const int64_t total = a.m * a.n;
+    int64_t blocks = (total + 255) / 256, cap = (int64_t)device_sm_count() * 8;
+    gemm_simt_combine_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(a, splits);
+    if (launches) ++*launches;
+  }
   return cudaGetLastError();
 }
 

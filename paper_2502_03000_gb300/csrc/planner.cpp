@@ -639,6 +639,11 @@ void Planner::emit_solve(const MatOperand& A, int64_t n, const MatOperand* B, in
   if (B) s.B = *B;
   s.X = X;
   s.tier = solve_tier(dt);
+  // an explicit inverse has no right-hand side to refine against: FP64 data
+  // is factored in FP64 (the paper's naive GETRF + GETRI in the data's type)
+  if (explicit_inverse && dt == ARMA_F64 &&
+      (e_.tier == ARMA_TIER_NATIVE || e_.tier == ARMA_TIER_LU32_IR64))
+    s.tier = ARMA_TIER_F64;
   s.explicit_inverse = explicit_inverse ? 1 : 0;
   s.scratch_bytes = solve_scratch_bytes(n, s.nrhs, s.tier);
   s.scratch = ref_ws(alloc_ws(s.scratch_bytes));

@@ -1,0 +1,106 @@
+"""inv(A)*B as a solve (Sec. I; Sec. III (9)): blocked LU with partial
+pivoting and, for the mixed-precision tiers, FP64 iterative refinement.
+Checked against the oracle's literal Gauss-Jordan inverse times B, against
+the normwise backward error, and for the reported device status."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2502_03000_gb300 as ag
+import synth
+from paper_2502_03000_gb300 import expr as E
+from tests.gpu_util import TOL, check, need_gpu, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return need_gpu()
+
+
+def solve(torch, A, B, tier="native", flags=0, dtype="f64"):
+    n, nrhs = B.shape
+    nodes, outs = E.config_solve(n, nrhs, dtype)
+    plan = ag.Plan(nodes, outs, tier=tier, flags=flags)
+    (X,) = plan(to_dev(A, dtype), to_dev(B, dtype))
+    torch.cuda.synchronize()
+    return to_host(X), plan.status()
+
+
+def well_conditioned(seed, n):
+    return synth.matrix(seed, 1, n, n, "f64") + n * np.eye(n) * 0.1 + np.eye(n)
+
+
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (5, 3), (64, 1), (65, 7), (200, 64), (257, 33)])
+@pytest.mark.parametrize("tier", ["f64", "lu32_ir64", "split_bf16"])
+def test_solve_small(torch, n, nrhs, tier):
+    A = well_conditioned(n, n)
+    B = synth.matrix(n + 1, 2, n, nrhs, "f64")
+    X, (st, info) = solve(torch, A, B, tier)
+    assert st == "ok", (st, info)
+    ref = oracle.solve_literal(A, B)
+    tol = {"f64": 1e-12, "lu32_ir64": 1e-12, "split_bf16": 1e-5}[tier]
+    assert oracle.rel_err(X, ref) <= tol
+    if tier != "split_bf16":
+        assert oracle.backward_error(A, X, B) <= 1e-14
+
+
+def test_solve_needs_pivoting(torch):
+    """a permutation-like matrix whose leading entries are zero"""
+    n = 97
+    P = np.eye(n)[np.random.default_rng(0).permutation(n)]
+    A = P + 1e-3 * synth.matrix(3, 1, n, n, "f64")
+    B = synth.matrix(3, 2, n, 4, "f64")
+    for tier in ("f64", "lu32_ir64"):
+        X, (st, _) = solve(torch, A, B, tier)
+        assert st == "ok"
+        assert oracle.rel_err(X, oracle.solve_literal(A, B)) <= 1e-11
+
+
+def test_singular_reported(torch):
+    n = 40
+    A = synth.matrix(4, 1, n, n, "f64")
+    A[:, 17] = 0.0
+    B = synth.matrix(4, 2, n, 2, "f64")
+    X, (st, info) = solve(torch, A, B, "f64")
+    assert st == "singular" and info >= 1
+
+
+@pytest.mark.parametrize("flags", [0, ag.PLAN_LITERAL])
+def test_explicit_inverse_and_literal(torch, flags):
+    n = 130
+    A = well_conditioned(7, n)
+    g = E.Graph()
+    Ai = g.input(0, n, n)
+    Bi = g.input(1, n, 5)
+    nodes, outs = g.build(E.inv(Ai), E.inv(Ai) * Bi)
+    B = synth.matrix(7, 2, n, 5, "f64")
+    plan = ag.Plan(nodes, outs, flags=flags)
+    got = plan(to_dev(A), to_dev(B))
+    torch.cuda.synchronize()
+    check(got, oracle.evaluate(nodes, outs, [A, B]), 1e-11, f"inverse flags={flags}")
+
+
+def test_solve_f32_inputs(torch):
+    n = 300
+    A = synth.cast(well_conditioned(9, n), "f32")
+    B = synth.matrix(9, 2, n, 8, "f32")
+    X, (st, _) = solve(torch, A, B, "native", dtype="f32")
+    assert st == "ok"
+    assert oracle.rel_err(X, oracle.solve_literal(A, B)) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_solve_conditioned_benchmark_size(torch, symmetric):
+    """A = Q1 diag(s) Q2^T, n = 4096, kappa = 1e6, B 4096 x 64 (the benchmark
+    configuration): backward error <= 1e-12, forward error <= 1e-12 * kappa
+    against an independent library solve."""
+    n, nrhs = 4096, 64
+    A = synth.conditioned_matrix(20250203 + 3, n, 1e6, symmetric=symmetric)
+    B = synth.matrix(20250203 + 3, 2, n, nrhs, "f64")
+    X, (st, info) = solve(torch, A, B, "lu32_ir64")
+    assert st == "ok", (st, info)
+    assert oracle.backward_error(A, X, B) <= 1e-12
+    Xn = np.linalg.solve(A, B)
+    assert oracle.rel_err(X, Xn) <= 1e-12 * 1e6
