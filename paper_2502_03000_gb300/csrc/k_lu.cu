@@ -343,15 +343,10 @@ __global__ void ir_update_kernel(double* X, const float* D, int64_t total, const
     X[t] += (double)D[t];
 }
 
-// sum of squares of a contiguous FP64 / FP32 array into out[k] (one block)
-template <typename T>
-__global__ void sumsq_kernel(const T* x, int64_t count, int64_t ld, int64_t rows, double* out, int k) {
+// second stage of a sum of squares: add the per-block partials in order
+__global__ void sum_partials_kernel(const double* part, int count, double* out, int k) {
   double s = 0.0;
-  for (int64_t t = threadIdx.x; t < count; t += blockDim.x) {
-    const int64_t c = t / rows, i = t - c * rows;
-    const double v = (double)x[i + c * ld];
-    s = fma(v, v, s);
-  }
+  for (int t = threadIdx.x; t < count; t += blockDim.x) s += part[t];
   double q = 0.0;
   block_sum2(s, q);
   if (threadIdx.x == 0) out[k] = s;
@@ -359,7 +354,7 @@ __global__ void sumsq_kernel(const T* x, int64_t count, int64_t ld, int64_t rows
 
 __global__ void sumsq_any_kernel(const void* x, int32_t dt, int64_t ld, int64_t rows, int64_t cols,
                                  double* partial) {
-  // grid-wide partials, finished by sumsq_kernel<double>
+  // per-block sums of squares, added up by sum_partials_kernel
   double s = 0.0;
   const int64_t total = rows * cols;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -553,9 +548,9 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
   store_kernel<float><<<grid_for(n * nrhs), 256, 0, s>>>(Y, n, nrhs, X64, n, ARMA_F64);
   // |A|_F, |B|_F once
   sumsq_any_kernel<<<512, 256, 0, s>>>(a.A, a.adt, a.lda, n, n, part);
-  sumsq_kernel<double><<<1, 256, 0, s>>>(part, 512, 512, 512, sq, 0);
+  sum_partials_kernel<<<1, 256, 0, s>>>(part, 512, sq, 0);
   sumsq_any_kernel<<<512, 256, 0, s>>>(a.B, a.bdt, a.ldb, n, nrhs, part);
-  sumsq_kernel<double><<<1, 256, 0, s>>>(part, 512, 512, 512, sq, 1);
+  sum_partials_kernel<<<1, 256, 0, s>>>(part, 512, sq, 1);
   norms_init_kernel<<<1, 32, 0, s>>>(ctl, sq);
   if (launches) *launches += 6;
   for (int it = 1; it <= MAX_IR; ++it) {
@@ -575,9 +570,9 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
     e = launch_gemm(g, s, launches);
     if (e != cudaSuccess) return e;
     sumsq_any_kernel<<<512, 256, 0, s>>>(R64, ARMA_F64, n, n, nrhs, part);
-    sumsq_kernel<double><<<1, 256, 0, s>>>(part, 512, 512, 512, sq + 2, 0);
+    sum_partials_kernel<<<1, 256, 0, s>>>(part, 512, sq + 2, 0);
     sumsq_any_kernel<<<512, 256, 0, s>>>(X64, ARMA_F64, n, n, nrhs, part);
-    sumsq_kernel<double><<<1, 256, 0, s>>>(part, 512, 512, 512, sq + 2, 1);
+    sum_partials_kernel<<<1, 256, 0, s>>>(part, 512, sq + 2, 1);
     ir_check_kernel<<<1, 32, 0, s>>>(ctl, sq + 2, it, a.status_code, a.status_info, it == MAX_IR);
     // d = (LU)^-1 P r in FP32; x += d
     gather_kernel<float><<<grid_for(n * nrhs), 256, 0, s>>>(R64, n, ARMA_F64, perm, Y, n, nrhs, &ctl->done);
