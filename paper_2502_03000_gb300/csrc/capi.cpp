@@ -56,6 +56,7 @@ arma_status run_step(const Step& st, const Bind& b, cudaStream_t s, int* launche
       for (int i = 0; i < e.nops; ++i) {
         a.ops[i] = e.ops[i];
         a.ops[i].sf = static_cast<float>(e.ops[i].s);
+        a.ops[i].sl = static_cast<float>(e.ops[i].s - static_cast<double>(a.ops[i].sf));
       }
       a.out = e.out.valid() ? mptr(b, e.out) : nullptr;
       a.out_ld = e.out_ld;

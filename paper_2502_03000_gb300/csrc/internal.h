@@ -67,8 +67,8 @@ struct EwIns {
   int32_t op;
   int32_t arg;   // operand index k or slot j
   double s;
-  float sf = 0.f;  // s rounded to FP32 (filled at eval time for FP32 passes)
-  int32_t pad = 0;
+  float sf = 0.f;  // s as a float pair sf + sl (filled at eval time):
+  float sl = 0.f;  //   sf alone is the FP32 scalar of FP32 passes
 };
 
 enum EwMode : int32_t { EW_FLAT = 0, EW_GRID = 1, EW_DIAG = 2 };

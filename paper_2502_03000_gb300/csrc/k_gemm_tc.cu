@@ -34,6 +34,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace arma {
 
@@ -68,6 +69,7 @@ struct Params {
   void* D; int64_t ldd; int32_t ddt;
   const void* C; int64_t ldc; int32_t cdt;
   double alpha, beta;
+  float beta_h, beta_l;     // beta as an exact float pair (FP64 epilogue)
   const void* rs; int64_t rs_inc; int32_t rsdt;
   const void* cs; int64_t cs_inc; int32_t csdt;
   int32_t* status;          // workspace status word (0 = ok)
@@ -357,15 +359,32 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int j = 0; j < BN / 2; ++j)
           if (col0 + j < p.n) dst[(col0 + j) * p.m] = sum[j];
       } else if (f64_out) {
-        const double rsv = p.rs ? load_as<double>(p.rs, row * p.rs_inc, p.rsdt) : 1.0;
+        // FP64 results without FP64 instructions: the FP32 accumulator is
+        // scaled in FP32, beta*C is added as an exact float pair and the
+        // pair is assembled into a double with integer operations
+        const float rsf = p.rs ? load_as<float>(p.rs, row * p.rs_inc, p.rsdt) : 1.f;
+        const ff::F2 b2{p.beta_h, p.beta_l};
+        double* Dd = static_cast<double*>(p.D);
 #pragma unroll
         for (int j = 0; j < BN / 2; ++j) {
           const int64_t col = col0 + j;
           if (col >= p.n) break;
-          double r = p.alpha * (double)sum[j] * rsv;
-          if (p.cs) r *= load_as<double>(p.cs, col * p.cs_inc, p.csdt);
-          if (p.C && p.beta != 0.0) r += p.beta * load_as<double>(p.C, row + col * p.ldc, p.cdt);
-          static_cast<double*>(p.D)[row + col * p.ldd] = r;
+          float r = alpha_f * sum[j] * rsf;
+          if (p.cs) r *= load_as<float>(p.cs, col * p.cs_inc, p.csdt);
+          double out;
+          if (p.C && p.beta != 0.0) {
+            const double cv = load_as<double>(p.C, row + col * p.ldc, p.cdt);
+            ff::F2 c2, t;
+            bool ok = ff::split(cv, c2);
+            if (ok) {
+              t = ff::axpy(b2, c2, ff::F2{r, 0.f});
+              ok = ff::in_range(t);
+            }
+            out = ok ? ff::to_double(t) : (double)r + p.beta * cv;
+          } else {
+            out = __longlong_as_double((long long)ff::f2d_bits(r));
+          }
+          Dd[row + col * p.ldd] = out;
         }
       } else {
         // FP32 / BF16 results: FP32 epilogue arithmetic (no FP64 pipe)
@@ -412,29 +431,46 @@ __device__ __forceinline__ uint16_t bf16_bits_of_window(uint32_t sign, int32_t e
   return (uint16_t)((sign >> 16) | ((uint32_t)be << 7) | (norm & 0x7Fu));
 }
 
-__device__ __forceinline__ void split3(double x, int dt, uint16_t (&s)[3]) {
-  if (dt == ARMA_F64) {
-    const uint64_t u = (uint64_t)__double_as_longlong(x);
-    const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
-    const int32_t e = (int32_t)((u >> 52) & 0x7FF);
-    if (e == 0 || e == 0x7FF) { s[0] = s[1] = s[2] = 0; return; }
-    const uint64_t m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // 53 bits
-    const int32_t E = e - 1023;   // value = m * 2^(E - 52)
-    s[0] = bf16_bits_of_window(sign, E - 7, (uint32_t)(m >> 45) & 0xFFu);
-    s[1] = bf16_bits_of_window(sign, E - 15, (uint32_t)(m >> 37) & 0xFFu);
-    s[2] = bf16_bits_of_window(sign, E - 23, (uint32_t)(m >> 29) & 0xFFu);
-  } else {
-    const float f = (float)x;   // exact for FP32 / BF16 storage
-    const uint32_t u = __float_as_uint(f);
-    const uint32_t sign = u & 0x80000000u;
-    const int32_t e = (int32_t)((u >> 23) & 0xFF);
-    if (e == 0 || e == 0xFF) { s[0] = s[1] = s[2] = 0; return; }
-    const uint32_t m = (u & 0x7FFFFFu) | (1u << 23);   // 24 bits
-    const int32_t E = e - 127;
-    s[0] = bf16_bits_of_window(sign, E - 7, (m >> 16) & 0xFFu);
-    s[1] = bf16_bits_of_window(sign, E - 15, (m >> 8) & 0xFFu);
-    s[2] = bf16_bits_of_window(sign, E - 23, m & 0xFFu);
-  }
+__device__ __forceinline__ void split3_f64(double x, uint16_t (&s)[3]) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
+  const int32_t e = (int32_t)((u >> 52) & 0x7FF);
+  if (e == 0 || e == 0x7FF) { s[0] = s[1] = s[2] = 0; return; }
+  const uint64_t m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // 53 bits
+  const int32_t E = e - 1023;   // value = m * 2^(E - 52)
+  s[0] = bf16_bits_of_window(sign, E - 7, (uint32_t)(m >> 45) & 0xFFu);
+  s[1] = bf16_bits_of_window(sign, E - 15, (uint32_t)(m >> 37) & 0xFFu);
+  s[2] = bf16_bits_of_window(sign, E - 23, (uint32_t)(m >> 29) & 0xFFu);
+}
+
+__device__ __forceinline__ void split3_f32(float f, uint16_t (&s)[3]) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t sign = u & 0x80000000u;
+  const int32_t e = (int32_t)((u >> 23) & 0xFF);
+  if (e == 0 || e == 0xFF) { s[0] = s[1] = s[2] = 0; return; }
+  const uint32_t m = (u & 0x7FFFFFu) | (1u << 23);   // 24 bits
+  const int32_t E = e - 127;
+  s[0] = bf16_bits_of_window(sign, E - 7, (m >> 16) & 0xFFu);
+  s[1] = bf16_bits_of_window(sign, E - 15, (m >> 8) & 0xFFu);
+  s[2] = bf16_bits_of_window(sign, E - 23, m & 0xFFu);
+}
+
+// double -> BF16, round to nearest even, integer operations only
+__device__ __forceinline__ uint16_t d2bf16_rn(double x) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  const uint16_t sign = (uint16_t)((u >> 48) & 0x8000u);
+  const int32_t e = (int32_t)((u >> 52) & 0x7FF);
+  const uint64_t m = u & 0xFFFFFFFFFFFFFull;
+  if (e == 0x7FF) return (uint16_t)(sign | 0x7F80u | (m ? 0x40u : 0u));
+  int32_t be = e - 1023 + 127;
+  if (e == 0 || be <= 0) return sign;                 // zero / below BF16 normal range
+  uint32_t keep = (uint32_t)(m >> 45);                // 7 fraction bits
+  const uint64_t rem = m & ((1ull << 45) - 1);
+  const uint64_t half = 1ull << 44;
+  if (rem > half || (rem == half && (keep & 1u))) ++keep;
+  if (keep == 128u) { keep = 0u; ++be; }
+  if (be >= 255) return (uint16_t)(sign | 0x7F80u);
+  return (uint16_t)(sign | ((uint32_t)be << 7) | keep);
 }
 
 struct PrepArgs {
@@ -456,12 +492,18 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepA
     if (a.trans) { l = l0 + tx; r = r0 + q; } else { r = r0 + tx; l = l0 + q; }
     uint16_t s[3] = {0, 0, 0};
     if (r < a.R && l < a.K) {
+      // native loads per storage type: no FP64-pipe conversions
       const int64_t idx = a.trans ? l + r * a.ldx : r + l * a.ldx;
-      const double x = load_as<double>(a.X, idx, a.xdt);
-      if (a.slices == 1) {
-        s[0] = __bfloat16_as_ushort(__float2bfloat16_rn((float)x));
+      if (a.xdt == ARMA_F64) {
+        const double x = static_cast<const double*>(a.X)[idx];
+        if (a.slices == 1) s[0] = d2bf16_rn(x);
+        else split3_f64(x, s);
+      } else if (a.xdt == ARMA_F32) {
+        const float x = static_cast<const float*>(a.X)[idx];
+        if (a.slices == 1) s[0] = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+        else split3_f32(x, s);
       } else {
-        split3(x, a.xdt, s);
+        s[0] = static_cast<const uint16_t*>(a.X)[idx];   // BF16 is its own first slice
       }
     }
     const int rr = (int)(r - r0), ll = (int)(l - l0);
@@ -629,6 +671,8 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   p.D = a.D; p.ldd = a.ldd; p.ddt = a.ddt;
   p.C = a.C; p.ldc = a.ldc; p.cdt = a.cdt;
   p.alpha = a.alpha; p.beta = a.beta;
+  p.beta_h = (float)a.beta;
+  p.beta_l = (float)(a.beta - (double)p.beta_h);
   p.rs = a.rs; p.rs_inc = a.rs_inc; p.rsdt = a.rsdt;
   p.cs = a.cs; p.cs_inc = a.cs_inc; p.csdt = a.csdt;
   p.status = a.status;
