@@ -200,3 +200,16 @@ def test_fused_f64_reductions_any_magnitude(torch, scale):
     host[2][:, : n // 2] *= 1e-12          # a spread of magnitudes inside one pass
     got = run(nodes, outs, host, "f64")
     check(got, oracle.evaluate(nodes, outs, host), TOL["f64"], f"scale {scale}")
+
+
+@pytest.mark.parametrize("s", [1e-50, 3e-13, 1e13, 1e60])
+def test_fused_f64_extreme_scalars(torch, s):
+    """scalars outside the float-pair range send the pass to native FP64"""
+    m, n = 131, 97
+    g = E.Graph()
+    A, B = g.input(0, m, n), g.input(1, m, n)
+    out = s * A + B % A
+    nodes, outs = g.build(out, E.accu(out), E.norm_fro(out))
+    host = inputs(98, [(m, n)] * 2, "f64")
+    got = run(nodes, outs, host, "f64")
+    check(got, oracle.evaluate(nodes, outs, host), TOL["f64"], f"scalar {s}")
