@@ -38,9 +38,14 @@ __device__ __forceinline__ bool split(double x, F2& r) {
   const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
   const unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
   r.h = __uint_as_float(sign | ((e - 896u) << 23) | (unsigned int)(mant >> 29));
-  const float rf = __uint2float_rn((unsigned int)(mant & 0x1FFFFFFFull));  // low 29 bits
-  const float scale = __uint_as_float((e - 948u) << 23);                  // 2^(e-1075)
-  r.l = __fmul_rn(sign ? -rf : rf, scale);
+  // lo: the low 29 significand bits, value rr * 2^(e-1075), built as float
+  // bits with integer operations (truncated to 24 bits)
+  const unsigned int rr = (unsigned int)(mant & 0x1FFFFFFFull);
+  if (rr == 0u) { r.l = 0.f; return true; }
+  const int nb = 32 - __clz(rr);                       // significant bits, 1..29
+  const unsigned int m24 = nb > 24 ? rr >> (nb - 24) : rr << (24 - nb);
+  const unsigned int el = e - 1075u + (unsigned int)(nb - 1) + 127u;   // >= 983-1075+127 > 0
+  r.l = __uint_as_float(sign | (el << 23) | (m24 & 0x7FFFFFu));
   return true;
 }
 

@@ -17,7 +17,6 @@
 #include <type_traits>
 
 #include "common.cuh"
-#include "ff.cuh"
 
 namespace arma {
 
@@ -325,155 +324,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) ew_flat_kernel(co
                   (a.red & 2) ? a.norm_out : nullptr, 1.0);
 }
 
-// ---- FP64 flat path on the FP32 pipes ----
-// The same accumulator machine, with every FP64 value carried as an exact
-// float pair (ff.cuh).  A chunk whose inputs or intermediates leave the
-// pair range is recomputed by the native FP64 interpreter, so results are
-// always within the FP64 tolerance.
-__device__ __noinline__ void ew_chunk_f64(const EwArgs& a, int64_t c, double (&acc)[4]) {
-  for (int v = 0; v < 4; ++v) {
-    const int64_t t = c * 4 + v;
-    double r = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    for (int pc = 0; pc < a.nops; ++pc) {
-      const int op = a.ops[pc].op, arg = a.ops[pc].arg;
-      const double s = a.ops[pc].s;
-      if (uses_operand(op)) {
-        r = ew_in<double>(op, r, static_cast<const double*>(a.in[arg])[t], s);
-      } else if (op == EW_PUSH) {
-        if (arg == 0) s0 = r; else if (arg == 1) s1 = r; else if (arg == 2) s2 = r; else s3 = r;
-      } else if (is_pop(op)) {
-        r = ew_pop<double>(op, arg == 0 ? s0 : arg == 1 ? s1 : arg == 2 ? s2 : s3, r);
-      } else {
-        r = ew_self<double>(op, r, s);
-      }
-    }
-    acc[v] = r;
-  }
-}
-
-template <int NIN, int STK>
-__global__ void __launch_bounds__(256, 2) ew_flat_ff_kernel(const __grid_constant__ EwArgs a) {
-  using ff::F2;
-  constexpr int V = 4;
-  const int64_t total = a.m * a.n;
-  const int64_t nchunk = total / V;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  double rs = 0.0, rq = 0.0;         // native-route contributions
-  F2 fs{0.f, 0.f}, fq{0.f, 0.f};     // pair-route sums
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunk; c += stride) {
-    F2 x[NIN][V];
-    bool ok = true;
-#pragma unroll
-    for (int k = 0; k < NIN; ++k) {
-      const uint4* q = reinterpret_cast<const uint4*>(static_cast<const double*>(a.in[k]) + c * V);
-      const uint4 r0 = __ldcs(q), r1 = __ldcs(q + 1);
-      const double d[4] = {__hiloint2double((int)r0.y, (int)r0.x), __hiloint2double((int)r0.w, (int)r0.z),
-                           __hiloint2double((int)r1.y, (int)r1.x), __hiloint2double((int)r1.w, (int)r1.z)};
-#pragma unroll
-      for (int v = 0; v < V; ++v) ok &= ff::split(d[v], x[k][v]);
-    }
-    F2 acc[V], st[STK > 0 ? STK : 1][V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = F2{0.f, 0.f};
-    for (int pc = 0; pc < a.nops; ++pc) {
-      const int op = a.ops[pc].op, arg = a.ops[pc].arg;
-      const F2 sc{a.ops[pc].sf, a.ops[pc].sl};
-#define ARMA_FF_SEL(BODY)                        \
-  _Pragma("unroll") for (int k = 0; k < NIN; ++k) \
-    if (k == arg) {                              \
-      _Pragma("unroll") for (int v = 0; v < V; ++v) { BODY; } \
-    }
-#define ARMA_FF_STK(BODY)                        \
-  _Pragma("unroll") for (int q = 0; q < STK; ++q) \
-    if (q == arg) {                              \
-      _Pragma("unroll") for (int v = 0; v < V; ++v) { BODY; } \
-    }
-      switch (op) {
-        case EW_LD: ARMA_FF_SEL(acc[v] = x[k][v]) break;
-        case EW_ADD: ARMA_FF_SEL(acc[v] = ff::add(acc[v], x[k][v])) break;
-        case EW_SUB: ARMA_FF_SEL(acc[v] = ff::sub(acc[v], x[k][v])) break;
-        case EW_RSUB: ARMA_FF_SEL(acc[v] = ff::sub(x[k][v], acc[v])) break;
-        case EW_MUL: ARMA_FF_SEL(acc[v] = ff::mul(acc[v], x[k][v])) break;
-        case EW_DIV: ARMA_FF_SEL(acc[v] = ff::div(acc[v], x[k][v])) break;
-        case EW_RDIV: ARMA_FF_SEL(acc[v] = ff::div(x[k][v], acc[v])) break;
-        case EW_AXPY: ARMA_FF_SEL(acc[v] = ff::axpy(sc, x[k][v], acc[v])) break;
-        case EW_SCAL:
-#pragma unroll
-          for (int v = 0; v < V; ++v) acc[v] = ff::mul(sc, acc[v]);
-          break;
-        case EW_DIVS:
-#pragma unroll
-          for (int v = 0; v < V; ++v) acc[v] = ff::div(acc[v], sc);
-          break;
-        case EW_ADDS:
-#pragma unroll
-          for (int v = 0; v < V; ++v) acc[v] = ff::add(acc[v], sc);
-          break;
-        case EW_NEG:
-#pragma unroll
-          for (int v = 0; v < V; ++v) acc[v] = ff::neg(acc[v]);
-          break;
-        case EW_PUSH: ARMA_FF_STK(st[q][v] = acc[v]) break;
-        case EW_POPADD: ARMA_FF_STK(acc[v] = ff::add(st[q][v], acc[v])) break;
-        case EW_POPSUB: ARMA_FF_STK(acc[v] = ff::sub(st[q][v], acc[v])) break;
-        case EW_POPMUL: ARMA_FF_STK(acc[v] = ff::mul(st[q][v], acc[v])) break;
-        case EW_POPDIV: ARMA_FF_STK(acc[v] = ff::div(st[q][v], acc[v])) break;
-        default: break;
-      }
-#undef ARMA_FF_SEL
-#undef ARMA_FF_STK
-#pragma unroll
-      for (int v = 0; v < V; ++v) ok &= ff::in_range(acc[v]);
-    }
-    if (__builtin_expect(ok, 1)) {
-      if (a.out) {
-        double o[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) o[v] = ff::to_double(acc[v]);
-        uint4* q = reinterpret_cast<uint4*>(static_cast<double*>(a.out) + c * V);
-        __stcs(q, make_uint4((unsigned)__double2loint(o[0]), (unsigned)__double2hiint(o[0]),
-                             (unsigned)__double2loint(o[1]), (unsigned)__double2hiint(o[1])));
-        __stcs(q + 1, make_uint4((unsigned)__double2loint(o[2]), (unsigned)__double2hiint(o[2]),
-                                 (unsigned)__double2loint(o[3]), (unsigned)__double2hiint(o[3])));
-      }
-      if (a.red) {
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          fs = ff::add(fs, acc[v]);
-          fq = ff::add(fq, ff::mul(acc[v], acc[v]));
-        }
-      }
-    } else {
-      double r[V];
-      ew_chunk_f64(a, c, r);
-      if (a.out)
-        for (int v = 0; v < V; ++v) static_cast<double*>(a.out)[c * V + v] = r[v];
-      if (a.red)
-        for (int v = 0; v < V; ++v) { rs += r[v]; rq = fma(r[v], r[v], rq); }
-    }
-  }
-  // ragged tail: native FP64, one element per thread
-  for (int64_t t = nchunk * V + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
-    double acc = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    for (int pc = 0; pc < a.nops; ++pc) {
-      const int op = a.ops[pc].op, arg = a.ops[pc].arg;
-      const double s = a.ops[pc].s;
-      if (uses_operand(op)) acc = ew_in<double>(op, acc, static_cast<const double*>(a.in[arg])[t], s);
-      else if (op == EW_PUSH) { if (arg == 0) s0 = acc; else if (arg == 1) s1 = acc; else if (arg == 2) s2 = acc; else s3 = acc; }
-      else if (is_pop(op)) acc = ew_pop<double>(op, arg == 0 ? s0 : arg == 1 ? s1 : arg == 2 ? s2 : s3, acc);
-      else acc = ew_self<double>(op, acc, s);
-    }
-    if (a.out) static_cast<double*>(a.out)[t] = acc;
-    if (a.red) { rs += acc; rq = fma(acc, acc, rq); }
-  }
-  if (a.red) {
-    rs += (double)fs.h + (double)fs.l;
-    rq += (double)fq.h + (double)fq.l;
-    reduce_finish(rs, rq, a.partials, a.ticket, (a.red & 1) ? a.sum_out : nullptr,
-                  (a.red & 2) ? a.norm_out : nullptr, 1.0);
-  }
-}
-
 typedef void (*EwKernel)(EwArgs);
 
 // Resident 256-thread blocks per SM for a kernel (cached): the streaming
@@ -505,33 +355,6 @@ EwKernel pick_flat(int nin) {
   }
 }
 
-template <int STK>
-EwKernel pick_ff(int nin) {
-  switch (nin) {
-    case 1: return ew_flat_ff_kernel<1, STK>;
-    case 2: return ew_flat_ff_kernel<2, STK>;
-    case 3: return ew_flat_ff_kernel<3, STK>;
-    case 4: return ew_flat_ff_kernel<4, STK>;
-    case 5: return ew_flat_ff_kernel<5, STK>;
-    case 6: return ew_flat_ff_kernel<6, STK>;
-    case 7: return ew_flat_ff_kernel<7, STK>;
-    case 8: return ew_flat_ff_kernel<8, STK>;
-    default: return nullptr;
-  }
-}
-
-// scalars of the program must be zero or inside the pair range, otherwise
-// a product with them could leave float range undetected (underflow to 0)
-bool ff_scalars_ok(const EwArgs& a) {
-  for (int i = 0; i < a.nops; ++i) {
-    const int op = a.ops[i].op;
-    if (op != EW_AXPY && op != EW_SCAL && op != EW_DIVS && op != EW_ADDS) continue;
-    const double m = a.ops[i].s < 0 ? -a.ops[i].s : a.ops[i].s;
-    if (m != 0.0 && (m < 0x1p-40 || m > 0x1p40)) return false;
-  }
-  return true;
-}
-
 template <typename T>
 EwKernel pick_flat_t(const EwArgs& a) {
   bool stack = false;
@@ -557,11 +380,8 @@ cudaError_t launch_ew(const EwArgs& a, cudaStream_t s, int* launches) {
     flat &= (a.compute_f64 != 0) == (dt == ARMA_F64);
   }
   EwKernel k;
-  bool stack = false;
-  for (int i = 0; i < a.nops; ++i) stack |= a.ops[i].op == EW_PUSH;
-  if (flat && dt == ARMA_F64 && ff_scalars_ok(a)) k = stack ? pick_ff<kMaxStack>(a.nin) : pick_ff<0>(a.nin);
-  else if (flat) k = dt == ARMA_F64 ? pick_flat_t<double>(a) : dt == ARMA_F32 ? pick_flat_t<float>(a)
-                                                                     : pick_flat_t<__nv_bfloat16>(a);
+  if (flat) k = dt == ARMA_F64 ? pick_flat_t<double>(a) : dt == ARMA_F32 ? pick_flat_t<float>(a)
+                                                                 : pick_flat_t<__nv_bfloat16>(a);
   else k = a.compute_f64 ? ew_strided_kernel<double> : ew_strided_kernel<float>;
   if (!k) return cudaErrorInvalidValue;
   int64_t work = total;

@@ -166,6 +166,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+      ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 struct WorkItem {
   int32_t tm, tn, split;
 };
@@ -328,77 +342,108 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t aphase = 0;
     for (int32_t w = blockIdx.x; w < total_work; w += gridDim.x) {
       WorkItem it = work_item(p, w);
-      float sum[BN / 2];
-#pragma unroll
-      for (int j = 0; j < BN / 2; ++j) sum[j] = 0.f;
+      const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
       bool ok = true;
-      for (int32_t c = 0; c < p.nchunks; ++c) {
-        // warp-uniform decision: tcgen05.ld below is .sync.aligned
-        ok = __all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * acc, aphase, abort));
-        if (!ok) break;
-        fence_after();
-        const uint32_t tb = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN + half * (BN / 2));
+      if (p.nchunks > 1) {
+        // chunks 0..n-2 are added into FP32 registers and released at once;
+        // the last chunk is added too and the sums are written back into
+        // its TMEM buffer, which the store loop below then reads
+        float sum[BN / 2];
 #pragma unroll
-        for (int c0 = 0; c0 < BN / 2; c0 += 16) {
-          float v[16];
-          tmem_ld16(tb + (uint32_t)c0, v);
+        for (int j = 0; j < BN / 2; ++j) sum[j] = 0.f;
+        for (int32_t c = 0; c < p.nchunks; ++c) {
+          ok = __all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * acc, aphase, abort));
+          if (!ok) break;
+          fence_after();
+          const uint32_t tb = tmem_base + lane_base + (uint32_t)(acc * BN + half * (BN / 2));
 #pragma unroll
-          for (int j = 0; j < 16; ++j) sum[c0 + j] += v[j];
-        }
-        fence_before();
-        mbar_arrive(tempty0 + 8 * acc);
-        if (++acc == 2) { acc = 0; aphase ^= 1u; }
-      }
-      if (!ok) break;
-      const int64_t row = (int64_t)it.tm * BM + quarter * 32 + lane;
-      if (row >= p.m) continue;
-      const int64_t col0 = (int64_t)it.tn * BN + half * (BN / 2);
-      if (p.partial) {
-        float* dst = p.P + (int64_t)it.split * p.m * p.n + row;
+          for (int c0 = 0; c0 < BN / 2; c0 += 16) {
+            float v[16];
+            tmem_ld16(tb + (uint32_t)c0, v);
 #pragma unroll
-        for (int j = 0; j < BN / 2; ++j)
-          if (col0 + j < p.n) dst[(col0 + j) * p.m] = sum[j];
-      } else if (f64_out) {
-        // FP64 results without FP64 instructions: the FP32 accumulator is
-        // scaled in FP32, beta*C is added as an exact float pair and the
-        // pair is assembled into a double with integer operations
-        const float rsf = p.rs ? load_as<float>(p.rs, row * p.rs_inc, p.rsdt) : 1.f;
-        const ff::F2 b2{p.beta_h, p.beta_l};
-        double* Dd = static_cast<double*>(p.D);
-#pragma unroll
-        for (int j = 0; j < BN / 2; ++j) {
-          const int64_t col = col0 + j;
-          if (col >= p.n) break;
-          float r = alpha_f * sum[j] * rsf;
-          if (p.cs) r *= load_as<float>(p.cs, col * p.cs_inc, p.csdt);
-          double out;
-          if (p.C && p.beta != 0.0) {
-            const double cv = load_as<double>(p.C, row + col * p.ldc, p.cdt);
-            ff::F2 c2, t;
-            bool ok = ff::split(cv, c2);
-            if (ok) {
-              t = ff::axpy(b2, c2, ff::F2{r, 0.f});
-              ok = ff::in_range(t);
-            }
-            out = ok ? ff::to_double(t) : (double)r + p.beta * cv;
-          } else {
-            out = __longlong_as_double((long long)ff::f2d_bits(r));
+            for (int j = 0; j < 16; ++j) sum[c0 + j] += v[j];
           }
-          Dd[row + col * p.ldd] = out;
+          if (c + 1 < p.nchunks) {
+            fence_before();
+            mbar_arrive(tempty0 + 8 * acc);
+            if (++acc == 2) { acc = 0; aphase ^= 1u; }
+          } else {
+#pragma unroll
+            for (int c0 = 0; c0 < BN / 2; c0 += 16) {
+              float v[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j) v[j] = sum[c0 + j];
+              tmem_st16(tb + (uint32_t)c0, v);
+            }
+            tmem_st_wait();
+          }
         }
       } else {
-        // FP32 / BF16 results: FP32 epilogue arithmetic (no FP64 pipe)
-        const float rsf = p.rs ? load_as<float>(p.rs, row * p.rs_inc, p.rsdt) : 1.f;
+        ok = __all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * acc, aphase, abort));
+        if (ok) fence_after();
+      }
+      if (!ok) break;
+      // store loop: 16 columns at a time from TMEM (compact code)
+      const int64_t row = (int64_t)it.tm * BM + quarter * 32 + lane;
+      const bool row_ok = row < p.m;
+      const int64_t colh = (int64_t)it.tn * BN + half * (BN / 2);
+      const uint32_t tb = tmem_base + lane_base + (uint32_t)(acc * BN + half * (BN / 2));
+      float rsf = 1.f;
+      if (!p.partial && p.rs && row_ok) rsf = load_as<float>(p.rs, row * p.rs_inc, p.rsdt);
+      const ff::F2 b2{p.beta_h, p.beta_l};
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN / 2; c0 += 16) {
+        float v[16];
+        tmem_ld16(tb + (uint32_t)c0, v);
+        if (!row_ok) continue;
+        const int64_t col0 = colh + c0;
+        if (p.partial) {
+          float* dst = p.P + (int64_t)it.split * p.m * p.n + row;
 #pragma unroll
-        for (int j = 0; j < BN / 2; ++j) {
-          const int64_t col = col0 + j;
-          if (col >= p.n) break;
-          float r = alpha_f * sum[j] * rsf;
-          if (p.cs) r *= load_as<float>(p.cs, col * p.cs_inc, p.csdt);
-          if (p.C && p.beta != 0.0) r = fmaf(beta_f, load_as<float>(p.C, row + col * p.ldc, p.cdt), r);
-          store_as<float>(p.D, row + col * p.ldd, p.ddt, r);
+          for (int j = 0; j < 16; ++j)
+            if (col0 + j < p.n) dst[(col0 + j) * p.m] = v[j];
+        } else if (f64_out) {
+          // FP64 results without FP64 instructions: FP32 scaling, beta*C as
+          // an exact float pair, the pair assembled into a double with
+          // integer operations
+          double* Dd = static_cast<double*>(p.D);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int64_t col = col0 + j;
+            if (col >= p.n) break;
+            float r = alpha_f * v[j] * rsf;
+            if (p.cs) r *= load_as<float>(p.cs, col * p.cs_inc, p.csdt);
+            double out;
+            if (p.C && p.beta != 0.0) {
+              const double cv = load_as<double>(p.C, row + col * p.ldc, p.cdt);
+              ff::F2 c2, t;
+              bool fine = ff::split(cv, c2);
+              if (fine) {
+                t = ff::axpy(b2, c2, ff::F2{r, 0.f});
+                fine = ff::in_range(t);
+              }
+              out = fine ? ff::to_double(t) : (double)r + p.beta * cv;
+            } else {
+              out = __longlong_as_double((long long)ff::f2d_bits(r));
+            }
+            Dd[row + col * p.ldd] = out;
+          }
+        } else {
+          // FP32 / BF16 results: FP32 epilogue arithmetic
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int64_t col = col0 + j;
+            if (col >= p.n) break;
+            float r = alpha_f * v[j] * rsf;
+            if (p.cs) r *= load_as<float>(p.cs, col * p.cs_inc, p.csdt);
+            if (p.C && p.beta != 0.0) r = fmaf(beta_f, load_as<float>(p.C, row + col * p.ldc, p.cdt), r);
+            store_as<float>(p.D, row + col * p.ldd, p.ddt, r);
+          }
         }
       }
+      fence_before();
+      mbar_arrive(tempty0 + 8 * acc);
+      if (++acc == 2) { acc = 0; aphase ^= 1u; }
     }
   }
 
