@@ -405,8 +405,16 @@ __global__ void __launch_bounds__(THREADS, 1)
         } else if (f64_out) {
           // FP64 results without FP64 instructions: FP32 scaling, beta*C as
           // an exact float pair, the pair assembled into a double with
-          // integer operations
+          // integer operations.  The 16 C values are loaded before any D
+          // store (C may alias D), so the loads overlap.
           double* Dd = static_cast<double*>(p.D);
+          const bool has_c = p.C && p.beta != 0.0;
+          double cv[16];
+          if (has_c) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              cv[j] = (col0 + j < p.n) ? load_as<double>(p.C, row + (col0 + j) * p.ldc, p.cdt) : 0.0;
+          }
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int64_t col = col0 + j;
@@ -414,15 +422,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             float r = alpha_f * v[j] * rsf;
             if (p.cs) r *= load_as<float>(p.cs, col * p.cs_inc, p.csdt);
             double out;
-            if (p.C && p.beta != 0.0) {
-              const double cv = load_as<double>(p.C, row + col * p.ldc, p.cdt);
+            if (has_c) {
               ff::F2 c2, t;
-              bool fine = ff::split(cv, c2);
+              bool fine = ff::split(cv[j], c2);
               if (fine) {
                 t = ff::axpy(b2, c2, ff::F2{r, 0.f});
                 fine = ff::in_range(t);
               }
-              out = fine ? ff::to_double(t) : (double)r + p.beta * cv;
+              out = fine ? ff::to_double(t) : (double)r + p.beta * cv[j];
             } else {
               out = __longlong_as_double((long long)ff::f2d_bits(r));
             }
@@ -430,13 +437,20 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         } else {
           // FP32 / BF16 results: FP32 epilogue arithmetic
+          const bool has_c = p.C && p.beta != 0.0;
+          float cf[16];
+          if (has_c) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              cf[j] = (col0 + j < p.n) ? load_as<float>(p.C, row + (col0 + j) * p.ldc, p.cdt) : 0.f;
+          }
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int64_t col = col0 + j;
             if (col >= p.n) break;
             float r = alpha_f * v[j] * rsf;
             if (p.cs) r *= load_as<float>(p.cs, col * p.cs_inc, p.csdt);
-            if (p.C && p.beta != 0.0) r = fmaf(beta_f, load_as<float>(p.C, row + col * p.ldc, p.cdt), r);
+            if (has_c) r = fmaf(beta_f, cf[j], r);
             store_as<float>(p.D, row + col * p.ldd, p.ddt, r);
           }
         }
