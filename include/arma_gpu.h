@@ -172,6 +172,37 @@ void arma_gpu_plan_free(arma_plan* plan);
 
 const char* arma_gpu_status_string(arma_status status);
 
+/* ---- Batched evaluation: many independent instances of one expression
+ * family (same nodes and outputs, per-instance sizes) in one grouped
+ * launch.  Each instance must reduce to a single product with folded
+ * transposes and scalars plus an optional added matrix,
+ *     D_i = alpha * op(A_i) * op(B_i) + beta * C_i,
+ * optionally with trace(op(A_i) * op(B_i)) as a further output: the folded
+ * product and diagonal-only trace of Sec. II / Sec. III (5), batched.
+ * A, B are FP32 or BF16, D FP32, traces FP64; accumulation is FP32.
+ * Otherwise arma_gpu_plan_batched returns ARMA_ERR_UNSUPPORTED. ---- */
+
+/* Plan count instances (exprs[i] describes instance i). */
+arma_status arma_gpu_plan_batched(const arma_expr* exprs, int32_t count, arma_plan** plan);
+
+/* Bytes of the problem table that describes one batch of pointers. */
+arma_status arma_gpu_batched_table_bytes(const arma_plan* plan, size_t* bytes);
+
+/* Fill a host buffer of arma_gpu_batched_table_bytes() bytes with the
+ * problem table: in_ptrs[i * n_slots + s] and out_ptrs[i * n_outputs + o]
+ * are device pointers of instance i (n_slots, n_outputs as in exprs[0]).
+ * The caller copies the table to device memory (once, if the pointers do
+ * not change). */
+arma_status arma_gpu_batched_table_fill(const arma_plan* plan, const void* const* in_ptrs,
+                                        void* const* out_ptrs, void* host_table);
+
+/* Evaluate every instance of the batch: one persistent grouped kernel over
+ * a tile list spanning all instances (plus one small kernel for traces).
+ * device_table is the filled table in device memory; workspace as in
+ * arma_gpu_eval.  Asynchronous on stream; capturable in a CUDA graph. */
+arma_status arma_gpu_eval_batched(const arma_plan* plan, const void* device_table, void* workspace,
+                                  size_t workspace_bytes, void* stream);
+
 /* Size of the library-owned scratch array used by arma_gpu_eval_fused_static. */
 #define ARMA_STATIC_SCRATCH_BYTES 131072
 

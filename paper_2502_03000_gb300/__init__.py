@@ -64,7 +64,9 @@ class Expr(ctypes.Structure):
 
 EXPORTS = ["arma_gpu_plan", "arma_gpu_plan_workspace", "arma_gpu_output_info", "arma_gpu_eval",
            "arma_gpu_eval_status", "arma_gpu_plan_info", "arma_gpu_plan_free",
-           "arma_gpu_status_string", "arma_gpu_chain_order", "arma_gpu_eval_fused_static"]
+           "arma_gpu_status_string", "arma_gpu_chain_order", "arma_gpu_eval_fused_static",
+           "arma_gpu_plan_batched", "arma_gpu_batched_table_bytes", "arma_gpu_batched_table_fill",
+           "arma_gpu_eval_batched"]
 STATIC_SCRATCH_BYTES = 131072
 
 
@@ -87,6 +89,10 @@ def lib() -> ctypes.CDLL:
     L.arma_gpu_chain_order.argtypes = [i32, ctypes.POINTER(i64), i32, ctypes.POINTER(i32),
                                        ctypes.POINTER(ctypes.c_uint64)]
     L.arma_gpu_eval_fused_static.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    L.arma_gpu_plan_batched.argtypes = [ctypes.POINTER(Expr), i32, ctypes.POINTER(vp)]
+    L.arma_gpu_batched_table_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.arma_gpu_batched_table_fill.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    L.arma_gpu_eval_batched.argtypes = [vp, vp, vp, ctypes.c_size_t, vp]
     return L
 
 
@@ -244,6 +250,80 @@ class Plan:
         code = lib().arma_gpu_eval_status(self._h, ctypes.c_void_p(ws.data_ptr()), ctypes.c_void_p(st),
                                           ctypes.byref(info))
         return STATUS.get(code, str(code)), int(info.value)
+
+
+class BatchedPlan:
+    """Many instances of one expression family evaluated by one grouped launch.
+
+    ``instances`` is a list of (nodes, outputs) with the same structure.
+    ``bind(inputs, outputs)`` builds the device problem table for lists of
+    per-instance tensors; ``__call__`` then runs the whole batch."""
+
+    def __init__(self, instances, tier="native", flags=0):
+        L = lib()
+        self.count = len(instances)
+        self._keep = []
+        exprs = (Expr * self.count)()
+        for i, (nodes, outs) in enumerate(instances):
+            arr = _mk_nodes(nodes)
+            o = (ctypes.c_int32 * len(outs))(*outs)
+            self._keep += [arr, o]
+            exprs[i] = Expr(len(nodes), len(outs), arr, o, TIERS[tier] if isinstance(tier, str) else int(tier),
+                            int(flags))
+        h = ctypes.c_void_p()
+        _check(L.arma_gpu_plan_batched(exprs, self.count, ctypes.byref(h)), "arma_gpu_plan_batched")
+        self._h = h
+        self.n_slots = 1 + max(d.get("slot", 0) for d in instances[0][0] if d["op"] == "input")
+        self.n_outs = len(instances[0][1])
+        tb = ctypes.c_size_t()
+        _check(L.arma_gpu_batched_table_bytes(h, ctypes.byref(tb)), "arma_gpu_batched_table_bytes")
+        self.table_bytes = int(tb.value)
+        ws = ctypes.c_size_t()
+        _check(L.arma_gpu_plan_workspace(h, ctypes.byref(ws)), "arma_gpu_plan_workspace")
+        self.workspace_bytes = int(ws.value)
+        self.table = None
+        self.ws = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().arma_gpu_plan_free(h)
+            except Exception:
+                pass
+
+    @property
+    def info(self) -> dict:
+        L = lib()
+        need = ctypes.c_size_t()
+        L.arma_gpu_plan_info(self._h, None, 0, ctypes.byref(need))
+        buf = ctypes.create_string_buffer(need.value)
+        _check(L.arma_gpu_plan_info(self._h, buf, need.value, None), "arma_gpu_plan_info")
+        return json.loads(buf.value.decode())
+
+    def bind(self, inputs, outputs, device):
+        """inputs[i][s], outputs[i][o]: tensors of instance i."""
+        import numpy as np
+        import torch
+        ins = (ctypes.c_void_p * (self.count * self.n_slots))()
+        outs = (ctypes.c_void_p * (self.count * self.n_outs))()
+        for i in range(self.count):
+            for s_, t in enumerate(inputs[i]):
+                ins[i * self.n_slots + s_] = t.data_ptr()
+            for o, t in enumerate(outputs[i]):
+                outs[i * self.n_outs + o] = t.data_ptr()
+        host = np.zeros(self.table_bytes, dtype=np.uint8)
+        _check(lib().arma_gpu_batched_table_fill(self._h, ins, outs, host.ctypes.data_as(ctypes.c_void_p)),
+               "arma_gpu_batched_table_fill")
+        self.table = torch.from_numpy(host).to(device)
+        self.ws = torch.empty(max(256, self.workspace_bytes), dtype=torch.uint8, device=device)
+
+    def __call__(self, stream=None):
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        _check(lib().arma_gpu_eval_batched(self._h, ctypes.c_void_p(self.table.data_ptr()),
+                                           ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                           ctypes.c_void_p(st)), "arma_gpu_eval_batched")
 
 
 def chain_order(dims, method: int = 0):

@@ -6,10 +6,12 @@
 #include <new>
 #include <string>
 
+#include "grouped.h"
 #include "internal.h"
 
 namespace arma {
 arma_status plan_expression(const arma_expr* e, arma_plan* p, std::string* msg);
+arma_status plan_batched(const arma_expr* exprs, int32_t count, arma_plan* p);
 arma_status chain_order_api(int32_t n, const int64_t* dims, int32_t method, int32_t* splits,
                             uint64_t* cost);
 }  // namespace arma
@@ -239,6 +241,95 @@ const char* arma_gpu_status_string(arma_status s) {
 arma_status arma_gpu_chain_order(int32_t n, const int64_t* dims, int32_t method, int32_t* splits,
                                  uint64_t* cost) {
   return chain_order_api(n, dims, method, splits, cost);
+}
+
+arma_status arma_gpu_plan_batched(const arma_expr* exprs, int32_t count, arma_plan** plan) {
+  if (!plan) return ARMA_ERR_INVALID;
+  *plan = nullptr;
+  arma_plan* p = new (std::nothrow) arma_plan();
+  if (!p) return ARMA_ERR_INVALID;
+  arma_status s;
+  try {
+    s = plan_batched(exprs, count, p);
+  } catch (...) {
+    s = ARMA_ERR_INVALID;
+  }
+  if (s != ARMA_OK) {
+    delete p;
+    return s;
+  }
+  *plan = p;
+  return ARMA_OK;
+}
+
+static size_t table_layout(const BatchedInfo& b, size_t* probs_off, size_t* prob_off, size_t* code_off) {
+  size_t off = 0;
+  *probs_off = off;
+  off += (size_t)b.count * sizeof(GroupedProblem);
+  off = (off + 255) / 256 * 256;
+  *prob_off = off;
+  off += (size_t)b.tiles * sizeof(int32_t);
+  off = (off + 255) / 256 * 256;
+  *code_off = off;
+  off += (size_t)b.tiles * sizeof(uint32_t);
+  return (off + 255) / 256 * 256;
+}
+
+arma_status arma_gpu_batched_table_bytes(const arma_plan* plan, size_t* bytes) {
+  if (!plan || !bytes || !plan->batched) return ARMA_ERR_INVALID;
+  size_t a, b, c;
+  *bytes = table_layout(plan->bi, &a, &b, &c);
+  return ARMA_OK;
+}
+
+arma_status arma_gpu_batched_table_fill(const arma_plan* plan, const void* const* in_ptrs,
+                                        void* const* out_ptrs, void* host_table) {
+  if (!plan || !plan->batched || !in_ptrs || !out_ptrs || !host_table) return ARMA_ERR_INVALID;
+  const BatchedInfo& b = plan->bi;
+  size_t po, pr, pc;
+  table_layout(b, &po, &pr, &pc);
+  char* base = static_cast<char*>(host_table);
+  GroupedProblem* probs = reinterpret_cast<GroupedProblem*>(base + po);
+  for (int32_t i = 0; i < b.count; ++i) {
+    const void* const* in = in_ptrs + (size_t)i * b.n_slots;
+    void* const* out = out_ptrs + (size_t)i * b.n_outs;
+    GroupedProblem& g = probs[i];
+    g.m = b.m[i]; g.n = b.n[i]; g.k = b.k[i];
+    g.A = in[b.slot_a]; g.lda = b.lda[i];
+    g.B = in[b.slot_b]; g.ldb = b.ldb[i];
+    g.C = b.slot_c >= 0 ? in[b.slot_c] : nullptr; g.ldc = b.ldc[i];
+    g.D = out[b.out_d]; g.ldd = g.m > 0 ? g.m : 1;
+    g.trace = b.out_t >= 0 ? static_cast<double*>(out[b.out_t]) : nullptr;
+    g.first_tile = b.first_tile[i];
+    g.tile = b.tile[i];
+    g.pad = 0;
+    if ((!g.A || !g.B || !g.D) && g.m * g.n > 0) return ARMA_ERR_INVALID;
+  }
+  std::memcpy(base + pr, b.tile_prob.data(), b.tile_prob.size() * sizeof(int32_t));
+  std::memcpy(base + pc, b.tile_code.data(), b.tile_code.size() * sizeof(uint32_t));
+  return ARMA_OK;
+}
+
+arma_status arma_gpu_eval_batched(const arma_plan* plan, const void* device_table, void* workspace,
+                                  size_t workspace_bytes, void* stream) {
+  if (!plan || !plan->batched || !device_table) return ARMA_ERR_INVALID;
+  if (!workspace || workspace_bytes < plan->ws_bytes) return ARMA_ERR_WORKSPACE;
+  const BatchedInfo& b = plan->bi;
+  size_t po, pr, pc;
+  table_layout(b, &po, &pr, &pc);
+  const char* base = static_cast<const char*>(device_table);
+  GroupedArgs g;
+  std::memset(&g, 0, sizeof g);
+  g.count = b.count; g.tiles = b.tiles;
+  g.probs = reinterpret_cast<const GroupedProblem*>(base + po);
+  g.tile_prob = reinterpret_cast<const int32_t*>(base + pr);
+  g.tile_code = reinterpret_cast<const uint32_t*>(base + pc);
+  g.ta = b.ta; g.tb = b.tb; g.abdt = b.abdt; g.cdt = b.cdt; g.ddt = b.ddt;
+  g.alpha = b.alpha; g.beta = b.beta;
+  g.alpha_f = (float)b.alpha; g.beta_f = (float)b.beta;
+  g.trace_partials = b.out_t >= 0 ? reinterpret_cast<double*>(static_cast<char*>(workspace) + kHeaderBytes) : nullptr;
+  int launches = 0;
+  return cuda_status(launch_grouped(g, static_cast<cudaStream_t>(stream), &launches));
 }
 
 }  // extern "C"

@@ -247,6 +247,22 @@ struct OutInfo {
   int32_t scalar;
 };
 
+// A batch of instances that all reduce to one product with folded scalars
+// (and optionally the trace of that product), evaluated by the grouped kernel.
+struct BatchedInfo {
+  int32_t count = 0;
+  int32_t slot_a = 0, slot_b = 0, slot_c = -1, out_d = 0, out_t = -1;
+  int32_t n_slots = 0, n_outs = 0;
+  int32_t ta = 0, tb = 0, abdt = ARMA_F32, cdt = ARMA_F32, ddt = ARMA_F32;
+  double alpha = 1.0, beta = 0.0;
+  std::vector<int64_t> m, n, k, lda, ldb, ldc;
+  std::vector<int32_t> tile;
+  std::vector<int64_t> first_tile;
+  std::vector<int32_t> tile_prob;
+  std::vector<uint32_t> tile_code;
+  int64_t tiles = 0;
+};
+
 }  // namespace arma
 
 struct arma_plan {
@@ -260,4 +276,6 @@ struct arma_plan {
   int32_t tier = 0;
   std::string log;          // JSON decision log
   double flops = 0, bytes = 0;
+  bool batched = false;
+  arma::BatchedInfo bi;
 };

@@ -1306,6 +1306,81 @@ arma_status plan_expression(const arma_expr* e, arma_plan* p, std::string* msg) 
   return s;
 }
 
+// Plan `count` instances of one expression family for the grouped kernel.
+arma_status plan_batched(const arma_expr* exprs, int32_t count, arma_plan* p) {
+  if (!exprs || count < 1) return ARMA_ERR_INVALID;
+  BatchedInfo& b = p->bi;
+  b.count = count;
+  for (int32_t i = 0; i < count; ++i) {
+    arma_plan one;
+    Planner pl(exprs[i], one);
+    arma_status st = pl.run();
+    if (st != ARMA_OK) return st;
+    const size_t ns = one.steps.size();
+    if (ns < 1 || ns > 2 || one.steps[0].kind != ST_GEMM) return ARMA_ERR_UNSUPPORTED;
+    const GemmStep& g = one.steps[0].gemm;
+    if (g.A.ref.kind != REF_INPUT || g.B.ref.kind != REF_INPUT || g.D.ref.kind != REF_OUTPUT)
+      return ARMA_ERR_UNSUPPORTED;
+    if (g.C.ref.valid() && g.C.ref.kind != REF_INPUT) return ARMA_ERR_UNSUPPORTED;
+    if (g.rowscale.ref.valid() || g.colscale.ref.valid()) return ARMA_ERR_UNSUPPORTED;
+    if (g.A.dtype != g.B.dtype || g.A.dtype == ARMA_F64 || g.D.dtype != ARMA_F32) return ARMA_ERR_UNSUPPORTED;
+    int32_t out_t = -1;
+    if (ns == 2) {
+      const Step& st2 = one.steps[1];
+      if (st2.kind != ST_DOT) return ARMA_ERR_UNSUPPORTED;
+      const DotStep& d = st2.dot;
+      if (d.A.ref.kind != REF_INPUT || d.B.ref.kind != REF_INPUT || d.A.ref.idx != g.A.ref.idx ||
+          d.B.ref.idx != g.B.ref.idx || d.A.trans != g.A.trans || d.B.trans != g.B.trans || d.alpha != 1.0 ||
+          d.out.kind != REF_OUTPUT)
+        return ARMA_ERR_UNSUPPORTED;
+      out_t = (int32_t)d.out.idx;
+    }
+    const int32_t sc = g.C.ref.valid() ? (int32_t)g.C.ref.idx : -1;
+    if (i == 0) {
+      b.slot_a = (int32_t)g.A.ref.idx; b.slot_b = (int32_t)g.B.ref.idx; b.slot_c = sc;
+      b.out_d = (int32_t)g.D.ref.idx; b.out_t = out_t;
+      b.n_slots = one.n_slots; b.n_outs = (int32_t)one.outs.size();
+      b.ta = g.A.trans; b.tb = g.B.trans; b.abdt = g.A.dtype;
+      b.cdt = g.C.ref.valid() ? g.C.dtype : ARMA_F32; b.ddt = g.D.dtype;
+      b.alpha = g.alpha; b.beta = g.beta;
+      p->outs = one.outs;
+      p->n_slots = one.n_slots;
+    } else if (b.slot_a != g.A.ref.idx || b.slot_b != g.B.ref.idx || b.slot_c != sc || b.out_d != g.D.ref.idx ||
+               b.out_t != out_t || b.ta != g.A.trans || b.tb != g.B.trans || b.abdt != g.A.dtype ||
+               b.alpha != g.alpha || b.beta != g.beta || b.n_slots != one.n_slots ||
+               b.n_outs != (int32_t)one.outs.size()) {
+      return ARMA_ERR_UNSUPPORTED;   // instances must share one structure
+    }
+    b.m.push_back(g.m); b.n.push_back(g.n); b.k.push_back(g.k);
+    b.lda.push_back(g.A.ld); b.ldb.push_back(g.B.ld); b.ldc.push_back(g.C.ref.valid() ? g.C.ld : 0);
+    // tile shape per problem: 32 x 32 runs at about half the efficiency of
+    // 64 x 64 per output, so it wins only when 64-tiles would pad more than 2x
+    const int64_t t32 = ((g.m + 31) / 32) * ((g.n + 31) / 32);
+    const int64_t t64 = ((g.m + 63) / 64) * ((g.n + 63) / 64);
+    const int32_t T = (t32 < 2 * t64) ? 32 : 64;
+    b.tile.push_back(T);
+    b.first_tile.push_back(b.tiles);
+    const int64_t ntm = (g.m + T - 1) / T, ntn = (g.n + T - 1) / T;
+    if (ntm > 65535 || ntn > 65535) return ARMA_ERR_UNSUPPORTED;
+    for (int64_t tm = 0; tm < ntm; ++tm)
+      for (int64_t tn = 0; tn < ntn; ++tn) {
+        b.tile_prob.push_back(i);
+        b.tile_code.push_back((uint32_t)((tm << 16) | tn));
+      }
+    b.tiles += ntm * ntn;
+    p->flops += 2.0 * (double)g.m * (double)g.n * (double)g.k;
+  }
+  p->batched = true;
+  p->ws_bytes = kHeaderBytes + (size_t)((b.tiles * 8 + 255) / 256 * 256);
+  std::ostringstream os;
+  os.precision(17);
+  os << "{\"mode\": \"batched\", \"count\": " << count << ", \"tiles\": " << b.tiles
+     << ", \"trace\": " << (b.out_t >= 0 ? "true" : "false") << ", \"flops\": " << p->flops
+     << ", \"workspace\": " << p->ws_bytes << ", \"steps\": [{\"kernel\": \"grouped\"}]}";
+  p->log = os.str();
+  return ARMA_OK;
+}
+
 arma_status chain_order_api(int32_t n, const int64_t* dims, int32_t method, int32_t* splits,
                             uint64_t* cost) {
   if (n < 1 || n > 4096 || !dims || method < 0 || method > 2) return ARMA_ERR_INVALID;

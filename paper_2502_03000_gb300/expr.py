@@ -152,3 +152,15 @@ def config_solve(n: int = 4096, nrhs: int = 64, dtype: str = "f64"):
     A = g.input(0, n, n, dtype)
     B = g.input(1, n, nrhs, dtype)
     return g.build(inv(A) * B)
+
+
+def config_batched_instance(m: int, n: int, k: int, dtype: str = "f32"):
+    """One instance of the batched family: 2*trans(A)*B + C and
+    trace(trans(A)*B), A k x m, B k x n (dtype), C m x n FP32; slots A=0,
+    B=1, C=2.  The trace is read as trace(A^T B) = sum over i < min(m, n)
+    of (A^T B)_ii, the conforming form of trace(A*B) for these shapes."""
+    g = Graph()
+    A = g.input(0, k, m, dtype)
+    B = g.input(1, k, n, dtype)
+    C = g.input(2, m, n, "f32")
+    return g.build(2 * A.t() * B + C, trace(A.t() * B))

@@ -1,0 +1,139 @@
+"""Batched evaluation: many independent 2*trans(A_i)*B_i + C_i and
+trace(A_i^T B_i) of uneven sizes in one grouped launch, against the oracle
+instance by instance; CUDA-graph replay; the full 10,000-instance batch on
+sampled instances."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2502_03000_gb300 as ag
+import synth
+from paper_2502_03000_gb300 import expr as E
+from tests.gpu_util import TOL, need_gpu, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return need_gpu()
+
+
+def sizes(seed, count, lo=8, hi=512):
+    m = synth.log_uniform_ints(seed, 1, count, lo, hi)
+    n = synth.log_uniform_ints(seed, 2, count, lo, hi)
+    k = synth.log_uniform_ints(seed, 3, count, lo, hi)
+    return m, n, k
+
+
+def build_batch(torch, seed, count, dtype, lo=8, hi=512):
+    m, n, k = sizes(seed, count, lo, hi)
+    inst, host, ins, outs = [], [], [], []
+    for i in range(count):
+        nodes, o = E.config_batched_instance(int(m[i]), int(n[i]), int(k[i]), dtype)
+        inst.append((nodes, o))
+        A = synth.matrix(seed + i, 1, int(k[i]), int(m[i]), dtype)
+        B = synth.matrix(seed + i, 2, int(k[i]), int(n[i]), dtype)
+        C = synth.matrix(seed + i, 3, int(m[i]), int(n[i]), "f32")
+        host.append([A, B, C])
+        ins.append([to_dev(A, dtype), to_dev(B, dtype), to_dev(C, "f32")])
+        outs.append([ag.empty_colmajor(int(m[i]), int(n[i]), torch.float32, "cuda"),
+                     torch.zeros(1, dtype=torch.float64, device="cuda")])
+    return inst, host, ins, outs
+
+
+def check_instance(nodes, o, host, out, dtype):
+    ref = oracle.evaluate(nodes, o, host)
+    D = to_host(out[0])
+    assert oracle.rel_err(D, ref[0]) <= TOL[dtype if dtype == "bf16" else "f32"]
+    # trace: compare against the size of its terms (a random trace can be near 0)
+    At = np.asarray(host[0], dtype=np.float64)
+    Bv = np.asarray(host[1], dtype=np.float64)
+    d = min(At.shape[1], Bv.shape[1])
+    terms = np.abs(At[:, :d] * Bv[:, :d]).sum()
+    t = to_host(out[1])
+    assert abs(t - ref[1]) <= 1e-6 * max(terms, 1e-300)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_batched_matches_oracle(torch, dtype):
+    inst, host, ins, outs = build_batch(torch, 101, 60, dtype)
+    bp = ag.BatchedPlan(inst)
+    assert bp.info["mode"] == "batched"
+    bp.bind(ins, outs, "cuda")
+    bp()
+    torch.cuda.synchronize()
+    for i in range(len(inst)):
+        check_instance(*inst[i], host[i], outs[i], dtype)
+
+
+def test_batched_tiny_and_degenerate(torch):
+    inst, host, ins, outs = build_batch(torch, 7, 30, "f32", lo=1, hi=40)
+    bp = ag.BatchedPlan(inst)
+    bp.bind(ins, outs, "cuda")
+    bp()
+    torch.cuda.synchronize()
+    for i in range(len(inst)):
+        check_instance(*inst[i], host[i], outs[i], "f32")
+
+
+def test_batched_graph_replay(torch):
+    inst, host, ins, outs = build_batch(torch, 55, 40, "f32")
+    bp = ag.BatchedPlan(inst)
+    bp.bind(ins, outs, "cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        bp(stream=s.cuda_stream)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    first = [o[0].clone() for o in outs]
+    for o in outs:
+        o[0].zero_()
+        o[1].zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bp(stream=torch.cuda.current_stream().cuda_stream)
+    g.replay()
+    torch.cuda.synchronize()
+    for a, o in zip(first, outs):
+        assert torch.equal(a, o[0])
+    for i in range(len(inst)):
+        check_instance(*inst[i], host[i], outs[i], "f32")
+
+
+def test_batched_rejects_other_families(torch):
+    g = E.Graph()
+    A, B = g.input(0, 16, 16, "f32"), g.input(1, 16, 16, "f32")
+    with pytest.raises(ag.ArmaError) as ei:
+        ag.BatchedPlan([g.build(A % B + A)])
+    assert ei.value.status == "unsupported"
+
+
+def test_batched_benchmark_size_sampled(torch):
+    """10,000 instances (m, n, k log-uniform in [8, 512]) in one launch;
+    sampled instances against the oracle"""
+    count = 10000
+    m, n, k = sizes(20250203 + 4, count)
+    inst, ins, outs = [], [], []
+    rng = np.random.default_rng(4)
+    sample = set(rng.choice(count, 24, replace=False).tolist())
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(20250203 + 4)
+
+    def uni(r, c):
+        return (torch.rand((c, r), device="cuda", generator=gen) * 2 - 1).t()
+
+    for i in range(count):
+        nodes, o = E.config_batched_instance(int(m[i]), int(n[i]), int(k[i]), "f32")
+        inst.append((nodes, o))
+        ins.append([uni(int(k[i]), int(m[i])), uni(int(k[i]), int(n[i])), uni(int(m[i]), int(n[i]))])
+        outs.append([ag.empty_colmajor(int(m[i]), int(n[i]), torch.float32, "cuda"),
+                     torch.zeros(1, dtype=torch.float64, device="cuda")])
+    bp = ag.BatchedPlan(inst)
+    bp.bind(ins, outs, "cuda")
+    bp()
+    torch.cuda.synchronize()
+    for i in sorted(sample):
+        h = [to_host(t) for t in ins[i]]
+        check_instance(*inst[i], h, outs[i], "f32")
