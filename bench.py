@@ -261,13 +261,206 @@ def bench_products(a):
                       "bf16_peak_tflops": peak, "peak_source": src, "tiers": res}), flush=True)
 
 
+def fp32_simt_peak_tflops():
+    # 152 SMs x 128 FP32 FMA lanes x 2 flops x 2.07 GHz (nominal unit counts and clock)
+    return 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def bench_batched(a):
+    """10,000 instances of 2*trans(A_i)*B_i + C_i and trace(A_i^T B_i), m, n, k
+    log-uniform in [8, 512]: one grouped launch (CUDA-graph replay) against
+    one evaluation per instance."""
+    import numpy as np
+    import torch
+    import paper_2502_03000_gb300 as ag
+    import synth
+    from paper_2502_03000_gb300 import expr as E
+    dev = torch.device("cuda", 0)
+    count = 10000
+    seed = 20250203 + 4
+    m = synth.log_uniform_ints(seed, 1, count, 8, 512)
+    n = synth.log_uniform_ints(seed, 2, count, 8, 512)
+    k = synth.log_uniform_ints(seed, 3, count, 8, 512)
+    flops = float(np.sum(2.0 * m * n * k))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for dt in ("f32", "bf16"):
+        td = torch.float32 if dt == "f32" else torch.bfloat16
+
+        def uni(r, c, t):
+            return (torch.rand((c, r), device=dev, generator=gen) * 2 - 1).to(t).t()
+        inst, ins, outs = [], [], []
+        for i in range(count):
+            mi, ni, ki = int(m[i]), int(n[i]), int(k[i])
+            inst.append(E.config_batched_instance(mi, ni, ki, dt))
+            ins.append([uni(ki, mi, td), uni(ki, ni, td), uni(mi, ni, torch.float32)])
+            outs.append([ag.empty_colmajor(mi, ni, torch.float32, dev),
+                         torch.zeros(1, dtype=torch.float64, device=dev)])
+        t0 = time.perf_counter()
+        bp = ag.BatchedPlan(inst)
+        bp.bind(ins, outs, dev)
+        plan_s = time.perf_counter() - t0
+        for _ in range(3):
+            bp()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            bp(stream=torch.cuda.current_stream().cuda_stream)
+        g.replay()
+        torch.cuda.synchronize()
+        ms = time_ms(g.replay, a.steps, stream)
+        # baseline: one evaluation (and its launches) per instance
+        plans = [ag.Plan(nd, o) for nd, o in inst]
+        for p_, x, y in zip(plans, ins, outs):
+            p_(*x, outputs=y)
+        torch.cuda.synchronize()
+        base_ms = time_ms(lambda: [p_(*x, outputs=y) for p_, x, y in zip(plans, ins, outs)], 1, stream)
+        launches = sum(len(p_.info["steps"]) for p_ in plans)
+        res[dt] = {"ms_per_batch": ms, "instances_per_s": count / (ms * 1e-3), "tflops": flops / ms / 1e9,
+                   "frac_of_fp32_simt_peak": flops / ms / 1e9 / fp32_simt_peak_tflops(),
+                   "per_instance_ms": base_ms, "vs_per_instance": base_ms / ms,
+                   "per_instance_planned_steps": launches, "tiles": bp.info["tiles"], "plan_s": plan_s}
+        del plans, bp, g, ins, outs
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "10000 x (2*trans(A_i)*B_i+C_i, trace(A_i^T B_i)), m,n,k log-uniform [8,512]",
+                      "flops_per_batch": flops, "fp32_simt_peak_tflops": fp32_simt_peak_tflops(),
+                      "results": res}), flush=True)
+
+
+def bench_chain(a):
+    """A*B*C*v, 4096x8192, 8192x512, 512x4096, 4096x1 FP64: chosen order
+    (right to left, three GEMVs) against the written left-to-right order."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_2502_03000_gb300 as ag
+    from paper_2502_03000_gb300 import expr as E
+    dev = torch.device("cuda", 0)
+    dims = (4096, 8192, 512, 4096, 1)
+    host, ins = [], []
+    for s_ in range(4):
+        h, d = dev_matrix(20250203 + 3, s_ + 5, dims[s_], dims[s_ + 1], "f64", dev)
+        host.append(h)
+        ins.append(d)
+    nodes, outs = E.config_chain(dims, "f64")
+    stream = torch.cuda.current_stream(dev)
+    ref = oracle.chain_eval(host, (0, 0, (1, 1, (2, 2, 3))))
+    hbm, src = peaks()
+    alg_bytes = 8.0 * (dims[0] * dims[1] + dims[1] * dims[2] + dims[2] * dims[3] + dims[3] + dims[0])
+    res = {}
+    for name, flags in (("dp", 0), ("paper_greedy", ag.PLAN_CHAIN_GREEDY), ("left_to_right", ag.PLAN_CHAIN_LEFT)):
+        p_ = ag.Plan(nodes, outs, flags=flags)
+        out = p_.alloc_outputs(dev)
+        p_(*ins, outputs=out)
+        torch.cuda.synchronize()
+        steps = a.steps if flags != ag.PLAN_CHAIN_LEFT else 2
+        ms = time_ms(lambda: p_(*ins, outputs=out), steps, stream)
+        err = oracle.rel_err(out[0].double().cpu().numpy(), ref)
+        res[name] = {"ms": ms, "flops": p_.info["flops"], "err_vs_oracle": err,
+                     "gbs": alg_bytes / (ms * 1e-3) / 1e9 if flags != ag.PLAN_CHAIN_LEFT else None}
+        p_._ws.clear()
+    res["dp"]["frac_of_hbm"] = res["dp"]["gbs"] / hbm
+    res["dp"]["vs_left_to_right"] = res["left_to_right"]["ms"] / res["dp"]["ms"]
+    print(json.dumps({"workload": "A*B*C*v dims (4096,8192,512,4096,1) FP64", "hbm_peak_gbs": hbm,
+                      "alg_bytes": alg_bytes, "results": res}), flush=True)
+
+
+def bench_solve(a):
+    """inv(A)*B, A = Q1 diag(s) Q2^T (n = 4096, kappa = 1e6), B 4096 x 64, per tier."""
+    import numpy as np
+    import torch
+    import paper_2502_03000_gb300 as ag
+    import synth
+    from paper_2502_03000_gb300 import expr as E
+    dev = torch.device("cuda", 0)
+    n, nrhs = 4096, 64
+    A = synth.conditioned_matrix(20250203 + 3, n, 1e6, symmetric=False)
+    B = synth.matrix(20250203 + 3, 2, n, nrhs, "f64")
+    Xref = np.linalg.solve(A, B)
+    dA = torch.from_numpy(np.ascontiguousarray(A.T)).to(dev).t()
+    dB = torch.from_numpy(np.ascontiguousarray(B.T)).to(dev).t()
+    nodes, outs = E.config_solve(n, nrhs)
+    stream = torch.cuda.current_stream(dev)
+    nA = np.linalg.norm(A)
+    res = {}
+    for tier in ("lu32_ir64", "f64", "split_bf16", "bf16"):
+        p_ = ag.Plan(nodes, outs, tier=tier)
+        out = p_.alloc_outputs(dev)
+        p_(dA, dB, outputs=out)
+        torch.cuda.synchronize()
+        ms = time_ms(lambda: p_(dA, dB, outputs=out), max(1, a.steps // 4), stream)
+        st, info = p_.status()
+        X = out[0].double().cpu().numpy()
+        bwd = float(np.linalg.norm(B - A @ X) / (nA * np.linalg.norm(X) + np.linalg.norm(B)))
+        fwd = float(np.linalg.norm(X - Xref) / np.linalg.norm(Xref))
+        res[tier] = {"ms": ms, "status": st, "info": info, "backward_err": bwd, "forward_err": fwd,
+                     "gflops": (2.0 / 3.0 * n ** 3 + 2.0 * n * n * nrhs) / ms / 1e6}
+        p_._ws.clear()
+    lit = ag.Plan(nodes, outs, flags=ag.PLAN_LITERAL)
+    out = lit.alloc_outputs(dev)
+    lit(dA, dB, outputs=out)
+    torch.cuda.synchronize()
+    lms = time_ms(lambda: lit(dA, dB, outputs=out), 1, stream)
+    X = out[0].double().cpu().numpy()
+    res["literal_inverse"] = {"ms": lms, "forward_err": float(np.linalg.norm(X - Xref) / np.linalg.norm(Xref))}
+    res["lu32_ir64"]["vs_literal"] = lms / res["lu32_ir64"]["ms"]
+    print(json.dumps({"workload": "inv(A)*B, A 4096x4096 kappa=1e6 (non-symmetric), B 4096x64 FP64",
+                      "results": res}), flush=True)
+
+
+def bench_plain(a):
+    """The six 256 x 256 FP64 expressions: optimised vs literal, and all six
+    optimised evaluations replayed as one CUDA graph."""
+    import torch
+    import oracle
+    import paper_2502_03000_gb300 as ag
+    from paper_2502_03000_gb300 import expr as E
+    import synth
+    dev = torch.device("cuda", 0)
+    n = 256
+    host = [synth.matrix(20250203 + 1, s_ + 1, n, n if s_ < 4 else 1, "f64") for s_ in range(5)]
+    ins = [torch.from_numpy(h.T.copy()).to(dev).t() for h in host]
+    exprs = E.config_plain(n, "f64")
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    opt_plans = []
+    for name, (nodes, outs) in exprs.items():
+        r = {}
+        for mode, flags in (("optimised", 0), ("literal", ag.PLAN_LITERAL)):
+            p_ = ag.Plan(nodes, outs, flags=flags)
+            out = p_.alloc_outputs(dev)
+            p_(*ins, outputs=out)
+            torch.cuda.synchronize()
+            ms = time_ms(lambda: p_(*ins, outputs=out), 200, stream)
+            got = out[0]
+            ref = oracle.evaluate(nodes, outs, host)[0]
+            val = got.double().cpu().numpy() if got.dim() == 2 else float(got.item())
+            r[mode] = {"us": ms * 1e3, "kernels": len(p_.info["steps"]), "err_vs_oracle": oracle.rel_err(val, ref)}
+            if mode == "optimised":
+                opt_plans.append((p_, out))
+        r["vs_literal"] = r["literal"]["us"] / r["optimised"]["us"]
+        res[name] = r
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for p_, out in opt_plans:
+            p_(*ins, outputs=out, stream=torch.cuda.current_stream().cuda_stream)
+    g.replay()
+    torch.cuda.synchronize()
+    gms = time_ms(g.replay, 200, stream)
+    print(json.dumps({"workload": "six expressions over 256x256 FP64 A,B,C,D and v", "results": res,
+                      "graph_replay_us_all_six": gms * 1e3}), flush=True)
+
+
 def main():
     a = args()
     if a.impl == "reference":
         run_reference(a)
         return
-    if a.workload == "products":
-        bench_products(a)
+    if a.workload != "fused":
+        {"products": bench_products, "batched": bench_batched, "chain": bench_chain,
+         "solve": bench_solve, "plain": bench_plain}[a.workload](a)
         return
     import numpy as np
     import torch
