@@ -172,6 +172,46 @@ void arma_gpu_plan_free(arma_plan* plan);
 
 const char* arma_gpu_status_string(arma_status status);
 
+/* ---- Cost model.  The paper chooses an evaluation by fixed rules
+ * (compile-time patterns, Sec. II; the greedy chain rule, Sec. II chain
+ * paragraph).  Here candidate plans of one expression (the flag variants
+ * above) are ranked either by a FLOP/byte roofline estimate or by a small
+ * learned network trained on timings this library records. ---- */
+
+#define ARMA_PLAN_FEATURES 16
+
+/* Host only: the plan's feature vector (log2 work and bytes, step counts
+ * per kernel kind, tensor-core share, literal flag, ...); n >= 16 floats. */
+arma_status arma_gpu_plan_features(const arma_plan* plan, float* features, int32_t n);
+
+/* Host only: estimated seconds, summing per step a launch plus the larger
+ * of its compute time and its memory time on GB300. */
+arma_status arma_gpu_plan_heuristic_cost(const arma_plan* plan, double* seconds);
+
+/* Cost network: y = W3 relu(W2 relu(W1 x + b1) + b2) + b3, FP32, with
+ * features <= 64 inputs and hidden <= 128 units; parameters packed as
+ * W1 (hidden x features, row-major), b1, W2 (hidden x hidden), b2, W3, b3.
+ * All pointers are device pointers; calls are asynchronous on stream. */
+int64_t arma_gpu_mlp_param_count(int32_t features, int32_t hidden);
+
+/* Workspace bytes for arma_gpu_mlp_grad with n samples. */
+size_t arma_gpu_mlp_workspace(int32_t features, int32_t hidden, int32_t n);
+
+/* y[i] = network(x[i * features ...]) for i < n. */
+arma_status arma_gpu_mlp_forward(const float* params, int32_t features, int32_t hidden, const float* x,
+                                 int32_t n, float* y, void* stream);
+
+/* grad = d/dparams of (1/n) sum_i (network(x_i) - target_i)^2; y_out (may be
+ * null) receives the predictions.  Deterministic: every gradient entry is
+ * summed over the samples in sample order. */
+arma_status arma_gpu_mlp_grad(const float* params, int32_t features, int32_t hidden, const float* x,
+                              const float* target, int32_t n, float* grad, float* y_out, void* workspace,
+                              size_t workspace_bytes, void* stream);
+
+/* One Adam step (Kingma and Ba, 2015) with bias correction for step >= 1. */
+arma_status arma_gpu_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t count,
+                              int32_t step, float lr, float beta1, float beta2, float eps, void* stream);
+
 /* ---- Batched evaluation: many independent instances of one expression
  * family (same nodes and outputs, per-instance sizes) in one grouped
  * launch.  Each instance must reduce to a single product with folded

@@ -66,7 +66,10 @@ EXPORTS = ["arma_gpu_plan", "arma_gpu_plan_workspace", "arma_gpu_output_info", "
            "arma_gpu_eval_status", "arma_gpu_plan_info", "arma_gpu_plan_free",
            "arma_gpu_status_string", "arma_gpu_chain_order", "arma_gpu_eval_fused_static",
            "arma_gpu_plan_batched", "arma_gpu_batched_table_bytes", "arma_gpu_batched_table_fill",
-           "arma_gpu_eval_batched"]
+           "arma_gpu_eval_batched", "arma_gpu_plan_features", "arma_gpu_plan_heuristic_cost",
+           "arma_gpu_mlp_param_count", "arma_gpu_mlp_workspace", "arma_gpu_mlp_forward", "arma_gpu_mlp_grad",
+           "arma_gpu_mlp_adam"]
+N_FEATURES = 16
 STATIC_SCRATCH_BYTES = 131072
 
 
@@ -93,6 +96,16 @@ def lib() -> ctypes.CDLL:
     L.arma_gpu_batched_table_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.arma_gpu_batched_table_fill.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
     L.arma_gpu_eval_batched.argtypes = [vp, vp, vp, ctypes.c_size_t, vp]
+    L.arma_gpu_plan_features.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
+    L.arma_gpu_plan_heuristic_cost.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.arma_gpu_mlp_param_count.argtypes = [i32, i32]
+    L.arma_gpu_mlp_param_count.restype = i64
+    L.arma_gpu_mlp_workspace.argtypes = [i32, i32, i32]
+    L.arma_gpu_mlp_workspace.restype = ctypes.c_size_t
+    L.arma_gpu_mlp_forward.argtypes = [vp, i32, i32, vp, i32, vp, vp]
+    L.arma_gpu_mlp_grad.argtypes = [vp, i32, i32, vp, vp, i32, vp, vp, vp, ctypes.c_size_t, vp]
+    L.arma_gpu_mlp_adam.argtypes = [vp, vp, vp, vp, i64, i32, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_float, vp]
     return L
 
 
@@ -188,6 +201,16 @@ class Plan:
         buf = ctypes.create_string_buffer(need.value)
         _check(L.arma_gpu_plan_info(self._h, buf, need.value, None), "arma_gpu_plan_info")
         return json.loads(buf.value.decode())
+
+    def features(self):
+        f = (ctypes.c_float * N_FEATURES)()
+        _check(lib().arma_gpu_plan_features(self._h, f, N_FEATURES), "arma_gpu_plan_features")
+        return list(f)
+
+    def heuristic_cost(self) -> float:
+        c = ctypes.c_double()
+        _check(lib().arma_gpu_plan_heuristic_cost(self._h, ctypes.byref(c)), "arma_gpu_plan_heuristic_cost")
+        return float(c.value)
 
     def workspace(self, device):
         import torch

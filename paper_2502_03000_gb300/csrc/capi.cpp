@@ -12,6 +12,8 @@
 namespace arma {
 arma_status plan_expression(const arma_expr* e, arma_plan* p, std::string* msg);
 arma_status plan_batched(const arma_expr* exprs, int32_t count, arma_plan* p);
+arma_status plan_features(const arma_plan* p, float* out, int32_t n);
+arma_status plan_heuristic(const arma_plan* p, double* seconds);
 arma_status chain_order_api(int32_t n, const int64_t* dims, int32_t method, int32_t* splits,
                             uint64_t* cost);
 }  // namespace arma
@@ -241,6 +243,14 @@ const char* arma_gpu_status_string(arma_status s) {
 arma_status arma_gpu_chain_order(int32_t n, const int64_t* dims, int32_t method, int32_t* splits,
                                  uint64_t* cost) {
   return chain_order_api(n, dims, method, splits, cost);
+}
+
+arma_status arma_gpu_plan_features(const arma_plan* plan, float* features, int32_t n) {
+  return plan_features(plan, features, n);
+}
+
+arma_status arma_gpu_plan_heuristic_cost(const arma_plan* plan, double* seconds) {
+  return plan_heuristic(plan, seconds);
 }
 
 arma_status arma_gpu_plan_batched(const arma_expr* exprs, int32_t count, arma_plan** plan) {

@@ -1381,6 +1381,78 @@ arma_status plan_batched(const arma_expr* exprs, int32_t count, arma_plan* p) {
   return ARMA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Plan features and the FLOP/byte heuristic (cost model inputs)
+// ---------------------------------------------------------------------------
+static double l2(double x) { return std::log2(1.0 + (x > 0 ? x : 0)); }
+
+arma_status plan_features(const arma_plan* p, float* out, int32_t n) {
+  if (!p || !out || n < ARMA_PLAN_FEATURES) return ARMA_ERR_INVALID;
+  double f[ARMA_PLAN_FEATURES] = {0};
+  double maxf = 0, maxb = 0, tc_flops = 0, split_flops = 0;
+  for (const Step& st : p->steps) {
+    f[2] += 1;
+    switch (st.kind) {
+      case ST_EW: f[3] += 1; break;
+      case ST_GEMM:
+        if (st.gemm.m == 1 || st.gemm.n == 1) f[5] += 1;
+        else f[4] += 1;
+        if (st.gemm.tier == ARMA_TIER_SPLIT_BF16 || st.gemm.tier == ARMA_TIER_BF16) tc_flops += st.flops;
+        if (st.gemm.tier == ARMA_TIER_SPLIT_BF16) split_flops += st.flops;
+        break;
+      case ST_DOT: f[6] += 1; break;
+      case ST_TRANSPOSE: case ST_DIAGBUILD: f[7] += 1; break;
+      case ST_SOLVE: f[8] += 1; break;
+    }
+    maxf = std::max(maxf, st.flops);
+    maxb = std::max(maxb, st.bytes);
+  }
+  f[0] = l2(p->flops);
+  f[1] = l2(p->bytes);
+  f[9] = l2(maxf);
+  f[10] = l2(maxb);
+  f[11] = l2((double)p->ws_bytes);
+  f[12] = p->flops > 0 ? tc_flops / p->flops : 0;
+  f[13] = (p->flags & ARMA_PLAN_LITERAL) ? 1 : 0;
+  f[14] = p->flops > 0 ? split_flops / p->flops : 0;
+  f[15] = l2(p->bytes > 0 ? p->flops / p->bytes : 0);
+  for (int i = 0; i < ARMA_PLAN_FEATURES; ++i) out[i] = (float)f[i];
+  for (int i = ARMA_PLAN_FEATURES; i < n; ++i) out[i] = 0.f;
+  return ARMA_OK;
+}
+
+// Roofline estimate in the paper's spirit (fewer operations and fewer
+// passes over memory are faster): every step costs a launch plus the larger
+// of its compute time and its memory time on GB300.
+arma_status plan_heuristic(const arma_plan* p, double* seconds) {
+  if (!p || !seconds) return ARMA_ERR_INVALID;
+  const double hbm = 6.5e12, launch = 4e-6, dp = 0.3e12, simt = 40e12, bf16 = 1.2e15;
+  double t = 0;
+  for (const Step& st : p->steps) {
+    double c = 0;
+    switch (st.kind) {
+      case ST_EW:
+        c = st.ew.compute_f64 ? st.flops / dp : 0;
+        break;
+      case ST_GEMM:
+        if (st.gemm.m == 1 || st.gemm.n == 1) c = 0;
+        else if (st.gemm.tier == ARMA_TIER_SPLIT_BF16) c = 6 * st.flops / bf16 + 2e-6;
+        else if (st.gemm.tier == ARMA_TIER_BF16) c = st.flops / bf16 + 2e-6;
+        else if (st.gemm.tier == ARMA_TIER_F64) c = st.flops / dp;
+        else c = st.flops / simt;
+        break;
+      case ST_SOLVE:
+        c = st.flops / (st.solve.tier == ARMA_TIER_F64 ? dp : 0.3e15) + (double)st.solve.n * 3e-6;
+        break;
+      default:
+        break;
+    }
+    t += launch + std::max(c, st.bytes / hbm);
+  }
+  *seconds = t;
+  return ARMA_OK;
+}
+
 arma_status chain_order_api(int32_t n, const int64_t* dims, int32_t method, int32_t* splits,
                             uint64_t* cost) {
   if (n < 1 || n > 4096 || !dims || method < 0 || method > 2) return ARMA_ERR_INVALID;
