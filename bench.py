@@ -453,6 +453,45 @@ def bench_plain(a):
                       "graph_replay_us_all_six": gms * 1e3}), flush=True)
 
 
+def bench_planner(a):
+    """5,000 random DAGs (depth <= 5, dims log-uniform 16..8192, FP32/BF16,
+    literal work capped at 2e11 FLOP): candidates timed, the cost network
+    trained on 80% by the library's kernels, held-out picks of the network,
+    the FLOP/byte heuristic and the literal plan against the best candidate."""
+    import math
+    import torch
+    from paper_2502_03000_gb300 import costmodel as cm
+    t0 = time.perf_counter()
+    dags = cm.make_dags(20250203 + 5, 5000, lo=16, hi=8192, cap_flops=2e11)
+    gen_s = time.perf_counter() - t0
+    recs, done = [], 0
+    t1 = time.perf_counter()
+    budget = float(os.environ.get("ARMA_PLANNER_BUDGET_S", "420"))
+    for i in range(0, len(dags), 100):
+        part = cm.collect(dags[i:i + 100], reps=2)
+        for r in part:
+            r["dag"] += i
+        recs += part
+        done = i + len(dags[i:i + 100])
+        if time.perf_counter() - t1 > budget:
+            break
+    collect_s = time.perf_counter() - t1
+    train, test = cm.split_train_test(recs, 0.8)
+    net = cm.CostNet(seed=0)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    losses = net.fit([r["features"] for r in train], [math.log(r["time"]) for r in train], steps=3000)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t2
+    res = cm.evaluate(test, net)
+    res_train = cm.evaluate(train, net)
+    print(json.dumps({"workload": "random DAGs, depth<=5, dims log-uniform [16,8192], FP32/BF16, literal <= 2e11 FLOP",
+                      "dags_timed": done, "records": len(recs), "train_records": len(train), "test_dags": res["dags"],
+                      "gen_s": gen_s, "collect_s": collect_s, "train_s": train_s, "train_steps": 3000,
+                      "loss_first_last": [losses[0], losses[-1]], "held_out": res,
+                      "train_fit": {k: res_train[k] for k in res_train if k.endswith("regret")}}), flush=True)
+
+
 def main():
     a = args()
     if a.impl == "reference":
@@ -460,7 +499,7 @@ def main():
         return
     if a.workload != "fused":
         {"products": bench_products, "batched": bench_batched, "chain": bench_chain,
-         "solve": bench_solve, "plain": bench_plain}[a.workload](a)
+         "solve": bench_solve, "plain": bench_plain, "planner": bench_planner}[a.workload](a)
         return
     import numpy as np
     import torch
