@@ -130,9 +130,14 @@ __device__ __forceinline__ bool split_ff(double x, float& hi, float& lo) {
   const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
   const unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
   hi = __uint_as_float(sign | ((e - 896u) << 23) | (unsigned int)(mant >> 29));
-  const float rf = __uint2float_rn((unsigned int)(mant & 0x1FFFFFFFull));  // low 29 bits
-  const float scale = __uint_as_float((e - 948u) << 23);                  // 2^(e-1075)
-  lo = __fmul_rn(sign ? -rf : rf, scale);
+  // lo from the low 29 significand bits, assembled as float bits with
+  // integer operations (no conversion instruction, which would use the FP64
+  // pipe); truncated to 24 bits
+  const unsigned int rr = (unsigned int)(mant & 0x1FFFFFFFull);
+  if (rr == 0u) { lo = 0.f; return true; }
+  const int nb = 32 - __clz(rr);
+  const unsigned int m24 = nb > 24 ? rr >> (nb - 24) : rr << (24 - nb);
+  lo = __uint_as_float(sign | ((e - 1075u + (unsigned int)(nb - 1) + 127u) << 23) | (m24 & 0x7FFFFFu));
   return true;
 }
 
