@@ -180,6 +180,18 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest value over all ranks (the whole job's time is that of
+    its slowest replica); the identity without torch.distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def time_ms(fn, steps, stream):
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -571,9 +583,7 @@ def main():
     clocks = clocks_stop(clk)
     total_ms = t_start.elapsed_time(t_end)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dev)
         torch.distributed.barrier()
     ms32 = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     ms64 = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)

@@ -1,0 +1,47 @@
+"""The N > 1 path of bench.py on CPU: independent replicas (no data-path
+collective) whose job time is the maximum over ranks, and whose throughput
+counts the work of every rank.  Two gloo ranks on 127.0.0.1."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    mine = 10.0 + 5.0 * rank                  # each replica's own time
+    total = bench.max_over_ranks(mine, "cpu")
+    dist.barrier()
+    q.put((rank, total))
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=5) for _ in range(2))
+    assert got == {0: 15.0, 1: 15.0}
+
+
+def test_single_rank_identity():
+    import bench
+    assert bench.max_over_ranks(3.5) == 3.5
