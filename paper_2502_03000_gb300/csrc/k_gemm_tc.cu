@@ -395,46 +395,56 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int c0 = 0; c0 < BN / 2; c0 += 16) {
         float v[16];
         tmem_ld16(tb + (uint32_t)c0, v);
-        if (!row_ok) continue;
         const int64_t col0 = colh + c0;
+        if (f64_out && !p.partial) {
+          // FP64 results without FP64 instructions: FP32 scaling, beta*C as
+          // an exact float pair, the pair assembled into a double with
+          // integer operations.  C is loaded before any D store (C may alias
+          // D).  Elements outside the pair range take an FP64 path that runs
+          // only when some lane of the warp needs it.
+          const bool has_c = p.C && p.beta != 0.0;
+          double cv[16], outv[16];
+          float rv[16];
+          uint32_t bad = 0u;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const bool in = row_ok && col0 + j < p.n;
+            cv[j] = (has_c && in) ? load_as<double>(p.C, row + (col0 + j) * p.ldc, p.cdt) : 0.0;
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            float r = alpha_f * v[j] * rsf;
+            if (p.cs && row_ok && col0 + j < p.n) r *= load_as<float>(p.cs, (col0 + j) * p.cs_inc, p.csdt);
+            rv[j] = r;
+            if (has_c) {
+              ff::F2 c2, t;
+              bool fine = ff::split(cv[j], c2);
+              t = ff::axpy(b2, c2, ff::F2{r, 0.f});
+              fine = fine && ff::in_range(t);
+              outv[j] = ff::to_double(t);
+              bad |= fine ? 0u : (1u << j);
+            } else {
+              outv[j] = __longlong_as_double((long long)ff::f2d_bits(r));
+            }
+          }
+          if (__any_sync(0xffffffffu, bad != 0u)) {
+            for (int j = 0; j < 16; ++j)
+              if (bad & (1u << j)) outv[j] = (double)rv[j] + p.beta * cv[j];
+          }
+          if (row_ok) {
+            double* Dd = static_cast<double*>(p.D);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (col0 + j < p.n) Dd[row + (col0 + j) * p.ldd] = outv[j];
+          }
+          continue;
+        }
+        if (!row_ok) continue;
         if (p.partial) {
           float* dst = p.P + (int64_t)it.split * p.m * p.n + row;
 #pragma unroll
           for (int j = 0; j < 16; ++j)
             if (col0 + j < p.n) dst[(col0 + j) * p.m] = v[j];
-        } else if (f64_out) {
-          // FP64 results without FP64 instructions: FP32 scaling, beta*C as
-          // an exact float pair, the pair assembled into a double with
-          // integer operations.  The 16 C values are loaded before any D
-          // store (C may alias D), so the loads overlap.
-          double* Dd = static_cast<double*>(p.D);
-          const bool has_c = p.C && p.beta != 0.0;
-          double cv[16];
-          if (has_c) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-              cv[j] = (col0 + j < p.n) ? load_as<double>(p.C, row + (col0 + j) * p.ldc, p.cdt) : 0.0;
-          }
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int64_t col = col0 + j;
-            if (col >= p.n) break;
-            float r = alpha_f * v[j] * rsf;
-            if (p.cs) r *= load_as<float>(p.cs, col * p.cs_inc, p.csdt);
-            double out;
-            if (has_c) {
-              ff::F2 c2, t;
-              bool fine = ff::split(cv[j], c2);
-              if (fine) {
-                t = ff::axpy(b2, c2, ff::F2{r, 0.f});
-                fine = ff::in_range(t);
-              }
-              out = fine ? ff::to_double(t) : (double)r + p.beta * cv[j];
-            } else {
-              out = __longlong_as_double((long long)ff::f2d_bits(r));
-            }
-            Dd[row + col * p.ldd] = out;
-          }
         } else {
           // FP32 / BF16 results: FP32 epilogue arithmetic
           const bool has_c = p.C && p.beta != 0.0;
