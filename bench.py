@@ -32,10 +32,12 @@ SEED = 20250203 + 2
 # columns of the bounded CPU sample (the oracle evaluates this column block)
 SAMPLE_COLS = 1024
 
-# DRAM bytes of one fused FP64 launch at n = 8192 from an ncu capture of the
-# same kernel source (profiles/ew_fused_8192.md); reported as null once the
-# kernel source no longer has this hash.
-NCU_TRAFFIC = {"kernel_src_sha1": None, "f64": None, "f32": None}
+# DRAM bytes (read + write) of one fused launch at n = 8192, scaled by 4 from
+# an ncu capture of the same kernel source at n = 4096 (the traffic grows in
+# proportion to the elements); see profiles/ew_fused_8192.md.  Reported as
+# null once the kernel source no longer has this hash.
+NCU_TRAFFIC = {"kernel_src_sha1": "3f2ed9549de3c1f47f1b2fa9eba5193e6e2d247e",
+               "f64": 4 * (536.983296e6 + 105.824256e6), "f32": 4 * (268.539904e6 + 37.313536e6)}
 
 
 def kernel_sha1() -> str:

@@ -153,18 +153,16 @@ __device__ __forceinline__ void ff_add(float& sh, float& sl, float xh, float xl)
 struct FFAcc {
   float sh = 0.f, sl = 0.f, qh = 0.f, ql = 0.f;
   double s64 = 0.0, q64 = 0.0;  // values outside the pair's range
-  __device__ __forceinline__ void add(double x) {
-    float hi, lo;
-    if (__builtin_expect(split_ff(x, hi, lo), 1)) {
-      ff_add(sh, sl, hi, lo);
-      const float p = __fmul_rn(hi, hi);
-      float pe = __fmaf_rn(hi, hi, -p);
-      pe = __fmaf_rn(__fmul_rn(2.f, hi), lo, pe);
-      ff_add(qh, ql, p, pe);
-    } else {
-      s64 += x;
-      q64 = fma(x, x, q64);
-    }
+  __device__ __forceinline__ void add_pair(float hi, float lo) {
+    ff_add(sh, sl, hi, lo);
+    const float p = __fmul_rn(hi, hi);
+    float pe = __fmaf_rn(hi, hi, -p);
+    pe = __fmaf_rn(__fmul_rn(2.f, hi), lo, pe);
+    ff_add(qh, ql, p, pe);
+  }
+  __device__ __forceinline__ void add_f64(double x) {
+    s64 += x;
+    q64 = fma(x, x, q64);
   }
   // FP32 chunk sums (already float): plain two-sums, no FP64 instruction
   __device__ __forceinline__ void add_f32(float ps, float pq) {
@@ -284,8 +282,20 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) ew_flat_kernel(co
     if (a.out) store_chunk<T, V, CT>(static_cast<T*>(a.out), c, acc);
     if (a.red) {
       if constexpr (kFF) {
+        // float-pair accumulation; the FP64 route for out-of-range values
+        // runs only when an active lane needs it, so that it is a branch
+        // and not FP64 instructions issued for every element
+        uint32_t bad = 0u;
 #pragma unroll
-        for (int v = 0; v < V; ++v) ff.add((double)acc[v]);
+        for (int v = 0; v < V; ++v) {
+          float hi, lo;
+          if (split_ff((double)acc[v], hi, lo)) ff.add_pair(hi, lo);
+          else bad |= 1u << v;
+        }
+        if (__any_sync(__activemask(), bad != 0u)) {
+          for (int v = 0; v < V; ++v)
+            if (bad & (1u << v)) ff.add_f64((double)acc[v]);
+        }
       } else {
         float ps = 0.f, pq = 0.f;
 #pragma unroll
