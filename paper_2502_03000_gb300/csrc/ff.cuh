@@ -49,6 +49,26 @@ __device__ __forceinline__ bool split(double x, F2& r) {
   return true;
 }
 
+// double -> float, round to nearest even, integer operations only.  Returns
+// false (and r unspecified) unless the result is a normal float or zero.
+__device__ __forceinline__ bool d2f_rn(double x, float& r) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned int e = (unsigned int)(u >> 52) & 0x7ffu;
+  const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
+  if (e == 0u && (u << 1) == 0ull) { r = __uint_as_float(sign); return true; }
+  if (e < 897u || e > 1150u) return false;              // float exponent 1..254
+  const unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
+  unsigned int m = (unsigned int)(mant >> 29);          // 23 fraction bits
+  const unsigned int rem = (unsigned int)(mant & 0x1FFFFFFFull);
+  unsigned int be = e - 896u;
+  if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) {
+    if (++m == 0x800000u) { m = 0u; ++be; }
+  }
+  if (be >= 255u) return false;
+  r = __uint_as_float(sign | (be << 23) | m);
+  return true;
+}
+
 // exact float -> double bits (normal floats and zero)
 __device__ __forceinline__ unsigned long long f2d_bits(float f) {
   const unsigned int u = __float_as_uint(f);

@@ -397,11 +397,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         tmem_ld16(tb + (uint32_t)c0, v);
         const int64_t col0 = colh + c0;
         if (f64_out && !p.partial) {
-          // FP64 results without FP64 instructions: FP32 scaling, beta*C as
-          // an exact float pair, the pair assembled into a double with
-          // integer operations.  C is loaded before any D store (C may alias
-          // D).  Elements outside the pair range take an FP64 path that runs
-          // only when some lane of the warp needs it.
+          // FP64 results without FP64 instructions.  The product of these
+          // tiers is FP32-accurate, so beta*C is added in FP32 too: C is
+          // rounded to float with integer operations (error <= 2^-24 |C|),
+          // the sum is widened to a double exactly by integer operations.
+          // C outside float range takes an FP64 path behind a warp vote.
+          // C is loaded before any D store (C may alias D).
           const bool has_c = p.C && p.beta != 0.0;
           double cv[16], outv[16];
           float rv[16];
@@ -417,15 +418,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (p.cs && row_ok && col0 + j < p.n) r *= load_as<float>(p.cs, (col0 + j) * p.cs_inc, p.csdt);
             rv[j] = r;
             if (has_c) {
-              ff::F2 c2, t;
-              bool fine = ff::split(cv[j], c2);
-              t = ff::axpy(b2, c2, ff::F2{r, 0.f});
-              fine = fine && ff::in_range(t);
-              outv[j] = ff::to_double(t);
+              float cf;
+              const bool fine = ff::d2f_rn(cv[j], cf);
               bad |= fine ? 0u : (1u << j);
-            } else {
-              outv[j] = __longlong_as_double((long long)ff::f2d_bits(r));
+              r = fmaf(beta_f, cf, r);
             }
+            outv[j] = __longlong_as_double((long long)ff::f2d_bits(r));
           }
           if (__any_sync(0xffffffffu, bad != 0u)) {
             for (int j = 0; j < 16; ++j)
@@ -590,6 +588,49 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepA
   }
 }
 
+// op(X) contiguous along K (the common case): each thread converts 8
+// consecutive K elements of one row and writes one 16-byte vector per slice
+__global__ void __launch_bounds__(256) prep_kcontig_kernel(const __grid_constant__ PrepArgs a) {
+  if (a.slices != 1 && a.slices != 3) return;
+  const int64_t groups = a.kp / 8;
+  const int64_t total = a.rpad * groups;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / groups, l0 = (t - r * groups) * 8;
+    __align__(16) uint16_t s0[8];
+    __align__(16) uint16_t s1[8];
+    __align__(16) uint16_t s2[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      uint16_t sl[3] = {0, 0, 0};
+      const int64_t l = l0 + e;
+      if (r < a.R && l < a.K) {
+        const int64_t idx = l + r * a.ldx;
+        if (a.xdt == ARMA_F64) {
+          const double x = static_cast<const double*>(a.X)[idx];
+          if (a.slices == 1) sl[0] = d2bf16_rn(x);
+          else split3_f64(x, sl);
+        } else if (a.xdt == ARMA_F32) {
+          const float x = static_cast<const float*>(a.X)[idx];
+          if (a.slices == 1) sl[0] = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+          else split3_f32(x, sl);
+        } else {
+          sl[0] = static_cast<const uint16_t*>(a.X)[idx];
+        }
+      }
+      s0[e] = sl[0]; s1[e] = sl[1]; s2[e] = sl[2];
+    }
+    uint4* o0 = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(a.out) + r * a.kp + l0);
+    *o0 = *reinterpret_cast<const uint4*>(s0);
+    if (a.slices == 3) {
+      uint4* o1 = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(a.out) + (a.rpad + r) * a.kp + l0);
+      uint4* o2 = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(a.out) + (2 * a.rpad + r) * a.kp + l0);
+      *o1 = *reinterpret_cast<const uint4*>(s1);
+      *o2 = *reinterpret_cast<const uint4*>(s2);
+    }
+  }
+}
+
 // D = alpha * diag(r) * (sum_s P_s) * diag(c) + beta * C, partials summed in FP64
 struct CombineArgs {
   int64_t m, n;
@@ -712,14 +753,23 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   PrepArgs pa;
   pa.X = a.A; pa.ldx = a.lda; pa.xdt = a.adt; pa.trans = a.ta;
   pa.R = a.m; pa.K = a.k; pa.rpad = g.mpad; pa.kp = g.kp; pa.slices = g.slices; pa.out = As;
-  dim3 ga((unsigned)((g.mpad + 31) / 32), (unsigned)((g.kp + 31) / 32));
-  prep_kernel<<<ga, 256, 0, s>>>(pa);
+  const int sms0 = device_sm_count();
+  auto prep = [&](const PrepArgs& pp) {
+    if (pp.trans) {
+      const int64_t total = pp.rpad * (pp.kp / 8);
+      int64_t blocks = (total + 255) / 256, cap = (int64_t)sms0 * 8;
+      prep_kcontig_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(pp);
+    } else {
+      dim3 gg((unsigned)((pp.rpad + 31) / 32), (unsigned)((pp.kp + 31) / 32));
+      prep_kernel<<<gg, 256, 0, s>>>(pp);
+    }
+  };
+  prep(pa);
   // op(B)^T (n x k): element (j, l) = op(B)(l, j) = tb ? B[j + l*ldb] : B[l + j*ldb]
   PrepArgs pb;
   pb.X = a.B; pb.ldx = a.ldb; pb.xdt = a.bdt; pb.trans = a.tb ? 0 : 1;
   pb.R = a.n; pb.K = a.k; pb.rpad = g.npad; pb.kp = g.kp; pb.slices = g.slices; pb.out = Bs;
-  dim3 gb((unsigned)((g.npad + 31) / 32), (unsigned)((g.kp + 31) / 32));
-  prep_kernel<<<gb, 256, 0, s>>>(pb);
+  prep(pb);
   if (launches) *launches += 2;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
