@@ -155,7 +155,8 @@ arma_status arma_gpu_eval(const arma_plan* plan, const void* const* in_ptrs,
                           void* stream);
 
 /* After the stream of an arma_gpu_eval has been synchronised: read the
- * device-side status the evaluation left in `workspace`.  Returns ARMA_OK,
+ * device-side status the evaluation left in `workspace`.  Returns ARMA_OK
+ * (info = refinement steps a mixed-precision solve took, else 0),
  * ARMA_ERR_SINGULAR (info = 1-based column of the zero pivot) or
  * ARMA_ERR_NOCONVERGE (info = refinement steps taken).  Synchronises `stream`. */
 arma_status arma_gpu_eval_status(const arma_plan* plan, const void* workspace, void* stream,

@@ -4,16 +4,22 @@
 // the smallest row index), then forward and back substitution, and for the
 // mixed-precision tiers FP64 iterative refinement.
 //
-//   panel      one cooperative launch per 64-column panel: each CTA keeps its
-//              block of panel rows in shared memory; per column the CTAs
-//              publish their local pivot candidate and meet at one grid
-//              barrier (bounded spin), then all pick the same pivot, swap and
-//              update locally
+//   panel      one launch per 64-column panel: each CTA keeps its block of
+//              panel rows in shared memory; per column the CTAs publish
+//              their local pivot candidate and meet at one barrier, then all
+//              pick the same pivot, swap and update locally.  The CTAs form
+//              one thread-block cluster (distributed shared memory, hardware
+//              barrier) when the panel fits, else a cooperative grid with a
+//              bounded-spin barrier in global memory
 //   laswp      the panel's row swaps applied to the other columns
-//   trsm       U12 = L11^-1 A12
+//   trsm       U12 = L11^-1 A12, one warp per column
 //   update     A22 -= L21 U12 through the product kernels: DFMA for the FP64
 //              tier, split-BF16 tcgen05 (FP32-accurate) or BF16 tcgen05
-//   trsv       one CTA per right-hand side: L then U substitution in smem
+//   trsv       blocked substitution over all right-hand sides in one
+//              cooperative launch: a CTA per (64-row block, 64 right-hand
+//              sides) subtracts the blocks its rows depend on as their flags
+//              are released, then solves its diagonal block (fallback: one
+//              launch per diagonal block)
 //   refine     r = B - A x in FP64 (DFMA), correction solved with the FP32
 //              factors, x += d in FP64, until the normwise backward error
 //              |r| / (|A||x| + |B|) <= 1e-14 or the step limit
@@ -35,6 +41,7 @@ constexpr int MAX_CTAS = 64;
 constexpr int MAX_IR = 10;
 constexpr double IR_TOL = 1e-14;
 constexpr unsigned int SPIN_LIMIT = 1u << 26;
+constexpr uint64_t WAIT_NS = 2000000000ull;     // 2 s bound on one wait
 
 struct Ctl {                    // device control block in the solve scratch
   unsigned int bar_count, bar_gen;
@@ -90,6 +97,28 @@ struct PanelArgs {
   int32_t* status; int64_t* info;
 };
 
+// the CTA's panel rows into shared memory, eight loads in flight per thread
+template <int NT, typename T>
+__device__ __forceinline__ void load_panel(T* sm, const T* A, int64_t ld, int64_t r0, int64_t j, int64_t nown,
+                                           int w, int64_t R) {
+  const int64_t total = nown * w;
+  for (int64_t t0 = 0; t0 < total; t0 += (int64_t)NT * 8) {
+    T v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t t = t0 + threadIdx.x + (int64_t)NT * k;
+      const int64_t c = t / nown, r = t - c * nown;
+      v[k] = t < total ? A[(r0 + r) + (j + c) * ld] : (T)0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t t = t0 + threadIdx.x + (int64_t)NT * k;
+      const int64_t c = t / nown, r = t - c * nown;
+      if (t < total) sm[c * R + r] = v[k];
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(PT) panel_kernel(const __grid_constant__ PanelArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -104,10 +133,7 @@ __global__ void __launch_bounds__(PT) panel_kernel(const __grid_constant__ Panel
   const int64_t r1 = min(r0 + R, a.n);                          // one past last
   const int64_t nown = r1 > r0 ? r1 - r0 : 0;
   const int w = a.w;
-  for (int64_t t = threadIdx.x; t < nown * w; t += PT) {
-    const int64_t c = t / nown, r = t - c * nown;
-    sm[c * R + r] = a.A[(r0 + r) + (a.j + c) * a.ld];
-  }
+  load_panel<PT>(sm, a.A, a.ld, r0, a.j, nown, w, R);
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int c = 0; c < w; ++c) {
@@ -144,27 +170,37 @@ __global__ void __launch_bounds__(PT) panel_kernel(const __grid_constant__ Panel
         a.cand_data[((int64_t)ph * MAX_CTAS + blockIdx.x) * NB + q] = sm[q * R + (s_p - r0)];
     if (d >= r0 && d < r1)
       for (int q = threadIdx.x; q < w; q += PT) a.drow[ph * NB + q] = sm[q * R + (d - r0)];
-    __threadfence();
-    // 2. all CTAs meet
+    // 2. all CTAs meet (the barrier orders this block's writes before its
+    //    arrival: bar.sync, then a device fence by the arriving thread)
     if (!grid_barrier(a.ctl, gridDim.x, a.status)) return;
-    // 3. every CTA picks the same pivot
-    if (threadIdx.x == 0) {
+    // 3. every CTA picks the same pivot: warp 0 reads the candidates in
+    //    parallel and reduces them (ties to the smallest row index)
+    if (wid == 0) {
       double v = -1.0;
       int64_t p = INT64_MAX;
       int win = -1;
-      for (unsigned int b = 0; b < gridDim.x; ++b) {
+      for (unsigned int b = lane; b < gridDim.x; b += 32) {
         const double cv = __ldcg(a.cand_val + ph * MAX_CTAS + b);
         const int64_t cr = __ldcg(reinterpret_cast<const long long*>(a.cand_row) + ph * MAX_CTAS + b);
         if (cv > v || (cv == v && cr < p)) { v = cv; p = cr; win = (int)b; }
       }
-      if (v <= 0.0) {             // exact zero column: singular, keep going
-        if (atomicCAS(a.status, 0, (int32_t)ARMA_ERR_SINGULAR) == 0) *a.info = d + 1;
-        p = d;
-        win = -1;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, v, off);
+        const int64_t op = __shfl_down_sync(0xffffffffu, p, off);
+        const int ow = __shfl_down_sync(0xffffffffu, win, off);
+        if (ov > v || (ov == v && op < p)) { v = ov; p = op; win = ow; }
       }
-      s_p = p;
-      s_win = win;
-      if (blockIdx.x == 0) a.piv[d] = (int32_t)p;
+      if (lane == 0) {
+        if (v <= 0.0) {             // exact zero column: singular, keep going
+          if (atomicCAS(a.status, 0, (int32_t)ARMA_ERR_SINGULAR) == 0) *a.info = d + 1;
+          p = d;
+          win = -1;
+        }
+        s_p = p;
+        s_win = win;
+        if (blockIdx.x == 0) a.piv[d] = (int32_t)p;
+      }
     }
     __syncthreads();
     const int64_t p = s_p;
@@ -203,6 +239,150 @@ __global__ void __launch_bounds__(PT) panel_kernel(const __grid_constant__ Panel
   }
 }
 
+// The same panel factorisation with the CTAs of one thread-block cluster:
+// candidates, the pivot row and row d are read from the owning CTA's shared
+// memory through the cluster's distributed shared memory, and the per-column
+// meeting point is the cluster's hardware barrier (all CTAs of a cluster are
+// co-resident, so the barrier needs no spin).  512 threads per CTA: thread
+// (slot, seg) owns rows slot, slot + 128, ... of the CTA and panel columns
+// 16 seg .. 16 seg + 15, so the rank-1 update of a column is spread over all
+// threads.  Every warp selects the pivot from the CTAs' candidates itself,
+// which saves a block barrier per column.  Used when the panel fits the
+// cluster's shared memory.
+constexpr int CPT = 512;
+constexpr int CSLOTS = CPT / 4;
+
+template <typename T>
+__device__ __forceinline__ void argmax_step(T& v, int64_t& r, int& win, int off) {
+  const T ov = __shfl_down_sync(0xffffffffu, v, off);
+  const int64_t orr = __shfl_down_sync(0xffffffffu, r, off);
+  const int ow = __shfl_down_sync(0xffffffffu, win, off);
+  if (ov > v || (ov == v && orr < r)) { v = ov; r = orr; win = ow; }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CPT) panel_cluster_kernel(const __grid_constant__ PanelArgs<T> a) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);   // [w][R] column-major
+  __shared__ T red_v[CPT / 32];
+  __shared__ int64_t red_r[CPT / 32];
+  __shared__ T c_val[2];                  // this CTA's candidate, per phase
+  __shared__ int64_t c_row[2];
+  __shared__ __align__(16) T c_data[2][NB];   // its candidate row
+  __shared__ __align__(16) T c_drow[2][NB];   // row d when owned here
+  const unsigned int nranks = cl.num_blocks();
+  const unsigned int rank = cl.block_rank();
+  const int64_t R = a.rows_per_cta;
+  const int64_t r0 = a.j + (int64_t)rank * R;
+  const int64_t r1 = min(r0 + R, a.n);
+  const int64_t nown = r1 > r0 ? r1 - r0 : 0;
+  const int w = a.w;
+  load_panel<CPT>(sm, a.A, a.ld, r0, a.j, nown, w, R);
+  __syncthreads();
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int slot = tid & (CSLOTS - 1), seg = tid / CSLOTS;
+  for (int c = 0; c < w; ++c) {
+    const int64_t d = a.j + c;
+    const int ph = c & 1;
+    const unsigned int downer = (unsigned int)((d - a.j) / R);
+    // A. this CTA's candidate: largest |value| of column c among rows >= d
+    {
+      T bv = (T)-1;
+      int64_t br = INT64_MAX;
+      int dummy = 0;
+      for (int64_t r = tid; r < nown; r += CPT) {
+        const int64_t g = r0 + r;
+        if (g < d) continue;
+        const T v = fabs(sm[c * R + r]);
+        if (v > bv || (v == bv && g < br)) { bv = v; br = g; }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) argmax_step(bv, br, dummy, off);
+      if (lane == 0) { red_v[wid] = bv; red_r[wid] = br; }
+      if (wid == 1 && rank == downer)
+        for (int q = lane; q < w; q += 32) c_drow[ph][q] = sm[q * R + (d - r0)];
+      __syncthreads();
+      if (wid == 0) {
+        bv = lane < CPT / 32 ? red_v[lane] : (T)-1;
+        br = lane < CPT / 32 ? red_r[lane] : INT64_MAX;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) argmax_step(bv, br, dummy, off);
+        br = __shfl_sync(0xffffffffu, br, 0);
+        if (lane == 0) { c_val[ph] = bv; c_row[ph] = br; }
+        if (br >= r0 && br < r1)
+          for (int q = lane; q < w; q += 32) c_data[ph][q] = sm[q * R + (br - r0)];
+      }
+    }
+    cl.sync();
+    // C. every warp picks the same pivot from the CTAs' candidates
+    T v = (T)-1;
+    int64_t p = INT64_MAX;
+    int win = -1;
+    if ((unsigned int)lane < nranks) {
+      v = *cl.map_shared_rank(&c_val[ph], (unsigned int)lane);
+      p = *cl.map_shared_rank(&c_row[ph], (unsigned int)lane);
+      win = lane;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) argmax_step(v, p, win, off);
+    v = __shfl_sync(0xffffffffu, v, 0);
+    p = __shfl_sync(0xffffffffu, p, 0);
+    win = __shfl_sync(0xffffffffu, win, 0);
+    if (v <= (T)0) {                      // exact zero column: singular, keep going
+      p = d;
+      win = -1;
+    }
+    if (tid == 0 && rank == 0) {
+      if (win < 0 && atomicCAS(a.status, 0, (int32_t)ARMA_ERR_SINGULAR) == 0) *a.info = d + 1;
+      a.piv[d] = (int32_t)p;
+    }
+    const T* prow = win >= 0 ? cl.map_shared_rank(&c_data[ph][0], (unsigned int)win)
+                             : cl.map_shared_rank(&c_drow[ph][0], downer);
+    T u[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) u[k] = seg * 16 + k < w ? prow[seg * 16 + k] : (T)0;
+    const T pv = prow[c];
+    // D. swap rows d and p (each thread its own columns), scale column c
+    if (p != d) {
+      const int64_t rd = d - r0, rp = p - r0;
+      if (rd >= 0 && rd < nown && (rd & (CSLOTS - 1)) == slot) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          if (seg * 16 + k < w) sm[(seg * 16 + k) * R + rd] = u[k];
+      }
+      if (rp >= 0 && rp < nown && (rp & (CSLOTS - 1)) == slot) {
+        const T* dr = cl.map_shared_rank(&c_drow[ph][0], downer);
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          if (seg * 16 + k < w) sm[(seg * 16 + k) * R + rp] = dr[seg * 16 + k];
+      }
+    }
+    if (win >= 0 && seg == (c >> 4))
+      for (int64_t r = slot; r < nown; r += CSLOTS)
+        if (r0 + r > d) sm[c * R + r] = sm[c * R + r] / pv;
+    __syncthreads();
+    // E. rank-1 update of the remaining columns of this thread's rows
+    if (win >= 0 && seg * 16 + 15 > c)
+      for (int64_t r = slot; r < nown; r += CSLOTS) {
+        if (r0 + r <= d) continue;
+        const T l = sm[c * R + r];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int q = seg * 16 + k;
+          if (q > c && q < w) sm[q * R + r] -= l * u[k];
+        }
+      }
+    __syncthreads();
+  }
+  cl.sync();                              // peers may still read this CTA's buffers
+  for (int64_t t = threadIdx.x; t < nown * w; t += CPT) {
+    const int64_t c = t / nown, r = t - c * nown;
+    a.A[(r0 + r) + (a.j + c) * a.ld] = sm[c * R + r];
+  }
+}
+
 // the panel's row swaps applied to columns outside [j, j + w)
 template <typename T>
 __global__ void laswp_kernel(T* A, int64_t ld, int64_t n, int64_t j, int w, const int32_t* piv) {
@@ -220,23 +400,335 @@ __global__ void laswp_kernel(T* A, int64_t ld, int64_t n, int64_t j, int w, cons
   }
 }
 
-// U12 = L11^-1 A12 (L11 unit lower w x w), one thread per column of A12
+// U12 = L11^-1 A12 (L11 unit lower w x w): one warp per column of A12, lane
+// l holding rows l and l + 32; the column is read and written coalesced
 template <typename T>
-__global__ void trsm_kernel(T* A, int64_t ld, int64_t n, int64_t j, int w) {
+__global__ void __launch_bounds__(256) trsm_kernel(T* A, int64_t ld, int64_t n, int64_t j, int w) {
   __shared__ T L[NB * NB];
   for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
     const int r = t % w, c = t / w;
     L[c * NB + r] = A[(j + r) + (j + c) * ld];
   }
   __syncthreads();
-  const int64_t col = j + w + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t col = j + w + (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (col >= n) return;
-  T x[NB];
-  for (int r = 0; r < w; ++r) x[r] = A[(j + r) + col * ld];
-  for (int r = 0; r < w; ++r)
-    for (int r2 = r + 1; r2 < w; ++r2) x[r2] -= L[r * NB + r2] * x[r];
-  for (int r = 0; r < w; ++r) A[(j + r) + col * ld] = x[r];
+  T* x = A + j + col * ld;
+  T x0 = lane < w ? x[lane] : (T)0;
+  T x1 = lane + 32 < w ? x[lane + 32] : (T)0;
+  for (int r = 0; r < w; ++r) {
+    const T xr = __shfl_sync(0xffffffffu, r < 32 ? x0 : x1, r & 31);
+    if (lane > r) x0 -= L[r * NB + lane] * xr;
+    if (lane + 32 > r && lane + 32 < w) x1 -= L[r * NB + lane + 32] * xr;
+  }
+  if (lane < w) x[lane] = x0;
+  if (lane + 32 < w) x[lane + 32] = x1;
 }
+
+// ---- blocked substitution helpers (64 x 64 blocks, 256 threads) ----
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// dst[c * NB + r] = src[r + c * ld] for r < rows, c < cols, zero elsewhere
+template <typename T>
+__device__ __forceinline__ void load_block(T* dst, const T* src, int64_t ld, int rows, int cols) {
+  T v[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int t = threadIdx.x + 256 * k, r = t & (NB - 1), c = t >> 6;
+    v[k] = (r < rows && c < cols) ? src[r + (int64_t)c * ld] : (T)0;
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) dst[threadIdx.x + 256 * k] = v[k];
+}
+
+// dst[c * (NB + 1) + r] = src[r + c * ld] (through L2: data other CTAs wrote)
+template <typename T>
+__device__ __forceinline__ void load_cols_cg(T* dst, const T* src, int64_t ld, int rows, int cols) {
+  T v[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int t = threadIdx.x + 256 * k, r = t & (NB - 1), c = t >> 6;
+    v[k] = (r < rows && c < cols) ? __ldcg(src + r + (int64_t)c * ld) : (T)0;
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int t = threadIdx.x + 256 * k, r = t & (NB - 1), c = t >> 6;
+    dst[c * (NB + 1) + r] = v[k];
+  }
+}
+
+__device__ __forceinline__ void ld16(const float* p, float (&o)[16]) {
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const float4 t = reinterpret_cast<const float4*>(p)[v];
+    o[4 * v] = t.x; o[4 * v + 1] = t.y; o[4 * v + 2] = t.z; o[4 * v + 3] = t.w;
+  }
+}
+__device__ __forceinline__ void ld16(const double* p, double (&o)[16]) {
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    const double2 t = reinterpret_cast<const double2*>(p)[v];
+    o[2 * v] = t.x; o[2 * v + 1] = t.y;
+  }
+}
+
+// thread (col, q) holds rows q*16 .. q*16+15 of column col in y:
+// y -= M X_k over m < kw, M column-major in Ms, X_k in Xs[col * (NB + 1) + m]
+template <typename T>
+__device__ __forceinline__ void block_update(T (&y)[16], const T* Ms, const T* Xs, int col, int q, int kw) {
+  for (int m = 0; m < kw; ++m) {
+    const T x = Xs[col * (NB + 1) + m];
+    T mv[16];
+    ld16(Ms + m * NB + q * 16, mv);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) y[k] -= mv[k] * x;
+  }
+}
+
+// unit-lower (LOWER) or upper solve with the diagonal block D (column-major,
+// dinv = reciprocals of its diagonal), rows distributed as in block_update;
+// the four threads of a column are consecutive lanes
+template <typename T, bool LOWER>
+__device__ __forceinline__ void block_solve(T (&y)[16], const T* D, const T* dinv, int w, int q, int lane) {
+  const int base = lane & ~3;
+  if (LOWER) {
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq)
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        const int r = qq * 16 + kk;
+        const T yr = __shfl_sync(0xffffffffu, y[kk], base | qq);
+        if (r < w && q >= qq) {
+          T dv[16];
+          ld16(D + r * NB + q * 16, dv);
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            if (q * 16 + k > r) y[k] -= dv[k] * yr;
+        }
+      }
+  } else {
+#pragma unroll
+    for (int qq = 3; qq >= 0; --qq)
+#pragma unroll
+      for (int kk = 15; kk >= 0; --kk) {
+        const int r = qq * 16 + kk;
+        T yr = __shfl_sync(0xffffffffu, y[kk], base | qq);
+        if (r < w) {
+          yr *= dinv[r];
+          if (q == qq) y[kk] = yr;
+          if (q <= qq) {
+            T dv[16];
+            ld16(D + r * NB + q * 16, dv);
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+              if (q * 16 + k < r) y[k] -= dv[k] * yr;
+          }
+        }
+      }
+  }
+}
+
+template <typename T>
+__host__ __device__ inline size_t coop_smem(void) {
+  return sizeof(T) * (2 * (size_t)NB * NB + (size_t)64 * (NB + 1) + NB);
+}
+
+// The whole substitution y := U^-1 L^-1 y in one cooperative launch: CTA
+// (i, c) owns block row i of a 64-column slice c.  Forward: it subtracts
+// L_ik z_k for k < i as each z_k is published (flag per block, release /
+// acquire), solves with L_ii and publishes z_i to Z.  Backward: it subtracts
+// U_ik y_k for k > i as each y_k is published to Y, solves with U_ii and
+// publishes y_i.  Every wait is bounded in time; a wait that runs out marks
+// the control block and the status, and every other wait then gives up.
+template <typename T>
+__global__ void __launch_bounds__(256) sub_coop_kernel(const T* __restrict__ LU, int64_t n, T* Y, T* Z,
+                                                       int64_t nrhs, unsigned int* flags, Ctl* ctl,
+                                                       int32_t* status, const int* skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* D = reinterpret_cast<T*>(smraw);
+  T* Ms = D + NB * NB;
+  T* Xs = Ms + NB * NB;
+  T* dinv = Xs + 64 * (NB + 1);
+  __shared__ int s_ok;
+  const int nb = gridDim.x, bi = blockIdx.x;
+  const int64_t j = (int64_t)bi * NB;
+  const int w = (int)(n - j < NB ? n - j : NB);
+  const int64_t c0 = (int64_t)blockIdx.y * 64;
+  const int ncols = (int)(nrhs - c0 < 64 ? nrhs - c0 : 64);
+  unsigned int* fwd = flags;
+  unsigned int* bwd = flags + (size_t)nb * gridDim.y;
+  const int tid = threadIdx.x, lane = tid & 31, col = tid >> 2, q = tid & 3;
+
+  auto wait = [&](const unsigned int* f) -> bool {
+    if (tid == 0) {
+      int ok = 1;
+      const uint64_t t0 = global_ns();
+      for (unsigned int it = 0; ld_acquire(f) == 0u; ++it) {
+        if (*(volatile int*)&ctl->err || it > SPIN_LIMIT || ((it & 255u) == 0u && global_ns() - t0 > WAIT_NS)) {
+          atomicExch(&ctl->err, 1);
+          atomicCAS(status, 0, (int32_t)ARMA_ERR_CUDA);
+          ok = 0;
+          break;
+        }
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+  };
+  auto publish = [&](T* dst, T (&y)[16], unsigned int* f) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) Xs[col * (NB + 1) + q * 16 + k] = y[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int t = tid + 256 * k, r = t & (NB - 1), c = t >> 6;
+      if (r < w && c < ncols) dst[r + (int64_t)c * n] = Xs[c * (NB + 1) + r];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_release(f, 1u);
+    }
+  };
+
+  load_block(D, LU + j + j * n, n, w, w);
+  load_cols_cg(Xs, Y + j + c0 * n, n, w, ncols);
+  __syncthreads();
+  if (tid < NB) {
+    const T p = D[tid * NB + tid];
+    dinv[tid] = (tid < w && p != (T)0) ? (T)1 / p : (T)0;
+  }
+  T y[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) y[k] = Xs[col * (NB + 1) + q * 16 + k];
+  __syncthreads();
+
+  for (int k = 0; k < bi; ++k) {                // forward: L_ik, k < i
+    load_block(Ms, LU + j + (int64_t)k * NB * n, n, w, NB);
+    if (!wait(fwd + (size_t)k * gridDim.y + blockIdx.y)) return;
+    load_cols_cg(Xs, Z + (int64_t)k * NB + c0 * n, n, NB, ncols);
+    __syncthreads();
+    block_update(y, Ms, Xs, col, q, NB);
+    __syncthreads();
+  }
+  block_solve<T, true>(y, D, dinv, w, q, lane);
+  publish(Z + j + c0 * n, y, fwd + (size_t)bi * gridDim.y + blockIdx.y);
+
+  for (int k = nb - 1; k > bi; --k) {           // backward: U_ik, k > i
+    const int wk = (int)(n - (int64_t)k * NB < NB ? n - (int64_t)k * NB : NB);
+    load_block(Ms, LU + j + (int64_t)k * NB * n, n, w, wk);
+    if (!wait(bwd + (size_t)k * gridDim.y + blockIdx.y)) return;
+    load_cols_cg(Xs, Y + (int64_t)k * NB + c0 * n, n, wk, ncols);
+    __syncthreads();
+    block_update(y, Ms, Xs, col, q, wk);
+    __syncthreads();
+  }
+  block_solve<T, false>(y, D, dinv, w, q, lane);
+  publish(Y + j + c0 * n, y, bwd + (size_t)bi * gridDim.y + blockIdx.y);
+}
+
+// One step of the blocked substitution for diagonal block j (w <= 64 rows)
+// and a 64-column slice of the right-hand sides.  Every CTA solves the
+// diagonal block redundantly (unit lower L_jj in the forward sweep, U_jj in
+// the backward sweep) from Yio's rows [j, j + w), then subtracts the block
+// column's product from its own SUB_ROWS rows of Yio in [r_begin,
+// r_begin + rows); CTA 0 also writes the solved rows to Yout.  Yio's rows
+// [j, j + w) are only read, so CTAs never race on them.
+//   solve: 4 threads per column, thread q holding rows 16q .. 16q + 15
+//   update: thread (i, g) computes row i for columns g, g + 8, ...
+// The fallback when the cooperative substitution does not fit the GPU.
+constexpr int SUB_ROWS = 32;
+
+template <typename T>
+__host__ __device__ inline size_t sub_smem(void) {
+  return sizeof(T) * ((size_t)NB * NB + (size_t)NB * (NB + 1) + (size_t)NB * SUB_ROWS + NB);
+}
+
+template <typename T, bool LOWER>
+__global__ void __launch_bounds__(256) sub_step_kernel(const T* __restrict__ LU, int64_t n, int64_t j, int w,
+                                                       T* Yio, T* Yout, int64_t nrhs, int64_t r_begin,
+                                                       int64_t rows, const int* skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* D = reinterpret_cast<T*>(smraw);              // [NB][NB], D[c * NB + r]
+  T* Ys = D + NB * NB;                              // [64][NB + 1], Ys[col * (NB + 1) + r]
+  T* At = Ys + NB * (NB + 1);                       // [NB][SUB_ROWS], At[r * SUB_ROWS + i]
+  T* dinv = At + NB * SUB_ROWS;                     // [NB]
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t c0 = (int64_t)blockIdx.y * 64;
+  const int ncols = (int)(nrhs - c0 < 64 ? nrhs - c0 : 64);
+  const int64_t rb = r_begin + (int64_t)blockIdx.x * SUB_ROWS;
+  const int64_t rem = r_begin + rows - rb;
+  const int nr = (int)(rem < SUB_ROWS ? (rem > 0 ? rem : 0) : SUB_ROWS);
+  load_block(D, LU + j + j * n, n, w, w);
+  load_cols_cg(Ys, Yio + j + c0 * n, n, w, ncols);
+  {
+    T v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int t = tid + 256 * k, i = t & (SUB_ROWS - 1), r = t / SUB_ROWS;
+      v[k] = (i < nr && r < w) ? LU[(rb + i) + (j + r) * n] : (T)0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) At[tid + 256 * k] = v[k];
+  }
+  __syncthreads();
+  if (tid < NB) {
+    const T p = D[tid * NB + tid];
+    dinv[tid] = (tid < w && p != (T)0) ? (T)1 / p : (T)0;
+  }
+  const int col = tid >> 2, q = tid & 3;
+  T y[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) y[k] = Ys[col * (NB + 1) + q * 16 + k];
+  __syncthreads();
+  block_solve<T, LOWER>(y, D, dinv, w, q, lane);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) Ys[col * (NB + 1) + q * 16 + k] = y[k];
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int t = tid; t < NB * 64; t += 256) {
+      const int r = t & (NB - 1), c = t >> 6;
+      if (r < w && c < ncols) Yout[(j + r) + (c0 + c) * n] = Ys[c * (NB + 1) + r];
+    }
+  if (nr == 0) return;
+  const int i = tid & (SUB_ROWS - 1), g = tid / SUB_ROWS;
+  T acc[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) acc[m] = 0;
+  for (int r = 0; r < w; ++r) {
+    const T av = At[r * SUB_ROWS + i];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) acc[m] += av * Ys[(g + 8 * m) * (NB + 1) + r];
+  }
+  if (i < nr)
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int c = g + 8 * m;
+      if (c < ncols) {
+        T* p = Yio + (rb + i) + (c0 + c) * n;
+        *p = *p - acc[m];
+      }
+    }
+}
+
 
 // perm = composition of the row swaps; Y(:, c) = P * B(:, c) (B null: identity)
 __global__ void perm_kernel(const int32_t* piv, int32_t* perm, int64_t n) {
@@ -263,36 +755,6 @@ __global__ void gather_kernel(const void* B, int64_t ldb, int32_t bdt, const int
     else v = (src == c) ? (T)1 : (T)0;
     Y[i + c * n] = v;
   }
-}
-
-// one CTA per right-hand side: y := U^-1 L^-1 y, y in shared memory
-template <typename T>
-__global__ void __launch_bounds__(256) trsv_kernel(const T* LU, int64_t ld, int64_t n, T* Y, int64_t ldy,
-                                                  const int* skip) {
-  if (skip && *skip) return;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* y = reinterpret_cast<T*>(smraw);
-  T* col = Y + (int64_t)blockIdx.x * ldy;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) y[i] = col[i];
-  __syncthreads();
-  for (int64_t i = 0; i < n; ++i) {            // unit lower
-    const T yi = y[i];
-    for (int64_t r = i + 1 + threadIdx.x; r < n; r += blockDim.x) y[r] -= LU[r + i * ld] * yi;
-    __syncthreads();
-  }
-  for (int64_t i = n - 1; i >= 0; --i) {       // upper
-    __shared__ T s_yi;
-    if (threadIdx.x == 0) {
-      const T piv = LU[i + i * ld];
-      s_yi = piv != (T)0 ? y[i] / piv : (T)0;
-      y[i] = s_yi;
-    }
-    __syncthreads();
-    const T yi = s_yi;
-    for (int64_t r = threadIdx.x; r < i; r += blockDim.x) y[r] -= LU[r + i * ld] * yi;
-    __syncthreads();
-  }
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) col[i] = y[i];
 }
 
 // convert A into the LU work matrix
@@ -325,6 +787,7 @@ __global__ void ir_check_kernel(Ctl* c, const double* sq, int step, int32_t* sta
   c->steps = step;
   if (bwd <= IR_TOL) {
     c->done = 1;
+    if (*status == 0) *info = step;   // refinement steps taken
   } else if (last) {
     if (atomicCAS(status, 0, (int32_t)ARMA_ERR_NOCONVERGE) == 0) *info = step;
   }
@@ -368,7 +831,7 @@ __global__ void sumsq_any_kernel(const void* x, int32_t dt, int64_t ld, int64_t 
 }
 
 struct Layout {
-  int64_t lu, piv, perm, cand_val, cand_row, cand_data, drow, ctl, gemm, y, x64, r64, sq, part, total;
+  int64_t lu, piv, perm, cand_val, cand_row, cand_data, drow, ctl, flags, gemm, y, z, x64, r64, sq, part, total;
   int64_t gemm_bytes;
   bool f64;
   bool refine;
@@ -389,6 +852,7 @@ Layout layout(int64_t n, int64_t nrhs, int32_t tier) {
   L.cand_data = take(2 * MAX_CTAS * NB * es);
   L.drow = take(2 * NB * es);
   L.ctl = take(sizeof(Ctl));
+  L.flags = take(2 * ((n + NB - 1) / NB) * ((nrhs + 63) / 64) * 4);
   const int32_t gt = L.f64 ? ARMA_TIER_F64 : tier == ARMA_TIER_BF16 ? ARMA_TIER_BF16 : ARMA_TIER_SPLIT_BF16;
   int64_t gb = gemm_tc_scratch_bytes(n, n, NB, gt);
   if (gb < 64 * n * 8) gb = 64 * n * 8;            // GEMV partials for 1-wide updates
@@ -403,12 +867,64 @@ Layout layout(int64_t n, int64_t nrhs, int32_t tier) {
   L.gemm_bytes = gb;
   L.gemm = take(gb);
   L.y = take(n * nrhs * es);
+  L.z = take(n * nrhs * es);
   L.x64 = L.refine ? take(n * nrhs * 8) : 0;
   L.r64 = L.refine ? take(n * nrhs * 8) : 0;
   L.sq = take(8 * 8);
   L.part = take(1024 * 8);
   L.total = off + 256;
   return L;
+}
+
+// the panel of `rows` rows starting at column pa.j: one cluster of up to 16
+// CTAs when it fits their shared memory, else the cooperative grid kernel
+template <typename T>
+cudaError_t launch_panel(PanelArgs<T>& pa, int64_t rows, int ctas, cudaStream_t s) {
+  static int cluster_max = -1;            // largest usable cluster size, probed once
+  if (cluster_max < 0) {
+    cluster_max = 8;
+    if (cudaFuncSetAttribute(panel_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+        cudaSuccess)
+      cluster_max = 16;
+    cudaGetLastError();
+  }
+  for (int cs = 1; cs <= cluster_max; cs *= 2) {
+    const int64_t R = (rows + cs - 1) / cs;
+    if (R > PT && cs < cluster_max) continue;       // aim for one row per thread
+    const size_t smem = (size_t)R * pa.w * sizeof(T);
+    if (smem > 160 * 1024) break;
+    if (cudaFuncSetAttribute(panel_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      break;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3((unsigned)cs);
+    cfg.blockDim = dim3(CPT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, panel_cluster_kernel<T>, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      break;
+    }
+    PanelArgs<T> pc = pa;
+    pc.rows_per_cta = R;
+    return cudaLaunchKernelEx(&cfg, panel_cluster_kernel<T>, pc);
+  }
+  cudaGetLastError();
+  const size_t smem = (size_t)pa.rows_per_cta * pa.w * sizeof(T);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* kargs[] = {&pa};
+  return cudaLaunchCooperativeKernel((const void*)panel_kernel<T>, dim3(ctas), dim3(PT), kargs, smem, s);
 }
 
 template <typename T>
@@ -444,12 +960,7 @@ cudaError_t factor(const SolveArgs& a, const Layout& L, char* base, cudaStream_t
     pa.ctl = ctl;
     pa.status = a.status_code;
     pa.info = a.status_info;
-    const size_t smem = (size_t)pa.rows_per_cta * w * sizeof(T);
-    if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    void* kargs[] = {&pa};
-    e = cudaLaunchCooperativeKernel((const void*)panel_kernel<T>, dim3(ctas), dim3(PT), kargs, smem, s);
+    cudaError_t e = launch_panel<T>(pa, rows, ctas, s);
     if (e != cudaSuccess) return e;
     if (launches) ++*launches;
     if (n > w) {
@@ -459,7 +970,7 @@ cudaError_t factor(const SolveArgs& a, const Layout& L, char* base, cudaStream_t
     }
     const int64_t rest = n - j - w;
     if (rest > 0) {
-      trsm_kernel<T><<<(unsigned)((rest + 127) / 128), 128, 0, s>>>(W, n, n, j, w);
+      trsm_kernel<T><<<(unsigned)((rest + 7) / 8), 256, 0, s>>>(W, n, n, j, w);
       if (launches) ++*launches;
       GemmArgs g;
       memset(&g, 0, sizeof g);
@@ -480,14 +991,54 @@ cudaError_t factor(const SolveArgs& a, const Layout& L, char* base, cudaStream_t
   return cudaGetLastError();
 }
 
+// y := U^-1 L^-1 y for all nrhs columns.  One cooperative launch when all
+// (block row, 64-column slice) CTAs fit on the GPU at once; otherwise one
+// launch per diagonal block and sweep: the forward sweep reduces Y in place
+// and writes the solved rows to Z, the backward sweep reduces Z in place and
+// writes the result to Y.  Either way the result is in Y.
 template <typename T>
-cudaError_t substitute(const T* W, int64_t n, T* Y, int64_t nrhs, const int* skip, cudaStream_t s, int* launches) {
-  const size_t smem = (size_t)n * sizeof(T);
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(trsv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t substitute(const T* W, int64_t n, T* Y, T* Z, int64_t nrhs, unsigned int* flags, Ctl* ctl,
+                       int32_t* status, const int* skip, cudaStream_t s, int* launches) {
+  const int64_t nb = (n + NB - 1) / NB;
+  const int64_t gy = (nrhs + 63) / 64;
+  if (gy > 65535) return cudaErrorInvalidConfiguration;
+  {
+    const size_t smem = coop_smem<T>();
+    int per_sm = 0;
+    if (cudaFuncSetAttribute(sub_coop_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+            cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sub_coop_kernel<T>, 256, smem) == cudaSuccess &&
+        nb * gy <= (int64_t)per_sm * device_sm_count()) {
+      cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)2 * nb * gy * sizeof(unsigned int), s);
+      if (e != cudaSuccess) return e;
+      void* args[] = {(void*)&W, (void*)&n, (void*)&Y, (void*)&Z, (void*)&nrhs, (void*)&flags, (void*)&ctl,
+                      (void*)&status, (void*)&skip};
+      e = cudaLaunchCooperativeKernel((const void*)sub_coop_kernel<T>, dim3((unsigned)nb, (unsigned)gy), dim3(256),
+                                      args, smem, s);
+      if (e == cudaSuccess) {
+        if (launches) ++*launches;
+        return cudaSuccess;
+      }
+    }
+    cudaGetLastError();
+  }
+  const size_t smem = sub_smem<T>();
+  cudaError_t e = cudaFuncSetAttribute(sub_step_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sub_step_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  trsv_kernel<T><<<(unsigned)nrhs, 256, smem, s>>>(W, n, n, Y, n, skip);
-  if (launches) ++*launches;
+  auto gx = [](int64_t rows) { return (unsigned)(rows > 0 ? (rows + SUB_ROWS - 1) / SUB_ROWS : 1); };
+  for (int64_t j = 0; j < n; j += NB) {
+    const int w = (int)(n - j < NB ? n - j : NB);
+    const int64_t rows = n - j - w;
+    sub_step_kernel<T, true><<<dim3(gx(rows), (unsigned)gy), 256, smem, s>>>(W, n, j, w, Y, Z, nrhs, j + w, rows, skip);
+    if (launches) ++*launches;
+  }
+  for (int64_t j = ((n - 1) / NB) * NB; j >= 0; j -= NB) {
+    const int w = (int)(n - j < NB ? n - j : NB);
+    sub_step_kernel<T, false><<<dim3(gx(j), (unsigned)gy), 256, smem, s>>>(W, n, j, w, Z, Y, nrhs, 0, j, skip);
+    if (launches) ++*launches;
+  }
   return cudaGetLastError();
 }
 
@@ -510,6 +1061,7 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
   const int sms = device_sm_count();
   int32_t* piv = reinterpret_cast<int32_t*>(base + L.piv);
   int32_t* perm = reinterpret_cast<int32_t*>(base + L.perm);
+  unsigned int* flags = reinterpret_cast<unsigned int*>(base + L.flags);
   auto grid_for = [&](int64_t total) {
     int64_t b = (total + 255) / 256, cap = (int64_t)sms * 8;
     return (unsigned)(b < 1 ? 1 : b < cap ? b : cap);
@@ -520,7 +1072,8 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
     double* Y = reinterpret_cast<double*>(base + L.y);
     perm_kernel<<<1, 32, 0, s>>>(piv, perm, n);
     gather_kernel<double><<<grid_for(n * nrhs), 256, 0, s>>>(a.B, a.ldb, a.bdt, perm, Y, n, nrhs, nullptr);
-    e = substitute<double>(reinterpret_cast<double*>(base + L.lu), n, Y, nrhs, nullptr, s, launches);
+    e = substitute<double>(reinterpret_cast<double*>(base + L.lu), n, Y, reinterpret_cast<double*>(base + L.z),
+                           nrhs, flags, ctl, a.status_code, nullptr, s, launches);
     if (e != cudaSuccess) return e;
     store_kernel<double><<<grid_for(n * nrhs), 256, 0, s>>>(Y, n, nrhs, a.X, a.ldx, a.xdt);
     if (launches) *launches += 3;
@@ -532,7 +1085,8 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
   float* Y = reinterpret_cast<float*>(base + L.y);
   perm_kernel<<<1, 32, 0, s>>>(piv, perm, n);
   gather_kernel<float><<<grid_for(n * nrhs), 256, 0, s>>>(a.B, a.ldb, a.bdt, perm, Y, n, nrhs, nullptr);
-  e = substitute<float>(W, n, Y, nrhs, nullptr, s, launches);
+  float* Z = reinterpret_cast<float*>(base + L.z);
+  e = substitute<float>(W, n, Y, Z, nrhs, flags, ctl, a.status_code, nullptr, s, launches);
   if (e != cudaSuccess) return e;
   if (launches) *launches += 2;
   if (!L.refine || !a.B) {
@@ -576,7 +1130,7 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
     ir_check_kernel<<<1, 32, 0, s>>>(ctl, sq + 2, it, a.status_code, a.status_info, it == MAX_IR);
     // d = (LU)^-1 P r in FP32; x += d
     gather_kernel<float><<<grid_for(n * nrhs), 256, 0, s>>>(R64, n, ARMA_F64, perm, Y, n, nrhs, &ctl->done);
-    e = substitute<float>(W, n, Y, nrhs, &ctl->done, s, launches);
+    e = substitute<float>(W, n, Y, Z, nrhs, flags, ctl, a.status_code, &ctl->done, s, launches);
     if (e != cudaSuccess) return e;
     ir_update_kernel<<<grid_for(n * nrhs), 256, 0, s>>>(X64, Y, n * nrhs, &ctl->done);
     if (launches) *launches += 7;

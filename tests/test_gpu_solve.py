@@ -32,7 +32,8 @@ def well_conditioned(seed, n):
     return synth.matrix(seed, 1, n, n, "f64") + n * np.eye(n) * 0.1 + np.eye(n)
 
 
-@pytest.mark.parametrize("n,nrhs", [(1, 1), (5, 3), (64, 1), (65, 7), (200, 64), (257, 33)])
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (5, 3), (64, 1), (65, 7), (200, 64), (257, 33), (300, 130),
+                                    (1000, 5)])
 @pytest.mark.parametrize("tier", ["f64", "lu32_ir64", "split_bf16"])
 def test_solve_small(torch, n, nrhs, tier):
     A = well_conditioned(n, n)
@@ -104,3 +105,27 @@ def test_solve_conditioned_benchmark_size(torch, symmetric):
     assert oracle.backward_error(A, X, B) <= 1e-12
     Xn = np.linalg.solve(A, B)
     assert oracle.rel_err(X, Xn) <= 1e-12 * 1e6
+
+
+def test_solve_panel_beyond_cluster_memory(torch):
+    """n = 5200 in FP64: the first panels hold more rows than one cluster's
+    shared memory and take the grid-barrier panel kernel, the later ones the
+    cluster kernel; both must give the same partial-pivoting factorisation."""
+    n, nrhs = 5200, 3
+    A = well_conditioned(11, n)
+    B = synth.matrix(12, 2, n, nrhs, "f64")
+    X, (st, info) = solve(torch, A, B, "f64")
+    assert st == "ok", (st, info)
+    assert oracle.backward_error(A, X, B) <= 1e-14
+    assert oracle.rel_err(X, np.linalg.solve(A, B)) <= 1e-12
+
+
+def test_refinement_steps_reported(torch):
+    """lu32_ir64 reports the refinement steps it took (info) on success."""
+    n = 4096
+    A = synth.conditioned_matrix(20250203 + 3, n, 1e6, symmetric=False)
+    B = synth.matrix(20250203 + 3, 2, n, 4, "f64")
+    X, (st, info) = solve(torch, A, B, "lu32_ir64")
+    assert st == "ok" and 1 <= info <= 10, (st, info)
+    _, (st64, info64) = solve(torch, A, B, "f64")
+    assert st64 == "ok" and info64 == 0
