@@ -28,6 +28,8 @@
 // its 1-based column in the workspace status; refinement that does not reach
 // its tolerance records ARMA_ERR_NOCONVERGE.
 #include <cooperative_groups.h>
+#include <type_traits>
+#include <utility>
 
 #include "common.cuh"
 
@@ -42,6 +44,7 @@ constexpr int MAX_IR = 10;
 constexpr double IR_TOL = 1e-14;
 constexpr unsigned int SPIN_LIMIT = 1u << 26;
 constexpr uint64_t WAIT_NS = 2000000000ull;     // 2 s bound on one wait
+constexpr int FLAG_STRIDE = 32;                 // substitution flags, one per 128 bytes
 
 struct Ctl {                    // device control block in the solve scratch
   unsigned int bar_count, bar_gen;
@@ -272,6 +275,9 @@ __global__ void __launch_bounds__(CPT) panel_cluster_kernel(const __grid_constan
   __shared__ int64_t c_row[2];
   __shared__ __align__(16) T c_data[2][NB];   // its candidate row
   __shared__ __align__(16) T c_drow[2][NB];   // row d when owned here
+  __shared__ __align__(16) T s_u[NB];     // the pivot row
+  __shared__ int64_t s_p;
+  __shared__ int s_win;
   const unsigned int nranks = cl.num_blocks();
   const unsigned int rank = cl.block_rank();
   const int64_t R = a.rows_per_cta;
@@ -316,34 +322,45 @@ __global__ void __launch_bounds__(CPT) panel_cluster_kernel(const __grid_constan
       }
     }
     cl.sync();
-    // C. every warp picks the same pivot from the CTAs' candidates
-    T v = (T)-1;
-    int64_t p = INT64_MAX;
-    int win = -1;
-    if ((unsigned int)lane < nranks) {
-      v = *cl.map_shared_rank(&c_val[ph], (unsigned int)lane);
-      p = *cl.map_shared_rank(&c_row[ph], (unsigned int)lane);
-      win = lane;
-    }
+    // C. warp 0 picks the pivot from the CTAs' candidates and copies the
+    //    pivot row into this CTA's shared memory
+    if (wid == 0) {
+      T v = (T)-1;
+      int64_t pp = INT64_MAX;
+      int wn = -1;
+      if ((unsigned int)lane < nranks) {
+        v = *cl.map_shared_rank(&c_val[ph], (unsigned int)lane);
+        pp = *cl.map_shared_rank(&c_row[ph], (unsigned int)lane);
+        wn = lane;
+      }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) argmax_step(v, p, win, off);
-    v = __shfl_sync(0xffffffffu, v, 0);
-    p = __shfl_sync(0xffffffffu, p, 0);
-    win = __shfl_sync(0xffffffffu, win, 0);
-    if (v <= (T)0) {                      // exact zero column: singular, keep going
-      p = d;
-      win = -1;
-    }
-    if (tid == 0 && rank == 0) {
-      if (win < 0 && atomicCAS(a.status, 0, (int32_t)ARMA_ERR_SINGULAR) == 0) *a.info = d + 1;
-      a.piv[d] = (int32_t)p;
-    }
-    const T* prow = win >= 0 ? cl.map_shared_rank(&c_data[ph][0], (unsigned int)win)
+      for (int off = 16; off > 0; off >>= 1) argmax_step(v, pp, wn, off);
+      v = __shfl_sync(0xffffffffu, v, 0);
+      pp = __shfl_sync(0xffffffffu, pp, 0);
+      wn = __shfl_sync(0xffffffffu, wn, 0);
+      if (v <= (T)0) {                    // exact zero column: singular, keep going
+        pp = d;
+        wn = -1;
+      }
+      const T* src = wn >= 0 ? cl.map_shared_rank(&c_data[ph][0], (unsigned int)wn)
                              : cl.map_shared_rank(&c_drow[ph][0], downer);
+      for (int q = lane; q < w; q += 32) s_u[q] = src[q];
+      if (lane == 0) {
+        s_p = pp;
+        s_win = wn;
+        if (rank == 0) {
+          if (wn < 0 && atomicCAS(a.status, 0, (int32_t)ARMA_ERR_SINGULAR) == 0) *a.info = d + 1;
+          a.piv[d] = (int32_t)pp;
+        }
+      }
+    }
+    __syncthreads();
+    const int64_t p = s_p;
+    const int win = s_win;
     T u[16];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) u[k] = seg * 16 + k < w ? prow[seg * 16 + k] : (T)0;
-    const T pv = prow[c];
+    for (int k = 0; k < 16; ++k) u[k] = seg * 16 + k < w ? s_u[seg * 16 + k] : (T)0;
+    const T pv = s_u[c];
     // D. swap rows d and p (each thread its own columns), scale column c
     if (p != d) {
       const int64_t rd = d - r0, rp = p - r0;
@@ -381,6 +398,220 @@ __global__ void __launch_bounds__(CPT) panel_cluster_kernel(const __grid_constan
     const int64_t c = t / nown, r = t - c * nown;
     a.A[(r0 + r) + (a.j + c) * a.ld] = sm[c * R + r];
   }
+}
+
+// The cluster panel with the panel held in registers: thread (slot, seg)
+// keeps rows slot and slot + 128 of its CTA, panel columns 16 seg ..
+// 16 seg + 15, so the rank-1 update touches no shared memory.  The column
+// loop is unrolled by 16 so that register indices are static.  Pivot
+// candidates are compared as monotone integer keys of |value| (warp
+// max/min reductions); ties go to the smallest row.  Rows per CTA <= 256
+// and >= w (the diagonal block lies in CTA 0).
+constexpr int RPT = 2;
+
+// row i of a thread's register rows, as selects (never an indexed access,
+// which would move the rows to local memory)
+template <typename T>
+__device__ __forceinline__ T pick(const T (&x)[RPT][16], int i, int kk) {
+  T v = x[0][kk];
+#pragma unroll
+  for (int q = 1; q < RPT; ++q) v = i == q ? x[q][kk] : v;
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ void blend(T (&x)[RPT][16], int i, int kk, T v) {
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) x[q][kk] = i == q ? v : x[q][kk];
+}
+
+// f(integral_constant<int, I>) for each I of the sequence, in order
+template <typename F, int... Is>
+__device__ __forceinline__ void static_for(F& f, std::integer_sequence<int, Is...>) {
+  (f(std::integral_constant<int, Is>{}), ...);
+}
+
+__device__ __forceinline__ uint32_t abs_key(float v) { return (__float_as_uint(v) & 0x7fffffffu) + 1u; }
+__device__ __forceinline__ uint64_t abs_key(double v) {
+  return ((uint64_t)__double_as_longlong(v) & 0x7fffffffffffffffull) + 1ull;
+}
+
+// warp-wide largest key, and the smallest row holding it
+__device__ __forceinline__ void warp_argmax(uint32_t& key, uint32_t& row) {
+  const uint32_t m = __reduce_max_sync(0xffffffffu, key);
+  row = __reduce_min_sync(0xffffffffu, key == m ? row : 0xffffffffu);
+  key = m;
+}
+__device__ __forceinline__ void warp_argmax(uint64_t& key, uint32_t& row) {
+  const uint32_t hi = __reduce_max_sync(0xffffffffu, (uint32_t)(key >> 32));
+  const uint32_t lo = __reduce_max_sync(0xffffffffu, (uint32_t)(key >> 32) == hi ? (uint32_t)key : 0u);
+  const uint64_t m = ((uint64_t)hi << 32) | lo;
+  row = __reduce_min_sync(0xffffffffu, key == m ? row : 0xffffffffu);
+  key = m;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CPT, 1) panel_reg_kernel(const __grid_constant__ PanelArgs<T> a) {
+  using K = typename std::conditional<sizeof(T) == 8, uint64_t, uint32_t>::type;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ K wkey[4];                   // per warp of the column's segment
+  __shared__ uint32_t wrow[4];
+  __shared__ K c_key[2];                  // this CTA's candidate, per phase
+  __shared__ uint32_t c_row[2];
+  __shared__ __align__(16) T c_data[2][NB];   // its candidate row
+  __shared__ __align__(16) T c_drow[2][NB];   // row d (CTA 0)
+  __shared__ T lbuf[CSLOTS * RPT];        // multipliers of column c
+  __shared__ __align__(16) T s_u[NB];     // the pivot row
+  __shared__ int64_t s_p;
+  __shared__ int s_win;
+  const unsigned int nranks = cl.num_blocks();
+  const unsigned int rank = cl.block_rank();
+  const int R = (int)a.rows_per_cta;
+  const int64_t r0 = a.j + (int64_t)rank * R;
+  const int64_t r1 = min(r0 + R, a.n);
+  const int nown = r1 > r0 ? (int)(r1 - r0) : 0;
+  const int w = a.w;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int slot = tid & (CSLOTS - 1), seg = tid / CSLOTS;
+  T x[RPT][16];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i)
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      const int rr = slot + CSLOTS * i, col = 16 * seg + kk;
+      x[i][kk] = (rr < nown && col < w) ? a.A[(r0 + rr) + (a.j + col) * a.ld] : (T)0;
+    }
+  for (int cb = 0; cb < 4 && 16 * cb < w; ++cb) {
+    auto column = [&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      const int c = 16 * cb + k;
+      if (c < w) {
+      const int64_t d = a.j + c;
+      const int ph = k & 1;
+      const int dl = (int)(d - r0);       // row d in this CTA's numbering
+      // A. per-warp candidates of column c (the warps of segment cb)
+      if (seg == cb) {
+        K key = 0;
+        uint32_t row = 0xffffffffu;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          const int rr = slot + CSLOTS * i;
+          if (rr < nown && r0 + rr >= d) {
+            const K kv = abs_key(x[i][k]);
+            if (kv > key) { key = kv; row = (uint32_t)(r0 + rr); }
+          }
+        }
+        warp_argmax(key, row);
+        if (lane == 0) { wkey[wid & 3] = key; wrow[wid & 3] = row; }
+      }
+      if (rank == 0 && dl >= 0 && dl < nown && (dl & (CSLOTS - 1)) == slot) {
+        const int i = dl / CSLOTS;
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk)
+          if (16 * seg + kk < w) c_drow[ph][16 * seg + kk] = pick(x, i, kk);
+      }
+      __syncthreads();
+      // B. the CTA's candidate; its owner threads publish the row
+      K ck = wkey[0];
+      uint32_t cr = wrow[0];
+#pragma unroll
+      for (int q = 1; q < 4; ++q)
+        if (wkey[q] > ck || (wkey[q] == ck && wrow[q] < cr)) { ck = wkey[q]; cr = wrow[q]; }
+      if (tid == 0) { c_key[ph] = ck; c_row[ph] = cr; }
+      if (ck != 0) {
+        const int cl_ = (int)((int64_t)cr - r0);
+        if ((cl_ & (CSLOTS - 1)) == slot) {
+          const int i = cl_ / CSLOTS;
+#pragma unroll
+          for (int kk = 0; kk < 16; ++kk)
+            if (16 * seg + kk < w) c_data[ph][16 * seg + kk] = pick(x, i, kk);
+        }
+      }
+      cl.sync();
+      // C. warp 0 selects the pivot among the CTAs' candidates and copies
+      //    the pivot row into this CTA's shared memory (one remote read per
+      //    value and CTA; every thread reading it remotely would queue the
+      //    whole cluster on the winner's shared memory)
+      if (wid == 0) {
+        K gk = 0;
+        uint32_t gr = 0xffffffffu, mine = 0xffffffffu;
+        if ((unsigned int)lane < nranks) {
+          gk = *cl.map_shared_rank(&c_key[ph], (unsigned int)lane);
+          gr = mine = *cl.map_shared_rank(&c_row[ph], (unsigned int)lane);
+        }
+        warp_argmax(gk, gr);
+        const bool sing = gk <= (K)1;     // |value| = 0 everywhere below d
+        const int wn = sing ? -1 : __ffs(__ballot_sync(0xffffffffu, mine == gr)) - 1;
+        const T* src = wn >= 0 ? cl.map_shared_rank(&c_data[ph][0], (unsigned int)wn)
+                               : cl.map_shared_rank(&c_drow[ph][0], 0u);
+        for (int q = lane; q < w; q += 32) s_u[q] = src[q];
+        if (lane == 0) {
+          s_p = sing ? d : (int64_t)gr;
+          s_win = wn;
+          if (rank == 0) {
+            if (sing && atomicCAS(a.status, 0, (int32_t)ARMA_ERR_SINGULAR) == 0) *a.info = d + 1;
+            a.piv[d] = (int32_t)(sing ? d : (int64_t)gr);
+          }
+        }
+      }
+      __syncthreads();
+      const int64_t p = s_p;
+      const bool singular = s_win < 0;
+      T u[16];
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) u[kk] = 16 * seg + kk < w ? s_u[16 * seg + kk] : (T)0;
+      const T pv = s_u[c];
+      // D. swap rows d and p
+      if (p != d) {
+        if (dl >= 0 && dl < nown && (dl & (CSLOTS - 1)) == slot) {
+          const int i = dl / CSLOTS;
+#pragma unroll
+          for (int kk = 0; kk < 16; ++kk) blend(x, i, kk, u[kk]);
+        }
+        const int pl = (int)(p - r0);
+        if (pl >= 0 && pl < nown && (pl & (CSLOTS - 1)) == slot) {
+          const T* dr = cl.map_shared_rank(&c_drow[ph][0], 0u);
+          const int i = pl / CSLOTS;
+#pragma unroll
+          for (int kk = 0; kk < 16; ++kk)
+            if (16 * seg + kk < w) blend(x, i, kk, dr[16 * seg + kk]);
+        }
+      }
+      // E. multipliers of column c, then the rank-1 update
+      if (seg == cb) {
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          const int rr = slot + CSLOTS * i;
+          T l = (T)0;
+          if (!singular && rr < nown && r0 + rr > d) {
+            l = x[i][k] / pv;
+            x[i][k] = l;
+          }
+          lbuf[rr] = l;
+        }
+      }
+      __syncthreads();
+      if (!singular && 16 * seg + 15 > c) {
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          const T l = lbuf[slot + CSLOTS * i];
+#pragma unroll
+          for (int kk = 0; kk < 16; ++kk)
+            if (16 * seg + kk > c) x[i][kk] -= l * u[kk];
+        }
+      }
+      }
+    };
+    static_for(column, std::make_integer_sequence<int, 16>{});
+  }
+  cl.sync();                              // peers may still read this CTA's buffers
+#pragma unroll
+  for (int i = 0; i < RPT; ++i)
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      const int rr = slot + CSLOTS * i, col = 16 * seg + kk;
+      if (rr < nown && col < w) a.A[(r0 + rr) + (a.j + col) * a.ld] = x[i][kk];
+    }
 }
 
 // the panel's row swaps applied to columns outside [j, j + w)
@@ -543,43 +774,92 @@ __device__ __forceinline__ void block_solve(T (&y)[16], const T* D, const T* din
   }
 }
 
+// inverses of the diagonal blocks: Linv_i = L_ii^-1 (unit lower) and
+// Uinv_i = U_ii^-1, each 64 x 64 column-major (zero-padded past the last
+// row), by the block solve applied to the identity.  A zero pivot gives a
+// zero row, as in the substitution.
 template <typename T>
-__host__ __device__ inline size_t coop_smem(void) {
-  return sizeof(T) * (2 * (size_t)NB * NB + (size_t)64 * (NB + 1) + NB);
+__global__ void __launch_bounds__(256) inv_diag_kernel(const T* __restrict__ LU, int64_t n, T* Linv, T* Uinv) {
+  __shared__ __align__(16) T D[NB * NB];
+  __shared__ T dinv[NB];
+  const int64_t j = (int64_t)blockIdx.x * NB;
+  const int w = (int)(n - j < NB ? n - j : NB);
+  const int tid = threadIdx.x, lane = tid & 31, col = tid >> 2, q = tid & 3;
+  load_block(D, LU + j + j * n, n, w, w);
+  __syncthreads();
+  if (tid < NB) {
+    const T p = D[tid * NB + tid];
+    dinv[tid] = (tid < w && p != (T)0) ? (T)1 / p : (T)0;
+  }
+  __syncthreads();
+  T* out[2] = {Linv + (int64_t)blockIdx.x * NB * NB, Uinv + (int64_t)blockIdx.x * NB * NB};
+#pragma unroll
+  for (int which = 0; which < 2; ++which) {
+    T y[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) y[k] = (q * 16 + k == col && col < w) ? (T)1 : (T)0;
+    if (which == 0) block_solve<T, true>(y, D, dinv, w, q, lane);
+    else block_solve<T, false>(y, D, dinv, w, q, lane);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) out[which][col * NB + q * 16 + k] = y[k];
+  }
 }
 
-// The whole substitution y := U^-1 L^-1 y in one cooperative launch: CTA
-// (i, c) owns block row i of a 64-column slice c.  Forward: it subtracts
-// L_ik z_k for k < i as each z_k is published (flag per block, release /
-// acquire), solves with L_ii and publishes z_i to Z.  Backward: it subtracts
-// U_ik y_k for k > i as each y_k is published to Y, solves with U_ii and
-// publishes y_i.  Every wait is bounded in time; a wait that runs out marks
-// the control block and the status, and every other wait then gives up.
+constexpr int CW = 16;          // right-hand sides per CTA of the cooperative substitution
+constexpr int XS = CW + 1;      // row stride of its right-hand-side tile in shared memory
+
 template <typename T>
-__global__ void __launch_bounds__(256) sub_coop_kernel(const T* __restrict__ LU, int64_t n, T* Y, T* Z,
+__host__ __device__ inline size_t coop_smem(void) {
+  return sizeof(T) * (2 * (size_t)NB * NB + (size_t)NB * XS);
+}
+
+__device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
+  const double2 t0 = reinterpret_cast<const double2*>(p)[0], t1 = reinterpret_cast<const double2*>(p)[1];
+  o[0] = t0.x; o[1] = t0.y; o[2] = t1.x; o[3] = t1.y;
+}
+
+// The whole substitution y := U^-1 L^-1 y in one cooperative launch.  CTA
+// (i, c) owns block row i (64 rows) of a 16-column slice c; thread (col, rq)
+// holds rows 4 rq .. 4 rq + 3 of column col.  Forward: for k < i it
+// subtracts L_ik z_k as soon as z_k is published (flag per block, release /
+// acquire), applies the inverted diagonal block, z_i = Linv_i y_i, and
+// publishes z_i to Z.  Backward: likewise with U_ik y_k for k > i and Uinv_i,
+// publishing to Y.  The next off-diagonal block is fetched into registers
+// while the current one is applied.  Every wait is bounded in time; a wait
+// that runs out marks the control block and the status, and every other wait
+// then gives up.
+template <typename T>
+__global__ void __launch_bounds__(256) sub_coop_kernel(const T* __restrict__ LU, const T* __restrict__ Linv,
+                                                       const T* __restrict__ Uinv, int64_t n, T* Y, T* Z,
                                                        int64_t nrhs, unsigned int* flags, Ctl* ctl,
                                                        int32_t* status, const int* skip) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* D = reinterpret_cast<T*>(smraw);
-  T* Ms = D + NB * NB;
-  T* Xs = Ms + NB * NB;
-  T* dinv = Xs + 64 * (NB + 1);
+  T* Ms = reinterpret_cast<T*>(smraw);   // off-diagonal block, Ms[m * NB + r]
+  T* Ds = Ms + NB * NB;                  // inverted diagonal block, same layout
+  T* Xs = Ds + NB * NB;                  // right-hand-side tile, Xs[m * XS + c]
   __shared__ int s_ok;
   const int nb = gridDim.x, bi = blockIdx.x;
   const int64_t j = (int64_t)bi * NB;
   const int w = (int)(n - j < NB ? n - j : NB);
-  const int64_t c0 = (int64_t)blockIdx.y * 64;
-  const int ncols = (int)(nrhs - c0 < 64 ? nrhs - c0 : 64);
-  unsigned int* fwd = flags;
-  unsigned int* bwd = flags + (size_t)nb * gridDim.y;
-  const int tid = threadIdx.x, lane = tid & 31, col = tid >> 2, q = tid & 3;
+  const int64_t c0 = (int64_t)blockIdx.y * CW;
+  const int ncols = (int)(nrhs - c0 < CW ? nrhs - c0 : CW);
+  unsigned int* fwd = flags;                   // one 128-byte line per flag
+  unsigned int* bwd = flags + (size_t)nb * gridDim.y * FLAG_STRIDE;
+  const int tid = threadIdx.x, col = tid & (CW - 1), rq = tid / CW;
+  auto flag = [&](unsigned int* f, int k) { return f + ((size_t)k * gridDim.y + blockIdx.y) * FLAG_STRIDE; };
+  auto rows_of = [&](int k) { return (int)(n - (int64_t)k * NB < NB ? n - (int64_t)k * NB : NB); };
 
   auto wait = [&](const unsigned int* f) -> bool {
     if (tid == 0) {
       int ok = 1;
       const uint64_t t0 = global_ns();
       for (unsigned int it = 0; ld_acquire(f) == 0u; ++it) {
+        __nanosleep(64);
         if (*(volatile int*)&ctl->err || it > SPIN_LIMIT || ((it & 255u) == 0u && global_ns() - t0 > WAIT_NS)) {
           atomicExch(&ctl->err, 1);
           atomicCAS(status, 0, (int32_t)ARMA_ERR_CUDA);
@@ -592,14 +872,73 @@ __global__ void __launch_bounds__(256) sub_coop_kernel(const T* __restrict__ LU,
     __syncthreads();
     return s_ok != 0;
   };
-  auto publish = [&](T* dst, T (&y)[16], unsigned int* f) {
+  // Xs := rows [0, rows) of src's 16-column slice (through L2), zero elsewhere
+  auto load_x = [&](const T* src, int rows) {
+    T v[4];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) Xs[col * (NB + 1) + q * 16 + k] = y[k];
-    __syncthreads();
+    for (int p = 0; p < 4; ++p) {
+      const int t = tid + 256 * p, m = t & (NB - 1), c = t >> 6;
+      v[p] = (m < rows && c < ncols) ? __ldcg(src + m + (int64_t)c * n) : (T)0;
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int t = tid + 256 * p, m = t & (NB - 1), c = t >> 6;
+      Xs[m * XS + c] = v[p];
+    }
+  };
+  T mv[16];
+  auto fetch_m = [&](const T* src, int rows, int cols) {
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       const int t = tid + 256 * k, r = t & (NB - 1), c = t >> 6;
-      if (r < w && c < ncols) dst[r + (int64_t)c * n] = Xs[c * (NB + 1) + r];
+      mv[k] = (r < rows && c < cols) ? src[r + (int64_t)c * n] : (T)0;
+    }
+  };
+  auto store_m = [&]() {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) Ms[tid + 256 * k] = mv[k];
+  };
+  auto load_d = [&](const T* src) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) Ds[tid + 256 * k] = src[tid + 256 * k];
+  };
+  T y[4];
+  // y -= Ms Xs over m < kw
+  auto sub = [&](int kw) {
+    for (int m = 0; m < kw; ++m) {
+      const T x = Xs[m * XS + col];
+      T a4[4];
+      ld4(Ms + m * NB + 4 * rq, a4);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) y[e] -= a4[e] * x;
+    }
+  };
+  // y := Ds y (the whole tile goes through Xs)
+  auto apply = [&]() {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) Xs[(4 * rq + e) * XS + col] = y[e];
+    __syncthreads();
+    T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll 8
+    for (int m = 0; m < NB; ++m) {
+      const T x = Xs[m * XS + col];
+      T a4[4];
+      ld4(Ds + m * NB + 4 * rq, a4);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[e] += a4[e] * x;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) y[e] = acc[e];
+    __syncthreads();
+  };
+  auto publish = [&](T* dst, unsigned int* f) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) Xs[(4 * rq + e) * XS + col] = y[e];
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int t = tid + 256 * p, r = t & (NB - 1), c = t >> 6;
+      if (r < w && c < ncols) dst[r + (int64_t)c * n] = Xs[r * XS + c];
     }
     __syncthreads();
     if (tid == 0) {
@@ -608,40 +947,41 @@ __global__ void __launch_bounds__(256) sub_coop_kernel(const T* __restrict__ LU,
     }
   };
 
-  load_block(D, LU + j + j * n, n, w, w);
-  load_cols_cg(Xs, Y + j + c0 * n, n, w, ncols);
+  load_x(Y + j + c0 * n, w);
+  load_d(Linv + (int64_t)bi * NB * NB);
   __syncthreads();
-  if (tid < NB) {
-    const T p = D[tid * NB + tid];
-    dinv[tid] = (tid < w && p != (T)0) ? (T)1 / p : (T)0;
-  }
-  T y[16];
 #pragma unroll
-  for (int k = 0; k < 16; ++k) y[k] = Xs[col * (NB + 1) + q * 16 + k];
+  for (int e = 0; e < 4; ++e) y[e] = Xs[(4 * rq + e) * XS + col];
   __syncthreads();
 
+  if (bi > 0) fetch_m(LU + j, w, NB);          // L_i0
   for (int k = 0; k < bi; ++k) {                // forward: L_ik, k < i
-    load_block(Ms, LU + j + (int64_t)k * NB * n, n, w, NB);
-    if (!wait(fwd + (size_t)k * gridDim.y + blockIdx.y)) return;
-    load_cols_cg(Xs, Z + (int64_t)k * NB + c0 * n, n, NB, ncols);
+    store_m();
+    if (k + 1 < bi) fetch_m(LU + j + (int64_t)(k + 1) * NB * n, w, NB);
+    if (!wait(flag(fwd, k))) return;
+    load_x(Z + (int64_t)k * NB + c0 * n, NB);
     __syncthreads();
-    block_update(y, Ms, Xs, col, q, NB);
+    sub(NB);
     __syncthreads();
   }
-  block_solve<T, true>(y, D, dinv, w, q, lane);
-  publish(Z + j + c0 * n, y, fwd + (size_t)bi * gridDim.y + blockIdx.y);
+  apply();
+  publish(Z + j + c0 * n, flag(fwd, bi));
 
+  load_d(Uinv + (int64_t)bi * NB * NB);
+  if (bi < nb - 1) fetch_m(LU + j + (int64_t)(nb - 1) * NB * n, w, rows_of(nb - 1));
   for (int k = nb - 1; k > bi; --k) {           // backward: U_ik, k > i
-    const int wk = (int)(n - (int64_t)k * NB < NB ? n - (int64_t)k * NB : NB);
-    load_block(Ms, LU + j + (int64_t)k * NB * n, n, w, wk);
-    if (!wait(bwd + (size_t)k * gridDim.y + blockIdx.y)) return;
-    load_cols_cg(Xs, Y + (int64_t)k * NB + c0 * n, n, wk, ncols);
+    const int wk = rows_of(k);
+    store_m();
+    if (k - 1 > bi) fetch_m(LU + j + (int64_t)(k - 1) * NB * n, w, rows_of(k - 1));
+    if (!wait(flag(bwd, k))) return;
+    load_x(Y + (int64_t)k * NB + c0 * n, wk);
     __syncthreads();
-    block_update(y, Ms, Xs, col, q, wk);
+    sub(wk);
     __syncthreads();
   }
-  block_solve<T, false>(y, D, dinv, w, q, lane);
-  publish(Y + j + c0 * n, y, bwd + (size_t)bi * gridDim.y + blockIdx.y);
+  __syncthreads();
+  apply();
+  publish(Y + j + c0 * n, flag(bwd, bi));
 }
 
 // One step of the blocked substitution for diagonal block j (w <= 64 rows)
@@ -831,7 +1171,8 @@ __global__ void sumsq_any_kernel(const void* x, int32_t dt, int64_t ld, int64_t 
 }
 
 struct Layout {
-  int64_t lu, piv, perm, cand_val, cand_row, cand_data, drow, ctl, flags, gemm, y, z, x64, r64, sq, part, total;
+  int64_t lu, piv, perm, cand_val, cand_row, cand_data, drow, ctl, flags, dinv, gemm, y, z, x64, r64, sq, part,
+      total;
   int64_t gemm_bytes;
   bool f64;
   bool refine;
@@ -852,7 +1193,8 @@ Layout layout(int64_t n, int64_t nrhs, int32_t tier) {
   L.cand_data = take(2 * MAX_CTAS * NB * es);
   L.drow = take(2 * NB * es);
   L.ctl = take(sizeof(Ctl));
-  L.flags = take(2 * ((n + NB - 1) / NB) * ((nrhs + 63) / 64) * 4);
+  L.flags = take(2 * ((n + NB - 1) / NB) * ((nrhs + CW - 1) / CW) * 4 * FLAG_STRIDE);
+  L.dinv = take(2 * ((n + NB - 1) / NB) * NB * NB * es);
   const int32_t gt = L.f64 ? ARMA_TIER_F64 : tier == ARMA_TIER_BF16 ? ARMA_TIER_BF16 : ARMA_TIER_SPLIT_BF16;
   int64_t gb = gemm_tc_scratch_bytes(n, n, NB, gt);
   if (gb < 64 * n * 8) gb = 64 * n * 8;            // GEMV partials for 1-wide updates
@@ -888,6 +1230,42 @@ cudaError_t launch_panel(PanelArgs<T>& pa, int64_t rows, int ctas, cudaStream_t 
       cluster_max = 16;
     cudaGetLastError();
   }
+  auto cluster_cfg = [&](cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int cs, size_t smem) {
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3((unsigned)cs);
+    cfg.blockDim = dim3(CPT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  };
+  // registers: the smallest cluster with <= 128 * RPT rows per CTA
+  for (int cs = 1; cs <= cluster_max; cs *= 2) {
+    const int64_t R = (rows + cs - 1) / cs;
+    if (R > CSLOTS * RPT) continue;
+    if (R < pa.w) break;
+    if (cs > 8 && cudaFuncSetAttribute(panel_reg_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                      cudaSuccess) {
+      cudaGetLastError();
+      break;
+    }
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    cluster_cfg(cfg, attr, cs, 0);
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, panel_reg_kernel<T>, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      break;
+    }
+    PanelArgs<T> pc = pa;
+    pc.rows_per_cta = R;
+    return cudaLaunchKernelEx(&cfg, panel_reg_kernel<T>, pc);
+  }
+  // shared memory
   for (int cs = 1; cs <= cluster_max; cs *= 2) {
     const int64_t R = (rows + cs - 1) / cs;
     if (R > PT && cs < cluster_max) continue;       // aim for one row per thread
@@ -897,18 +1275,8 @@ cudaError_t launch_panel(PanelArgs<T>& pa, int64_t rows, int ctas, cudaStream_t 
         cudaSuccess)
       break;
     cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof cfg);
-    cfg.gridDim = dim3((unsigned)cs);
-    cfg.blockDim = dim3(CPT);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cluster_cfg(cfg, attr, cs, smem);
     int nclusters = 0;
     if (cudaOccupancyMaxActiveClusters(&nclusters, panel_cluster_kernel<T>, &cfg) != cudaSuccess || nclusters < 1) {
       cudaGetLastError();
@@ -997,23 +1365,26 @@ cudaError_t factor(const SolveArgs& a, const Layout& L, char* base, cudaStream_t
 // and writes the solved rows to Z, the backward sweep reduces Z in place and
 // writes the result to Y.  Either way the result is in Y.
 template <typename T>
-cudaError_t substitute(const T* W, int64_t n, T* Y, T* Z, int64_t nrhs, unsigned int* flags, Ctl* ctl,
-                       int32_t* status, const int* skip, cudaStream_t s, int* launches) {
+cudaError_t substitute(const T* W, const T* Linv, const T* Uinv, int64_t n, T* Y, T* Z, int64_t nrhs,
+                       unsigned int* flags, Ctl* ctl, int32_t* status, const int* skip, cudaStream_t s,
+                       int* launches) {
   const int64_t nb = (n + NB - 1) / NB;
   const int64_t gy = (nrhs + 63) / 64;
   if (gy > 65535) return cudaErrorInvalidConfiguration;
   {
+    const int64_t gc = (nrhs + CW - 1) / CW;
     const size_t smem = coop_smem<T>();
     int per_sm = 0;
-    if (cudaFuncSetAttribute(sub_coop_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+    if (gc <= 65535 &&
+        cudaFuncSetAttribute(sub_coop_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
             cudaSuccess &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sub_coop_kernel<T>, 256, smem) == cudaSuccess &&
-        nb * gy <= (int64_t)per_sm * device_sm_count()) {
-      cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)2 * nb * gy * sizeof(unsigned int), s);
+        nb * gc <= (int64_t)per_sm * device_sm_count()) {
+      cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)2 * nb * gc * FLAG_STRIDE * sizeof(unsigned int), s);
       if (e != cudaSuccess) return e;
-      void* args[] = {(void*)&W, (void*)&n, (void*)&Y, (void*)&Z, (void*)&nrhs, (void*)&flags, (void*)&ctl,
-                      (void*)&status, (void*)&skip};
-      e = cudaLaunchCooperativeKernel((const void*)sub_coop_kernel<T>, dim3((unsigned)nb, (unsigned)gy), dim3(256),
+      void* args[] = {(void*)&W, (void*)&Linv, (void*)&Uinv, (void*)&n, (void*)&Y, (void*)&Z, (void*)&nrhs,
+                      (void*)&flags, (void*)&ctl, (void*)&status, (void*)&skip};
+      e = cudaLaunchCooperativeKernel((const void*)sub_coop_kernel<T>, dim3((unsigned)nb, (unsigned)gc), dim3(256),
                                       args, smem, s);
       if (e == cudaSuccess) {
         if (launches) ++*launches;
@@ -1062,6 +1433,7 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
   int32_t* piv = reinterpret_cast<int32_t*>(base + L.piv);
   int32_t* perm = reinterpret_cast<int32_t*>(base + L.perm);
   unsigned int* flags = reinterpret_cast<unsigned int*>(base + L.flags);
+  const int64_t nb = (n + NB - 1) / NB;
   auto grid_for = [&](int64_t total) {
     int64_t b = (total + 255) / 256, cap = (int64_t)sms * 8;
     return (unsigned)(b < 1 ? 1 : b < cap ? b : cap);
@@ -1069,24 +1441,32 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
   if (L.f64) {
     e = factor<double>(a, L, base, s, launches);
     if (e != cudaSuccess) return e;
+    const double* W = reinterpret_cast<const double*>(base + L.lu);
+    double* Linv = reinterpret_cast<double*>(base + L.dinv);
+    double* Uinv = Linv + nb * NB * NB;
+    inv_diag_kernel<double><<<(unsigned)nb, 256, 0, s>>>(W, n, Linv, Uinv);
     double* Y = reinterpret_cast<double*>(base + L.y);
     perm_kernel<<<1, 32, 0, s>>>(piv, perm, n);
     gather_kernel<double><<<grid_for(n * nrhs), 256, 0, s>>>(a.B, a.ldb, a.bdt, perm, Y, n, nrhs, nullptr);
-    e = substitute<double>(reinterpret_cast<double*>(base + L.lu), n, Y, reinterpret_cast<double*>(base + L.z),
-                           nrhs, flags, ctl, a.status_code, nullptr, s, launches);
+    e = substitute<double>(W, Linv, Uinv, n, Y, reinterpret_cast<double*>(base + L.z), nrhs, flags, ctl,
+                           a.status_code, nullptr, s, launches);
     if (e != cudaSuccess) return e;
     store_kernel<double><<<grid_for(n * nrhs), 256, 0, s>>>(Y, n, nrhs, a.X, a.ldx, a.xdt);
-    if (launches) *launches += 3;
+    if (launches) *launches += 4;
     return cudaGetLastError();
   }
   e = factor<float>(a, L, base, s, launches);
   if (e != cudaSuccess) return e;
   const float* W = reinterpret_cast<const float*>(base + L.lu);
+  float* Linv = reinterpret_cast<float*>(base + L.dinv);
+  float* Uinv = Linv + nb * NB * NB;
+  inv_diag_kernel<float><<<(unsigned)nb, 256, 0, s>>>(W, n, Linv, Uinv);
+  if (launches) ++*launches;
   float* Y = reinterpret_cast<float*>(base + L.y);
   perm_kernel<<<1, 32, 0, s>>>(piv, perm, n);
   gather_kernel<float><<<grid_for(n * nrhs), 256, 0, s>>>(a.B, a.ldb, a.bdt, perm, Y, n, nrhs, nullptr);
   float* Z = reinterpret_cast<float*>(base + L.z);
-  e = substitute<float>(W, n, Y, Z, nrhs, flags, ctl, a.status_code, nullptr, s, launches);
+  e = substitute<float>(W, Linv, Uinv, n, Y, Z, nrhs, flags, ctl, a.status_code, nullptr, s, launches);
   if (e != cudaSuccess) return e;
   if (launches) *launches += 2;
   if (!L.refine || !a.B) {
@@ -1130,7 +1510,7 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
     ir_check_kernel<<<1, 32, 0, s>>>(ctl, sq + 2, it, a.status_code, a.status_info, it == MAX_IR);
     // d = (LU)^-1 P r in FP32; x += d
     gather_kernel<float><<<grid_for(n * nrhs), 256, 0, s>>>(R64, n, ARMA_F64, perm, Y, n, nrhs, &ctl->done);
-    e = substitute<float>(W, n, Y, Z, nrhs, flags, ctl, a.status_code, &ctl->done, s, launches);
+    e = substitute<float>(W, Linv, Uinv, n, Y, Z, nrhs, flags, ctl, a.status_code, &ctl->done, s, launches);
     if (e != cudaSuccess) return e;
     ir_update_kernel<<<grid_for(n * nrhs), 256, 0, s>>>(X64, Y, n * nrhs, &ctl->done);
     if (launches) *launches += 7;

@@ -129,3 +129,16 @@ def test_refinement_steps_reported(torch):
     assert st == "ok" and 1 <= info <= 10, (st, info)
     _, (st64, info64) = solve(torch, A, B, "f64")
     assert st64 == "ok" and info64 == 0
+
+
+@pytest.mark.parametrize("tier", ["f64", "lu32_ir64"])
+def test_solve_many_right_hand_sides(torch, tier):
+    """20000 right-hand sides: more (block row, 16-column slice) CTAs than the
+    GPU holds at once, so the substitution takes its per-block launches."""
+    n, nrhs = 256, 20000
+    A = well_conditioned(13, n)
+    B = synth.matrix(14, 2, n, nrhs, "f64")
+    X, (st, info) = solve(torch, A, B, tier)
+    assert st == "ok", (st, info)
+    assert oracle.rel_err(X, oracle.solve_literal(A, B)) <= 1e-12
+    assert oracle.backward_error(A, X, B) <= 1e-14
