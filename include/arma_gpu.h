@@ -173,6 +173,11 @@ void arma_gpu_plan_free(arma_plan* plan);
 
 const char* arma_gpu_status_string(arma_status status);
 
+/* Name and text of the last CUDA runtime error behind an ARMA_ERR_CUDA
+ * returned to the calling thread ("" if none).  The string is owned by the
+ * library and stays valid until the thread's next failing call. */
+const char* arma_gpu_last_cuda_error(void);
+
 /* ---- Cost model.  The paper chooses an evaluation by fixed rules
  * (compile-time patterns, Sec. II; the greedy chain rule, Sec. II chain
  * paragraph).  Here candidate plans of one expression (the flag variants

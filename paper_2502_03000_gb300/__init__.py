@@ -43,10 +43,11 @@ STATUS = {0: "ok", 1: "invalid", 2: "shape", 3: "dtype", 4: "align", 5: "workspa
 
 
 class ArmaError(RuntimeError):
-    def __init__(self, code: int, where: str):
+    def __init__(self, code: int, where: str, detail: str = ""):
         self.code = code
         self.status = STATUS.get(code, str(code))
-        super().__init__(f"{where}: {self.status} ({code})")
+        self.detail = detail
+        super().__init__(f"{where}: {self.status} ({code})" + (f": {detail}" if detail else ""))
 
 
 class Node(ctypes.Structure):
@@ -64,7 +65,8 @@ class Expr(ctypes.Structure):
 
 EXPORTS = ["arma_gpu_plan", "arma_gpu_plan_workspace", "arma_gpu_output_info", "arma_gpu_eval",
            "arma_gpu_eval_status", "arma_gpu_plan_info", "arma_gpu_plan_free",
-           "arma_gpu_status_string", "arma_gpu_chain_order", "arma_gpu_eval_fused_static",
+           "arma_gpu_status_string", "arma_gpu_last_cuda_error", "arma_gpu_chain_order",
+           "arma_gpu_eval_fused_static",
            "arma_gpu_plan_batched", "arma_gpu_batched_table_bytes", "arma_gpu_batched_table_fill",
            "arma_gpu_eval_batched", "arma_gpu_plan_features", "arma_gpu_plan_heuristic_cost",
            "arma_gpu_mlp_param_count", "arma_gpu_mlp_workspace", "arma_gpu_mlp_forward", "arma_gpu_mlp_grad",
@@ -89,6 +91,8 @@ def lib() -> ctypes.CDLL:
     L.arma_gpu_plan_free.restype = None
     L.arma_gpu_status_string.argtypes = [ctypes.c_int]
     L.arma_gpu_status_string.restype = ctypes.c_char_p
+    L.arma_gpu_last_cuda_error.argtypes = []
+    L.arma_gpu_last_cuda_error.restype = ctypes.c_char_p
     L.arma_gpu_chain_order.argtypes = [i32, ctypes.POINTER(i64), i32, ctypes.POINTER(i32),
                                        ctypes.POINTER(ctypes.c_uint64)]
     L.arma_gpu_eval_fused_static.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
@@ -111,7 +115,10 @@ def lib() -> ctypes.CDLL:
 
 def _check(code: int, where: str):
     if code != 0:
-        raise ArmaError(code, where)
+        detail = ""
+        if STATUS.get(code) == "cuda":
+            detail = (lib().arma_gpu_last_cuda_error() or b"").decode(errors="replace")
+        raise ArmaError(code, where, detail)
 
 
 def torch_dtype(dt: int):

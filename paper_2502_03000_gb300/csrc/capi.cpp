@@ -1,3 +1,4 @@
+#include <cstdio>
 // C-ABI entry points (include/arma_gpu.h) and the executor that enqueues a
 // plan's steps on the caller's stream.
 #include <cuda_runtime.h>
@@ -40,7 +41,14 @@ const void* cptr(const Bind& b, const Ref& r) {
 }
 void* mptr(const Bind& b, const Ref& r) { return const_cast<void*>(cptr(b, r)); }
 
-arma_status cuda_status(cudaError_t e) { return e == cudaSuccess ? ARMA_OK : ARMA_ERR_CUDA; }
+thread_local char g_last_cuda[160] = "";
+
+// records the CUDA error for arma_gpu_last_cuda_error() and maps it
+arma_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return ARMA_OK;
+  snprintf(g_last_cuda, sizeof g_last_cuda, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+  return ARMA_ERR_CUDA;
+}
 
 arma_status run_step(const Step& st, const Bind& b, cudaStream_t s, int* launches) {
   unsigned int* tickets = reinterpret_cast<unsigned int*>(b.ws + 64);
@@ -188,7 +196,7 @@ arma_status arma_gpu_eval(const arma_plan* plan, const void* const* in_ptrs, voi
   Bind b{in_ptrs, out_ptrs, static_cast<char*>(workspace), plan->n_slots,
          (int32_t)plan->outs.size()};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(workspace, 0, kHeaderBytes, s) != cudaSuccess) return ARMA_ERR_CUDA;
+  if (cudaError_t e = cudaMemsetAsync(workspace, 0, kHeaderBytes, s)) return cuda_status(e);
   int launches = 0;
   for (const Step& st : plan->steps) {
     arma_status r = run_step(st, b, s, &launches);
@@ -202,9 +210,8 @@ arma_status arma_gpu_eval_status(const arma_plan* plan, const void* workspace, v
   if (!plan || !workspace) return ARMA_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int64_t hdr[2] = {0, 0};
-  if (cudaStreamSynchronize(s) != cudaSuccess) return ARMA_ERR_CUDA;
-  if (cudaMemcpy(hdr, workspace, sizeof hdr, cudaMemcpyDeviceToHost) != cudaSuccess)
-    return ARMA_ERR_CUDA;
+  if (cudaError_t e = cudaStreamSynchronize(s)) return cuda_status(e);
+  if (cudaError_t e = cudaMemcpy(hdr, workspace, sizeof hdr, cudaMemcpyDeviceToHost)) return cuda_status(e);
   int32_t code = static_cast<int32_t>(hdr[0] & 0xffffffff);
   if (info) *info = hdr[1];
   if (code == 0) return ARMA_OK;
@@ -223,6 +230,8 @@ arma_status arma_gpu_plan_info(const arma_plan* plan, char* buf, size_t len, siz
 }
 
 void arma_gpu_plan_free(arma_plan* plan) { delete plan; }
+
+const char* arma_gpu_last_cuda_error(void) { return g_last_cuda; }
 
 const char* arma_gpu_status_string(arma_status s) {
   switch (s) {

@@ -69,6 +69,8 @@ struct Params {
   void* D; int64_t ldd; int32_t ddt;
   const void* C; int64_t ldc; int32_t cdt;
   double alpha, beta;
+  float alpha_f, beta_f;    // alpha and beta rounded to float
+  int32_t has_c;            // beta != 0
   float beta_h, beta_l;     // beta as an exact float pair (FP64 epilogue)
   const void* rs; int64_t rs_inc; int32_t rsdt;
   const void* cs; int64_t cs_inc; int32_t csdt;
@@ -337,7 +339,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int quarter = warp & 3;
     const int half = (warp - 2) >> 2;
     const bool f64_out = p.ddt == ARMA_F64;
-    const float alpha_f = (float)p.alpha, beta_f = (float)p.beta;
+    const bool d_bf16 = p.ddt == ARMA_BF16;
+    const bool has_c = p.C != nullptr && p.has_c;
+    const float alpha_f = p.alpha_f, beta_f = has_c ? p.beta_f : 0.f;
     int acc = 0;
     uint32_t aphase = 0;
     for (int32_t w = blockIdx.x; w < total_work; w += gridDim.x) {
@@ -390,76 +394,91 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t tb = tmem_base + lane_base + (uint32_t)(acc * BN + half * (BN / 2));
       float rsf = 1.f;
       if (!p.partial && p.rs && row_ok) rsf = load_as<float>(p.rs, row * p.rs_inc, p.rsdt);
-      const ff::F2 b2{p.beta_h, p.beta_l};
 #pragma unroll 1
       for (int c0 = 0; c0 < BN / 2; c0 += 16) {
         float v[16];
         tmem_ld16(tb + (uint32_t)c0, v);
         const int64_t col0 = colh + c0;
-        if (f64_out && !p.partial) {
-          // FP64 results without FP64 instructions.  The product of these
-          // tiers is FP32-accurate, so beta*C is added in FP32 too: C is
-          // rounded to float with integer operations (error <= 2^-24 |C|),
-          // the sum is widened to a double exactly by integer operations.
-          // C outside float range takes an FP64 path behind a warp vote.
-          // C is loaded before any D store (C may alias D).
-          const bool has_c = p.C && p.beta != 0.0;
-          double cv[16], outv[16];
-          float rv[16];
-          uint32_t bad = 0u;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const bool in = row_ok && col0 + j < p.n;
-            cv[j] = (has_c && in) ? load_as<double>(p.C, row + (col0 + j) * p.ldc, p.cdt) : 0.0;
-          }
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            float r = alpha_f * v[j] * rsf;
-            if (p.cs && row_ok && col0 + j < p.n) r *= load_as<float>(p.cs, (col0 + j) * p.cs_inc, p.csdt);
-            rv[j] = r;
-            if (has_c) {
-              float cf;
-              const bool fine = ff::d2f_rn(cv[j], cf);
-              bad |= fine ? 0u : (1u << j);
-              r = fmaf(beta_f, cf, r);
-            }
-            outv[j] = __longlong_as_double((long long)ff::f2d_bits(r));
-          }
-          if (__any_sync(0xffffffffu, bad != 0u)) {
-            for (int j = 0; j < 16; ++j)
-              if (bad & (1u << j)) outv[j] = (double)rv[j] + p.beta * cv[j];
-          }
-          if (row_ok) {
-            double* Dd = static_cast<double*>(p.D);
+        if (p.partial) {                  // uniform: the warp skips the rest together
+          float* dst = p.P + (int64_t)it.split * p.m * p.n + row;
+          if (row_ok)
 #pragma unroll
             for (int j = 0; j < 16; ++j)
-              if (col0 + j < p.n) Dd[row + (col0 + j) * p.ldd] = outv[j];
-          }
+              if (col0 + j < p.n) dst[(col0 + j) * p.m] = v[j];
           continue;
         }
-        if (!row_ok) continue;
-        if (p.partial) {
-          float* dst = p.P + (int64_t)it.split * p.m * p.n + row;
+        // The product of these tiers is FP32-accurate, so beta*C is added in
+        // FP32: C is read as a float with integer operations (an FP64 C
+        // rounded to nearest, error <= 2^-24 |C|); FP64 results are widened
+        // exactly by integer operations, so the epilogue issues no FP64
+        // instruction.  An FP64 C outside float range is finished in FP64
+        // behind a warp vote; its D element is stored only then, after C was
+        // read again (C may alias D).
+        // loads first (one uniform branch per storage type), then arithmetic
+        float cf[16];
+        uint32_t bad = 0u;
+        if (has_c && p.cdt == ARMA_F64) {
+          const double* Cd = static_cast<const double*>(p.C);
+          double cd[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (col0 + j < p.n) dst[(col0 + j) * p.m] = v[j];
-        } else {
-          // FP32 / BF16 results: FP32 epilogue arithmetic
-          const bool has_c = p.C && p.beta != 0.0;
-          float cf[16];
-          if (has_c) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-              cf[j] = (col0 + j < p.n) ? load_as<float>(p.C, row + (col0 + j) * p.ldc, p.cdt) : 0.f;
-          }
+          for (int j = 0; j < 16; ++j) cd[j] = (row_ok && col0 + j < p.n) ? Cd[row + (col0 + j) * p.ldc] : 0.0;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
+            float f;
+            if (!ff::d2f_rn(cd[j], f)) {
+              bad |= 1u << j;
+              f = 0.f;
+            }
+            cf[j] = f;
+          }
+        } else if (has_c && p.cdt == ARMA_F32) {
+          const float* Cf = static_cast<const float*>(p.C);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) cf[j] = (row_ok && col0 + j < p.n) ? Cf[row + (col0 + j) * p.ldc] : 0.f;
+        } else if (has_c) {
+          const unsigned short* Cb = static_cast<const unsigned short*>(p.C);
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            cf[j] = (row_ok && col0 + j < p.n) ? __uint_as_float((uint32_t)Cb[row + (col0 + j) * p.ldc] << 16) : 0.f;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) cf[j] = 0.f;
+        }
+        float rr[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          float r = alpha_f * v[j] * rsf;
+          if (p.cs && col0 + j < p.n) r *= load_as<float>(p.cs, (col0 + j) * p.cs_inc, p.csdt);
+          rr[j] = fmaf(beta_f, cf[j], r);
+        }
+        if (row_ok) {
+          const int64_t at0 = row + col0 * p.ldd;
+          if (f64_out) {
+            long long* D = static_cast<long long*>(p.D) + at0;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (col0 + j < p.n && !(bad & (1u << j))) D[j * p.ldd] = (long long)ff::f2d_bits(rr[j]);
+          } else if (d_bf16) {
+            __nv_bfloat16* D = static_cast<__nv_bfloat16*>(p.D) + at0;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (col0 + j < p.n) D[j * p.ldd] = __float2bfloat16_rn(rr[j]);
+          } else {
+            float* D = static_cast<float*>(p.D) + at0;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (col0 + j < p.n) D[j * p.ldd] = rr[j];
+          }
+        }
+        if (__any_sync(0xffffffffu, bad != 0u)) {   // every lane of the warp gets here
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if (!(bad & (1u << j))) continue;
             const int64_t col = col0 + j;
-            if (col >= p.n) break;
             float r = alpha_f * v[j] * rsf;
             if (p.cs) r *= load_as<float>(p.cs, col * p.cs_inc, p.csdt);
-            if (has_c) r = fmaf(beta_f, cf[j], r);
-            store_as<float>(p.D, row + col * p.ldd, p.ddt, r);
+            const double t = (double)r + p.beta * static_cast<const double*>(p.C)[row + col * p.ldc];
+            store_as<double>(p.D, row + col * p.ldd, p.ddt, t);
           }
         }
       }
@@ -548,34 +567,47 @@ struct PrepArgs {
 };
 
 // 32 x 32 tiles through shared memory: read along X's contiguous index,
-// write along K
+// write along K.  The storage-type branch sits outside the row loop, so a
+// thread's four loads are in flight together.
+template <typename XT>
+__device__ __forceinline__ void prep_tile_load(const PrepArgs& a, int64_t r0, int64_t l0, int tx, int ty,
+                                               uint16_t (&t)[3][32][33]) {
+  XT x[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int q = ty + 8 * k;
+    int64_t r, l;
+    if (a.trans) { l = l0 + tx; r = r0 + q; } else { r = r0 + tx; l = l0 + q; }
+    x[k] = (r < a.R && l < a.K) ? static_cast<const XT*>(a.X)[a.trans ? l + r * a.ldx : r + l * a.ldx] : XT(0);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int q = ty + 8 * k;
+    uint16_t sl[3] = {0, 0, 0};
+    if constexpr (sizeof(XT) == 8) {
+      if (a.slices == 1) sl[0] = d2bf16_rn(x[k]);
+      else split3_f64(x[k], sl);
+    } else if constexpr (sizeof(XT) == 4) {
+      if (a.slices == 1) sl[0] = __bfloat16_as_ushort(__float2bfloat16_rn(x[k]));
+      else split3_f32(x[k], sl);
+    } else {
+      sl[0] = x[k];                      // BF16 is its own first slice
+    }
+    const int rr = a.trans ? q : tx, ll = a.trans ? tx : q;
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+      if (u < a.slices) t[u][rr][ll] = sl[u];
+  }
+}
+
 __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepArgs a) {
   __shared__ uint16_t t[3][32][33];
   if (a.slices != 1 && a.slices != 3) return;   // the tile above holds at most 3 slices
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t r0 = (int64_t)blockIdx.x * 32, l0 = (int64_t)blockIdx.y * 32;
-  for (int q = ty; q < 32; q += 8) {
-    int64_t r, l;
-    if (a.trans) { l = l0 + tx; r = r0 + q; } else { r = r0 + tx; l = l0 + q; }
-    uint16_t s[3] = {0, 0, 0};
-    if (r < a.R && l < a.K) {
-      // native loads per storage type: no FP64-pipe conversions
-      const int64_t idx = a.trans ? l + r * a.ldx : r + l * a.ldx;
-      if (a.xdt == ARMA_F64) {
-        const double x = static_cast<const double*>(a.X)[idx];
-        if (a.slices == 1) s[0] = d2bf16_rn(x);
-        else split3_f64(x, s);
-      } else if (a.xdt == ARMA_F32) {
-        const float x = static_cast<const float*>(a.X)[idx];
-        if (a.slices == 1) s[0] = __bfloat16_as_ushort(__float2bfloat16_rn(x));
-        else split3_f32(x, s);
-      } else {
-        s[0] = static_cast<const uint16_t*>(a.X)[idx];   // BF16 is its own first slice
-      }
-    }
-    const int rr = (int)(r - r0), ll = (int)(l - l0);
-    for (int u = 0; u < a.slices; ++u) t[u][rr][ll] = s[u];
-  }
+  if (a.xdt == ARMA_F64) prep_tile_load<double>(a, r0, l0, tx, ty, t);
+  else if (a.xdt == ARMA_F32) prep_tile_load<float>(a, r0, l0, tx, ty, t);
+  else prep_tile_load<uint16_t>(a, r0, l0, tx, ty, t);
   __syncthreads();
   for (int q = ty; q < 32; q += 8) {
     const int64_t r = r0 + q, l = l0 + tx;
@@ -589,7 +621,32 @@ __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepA
 }
 
 // op(X) contiguous along K (the common case): each thread converts 8
-// consecutive K elements of one row and writes one 16-byte vector per slice
+// consecutive K elements of one row and writes one 16-byte vector per slice.
+// The storage-type branch sits outside the element loop, so the eight loads
+// of a thread are in flight together.
+template <typename XT>
+__device__ __forceinline__ void prep_group(const PrepArgs& a, int64_t r, int64_t l0, uint16_t (&s0)[8],
+                                           uint16_t (&s1)[8], uint16_t (&s2)[8]) {
+  const XT* X = static_cast<const XT*>(a.X) + r * a.ldx;
+  XT x[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) x[e] = (r < a.R && l0 + e < a.K) ? X[l0 + e] : XT(0);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    uint16_t sl[3] = {0, 0, 0};
+    if constexpr (sizeof(XT) == 8) {
+      if (a.slices == 1) sl[0] = d2bf16_rn(x[e]);
+      else split3_f64(x[e], sl);
+    } else if constexpr (sizeof(XT) == 4) {
+      if (a.slices == 1) sl[0] = __bfloat16_as_ushort(__float2bfloat16_rn(x[e]));
+      else split3_f32(x[e], sl);
+    } else {
+      sl[0] = x[e];                      // BF16 is its own first slice
+    }
+    s0[e] = sl[0]; s1[e] = sl[1]; s2[e] = sl[2];
+  }
+}
+
 __global__ void __launch_bounds__(256) prep_kcontig_kernel(const __grid_constant__ PrepArgs a) {
   if (a.slices != 1 && a.slices != 3) return;
   const int64_t groups = a.kp / 8;
@@ -600,26 +657,9 @@ __global__ void __launch_bounds__(256) prep_kcontig_kernel(const __grid_constant
     __align__(16) uint16_t s0[8];
     __align__(16) uint16_t s1[8];
     __align__(16) uint16_t s2[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      uint16_t sl[3] = {0, 0, 0};
-      const int64_t l = l0 + e;
-      if (r < a.R && l < a.K) {
-        const int64_t idx = l + r * a.ldx;
-        if (a.xdt == ARMA_F64) {
-          const double x = static_cast<const double*>(a.X)[idx];
-          if (a.slices == 1) sl[0] = d2bf16_rn(x);
-          else split3_f64(x, sl);
-        } else if (a.xdt == ARMA_F32) {
-          const float x = static_cast<const float*>(a.X)[idx];
-          if (a.slices == 1) sl[0] = __bfloat16_as_ushort(__float2bfloat16_rn(x));
-          else split3_f32(x, sl);
-        } else {
-          sl[0] = static_cast<const uint16_t*>(a.X)[idx];
-        }
-      }
-      s0[e] = sl[0]; s1[e] = sl[1]; s2[e] = sl[2];
-    }
+    if (a.xdt == ARMA_F64) prep_group<double>(a, r, l0, s0, s1, s2);
+    else if (a.xdt == ARMA_F32) prep_group<float>(a, r, l0, s0, s1, s2);
+    else prep_group<uint16_t>(a, r, l0, s0, s1, s2);
     uint4* o0 = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(a.out) + r * a.kp + l0);
     *o0 = *reinterpret_cast<const uint4*>(s0);
     if (a.slices == 3) {
@@ -790,6 +830,8 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   p.D = a.D; p.ldd = a.ldd; p.ddt = a.ddt;
   p.C = a.C; p.ldc = a.ldc; p.cdt = a.cdt;
   p.alpha = a.alpha; p.beta = a.beta;
+  p.alpha_f = (float)a.alpha; p.beta_f = (float)a.beta;
+  p.has_c = a.C != nullptr && a.beta != 0.0;
   p.beta_h = (float)a.beta;
   p.beta_l = (float)(a.beta - (double)p.beta_h);
   p.rs = a.rs; p.rs_inc = a.rs_inc; p.rsdt = a.rsdt;

@@ -1070,9 +1070,33 @@ __global__ void __launch_bounds__(256) sub_step_kernel(const T* __restrict__ LU,
 }
 
 
-// perm = composition of the row swaps; Y(:, c) = P * B(:, c) (B null: identity)
-__global__ void perm_kernel(const int32_t* piv, int32_t* perm, int64_t n) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// perm = composition of the row swaps; Y(:, c) = P * B(:, c) (B null: identity).
+// The swaps are sequential; with n <= PERM_SMEM they run in shared memory
+// (one thread), after the whole block has staged piv and the identity.
+constexpr int64_t PERM_SMEM = 24576;
+
+__global__ void __launch_bounds__(1024) perm_kernel(const int32_t* piv, int32_t* perm, int64_t n) {
+  extern __shared__ int32_t sp[];        // [n] perm, [n] piv when n <= PERM_SMEM
+  if (n <= PERM_SMEM) {
+    int32_t* sperm = sp;
+    int32_t* spiv = sp + n;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      sperm[i] = (int32_t)i;
+      spiv[i] = piv[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int64_t d = 0; d < n; ++d) {
+        const int32_t p = spiv[d];
+        const int32_t t = sperm[d];
+        sperm[d] = sperm[p];
+        sperm[p] = t;
+      }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) perm[i] = sperm[i];
+    return;
+  }
+  if (threadIdx.x != 0) return;
   for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
   for (int64_t d = 0; d < n; ++d) {
     const int64_t p = piv[d];
@@ -1080,6 +1104,16 @@ __global__ void perm_kernel(const int32_t* piv, int32_t* perm, int64_t n) {
     perm[d] = perm[p];
     perm[p] = t;
   }
+}
+
+cudaError_t launch_perm(const int32_t* piv, int32_t* perm, int64_t n, cudaStream_t s) {
+  const size_t smem = n <= PERM_SMEM ? (size_t)n * 8 : 0;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(perm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  perm_kernel<<<1, 1024, smem, s>>>(piv, perm, n);
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -1446,7 +1480,8 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
     double* Uinv = Linv + nb * NB * NB;
     inv_diag_kernel<double><<<(unsigned)nb, 256, 0, s>>>(W, n, Linv, Uinv);
     double* Y = reinterpret_cast<double*>(base + L.y);
-    perm_kernel<<<1, 32, 0, s>>>(piv, perm, n);
+    e = launch_perm(piv, perm, n, s);
+    if (e != cudaSuccess) return e;
     gather_kernel<double><<<grid_for(n * nrhs), 256, 0, s>>>(a.B, a.ldb, a.bdt, perm, Y, n, nrhs, nullptr);
     e = substitute<double>(W, Linv, Uinv, n, Y, reinterpret_cast<double*>(base + L.z), nrhs, flags, ctl,
                            a.status_code, nullptr, s, launches);
@@ -1463,7 +1498,8 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
   inv_diag_kernel<float><<<(unsigned)nb, 256, 0, s>>>(W, n, Linv, Uinv);
   if (launches) ++*launches;
   float* Y = reinterpret_cast<float*>(base + L.y);
-  perm_kernel<<<1, 32, 0, s>>>(piv, perm, n);
+  e = launch_perm(piv, perm, n, s);
+  if (e != cudaSuccess) return e;
   gather_kernel<float><<<grid_for(n * nrhs), 256, 0, s>>>(a.B, a.ldb, a.bdt, perm, Y, n, nrhs, nullptr);
   float* Z = reinterpret_cast<float*>(base + L.z);
   e = substitute<float>(W, Linv, Uinv, n, Y, Z, nrhs, flags, ctl, a.status_code, nullptr, s, launches);
