@@ -51,15 +51,16 @@ __device__ __forceinline__ bool split(double x, F2& r) {
 
 // double -> float, round to nearest even, integer operations only.  Returns
 // false (and r unspecified) unless the result is a normal float or zero.
+// Works on the two 32-bit halves: 64-bit integer operations issue to the
+// FP64 pipe on this GPU.
 __device__ __forceinline__ bool d2f_rn(double x, float& r) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const unsigned int e = (unsigned int)(u >> 52) & 0x7ffu;
-  const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
-  if (e == 0u && (u << 1) == 0ull) { r = __uint_as_float(sign); return true; }
+  const unsigned int uh = (unsigned int)__double2hiint(x), ul = (unsigned int)__double2loint(x);
+  const unsigned int e = (uh >> 20) & 0x7ffu;
+  const unsigned int sign = uh & 0x80000000u;
+  if (e == 0u && ((uh << 1) | ul) == 0u) { r = __uint_as_float(sign); return true; }
   if (e < 897u || e > 1150u) return false;              // float exponent 1..254
-  const unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
-  unsigned int m = (unsigned int)(mant >> 29);          // 23 fraction bits
-  const unsigned int rem = (unsigned int)(mant & 0x1FFFFFFFull);
+  unsigned int m = ((uh & 0xFFFFFu) << 3) | (ul >> 29);  // 23 fraction bits
+  const unsigned int rem = ul & 0x1FFFFFFFu;
   unsigned int be = e - 896u;
   if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) {
     if (++m == 0x800000u) { m = 0u; ++be; }
@@ -69,13 +70,18 @@ __device__ __forceinline__ bool d2f_rn(double x, float& r) {
   return true;
 }
 
-// exact float -> double bits (normal floats and zero)
-__device__ __forceinline__ unsigned long long f2d_bits(float f) {
+// exact float -> double (normal floats and zero), from 32-bit halves
+__device__ __forceinline__ double f2d_exact(float f) {
   const unsigned int u = __float_as_uint(f);
-  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
   const unsigned int e = (u >> 23) & 0xffu;
-  if (e == 0u) return sign;  // zero (denormals flushed; callers keep |h| >= 2^-96)
-  return sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+  if (e == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);   // zero (denormals flushed)
+  const unsigned int hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// the same as a 64-bit pattern
+__device__ __forceinline__ unsigned long long f2d_bits(float f) {
+  return (unsigned long long)__double_as_longlong(f2d_exact(f));
 }
 
 // hi + lo as a double, by integer operations (no FP64 instruction).  Needs a

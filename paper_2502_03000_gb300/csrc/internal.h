@@ -60,6 +60,9 @@ enum EwOpcode : int32_t {
   EW_POPSUB,     // acc = S_j - acc
   EW_POPMUL,     // acc = S_j * acc
   EW_POPDIV,     // acc = S_j / acc
+  EW_FMA,        // acc = X_k * X_k2 + acc      (k2 = arg2)
+  EW_FNMA,       // acc = -(X_k * X_k2) + acc
+  EW_LDP2,       // acc = s * X_k, s = +-2^arg2: exact; FP64 passes scale the exponent field
   EW_NOPS
 };
 
@@ -69,6 +72,7 @@ struct EwIns {
   double s;
   float sf = 0.f;  // s as a float pair sf + sl (filled at eval time):
   float sl = 0.f;  //   sf alone is the FP32 scalar of FP32 passes
+  int32_t arg2 = 0;  // second operand (EW_FMA, EW_FNMA) or exponent (EW_LDP2)
 };
 
 enum EwMode : int32_t { EW_FLAT = 0, EW_GRID = 1, EW_DIAG = 2 };

@@ -46,6 +46,7 @@ __device__ __forceinline__ CT ew_in(int op, CT acc, CT x, double s) {
     case EW_DIV: return acc / x;
     case EW_RDIV: return x / acc;
     case EW_AXPY: return fma((CT)s, x, acc);
+    case EW_LDP2: return (CT)s * x;   // exact: s is a power of two
     default: return acc;
   }
 }
@@ -70,8 +71,9 @@ __device__ __forceinline__ CT ew_self(int op, CT acc, double s) {
   }
 }
 
-__device__ __forceinline__ bool uses_operand(int op) { return op <= EW_AXPY; }
-__device__ __forceinline__ bool is_pop(int op) { return op >= EW_POPADD; }
+__device__ __forceinline__ bool uses_operand(int op) { return op <= EW_AXPY || op == EW_LDP2; }
+__device__ __forceinline__ bool uses_two(int op) { return op == EW_FMA || op == EW_FNMA; }
+__device__ __forceinline__ bool is_pop(int op) { return op >= EW_POPADD && op <= EW_POPDIV; }
 
 // ---- strided path: one element per step, any operand layout ----
 template <typename CT>
@@ -92,6 +94,14 @@ __global__ void __launch_bounds__(256) ew_strided_kernel(const __grid_constant__
         if ((a.in_flags[arg] & EWF_DIAGMASK) && i != j) x = 0;
         else x = load_as<CT>(a.in[arg], i * a.rs[arg] + j * a.cs[arg], a.in_dtype[arg]);
         acc = ew_in<CT>(op, acc, x, s);
+      } else if (uses_two(op)) {
+        const int arg2 = a.ops[pc].arg2;
+        CT x, y;
+        if ((a.in_flags[arg] & EWF_DIAGMASK) && i != j) x = 0;
+        else x = load_as<CT>(a.in[arg], i * a.rs[arg] + j * a.cs[arg], a.in_dtype[arg]);
+        if ((a.in_flags[arg2] & EWF_DIAGMASK) && i != j) y = 0;
+        else y = load_as<CT>(a.in[arg2], i * a.rs[arg2] + j * a.cs[arg2], a.in_dtype[arg2]);
+        acc = op == EW_FMA ? fma(x, y, acc) : fma(-x, y, acc);
       } else if (op == EW_PUSH) {
         if (arg == 0) s0 = acc; else if (arg == 1) s1 = acc; else if (arg == 2) s2 = acc; else s3 = acc;
       } else if (is_pop(op)) {
@@ -121,19 +131,20 @@ __global__ void __launch_bounds__(256) ew_strided_kernel(const __grid_constant__
 // split into its pair with integer operations only.  Values outside the
 // pair's exponent range take the FP64 route.
 __device__ __forceinline__ bool split_ff(double x, float& hi, float& lo) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const unsigned int e = (unsigned int)(u >> 52) & 0x7ffu;
-  if (e == 0u && (u << 1) == 0ull) { hi = 0.f; lo = 0.f; return true; }  // +-0
+  // 32-bit halves only: 64-bit integer operations on the bit pattern issue
+  // to the FP64 pipe on this GPU
+  const unsigned int uh = (unsigned int)__double2hiint(x), ul = (unsigned int)__double2loint(x);
+  const unsigned int e = (uh >> 20) & 0x7ffu;
+  if (e == 0u && ((uh << 1) | ul) == 0u) { hi = 0.f; lo = 0.f; return true; }  // +-0
   // |x| in [2^-51, 2^51): hi, lo, hi^2 and its rounding error all stay
   // normal floats, and per-thread sums of squares cannot overflow
   if (e < 972u || e > 1073u) return false;
-  const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
-  const unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
-  hi = __uint_as_float(sign | ((e - 896u) << 23) | (unsigned int)(mant >> 29));
+  const unsigned int sign = uh & 0x80000000u;
+  hi = __uint_as_float(sign | ((e - 896u) << 23) | ((uh & 0xFFFFFu) << 3) | (ul >> 29));
   // lo from the low 29 significand bits, assembled as float bits with
   // integer operations (no conversion instruction, which would use the FP64
   // pipe); truncated to 24 bits
-  const unsigned int rr = (unsigned int)(mant & 0x1FFFFFFFull);
+  const unsigned int rr = ul & 0x1FFFFFFFu;
   if (rr == 0u) { lo = 0.f; return true; }
   const int nb = 32 - __clz(rr);
   const unsigned int m24 = nb > 24 ? rr >> (nb - 24) : rr << (24 - nb);
@@ -274,6 +285,52 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) ew_flat_kernel(co
         case EW_POPSUB: ARMA_EW_STK(acc[v] = st[q][v] - acc[v]) break;
         case EW_POPMUL: ARMA_EW_STK(acc[v] = st[q][v] * acc[v]) break;
         case EW_POPDIV: ARMA_EW_STK(acc[v] = st[q][v] / acc[v]) break;
+        case EW_FMA:
+        case EW_FNMA: {
+          const int arg2 = a.ops[pc].arg2;
+          CT y[V];
+#pragma unroll
+          for (int v = 0; v < V; ++v) y[v] = 0;
+#pragma unroll
+          for (int k = 0; k < NIN; ++k)
+            if (k == arg2)
+#pragma unroll
+              for (int v = 0; v < V; ++v) y[v] = x[k][v];
+          if (op == EW_FMA) {
+            ARMA_EW_SEL(acc[v] = fma(x[k][v], y[v], acc[v]))
+          } else {
+            ARMA_EW_SEL(acc[v] = fma(-x[k][v], y[v], acc[v]))
+          }
+          break;
+        }
+        case EW_LDP2:
+          if constexpr (kFF) {
+            // sign and exponent of the bit pattern adjusted with integer
+            // operations; zeros, subnormals, infinities and results outside
+            // the normal range take an FP64 multiply behind a warp vote
+            // (32-bit halves: 64-bit integer operations issue to the FP64 pipe)
+            const int e2 = a.ops[pc].arg2;
+            const unsigned int flip = sc < 0.0 ? 0x80000000u : 0u;
+            uint32_t bad = 0u;
+            ARMA_EW_SEL({
+              const unsigned int uh = (unsigned int)__double2hiint(x[k][v]);
+              const unsigned int ul = (unsigned int)__double2loint(x[k][v]);
+              const int ex = (int)((uh >> 20) & 0x7ffu);
+              const int ne = ex + e2;
+              const bool ok = ex != 0 && ex != 0x7ff && ne > 0 && ne < 0x7ff;
+              const unsigned int nh = (uh + ((unsigned int)e2 << 20)) ^ flip;
+              acc[v] = __hiloint2double((int)(ok ? nh : uh), (int)ul);
+              bad |= ok ? 0u : (1u << v);
+            })
+            if (__any_sync(__activemask(), bad != 0u)) {
+#pragma unroll
+              for (int v = 0; v < V; ++v)
+                if (bad & (1u << v)) acc[v] = sc * acc[v];
+            }
+          } else {
+            ARMA_EW_SEL(acc[v] = sc * x[k][v])
+          }
+          break;
         default: break;
       }
 #undef ARMA_EW_SEL
@@ -318,6 +375,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) ew_flat_kernel(co
       if (uses_operand(op)) {
         CT x = load_as<CT>(a.in[arg], t, a.in_dtype[arg]);
         acc = ew_in<CT>(op, acc, x, s);
+      } else if (uses_two(op)) {
+        const int arg2 = a.ops[pc].arg2;
+        const CT x = load_as<CT>(a.in[arg], t, a.in_dtype[arg]);
+        const CT y = load_as<CT>(a.in[arg2], t, a.in_dtype[arg2]);
+        acc = op == EW_FMA ? fma(x, y, acc) : fma(-x, y, acc);
       } else if (op == EW_PUSH) {
         if (arg == 0) s0 = acc; else if (arg == 1) s1 = acc; else if (arg == 2) s2 = acc; else s3 = acc;
       } else if (is_pop(op)) {

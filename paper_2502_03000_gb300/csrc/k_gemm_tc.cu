@@ -454,10 +454,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (row_ok) {
           const int64_t at0 = row + col0 * p.ldd;
           if (f64_out) {
-            long long* D = static_cast<long long*>(p.D) + at0;
+            double* D = static_cast<double*>(p.D) + at0;
 #pragma unroll
             for (int j = 0; j < 16; ++j)
-              if (col0 + j < p.n && !(bad & (1u << j))) D[j * p.ldd] = (long long)ff::f2d_bits(rr[j]);
+              if (col0 + j < p.n && !(bad & (1u << j))) D[j * p.ldd] = ff::f2d_exact(rr[j]);
           } else if (d_bf16) {
             __nv_bfloat16* D = static_cast<__nv_bfloat16*>(p.D) + at0;
 #pragma unroll
@@ -517,16 +517,18 @@ __device__ __forceinline__ uint16_t bf16_bits_of_window(uint32_t sign, int32_t e
   return (uint16_t)((sign >> 16) | ((uint32_t)be << 7) | (norm & 0x7Fu));
 }
 
+// (32-bit halves throughout: 64-bit integer operations issue to the FP64
+// pipe on this GPU)
 __device__ __forceinline__ void split3_f64(double x, uint16_t (&s)[3]) {
-  const uint64_t u = (uint64_t)__double_as_longlong(x);
-  const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
-  const int32_t e = (int32_t)((u >> 52) & 0x7FF);
+  const uint32_t uh = (uint32_t)__double2hiint(x), ul = (uint32_t)__double2loint(x);
+  const uint32_t sign = uh & 0x80000000u;
+  const int32_t e = (int32_t)((uh >> 20) & 0x7FF);
   if (e == 0 || e == 0x7FF) { s[0] = s[1] = s[2] = 0; return; }
-  const uint64_t m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // 53 bits
+  const uint32_t mh = (uh & 0xFFFFFu) | 0x100000u;   // significand bits 52..32
   const int32_t E = e - 1023;   // value = m * 2^(E - 52)
-  s[0] = bf16_bits_of_window(sign, E - 7, (uint32_t)(m >> 45) & 0xFFu);
-  s[1] = bf16_bits_of_window(sign, E - 15, (uint32_t)(m >> 37) & 0xFFu);
-  s[2] = bf16_bits_of_window(sign, E - 23, (uint32_t)(m >> 29) & 0xFFu);
+  s[0] = bf16_bits_of_window(sign, E - 7, (mh >> 13) & 0xFFu);
+  s[1] = bf16_bits_of_window(sign, E - 15, (mh >> 5) & 0xFFu);
+  s[2] = bf16_bits_of_window(sign, E - 23, ((mh << 3) | (ul >> 29)) & 0xFFu);
 }
 
 __device__ __forceinline__ void split3_f32(float f, uint16_t (&s)[3]) {
@@ -541,19 +543,20 @@ __device__ __forceinline__ void split3_f32(float f, uint16_t (&s)[3]) {
   s[2] = bf16_bits_of_window(sign, E - 23, m & 0xFFu);
 }
 
-// double -> BF16, round to nearest even, integer operations only
+// double -> BF16, round to nearest even, integer operations only (32-bit
+// halves)
 __device__ __forceinline__ uint16_t d2bf16_rn(double x) {
-  const uint64_t u = (uint64_t)__double_as_longlong(x);
-  const uint16_t sign = (uint16_t)((u >> 48) & 0x8000u);
-  const int32_t e = (int32_t)((u >> 52) & 0x7FF);
-  const uint64_t m = u & 0xFFFFFFFFFFFFFull;
-  if (e == 0x7FF) return (uint16_t)(sign | 0x7F80u | (m ? 0x40u : 0u));
+  const uint32_t uh = (uint32_t)__double2hiint(x), ul = (uint32_t)__double2loint(x);
+  const uint16_t sign = (uint16_t)((uh >> 16) & 0x8000u);
+  const int32_t e = (int32_t)((uh >> 20) & 0x7FF);
+  if (e == 0x7FF) return (uint16_t)(sign | 0x7F80u | (((uh & 0xFFFFFu) | ul) ? 0x40u : 0u));
   int32_t be = e - 1023 + 127;
   if (e == 0 || be <= 0) return sign;                 // zero / below BF16 normal range
-  uint32_t keep = (uint32_t)(m >> 45);                // 7 fraction bits
-  const uint64_t rem = m & ((1ull << 45) - 1);
-  const uint64_t half = 1ull << 44;
-  if (rem > half || (rem == half && (keep & 1u))) ++keep;
+  uint32_t keep = (uh & 0xFFFFFu) >> 13;              // 7 fraction bits
+  const uint32_t rh = uh & 0x1FFFu;                   // remainder: rh:ul, half = 0x1000:0
+  const bool above = rh > 0x1000u || (rh == 0x1000u && ul != 0u);
+  const bool tie = rh == 0x1000u && ul == 0u;
+  if (above || (tie && (keep & 1u))) ++keep;
   if (keep == 128u) { keep = 0u; ++be; }
   if (be >= 255) return (uint16_t)(sign | 0x7F80u);
   return (uint16_t)(sign | ((uint32_t)be << 7) | keep);
@@ -649,11 +652,13 @@ __device__ __forceinline__ void prep_group(const PrepArgs& a, int64_t r, int64_t
 
 __global__ void __launch_bounds__(256) prep_kcontig_kernel(const __grid_constant__ PrepArgs a) {
   if (a.slices != 1 && a.slices != 3) return;
-  const int64_t groups = a.kp / 8;
-  const int64_t total = a.rpad * groups;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = t / groups, l0 = (t - r * groups) * 8;
+  // 32-bit index arithmetic (the host keeps rpad * kp / 8 below 2^31): a
+  // 64-bit division per group costs more than the conversion itself
+  const uint32_t groups = (uint32_t)(a.kp / 8);
+  const uint32_t total = (uint32_t)(a.rpad * (a.kp / 8));
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const uint32_t rr = t / groups;
+    const int64_t r = rr, l0 = (int64_t)(t - rr * groups) * 8;
     __align__(16) uint16_t s0[8];
     __align__(16) uint16_t s1[8];
     __align__(16) uint16_t s2[8];
@@ -795,7 +800,7 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   pa.R = a.m; pa.K = a.k; pa.rpad = g.mpad; pa.kp = g.kp; pa.slices = g.slices; pa.out = As;
   const int sms0 = device_sm_count();
   auto prep = [&](const PrepArgs& pp) {
-    if (pp.trans) {
+    if (pp.trans && pp.rpad * (pp.kp / 8) < (1ll << 31)) {
       const int64_t total = pp.rpad * (pp.kp / 8);
       int64_t blocks = (total + 255) / 256, cap = (int64_t)sms0 * 8;
       prep_kcontig_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(pp);

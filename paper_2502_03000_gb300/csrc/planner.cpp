@@ -260,11 +260,22 @@ class Planner {
   };
   bool ew_is_leaf(int y, int root) const;
   int ew_operand(EwBuild& b, int y);
-  void ew_emit(EwBuild& b, int op, int arg, double s) {
+  void ew_emit(EwBuild& b, int op, int arg, double s, int arg2 = 0) {
     if (b.st.nops >= kMaxOps) { b.overflow = true; return; }
-    b.st.ops[b.st.nops++] = {op, arg, s};
+    EwIns& in = b.st.ops[b.st.nops++];
+    in = EwIns{op, arg, s};
+    in.arg2 = arg2;
   }
   void ew_compile(EwBuild& b, int y, int depth, int root);
+  // a sum of signed terms: leaves (times a scalar), elementwise products of
+  // two leaves, and at most one other subtree
+  struct SumTerm {
+    int kind;    // 0 leaf, 1 product of two leaves, 2 other subtree
+    int a, b;
+    double c;    // coefficient (+-1 for kinds 1 and 2)
+  };
+  bool sum_terms(int y, double sign, int root, bool top, std::vector<SumTerm>& t) const;
+  bool ew_sum(EwBuild& b, int y, int depth, int root);
   bool ew_leafable_view(int y) const;
   void linearize(int x, double c, std::vector<std::pair<int, double>>& terms, bool top);
 };
@@ -440,6 +451,99 @@ int Planner::ew_operand(EwBuild& b, int y) {
   return k;
 }
 
+bool Planner::sum_terms(int y, double sign, int root, bool top, std::vector<SumTerm>& t) const {
+  if (t.size() > 16) return false;
+  if (!top && ew_is_leaf(y, root)) { t.push_back({0, y, -1, sign}); return true; }
+  const arma_node& d = nd_[y];
+  switch (d.op) {
+    case ARMA_OP_ADD:
+      return sum_terms(d.a, sign, root, false, t) && sum_terms(d.b, sign, root, false, t);
+    case ARMA_OP_SUB:
+      return sum_terms(d.a, sign, root, false, t) && sum_terms(d.b, -sign, root, false, t);
+    case ARMA_OP_NEG:
+      return sum_terms(d.a, -sign, root, false, t);
+    case ARMA_OP_SCALE:
+      if (ew_is_leaf(d.a, root)) { t.push_back({0, d.a, -1, sign * d.scalar}); return true; }
+      break;
+    case ARMA_OP_DIV_SCALAR:
+      if (ew_is_leaf(d.a, root)) { t.push_back({0, d.a, -1, sign / d.scalar}); return true; }
+      break;
+    case ARMA_OP_SCHUR:
+      if (ew_is_leaf(d.a, root) && ew_is_leaf(d.b, root)) { t.push_back({1, d.a, d.b, sign}); return true; }
+      break;
+    default:
+      break;
+  }
+  t.push_back({2, y, -1, sign});
+  return true;
+}
+
+// A sum containing elementwise products of two leaves is evaluated as: the
+// one general subtree (or a scaled leaf) first, then the other scaled leaves
+// (fused multiply-adds), then each product as acc = +-x*y + acc (one fused
+// multiply-add each).  A leading leaf whose coefficient is +-2^e is loaded
+// with EW_LDP2, which FP64 passes apply to the exponent field exactly.  This
+// is a reordering of the sum (rounding differs from left to right by a few
+// units of the last place).
+bool Planner::ew_sum(EwBuild& b, int y, int depth, int root) {
+  std::vector<SumTerm> t;
+  if (!sum_terms(y, 1.0, root, true, t)) return false;
+  int nprod = 0, ngen = 0;
+  for (const SumTerm& u : t) {
+    nprod += u.kind == 1;
+    ngen += u.kind == 2;
+  }
+  if (nprod == 0 || ngen > 1 || t.size() < 2) return false;
+  auto pow2 = [](double c, int& e) {
+    int ex = 0;
+    const double m = std::frexp(std::fabs(c), &ex);
+    e = ex - 1;
+    return c != 0.0 && m == 0.5 && e >= -1000 && e <= 1000;
+  };
+  std::vector<char> done(t.size(), 0);
+  // the first term: the general subtree, else a leaf (power-of-two
+  // coefficient preferred), else the first product
+  int first = -1;
+  for (size_t i = 0; i < t.size() && first < 0; ++i)
+    if (t[i].kind == 2) first = (int)i;
+  int e2 = 0;
+  for (size_t i = 0; i < t.size() && first < 0; ++i)
+    if (t[i].kind == 0 && pow2(t[i].c, e2)) first = (int)i;
+  for (size_t i = 0; i < t.size() && first < 0; ++i)
+    if (t[i].kind == 0) first = (int)i;
+  if (first < 0) first = 0;
+  const SumTerm& f = t[first];
+  done[first] = 1;
+  if (f.kind == 2) {
+    ew_compile(b, f.a, depth, root);
+    if (f.c < 0) ew_emit(b, EW_NEG, 0, 0);
+  } else if (f.kind == 0) {
+    int e = 0;
+    if (pow2(f.c, e)) ew_emit(b, EW_LDP2, ew_operand(b, f.a), f.c, e);
+    else {
+      ew_emit(b, EW_LD, ew_operand(b, f.a), 0);
+      ew_emit(b, EW_SCAL, 0, f.c);
+    }
+  } else {
+    ew_emit(b, EW_LD, ew_operand(b, f.a), 0);
+    ew_emit(b, EW_MUL, ew_operand(b, f.b), 0);
+    if (f.c < 0) ew_emit(b, EW_NEG, 0, 0);
+  }
+  for (size_t i = 0; i < t.size(); ++i) {
+    if (done[i] || t[i].kind != 0) continue;
+    const int k = ew_operand(b, t[i].a);
+    if (t[i].c == 1.0) ew_emit(b, EW_ADD, k, 0);
+    else if (t[i].c == -1.0) ew_emit(b, EW_SUB, k, 0);
+    else ew_emit(b, EW_AXPY, k, t[i].c);
+  }
+  for (size_t i = 0; i < t.size(); ++i) {
+    if (done[i] || t[i].kind != 1) continue;
+    const int ka = ew_operand(b, t[i].a), kb = ew_operand(b, t[i].b);
+    ew_emit(b, t[i].c > 0 ? EW_FMA : EW_FNMA, ka, 0, kb);
+  }
+  return true;
+}
+
 void Planner::ew_compile(EwBuild& b, int y, int depth, int root) {
   if (b.overflow) return;
   if (ew_is_leaf(y, root)) { ew_emit(b, EW_LD, ew_operand(b, y), 0); return; }
@@ -451,6 +555,8 @@ void Planner::ew_compile(EwBuild& b, int y, int depth, int root) {
     case ARMA_OP_NEG: ew_compile(b, d.a, depth, root); ew_emit(b, EW_NEG, 0, 0); return;
     default: break;
   }
+  if ((d.op == ARMA_OP_ADD || d.op == ARMA_OP_SUB) && !literal_ && ew_sum(b, y, depth, root))
+    return;
   int A = d.a, B = d.b, op = d.op;
   static const int in_op[] = {0, EW_ADD, EW_SUB, EW_MUL, EW_DIV};
   static const int rev_op[] = {0, EW_ADD, EW_RSUB, EW_MUL, EW_RDIV};
@@ -482,6 +588,30 @@ void Planner::ew_compile(EwBuild& b, int y, int depth, int root) {
   ew_emit(b, EW_PUSH, depth, 0);
   ew_compile(b, B, depth + 1, root);
   ew_emit(b, pop_op[op], depth, 0);
+}
+
+// the instruction list of a fused pass, e.g. " ldp2 x2 -0.5; axpy x1 3; fma x0 x3"
+static std::string ew_program_text(const EwStep& s) {
+  static const char* names[] = {"ld", "add", "sub", "rsub", "mul", "div", "rdiv", "axpy", "scal", "divs",
+                                "adds", "neg", "push", "popadd", "popsub", "popmul", "popdiv", "fma", "fnma",
+                                "ldp2"};
+  static_assert(sizeof(names) / sizeof(names[0]) == EW_NOPS, "one name per opcode");
+  std::ostringstream os;
+  os.precision(17);
+  for (int i = 0; i < s.nops; ++i) {
+    const EwIns& in = s.ops[i];
+    os << (i ? "; " : " ") << names[in.op];
+    switch (in.op) {
+      case EW_LD: case EW_ADD: case EW_SUB: case EW_RSUB: case EW_MUL: case EW_DIV: case EW_RDIV:
+        os << " x" << in.arg; break;
+      case EW_AXPY: case EW_LDP2: os << " x" << in.arg << " " << in.s; break;
+      case EW_SCAL: case EW_DIVS: case EW_ADDS: os << " " << in.s; break;
+      case EW_FMA: case EW_FNMA: os << " x" << in.arg << " x" << in.arg2; break;
+      case EW_PUSH: case EW_POPADD: case EW_POPSUB: case EW_POPMUL: case EW_POPDIV: os << " s" << in.arg; break;
+      default: break;
+    }
+  }
+  return os.str();
 }
 
 static double ew_bytes(const EwStep& s) {
@@ -565,7 +695,7 @@ void Planner::plan_ew_root(int x, const MatOperand* dest, bool diag_mode, Ref su
     os << "fused elementwise pass (" << (s.mode == EW_FLAT ? "flat" : s.mode == EW_GRID ? "strided" : "diagonal")
        << ", " << s.nin << " operands, " << s.nops << " instructions"
        << (dest ? ", stored" : ", not stored") << ((s.red & 1) ? ", +sum" : "")
-       << ((s.red & 2) ? ", +sumsq" : "") << ") for node " << x;
+       << ((s.red & 2) ? ", +sumsq" : "") << ") for node " << x << "; program:" << ew_program_text(s);
     st.note = os.str();
     push_step(std::move(st));
     return;

@@ -155,6 +155,21 @@ def test_rewrites_fused_and_chain_and_solve():
     assert kernels(ag.Plan(*E.config_solve(64, 3), flags=ag.PLAN_LITERAL)) == ["solve", "gemm"]
 
 
+def test_fused_program_contracts_products():
+    """A%B + 3*C - D/2: the sum is reordered so that the product becomes one
+    fused multiply-add and the power-of-two term an exact exponent load:
+    two FMAs per element instead of a multiply and two FMAs."""
+    for dt in ("f64", "f32"):
+        note = ag.Plan(*E.config_fused(128, dt)).info["steps"][0]["note"]
+        prog = [ins.split()[0] for ins in note.split("program:")[1].split(";")]
+        assert prog == ["ldp2", "axpy", "fma"], note
+    # no product in the sum: the plain left-to-right program
+    g = E.Graph()
+    A, C, D = (g.input(k, 8, 8) for k in range(3))
+    note = ag.Plan(*g.build(C + A - 2 * D)).info["steps"][0]["note"]
+    assert [i.split()[0] for i in note.split("program:")[1].split(";")] == ["ld", "add", "axpy"], note
+
+
 def test_plan_info_is_json():
     p = ag.Plan(*E.config_products(256))
     info = p.info

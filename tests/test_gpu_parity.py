@@ -213,3 +213,52 @@ def test_fused_f64_extreme_scalars(torch, s):
     host = inputs(98, [(m, n)] * 2, "f64")
     got = run(nodes, outs, host, "f64")
     check(got, oracle.evaluate(nodes, outs, host), TOL["f64"], f"scalar {s}")
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_fused_power_of_two_load_edges(torch, dtype):
+    """s*D with s = +-2^e is loaded by exponent arithmetic in FP64 passes;
+    zeros, subnormals, values that overflow or underflow, infinities and NaNs
+    take the FP64 multiply.  With B = 0 the products add only zeros, so the
+    result equals s*D exactly."""
+    m, n = 67, 33
+    rng = np.random.default_rng(5)
+    D = rng.uniform(-1, 1, (m, n)) * np.exp2(rng.integers(-60, 60, (m, n)))
+    big, tiny = (1.5e308, 5e-324) if dtype == "f64" else (3e38, 1.4e-45)
+    special = [0.0, -0.0, tiny, -tiny, 1e-310 if dtype == "f64" else 1e-40, big, -big, np.inf, -np.inf, np.nan]
+    D.flat[: len(special)] = special
+    A = rng.uniform(-1, 1, (m, n))
+    B = np.zeros((m, n))
+    host = [synth.cast(x, dtype) for x in (A, B, D)]
+    for s in (4.0, -0.25, 2.0 ** -1000, -(2.0 ** 900), 1.0, -1.0):
+        if dtype == "f32" and abs(np.log2(abs(s))) > 100:
+            continue
+        g = E.Graph()
+        a, b, d = (g.input(k, m, n, dtype) for k in range(3))
+        out = s * d + a % b
+        nodes, outs = g.build(out)
+        plan = ag.Plan(nodes, outs)
+        assert "ldp2" in plan.info["steps"][0]["note"], plan.info["steps"][0]["note"]
+        (got,) = plan(*[to_dev(h, dtype) for h in host])
+        torch.cuda.synchronize()
+        want = (synth.cast(s * host[2].astype(np.float64), dtype) if dtype == "f32"
+                else s * host[2])
+        np.testing.assert_array_equal(to_host(got), want, err_msg=f"s = {s}")
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_fused_contracted_sums(torch, dtype):
+    """sums with elementwise products become fused multiply-adds in a new
+    order; every mix of signs, scalars and one general subtree must still
+    match the literal oracle within the dtype's tolerance"""
+    m, n = 190, 77
+    host = inputs(321, [(m, n)] * 5, dtype)
+    g = E.Graph()
+    A, B, C, D, F = (g.input(k, m, n, dtype) for k in range(5))
+    exprs = [A % B + 3 * C - D / 2, C - A % B, -(A % B) - D % F + 0.125 * C,
+             A % B + (C + D) % F - 2 * D, D / 4 - A % B + C % C, (A + B) / (C % C + 2) - A % D,
+             -(D % F) - (A % B)]
+    for k, e in enumerate(exprs):
+        nodes, outs = g.build(e, E.accu(e))
+        got = run(nodes, outs, host, dtype)
+        check(got, oracle.evaluate(nodes, outs, host), TOL[dtype], f"expression {k}")
