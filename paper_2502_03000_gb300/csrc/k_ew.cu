@@ -186,7 +186,7 @@ struct FFAcc {
 
 // ---- flat path: contiguous operands of one storage type T ----
 template <typename T> struct VecTraits;
-template <> struct VecTraits<double> { static constexpr int V = 4; typedef double CT; };
+template <> struct VecTraits<double> { static constexpr int V = 2; typedef double CT; };
 template <> struct VecTraits<float> { static constexpr int V = 8; typedef float CT; };
 template <> struct VecTraits<__nv_bfloat16> { static constexpr int V = 8; typedef float CT; };
 
@@ -223,7 +223,7 @@ __device__ __forceinline__ void store_chunk(T* __restrict__ p, int64_t c, const 
 // STK: spill slots the program may use (0 when it never pushes), so that
 // programs without spills do not hold dead registers.
 template <typename T, int NIN, int STK>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) ew_flat_kernel(const __grid_constant__ EwArgs a) {
+__global__ void __launch_bounds__(256, 3) ew_flat_kernel(const __grid_constant__ EwArgs a) {
   constexpr int V = VecTraits<T>::V;
   typedef typename VecTraits<T>::CT CT;
   constexpr bool kFF = std::is_same<T, double>::value;
