@@ -171,8 +171,16 @@ __global__ void __launch_bounds__(256) gemv_rows_kernel(const __grid_constant__ 
     int64_t cnt = le - l0 < 256 ? le - l0 : 256;
     if (i < a.rows) {
       if (a.mdt == ARMA_F64) {
-        const double* M = static_cast<const double*>(a.M);
-        for (int u = 0; u < cnt; ++u) sum = fma(M[i + (l0 + u) * a.csm], xs[u], sum);
+        // four independent accumulators: the DFMA latency is not a chain
+        const double* M = static_cast<const double*>(a.M) + i + l0 * a.csm;
+        double s4[4] = {0.0, 0.0, 0.0, 0.0};
+        int u = 0;
+        for (; u + 4 <= cnt; u += 4) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) s4[q] = fma(M[(int64_t)(u + q) * a.csm], xs[u + q], s4[q]);
+        }
+        for (; u < cnt; ++u) s4[0] = fma(M[(int64_t)u * a.csm], xs[u], s4[0]);
+        sum += (s4[0] + s4[1]) + (s4[2] + s4[3]);
       } else {
         for (int u = 0; u < cnt; ++u) sum = fma(load_as<double>(a.M, i + (l0 + u) * a.csm, a.mdt), xs[u], sum);
       }
@@ -206,11 +214,15 @@ __global__ void __launch_bounds__(256) gemv_cols_kernel(const __grid_constant__ 
   if (lane == 0) gemv_out(a, i, sum);
 }
 
+// K splits of the row kernel: enough CTAs for 4 per SM, chunks of at least
+// 32 columns, at most 64 splits (the partials buffer holds 64 x rows).  A
+// short, wide GEMV (512 x 4096, or 8192 x 512) would otherwise run on a few
+// dozen CTAs and leave the GPU latency-bound.
 int gemv_splits(int64_t rows, int64_t k) {
   int64_t blocks = (rows + 255) / 256;
   int64_t want = (int64_t)device_sm_count() * 4;
   int64_t s = (want + blocks - 1) / blocks;
-  int64_t smax = (k + 511) / 512;
+  int64_t smax = (k + 31) / 32;
   if (s > smax) s = smax;
   if (s > 64) s = 64;
   return s < 1 ? 1 : (int)s;
