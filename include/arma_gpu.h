@@ -109,6 +109,7 @@ typedef enum {
                                         instead of the exact minimum-cost order */
 #define ARMA_PLAN_COST_MLP     0x8u  /* rank candidate plans with the learned cost model */
 #define ARMA_PLAN_NO_FUSE      0x10u /* optimised rewrites but no elementwise fusion */
+#define ARMA_PLAN_NO_TENSOR    0x20u /* batched plans: SIMT tiles instead of tensor-core tiles */
 
 typedef struct arma_node {
   int32_t op;        /* arma_op */

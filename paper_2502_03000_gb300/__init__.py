@@ -37,7 +37,7 @@ OPS = {"input": 0, "add": 1, "sub": 2, "schur": 3, "div": 4, "scale": 5, "div_sc
        "add_scalar": 7, "neg": 8, "trans": 9, "matmul": 10, "diagmat": 11, "trace": 12,
        "accu": 13, "norm_fro": 14, "inv": 15}
 TIERS = {"native": 0, "f64": 1, "split_bf16": 2, "bf16": 3, "lu32_ir64": 4}
-PLAN_LITERAL, PLAN_CHAIN_LEFT, PLAN_CHAIN_GREEDY, PLAN_COST_MLP, PLAN_NO_FUSE = 1, 2, 4, 8, 16
+PLAN_LITERAL, PLAN_CHAIN_LEFT, PLAN_CHAIN_GREEDY, PLAN_COST_MLP, PLAN_NO_FUSE, PLAN_NO_TENSOR = 1, 2, 4, 8, 16, 32
 STATUS = {0: "ok", 1: "invalid", 2: "shape", 3: "dtype", 4: "align", 5: "workspace",
           6: "singular", 7: "noconverge", 8: "cuda", 9: "unsupported"}
 
@@ -347,6 +347,15 @@ class BatchedPlan:
                "arma_gpu_batched_table_fill")
         self.table = torch.from_numpy(host).to(device)
         self.ws = torch.empty(max(256, self.workspace_bytes), dtype=torch.uint8, device=device)
+
+    def status(self, stream=None):
+        """Device-side status of the last batched evaluation (synchronises)."""
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        info = ctypes.c_int64()
+        code = lib().arma_gpu_eval_status(self._h, ctypes.c_void_p(self.ws.data_ptr()), ctypes.c_void_p(st),
+                                          ctypes.byref(info))
+        return STATUS.get(code, str(code)), int(info.value)
 
     def __call__(self, stream=None):
         import torch

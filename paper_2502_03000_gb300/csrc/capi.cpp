@@ -347,8 +347,12 @@ arma_status arma_gpu_eval_batched(const arma_plan* plan, const void* device_tabl
   g.alpha = b.alpha; g.beta = b.beta;
   g.alpha_f = (float)b.alpha; g.beta_f = (float)b.beta;
   g.trace_partials = b.out_t >= 0 ? reinterpret_cast<double*>(static_cast<char*>(workspace) + kHeaderBytes) : nullptr;
+  g.tc = b.tc;
+  g.status = static_cast<int32_t*>(workspace);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaError_t e = cudaMemsetAsync(workspace, 0, 16, s)) return cuda_status(e);
   int launches = 0;
-  return cuda_status(launch_grouped(g, static_cast<cudaStream_t>(stream), &launches));
+  return cuda_status(launch_grouped(g, s, &launches));
 }
 
 }  // extern "C"

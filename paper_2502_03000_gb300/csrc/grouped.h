@@ -13,7 +13,7 @@ struct GroupedProblem {       // one per problem, in the device table
   void* D; int64_t ldd;
   double* trace;                // may be null
   int64_t first_tile;           // index of tile (0, 0) in the tile list
-  int32_t tile;                 // tile edge: 32 or 64
+  int32_t tile;                 // tile edge: 32 or 64 (SIMT), 128 (tensor cores)
   int32_t pad;
 };
 
@@ -26,8 +26,11 @@ struct GroupedArgs {
   double alpha, beta;
   float alpha_f, beta_f;
   double* trace_partials;       // [tiles] (diagonal tiles only), null without traces
+  int32_t tc;                   // 1: 128 x 128 tiles on the tensor cores
+  int32_t* status;              // workspace status word (device-side failures)
 };
 
 cudaError_t launch_grouped(const GroupedArgs& g, cudaStream_t s, int* launches);
+cudaError_t launch_grouped_tc(const GroupedArgs& g, cudaStream_t s, int* launches);
 
 }  // namespace arma

@@ -258,6 +258,7 @@ struct BatchedInfo {
   int32_t slot_a = 0, slot_b = 0, slot_c = -1, out_d = 0, out_t = -1;
   int32_t n_slots = 0, n_outs = 0;
   int32_t ta = 0, tb = 0, abdt = ARMA_F32, cdt = ARMA_F32, ddt = ARMA_F32;
+  int32_t tc = 0;           // 128 x 128 tiles on the tensor cores
   double alpha = 1.0, beta = 0.0;
   std::vector<int64_t> m, n, k, lda, ldb, ldc;
   std::vector<int32_t> tile;

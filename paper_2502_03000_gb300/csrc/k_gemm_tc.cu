@@ -35,6 +35,7 @@
 
 #include "common.cuh"
 #include "ff.cuh"
+#include "tc_ops.cuh"
 
 namespace arma {
 
@@ -48,7 +49,6 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barrier
 constexpr int TMEM_COLS = 512;
 constexpr int THREADS = 320;          // producer, MMA, 8 epilogue warps
 constexpr int EPI_THREADS = 256;
-constexpr uint32_t WAIT_LIMIT = 1u << 22;     // try_wait iterations before giving up
 
 // slice pairs (a, b) of the split tier, smallest contribution first
 __constant__ int kTermA[6] = {2, 1, 0, 1, 0, 0};
@@ -76,111 +76,6 @@ struct Params {
   const void* cs; int64_t cs_inc; int32_t csdt;
   int32_t* status;          // workspace status word (0 = ok)
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// bounded wait; returns false (and raises the CTA abort flag) on timeout or
-// when another role already aborted
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
-  for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
-    if (mbar_try(bar, parity)) return true;
-    if ((i & 255u) == 255u && *abort) return false;
-  }
-  *abort = 1;
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int32_t x,
-                                            int32_t y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
-      : "memory");
-}
-
-// K-major, 128-byte swizzle: 8-row groups of 1024 bytes (SBO), version 1
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
-  d |= (uint64_t)1 << 46;              // descriptor version
-  d |= (uint64_t)2 << 61;              // SWIZZLE_128B
-  return d;
-}
-
-// kind::f16 instruction descriptor: D=F32, A=B=BF16, both K-major, N, M
-__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
-      ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
-        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
-        "r"(__float_as_uint(v[15]))
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 struct WorkItem {
   int32_t tm, tn, split;
@@ -502,21 +397,6 @@ __global__ void __launch_bounds__(THREADS, 1)
 // operand preparation: op(X) (R x K, any storage type, either orientation)
 // -> T BF16 slices, K-major, rows padded to rpad, row stride kp (>= K, zero fill)
 // ---------------------------------------------------------------------------
-// The slices come from the binary expansion: slice 0 holds the leading 8
-// significand bits, slice 1 the next 8, slice 2 the next 8 (integer
-// operations only; each slice is exactly a BF16).  For one slice the value
-// is rounded to nearest BF16.
-__device__ __forceinline__ uint16_t bf16_bits_of_window(uint32_t sign, int32_t exp2_lsb, uint32_t win) {
-  // value = win * 2^exp2_lsb with win < 256; returns exact BF16 bits (0 if win == 0)
-  if (win == 0u) return 0;
-  const int lz = __clz(win) - 24;          // leading zeros inside the 8-bit window
-  const uint32_t norm = win << lz;         // bit 7 set
-  const int32_t e = exp2_lsb + 7 - lz;     // exponent of the leading bit
-  const int32_t be = e + 127;
-  if (be <= 0 || be >= 255) return 0;      // outside BF16's normal range: dropped
-  return (uint16_t)((sign >> 16) | ((uint32_t)be << 7) | (norm & 0x7Fu));
-}
-
 // (32-bit halves throughout: 64-bit integer operations issue to the FP64
 // pipe on this GPU)
 __device__ __forceinline__ void split3_f64(double x, uint16_t (&s)[3]) {
@@ -531,17 +411,6 @@ __device__ __forceinline__ void split3_f64(double x, uint16_t (&s)[3]) {
   s[2] = bf16_bits_of_window(sign, E - 23, ((mh << 3) | (ul >> 29)) & 0xFFu);
 }
 
-__device__ __forceinline__ void split3_f32(float f, uint16_t (&s)[3]) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t sign = u & 0x80000000u;
-  const int32_t e = (int32_t)((u >> 23) & 0xFF);
-  if (e == 0 || e == 0xFF) { s[0] = s[1] = s[2] = 0; return; }
-  const uint32_t m = (u & 0x7FFFFFu) | (1u << 23);   // 24 bits
-  const int32_t E = e - 127;
-  s[0] = bf16_bits_of_window(sign, E - 7, (m >> 16) & 0xFFu);
-  s[1] = bf16_bits_of_window(sign, E - 15, (m >> 8) & 0xFFu);
-  s[2] = bf16_bits_of_window(sign, E - 23, m & 0xFFu);
-}
 
 // double -> BF16, round to nearest even, integer operations only (32-bit
 // halves)

@@ -16,37 +16,66 @@
 namespace arma {
 namespace {
 
-template <int T>   // tile edge: 32 or 64; 256 threads, (T/16)^2 outputs each
+constexpr int GBK = 32;   // K per shared-memory stage
+
+__device__ __forceinline__ float widen(float x) { return x; }
+__device__ __forceinline__ float widen(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// One output tile.  AT is the storage type of A and B (FP32 or BF16, widened
+// exactly); the element type is a template parameter so that no load carries
+// conversion code for the other types.  The next K block is fetched into
+// registers while the current one is multiplied out of shared memory.
+template <typename AT, int T>   // tile edge: 32 or 64; 256 threads, (T/16)^2 outputs each
 __device__ __forceinline__ void grouped_tile(const GroupedProblem& pb, int tm, int tn, const GroupedArgs& g,
-                                             float (&As)[16][65], float (&Bs)[16][65], double* diag_out) {
-  constexpr int R = T / 16;   // outputs per thread per dimension
+                                             float (&As)[GBK][65], float (&Bs)[GBK][65], double* diag_out) {
+  constexpr int R = T / 16;             // outputs per thread per dimension
+  constexpr int NL = T * GBK / 256;     // elements per thread per operand and K block
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t i0 = (int64_t)tm * T, j0 = (int64_t)tn * T;
+  const AT* A = static_cast<const AT*>(pb.A);
+  const AT* B = static_cast<const AT*>(pb.B);
+  float ra[NL], rb[NL];
+  // element e of this thread: op(A)(ii, ll) and op(B)(ll, jj), each read
+  // along its contiguous index
+  auto a_at = [&](int e, int& ii, int& ll) {
+    const int x = tid + 256 * e;
+    if (g.ta) { ll = x % GBK; ii = x / GBK; } else { ii = x % T; ll = x / T; }
+  };
+  auto b_at = [&](int e, int& ll, int& jj) {
+    const int x = tid + 256 * e;
+    if (!g.tb) { ll = x % GBK; jj = x / GBK; } else { jj = x % T; ll = x / T; }
+  };
+  auto fetch = [&](int64_t l0) {
+#pragma unroll
+    for (int e = 0; e < NL; ++e) {
+      int ii, ll, jj, lb;
+      a_at(e, ii, ll);
+      const int64_t gi = i0 + ii, gl = l0 + ll;
+      ra[e] = (gi < pb.m && gl < pb.k) ? widen(A[g.ta ? gl + gi * pb.lda : gi + gl * pb.lda]) : 0.f;
+      b_at(e, lb, jj);
+      const int64_t gj = j0 + jj, gl2 = l0 + lb;
+      rb[e] = (gl2 < pb.k && gj < pb.n) ? widen(B[g.tb ? gj + gl2 * pb.ldb : gl2 + gj * pb.ldb]) : 0.f;
+    }
+  };
   float acc[R][R];
 #pragma unroll
   for (int r = 0; r < R; ++r)
 #pragma unroll
     for (int c = 0; c < R; ++c) acc[r][c] = 0.f;
-  for (int64_t l0 = 0; l0 < pb.k; l0 += 16) {
-    // op(A) tile T x 16 and op(B) tile 16 x T, loaded along the contiguous index
-    for (int e = tid; e < T * 16; e += 256) {
-      int ii, ll;
-      if (!g.ta) { ii = e % T; ll = e / T; } else { ll = e & 15; ii = e >> 4; }
-      const int64_t gi = i0 + ii, gl = l0 + ll;
-      float v = 0.f;
-      if (gi < pb.m && gl < pb.k) v = load_as<float>(pb.A, g.ta ? gl + gi * pb.lda : gi + gl * pb.lda, g.abdt);
-      As[ll][ii] = v;
-      int jj;
-      if (!g.tb) { ll = e & 15; jj = e >> 4; } else { jj = e % T; ll = e / T; }
-      const int64_t gj = j0 + jj;
-      const int64_t gl2 = l0 + ll;
-      float w = 0.f;
-      if (gl2 < pb.k && gj < pb.n) w = load_as<float>(pb.B, g.tb ? gj + gl2 * pb.ldb : gl2 + gj * pb.ldb, g.abdt);
-      Bs[ll][jj] = w;
+  fetch(0);
+  for (int64_t l0 = 0; l0 < pb.k; l0 += GBK) {
+#pragma unroll
+    for (int e = 0; e < NL; ++e) {
+      int ii, ll, jj, lb;
+      a_at(e, ii, ll);
+      As[ll][ii] = ra[e];
+      b_at(e, lb, jj);
+      Bs[lb][jj] = rb[e];
     }
     __syncthreads();
-#pragma unroll
-    for (int l = 0; l < 16; ++l) {
+    if (l0 + GBK < pb.k) fetch(l0 + GBK);
+#pragma unroll 8
+    for (int l = 0; l < GBK; ++l) {
       float av[R], bv[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) av[r] = As[l][tx + 16 * r];
@@ -59,20 +88,36 @@ __device__ __forceinline__ void grouped_tile(const GroupedProblem& pb, int tm, i
     }
     __syncthreads();
   }
+  // epilogue: D = alpha * acc + beta * C (D is FP32); C read per its type
   double dsum = 0.0;
+  const bool has_c = pb.C && g.beta != 0.0;
+  float* D = static_cast<float*>(pb.D);
+  // the storage type of C is uniform: one branch per tile, not per element
+  auto store = [&](auto load_c) {
 #pragma unroll
-  for (int c = 0; c < R; ++c) {
-    const int64_t j = j0 + ty + 16 * c;
-    if (j >= pb.n) continue;
+    for (int c = 0; c < R; ++c) {
+      const int64_t j = j0 + ty + 16 * c;
+      if (j >= pb.n) continue;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int64_t i = i0 + tx + 16 * r;
-      if (i >= pb.m) continue;
-      if (i == j) dsum += (double)acc[r][c];
-      float v = g.alpha_f * acc[r][c];
-      if (pb.C && g.beta != 0.0) v = fmaf(g.beta_f, load_as<float>(pb.C, i + j * pb.ldc, g.cdt), v);
-      store_as<float>(pb.D, i + j * pb.ldd, g.ddt, v);
+      for (int r = 0; r < R; ++r) {
+        const int64_t i = i0 + tx + 16 * r;
+        if (i >= pb.m) continue;
+        if (i == j) dsum += (double)acc[r][c];
+        float v = g.alpha_f * acc[r][c];
+        if (has_c) v = fmaf(g.beta_f, load_c(i + j * pb.ldc), v);
+        D[i + j * pb.ldd] = v;
+      }
     }
+  };
+  if (!has_c || g.cdt == ARMA_F32) {
+    const float* C = static_cast<const float*>(pb.C);
+    store([&](int64_t x) { return C[x]; });
+  } else if (g.cdt == ARMA_BF16) {
+    const __nv_bfloat16* C = static_cast<const __nv_bfloat16*>(pb.C);
+    store([&](int64_t x) { return __bfloat162float(C[x]); });
+  } else {
+    const double* C = static_cast<const double*>(pb.C);
+    store([&](int64_t x) { return (float)C[x]; });
   }
   if (diag_out) {   // diagonal tile: this tile's share of the trace
     double q = 0.0;
@@ -81,9 +126,10 @@ __device__ __forceinline__ void grouped_tile(const GroupedProblem& pb, int tm, i
   }
 }
 
+template <typename AT>
 __global__ void __launch_bounds__(256) grouped_kernel(const __grid_constant__ GroupedArgs g) {
-  __shared__ float As[16][65];
-  __shared__ float Bs[16][65];
+  __shared__ float As[GBK][65];
+  __shared__ float Bs[GBK][65];
   const GroupedProblem* probs = g.probs;
   for (int64_t t = blockIdx.x; t < g.tiles; t += gridDim.x) {
     const uint32_t code = g.tile_code[t];
@@ -91,8 +137,8 @@ __global__ void __launch_bounds__(256) grouped_kernel(const __grid_constant__ Gr
     const GroupedProblem pb = probs[p];
     const int tm = (int)(code >> 16), tn = (int)(code & 0xFFFFu);
     double* dout = (g.trace_partials && tm == tn) ? g.trace_partials + t : nullptr;
-    if (pb.tile == 32) grouped_tile<32>(pb, tm, tn, g, As, Bs, dout);
-    else grouped_tile<64>(pb, tm, tn, g, As, Bs, dout);
+    if (pb.tile == 32) grouped_tile<AT, 32>(pb, tm, tn, g, As, Bs, dout);
+    else grouped_tile<AT, 64>(pb, tm, tn, g, As, Bs, dout);
   }
 }
 
@@ -113,10 +159,19 @@ __global__ void grouped_trace_kernel(const __grid_constant__ GroupedArgs g) {
 
 cudaError_t launch_grouped(const GroupedArgs& g, cudaStream_t s, int* launches) {
   if (g.tiles == 0) return cudaSuccess;
+  if (g.tc) {
+    cudaError_t e = launch_grouped_tc(g, s, launches);
+    if (e != cudaSuccess || !g.trace_partials) return e;
+    grouped_trace_kernel<<<(unsigned)((g.count + 255) / 256), 256, 0, s>>>(g);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+  }
   const int sms = device_sm_count();
   int64_t grid = (int64_t)sms * 8;
   if (grid > g.tiles) grid = g.tiles;
-  grouped_kernel<<<(unsigned)grid, 256, 0, s>>>(g);
+  if (g.abdt == ARMA_BF16) grouped_kernel<__nv_bfloat16><<<(unsigned)grid, 256, 0, s>>>(g);
+  else if (g.abdt == ARMA_F32) grouped_kernel<float><<<(unsigned)grid, 256, 0, s>>>(g);
+  else return cudaErrorInvalidValue;
   if (launches) ++*launches;
   if (g.trace_partials) {
     grouped_trace_kernel<<<(unsigned)((g.count + 255) / 256), 256, 0, s>>>(g);

@@ -137,3 +137,55 @@ def test_batched_benchmark_size_sampled(torch):
     for i in sorted(sample):
         h = [to_host(t) for t in ins[i]]
         check_instance(*inst[i], h, outs[i], "f32")
+
+
+def batch_of(torch, shapes, dtype, seed):
+    inst, host, ins, outs = [], [], [], []
+    for i, (m, n, k) in enumerate(shapes):
+        nodes, o = E.config_batched_instance(m, n, k, dtype)
+        inst.append((nodes, o))
+        A = synth.matrix(seed + i, 1, k, m, dtype)
+        B = synth.matrix(seed + i, 2, k, n, dtype)
+        C = synth.matrix(seed + i, 3, m, n, "f32")
+        host.append([A, B, C])
+        ins.append([to_dev(A, dtype), to_dev(B, dtype), to_dev(C, "f32")])
+        outs.append([ag.empty_colmajor(m, n, torch.float32, "cuda"),
+                     torch.zeros(1, dtype=torch.float64, device="cuda")])
+    return inst, host, ins, outs
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_batched_tensor_core_tiles(torch, dtype):
+    """128 x 128 tcgen05 tiles (BF16 operands; FP32 operands take the SIMT
+    tiles): exact tile, ragged edges in m, n and K, several K blocks, K
+    longer than the 512 of the benchmark, one element"""
+    shapes = [(128, 128, 64), (129, 127, 65), (300, 257, 1000), (1, 1, 1), (8, 300, 3), (256, 5, 130),
+              (640, 384, 16)]
+    inst, host, ins, outs = batch_of(torch, shapes, dtype, 900)
+    bp = ag.BatchedPlan(inst)
+    assert bp.info["tensor_cores"] is (dtype == "bf16")
+    assert bp.info["steps"][0]["kernel"] == ("grouped_tc" if dtype == "bf16" else "grouped")
+    bp.bind(ins, outs, "cuda")
+    bp()
+    torch.cuda.synchronize()
+    assert bp.status()[0] == "ok"
+    for i in range(len(inst)):
+        check_instance(*inst[i], host[i], outs[i], dtype)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_batched_tensor_and_simt_paths_agree(torch, dtype):
+    """the SIMT tiles (PLAN_NO_TENSOR) and the tensor-core tiles meet the
+    same oracle on the same batch"""
+    inst, host, ins, outs = build_batch(torch, 303, 40, dtype)
+    for flags in (0, ag.PLAN_NO_TENSOR):
+        bp = ag.BatchedPlan(inst, flags=flags)
+        assert bp.info["tensor_cores"] is (flags == 0 and dtype == "bf16")
+        bp.bind(ins, outs, "cuda")
+        for o in outs:
+            o[0].fill_(float("nan"))
+            o[1].zero_()
+        bp()
+        torch.cuda.synchronize()
+        for i in range(len(inst)):
+            check_instance(*inst[i], host[i], outs[i], dtype)
