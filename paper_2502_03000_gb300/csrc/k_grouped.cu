@@ -25,9 +25,24 @@ __device__ __forceinline__ float widen(__nv_bfloat16 x) { return __bfloat162floa
 // exactly); the element type is a template parameter so that no load carries
 // conversion code for the other types.  The next K block is fetched into
 // registers while the current one is multiplied out of shared memory.
+constexpr int SROW = 68;  // shared row stride in floats: 16-byte aligned rows for vector reads
+
+// thread (tx, ty) owns rows R tx .. R tx + R - 1 and columns R ty .. R ty + R - 1
+// of the tile, read from shared memory as R-wide vectors
+template <int R>
+__device__ __forceinline__ void ldsR(const float* p, float (&v)[R]) {
+  if constexpr (R == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  }
+}
+
 template <typename AT, int T>   // tile edge: 32 or 64; 256 threads, (T/16)^2 outputs each
 __device__ __forceinline__ void grouped_tile(const GroupedProblem& pb, int tm, int tn, const GroupedArgs& g,
-                                             float (&As)[GBK][65], float (&Bs)[GBK][65], double* diag_out) {
+                                             float (&As)[GBK][SROW], float (&Bs)[GBK][SROW], double* diag_out) {
   constexpr int R = T / 16;             // outputs per thread per dimension
   constexpr int NL = T * GBK / 256;     // elements per thread per operand and K block
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -77,10 +92,8 @@ __device__ __forceinline__ void grouped_tile(const GroupedProblem& pb, int tm, i
 #pragma unroll 8
     for (int l = 0; l < GBK; ++l) {
       float av[R], bv[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) av[r] = As[l][tx + 16 * r];
-#pragma unroll
-      for (int c = 0; c < R; ++c) bv[c] = Bs[l][ty + 16 * c];
+      ldsR<R>(&As[l][R * tx], av);
+      ldsR<R>(&Bs[l][R * ty], bv);
 #pragma unroll
       for (int r = 0; r < R; ++r)
 #pragma unroll
@@ -96,11 +109,11 @@ __device__ __forceinline__ void grouped_tile(const GroupedProblem& pb, int tm, i
   auto store = [&](auto load_c) {
 #pragma unroll
     for (int c = 0; c < R; ++c) {
-      const int64_t j = j0 + ty + 16 * c;
+      const int64_t j = j0 + R * ty + c;
       if (j >= pb.n) continue;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const int64_t i = i0 + tx + 16 * r;
+        const int64_t i = i0 + R * tx + r;
         if (i >= pb.m) continue;
         if (i == j) dsum += (double)acc[r][c];
         float v = g.alpha_f * acc[r][c];
@@ -127,9 +140,9 @@ __device__ __forceinline__ void grouped_tile(const GroupedProblem& pb, int tm, i
 }
 
 template <typename AT>
-__global__ void __launch_bounds__(256) grouped_kernel(const __grid_constant__ GroupedArgs g) {
-  __shared__ float As[GBK][65];
-  __shared__ float Bs[GBK][65];
+__global__ void __launch_bounds__(256, 2) grouped_kernel(const __grid_constant__ GroupedArgs g) {
+  __shared__ __align__(16) float As[GBK][SROW];
+  __shared__ __align__(16) float Bs[GBK][SROW];
   const GroupedProblem* probs = g.probs;
   for (int64_t t = blockIdx.x; t < g.tiles; t += gridDim.x) {
     const uint32_t code = g.tile_code[t];
