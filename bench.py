@@ -315,8 +315,8 @@ def bench_batched(a):
             outs.append([ag.empty_colmajor(mi, ni, torch.float32, dev),
                          torch.zeros(1, dtype=torch.float64, device=dev)])
         t0 = time.perf_counter()
-        bp = ag.BatchedPlan(inst)
-        bp.bind(ins, outs, dev)
+        from paper_2502_03000_gb300 import autotune
+        bp, tuned = autotune.tune(inst, ins, outs, dev)
         plan_s = time.perf_counter() - t0
         for _ in range(3):
             bp()
@@ -337,7 +337,9 @@ def bench_batched(a):
         res[dt] = {"ms_per_batch": ms, "instances_per_s": count / (ms * 1e-3), "tflops": flops / ms / 1e9,
                    "frac_of_fp32_simt_peak": flops / ms / 1e9 / fp32_simt_peak_tflops(),
                    "per_instance_ms": base_ms, "vs_per_instance": base_ms / ms,
-                   "per_instance_planned_steps": launches, "tiles": bp.info["tiles"], "plan_s": plan_s}
+                   "per_instance_planned_steps": launches, "tiles": bp.info["tiles"],
+                   "kernel": bp.info["steps"][0]["kernel"], "tile": bp.info["tile"],
+                   "autotune_ms": tuned, "plan_and_tune_s": plan_s}
         del plans, bp, g, ins, outs
         torch.cuda.empty_cache()
     print(json.dumps({"workload": "10000 x (2*trans(A_i)*B_i+C_i, trace(A_i^T B_i)), m,n,k log-uniform [8,512]",

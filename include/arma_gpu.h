@@ -110,6 +110,8 @@ typedef enum {
 #define ARMA_PLAN_COST_MLP     0x8u  /* rank candidate plans with the learned cost model */
 #define ARMA_PLAN_NO_FUSE      0x10u /* optimised rewrites but no elementwise fusion */
 #define ARMA_PLAN_NO_TENSOR    0x20u /* batched plans: SIMT tiles instead of tensor-core tiles */
+#define ARMA_PLAN_TILE64       0x40u /* batched SIMT tiles: 64 x 64 for every problem */
+#define ARMA_PLAN_TILE32       0x80u /* batched SIMT tiles: 32 x 32 for every problem */
 
 typedef struct arma_node {
   int32_t op;        /* arma_op */

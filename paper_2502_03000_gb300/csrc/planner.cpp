@@ -1489,13 +1489,16 @@ arma_status plan_batched(const arma_expr* exprs, int32_t count, arma_plan* p) {
     // than the SIMT tiles for this size mix (5.5 against 3.7 ms for 10,000
     // problems of 8..512).  SIMT tiles: 32 x 32 runs at about half the
     // efficiency of 64 x 64 per output and wins only when 64-tiles would pad
-    // more than 2x.  ARMA_PLAN_NO_TENSOR keeps BF16 on the SIMT tiles.
+    // more than 2x (ARMA_PLAN_TILE64 / ARMA_PLAN_TILE32 force one shape; the
+    // Python autotuner times these candidates).  ARMA_PLAN_NO_TENSOR keeps
+    // BF16 on the SIMT tiles.
     if (i == 0)
       b.tc = (g.A.trans == 1 && g.B.trans == 0 && g.A.dtype == ARMA_BF16 && !(exprs[0].flags & ARMA_PLAN_NO_TENSOR))
                  ? 1 : 0;
     const int64_t t32 = ((g.m + 31) / 32) * ((g.n + 31) / 32);
     const int64_t t64 = ((g.m + 63) / 64) * ((g.n + 63) / 64);
-    const int32_t T = b.tc ? 128 : (t32 < 2 * t64) ? 32 : 64;
+    const uint32_t fl = exprs[0].flags;
+    const int32_t T = b.tc ? 128 : (fl & ARMA_PLAN_TILE64) ? 64 : (fl & ARMA_PLAN_TILE32) ? 32 : (t32 < 2 * t64) ? 32 : 64;
     b.tile.push_back(T);
     b.first_tile.push_back(b.tiles);
     const int64_t ntm = (g.m + T - 1) / T, ntn = (g.n + T - 1) / T;
@@ -1515,7 +1518,8 @@ arma_status plan_batched(const arma_expr* exprs, int32_t count, arma_plan* p) {
   os << "{\"mode\": \"batched\", \"count\": " << count << ", \"tiles\": " << b.tiles
      << ", \"trace\": " << (b.out_t >= 0 ? "true" : "false") << ", \"flops\": " << p->flops
      << ", \"workspace\": " << p->ws_bytes << ", \"tensor_cores\": " << (b.tc ? "true" : "false")
-     << ", \"tile\": " << (b.tc ? 128 : 0) << ", \"steps\": [{\"kernel\": \"" << (b.tc ? "grouped_tc" : "grouped")
+     << ", \"tile\": " << (b.tc ? 128 : (exprs[0].flags & ARMA_PLAN_TILE64) ? 64 : (exprs[0].flags & ARMA_PLAN_TILE32) ? 32 : 0)
+     << ", \"steps\": [{\"kernel\": \"" << (b.tc ? "grouped_tc" : "grouped")
      << "\"}]}";
   p->log = os.str();
   return ARMA_OK;

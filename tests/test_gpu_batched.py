@@ -189,3 +189,20 @@ def test_batched_tensor_and_simt_paths_agree(torch, dtype):
         torch.cuda.synchronize()
         for i in range(len(inst)):
             check_instance(*inst[i], host[i], outs[i], dtype)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_batched_autotune(torch, dtype):
+    """the autotuner times the distinct tilings of the batch, keeps the
+    fastest, and that plan meets the oracle; a second call with the same
+    batch family reuses the choice"""
+    from paper_2502_03000_gb300 import autotune
+    inst, host, ins, outs = build_batch(torch, 404, 50, dtype)
+    bp, times = autotune.tune(inst, ins, outs, "cuda", reps=2)
+    assert len(times) >= 2 and all(t > 0 for t in times.values())
+    bp()
+    torch.cuda.synchronize()
+    for i in range(len(inst)):
+        check_instance(*inst[i], host[i], outs[i], dtype)
+    bp2, times2 = autotune.tune(inst, ins, outs, "cuda", reps=2)
+    assert len(times2) == 1 and list(times2)[0] == min(times, key=times.get)
