@@ -469,8 +469,28 @@ def bench_plain(a):
     g.replay()
     torch.cuda.synchronize()
     gms = time_ms(g.replay, 200, stream)
+    # the diagonal-only rewrites ranked next (diagmat(A*B), v'*diagmat(B)*w),
+    # at the paper's largest size (n = 1000) and at 256
+    nxt = {}
+    for nn in (256, 1000):
+        hn = [synth.matrix(20250203 + 6, s_ + 1, nn, nn if s_ < 2 else 1, "f64") for s_ in range(4)]
+        dn = [torch.from_numpy(h.T.copy()).to(dev).t() for h in hn]
+        for name, (nodes, outs) in E.config_next(nn, "f64").items():
+            r = {}
+            for mode, flags in (("optimised", 0), ("literal", ag.PLAN_LITERAL)):
+                p_ = ag.Plan(nodes, outs, flags=flags)
+                out = p_.alloc_outputs(dev)
+                p_(*dn, outputs=out)
+                torch.cuda.synchronize()
+                ms = time_ms(lambda: p_(*dn, outputs=out), 100, stream)
+                ref = oracle.evaluate(nodes, outs, hn)[0]
+                got = out[0].double().cpu().numpy()
+                r[mode] = {"us": ms * 1e3, "kernels": [st["kernel"] for st in p_.info["steps"]],
+                           "err_vs_oracle": oracle.rel_err(got, ref)}
+            r["vs_literal"] = r["literal"]["us"] / r["optimised"]["us"]
+            nxt[f"{name}_n{nn}"] = r
     print(json.dumps({"workload": "six expressions over 256x256 FP64 A,B,C,D and v", "results": res,
-                      "graph_replay_us_all_six": gms * 1e3}), flush=True)
+                      "graph_replay_us_all_six": gms * 1e3, "next_rows": nxt}), flush=True)
 
 
 def bench_planner(a):

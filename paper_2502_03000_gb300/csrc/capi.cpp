@@ -109,6 +109,7 @@ arma_status run_step(const Step& st, const Bind& b, cudaStream_t s, int* launche
       a.out = reinterpret_cast<double*>(mptr(b, d.out));
       a.partials = reinterpret_cast<double*>(mptr(b, d.partials));
       a.ticket = tickets + d.ticket;
+      a.per_diag = d.per_diag;
       return cuda_status(launch_diagdot(a, s, launches));
     }
     case ST_TRANSPOSE:

@@ -178,6 +178,7 @@ struct DotStep {
   Ref out;
   Ref partials;
   int32_t ticket = 0;
+  int32_t per_diag = 0;     // 1: out[i] = alpha * (op(A) op(B))_ii for i < min(m, n) (FP64 vector)
 };
 
 struct DotArgs {
@@ -188,9 +189,11 @@ struct DotArgs {
   double* out;
   double* partials;
   unsigned int* ticket;
+  int32_t per_diag;
 };
 
 cudaError_t launch_diagdot(const DotArgs& a, cudaStream_t s, int* launches);
+constexpr int DIAGVEC_MAX_CHUNKS = 16;   // K chunks of the per-diagonal product (partials rows)
 
 // --------------------------------------------------------------------------
 // Literal-plan helpers and the solve

@@ -312,6 +312,61 @@ __global__ void __launch_bounds__(256) diagdot_kernel(const __grid_constant__ Do
   reduce_finish(sum, 0.0, a.partials, a.ticket, a.out, nullptr, a.alpha);
 }
 
+// the diagonal of op(A) op(B) alone (diagmat of a product, Sec. III (4)):
+// a CTA per 32 diagonal elements walks K in 32-wide tiles, read as in the
+// trace kernel; each warp keeps the sums of its rows and reduces them across
+// the K lanes at the end.  out[i] = alpha * sum_l op(A)(i, l) op(B)(l, i).
+// blockIdx.y selects one of gridDim.y K chunks; with more than one chunk
+// the sums go to partials[chunk][i] and diagvec_finish adds them in chunk
+// order (deterministic)
+__global__ void __launch_bounds__(256) diagvec_kernel(const __grid_constant__ DotArgs a) {
+  __shared__ double As[32][33];
+  __shared__ double Bs[32][33];
+  const int64_t d = a.m < a.n ? a.m : a.n;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int64_t kt = (a.k + 31) / 32, per = (kt + gridDim.y - 1) / gridDim.y;
+  const int64_t lb = (int64_t)blockIdx.y * per * 32, le = min(a.k, lb + per * 32);
+  double sum[4] = {0.0, 0.0, 0.0, 0.0};                 // rows ty, ty + 8, ty + 16, ty + 24
+  for (int64_t l0 = lb; l0 < le; l0 += 32) {
+    for (int r = ty; r < 32; r += 8) {
+      int ii = a.ta ? r : tx, ll = a.ta ? tx : r;
+      int64_t gi = i0 + ii, gl = l0 + ll;
+      double v = 0.0;
+      if (gi < d && gl < le) v = load_as<double>(a.A, a.ta ? gl + gi * a.lda : gi + gl * a.lda, a.adt);
+      As[ii][ll] = v;
+      ll = a.tb ? r : tx;
+      ii = a.tb ? tx : r;
+      gi = i0 + ii; gl = l0 + ll;
+      double w = 0.0;
+      if (gi < d && gl < le) w = load_as<double>(a.B, a.tb ? gi + gl * a.ldb : gl + gi * a.ldb, a.bdt);
+      Bs[ii][ll] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sum[q] = fma(As[ty + 8 * q][tx], Bs[ty + 8 * q][tx], sum[q]);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double t = warp_sum(sum[q]);
+    const int64_t i = i0 + ty + 8 * q;
+    if (tx == 0 && i < d) {
+      if (gridDim.y == 1) a.out[i] = a.alpha * t;
+      else a.partials[(int64_t)blockIdx.y * d + i] = t;
+    }
+  }
+}
+
+__global__ void diagvec_finish_kernel(const __grid_constant__ DotArgs a, int chunks) {
+  const int64_t d = a.m < a.n ? a.m : a.n;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d) return;
+  double t = 0.0;
+  for (int c = 0; c < chunks; ++c) t += a.partials[(int64_t)c * d + i];
+  a.out[i] = a.alpha * t;
+}
+
 // ---------------------------------------------------------------------------
 // literal-plan copies
 // ---------------------------------------------------------------------------
@@ -386,7 +441,24 @@ cudaError_t launch_diagdot(const DotArgs& a, cudaStream_t s, int* launches) {
   int64_t cap = (int64_t)device_sm_count() * 8;
   if (cap > kMaxRedBlocks) cap = kMaxRedBlocks;
   int grid = (int)(tiles < 1 ? 1 : tiles > cap ? cap : tiles);
-  diagdot_kernel<<<grid, 256, 0, s>>>(a);
+  if (a.per_diag) {
+    if (d == 0) return cudaSuccess;
+    // K chunks: about 4 CTAs per SM, each chunk at least 128 of K, at most
+    // DIAGVEC_MAX_CHUNKS (the partials buffer holds that many rows of d)
+    const int64_t rb = (d + 31) / 32;
+    int64_t chunks = ((int64_t)device_sm_count() * 4 + rb - 1) / rb;
+    const int64_t cmax = (a.k + 127) / 128;
+    if (chunks > cmax) chunks = cmax;
+    if (chunks > DIAGVEC_MAX_CHUNKS) chunks = DIAGVEC_MAX_CHUNKS;
+    if (chunks < 1 || !a.partials) chunks = 1;
+    diagvec_kernel<<<dim3((unsigned)rb, (unsigned)chunks), 256, 0, s>>>(a);
+    if (chunks > 1) {
+      if (launches) ++*launches;
+      diagvec_finish_kernel<<<(unsigned)((d + 255) / 256), 256, 0, s>>>(a, (int)chunks);
+    }
+  } else {
+    diagdot_kernel<<<grid, 256, 0, s>>>(a);
+  }
   if (launches) ++*launches;
   return cudaGetLastError();
 }

@@ -938,6 +938,60 @@ void Planner::plan_product(int x, MatOperand dest, double alpha_extra, const Mat
     f[i].kind = Factor::DENSE;
     f[i].m = X;
   }
+  // a^T diagmat(X) c (a, c vectors): sum_i a_i X_ii c_i in one strided
+  // elementwise pass with a reduction (Sec. III (7)), no dense diagonal
+  if (!literal_ && f.size() == 3 && f[0].kind == Factor::DENSE && f[0].rows == 1 && f[1].kind == Factor::DIAG &&
+      f[2].kind == Factor::DENSE && f[2].cols == 1 && info_[x].rows == 1 && info_[x].cols == 1) {
+    const int64_t len = f[1].rows;
+    EwStep s;
+    s.m = len;
+    s.n = 1;
+    s.mode = EW_FLAT;
+    s.compute_f64 = dest.dtype == ARMA_F64 ? 1 : 0;
+    // element i of a 1 x len factor / len x 1 factor, as a stride from its base
+    auto stride_of = [](const MatOperand& m, bool row_vec) -> int64_t {
+      return row_vec ? (m.trans ? 1 : m.ld) : (m.trans ? m.ld : 1);
+    };
+    s.in[0].ref = f[0].m.ref; s.in[0].dtype = f[0].m.dtype; s.in[0].rs = stride_of(f[0].m, true); s.in[0].cs = 0;
+    s.in[1].ref = f[1].v.ref; s.in[1].dtype = f[1].v.dtype; s.in[1].rs = f[1].v.inc; s.in[1].cs = 0;
+    s.in[2].ref = f[2].m.ref; s.in[2].dtype = f[2].m.dtype; s.in[2].rs = stride_of(f[2].m, false); s.in[2].cs = 0;
+    s.nin = 3;
+    s.ops[s.nops++] = {EW_LD, 0, 0};
+    s.ops[s.nops++] = {EW_MUL, 1, 0};
+    s.ops[s.nops++] = {EW_MUL, 2, 0};
+    if (alpha != 1.0) s.ops[s.nops++] = {EW_SCAL, 0, alpha};
+    const bool direct = dest.dtype == ARMA_F64;
+    MatOperand acc = direct ? dest : temp_mat(1, 1, ARMA_F64);
+    s.red = 1;
+    s.sum_out = acc.ref;
+    s.partials = ref_ws(alloc_ws(2 * kMaxRedBlocks * sizeof(double)));
+    s.ticket = alloc_ticket();
+    if (!ew_is_flat(s)) s.mode = EW_GRID;
+    Step st;
+    st.kind = ST_EW;
+    st.ew = s;
+    st.flops = 3.0 * (double)len;
+    st.bytes = ew_bytes(s);
+    st.note = "a'*diagmat(X)*c as one diagonal reduction pass (no dense diagonal, no product)";
+    push_step(std::move(st));
+    if (!direct) {   // the FP64 sum stored in the product's element type
+      EwStep c;
+      c.m = 1; c.n = 1;
+      c.mode = EW_GRID;
+      c.in[0].ref = acc.ref; c.in[0].dtype = ARMA_F64; c.in[0].rs = 1; c.in[0].cs = 1;
+      c.nin = 1;
+      c.ops[c.nops++] = {EW_LD, 0, 0};
+      c.out = dest.ref; c.out_ld = dest.ld; c.out_dtype = dest.dtype;
+      Step sc;
+      sc.kind = ST_EW;
+      sc.ew = c;
+      sc.bytes = 8.0 + dtype_size(dest.dtype);
+      sc.note = "sum stored in the result's element type";
+      push_step(std::move(sc));
+    }
+    loc_[x] = dest;
+    return;
+  }
   // leading / trailing diagonal factors become row / column scalings
   VecOperand rs, cs;
   bool has_rs = false, has_cs = false;
@@ -1067,6 +1121,45 @@ MatOperand Planner::materialize(int x) {
     }
     case ARMA_OP_DIAGMAT: {
       const NInfo& v = info_[d.a];
+      const arma_node& ad = nd_[d.a];
+      const bool a_inner = !loc_[d.a].ref.valid() && uses_[d.a] <= 1 && out_of_[d.a] < 0;
+      const bool scaled = ad.op == ARMA_OP_SCALE || ad.op == ARMA_OP_NEG || ad.op == ARMA_OP_DIV_SCALAR;
+      if (!literal_ && a_inner && (ad.op == ARMA_OP_MATMUL || scaled) && v.rows > 1 && v.cols > 1) {
+        // diagmat(s*A*B): only the diagonal of the product (Sec. III (4)),
+        // then the diagonal placed into the zero matrix
+        double alpha = 1.0;
+        std::vector<Factor> f;
+        flatten_product(d.a, alpha, f);
+        bool two_dense = f.size() == 2 && f[0].kind == Factor::DENSE && f[1].kind == Factor::DENSE;
+        if (two_dense) {
+          const int64_t dn = std::min(v.rows, v.cols);
+          MatOperand dv = temp_mat(dn, 1, ARMA_F64);
+          DotStep ds;
+          ds.m = f[0].rows; ds.k = f[0].cols; ds.n = f[1].cols;
+          ds.A = f[0].m; ds.B = f[1].m;
+          ds.alpha = alpha;
+          ds.out = dv.ref;
+          ds.per_diag = 1;
+          ds.partials = ref_ws(alloc_ws((int64_t)DIAGVEC_MAX_CHUNKS * dn * (int64_t)sizeof(double)));
+          Step st;
+          st.kind = ST_DOT;
+          st.dot = ds;
+          st.flops = 2.0 * (double)dn * (double)ds.k;
+          st.bytes = (double)dn * (double)ds.k * (dtype_size(ds.A.dtype) + dtype_size(ds.B.dtype));
+          st.note = "diagmat(A*B) as a diagonal-only product: d_i = sum_l A_il B_li";
+          push_step(std::move(st));
+          Step sb;
+          sb.kind = ST_DIAGBUILD;
+          sb.cm = info_[x].rows; sb.cn = info_[x].cols;
+          sb.csrc = dv;
+          sb.cinc = 1;
+          sb.cdst = dest;
+          sb.bytes = (double)(sb.cm * sb.cn) * dtype_size(dest.dtype);
+          sb.note = "the product's diagonal placed into the result";
+          push_step(std::move(sb));
+          break;
+        }
+      }
       if (v.rows == 1 || v.cols == 1) {
         MatOperand src = materialize(d.a);
         Step st;
@@ -1079,7 +1172,25 @@ MatOperand Planner::materialize(int x) {
         st.note = "diagmat(v) built densely (result needed as a matrix)";
         push_step(std::move(st));
       } else {
-        plan_ew_root(x, &dest, false, Ref(), Ref(), true);
+        // diagmat(X) of any other matrix: X (materialised), its off-diagonal
+        // zeroed in one pass
+        MatOperand src = materialize(d.a);
+        if (err_ != ARMA_OK) break;
+        EwStep s;
+        s.m = info_[x].rows; s.n = info_[x].cols;
+        s.mode = EW_GRID;
+        s.compute_f64 = info_[x].dtype == ARMA_F64 ? 1 : 0;
+        s.in[0].ref = src.ref; s.in[0].rs = 1; s.in[0].cs = src.ld;
+        s.in[0].dtype = src.dtype; s.in[0].flags = EWF_DIAGMASK;
+        s.nin = 1;
+        s.ops[s.nops++] = {EW_LD, 0, 0};
+        s.out = dest.ref; s.out_ld = dest.ld; s.out_dtype = dest.dtype;
+        Step st;
+        st.kind = ST_EW;
+        st.ew = s;
+        st.bytes = ew_bytes(s);
+        st.note = "diagmat of a materialised matrix (off-diagonal zeroed)";
+        push_step(std::move(st));
       }
       break;
     }

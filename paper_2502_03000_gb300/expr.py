@@ -121,6 +121,21 @@ def config_plain(n: int = 256, dtype: str = "f64"):
     return out
 
 
+def config_next(n: int = 256, dtype: str = "f64"):
+    """The diagonal-only rewrites ranked next after the hot path: diagmat(A*B)
+    (Sec. III (4)) and trans(v)*diagmat(B)*w (Sec. III (7)).  Slots: A=0,
+    B=1 (n x n), v=2, w=3 (n x 1)."""
+    out = {}
+    for name in ("diagmatAB", "vdiagBw"):
+        g = Graph()
+        A, B = g.input(0, n, n, dtype), g.input(1, n, n, dtype)
+        v, w = g.input(2, n, 1, dtype), g.input(3, n, 1, dtype)
+        e = {"diagmatAB": lambda: diagmat(A * B),
+             "vdiagBw": lambda: v.t() * diagmat(B) * w}[name]()
+        out[name] = g.build(e)
+    return out
+
+
 def config_fused(n: int = 8192, dtype: str = "f32"):
     """out = A%B + 3*C - D/2 with accu(out) and norm(out,'fro'); slots A..D = 0..3."""
     g = Graph()

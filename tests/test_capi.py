@@ -155,6 +155,16 @@ def test_rewrites_fused_and_chain_and_solve():
     assert kernels(ag.Plan(*E.config_solve(64, 3), flags=ag.PLAN_LITERAL)) == ["solve", "gemm"]
 
 
+def test_rewrites_next_rows():
+    """diagmat(A*B): only the product's diagonal (no GEMM); v'*diagmat(B)*w:
+    one diagonal reduction pass (no dense diagonal, no product)"""
+    plans = {k: kernels(ag.Plan(*v)) for k, v in E.config_next(64).items()}
+    assert plans["diagmatAB"] == ["diagdot", "diagbuild"]
+    assert plans["vdiagBw"] == ["ew"]
+    lit = {k: kernels(ag.Plan(*v, flags=ag.PLAN_LITERAL)) for k, v in E.config_next(64).items()}
+    assert "gemm" in lit["diagmatAB"] and "gemm" in lit["vdiagBw"]
+
+
 def test_fused_program_contracts_products():
     """A%B + 3*C - D/2: the sum is reordered so that the product becomes one
     fused multiply-add and the power-of-two term an exact exponent load:

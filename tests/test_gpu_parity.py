@@ -262,3 +262,94 @@ def test_fused_contracted_sums(torch, dtype):
         nodes, outs = g.build(e, E.accu(e))
         got = run(nodes, outs, host, dtype)
         check(got, oracle.evaluate(nodes, outs, host), TOL[dtype], f"expression {k}")
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("mkn", [(1, 1, 1), (37, 53, 29), (100, 100, 100), (257, 130, 64), (64, 513, 300)])
+def test_diagmat_of_product(torch, dtype, mkn):
+    """diagmat(op(A)*op(B)) from the diagonal alone (Sec. III (4)), every
+    transpose combination and scalar factors, rectangular results included"""
+    m, k, n = mkn
+    for ta in (0, 1):
+        for tb in (0, 1):
+            g = E.Graph()
+            A = g.input(0, k if ta else m, m if ta else k, dtype)
+            B = g.input(1, n if tb else k, k if tb else n, dtype)
+            opA = A.t() if ta else A
+            opB = B.t() if tb else B
+            nodes, outs = g.build(E.diagmat(-0.5 * (opA * opB)))
+            plan = ag.Plan(nodes, outs)
+            if m > 1 and n > 1:   # a 1 x n or m x 1 product is a vector: diagmat builds from it
+                assert [s["kernel"] for s in plan.info["steps"]] == ["diagdot", "diagbuild"]
+            host = inputs(600 + m + n + k + 2 * ta + tb, [(k if ta else m, m if ta else k),
+                                                         (n if tb else k, k if tb else n)], dtype)
+            got = run(nodes, outs, host, dtype)
+            check(got, oracle.evaluate(nodes, outs, host), TOL[dtype], f"{mkn} {ta}{tb}")
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n", [1, 7, 256, 1000, 4099])
+def test_vector_diagmat_vector(torch, dtype, n):
+    """v'*diagmat(B)*w and v'*diagmat(u)*w as one diagonal reduction pass
+    (Sec. III (7)); vectors given as columns or as transposed rows"""
+    for diag_of in ("matrix", "vector"):
+        for vt in (0, 1):
+            g = E.Graph()
+            v = g.input(0, 1, n, dtype) if vt else g.input(0, n, 1, dtype)
+            X = g.input(1, n, n, dtype) if diag_of == "matrix" else g.input(1, n, 1, dtype)
+            w = g.input(2, n, 1, dtype)
+            left = v if vt else v.t()
+            nodes, outs = g.build(3.0 * (left * E.diagmat(X) * w))
+            plan = ag.Plan(nodes, outs)
+            assert plan.info["steps"][0]["kernel"] == "ew"
+            host = inputs(700 + n + vt, [(1, n) if vt else (n, 1), (n, n) if diag_of == "matrix" else (n, 1),
+                                         (n, 1)], dtype)
+            got = run(nodes, outs, host, dtype)
+            ref = oracle.evaluate(nodes, outs, host)
+            # a scalar from n terms: its error is relative to the size of the terms
+            terms = np.abs(np.asarray(host[0], dtype=np.float64).reshape(-1)
+                           * (np.diag(np.asarray(host[1], dtype=np.float64)) if diag_of == "matrix"
+                              else np.asarray(host[1], dtype=np.float64).reshape(-1))
+                           * np.asarray(host[2], dtype=np.float64).reshape(-1)).sum() * 3.0
+            assert abs(float(to_host(got[0]).reshape(-1)[0]) - float(np.asarray(ref[0]).reshape(-1)[0])) <= \
+                TOL[dtype] * max(terms, 1e-300), (diag_of, vt)
+
+
+def test_golden_fixtures_on_gpu(torch):
+    """every hand-computed fixture of the paper's expressions, through the
+    CUDA path in FP64, equals its stored value within the fixture's
+    tolerance (small integers: exactly)"""
+    import glob
+    import json
+    import os
+    for path in sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "*.json"))):
+        fx = json.load(open(path))
+        if "nodes" not in fx:
+            continue
+        nodes = [dict(nd) for nd in fx["nodes"]]
+        for nd in nodes:
+            if nd["op"] == "input":
+                nd.setdefault("dtype", "f64")
+                nd.setdefault("ld", max(1, nd["rows"]))
+        host = [np.array(fx["inputs"][s_], dtype=np.float64) for s_ in fx["slots"]]
+        got = run(nodes, fx["outputs"], host, "f64")
+        for g_, e_ in zip(got, fx["expected"]):
+            e = np.array(e_, dtype=np.float64)
+            v = np.asarray(to_host(g_), dtype=np.float64).reshape(e.shape)
+            tol = max(fx["tol"], 1e-14) * max(1.0, float(np.max(np.abs(e))))
+            assert np.max(np.abs(v - e)) <= tol, (os.path.basename(path), v, e)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_diagmat_of_matrix_expressions(torch, dtype):
+    """diagmat of a matrix that is not a bare product: the matrix, then its
+    off-diagonal zeroed (square and rectangular)"""
+    for (m, n) in [(40, 40), (33, 70), (90, 17)]:
+        g = E.Graph()
+        A, C, D = g.input(0, m, n, dtype), g.input(1, m, n, dtype), g.input(2, m, n, dtype)
+        B = g.input(3, n, n, dtype)
+        host = inputs(800 + m + n, [(m, n), (m, n), (m, n), (n, n)], dtype)
+        for e in (E.diagmat(A), E.diagmat(A + C % D), E.diagmat(A * B + C), E.diagmat(2.0 * (A * B) - C)):
+            nodes, outs = g.build(e)
+            got = run(nodes, outs, host, dtype)
+            check(got, oracle.evaluate(nodes, outs, host), TOL[dtype], f"{m}x{n}")
