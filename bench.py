@@ -469,8 +469,8 @@ def bench_plain(a):
     g.replay()
     torch.cuda.synchronize()
     gms = time_ms(g.replay, 200, stream)
-    # the diagonal-only rewrites ranked next (diagmat(A*B), v'*diagmat(B)*w),
-    # at the paper's largest size (n = 1000) and at 256
+    # the rewrites ranked next (diagmat(A*B), v'*diagmat(B)*w, A(:,1) + B(2,:)'
+    # read as views), at the paper's largest size (n = 1000) and at 256
     nxt = {}
     for nn in (256, 1000):
         hn = [synth.matrix(20250203 + 6, s_ + 1, nn, nn if s_ < 2 else 1, "f64") for s_ in range(4)]

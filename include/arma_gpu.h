@@ -86,7 +86,10 @@ typedef enum {
   ARMA_OP_TRACE = 12,      /* sum of the main diagonal -> FP64 scalar */
   ARMA_OP_ACCU = 13,       /* sum of all elements -> FP64 scalar */
   ARMA_OP_NORM_FRO = 14,   /* sqrt(sum of squares) -> FP64 scalar */
-  ARMA_OP_INV = 15         /* matrix inverse (square a) */
+  ARMA_OP_INV = 15,        /* matrix inverse (square a) */
+  ARMA_OP_SUBMAT = 16      /* view of a: rows [slot, slot + rows), columns [ld, ld + cols)
+                              (node fields: slot = first row, ld = first column, rows x
+                              cols = size); elementwise expressions read it in place */
 } arma_op;
 
 /* Precision tier for products and solves (elementwise work always runs in

@@ -237,6 +237,18 @@ _SCAL = {"scale": scale, "div_scalar": div_scalar, "add_scalar": add_scalar}
 _RED = {"trace": trace, "accu": accu, "norm_fro": norm_fro}
 
 
+def submat(x, r0: int, c0: int, rows: int, cols: int):
+    """The block x(r0 : r0+rows-1, c0 : c0+cols-1) as a new FP64 matrix
+    (Armadillo's submatrix view, Sec. III (2), materialised literally)."""
+    x = f64(x)
+    if r0 < 0 or c0 < 0 or r0 + rows > x.shape[0] or c0 + cols > x.shape[1]:
+        raise ValueError("submatrix outside the matrix")
+    out = np.zeros((rows, cols), order="F")
+    for j in range(cols):
+        out[:, j] = x[r0:r0 + rows, c0 + j]
+    return out
+
+
 def evaluate(nodes, outputs, inputs):
     """Evaluate ``nodes`` literally and return the values of ``outputs``.
 
@@ -266,6 +278,8 @@ def evaluate(nodes, outputs, inputs):
             vals.append(_RED[op](vals[nd["a"]]))
         elif op == "inv":
             vals.append(inv(vals[nd["a"]]))
+        elif op == "submat":
+            vals.append(submat(vals[nd["a"]], nd["slot"], nd["ld"], nd["rows"], nd["cols"]))
         else:
             raise ValueError(f"unknown op {op!r}")
     return [vals[o] for o in outputs]

@@ -35,7 +35,7 @@ F64, F32, BF16 = 0, 1, 2
 DTYPES = {"f64": F64, "f32": F32, "bf16": BF16}
 OPS = {"input": 0, "add": 1, "sub": 2, "schur": 3, "div": 4, "scale": 5, "div_scalar": 6,
        "add_scalar": 7, "neg": 8, "trans": 9, "matmul": 10, "diagmat": 11, "trace": 12,
-       "accu": 13, "norm_fro": 14, "inv": 15}
+       "accu": 13, "norm_fro": 14, "inv": 15, "submat": 16}
 TIERS = {"native": 0, "f64": 1, "split_bf16": 2, "bf16": 3, "lu32_ir64": 4}
 PLAN_LITERAL, PLAN_CHAIN_LEFT, PLAN_CHAIN_GREEDY, PLAN_COST_MLP, PLAN_NO_FUSE, PLAN_NO_TENSOR = 1, 2, 4, 8, 16, 32
 PLAN_TILE64, PLAN_TILE32 = 64, 128

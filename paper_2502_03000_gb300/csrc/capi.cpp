@@ -61,7 +61,7 @@ arma_status run_step(const Step& st, const Bind& b, cudaStream_t s, int* launche
       a.mode = e.mode; a.nin = e.nin; a.nops = e.nops; a.red = e.red;
       a.compute_f64 = e.compute_f64; a.out_dtype = e.out_dtype;
       for (int k = 0; k < e.nin; ++k) {
-        a.in[k] = cptr(b, e.in[k].ref);
+        a.in[k] = static_cast<const char*>(cptr(b, e.in[k].ref)) + e.in[k].off * (int64_t)dtype_size(e.in[k].dtype);
         a.rs[k] = e.in[k].rs; a.cs[k] = e.in[k].cs;
         a.in_dtype[k] = e.in[k].dtype; a.in_flags[k] = e.in[k].flags;
       }

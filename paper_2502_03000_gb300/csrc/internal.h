@@ -82,7 +82,8 @@ enum : int32_t { EWF_DIAGMASK = 1 };  // value is zero off the main diagonal
 
 struct EwOperand {
   Ref ref;
-  int64_t rs = 1, cs = 0;   // element (i, j) at base[i*rs + j*cs]
+  int64_t off = 0;          // element offset of the view from the buffer's base
+  int64_t rs = 1, cs = 0;   // element (i, j) at base[off + i*rs + j*cs]
   int32_t dtype = ARMA_F64;
   int32_t flags = 0;
 };

@@ -150,8 +150,8 @@ bool is_reduction(int op) {
 const char* op_name(int op) {
   static const char* names[] = {"input", "add", "sub", "schur", "div", "scale", "div_scalar",
                                 "add_scalar", "neg", "trans", "matmul", "diagmat", "trace",
-                                "accu", "norm_fro", "inv"};
-  return (op >= 0 && op <= ARMA_OP_INV) ? names[op] : "?";
+                                "accu", "norm_fro", "inv", "submat"};
+  return (op >= 0 && op <= ARMA_OP_SUBMAT) ? names[op] : "?";
 }
 const char* tier_name(int t) {
   static const char* names[] = {"native", "f64", "split_bf16", "bf16", "lu32_ir64"};
@@ -297,7 +297,7 @@ arma_status Planner::validate() {
     const arma_node& d = nd_[i];
     NInfo& I = info_[i];
     char buf[160];
-    if (d.op < 0 || d.op > ARMA_OP_INV) {
+    if (d.op < 0 || d.op > ARMA_OP_SUBMAT) {
       snprintf(buf, sizeof buf, "node %d: unknown op %d", i, d.op);
       return fail(ARMA_ERR_INVALID, buf);
     }
@@ -372,6 +372,17 @@ arma_status Planner::validate() {
       case ARMA_OP_TRACE: case ARMA_OP_ACCU: case ARMA_OP_NORM_FRO:
         I.rows = I.cols = 1; I.dtype = ARMA_F64; I.scalar = true;
         break;
+      case ARMA_OP_SUBMAT: {
+        const int64_t r0 = d.slot, c0 = d.ld;
+        if (r0 < 0 || c0 < 0 || d.rows < 0 || d.cols < 0 || r0 + d.rows > A.rows || c0 + d.cols > A.cols) {
+          snprintf(buf, sizeof buf, "node %d (submat): rows [%lld, %lld) x cols [%lld, %lld) outside %lldx%lld", i,
+                   (long long)r0, (long long)(r0 + d.rows), (long long)c0, (long long)(c0 + d.cols),
+                   (long long)A.rows, (long long)A.cols);
+          return fail(ARMA_ERR_SHAPE, buf);
+        }
+        I.rows = d.rows; I.cols = d.cols; I.dtype = A.dtype;
+        break;
+      }
       case ARMA_OP_INV:
         if (A.rows != A.cols) return fail(ARMA_ERR_SHAPE, "inv needs a square matrix");
         if (A.dtype == ARMA_BF16) return fail(ARMA_ERR_DTYPE, "inv of a BF16 matrix is not supported");
@@ -401,13 +412,17 @@ arma_status Planner::validate() {
 // ---------------------------------------------------------------------------
 // A view that the elementwise kernel can read directly without a pass of
 // its own: an input or materialised matrix, its transpose, or a diagonal.
+// y read in place: an input or a materialised node, seen through a chain of
+// transposes and submatrix views (and at most one diagmat, outermost)
 bool Planner::ew_leafable_view(int y) const {
   const arma_node& d = nd_[y];
   if (d.op == ARMA_OP_INPUT || loc_[y].ref.valid()) return true;
-  if ((d.op == ARMA_OP_TRANS || d.op == ARMA_OP_DIAGMAT) &&
-      (nd_[d.a].op == ARMA_OP_INPUT || loc_[d.a].ref.valid()))
-    return true;
-  return false;
+  int z = y;
+  if (d.op == ARMA_OP_DIAGMAT) z = d.a;
+  while (!loc_[z].ref.valid() && (nd_[z].op == ARMA_OP_TRANS || nd_[z].op == ARMA_OP_SUBMAT)) z = nd_[z].a;
+  if (z == y) return false;
+  return nd_[z].op == ARMA_OP_INPUT || loc_[z].ref.valid() ||
+         (nd_[y].op == ARMA_OP_DIAGMAT && z == d.a);   // diagmat(x): x materialised first
 }
 
 bool Planner::ew_is_leaf(int y, int root) const {
@@ -424,26 +439,38 @@ int Planner::ew_operand(EwBuild& b, int y) {
   if (b.st.nin >= kMaxIn) { b.overflow = true; return 0; }
   EwOperand op;
   const arma_node& d = nd_[y];
-  int base = y;
-  bool tr = false, dg = false;
-  if (!loc_[y].ref.valid() && d.op == ARMA_OP_TRANS) { base = d.a; tr = true; }
-  else if (!loc_[y].ref.valid() && d.op == ARMA_OP_DIAGMAT) { base = d.a; dg = true; }
+  bool dg = false;
+  int top = y;
+  if (!loc_[y].ref.valid() && d.op == ARMA_OP_DIAGMAT) { top = d.a; dg = true; }
+  // the chain of transposes and submatrix views from top down to its base
+  std::vector<int> chain;
+  int base = top;
+  while (!loc_[base].ref.valid() && (nd_[base].op == ARMA_OP_TRANS || nd_[base].op == ARMA_OP_SUBMAT)) {
+    chain.push_back(base);
+    base = nd_[base].a;
+  }
   MatOperand src = materialize(base);
   op.ref = src.ref;
   op.dtype = src.dtype;
-  const NInfo& bi = info_[base];
+  // element (i, j) of the view at base[off + i*rs + j*cs], composed from the base up
+  int64_t off = 0, rs = 1, cs = src.ld;
+  for (auto it = chain.rbegin(); it != chain.rend(); ++it) {
+    const arma_node& v = nd_[*it];
+    if (v.op == ARMA_OP_TRANS) std::swap(rs, cs);
+    else off += (int64_t)v.slot * rs + v.ld * cs;   // SUBMAT: first row, first column
+  }
+  op.off = off;
+  const NInfo& ti = info_[top];
   if (dg) {
     op.flags = EWF_DIAGMASK;
-    if (bi.rows == 1 || bi.cols == 1) {   // vector v -> value v_i on (i, i)
-      op.rs = (bi.rows == 1) ? src.ld : 1;
+    if (ti.rows == 1 || ti.cols == 1) {   // vector v -> value v_i on (i, i)
+      op.rs = (ti.rows == 1) ? cs : rs;
       op.cs = 0;
     } else {
-      op.rs = 1; op.cs = src.ld;
+      op.rs = rs; op.cs = cs;
     }
-  } else if (tr) {
-    op.rs = src.ld; op.cs = 1;
   } else {
-    op.rs = 1; op.cs = src.ld;
+    op.rs = rs; op.cs = cs;
   }
   int k = b.st.nin++;
   b.st.in[k] = op;
@@ -1200,6 +1227,26 @@ MatOperand Planner::materialize(int x) {
                  "inv(A) needed as a matrix");
       break;
     }
+    case ARMA_OP_SUBMAT: {
+      // a view needed as a matrix of its own: one copy pass reading it in place
+      EwBuild b;
+      const int k = ew_operand(b, x);
+      if (b.overflow || err_ != ARMA_OK) { if (err_ == ARMA_OK) fail(ARMA_ERR_UNSUPPORTED, "submat view"); break; }
+      EwStep& s = b.st;
+      s.ops[s.nops++] = {EW_LD, k, 0};
+      s.m = info_[x].rows; s.n = info_[x].cols;
+      s.mode = EW_FLAT;
+      s.compute_f64 = info_[x].dtype == ARMA_F64 ? 1 : 0;
+      s.out = dest.ref; s.out_ld = dest.ld; s.out_dtype = dest.dtype;
+      if (!ew_is_flat(s)) s.mode = EW_GRID;
+      Step st;
+      st.kind = ST_EW;
+      st.ew = s;
+      st.bytes = ew_bytes(s);
+      st.note = "submatrix view copied (result needed as a matrix)";
+      push_step(std::move(st));
+      break;
+    }
     default: {
       if (!is_ew_op(d.op)) { fail(ARMA_ERR_UNSUPPORTED, "cannot materialise node"); break; }
       // 2*A*B + C and friends: one product term plus an elementwise rest
@@ -1488,6 +1535,23 @@ void Planner::literal() {
     } else if (d.op == ARMA_OP_INV) {
       emit_solve(loc_[d.a], info_[x].rows, nullptr, info_[x].rows, dest, info_[x].dtype, true,
                  "literal explicit inverse");
+    } else if (d.op == ARMA_OP_SUBMAT) {
+      EwStep s;
+      s.m = info_[x].rows; s.n = info_[x].cols;
+      s.mode = EW_GRID;
+      s.compute_f64 = info_[x].dtype == ARMA_F64 ? 1 : 0;
+      s.in[0].ref = loc_[d.a].ref; s.in[0].rs = 1; s.in[0].cs = loc_[d.a].ld;
+      s.in[0].off = (int64_t)d.slot + d.ld * loc_[d.a].ld;
+      s.in[0].dtype = loc_[d.a].dtype;
+      s.nin = 1;
+      s.ops[s.nops++] = {EW_LD, 0, 0};
+      s.out = dest.ref; s.out_ld = dest.ld; s.out_dtype = dest.dtype;
+      Step st;
+      st.kind = ST_EW;
+      st.ew = s;
+      st.bytes = ew_bytes(s);
+      st.note = "literal submatrix copy";
+      push_step(std::move(st));
     }
     loc_[x] = dest;
   }

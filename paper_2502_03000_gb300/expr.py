@@ -28,6 +28,24 @@ class Graph:
     def build(self, *outs: "X"):
         return [dict(d) for d in self.nodes], [o.i for o in outs]
 
+    def shape(self, i: int) -> tuple[int, int]:
+        """(rows, cols) of node i."""
+        d = self.nodes[i]
+        op = d["op"]
+        if op in ("input", "submat"):
+            return d["rows"], d["cols"]
+        if op == "trans":
+            r, c = self.shape(d["a"])
+            return c, r
+        if op == "matmul":
+            return self.shape(d["a"])[0], self.shape(d["b"])[1]
+        if op == "diagmat":
+            r, c = self.shape(d["a"])
+            return (r * c, r * c) if r == 1 or c == 1 else (r, c)
+        if op in ("trace", "accu", "norm_fro"):
+            return 1, 1
+        return self.shape(d["a"])
+
 
 class X:
     __array_priority__ = 1000
@@ -63,6 +81,21 @@ class X:
 
     def __matmul__(self, o):
         return self._bin("matmul", o)
+
+    def sub(self, r0: int, c0: int, rows: int, cols: int):
+        """Submatrix view: rows r0 .. r0+rows-1, columns c0 .. c0+cols-1."""
+        return self.g._add({"op": "submat", "a": self.i, "slot": int(r0), "ld": int(c0),
+                            "rows": int(rows), "cols": int(cols)})
+
+    def col(self, j: int):
+        """Column j as an m x 1 view (Armadillo's A.col(j) / A(:, j))."""
+        m, _ = self.g.shape(self.i)
+        return self.sub(0, j, m, 1)
+
+    def row(self, i: int):
+        """Row i as a 1 x n view (Armadillo's A.row(i) / A(i, :))."""
+        _, n = self.g.shape(self.i)
+        return self.sub(i, 0, 1, n)
 
     def __mod__(self, o):
         return self._bin("schur", o)
@@ -122,16 +155,17 @@ def config_plain(n: int = 256, dtype: str = "f64"):
 
 
 def config_next(n: int = 256, dtype: str = "f64"):
-    """The diagonal-only rewrites ranked next after the hot path: diagmat(A*B)
-    (Sec. III (4)) and trans(v)*diagmat(B)*w (Sec. III (7)).  Slots: A=0,
-    B=1 (n x n), v=2, w=3 (n x 1)."""
+    """The rewrites ranked next after the hot path: diagmat(A*B) (Sec. III
+    (4)), trans(v)*diagmat(B)*w (Sec. III (7)) and A(:,1) + B(2,:)^T read as
+    views (Sec. III (2)).  Slots: A=0, B=1 (n x n), v=2, w=3 (n x 1)."""
     out = {}
-    for name in ("diagmatAB", "vdiagBw"):
+    for name in ("diagmatAB", "vdiagBw", "colrow"):
         g = Graph()
         A, B = g.input(0, n, n, dtype), g.input(1, n, n, dtype)
         v, w = g.input(2, n, 1, dtype), g.input(3, n, 1, dtype)
         e = {"diagmatAB": lambda: diagmat(A * B),
-             "vdiagBw": lambda: v.t() * diagmat(B) * w}[name]()
+             "vdiagBw": lambda: v.t() * diagmat(B) * w,
+             "colrow": lambda: A.col(1) + B.row(2).t()}[name]()
         out[name] = g.build(e)
     return out
 

@@ -161,8 +161,28 @@ def test_rewrites_next_rows():
     plans = {k: kernels(ag.Plan(*v)) for k, v in E.config_next(64).items()}
     assert plans["diagmatAB"] == ["diagdot", "diagbuild"]
     assert plans["vdiagBw"] == ["ew"]
+    assert plans["colrow"] == ["ew"]
     lit = {k: kernels(ag.Plan(*v, flags=ag.PLAN_LITERAL)) for k, v in E.config_next(64).items()}
     assert "gemm" in lit["diagmatAB"] and "gemm" in lit["vdiagBw"]
+
+
+def test_submatrix_views_in_place():
+    """A(:,1) + B(2,:)^T (Sec. III (2)) is one strided pass reading both
+    views in place; the literal plan copies both and transposes; views
+    outside the matrix are shape errors"""
+    g = E.Graph()
+    A, B = g.input(0, 50, 50), g.input(1, 50, 50)
+    nodes, outs = g.build(A.col(1) + B.row(2).t())
+    p = ag.Plan(nodes, outs)
+    assert kernels(p) == ["ew"] and "strided" in p.info["steps"][0]["note"]
+    assert kernels(ag.Plan(nodes, outs, flags=ag.PLAN_LITERAL)) == ["ew", "ew", "transpose", "ew"]
+    g = E.Graph()
+    A = g.input(0, 10, 10)
+    for bad in ((5, 0, 6, 1), (0, 9, 1, 2), (-1, 0, 1, 1)):
+        nodes, outs = g.build(A.sub(*bad) * 2.0)
+        with pytest.raises(ag.ArmaError) as ei:
+            ag.Plan(nodes, outs)
+        assert ei.value.status == "shape"
 
 
 def test_fused_program_contracts_products():

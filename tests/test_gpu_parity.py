@@ -353,3 +353,63 @@ def test_diagmat_of_matrix_expressions(torch, dtype):
             nodes, outs = g.build(e)
             got = run(nodes, outs, host, dtype)
             check(got, oracle.evaluate(nodes, outs, host), TOL[dtype], f"{m}x{n}")
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n", [1, 100, 250, 1000])
+def test_column_plus_transposed_row(torch, dtype, n):
+    """C = A(:,1) + B(2,:)^T (Sec. III (2)) read in place, one pass"""
+    g = E.Graph()
+    A, B = g.input(0, n, max(n, 2), dtype), g.input(1, max(n, 3), n, dtype)
+    nodes, outs = g.build(A.col(1) + B.row(2).t())
+    host = inputs(900 + n, [(n, max(n, 2)), (max(n, 3), n)], dtype)
+    ref = oracle.evaluate(nodes, outs, host)
+    for flags in (0, ag.PLAN_LITERAL):
+        check(run(nodes, outs, host, dtype, flags), ref, TOL[dtype], f"n={n} flags={flags}")
+
+
+@pytest.mark.parametrize("layout", [dict(), dict(pad=5, offset=3)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_submatrix_views(torch, dtype, layout):
+    """ragged blocks at odd offsets, transposed views, views of views and
+    of transposes, reductions over views, views in products; inputs with a
+    padded leading dimension and a misaligned start"""
+    m, n = 203, 171
+    ld = m + layout.get("pad", 0)
+    g = E.Graph()
+    A, B, C = (g.input(s, m, n, dtype, ld=ld) for s in range(3))
+    Q = g.input(3, n, m, dtype, ld=n + layout.get("pad", 0))
+    host = inputs(950, [(m, n), (m, n), (m, n), (n, m)], dtype)
+    va, vb = A.sub(3, 7, 150, 101), B.sub(50, 70, 150, 101)
+    cases = {
+        "block": 2.0 * va - vb,
+        "fused": va % vb + 3.0 * C.sub(1, 1, 150, 101),
+        "transposed": A.sub(5, 9, 60, 140).t() + Q.sub(9, 5, 140, 60),
+        "view_of_view": A.sub(10, 10, 120, 120).sub(7, 3, 80, 90) * 0.5,
+        "view_of_transpose": A.t().sub(11, 17, 100, 150) - Q.sub(0, 1, 100, 150),
+        "column_row": A.col(n - 1).sub(0, 0, n, 1) + C.row(m - 1).t(),
+        "product": A.sub(0, 0, 100, 171) * Q.sub(0, 3, 171, 90),
+        "product_transposed": va.t() * vb,
+    }
+    for name, e in cases.items():
+        nodes, outs = g.build(e, E.accu(e), E.norm_fro(e))
+        ref = oracle.evaluate(nodes, outs, host)
+        for flags in (0, ag.PLAN_LITERAL):
+            got = run(nodes, outs, host, dtype, flags, **layout)
+            check(got, ref, TOL[dtype] * (10 if name.startswith("product") else 1), f"{name} flags={flags}")
+
+
+def test_empty_and_whole_views(torch):
+    """a 0-column view gives an empty result and zero reductions; a view of
+    the whole matrix is the matrix"""
+    g = E.Graph()
+    A = g.input(0, 40, 30)
+    host = inputs(990, [(40, 30)], "f64")
+    nodes, outs = g.build(A.sub(0, 0, 40, 30) * 3.0, E.accu(A.sub(0, 0, 40, 30)))
+    check(run(nodes, outs, host, "f64"), oracle.evaluate(nodes, outs, host), TOL["f64"], "whole")
+    g = E.Graph()
+    A = g.input(0, 40, 30)
+    v = A.sub(5, 30, 10, 0)
+    nodes, outs = g.build(v * 2.0, E.accu(v))
+    got = run(nodes, outs, host, "f64")
+    assert got[0].shape == (10, 0) and to_host(got[1]) == 0.0

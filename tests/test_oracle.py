@@ -228,3 +228,18 @@ def test_exact_fraction_inverse(orc):
         return r[0][0] * r[1][1] - r[0][1] * r[1][0]
     exact = [[Fraction((-1) ** (i + j) * minor(j, i), d) for j in range(3)] for i in range(3)]
     np.testing.assert_allclose(orc.inv(A), np.array(exact, dtype=np.float64), rtol=0, atol=1e-15)
+
+
+def test_submat_against_index_arithmetic(orc):
+    """the oracle's submatrix equals element-by-element index arithmetic on
+    the column-major storage (a different route from its own slicing)"""
+    rng = np.random.default_rng(12)
+    for (m, n, r0, c0, rows, cols) in [(5, 7, 1, 2, 3, 4), (4, 4, 0, 0, 4, 4), (6, 3, 5, 2, 1, 1), (3, 8, 0, 7, 3, 1)]:
+        x = np.asfortranarray(rng.standard_normal((m, n)))
+        flat = x.ravel(order="F")
+        got = orc.submat(x, r0, c0, rows, cols)
+        for j in range(cols):
+            for i in range(rows):
+                assert got[i, j] == flat[(r0 + i) + (c0 + j) * m]
+    with pytest.raises(ValueError):
+        orc.submat(np.zeros((3, 3)), 2, 0, 2, 1)

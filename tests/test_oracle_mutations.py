@@ -18,6 +18,7 @@ PINS = [
     T.test_small_integer_brute_force, T.test_accu_vs_fsum_and_dot, T.test_norm_fro,
     T.test_matmul_vs_numpy_and_transpose_identity, T.test_trace_invariants, T.test_diagmat,
     T.test_inverse, T.test_solve_literal_and_backward_error, T.test_exact_fraction_inverse,
+    T.test_submat_against_index_arithmetic,
 ]
 
 
@@ -81,6 +82,13 @@ def _mut_schur_as_add(a, b):
     return oracle.f64(a) + oracle.f64(b)
 
 
+def _mut_submat_row_major(x, r0, c0, rows, cols):
+    # first row and first column swapped (a row-major reading of the offsets)
+    x = oracle.f64(x)
+    r0, c0 = min(c0, x.shape[0] - rows), min(r0, x.shape[1] - cols)
+    return np.asfortranarray(x[r0:r0 + rows, c0:c0 + cols])
+
+
 MUTANTS = {
     "matmul_transposed_operand": ("matmul", _mut_matmul_transposed),
     "matmul_dropped_term": ("matmul", _mut_matmul_dropped_term),
@@ -91,6 +99,7 @@ MUTANTS = {
     "inv_without_pivoting": ("inv", _mut_inv_no_pivot),
     "norm_without_sqrt": ("norm_fro", _mut_norm_no_sqrt),
     "schur_as_sum": ("schur", _mut_schur_as_add),
+    "submat_offsets_swapped": ("submat", _mut_submat_row_major),
 }
 
 
