@@ -470,14 +470,18 @@ def bench_plain(a):
     torch.cuda.synchronize()
     gms = time_ms(g.replay, 200, stream)
     # the rewrites ranked next (diagmat(A*B), v'*diagmat(B)*w, A(:,1) + B(2,:)'
-    # read as views), at the paper's largest size (n = 1000) and at 256
+    # read as views, A*A' as a symmetric product), at the paper's largest size
+    # (n = 1000) and at 256
     nxt = {}
     for nn in (256, 1000):
         hn = [synth.matrix(20250203 + 6, s_ + 1, nn, nn if s_ < 2 else 1, "f64") for s_ in range(4)]
         dn = [torch.from_numpy(h.T.copy()).to(dev).t() for h in hn]
         for name, (nodes, outs) in E.config_next(nn, "f64").items():
             r = {}
-            for mode, flags in (("optimised", 0), ("literal", ag.PLAN_LITERAL)):
+            modes = (("optimised", 0), ("literal", ag.PLAN_LITERAL))
+            if name == "AAt":   # and the general product with the transpose folded
+                modes += (("no_syrk", ag.PLAN_NO_SYRK),)
+            for mode, flags in modes:
                 p_ = ag.Plan(nodes, outs, flags=flags)
                 out = p_.alloc_outputs(dev)
                 p_(*dn, outputs=out)

@@ -115,6 +115,10 @@ typedef enum {
 #define ARMA_PLAN_NO_TENSOR    0x20u /* batched plans: SIMT tiles instead of tensor-core tiles */
 #define ARMA_PLAN_TILE64       0x40u /* batched SIMT tiles: 64 x 64 for every problem */
 #define ARMA_PLAN_TILE32       0x80u /* batched SIMT tiles: 32 x 32 for every problem */
+#define ARMA_PLAN_NO_SYRK      0x100u /* products X*X^T and X^T*X as general products (the
+                                         paper's semi-optimised mapping to xGEMM, Sec. III (8));
+                                         by default only their lower triangle is computed and
+                                         then mirrored (xSYRK, Sec. II run-time analysis) */
 
 typedef struct arma_node {
   int32_t op;        /* arma_op */

@@ -38,7 +38,7 @@ OPS = {"input": 0, "add": 1, "sub": 2, "schur": 3, "div": 4, "scale": 5, "div_sc
        "accu": 13, "norm_fro": 14, "inv": 15, "submat": 16}
 TIERS = {"native": 0, "f64": 1, "split_bf16": 2, "bf16": 3, "lu32_ir64": 4}
 PLAN_LITERAL, PLAN_CHAIN_LEFT, PLAN_CHAIN_GREEDY, PLAN_COST_MLP, PLAN_NO_FUSE, PLAN_NO_TENSOR = 1, 2, 4, 8, 16, 32
-PLAN_TILE64, PLAN_TILE32 = 64, 128
+PLAN_TILE64, PLAN_TILE32, PLAN_NO_SYRK = 64, 128, 256
 STATUS = {0: "ok", 1: "invalid", 2: "shape", 3: "dtype", 4: "align", 5: "workspace",
           6: "singular", 7: "noconverge", 8: "cuda", 9: "unsupported"}
 

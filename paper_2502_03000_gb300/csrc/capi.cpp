@@ -96,6 +96,9 @@ arma_status run_step(const Step& st, const Bind& b, cudaStream_t s, int* launche
       a.scratch = g.scratch.valid() ? mptr(b, g.scratch) : nullptr;
       a.scratch_bytes = g.scratch_bytes;
       a.status = reinterpret_cast<int32_t*>(b.ws);
+      // the run-time half of the symmetric-product check: two slots bound
+      // to the same memory (launch_gemm re-checks every condition)
+      a.sym = g.sym == 1 || (g.sym == 2 && a.A == a.B) ? 1 : 0;
       return cuda_status(launch_gemm(a, s, launches));
     }
     case ST_DOT: {

@@ -146,6 +146,12 @@ struct GemmStep {
   double alpha = 1.0, beta = 0.0;
   VecOperand rowscale, colscale;  // optional
   int32_t tier = ARMA_TIER_F64;
+  // symmetric product op(A) op(B) = X X^T or X^T X (the paper's run-time
+  // analysis that maps A*A^T to xSYRK, Sec. II): 1 when both operands are the
+  // same value, one of them transposed (known when planning); 2 when they are
+  // two input slots of the same shape and layout, decided at evaluation by
+  // comparing the bound pointers
+  int32_t sym = 0;
   Ref scratch;              // workspace for operand conversion / split-K partials
   int64_t scratch_bytes = 0;
 };
@@ -163,6 +169,8 @@ struct GemmArgs {
   void* scratch; int64_t scratch_bytes;
   int32_t* status;   // workspace status word (device-side failures)
   const int* skip;   // optional: the kernels return at once when *skip != 0
+  int32_t sym;       // 1: A == B, lda == ldb, ta != tb, no C or scalings: only the
+                     // lower-triangle tiles are computed, the rest is mirrored
 };
 
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s, int* launches);
@@ -205,6 +213,9 @@ struct CopyArgs {  // transpose / diagonal build
   void* dst; int64_t ldd; int32_t ddt;
 };
 cudaError_t launch_transpose(const CopyArgs& a, cudaStream_t s, int* launches);
+// D(i, j) = D(j, i) for i < j: the strictly upper triangle of an n x n matrix
+// from its lower triangle (the second half of a symmetric product)
+cudaError_t launch_mirror_lower(void* D, int64_t n, int64_t ldd, int32_t ddt, cudaStream_t s, int* launches);
 cudaError_t launch_diag_build(const CopyArgs& a, cudaStream_t s, int* launches);
 
 // X = inv(A) * B  (n x n, n x nrhs) by blocked LU with partial pivoting

@@ -31,7 +31,16 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const __grid_constant__ 
   __shared__ AT As[BK][BM + 1];
   __shared__ AT Bs[BK][BN + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int64_t i0 = (int64_t)blockIdx.x * BM, j0 = (int64_t)blockIdx.y * BN;
+  int64_t ti = blockIdx.x, tj = blockIdx.y;
+  if (a.sym) {
+    // lower-triangle tiles only, row by row: tile row ti holds ti + 1 tiles
+    const int64_t b = blockIdx.x;
+    ti = (int64_t)((sqrtf(8.f * (float)b + 1.f) - 1.f) * 0.5f);
+    while (ti * (ti + 1) / 2 > b) --ti;
+    while ((ti + 1) * (ti + 2) / 2 <= b) ++ti;
+    tj = b - ti * (ti + 1) / 2;
+  }
+  const int64_t i0 = ti * BM, j0 = tj * BN;
   const int64_t kchunk = (a.k + gridDim.z - 1) / gridDim.z;
   const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
   const int64_t kend = kbeg + kchunk < a.k ? kbeg + kchunk : a.k;
@@ -111,6 +120,7 @@ __global__ void __launch_bounds__(256) gemm_simt_combine_kernel(const __grid_con
   const double* P = static_cast<const double*>(a.scratch);
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = t / a.m, i = t - j * a.m;
+    if (a.sym && i < j) continue;   // not computed; mirrored afterwards
     double s = 0.0;
     for (int z = 0; z < splits; ++z) s += P[(int64_t)z * total + t];
     double v = a.alpha * s;
@@ -121,12 +131,24 @@ __global__ void __launch_bounds__(256) gemm_simt_combine_kernel(const __grid_con
   }
 }
 
+// The K split minimises the busiest SM's share of the multiply-adds (the
+// FP64 pipe does 2 per SM and clock here, so even a 64 x 64 x 16 piece is
+// 32k clocks) plus the combine pass: s partial sums written and read back at
+// HBM speed and one more launch, all in SM clocks.  Every K piece is at
+// least one BK block, and the partial sums stay within 256 MB.
 int simt_splits(int64_t m, int64_t n, int64_t k) {
+  constexpr int64_t SMS = 152;
   const int64_t tiles = ((m + BM - 1) / BM) * ((n + BN - 1) / BN);
-  const int64_t want = 2 * (int64_t)152;
-  int64_t s = 1;
-  while (tiles * s < want && k / (s * 2) >= 4 * BK && s < 32) s *= 2;
-  return (int)s;
+  int best = 1;
+  double best_cost = 0.0;
+  for (int s = 1; s <= 64; s *= 2) {
+    if (s > 1 && ((k + s - 1) / s < BK || (double)s * (double)m * (double)n * 8.0 > 256e6)) break;
+    const int64_t waves = (tiles * s + SMS - 1) / SMS;
+    double cost = (double)waves * (double)((k + s - 1) / s) * (BM * BN / 2);
+    if (s > 1) cost += (double)s * (double)m * (double)n * 16.0 * 3.04e-4 + 4000.0;
+    if (s == 1 || cost < best_cost) { best = s; best_cost = cost; }
+  }
+  return best;
 }
 
 // ---------------------------------------------------------------------------
@@ -396,7 +418,39 @@ __global__ void __launch_bounds__(256) diag_build_kernel(const __grid_constant__
   }
 }
 
+// D(i, j) = D(j, i) for i < j, in 32 x 32 blocks through shared memory: the
+// block of the lower triangle is read along its columns and written
+// transposed into the upper triangle (element bits copied unchanged)
+template <typename E>
+__global__ void __launch_bounds__(256) mirror_lower_kernel(E* D, int64_t n, int64_t ldd) {
+  __shared__ E t[32][33];
+  const int64_t bi = blockIdx.y, bj = blockIdx.x;   // destination block (upper: bi <= bj)
+  if (bi > bj) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int q = ty; q < 32; q += 8) {
+    const int64_t r = bj * 32 + tx, c = bi * 32 + q;
+    if (r < n && c < n) t[q][tx] = D[r + c * ldd];
+  }
+  __syncthreads();
+  for (int q = ty; q < 32; q += 8) {
+    const int64_t i = bi * 32 + tx, j = bj * 32 + q;
+    if (i < j && j < n) D[i + j * ldd] = t[tx][q];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_mirror_lower(void* D, int64_t n, int64_t ldd, int32_t ddt, cudaStream_t s, int* launches) {
+  if (n < 2) return cudaSuccess;
+  const int64_t T = (n + 31) / 32;
+  if (T > 65535) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)T, (unsigned)T);
+  if (ddt == ARMA_F64) mirror_lower_kernel<unsigned long long><<<grid, 256, 0, s>>>(static_cast<unsigned long long*>(D), n, ldd);
+  else if (ddt == ARMA_F32) mirror_lower_kernel<unsigned int><<<grid, 256, 0, s>>>(static_cast<unsigned int*>(D), n, ldd);
+  else mirror_lower_kernel<unsigned short><<<grid, 256, 0, s>>>(static_cast<unsigned short*>(D), n, ldd);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
 
 int64_t gemm_simt_scratch_bytes(int64_t m, int64_t n, int64_t k) {
   const int s = simt_splits(m, n, k);
@@ -413,13 +467,21 @@ int64_t gemm_scratch_bytes(const GemmStep& g) {
   return tc > simt ? tc : simt;
 }
 
-cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s, int* launches) {
-  if (a.m == 0 || a.n == 0) return cudaSuccess;
-  if (a.n == 1 || a.m == 1) return launch_gemv(a, s, launches);
+bool gemm_sym_valid(const GemmArgs& a) {
+  return a.sym && a.m == a.n && a.A == a.B && a.lda == a.ldb && a.adt == a.bdt && a.ta != a.tb &&
+         !(a.C && a.beta != 0.0) && !a.rs && !a.cs;
+}
+
+cudaError_t launch_gemm(const GemmArgs& a0, cudaStream_t s, int* launches) {
+  if (a0.m == 0 || a0.n == 0) return cudaSuccess;
+  if (a0.n == 1 || a0.m == 1) return launch_gemv(a0, s, launches);
+  GemmArgs a = a0;
+  a.sym = gemm_sym_valid(a0) ? 1 : 0;   // anything else is a general product
   if (a.tier != ARMA_TIER_F64 && gemm_tc_supported(a)) return launch_gemm_tc(a, s, launches);
   int splits = simt_splits(a.m, a.n, a.k);
   if (splits > 1 && (!a.scratch || a.scratch_bytes < (int64_t)splits * a.m * a.n * 8)) splits = 1;
-  dim3 grid((unsigned)((a.m + BM - 1) / BM), (unsigned)((a.n + BN - 1) / BN), (unsigned)splits);
+  const int64_t tm = (a.m + BM - 1) / BM, tn = (a.n + BN - 1) / BN;
+  dim3 grid((unsigned)(a.sym ? tm * (tm + 1) / 2 : tm), (unsigned)(a.sym ? 1 : tn), (unsigned)splits);
   if (grid.y > 65535) return cudaErrorInvalidConfiguration;
   if (a.tier == ARMA_TIER_F64 || a.adt == ARMA_F64 || a.bdt == ARMA_F64)
     gemm_simt_kernel<double><<<grid, 256, 0, s>>>(a);
@@ -431,6 +493,11 @@ cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s, int* launches) {
     int64_t blocks = (total + 255) / 256, cap = (int64_t)device_sm_count() * 8;
     gemm_simt_combine_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(a, splits);
     if (launches) ++*launches;
+  }
+  if (a.sym) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_mirror_lower(a.D, a.n, a.ldd, a.ddt, s, launches);
   }
   return cudaGetLastError();
 }

@@ -75,13 +75,51 @@ struct Params {
   const void* rs; int64_t rs_inc; int32_t rsdt;
   const void* cs; int64_t cs_inc; int32_t csdt;
   int32_t* status;          // workspace status word (0 = ok)
+  int32_t sym;              // 1: X X^T / X^T X, lower-triangle tiles only (tiles_m == 2 tiles_n)
 };
 
 struct WorkItem {
   int32_t tm, tn, split;
 };
 
+// Symmetric products keep the tiles that reach the lower triangle: tile row
+// tm (rows 128 tm ..) meets tile column tn (columns 256 tn ..) there iff
+// tn <= tm / 2, so row tm holds tm / 2 + 1 tiles and the first x rows hold
+// tri_rows(x) of them.
+__device__ __forceinline__ int32_t tri_rows(int32_t x) {
+  const int32_t y = x >> 1;
+  return (x & 1) ? (y + 1) * (y + 1) : y * (y + 1);
+}
+
+__device__ __forceinline__ WorkItem work_item_sym(const Params& p, int32_t w) {
+  // the same grouping as below, over the lower-triangle tiles: groups of 16
+  // tile rows; inside a group, tile columns in order, each over the group's
+  // rows that reach it
+  const int32_t per_split = tri_rows(p.tiles_m);
+  WorkItem it;
+  it.split = w / per_split;
+  const int32_t r = w - it.split * per_split;
+  const int32_t G = 16;
+  int32_t a = 0;
+  while (a + G < p.tiles_m && tri_rows(a + G) <= r) a += G;
+  const int32_t b = min(a + G, p.tiles_m), gsize = b - a;
+  int32_t q = r - tri_rows(a);
+  const int32_t full = a / 2 + 1;           // columns every row of the group reaches
+  if (q < full * gsize) {
+    it.tn = q / gsize;
+    it.tm = a + q % gsize;
+    return it;
+  }
+  q -= full * gsize;
+  int32_t tn = full;
+  while (q >= b - 2 * tn) { q -= b - 2 * tn; ++tn; }
+  it.tn = tn;
+  it.tm = 2 * tn + q;
+  return it;
+}
+
 __device__ __forceinline__ WorkItem work_item(const Params& p, int32_t w) {
+  if (p.sym) return work_item_sym(p, w);
   // split outermost; inside a split, groups of 16 tile rows sweep the tile
   // columns so that concurrently running CTAs share A and B panels in L2
   const int32_t per_split = p.tiles_m * p.tiles_n;
@@ -113,7 +151,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t kb_total = p.kb_per_split;
-  const int32_t total_work = p.tiles_m * p.tiles_n * p.splits;
+  const int32_t total_work = (p.sym ? tri_rows(p.tiles_m) : p.tiles_m * p.tiles_n) * p.splits;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -555,6 +593,7 @@ struct CombineArgs {
   double alpha, beta;
   const void* rs; int64_t rs_inc; int32_t rsdt;
   const void* cs; int64_t cs_inc; int32_t csdt;
+  int32_t sym;   // partials hold the lower-triangle tiles only
 };
 
 __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ CombineArgs a) {
@@ -562,6 +601,7 @@ __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ Co
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t col = t / a.m, row = t - col * a.m;
+    if (a.sym && row < col) continue;   // mirrored afterwards
     double s = 0.0;
     for (int k = 0; k < a.splits; ++k) s += (double)a.P[(int64_t)k * total + t];
     double r = a.alpha * s;
@@ -583,13 +623,15 @@ struct Geometry {
   int64_t a_bytes, b_bytes, p_bytes;
 };
 
-Geometry geometry(int64_t m, int64_t n, int64_t k, int32_t tier) {
+// sym: op(B)^T is op(A), so one prepared operand serves both TMA maps; its
+// rows are padded to a multiple of both tile heights
+Geometry geometry(int64_t m, int64_t n, int64_t k, int32_t tier, bool sym = false) {
   Geometry g;
   g.terms = tier == ARMA_TIER_SPLIT_BF16 ? 6 : 1;
   g.slices = tier == ARMA_TIER_SPLIT_BF16 ? 3 : 1;
   g.kp = (k + 7) / 8 * 8;
-  g.mpad = (m + BM - 1) / BM * BM;
-  g.npad = (n + BN - 1) / BN * BN;
+  g.mpad = sym ? (m + BN - 1) / BN * BN : (m + BM - 1) / BM * BM;
+  g.npad = sym ? g.mpad : (n + BN - 1) / BN * BN;
   g.tiles_m = (int32_t)(g.mpad / BM);
   g.tiles_n = (int32_t)(g.npad / BN);
   const int64_t kb = (k + BK - 1) / BK;
@@ -605,7 +647,7 @@ Geometry geometry(int64_t m, int64_t n, int64_t k, int32_t tier) {
   if (g.chunk_kb < 1) g.chunk_kb = 1;
   g.nchunks = (g.kb_per_split + g.chunk_kb - 1) / g.chunk_kb;
   g.a_bytes = (int64_t)g.slices * g.mpad * g.kp * 2;
-  g.b_bytes = (int64_t)g.slices * g.npad * g.kp * 2;
+  g.b_bytes = sym ? 0 : (int64_t)g.slices * g.npad * g.kp * 2;
   g.p_bytes = g.splits > 1 ? (int64_t)g.splits * m * n * 4 : 0;
   return g;
 }
@@ -644,7 +686,7 @@ bool gemm_tc_supported(const GemmArgs& a) {
   if (a.m < 1 || a.n < 1 || a.k < 1) return false;
   if (a.m > (1ll << 30) || a.n > (1ll << 30) || a.k > (1ll << 30)) return false;
   if (!a.scratch) return false;
-  tc::Geometry g = tc::geometry(a.m, a.n, a.k, a.tier);
+  tc::Geometry g = tc::geometry(a.m, a.n, a.k, a.tier, a.sym != 0);
   return a.scratch_bytes >= g.a_bytes + g.b_bytes + g.p_bytes + 1024;
 }
 
@@ -657,7 +699,8 @@ int64_t gemm_tc_scratch_bytes(int64_t m, int64_t n, int64_t k, int32_t tier) {
 
 cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   using namespace tc;
-  Geometry g = geometry(a.m, a.n, a.k, a.tier);
+  const bool sym = a.sym != 0;
+  Geometry g = geometry(a.m, a.n, a.k, a.tier, sym);
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(a.scratch) + 255) & ~uintptr_t(255));
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(base);
   __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(base + ((g.a_bytes + 255) / 256) * 256);
@@ -683,14 +726,14 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   PrepArgs pb;
   pb.X = a.B; pb.ldx = a.ldb; pb.xdt = a.bdt; pb.trans = a.tb ? 0 : 1;
   pb.R = a.n; pb.K = a.k; pb.rpad = g.npad; pb.kp = g.kp; pb.slices = g.slices; pb.out = Bs;
-  prep(pb);
-  if (launches) *launches += 2;
+  if (!sym) prep(pb);
+  if (launches) *launches += sym ? 1 : 2;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
 
   CUtensorMap mapA, mapB;
   if (!make_map(&mapA, As, g.kp, (int64_t)g.slices * g.mpad, BM)) return cudaErrorInvalidValue;
-  if (!make_map(&mapB, Bs, g.kp, (int64_t)g.slices * g.npad, BN)) return cudaErrorInvalidValue;
+  if (!make_map(&mapB, sym ? As : Bs, g.kp, (int64_t)g.slices * g.npad, BN)) return cudaErrorInvalidValue;
 
   Params p;
   memset(&p, 0, sizeof p);
@@ -711,6 +754,7 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   p.rs = a.rs; p.rs_inc = a.rs_inc; p.rsdt = a.rsdt;
   p.cs = a.cs; p.cs_inc = a.cs_inc; p.csdt = a.csdt;
   p.status = a.status;
+  p.sym = sym ? 1 : 0;
 
   static bool attr_set[64] = {false};
   int dev = 0;
@@ -721,13 +765,15 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  const int64_t work = (int64_t)g.tiles_m * g.tiles_n * g.splits;
+  const int64_t per_split = sym ? (g.tiles_m / 2) * (int64_t)(g.tiles_m / 2 + 1) : (int64_t)g.tiles_m * g.tiles_n;
+  const int64_t work = per_split * g.splits;
   const int sms = device_sm_count();
   const int grid = (int)(work < sms ? work : sms);
   gemm_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(mapA, mapB, p);
   if (launches) ++*launches;
   e = cudaGetLastError();
-  if (e != cudaSuccess || g.splits == 1) return e;
+  if (e != cudaSuccess) return e;
+  if (g.splits == 1) return sym ? launch_mirror_lower(a.D, a.n, a.ldd, a.ddt, s, launches) : e;
 
   CombineArgs c;
   c.m = a.m; c.n = a.n; c.splits = g.splits; c.P = P;
@@ -736,11 +782,14 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   c.alpha = a.alpha; c.beta = a.beta;
   c.rs = a.rs; c.rs_inc = a.rs_inc; c.rsdt = a.rsdt;
   c.cs = a.cs; c.cs_inc = a.cs_inc; c.csdt = a.csdt;
+  c.sym = sym ? 1 : 0;
   const int64_t total = a.m * a.n;
   int64_t blocks = (total + 255) / 256, cap = (int64_t)sms * 8;
   combine_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(c);
   if (launches) ++*launches;
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !sym) return e;
+  return launch_mirror_lower(a.D, a.n, a.ldd, a.ddt, s, launches);
 }
 
 }  // namespace arma

@@ -771,16 +771,27 @@ void Planner::emit_gemm(int64_t m, int64_t n, int64_t k, const MatOperand& A, co
   int32_t dt = (A.dtype == ARMA_F64 && B.dtype == ARMA_F64) ? ARMA_F64
                : (A.dtype == ARMA_BF16 && B.dtype == ARMA_BF16) ? ARMA_BF16 : ARMA_F32;
   g.tier = product_tier(dt);
+  // Symmetric products (Sec. II run-time analysis, Sec. III (8)): the same
+  // value on both sides, one side transposed, no beta*C and no diagonal
+  // scalings.  The same node is known now; two input slots of the same shape
+  // and layout are compared by pointer at evaluation.
+  if (!literal_ && !(e_.flags & ARMA_PLAN_NO_SYRK) && m == n && m > 1 && A.trans != B.trans &&
+      A.dtype == B.dtype && A.ld == B.ld && !g.C.ref.valid() && !rs && !cs && A.ref.kind == B.ref.kind) {
+    if (A.ref.idx == B.ref.idx) g.sym = 1;
+    else if (A.ref.kind == REF_INPUT) g.sym = 2;
+  }
   g.scratch_bytes = gemm_scratch_bytes(g);
   if (g.scratch_bytes > 0) g.scratch = ref_ws(alloc_ws(g.scratch_bytes));
   Step st;
   st.kind = ST_GEMM;
   st.gemm = g;
-  st.flops = 2.0 * (double)m * (double)n * (double)k;
+  // a symmetric product computes n (n + 1) / 2 of the n^2 dot products
+  st.flops = g.sym == 1 ? (double)m * (double)(m + 1) * (double)k : 2.0 * (double)m * (double)n * (double)k;
   st.bytes = (double)(m * k) * dtype_size(A.dtype) + (double)(k * n) * dtype_size(B.dtype) +
              (double)(m * n) * dtype_size(D.dtype) * (g.C.ref.valid() ? 2.0 : 1.0);
   std::ostringstream os;
-  os << (n == 1 || m == 1 ? "gemv" : "gemm") << " " << m << "x" << n << "x" << k << " op(A)="
+  os << (n == 1 || m == 1 ? "gemv" : g.sym == 1 ? "syrk" : "gemm") << " " << m << "x" << n << "x" << k
+     << (g.sym == 2 ? " (symmetric if both slots hold the same matrix)" : "") << " op(A)="
      << (A.trans ? "T" : "N") << " op(B)=" << (B.trans ? "T" : "N") << " alpha=" << alpha
      << " beta=" << g.beta << (rs ? " rowscale" : "") << (cs ? " colscale" : "") << " tier="
      << tier_name(g.tier) << " (" << why << ")";
@@ -1594,7 +1605,8 @@ arma_status Planner::run() {
     p_.bytes += s.bytes;
     std::string note = s.note;
     for (auto& ch : note) if (ch == '"') ch = '\'';
-    os << (i ? ", " : "") << "{\"kernel\": \"" << kn[s.kind] << "\", \"flops\": " << s.flops
+    const char* kname = (s.kind == ST_GEMM && s.gemm.sym == 1 && s.gemm.m > 1) ? "syrk" : kn[s.kind];
+    os << (i ? ", " : "") << "{\"kernel\": \"" << kname << "\", \"flops\": " << s.flops
        << ", \"bytes\": " << s.bytes << ", \"note\": \"" << note << "\"}";
   }
   os << "], \"flops\": " << p_.flops << ", \"bytes\": " << p_.bytes << "}";

@@ -156,16 +156,18 @@ def config_plain(n: int = 256, dtype: str = "f64"):
 
 def config_next(n: int = 256, dtype: str = "f64"):
     """The rewrites ranked next after the hot path: diagmat(A*B) (Sec. III
-    (4)), trans(v)*diagmat(B)*w (Sec. III (7)) and A(:,1) + B(2,:)^T read as
-    views (Sec. III (2)).  Slots: A=0, B=1 (n x n), v=2, w=3 (n x 1)."""
+    (4)), trans(v)*diagmat(B)*w (Sec. III (7)), A(:,1) + B(2,:)^T read as
+    views (Sec. III (2)) and the symmetric product A*A^T (Sec. III (8)).
+    Slots: A=0, B=1 (n x n), v=2, w=3 (n x 1)."""
     out = {}
-    for name in ("diagmatAB", "vdiagBw", "colrow"):
+    for name in ("diagmatAB", "vdiagBw", "colrow", "AAt"):
         g = Graph()
         A, B = g.input(0, n, n, dtype), g.input(1, n, n, dtype)
         v, w = g.input(2, n, 1, dtype), g.input(3, n, 1, dtype)
         e = {"diagmatAB": lambda: diagmat(A * B),
              "vdiagBw": lambda: v.t() * diagmat(B) * w,
-             "colrow": lambda: A.col(1) + B.row(2).t()}[name]()
+             "colrow": lambda: A.col(1) + B.row(2).t(),
+             "AAt": lambda: A * A.t()}[name]()
         out[name] = g.build(e)
     return out
 

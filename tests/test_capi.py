@@ -162,8 +162,32 @@ def test_rewrites_next_rows():
     assert plans["diagmatAB"] == ["diagdot", "diagbuild"]
     assert plans["vdiagBw"] == ["ew"]
     assert plans["colrow"] == ["ew"]
+    assert plans["AAt"] == ["syrk"]
     lit = {k: kernels(ag.Plan(*v, flags=ag.PLAN_LITERAL)) for k, v in E.config_next(64).items()}
     assert "gemm" in lit["diagmatAB"] and "gemm" in lit["vdiagBw"]
+
+
+def test_symmetric_products_plan():
+    """X*X^T and X^T*X (Sec. III (8)) plan as a symmetric product when the
+    same value sits on both sides; a beta*C term, a different operand or
+    the no-syrk flag give a general product; two input slots are marked for
+    the pointer comparison at evaluation"""
+    g = E.Graph()
+    A, B = g.input(0, 50, 30), g.input(1, 50, 30)
+    X = A + B
+    for e in (A * A.t(), A.t() * A, 2.0 * (A * A.t()), X * X.t()):
+        nodes, outs = g.build(e)
+        assert kernels(ag.Plan(nodes, outs))[-1] == "syrk"
+        assert kernels(ag.Plan(nodes, outs, flags=ag.PLAN_NO_SYRK))[-1] == "gemm"
+        assert "syrk" not in kernels(ag.Plan(nodes, outs, flags=ag.PLAN_LITERAL))
+    nodes, outs = g.build(A * A.t() + g.input(2, 50, 50))
+    assert kernels(ag.Plan(nodes, outs)) == ["gemm"]
+    nodes, outs = g.build(A * B.t())
+    p = ag.Plan(nodes, outs)
+    assert kernels(p) == ["gemm"] and "symmetric if both slots" in p.info["steps"][0]["note"]
+    nodes, outs = g.build(A * A.t())
+    p = ag.Plan(nodes, outs)
+    assert p.info["steps"][0]["flops"] == 50 * 51 * 30
 
 
 def test_submatrix_views_in_place():
