@@ -493,6 +493,29 @@ def bench_plain(a):
                            "err_vs_oracle": oracle.rel_err(got, ref)}
             r["vs_literal"] = r["literal"]["us"] / r["optimised"]["us"]
             nxt[f"{name}_n{nn}"] = r
+    # solve(A, b) with A tridiagonal (Sec. III (10)) at the paper's sizes:
+    # the analysed solve (band LU) against the literal dense LU.  A has
+    # uniform [-1, 1) off-diagonals and diagonal uniform [-1, 1) + 3.
+    for nn in (100, 250, 500, 1000, 4096):
+        a_h = synth.band_matrix(20250203 + 10, 1, nn, 1, 1, "f64", diag_shift=3.0)
+        b_h = synth.matrix(20250203 + 10, 2, nn, 1, "f64")
+        g = E.Graph()
+        nodes, outs = g.build(E.solve(g.input(0, nn, nn), g.input(1, nn, 1)))
+        a_d = torch.from_numpy(a_h.T.copy()).to(dev).t()
+        b_d = torch.from_numpy(b_h.T.copy()).to(dev).t()
+        ref = oracle.solve_band(a_h, b_h, 1, 1)
+        r = {}
+        for mode, flags in (("optimised", 0), ("literal", ag.PLAN_LITERAL)):
+            p_ = ag.Plan(nodes, outs, flags=flags)
+            out = p_.alloc_outputs(dev)
+            p_(a_d, b_d, outputs=out)
+            torch.cuda.synchronize()
+            reps = 50 if mode == "optimised" or nn <= 1000 else 5
+            ms = time_ms(lambda: p_(a_d, b_d, outputs=out), reps, stream)
+            r[mode] = {"us": ms * 1e3, "path": p_.solve_path()[0],
+                       "err_vs_oracle": oracle.rel_err(out[0].double().cpu().numpy(), ref)}
+        r["vs_literal"] = r["literal"]["us"] / r["optimised"]["us"]
+        nxt[f"solve_tridiag_n{nn}"] = r
     print(json.dumps({"workload": "six expressions over 256x256 FP64 A,B,C,D and v", "results": res,
                       "graph_replay_us_all_six": gms * 1e3, "next_rows": nxt}), flush=True)
 

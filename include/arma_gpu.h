@@ -87,10 +87,29 @@ typedef enum {
   ARMA_OP_ACCU = 13,       /* sum of all elements -> FP64 scalar */
   ARMA_OP_NORM_FRO = 14,   /* sqrt(sum of squares) -> FP64 scalar */
   ARMA_OP_INV = 15,        /* matrix inverse (square a) */
-  ARMA_OP_SUBMAT = 16      /* view of a: rows [slot, slot + rows), columns [ld, ld + cols)
+  ARMA_OP_SUBMAT = 16,     /* view of a: rows [slot, slot + rows), columns [ld, ld + cols)
                               (node fields: slot = first row, ld = first column, rows x
                               cols = size); elementwise expressions read it in place */
+  ARMA_OP_SOLVE = 17       /* solve(a, b): X with a X = b, a square (Sec. III (10)).  The
+                              optimised plan analyses a when evaluated and picks the solver
+                              (arma_solve_path); the literal plan always factors a densely. */
 } arma_op;
+
+/* The solver an analysed solve took (Sec. III (10); the band, triangular and
+ * symmetry checks of the solve trace, Fig. 3), in the order they are tried.
+ * Diagonal, band and triangular solves compute in the data's precision;
+ * the general solve follows the plan's tier. */
+typedef enum {
+  ARMA_SOLVE_NONE = 0,      /* no analysed solve ran (literal plan, or the stream was
+                               being captured into a graph: then the general solve) */
+  ARMA_SOLVE_GENERAL = 1,   /* dense LU with partial pivoting (+ refinement per tier) */
+  ARMA_SOLVE_DIAGONAL = 2,  /* X = B ./ diag(A) */
+  ARMA_SOLVE_BAND = 3,      /* band LU with partial pivoting: kl <= 31 subdiagonals,
+                               ku <= 32 superdiagonals, 4 (2 kl + ku + 1) <= n
+                               (tridiagonal systems included) */
+  ARMA_SOLVE_UPPER = 4,     /* upper triangular: back substitution */
+  ARMA_SOLVE_LOWER = 5      /* lower triangular: forward substitution */
+} arma_solve_path;
 
 /* Precision tier for products and solves (elementwise work always runs in
  * the operands' own type, FP32 arithmetic for BF16 data). */
@@ -119,6 +138,9 @@ typedef enum {
                                          paper's semi-optimised mapping to xGEMM, Sec. III (8));
                                          by default only their lower triangle is computed and
                                          then mirrored (xSYRK, Sec. II run-time analysis) */
+#define ARMA_PLAN_NO_SOLVE_ANALYSIS 0x200u /* solves skip the run-time analysis of their
+                                         matrix: always the general LU, and the evaluation
+                                         never waits on its stream */
 
 typedef struct arma_node {
   int32_t op;        /* arma_op */
@@ -171,6 +193,16 @@ arma_status arma_gpu_eval(const arma_plan* plan, const void* const* in_ptrs,
  * ARMA_ERR_NOCONVERGE (info = refinement steps taken).  Synchronises `stream`. */
 arma_status arma_gpu_eval_status(const arma_plan* plan, const void* workspace, void* stream,
                                  int64_t* info);
+
+/* After the stream of an arma_gpu_eval has been synchronised: the solver
+ * the plan's (last) analysed solve took and what the analysis of its matrix
+ * found: lower and upper bandwidth (largest i - j and j - i over non-zero
+ * elements) and whether it equals its transpose exactly.  An optimised solve
+ * waits on its stream for this analysis before it launches the solver; the
+ * record lives in `workspace`.  Any output pointer may be NULL.
+ * Synchronises `stream`. */
+arma_status arma_gpu_eval_solve_path(const arma_plan* plan, const void* workspace, void* stream,
+                                     int32_t* path, int32_t* kl, int32_t* ku, int32_t* symmetric);
 
 /* Human- and machine-readable decision log of the plan (JSON text): the
  * rewrites taken, chain order, precision tier, kernels, predicted work.

@@ -28,7 +28,15 @@ Expression format (plain data, shared with the tests): a list of node
 dicts in topological order, e.g. ``{"op": "input", "slot": 0, "rows": m,
 "cols": n}``, ``{"op": "add", "a": 0, "b": 1}``, ``{"op": "scale", "a": 2,
 "s": 2.0}``; the ops are input, add, sub, schur, div, scale, div_scalar,
-add_scalar, neg, trans, matmul, diagmat, trace, accu, norm_fro, inv.
+add_scalar, neg, trans, matmul, diagmat, trace, accu, norm_fro, inv, submat,
+solve.
+
+Structured solves (Sec. III (10); the band, triangular and symmetry checks
+of the solve trace in Fig. 3) have their own functions at the end: the
+analysis of the matrix (``band_widths``, ``is_symmetric``), the choice it
+leads to (``solve_path``) and the tailored solvers (``solve_band``: Gaussian
+elimination with partial pivoting kept inside the band; ``solve_triangular``:
+plain substitution), written in Python loops for the test sizes.
 """
 from __future__ import annotations
 
@@ -280,6 +288,9 @@ def evaluate(nodes, outputs, inputs):
             vals.append(inv(vals[nd["a"]]))
         elif op == "submat":
             vals.append(submat(vals[nd["a"]], nd["slot"], nd["ld"], nd["rows"], nd["cols"]))
+        elif op == "solve":
+            # solve(A, B) means X = A^-1 B (Sec. III (9), (10)); taken literally
+            vals.append(matmul(inv(vals[nd["a"]]), vals[nd["b"]]))
         else:
             raise ValueError(f"unknown op {op!r}")
     return [vals[o] for o in outputs]
@@ -432,3 +443,106 @@ def all_permutations_agree(mats) -> float:
 def all_trees(n):
     """Every binary tree over n factors (for the tests)."""
     return list(_trees(0, n - 1))
+
+
+# ---------------------------------------------------------------------------
+# structured solves (Sec. III (10); Fig. 3: band check, triangular checks,
+# symmetry check, then the tailored solver)
+# ---------------------------------------------------------------------------
+
+BAND_MAX_KL, BAND_MAX_KU = 31, 32
+
+
+def band_widths(a):
+    """(kl, ku): the largest i - j and the largest j - i over the non-zero
+    elements of a (0 when there are none below / above the diagonal)."""
+    a = f64(a)
+    kl = ku = 0
+    rows, cols = np.nonzero(a)
+    for i, j in zip(rows.tolist(), cols.tolist()):
+        if i > j:
+            kl = max(kl, i - j)
+        elif j > i:
+            ku = max(ku, j - i)
+    return kl, ku
+
+
+def is_symmetric(a) -> bool:
+    """a equals its transpose element by element (0.0 and -0.0 are equal)."""
+    a = f64(a)
+    if a.shape[0] != a.shape[1]:
+        return False
+    return bool(np.all(a == a.T))
+
+
+def solve_path(a) -> str:
+    """The solver the analysis selects, tried in the order of the solve trace
+    of Fig. 3: a diagonal matrix; a band matrix (at most 31 sub- and 32
+    superdiagonals, and band storage at most a quarter of the rows); an
+    upper or lower triangular matrix; otherwise the general solver."""
+    a = f64(a)
+    n = a.shape[0]
+    kl, ku = band_widths(a)
+    if kl == 0 and ku == 0:
+        return "diagonal"
+    if kl <= BAND_MAX_KL and ku <= BAND_MAX_KU and 4 * (2 * kl + ku + 1) <= n:
+        return "band"
+    if kl == 0:
+        return "upper"
+    if ku == 0:
+        return "lower"
+    return "general"
+
+
+def solve_band(a, b, kl: int, ku: int):
+    """X with A X = B for A with kl sub- and ku superdiagonals: Gaussian
+    elimination with partial pivoting in which every step touches only the
+    rows j .. j + kl and the columns j .. j + kl + ku (the row interchanges
+    can widen U by kl superdiagonals), the right-hand sides eliminated
+    alongside, then back substitution with the banded U.  Raises
+    SingularMatrix on an exactly zero pivot."""
+    u = f64(a).copy()
+    x = f64(b).copy()
+    n = u.shape[0]
+    for j in range(n):
+        last = min(j + kl, n - 1)
+        p = j
+        for i in range(j + 1, last + 1):      # the first largest magnitude
+            if abs(u[i, j]) > abs(u[p, j]):
+                p = i
+        if u[p, j] == 0.0:
+            raise SingularMatrix(f"solve_band: zero pivot in column {j}")
+        ju = min(j + kl + ku, n - 1)
+        if p != j:
+            u[[j, p], j:ju + 1] = u[[p, j], j:ju + 1]
+            x[[j, p], :] = x[[p, j], :]
+        for i in range(j + 1, last + 1):
+            m = u[i, j] / u[j, j]
+            u[i, j] = 0.0
+            for c in range(j + 1, ju + 1):
+                u[i, c] -= m * u[j, c]
+            x[i, :] -= m * x[j, :]
+    for j in range(n - 1, -1, -1):
+        ju = min(j + kl + ku, n - 1)
+        for c in range(j + 1, ju + 1):
+            x[j, :] -= u[j, c] * x[c, :]
+        x[j, :] /= u[j, j]
+    return x
+
+
+def solve_triangular(a, b, lower: bool):
+    """X with A X = B for triangular A by plain substitution (forward for
+    lower, backward for upper).  Raises SingularMatrix on a zero diagonal
+    element."""
+    a = f64(a)
+    x = f64(b).copy()
+    n = a.shape[0]
+    order = range(n) if lower else range(n - 1, -1, -1)
+    for j in order:
+        if a[j, j] == 0.0:
+            raise SingularMatrix(f"solve_triangular: zero diagonal element in row {j}")
+        known = range(j) if lower else range(j + 1, n)
+        for c in known:
+            x[j, :] -= a[j, c] * x[c, :]
+        x[j, :] /= a[j, j]
+    return x

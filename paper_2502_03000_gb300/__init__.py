@@ -35,10 +35,10 @@ F64, F32, BF16 = 0, 1, 2
 DTYPES = {"f64": F64, "f32": F32, "bf16": BF16}
 OPS = {"input": 0, "add": 1, "sub": 2, "schur": 3, "div": 4, "scale": 5, "div_scalar": 6,
        "add_scalar": 7, "neg": 8, "trans": 9, "matmul": 10, "diagmat": 11, "trace": 12,
-       "accu": 13, "norm_fro": 14, "inv": 15, "submat": 16}
+       "accu": 13, "norm_fro": 14, "inv": 15, "submat": 16, "solve": 17}
 TIERS = {"native": 0, "f64": 1, "split_bf16": 2, "bf16": 3, "lu32_ir64": 4}
 PLAN_LITERAL, PLAN_CHAIN_LEFT, PLAN_CHAIN_GREEDY, PLAN_COST_MLP, PLAN_NO_FUSE, PLAN_NO_TENSOR = 1, 2, 4, 8, 16, 32
-PLAN_TILE64, PLAN_TILE32, PLAN_NO_SYRK = 64, 128, 256
+PLAN_TILE64, PLAN_TILE32, PLAN_NO_SYRK, PLAN_NO_SOLVE_ANALYSIS = 64, 128, 256, 512
 STATUS = {0: "ok", 1: "invalid", 2: "shape", 3: "dtype", 4: "align", 5: "workspace",
           6: "singular", 7: "noconverge", 8: "cuda", 9: "unsupported"}
 
@@ -65,7 +65,7 @@ class Expr(ctypes.Structure):
 
 
 EXPORTS = ["arma_gpu_plan", "arma_gpu_plan_workspace", "arma_gpu_output_info", "arma_gpu_eval",
-           "arma_gpu_eval_status", "arma_gpu_plan_info", "arma_gpu_plan_free",
+           "arma_gpu_eval_status", "arma_gpu_eval_solve_path", "arma_gpu_plan_info", "arma_gpu_plan_free",
            "arma_gpu_status_string", "arma_gpu_last_cuda_error", "arma_gpu_chain_order",
            "arma_gpu_eval_fused_static",
            "arma_gpu_plan_batched", "arma_gpu_batched_table_bytes", "arma_gpu_batched_table_fill",
@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
     L.arma_gpu_output_info.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)]
     L.arma_gpu_eval.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, ctypes.c_size_t, vp]
     L.arma_gpu_eval_status.argtypes = [vp, vp, vp, ctypes.POINTER(i64)]
+    L.arma_gpu_eval_solve_path.argtypes = [vp, vp, vp] + [ctypes.POINTER(i32)] * 4
     L.arma_gpu_plan_info.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     L.arma_gpu_plan_free.argtypes = [vp]
     L.arma_gpu_plan_free.restype = None
@@ -281,6 +282,24 @@ class Plan:
         code = lib().arma_gpu_eval_status(self._h, ctypes.c_void_p(ws.data_ptr()), ctypes.c_void_p(st),
                                           ctypes.byref(info))
         return STATUS.get(code, str(code)), int(info.value)
+
+
+SOLVE_PATHS = {0: "none", 1: "general", 2: "diagonal", 3: "band", 4: "upper", 5: "lower"}
+
+
+def _solve_path(self, workspace=None, stream=None):
+    """The solver the last evaluation's analysed solve took and what the
+    analysis of its matrix found (synchronises): (path, kl, ku, symmetric)."""
+    import torch
+    ws = workspace if workspace is not None else next(iter(self._ws.values()))
+    st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(lib().arma_gpu_eval_solve_path(self._h, ctypes.c_void_p(ws.data_ptr()), ctypes.c_void_p(st),
+                                          *[ctypes.byref(x) for x in v]), "arma_gpu_eval_solve_path")
+    return SOLVE_PATHS.get(v[0].value, str(v[0].value)), v[1].value, v[2].value, bool(v[3].value)
+
+
+Plan.solve_path = _solve_path
 
 
 class BatchedPlan:

@@ -137,6 +137,8 @@ arma_status run_step(const Step& st, const Bind& b, cudaStream_t s, int* launche
       a.scratch = mptr(b, v.scratch); a.scratch_bytes = v.scratch_bytes;
       a.status_code = reinterpret_cast<int32_t*>(b.ws);
       a.status_info = reinterpret_cast<int64_t*>(b.ws + 8);
+      a.analyse = v.analyse;
+      a.props = reinterpret_cast<int32_t*>(b.ws + kSolveRecordOffset);
       return cuda_status(launch_solve(a, s, launches));
     }
   }
@@ -220,6 +222,22 @@ arma_status arma_gpu_eval_status(const arma_plan* plan, const void* workspace, v
   if (info) *info = hdr[1];
   if (code == 0) return ARMA_OK;
   return static_cast<arma_status>(code);
+}
+
+arma_status arma_gpu_eval_solve_path(const arma_plan* plan, const void* workspace, void* stream,
+                                     int32_t* path, int32_t* kl, int32_t* ku, int32_t* symmetric) {
+  if (!plan || !workspace) return ARMA_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int32_t rec[SP_WORDS] = {0, 0, 0, 0, 0, 0};
+  if (cudaError_t e = cudaStreamSynchronize(s)) return cuda_status(e);
+  if (cudaError_t e = cudaMemcpy(rec, static_cast<const char*>(workspace) + kSolveRecordOffset, sizeof rec,
+                                 cudaMemcpyDeviceToHost))
+    return cuda_status(e);
+  if (path) *path = rec[SP_PATH];
+  if (kl) *kl = rec[SP_KL];
+  if (ku) *ku = rec[SP_KU];
+  if (symmetric) *symmetric = rec[SP_PATH] != ARMA_SOLVE_NONE && rec[SP_ASYM] == 0 ? 1 : 0;
+  return ARMA_OK;
 }
 
 arma_status arma_gpu_plan_info(const arma_plan* plan, char* buf, size_t len, size_t* needed) {

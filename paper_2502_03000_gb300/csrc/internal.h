@@ -224,9 +224,19 @@ struct SolveStep {
   MatOperand A, B, X;      // B may be absent: X = inv(A)
   int32_t tier = ARMA_TIER_LU32_IR64;
   int32_t explicit_inverse = 0;  // literal plan: form inv(A) then multiply
+  int32_t analyse = 0;     // run-time analysis of A picks the solver (Sec. III (10))
   Ref scratch;
   int64_t scratch_bytes = 0;
 };
+
+// The solve record in the workspace header (int32 words at byte 16): the
+// solver taken and what the analysis of A found.
+enum SolveProp : int32_t { SP_PATH = 0, SP_KL = 1, SP_KU = 2, SP_ASYM = 3, SP_ZDIAG = 4, SP_FALLBACK = 5,
+                           SP_WORDS = 6 };
+constexpr size_t kSolveRecordOffset = 16;
+
+// band solver limits: kl <= 31 keeps the pivot candidates within one warp
+constexpr int32_t kBandMaxKl = 31, kBandMaxKu = 32;
 
 struct SolveArgs {
   int64_t n, nrhs;
@@ -237,9 +247,32 @@ struct SolveArgs {
   void* scratch; int64_t scratch_bytes;
   int32_t* status_code;   // workspace header
   int64_t* status_info;
+  int32_t analyse;        // 1: analyse A first and dispatch
+  int32_t* props;         // the solve record (SP_WORDS int32)
 };
-int64_t solve_scratch_bytes(int64_t n, int64_t nrhs, int32_t tier);
+int64_t solve_scratch_bytes(int64_t n, int64_t nrhs, int32_t tier, int32_t analyse = 0);
 cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches);
+
+struct BandArgs {
+  int64_t n, nrhs;
+  int32_t kl, ku;
+  const void* A; int64_t lda; int32_t adt;
+  const void* B; int64_t ldb; int32_t bdt;   // null: identity
+  void* X; int64_t ldx; int32_t xdt;
+  void* work;             // band_work_bytes() when the band does not fit shared memory
+  int32_t in_smem;
+  int32_t* status; int64_t* info;
+  int32_t refine;         // FP64 data: FP32 factors + FP64 refinement (tridiagonal)
+  int32_t* fallback;      // set when that refinement gives up
+  const int32_t* gate;    // the kernel runs only when *gate != 0 (null: always)
+};
+int64_t band_work_bytes(int64_t n, int64_t nrhs, int32_t kl, int32_t ku, int32_t es);
+cudaError_t launch_analyse(const void* A, int64_t lda, int32_t adt, int64_t n, int32_t* props, cudaStream_t s,
+                           int* launches);
+cudaError_t launch_set_props(int32_t* props, int32_t path, int32_t* status, int64_t* info, int64_t singular_at,
+                             cudaStream_t s, int* launches);
+cudaError_t launch_diag_solve(const SolveArgs& a, bool f64, cudaStream_t s, int* launches);
+cudaError_t launch_band_solve(BandArgs a, bool f64, cudaStream_t s, int* launches);
 
 // --------------------------------------------------------------------------
 // Plan

@@ -731,11 +731,12 @@ __device__ __forceinline__ void block_update(T (&y)[16], const T* Ms, const T* X
   }
 }
 
-// unit-lower (LOWER) or upper solve with the diagonal block D (column-major,
-// dinv = reciprocals of its diagonal), rows distributed as in block_update;
-// the four threads of a column are consecutive lanes
+// lower (unit diagonal unless !unit) or upper solve with the diagonal block
+// D (column-major, dinv = reciprocals of its diagonal), rows distributed as
+// in block_update; the four threads of a column are consecutive lanes
 template <typename T, bool LOWER>
-__device__ __forceinline__ void block_solve(T (&y)[16], const T* D, const T* dinv, int w, int q, int lane) {
+__device__ __forceinline__ void block_solve(T (&y)[16], const T* D, const T* dinv, int w, int q, int lane,
+                                            bool unit = true) {
   const int base = lane & ~3;
   if (LOWER) {
 #pragma unroll
@@ -743,7 +744,11 @@ __device__ __forceinline__ void block_solve(T (&y)[16], const T* D, const T* din
 #pragma unroll
       for (int kk = 0; kk < 16; ++kk) {
         const int r = qq * 16 + kk;
-        const T yr = __shfl_sync(0xffffffffu, y[kk], base | qq);
+        T yr = __shfl_sync(0xffffffffu, y[kk], base | qq);
+        if (!unit && r < w) {
+          yr *= dinv[r];
+          if (q == qq) y[kk] = yr;
+        }
         if (r < w && q >= qq) {
           T dv[16];
           ld16(D + r * NB + q * 16, dv);
@@ -777,15 +782,19 @@ __device__ __forceinline__ void block_solve(T (&y)[16], const T* D, const T* din
 // inverses of the diagonal blocks: Linv_i = L_ii^-1 (unit lower) and
 // Uinv_i = U_ii^-1, each 64 x 64 column-major (zero-padded past the last
 // row), by the block solve applied to the identity.  A zero pivot gives a
-// zero row, as in the substitution.
+// zero row, as in the substitution.  With lower_nonunit the matrix is a
+// lower-triangular system matrix itself: Linv_i inverts its whole lower
+// block, diagonal included (Uinv_i is then not used).
 template <typename T>
-__global__ void __launch_bounds__(256) inv_diag_kernel(const T* __restrict__ LU, int64_t n, T* Linv, T* Uinv) {
+__global__ void __launch_bounds__(256) inv_diag_kernel(const T* __restrict__ LU, int64_t n, T* Linv, T* Uinv,
+                                                       int64_t lda = 0, int lower_nonunit = 0) {
   __shared__ __align__(16) T D[NB * NB];
   __shared__ T dinv[NB];
+  if (lda == 0) lda = n;
   const int64_t j = (int64_t)blockIdx.x * NB;
   const int w = (int)(n - j < NB ? n - j : NB);
   const int tid = threadIdx.x, lane = tid & 31, col = tid >> 2, q = tid & 3;
-  load_block(D, LU + j + j * n, n, w, w);
+  load_block(D, LU + j + j * lda, lda, w, w);
   __syncthreads();
   if (tid < NB) {
     const T p = D[tid * NB + tid];
@@ -798,7 +807,7 @@ __global__ void __launch_bounds__(256) inv_diag_kernel(const T* __restrict__ LU,
     T y[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) y[k] = (q * 16 + k == col && col < w) ? (T)1 : (T)0;
-    if (which == 0) block_solve<T, true>(y, D, dinv, w, q, lane);
+    if (which == 0) block_solve<T, true>(y, D, dinv, w, q, lane, !lower_nonunit);
     else block_solve<T, false>(y, D, dinv, w, q, lane);
 #pragma unroll
     for (int k = 0; k < 16; ++k) out[which][col * NB + q * 16 + k] = y[k];
@@ -832,11 +841,16 @@ __device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
 // while the current one is applied.  Every wait is bounded in time; a wait
 // that runs out marks the control block and the status, and every other wait
 // then gives up.
+// lda is the leading dimension of LU; sweeps selects the forward (bit 0)
+// and backward (bit 1) halves: a triangular system matrix needs only one,
+// and the result is then in Z (forward only) or Y (backward only, whose
+// input is then read from Y).
 template <typename T>
 __global__ void __launch_bounds__(256) sub_coop_kernel(const T* __restrict__ LU, const T* __restrict__ Linv,
                                                        const T* __restrict__ Uinv, int64_t n, T* Y, T* Z,
                                                        int64_t nrhs, unsigned int* flags, Ctl* ctl,
-                                                       int32_t* status, const int* skip) {
+                                                       int32_t* status, const int* skip, int64_t lda,
+                                                       int sweeps) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* Ms = reinterpret_cast<T*>(smraw);   // off-diagonal block, Ms[m * NB + r]
@@ -891,7 +905,7 @@ __global__ void __launch_bounds__(256) sub_coop_kernel(const T* __restrict__ LU,
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       const int t = tid + 256 * k, r = t & (NB - 1), c = t >> 6;
-      mv[k] = (r < rows && c < cols) ? src[r + (int64_t)c * n] : (T)0;
+      mv[k] = (r < rows && c < cols) ? src[r + (int64_t)c * lda] : (T)0;
     }
   };
   auto store_m = [&]() {
@@ -948,31 +962,34 @@ __global__ void __launch_bounds__(256) sub_coop_kernel(const T* __restrict__ LU,
   };
 
   load_x(Y + j + c0 * n, w);
-  load_d(Linv + (int64_t)bi * NB * NB);
+  if (sweeps & 1) load_d(Linv + (int64_t)bi * NB * NB);
   __syncthreads();
 #pragma unroll
   for (int e = 0; e < 4; ++e) y[e] = Xs[(4 * rq + e) * XS + col];
   __syncthreads();
 
-  if (bi > 0) fetch_m(LU + j, w, NB);          // L_i0
-  for (int k = 0; k < bi; ++k) {                // forward: L_ik, k < i
-    store_m();
-    if (k + 1 < bi) fetch_m(LU + j + (int64_t)(k + 1) * NB * n, w, NB);
-    if (!wait(flag(fwd, k))) return;
-    load_x(Z + (int64_t)k * NB + c0 * n, NB);
-    __syncthreads();
-    sub(NB);
-    __syncthreads();
+  if (sweeps & 1) {
+    if (bi > 0) fetch_m(LU + j, w, NB);          // L_i0
+    for (int k = 0; k < bi; ++k) {                // forward: L_ik, k < i
+      store_m();
+      if (k + 1 < bi) fetch_m(LU + j + (int64_t)(k + 1) * NB * lda, w, NB);
+      if (!wait(flag(fwd, k))) return;
+      load_x(Z + (int64_t)k * NB + c0 * n, NB);
+      __syncthreads();
+      sub(NB);
+      __syncthreads();
+    }
+    apply();
+    publish(Z + j + c0 * n, flag(fwd, bi));
   }
-  apply();
-  publish(Z + j + c0 * n, flag(fwd, bi));
+  if (!(sweeps & 2)) return;
 
   load_d(Uinv + (int64_t)bi * NB * NB);
-  if (bi < nb - 1) fetch_m(LU + j + (int64_t)(nb - 1) * NB * n, w, rows_of(nb - 1));
+  if (bi < nb - 1) fetch_m(LU + j + (int64_t)(nb - 1) * NB * lda, w, rows_of(nb - 1));
   for (int k = nb - 1; k > bi; --k) {           // backward: U_ik, k > i
     const int wk = rows_of(k);
     store_m();
-    if (k - 1 > bi) fetch_m(LU + j + (int64_t)(k - 1) * NB * n, w, rows_of(k - 1));
+    if (k - 1 > bi) fetch_m(LU + j + (int64_t)(k - 1) * NB * lda, w, rows_of(k - 1));
     if (!wait(flag(bwd, k))) return;
     load_x(Y + (int64_t)k * NB + c0 * n, wk);
     __syncthreads();
@@ -1004,7 +1021,7 @@ __host__ __device__ inline size_t sub_smem(void) {
 template <typename T, bool LOWER>
 __global__ void __launch_bounds__(256) sub_step_kernel(const T* __restrict__ LU, int64_t n, int64_t j, int w,
                                                        T* Yio, T* Yout, int64_t nrhs, int64_t r_begin,
-                                                       int64_t rows, const int* skip) {
+                                                       int64_t rows, const int* skip, int64_t lda, int unit) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* D = reinterpret_cast<T*>(smraw);              // [NB][NB], D[c * NB + r]
@@ -1017,14 +1034,14 @@ __global__ void __launch_bounds__(256) sub_step_kernel(const T* __restrict__ LU,
   const int64_t rb = r_begin + (int64_t)blockIdx.x * SUB_ROWS;
   const int64_t rem = r_begin + rows - rb;
   const int nr = (int)(rem < SUB_ROWS ? (rem > 0 ? rem : 0) : SUB_ROWS);
-  load_block(D, LU + j + j * n, n, w, w);
+  load_block(D, LU + j + j * lda, lda, w, w);
   load_cols_cg(Ys, Yio + j + c0 * n, n, w, ncols);
   {
     T v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const int t = tid + 256 * k, i = t & (SUB_ROWS - 1), r = t / SUB_ROWS;
-      v[k] = (i < nr && r < w) ? LU[(rb + i) + (j + r) * n] : (T)0;
+      v[k] = (i < nr && r < w) ? LU[(rb + i) + (j + r) * lda] : (T)0;
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) At[tid + 256 * k] = v[k];
@@ -1039,7 +1056,7 @@ __global__ void __launch_bounds__(256) sub_step_kernel(const T* __restrict__ LU,
 #pragma unroll
   for (int k = 0; k < 16; ++k) y[k] = Ys[col * (NB + 1) + q * 16 + k];
   __syncthreads();
-  block_solve<T, LOWER>(y, D, dinv, w, q, lane);
+  block_solve<T, LOWER>(y, D, dinv, w, q, lane, unit != 0);
 #pragma unroll
   for (int k = 0; k < 16; ++k) Ys[col * (NB + 1) + q * 16 + k] = y[k];
   __syncthreads();
@@ -1207,12 +1224,13 @@ __global__ void sumsq_any_kernel(const void* x, int32_t dt, int64_t ld, int64_t 
 struct Layout {
   int64_t lu, piv, perm, cand_val, cand_row, cand_data, drow, ctl, flags, dinv, gemm, y, z, x64, r64, sq, part,
       total;
+  int64_t tri_dinv, tri_y, tri_z, band;   // structured solvers (analysed solves only)
   int64_t gemm_bytes;
   bool f64;
   bool refine;
 };
 
-Layout layout(int64_t n, int64_t nrhs, int32_t tier) {
+Layout layout(int64_t n, int64_t nrhs, int32_t tier, int32_t analyse = 0) {
   Layout L;
   L.f64 = tier == ARMA_TIER_F64;
   L.refine = tier == ARMA_TIER_LU32_IR64 || tier == ARMA_TIER_BF16;
@@ -1248,6 +1266,13 @@ Layout layout(int64_t n, int64_t nrhs, int32_t tier) {
   L.r64 = L.refine ? take(n * nrhs * 8) : 0;
   L.sq = take(8 * 8);
   L.part = take(1024 * 8);
+  L.tri_dinv = L.tri_y = L.tri_z = L.band = 0;
+  if (analyse) {   // sized for FP64 data
+    L.tri_dinv = take(2 * ((n + NB - 1) / NB) * NB * NB * 8);
+    L.tri_y = take(n * nrhs * 8);
+    L.tri_z = take(n * nrhs * 8);
+    L.band = take(band_work_bytes(n, nrhs, kBandMaxKl, kBandMaxKu, 8));
+  }
   L.total = off + 256;
   return L;
 }
@@ -1398,10 +1423,15 @@ cudaError_t factor(const SolveArgs& a, const Layout& L, char* base, cudaStream_t
 // launch per diagonal block and sweep: the forward sweep reduces Y in place
 // and writes the solved rows to Z, the backward sweep reduces Z in place and
 // writes the result to Y.  Either way the result is in Y.
+// y := U^-1 L^-1 y with LU factors W (ld = n), or with a triangular system
+// matrix W (leading dimension lda): sweeps = 1 for lower (non-unit
+// diagonal, result in Z), 2 for upper (result in Y), 3 for LU factors
+// (unit lower L; result in Y).
 template <typename T>
 cudaError_t substitute(const T* W, const T* Linv, const T* Uinv, int64_t n, T* Y, T* Z, int64_t nrhs,
                        unsigned int* flags, Ctl* ctl, int32_t* status, const int* skip, cudaStream_t s,
-                       int* launches) {
+                       int* launches, int64_t lda = 0, int sweeps = 3) {
+  if (lda == 0) lda = n;
   const int64_t nb = (n + NB - 1) / NB;
   const int64_t gy = (nrhs + 63) / 64;
   if (gy > 65535) return cudaErrorInvalidConfiguration;
@@ -1417,7 +1447,7 @@ cudaError_t substitute(const T* W, const T* Linv, const T* Uinv, int64_t n, T* Y
       cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)2 * nb * gc * FLAG_STRIDE * sizeof(unsigned int), s);
       if (e != cudaSuccess) return e;
       void* args[] = {(void*)&W, (void*)&Linv, (void*)&Uinv, (void*)&n, (void*)&Y, (void*)&Z, (void*)&nrhs,
-                      (void*)&flags, (void*)&ctl, (void*)&status, (void*)&skip};
+                      (void*)&flags, (void*)&ctl, (void*)&status, (void*)&skip, (void*)&lda, (void*)&sweeps};
       e = cudaLaunchCooperativeKernel((const void*)sub_coop_kernel<T>, dim3((unsigned)nb, (unsigned)gc), dim3(256),
                                       args, smem, s);
       if (e == cudaSuccess) {
@@ -1433,35 +1463,144 @@ cudaError_t substitute(const T* W, const T* Linv, const T* Uinv, int64_t n, T* Y
     e = cudaFuncSetAttribute(sub_step_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   auto gx = [](int64_t rows) { return (unsigned)(rows > 0 ? (rows + SUB_ROWS - 1) / SUB_ROWS : 1); };
-  for (int64_t j = 0; j < n; j += NB) {
-    const int w = (int)(n - j < NB ? n - j : NB);
-    const int64_t rows = n - j - w;
-    sub_step_kernel<T, true><<<dim3(gx(rows), (unsigned)gy), 256, smem, s>>>(W, n, j, w, Y, Z, nrhs, j + w, rows, skip);
-    if (launches) ++*launches;
+  // the forward steps read Y and write Z; the backward steps read Z and write Y
+  if (sweeps & 1) {
+    for (int64_t j = 0; j < n; j += NB) {
+      const int w = (int)(n - j < NB ? n - j : NB);
+      const int64_t rows = n - j - w;
+      sub_step_kernel<T, true><<<dim3(gx(rows), (unsigned)gy), 256, smem, s>>>(W, n, j, w, Y, Z, nrhs, j + w, rows,
+                                                                               skip, lda, sweeps == 3 ? 1 : 0);
+      if (launches) ++*launches;
+    }
+  } else {
+    e = cudaMemcpyAsync(Z, Y, (size_t)n * nrhs * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
   }
-  for (int64_t j = ((n - 1) / NB) * NB; j >= 0; j -= NB) {
-    const int w = (int)(n - j < NB ? n - j : NB);
-    sub_step_kernel<T, false><<<dim3(gx(j), (unsigned)gy), 256, smem, s>>>(W, n, j, w, Z, Y, nrhs, 0, j, skip);
-    if (launches) ++*launches;
+  if (sweeps & 2) {
+    for (int64_t j = ((n - 1) / NB) * NB; j >= 0; j -= NB) {
+      const int w = (int)(n - j < NB ? n - j : NB);
+      sub_step_kernel<T, false><<<dim3(gx(j), (unsigned)gy), 256, smem, s>>>(W, n, j, w, Z, Y, nrhs, 0, j, skip,
+                                                                             lda, 1);
+      if (launches) ++*launches;
+    }
   }
   return cudaGetLastError();
 }
 
 }  // namespace lu
 
-int64_t solve_scratch_bytes(int64_t n, int64_t nrhs, int32_t tier) {
-  return lu::layout(n, nrhs, tier).total;
+namespace lu {
+
+template <typename T>
+__global__ void rhs_kernel(const void* B, int64_t ldb, int32_t bdt, T* Y, int64_t n, int64_t nrhs) {
+  const int64_t total = n * nrhs;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = t / n, i = t - c * n;
+    Y[t] = B ? load_as<T>(B, i + c * ldb, bdt) : (T)(i == c ? 1 : 0);
+  }
+}
+
+// A triangular system solved by substitution with A itself (no
+// factorisation): the inverted diagonal blocks of A, then one sweep of the
+// cooperative substitution, in the data's own precision.
+template <typename T>
+cudaError_t solve_triangular(const SolveArgs& a, const Layout& L, char* base, bool lower, Ctl* ctl, cudaStream_t s,
+                             int* launches) {
+  const int64_t n = a.n, nrhs = a.nrhs, nb = (n + NB - 1) / NB;
+  const T* W = static_cast<const T*>(a.A);
+  T* Linv = reinterpret_cast<T*>(base + L.tri_dinv);
+  T* Uinv = Linv + nb * NB * NB;
+  inv_diag_kernel<T><<<(unsigned)nb, 256, 0, s>>>(W, n, Linv, Uinv, a.lda, lower ? 1 : 0);
+  T* Y = reinterpret_cast<T*>(base + L.tri_y);
+  T* Z = reinterpret_cast<T*>(base + L.tri_z);
+  int64_t blocks = (n * nrhs + 255) / 256, cap = (int64_t)device_sm_count() * 8;
+  const unsigned g = (unsigned)(blocks < 1 ? 1 : blocks < cap ? blocks : cap);
+  rhs_kernel<T><<<g, 256, 0, s>>>(a.B, a.ldb, a.bdt, Y, n, nrhs);
+  if (launches) *launches += 2;
+  cudaError_t e = substitute<T>(W, Linv, Uinv, n, Y, Z, nrhs, reinterpret_cast<unsigned int*>(base + L.flags), ctl,
+                                a.status_code, nullptr, s, launches, a.lda, lower ? 1 : 2);
+  if (e != cudaSuccess) return e;
+  store_kernel<T><<<g, 256, 0, s>>>(lower ? Z : Y, n, nrhs, a.X, a.ldx, a.xdt);
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+// The analysis of A (bandwidths, symmetry, zero diagonal) and the choice of
+// solver, in the order of the solve trace of Fig. 3: diagonal, band, then
+// triangular; anything else is the general LU solve (returns false).  The
+// host waits for the analysis: the choice is made on the host, as the
+// library's CPU counterpart does.  Under stream capture nothing is analysed.
+bool solve_structured(const SolveArgs& a, const Layout& L, char* base, Ctl* ctl, cudaStream_t s, int* launches,
+                      cudaError_t* err) {
+  *err = cudaSuccess;
+  if (!a.analyse || !a.props) return false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if ((*err = cudaStreamIsCapturing(s, &cs)) != cudaSuccess) return true;
+  if (cs != cudaStreamCaptureStatusNone) return false;
+  const int64_t n = a.n;
+  if ((*err = launch_analyse(a.A, a.lda, a.adt, n, a.props, s, launches)) != cudaSuccess) return true;
+  int32_t h[SP_WORDS] = {0, 0, 0, 0, 0, 0};
+  if ((*err = cudaMemcpyAsync(h, a.props, sizeof h, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return true;
+  if ((*err = cudaStreamSynchronize(s)) != cudaSuccess) return true;
+  const int32_t kl = h[SP_KL], ku = h[SP_KU], zd = h[SP_ZDIAG];
+  const bool typed = a.adt == ARMA_F64 || a.adt == ARMA_F32;
+  const bool f64 = a.adt == ARMA_F64;
+  int32_t path = ARMA_SOLVE_GENERAL;
+  if (typed) {
+    if (kl == 0 && ku == 0) path = ARMA_SOLVE_DIAGONAL;
+    else if (kl <= kBandMaxKl && ku <= kBandMaxKu && (int64_t)(2 * kl + ku + 1) * 4 <= n) path = ARMA_SOLVE_BAND;
+    else if (kl == 0) path = ARMA_SOLVE_UPPER;
+    else if (ku == 0) path = ARMA_SOLVE_LOWER;
+  }
+  // a triangular (or diagonal) matrix is singular exactly when a diagonal element is zero
+  const bool tri = path == ARMA_SOLVE_DIAGONAL || path == ARMA_SOLVE_UPPER || path == ARMA_SOLVE_LOWER;
+  const int64_t sing = (tri && zd > 0) ? n - zd + 1 : 0;
+  if ((*err = launch_set_props(a.props, path, a.status_code, a.status_info, sing, s, launches)) != cudaSuccess)
+    return true;
+  if (path == ARMA_SOLVE_GENERAL) return false;
+  if (sing) return true;
+  switch (path) {
+    case ARMA_SOLVE_DIAGONAL:
+      *err = launch_diag_solve(a, f64, s, launches);
+      break;
+    case ARMA_SOLVE_BAND: {
+      BandArgs b;
+      memset(&b, 0, sizeof b);
+      b.n = n; b.nrhs = a.nrhs; b.kl = kl; b.ku = ku;
+      b.A = a.A; b.lda = a.lda; b.adt = a.adt;
+      b.B = a.B; b.ldb = a.ldb; b.bdt = a.bdt;
+      b.X = a.X; b.ldx = a.ldx; b.xdt = a.xdt;
+      b.work = base + L.band;
+      b.status = a.status_code; b.info = a.status_info;
+      b.refine = a.tier != ARMA_TIER_F64 ? 1 : 0;
+      b.fallback = a.props + SP_FALLBACK;
+      *err = launch_band_solve(b, f64, s, launches);
+      break;
+    }
+    default:
+      *err = f64 ? solve_triangular<double>(a, L, base, path == ARMA_SOLVE_LOWER, ctl, s, launches)
+                 : solve_triangular<float>(a, L, base, path == ARMA_SOLVE_LOWER, ctl, s, launches);
+  }
+  return true;
+}
+
+}  // namespace lu
+
+int64_t solve_scratch_bytes(int64_t n, int64_t nrhs, int32_t tier, int32_t analyse) {
+  return lu::layout(n, nrhs, tier, analyse).total;
 }
 
 cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
   using namespace lu;
   const int64_t n = a.n, nrhs = a.nrhs;
   if (n == 0 || nrhs == 0) return cudaSuccess;
-  Layout L = layout(n, nrhs, a.tier);
+  Layout L = layout(n, nrhs, a.tier, a.analyse);
   if (a.scratch_bytes < L.total) return cudaErrorInvalidValue;
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(a.scratch) + 255) & ~uintptr_t(255));
   Ctl* ctl = reinterpret_cast<Ctl*>(base + L.ctl);
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
+  if (e != cudaSuccess) return e;
+  if (solve_structured(a, L, base, ctl, s, launches, &e)) return e;
   if (e != cudaSuccess) return e;
   const int sms = device_sm_count();
   int32_t* piv = reinterpret_cast<int32_t*>(base + L.piv);

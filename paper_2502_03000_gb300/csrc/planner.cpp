@@ -142,7 +142,7 @@ bool is_ew_op(int op) {
 }
 bool is_binary(int op) {
   return op == ARMA_OP_ADD || op == ARMA_OP_SUB || op == ARMA_OP_SCHUR || op == ARMA_OP_DIV ||
-         op == ARMA_OP_MATMUL;
+         op == ARMA_OP_MATMUL || op == ARMA_OP_SOLVE;
 }
 bool is_reduction(int op) {
   return op == ARMA_OP_TRACE || op == ARMA_OP_ACCU || op == ARMA_OP_NORM_FRO;
@@ -150,8 +150,8 @@ bool is_reduction(int op) {
 const char* op_name(int op) {
   static const char* names[] = {"input", "add", "sub", "schur", "div", "scale", "div_scalar",
                                 "add_scalar", "neg", "trans", "matmul", "diagmat", "trace",
-                                "accu", "norm_fro", "inv", "submat"};
-  return (op >= 0 && op <= ARMA_OP_SUBMAT) ? names[op] : "?";
+                                "accu", "norm_fro", "inv", "submat", "solve"};
+  return (op >= 0 && op <= ARMA_OP_SOLVE) ? names[op] : "?";
 }
 const char* tier_name(int t) {
   static const char* names[] = {"native", "f64", "split_bf16", "bf16", "lu32_ir64"};
@@ -297,7 +297,7 @@ arma_status Planner::validate() {
     const arma_node& d = nd_[i];
     NInfo& I = info_[i];
     char buf[160];
-    if (d.op < 0 || d.op > ARMA_OP_SUBMAT) {
+    if (d.op < 0 || d.op > ARMA_OP_SOLVE) {
       snprintf(buf, sizeof buf, "node %d: unknown op %d", i, d.op);
       return fail(ARMA_ERR_INVALID, buf);
     }
@@ -381,6 +381,20 @@ arma_status Planner::validate() {
           return fail(ARMA_ERR_SHAPE, buf);
         }
         I.rows = d.rows; I.cols = d.cols; I.dtype = A.dtype;
+        break;
+      }
+      case ARMA_OP_SOLVE: {
+        const NInfo& B = info_[d.b];
+        if (A.rows != A.cols) return fail(ARMA_ERR_SHAPE, "solve needs a square matrix");
+        if (B.rows != A.rows) {
+          snprintf(buf, sizeof buf, "node %d (solve): %lldx%lld matrix, %lldx%lld right-hand side", i,
+                   (long long)A.rows, (long long)A.cols, (long long)B.rows, (long long)B.cols);
+          return fail(ARMA_ERR_SHAPE, buf);
+        }
+        if (A.dtype == ARMA_BF16 || B.dtype == ARMA_BF16)
+          return fail(ARMA_ERR_DTYPE, "solve with BF16 operands is not supported");
+        if (A.dtype != B.dtype) return fail(ARMA_ERR_DTYPE, "solve operands differ in dtype");
+        I.rows = A.rows; I.cols = B.cols; I.dtype = A.dtype;
         break;
       }
       case ARMA_OP_INV:
@@ -813,7 +827,10 @@ void Planner::emit_solve(const MatOperand& A, int64_t n, const MatOperand* B, in
       (e_.tier == ARMA_TIER_NATIVE || e_.tier == ARMA_TIER_LU32_IR64))
     s.tier = ARMA_TIER_F64;
   s.explicit_inverse = explicit_inverse ? 1 : 0;
-  s.scratch_bytes = solve_scratch_bytes(n, s.nrhs, s.tier);
+  // the run-time analysis that picks a diagonal, band or triangular solver
+  // (Sec. III (10)); the literal plan and explicit inverses factor densely
+  s.analyse = (!literal_ && !explicit_inverse && !(e_.flags & ARMA_PLAN_NO_SOLVE_ANALYSIS)) ? 1 : 0;
+  s.scratch_bytes = solve_scratch_bytes(n, s.nrhs, s.tier, s.analyse);
   s.scratch = ref_ws(alloc_ws(s.scratch_bytes));
   Step st;
   st.kind = ST_SOLVE;
@@ -822,7 +839,8 @@ void Planner::emit_solve(const MatOperand& A, int64_t n, const MatOperand* B, in
   st.flops = 2.0 / 3.0 * dn * dn * dn + 2.0 * dn * dn * (double)s.nrhs;
   st.bytes = dn * dn * dtype_size(A.dtype) + 2.0 * dn * (double)s.nrhs * dtype_size(X.dtype);
   std::ostringstream os;
-  os << "LU solve n=" << n << " nrhs=" << s.nrhs << " tier=" << tier_name(s.tier) << " (" << why << ")";
+  os << (s.analyse ? "analysed solve (diagonal / band / triangular / LU) n=" : "LU solve n=") << n
+     << " nrhs=" << s.nrhs << " tier=" << tier_name(s.tier) << " (" << why << ")";
   st.note = os.str();
   push_step(std::move(st));
 }
@@ -1238,6 +1256,11 @@ MatOperand Planner::materialize(int x) {
                  "inv(A) needed as a matrix");
       break;
     }
+    case ARMA_OP_SOLVE: {
+      MatOperand A = materialize(d.a), B = materialize(d.b);
+      emit_solve(A, info_[x].rows, &B, info_[x].cols, dest, info_[x].dtype, false, "solve(A, B)");
+      break;
+    }
     case ARMA_OP_SUBMAT: {
       // a view needed as a matrix of its own: one copy pass reading it in place
       EwBuild b;
@@ -1546,6 +1569,9 @@ void Planner::literal() {
     } else if (d.op == ARMA_OP_INV) {
       emit_solve(loc_[d.a], info_[x].rows, nullptr, info_[x].rows, dest, info_[x].dtype, true,
                  "literal explicit inverse");
+    } else if (d.op == ARMA_OP_SOLVE) {
+      emit_solve(loc_[d.a], info_[x].rows, &loc_[d.b], info_[x].cols, dest, info_[x].dtype, false,
+                 "literal solve: dense LU, the matrix's structure not examined");
     } else if (d.op == ARMA_OP_SUBMAT) {
       EwStep s;
       s.m = info_[x].rows; s.n = info_[x].cols;

@@ -37,7 +37,7 @@ class Graph:
         if op == "trans":
             r, c = self.shape(d["a"])
             return c, r
-        if op == "matmul":
+        if op in ("matmul", "solve"):
             return self.shape(d["a"])[0], self.shape(d["b"])[1]
         if op == "diagmat":
             r, c = self.shape(d["a"])
@@ -131,6 +131,11 @@ def norm_fro(x: X) -> X:
 
 def inv(x: X) -> X:
     return x.g._add({"op": "inv", "a": x.i})
+
+
+def solve(a: X, b: X) -> X:
+    """X with a X = b (Armadillo's solve(A, B))."""
+    return a.g._add({"op": "solve", "a": a.i, "b": b.i})
 
 
 # ---- the benchmark expressions (seeded shapes; names follow the paper) ----

@@ -186,3 +186,19 @@ def log_uniform_ints(seed: int, stream: int, count: int, lo: int, hi: int) -> np
     u = (z >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
     v = np.exp(math.log(lo) + u * (math.log(hi) - math.log(lo)))
     return np.clip(np.rint(v), lo, hi).astype(np.int64)
+
+
+def band_matrix(seed: int, stream: int, n: int, kl: int, ku: int, dtype: str = "f64",
+                diag_shift: float = 0.0, zero_diag_every: int = 0) -> np.ndarray:
+    """An n x n matrix whose entries on diagonals -kl .. ku are uniform
+    [-1, 1) (the main diagonal shifted by ``diag_shift``) and zero elsewhere.
+    With ``zero_diag_every`` = k > 0, every k-th main-diagonal entry is set
+    to zero, so elimination without row exchanges would break down there."""
+    v = uniform_flat(seed, stream, n * n).reshape((n, n), order="F")
+    i, j = np.indices((n, n))
+    a = np.where((i - j <= kl) & (j - i <= ku), v, 0.0)
+    a[np.arange(n), np.arange(n)] += diag_shift
+    if zero_diag_every > 0:
+        z = np.arange(0, n, zero_diag_every)
+        a[z, z] = 0.0
+    return cast(a, dtype)

@@ -190,6 +190,29 @@ def test_symmetric_products_plan():
     assert p.info["steps"][0]["flops"] == 50 * 51 * 30
 
 
+def test_solve_plans():
+    """solve(A, B) and inv(A)*B plan an analysed solve; the literal plan and
+    the no-analysis flag plan a dense LU; shapes and dtypes are checked"""
+    g = E.Graph()
+    A, B = g.input(0, 40, 40), g.input(1, 40, 3)
+    for e in (E.solve(A, B), E.inv(A) * B):
+        nodes, outs = g.build(e)
+        assert "analysed solve" in ag.Plan(nodes, outs).info["steps"][0]["note"]
+        for f in (ag.PLAN_LITERAL, ag.PLAN_NO_SOLVE_ANALYSIS):
+            assert "analysed" not in " ".join(s["note"] for s in ag.Plan(nodes, outs, flags=f).info["steps"])
+    for bad in (((40, 30), (40, 3)), ((40, 40), (39, 3))):
+        g = E.Graph()
+        nodes, outs = g.build(E.solve(g.input(0, *bad[0]), g.input(1, *bad[1])))
+        with pytest.raises(ag.ArmaError) as ei:
+            ag.Plan(nodes, outs)
+        assert ei.value.status == "shape"
+    g = E.Graph()
+    nodes, outs = g.build(E.solve(g.input(0, 8, 8, "f32"), g.input(1, 8, 1, "f64")))
+    with pytest.raises(ag.ArmaError) as ei:
+        ag.Plan(nodes, outs)
+    assert ei.value.status == "dtype"
+
+
 def test_submatrix_views_in_place():
     """A(:,1) + B(2,:)^T (Sec. III (2)) is one strided pass reading both
     views in place; the literal plan copies both and transposes; views

@@ -243,3 +243,82 @@ def test_submat_against_index_arithmetic(orc):
                 assert got[i, j] == flat[(r0 + i) + (c0 + j) * m]
     with pytest.raises(ValueError):
         orc.submat(np.zeros((3, 3)), 2, 0, 2, 1)
+
+
+# ------------------------------------------------- structured solves (Sec. III (10))
+
+def _band(rng, n, kl, ku):
+    """a matrix whose non-zero diagonals are exactly -kl .. ku (no zeros on them)"""
+    a = np.zeros((n, n))
+    for d in range(-kl, ku + 1):
+        v = rng.uniform(0.5, 1.5, n - abs(d)) * rng.choice([-1.0, 1.0], n - abs(d))
+        a += np.diag(v, d)
+    return a
+
+
+def test_band_widths_and_symmetry(orc):
+    rng = np.random.default_rng(30)
+    for (n, kl, ku) in [(10, 1, 1), (40, 3, 7), (17, 0, 4), (17, 5, 0), (9, 0, 0), (6, 5, 5)]:
+        assert orc.band_widths(_band(rng, n, kl, ku)) == (kl, ku)
+    assert orc.band_widths(np.zeros((5, 5))) == (0, 0)
+    a = np.zeros((8, 8))
+    a[7, 0] = -0.0          # a negative zero is a zero
+    a[0, 6] = 1e-300
+    assert orc.band_widths(a) == (0, 6)
+    s = rng.standard_normal((9, 9))
+    s = s + s.T
+    assert orc.is_symmetric(s)
+    s[2, 5] += 1e-15
+    assert not orc.is_symmetric(s)
+    z = np.eye(4)
+    z[1, 2], z[2, 1] = 0.0, -0.0
+    assert orc.is_symmetric(z)
+
+
+def test_solve_path_order(orc):
+    """the order of the checks in the solve trace of Fig. 3: band first, then
+    triangular, then general; a diagonal matrix is the narrowest band"""
+    rng = np.random.default_rng(31)
+    assert orc.solve_path(_band(rng, 100, 0, 0)) == "diagonal"
+    assert orc.solve_path(_band(rng, 100, 1, 1)) == "band"
+    assert orc.solve_path(_band(rng, 100, 0, 1)) == "band"        # bidiagonal: band before triangular
+    assert orc.solve_path(_band(rng, 400, 31, 32)) == "band"
+    assert orc.solve_path(_band(rng, 300, 31, 32)) == "general"     # 4 (2 kl + ku + 1) > n
+    assert orc.solve_path(_band(rng, 200, 32, 0)) == "lower"        # 32 subdiagonals: not a band
+    assert orc.solve_path(np.triu(rng.standard_normal((50, 50)))) == "upper"
+    assert orc.solve_path(np.tril(rng.standard_normal((50, 50)))) == "lower"
+    assert orc.solve_path(_band(rng, 12, 1, 1)) == "general"      # band storage would not pay
+    assert orc.solve_path(rng.standard_normal((30, 30))) == "general"
+    assert orc.solve_path(_band(rng, 300, 40, 2)) == "general"     # too many subdiagonals
+
+
+def test_solve_band_against_dense_and_exact(orc):
+    rng = np.random.default_rng(32)
+    for (n, kl, ku, k) in [(50, 1, 1, 1), (64, 3, 5, 4), (40, 0, 2, 2), (33, 4, 0, 3)]:
+        a = _band(rng, n, kl, ku)
+        b = rng.standard_normal((n, k))
+        x = orc.solve_band(a, b, kl, ku)
+        ref = np.linalg.solve(a, b)
+        assert np.max(np.abs(x - ref)) <= 1e-10 * max(1.0, np.max(np.abs(ref))) * np.linalg.cond(a)
+    # a zero leading diagonal element: the pivot search must exchange rows
+    a = np.array([[0, 2, 0, 0], [1, 1, 3, 0], [0, 4, 1, 1], [0, 0, 2, 5]], dtype=float)
+    xs = np.array([[1.0], [-2.0], [3.0], [0.5]])
+    x = orc.solve_band(a, a @ xs, 1, 1)
+    assert np.max(np.abs(x - xs)) < 1e-14
+    with pytest.raises(orc.SingularMatrix):
+        orc.solve_band(np.array([[1.0, 2.0, 0.0], [2.0, 4.0, 0.0], [0.0, 1.0, 1.0]]), np.ones((3, 1)), 1, 1)
+
+
+def test_solve_triangular_against_scipy(orc):
+    sla = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(33)
+    for lower in (True, False):
+        a = rng.standard_normal((40, 40)) + 8 * np.eye(40)
+        a = np.tril(a) if lower else np.triu(a)
+        b = rng.standard_normal((40, 3))
+        x = orc.solve_triangular(a, b, lower)
+        assert np.max(np.abs(x - sla.solve_triangular(a, b, lower=lower))) < 1e-13
+    a = np.triu(np.ones((4, 4)))
+    a[2, 2] = 0.0
+    with pytest.raises(orc.SingularMatrix):
+        orc.solve_triangular(a, np.ones((4, 1)), False)

@@ -18,7 +18,8 @@ PINS = [
     T.test_small_integer_brute_force, T.test_accu_vs_fsum_and_dot, T.test_norm_fro,
     T.test_matmul_vs_numpy_and_transpose_identity, T.test_trace_invariants, T.test_diagmat,
     T.test_inverse, T.test_solve_literal_and_backward_error, T.test_exact_fraction_inverse,
-    T.test_submat_against_index_arithmetic,
+    T.test_submat_against_index_arithmetic, T.test_band_widths_and_symmetry, T.test_solve_path_order,
+    T.test_solve_band_against_dense_and_exact, T.test_solve_triangular_against_scipy,
 ]
 
 
@@ -89,6 +90,35 @@ def _mut_submat_row_major(x, r0, c0, rows, cols):
     return np.asfortranarray(x[r0:r0 + rows, c0:c0 + cols])
 
 
+def _mut_band_no_pivoting(a, b, kl, ku):
+    # elimination without the row exchanges
+    u, x = oracle.f64(a).copy(), oracle.f64(b).copy()
+    n = u.shape[0]
+    for j in range(n):
+        if u[j, j] == 0.0:
+            raise oracle.SingularMatrix("zero pivot without row search")
+        for i in range(j + 1, min(j + kl, n - 1) + 1):
+            m = u[i, j] / u[j, j]
+            u[i, j:] -= m * u[j, j:]
+            x[i] -= m * x[j]
+    for j in range(n - 1, -1, -1):
+        x[j] = (x[j] - u[j, j + 1:] @ x[j + 1:]) / u[j, j]
+    return x
+
+
+def _mut_band_widths_swapped(a):
+    kl, ku = _orig_band_widths(a)
+    return ku, kl
+
+
+def _mut_triangular_wrong_side(a, b, lower):
+    return _orig_solve_triangular(a, b, not lower)
+
+
+_orig_band_widths = oracle.band_widths
+_orig_solve_triangular = oracle.solve_triangular
+
+
 MUTANTS = {
     "matmul_transposed_operand": ("matmul", _mut_matmul_transposed),
     "matmul_dropped_term": ("matmul", _mut_matmul_dropped_term),
@@ -100,6 +130,9 @@ MUTANTS = {
     "norm_without_sqrt": ("norm_fro", _mut_norm_no_sqrt),
     "schur_as_sum": ("schur", _mut_schur_as_add),
     "submat_offsets_swapped": ("submat", _mut_submat_row_major),
+    "band_without_pivoting": ("solve_band", _mut_band_no_pivoting),
+    "band_widths_swapped": ("band_widths", _mut_band_widths_swapped),
+    "triangular_wrong_side": ("solve_triangular", _mut_triangular_wrong_side),
 }
 
 
