@@ -108,7 +108,10 @@ typedef enum {
                                ku <= 32 superdiagonals, 4 (2 kl + ku + 1) <= n
                                (tridiagonal systems included) */
   ARMA_SOLVE_UPPER = 4,     /* upper triangular: back substitution */
-  ARMA_SOLVE_LOWER = 5      /* lower triangular: forward substitution */
+  ARMA_SOLVE_LOWER = 5,     /* lower triangular: forward substitution */
+  ARMA_SOLVE_CHOLESKY = 6   /* symmetric with a positive diagonal: Cholesky, no pivoting
+                               (+ refinement per tier); a matrix that turns out not to be
+                               positive definite is solved by the general LU (path 1) */
 } arma_solve_path;
 
 /* Precision tier for products and solves (elementwise work always runs in

@@ -479,7 +479,9 @@ def solve_path(a) -> str:
     """The solver the analysis selects, tried in the order of the solve trace
     of Fig. 3: a diagonal matrix; a band matrix (at most 31 sub- and 32
     superdiagonals, and band storage at most a quarter of the rows); an
-    upper or lower triangular matrix; otherwise the general solver."""
+    upper or lower triangular matrix; a symmetric matrix with a positive
+    diagonal whose Cholesky factorisation succeeds; otherwise the general
+    solver."""
     a = f64(a)
     n = a.shape[0]
     kl, ku = band_widths(a)
@@ -491,7 +493,35 @@ def solve_path(a) -> str:
         return "upper"
     if ku == 0:
         return "lower"
+    if n > 1 and is_symmetric(a) and bool(np.all(np.diag(a) > 0.0)):
+        try:
+            cholesky(a)
+            return "cholesky"
+        except NotPositiveDefinite:
+            pass
     return "general"
+
+
+class NotPositiveDefinite(ArithmeticError):
+    pass
+
+
+def cholesky(a):
+    """Lower-triangular L with L L^T = A, column by column: l_jj is the square
+    root of a_jj minus the squares already in row j, the entries below it are
+    the remaining inner products divided by l_jj.  Raises NotPositiveDefinite
+    when a pivot is not positive."""
+    a = f64(a)
+    n = a.shape[0]
+    L = np.zeros((n, n), order="F")
+    for j in range(n):
+        d = a[j, j] - float(np.dot(L[j, :j], L[j, :j]))
+        if not d > 0.0:
+            raise NotPositiveDefinite(f"cholesky: pivot {d!r} in column {j}")
+        L[j, j] = math.sqrt(d)
+        for i in range(j + 1, n):
+            L[i, j] = (a[i, j] - float(np.dot(L[i, :j], L[j, :j]))) / L[j, j]
+    return L
 
 
 def solve_band(a, b, kl: int, ku: int):

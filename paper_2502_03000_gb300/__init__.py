@@ -284,7 +284,7 @@ class Plan:
         return STATUS.get(code, str(code)), int(info.value)
 
 
-SOLVE_PATHS = {0: "none", 1: "general", 2: "diagonal", 3: "band", 4: "upper", 5: "lower"}
+SOLVE_PATHS = {0: "none", 1: "general", 2: "diagonal", 3: "band", 4: "upper", 5: "lower", 6: "cholesky"}
 
 
 def _solve_path(self, workspace=None, stream=None):

@@ -228,7 +228,7 @@ arma_status arma_gpu_eval_solve_path(const arma_plan* plan, const void* workspac
                                      int32_t* path, int32_t* kl, int32_t* ku, int32_t* symmetric) {
   if (!plan || !workspace) return ARMA_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int32_t rec[SP_WORDS] = {0, 0, 0, 0, 0, 0};
+  int32_t rec[SP_WORDS] = {};
   if (cudaError_t e = cudaStreamSynchronize(s)) return cuda_status(e);
   if (cudaError_t e = cudaMemcpy(rec, static_cast<const char*>(workspace) + kSolveRecordOffset, sizeof rec,
                                  cudaMemcpyDeviceToHost))

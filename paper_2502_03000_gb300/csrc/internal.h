@@ -232,7 +232,7 @@ struct SolveStep {
 // The solve record in the workspace header (int32 words at byte 16): the
 // solver taken and what the analysis of A found.
 enum SolveProp : int32_t { SP_PATH = 0, SP_KL = 1, SP_KU = 2, SP_ASYM = 3, SP_ZDIAG = 4, SP_FALLBACK = 5,
-                           SP_WORDS = 6 };
+                           SP_NONPOS = 6, SP_WORDS = 7 };
 constexpr size_t kSolveRecordOffset = 16;
 
 // band solver limits: kl <= 31 keeps the pivot candidates within one warp

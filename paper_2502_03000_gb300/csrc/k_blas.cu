@@ -467,16 +467,21 @@ int64_t gemm_scratch_bytes(const GemmStep& g) {
   return tc > simt ? tc : simt;
 }
 
-bool gemm_sym_valid(const GemmArgs& a) {
-  return a.sym && a.m == a.n && a.A == a.B && a.lda == a.ldb && a.adt == a.bdt && a.ta != a.tb &&
-         !(a.C && a.beta != 0.0) && !a.rs && !a.cs;
+// sym 1: a symmetric product (no beta*C), mirrored; sym 2: only the lower
+// triangle of D is computed (with beta*C), the upper triangle is untouched
+int gemm_sym_valid(const GemmArgs& a) {
+  if (!(a.sym == 1 || a.sym == 2) || a.m != a.n || a.A != a.B || a.lda != a.ldb || a.adt != a.bdt ||
+      a.ta == a.tb || a.rs || a.cs)
+    return 0;
+  if (a.sym == 1 && a.C && a.beta != 0.0) return 0;
+  return a.sym;
 }
 
 cudaError_t launch_gemm(const GemmArgs& a0, cudaStream_t s, int* launches) {
   if (a0.m == 0 || a0.n == 0) return cudaSuccess;
   if (a0.n == 1 || a0.m == 1) return launch_gemv(a0, s, launches);
   GemmArgs a = a0;
-  a.sym = gemm_sym_valid(a0) ? 1 : 0;   // anything else is a general product
+  a.sym = gemm_sym_valid(a0);   // anything else is a general product
   if (a.tier != ARMA_TIER_F64 && gemm_tc_supported(a)) return launch_gemm_tc(a, s, launches);
   int splits = simt_splits(a.m, a.n, a.k);
   if (splits > 1 && (!a.scratch || a.scratch_bytes < (int64_t)splits * a.m * a.n * 8)) splits = 1;
@@ -494,7 +499,7 @@ cudaError_t launch_gemm(const GemmArgs& a0, cudaStream_t s, int* launches) {
     gemm_simt_combine_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(a, splits);
     if (launches) ++*launches;
   }
-  if (a.sym) {
+  if (a.sym == 1) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_mirror_lower(a.D, a.n, a.ldd, a.ddt, s, launches);

@@ -75,7 +75,8 @@ struct Params {
   const void* rs; int64_t rs_inc; int32_t rsdt;
   const void* cs; int64_t cs_inc; int32_t csdt;
   int32_t* status;          // workspace status word (0 = ok)
-  int32_t sym;              // 1: X X^T / X^T X, lower-triangle tiles only (tiles_m == 2 tiles_n)
+  int32_t sym;              // 1, 2: X X^T / X^T X, lower-triangle tiles only (tiles_m == 2 tiles_n)
+  const int* skip;          // optional: return at once when *skip != 0
 };
 
 struct WorkItem {
@@ -139,6 +140,7 @@ __device__ __forceinline__ WorkItem work_item(const Params& p, int32_t w) {
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ Params p) {
+  if (p.skip && *p.skip) return;            // uniform: before any barrier or TMEM allocation
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -474,6 +476,7 @@ struct PrepArgs {
   int64_t R, K, rpad, kp;
   int32_t slices;        // 1 or 3
   __nv_bfloat16* out;    // [slices][rpad][kp]
+  const int* skip;       // optional: return at once when *skip != 0
 };
 
 // 32 x 32 tiles through shared memory: read along X's contiguous index,
@@ -512,6 +515,7 @@ __device__ __forceinline__ void prep_tile_load(const PrepArgs& a, int64_t r0, in
 
 __global__ void __launch_bounds__(256) prep_kernel(const __grid_constant__ PrepArgs a) {
   __shared__ uint16_t t[3][32][33];
+  if (a.skip && *a.skip) return;
   if (a.slices != 1 && a.slices != 3) return;   // the tile above holds at most 3 slices
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t r0 = (int64_t)blockIdx.x * 32, l0 = (int64_t)blockIdx.y * 32;
@@ -559,6 +563,7 @@ __device__ __forceinline__ void prep_group(const PrepArgs& a, int64_t r, int64_t
 
 __global__ void __launch_bounds__(256) prep_kcontig_kernel(const __grid_constant__ PrepArgs a) {
   if (a.slices != 1 && a.slices != 3) return;
+  if (a.skip && *a.skip) return;
   // 32-bit index arithmetic (the host keeps rpad * kp / 8 below 2^31): a
   // 64-bit division per group costs more than the conversion itself
   const uint32_t groups = (uint32_t)(a.kp / 8);
@@ -594,9 +599,11 @@ struct CombineArgs {
   const void* rs; int64_t rs_inc; int32_t rsdt;
   const void* cs; int64_t cs_inc; int32_t csdt;
   int32_t sym;   // partials hold the lower-triangle tiles only
+  const int* skip;
 };
 
 __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ CombineArgs a) {
+  if (a.skip && *a.skip) return;
   const int64_t total = a.m * a.n;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -710,6 +717,7 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   PrepArgs pa;
   pa.X = a.A; pa.ldx = a.lda; pa.xdt = a.adt; pa.trans = a.ta;
   pa.R = a.m; pa.K = a.k; pa.rpad = g.mpad; pa.kp = g.kp; pa.slices = g.slices; pa.out = As;
+  pa.skip = a.skip;
   const int sms0 = device_sm_count();
   auto prep = [&](const PrepArgs& pp) {
     if (pp.trans && pp.rpad * (pp.kp / 8) < (1ll << 31)) {
@@ -726,6 +734,7 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   PrepArgs pb;
   pb.X = a.B; pb.ldx = a.ldb; pb.xdt = a.bdt; pb.trans = a.tb ? 0 : 1;
   pb.R = a.n; pb.K = a.k; pb.rpad = g.npad; pb.kp = g.kp; pb.slices = g.slices; pb.out = Bs;
+  pb.skip = a.skip;
   if (!sym) prep(pb);
   if (launches) *launches += sym ? 1 : 2;
   cudaError_t e = cudaGetLastError();
@@ -755,6 +764,7 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   p.cs = a.cs; p.cs_inc = a.cs_inc; p.csdt = a.csdt;
   p.status = a.status;
   p.sym = sym ? 1 : 0;
+  p.skip = a.skip;
 
   static bool attr_set[64] = {false};
   int dev = 0;
@@ -773,7 +783,7 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   if (launches) ++*launches;
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (g.splits == 1) return sym ? launch_mirror_lower(a.D, a.n, a.ldd, a.ddt, s, launches) : e;
+  if (g.splits == 1) return a.sym == 1 ? launch_mirror_lower(a.D, a.n, a.ldd, a.ddt, s, launches) : e;
 
   CombineArgs c;
   c.m = a.m; c.n = a.n; c.splits = g.splits; c.P = P;
@@ -783,12 +793,13 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   c.rs = a.rs; c.rs_inc = a.rs_inc; c.rsdt = a.rsdt;
   c.cs = a.cs; c.cs_inc = a.cs_inc; c.csdt = a.csdt;
   c.sym = sym ? 1 : 0;
+  c.skip = a.skip;
   const int64_t total = a.m * a.n;
   int64_t blocks = (total + 255) / 256, cap = (int64_t)sms * 8;
   combine_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(c);
   if (launches) ++*launches;
   e = cudaGetLastError();
-  if (e != cudaSuccess || !sym) return e;
+  if (e != cudaSuccess || a.sym != 1) return e;
   return launch_mirror_lower(a.D, a.n, a.ldd, a.ddt, s, launches);
 }
 

@@ -51,7 +51,7 @@ struct Ctl {                    // device control block in the solve scratch
   int err;                      // barrier timeout
   int done;                     // refinement converged
   int steps;                    // refinement steps taken
-  int pad;
+  int chol_fail;                // Cholesky met a pivot <= 0: 1 + its column
   double nrmA, nrmB, nrmR, nrmX;
 };
 
@@ -1427,10 +1427,119 @@ cudaError_t factor(const SolveArgs& a, const Layout& L, char* base, cudaStream_t
 // matrix W (leading dimension lda): sweeps = 1 for lower (non-unit
 // diagonal, result in Z), 2 for upper (result in Y), 3 for LU factors
 // (unit lower L; result in Y).
+// ---------------------------------------------------------------------------
+// Cholesky A = L L^T for symmetric positive definite A (the symmetric branch
+// of the solve trace, Fig. 3): right-looking, 64-column panels, no pivoting.
+// Per panel: the diagonal block is factored in shared memory by one CTA and
+// inverted (the substitution's inverse-diagonal-block kernel); the rows below
+// become L_21 = A_21 L_jj^-T, a product; the trailing matrix takes
+// A_22 -= L_21 L_21^T through the product kernels' lower-triangle schedule
+// (sym = 2).  A pivot <= 0 (or NaN) means A is not positive definite: the
+// column is recorded in the control block and every later kernel of the
+// factorisation returns at once.
+// ---------------------------------------------------------------------------
+// The diagonal block: S holds the not yet factored part (lower triangle).
+// Step c: every thread reads the pivot S[c][c] itself (no extra barrier),
+// thread (r, g) = (tid % 64, tid / 64) subtracts l_r l_k from S[r][k] for
+// k = c + 1 + g, c + 5 + g, ... <= r, and L's column c goes straight to
+// global memory, so S's column c is only read during the step: one barrier
+// per column.
+template <typename T>
+__global__ void __launch_bounds__(256) chol_diag_kernel(T* W, int64_t ld, int64_t j, int w, Ctl* ctl) {
+  __shared__ T S[NB][NB + 1];   // S[r][c] = block (r, c), lower part
+  if (*(volatile int*)&ctl->chol_fail) return;
+  const int tid = threadIdx.x, r = tid & (NB - 1), g = tid >> 6;
+  for (int t = tid; t < NB * NB; t += 256) {
+    const int rr = t & (NB - 1), cc = t >> 6;
+    S[rr][cc] = (rr < w && cc < w && rr >= cc) ? W[(j + rr) + (j + cc) * ld] : (T)0;
+  }
+  for (int c = 0; c < w; ++c) {
+    __syncthreads();
+    const T d = S[c][c];
+    if (!(d > (T)0)) {                       // uniform: every thread read the same pivot
+      if (tid == 0) atomicCAS(&ctl->chol_fail, 0, (int)(j + c + 1));
+      return;
+    }
+    const T sq = sqrt(d), inv = (T)1 / sq;
+    if (r > c && r < w) {
+      const T lr = S[r][c] * inv;
+      for (int k = c + 1 + g; k <= r; k += 4) S[r][k] -= lr * (S[k][c] * inv);
+      if (g == 0) W[(j + r) + (j + c) * ld] = lr;
+    }
+    if (tid == 0) W[(j + c) + (j + c) * ld] = sq;
+  }
+}
+
+__global__ void iota_kernel(int32_t* p, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = (int32_t)i;
+}
+
+// W := the Cholesky factor of A in its lower triangle (the upper triangle is
+// left as scratch; the caller mirrors L into it for the substitution)
+template <typename T>
+cudaError_t factor_cholesky(const SolveArgs& a, const Layout& L, char* base, cudaStream_t s, int* launches) {
+  const int64_t n = a.n;
+  T* W = reinterpret_cast<T*>(base + L.lu);
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + L.ctl);
+  const int sms = device_sm_count();
+  {
+    int64_t blocks = (n * n + 255) / 256, cap = (int64_t)sms * 8;
+    copy_kernel<T><<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(a.A, a.lda, a.adt, W, n);
+    if (launches) ++*launches;
+  }
+  const int32_t gt = L.f64 ? ARMA_TIER_F64 : a.tier == ARMA_TIER_BF16 ? ARMA_TIER_BF16 : ARMA_TIER_SPLIT_BF16;
+  const int64_t nb = (n + NB - 1) / NB;
+  T* Dinv = reinterpret_cast<T*>(base + L.dinv);   // [2 nb][NB][NB]; rewritten after the factorisation
+  const int dt = L.f64 ? ARMA_F64 : ARMA_F32;
+  for (int64_t j = 0; j < n; j += NB) {
+    const int w = (int)(n - j < NB ? n - j : NB);
+    chol_diag_kernel<T><<<1, 256, 0, s>>>(W, n, j, w, ctl);
+    if (launches) ++*launches;
+    const int64_t rest = n - j - w;
+    if (rest <= 0) continue;
+    // L_jj^-1 (non-unit lower), then L_21 = A_21 (L_jj^-1)^T in place
+    T* Li = Dinv + (j / NB) * NB * NB;
+    inv_diag_kernel<T><<<1, 256, 0, s>>>(W + j + j * n, (int64_t)w, Li, Dinv + (nb + j / NB) * NB * NB, n, 1);
+    if (launches) ++*launches;
+    {
+      GemmArgs t;
+      memset(&t, 0, sizeof t);
+      t.m = rest; t.n = w; t.k = w;
+      t.A = W + (j + w) + j * n; t.lda = n; t.ta = 0; t.adt = dt;
+      t.B = Li; t.ldb = NB; t.tb = 1; t.bdt = dt;
+      t.D = W + (j + w) + j * n; t.ldd = n; t.ddt = dt;
+      t.alpha = 1.0;
+      t.tier = gt;
+      t.scratch = base + L.gemm; t.scratch_bytes = L.gemm_bytes;
+      t.status = a.status_code;
+      t.skip = &ctl->chol_fail;
+      cudaError_t e = launch_gemm(t, s, launches);
+      if (e != cudaSuccess) return e;
+    }
+    GemmArgs g;
+    memset(&g, 0, sizeof g);
+    g.m = rest; g.n = rest; g.k = w;
+    g.A = W + (j + w) + j * n; g.lda = n; g.ta = 0; g.adt = dt;
+    g.B = W + (j + w) + j * n; g.ldb = n; g.tb = 1; g.bdt = dt;
+    g.C = W + (j + w) + (j + w) * n; g.ldc = n; g.cdt = dt;
+    g.D = W + (j + w) + (j + w) * n; g.ldd = n; g.ddt = dt;
+    g.alpha = -1.0; g.beta = 1.0;
+    g.tier = gt;
+    g.sym = 2;                                   // lower triangle only, C kept
+    g.scratch = base + L.gemm; g.scratch_bytes = L.gemm_bytes;
+    g.status = a.status_code;
+    g.skip = &ctl->chol_fail;
+    cudaError_t e = launch_gemm(g, s, launches);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t substitute(const T* W, const T* Linv, const T* Uinv, int64_t n, T* Y, T* Z, int64_t nrhs,
                        unsigned int* flags, Ctl* ctl, int32_t* status, const int* skip, cudaStream_t s,
-                       int* launches, int64_t lda = 0, int sweeps = 3) {
+                       int* launches, int64_t lda = 0, int sweeps = 3, int unit_lower = 1) {
   if (lda == 0) lda = n;
   const int64_t nb = (n + NB - 1) / NB;
   const int64_t gy = (nrhs + 63) / 64;
@@ -1469,7 +1578,7 @@ cudaError_t substitute(const T* W, const T* Linv, const T* Uinv, int64_t n, T* Y
       const int w = (int)(n - j < NB ? n - j : NB);
       const int64_t rows = n - j - w;
       sub_step_kernel<T, true><<<dim3(gx(rows), (unsigned)gy), 256, smem, s>>>(W, n, j, w, Y, Z, nrhs, j + w, rows,
-                                                                               skip, lda, sweeps == 3 ? 1 : 0);
+                                                                               skip, lda, unit_lower);
       if (launches) ++*launches;
     }
   } else {
@@ -1518,7 +1627,7 @@ cudaError_t solve_triangular(const SolveArgs& a, const Layout& L, char* base, bo
   rhs_kernel<T><<<g, 256, 0, s>>>(a.B, a.ldb, a.bdt, Y, n, nrhs);
   if (launches) *launches += 2;
   cudaError_t e = substitute<T>(W, Linv, Uinv, n, Y, Z, nrhs, reinterpret_cast<unsigned int*>(base + L.flags), ctl,
-                                a.status_code, nullptr, s, launches, a.lda, lower ? 1 : 2);
+                                a.status_code, nullptr, s, launches, a.lda, lower ? 1 : 2, 0);
   if (e != cudaSuccess) return e;
   store_kernel<T><<<g, 256, 0, s>>>(lower ? Z : Y, n, nrhs, a.X, a.ldx, a.xdt);
   if (launches) ++*launches;
@@ -1531,15 +1640,16 @@ cudaError_t solve_triangular(const SolveArgs& a, const Layout& L, char* base, bo
 // host waits for the analysis: the choice is made on the host, as the
 // library's CPU counterpart does.  Under stream capture nothing is analysed.
 bool solve_structured(const SolveArgs& a, const Layout& L, char* base, Ctl* ctl, cudaStream_t s, int* launches,
-                      cudaError_t* err) {
+                      cudaError_t* err, bool* try_chol) {
   *err = cudaSuccess;
+  *try_chol = false;
   if (!a.analyse || !a.props) return false;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if ((*err = cudaStreamIsCapturing(s, &cs)) != cudaSuccess) return true;
   if (cs != cudaStreamCaptureStatusNone) return false;
   const int64_t n = a.n;
   if ((*err = launch_analyse(a.A, a.lda, a.adt, n, a.props, s, launches)) != cudaSuccess) return true;
-  int32_t h[SP_WORDS] = {0, 0, 0, 0, 0, 0};
+  int32_t h[SP_WORDS] = {};
   if ((*err = cudaMemcpyAsync(h, a.props, sizeof h, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return true;
   if ((*err = cudaStreamSynchronize(s)) != cudaSuccess) return true;
   const int32_t kl = h[SP_KL], ku = h[SP_KU], zd = h[SP_ZDIAG];
@@ -1557,7 +1667,12 @@ bool solve_structured(const SolveArgs& a, const Layout& L, char* base, Ctl* ctl,
   const int64_t sing = (tri && zd > 0) ? n - zd + 1 : 0;
   if ((*err = launch_set_props(a.props, path, a.status_code, a.status_info, sing, s, launches)) != cudaSuccess)
     return true;
-  if (path == ARMA_SOLVE_GENERAL) return false;
+  if (path == ARMA_SOLVE_GENERAL) {
+    // symmetric with a positive diagonal: worth a Cholesky attempt (recorded
+    // by the caller once the factorisation has shown whether it succeeded)
+    *try_chol = typed && h[SP_ASYM] == 0 && h[SP_NONPOS] == 0 && n > 1;
+    return false;
+  }
   if (sing) return true;
   switch (path) {
     case ARMA_SOLVE_DIAGONAL:
@@ -1600,7 +1715,8 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
   Ctl* ctl = reinterpret_cast<Ctl*>(base + L.ctl);
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s);
   if (e != cudaSuccess) return e;
-  if (solve_structured(a, L, base, ctl, s, launches, &e)) return e;
+  bool chol = false;
+  if (solve_structured(a, L, base, ctl, s, launches, &e, &chol)) return e;
   if (e != cudaSuccess) return e;
   const int sms = device_sm_count();
   int32_t* piv = reinterpret_cast<int32_t*>(base + L.piv);
@@ -1611,37 +1727,60 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
     int64_t b = (total + 255) / 256, cap = (int64_t)sms * 8;
     return (unsigned)(b < 1 ? 1 : b < cap ? b : cap);
   };
+  // Cholesky first when the analysis allows it; a pivot <= 0 sends the
+  // solve to the LU factorisation (the host waits once more to know)
+  auto try_cholesky = [&](auto tag) -> cudaError_t {
+    using T = decltype(tag);
+    cudaError_t ee = factor_cholesky<T>(a, L, base, s, launches);
+    if (ee != cudaSuccess) return ee;
+    int fail = 0;
+    if ((ee = cudaMemcpyAsync(&fail, &ctl->chol_fail, sizeof fail, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return ee;
+    if ((ee = cudaStreamSynchronize(s)) != cudaSuccess) return ee;
+    chol = fail == 0;
+    if ((ee = launch_set_props(a.props, chol ? ARMA_SOLVE_CHOLESKY : ARMA_SOLVE_GENERAL, a.status_code,
+                               a.status_info, 0, s, launches)) != cudaSuccess)
+      return ee;
+    if (!chol) return factor<T>(a, L, base, s, launches);
+    // the substitution reads U from the upper triangle: U = L^T, and an
+    // identity permutation
+    T* W = reinterpret_cast<T*>(base + L.lu);
+    if ((ee = launch_mirror_lower(W, n, n, L.f64 ? ARMA_F64 : ARMA_F32, s, launches)) != cudaSuccess) return ee;
+    iota_kernel<<<grid_for(n), 256, 0, s>>>(piv, n);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+  };
   if (L.f64) {
-    e = factor<double>(a, L, base, s, launches);
+    e = chol ? try_cholesky(0.0) : factor<double>(a, L, base, s, launches);
     if (e != cudaSuccess) return e;
     const double* W = reinterpret_cast<const double*>(base + L.lu);
     double* Linv = reinterpret_cast<double*>(base + L.dinv);
     double* Uinv = Linv + nb * NB * NB;
-    inv_diag_kernel<double><<<(unsigned)nb, 256, 0, s>>>(W, n, Linv, Uinv);
+    inv_diag_kernel<double><<<(unsigned)nb, 256, 0, s>>>(W, n, Linv, Uinv, 0, chol ? 1 : 0);
     double* Y = reinterpret_cast<double*>(base + L.y);
     e = launch_perm(piv, perm, n, s);
     if (e != cudaSuccess) return e;
     gather_kernel<double><<<grid_for(n * nrhs), 256, 0, s>>>(a.B, a.ldb, a.bdt, perm, Y, n, nrhs, nullptr);
     e = substitute<double>(W, Linv, Uinv, n, Y, reinterpret_cast<double*>(base + L.z), nrhs, flags, ctl,
-                           a.status_code, nullptr, s, launches);
+                           a.status_code, nullptr, s, launches, 0, 3, chol ? 0 : 1);
     if (e != cudaSuccess) return e;
     store_kernel<double><<<grid_for(n * nrhs), 256, 0, s>>>(Y, n, nrhs, a.X, a.ldx, a.xdt);
     if (launches) *launches += 4;
     return cudaGetLastError();
   }
-  e = factor<float>(a, L, base, s, launches);
+  e = chol ? try_cholesky(0.0f) : factor<float>(a, L, base, s, launches);
   if (e != cudaSuccess) return e;
   const float* W = reinterpret_cast<const float*>(base + L.lu);
   float* Linv = reinterpret_cast<float*>(base + L.dinv);
   float* Uinv = Linv + nb * NB * NB;
-  inv_diag_kernel<float><<<(unsigned)nb, 256, 0, s>>>(W, n, Linv, Uinv);
+  inv_diag_kernel<float><<<(unsigned)nb, 256, 0, s>>>(W, n, Linv, Uinv, 0, chol ? 1 : 0);
   if (launches) ++*launches;
   float* Y = reinterpret_cast<float*>(base + L.y);
   e = launch_perm(piv, perm, n, s);
   if (e != cudaSuccess) return e;
   gather_kernel<float><<<grid_for(n * nrhs), 256, 0, s>>>(a.B, a.ldb, a.bdt, perm, Y, n, nrhs, nullptr);
   float* Z = reinterpret_cast<float*>(base + L.z);
-  e = substitute<float>(W, Linv, Uinv, n, Y, Z, nrhs, flags, ctl, a.status_code, nullptr, s, launches);
+  e = substitute<float>(W, Linv, Uinv, n, Y, Z, nrhs, flags, ctl, a.status_code, nullptr, s, launches, 0, 3,
+                        chol ? 0 : 1);
   if (e != cudaSuccess) return e;
   if (launches) *launches += 2;
   if (!L.refine || !a.B) {
@@ -1685,7 +1824,8 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
     ir_check_kernel<<<1, 32, 0, s>>>(ctl, sq + 2, it, a.status_code, a.status_info, it == MAX_IR);
     // d = (LU)^-1 P r in FP32; x += d
     gather_kernel<float><<<grid_for(n * nrhs), 256, 0, s>>>(R64, n, ARMA_F64, perm, Y, n, nrhs, &ctl->done);
-    e = substitute<float>(W, Linv, Uinv, n, Y, Z, nrhs, flags, ctl, a.status_code, &ctl->done, s, launches);
+    e = substitute<float>(W, Linv, Uinv, n, Y, Z, nrhs, flags, ctl, a.status_code, &ctl->done, s, launches, 0, 3,
+                          chol ? 0 : 1);
     if (e != cudaSuccess) return e;
     ir_update_kernel<<<grid_for(n * nrhs), 256, 0, s>>>(X64, Y, n * nrhs, &ctl->done);
     if (launches) *launches += 7;

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) analyse_kernel(const E* __restrict__ A, i
   const int64_t bi = blockIdx.y, bj = blockIdx.x;
   if (bi < bj) return;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  int kl = 0, ku = 0, asym = 0, zd = 0;
+  int kl = 0, ku = 0, asym = 0, zd = 0, nonpos = 0;
   // mirror tile: element (r, c) = (32 bj + tx, 32 bi + q) kept as t[q][tx]
   for (int q = ty; q < 32; q += 8) {
     const int64_t r = bj * 32 + tx, c = bi * 32 + q;
@@ -77,13 +77,16 @@ __global__ void __launch_bounds__(256) analyse_kernel(const E* __restrict__ A, i
     } else if (i == j) {
       zd = max(zd, (int)(n - i));
     }
+    if (i == j && !(v > E(0))) nonpos = 1;     // a diagonal element <= 0 (or NaN)
     if (!same(v, t[tx][q])) asym = 1;
   }
   kl = __reduce_max_sync(0xffffffffu, kl);
   ku = __reduce_max_sync(0xffffffffu, ku);
   asym = __reduce_or_sync(0xffffffffu, asym);
   zd = __reduce_max_sync(0xffffffffu, zd);
+  nonpos = __reduce_or_sync(0xffffffffu, nonpos);
   if ((threadIdx.x & 31) == 0) {
+    if (nonpos) atomicOr(props + SP_NONPOS, 1);
     if (kl) atomicMax(props + SP_KL, kl);
     if (ku) atomicMax(props + SP_KU, ku);
     if (asym) atomicOr(props + SP_ASYM, 1);

@@ -45,7 +45,7 @@ def expect(a, b):
         return path, oracle.solve_band(a, b, kl, ku)
     if path in ("upper", "lower"):
         return path, oracle.solve_triangular(a, b, path == "lower")
-    return path, oracle.matmul(oracle.inv(a), b)
+    return path, oracle.matmul(oracle.inv(a), b)      # "cholesky" and "general": the definition
 
 
 TOL = {"f64": 1e-11, "f32": 2e-4}
@@ -194,3 +194,50 @@ def test_tridiagonal_tiers_and_fallback(torch):
     x = run(plan, tiny, b)
     assert plan.status()[0] == "ok" and plan.solve_path()[0] == "band"
     assert oracle.rel_err(x, oracle.solve_band(tiny, b, 1, 1)) <= 1e-13
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n,k", [(2, 1), (64, 1), (130, 7), (1000, 64), (777, 3)])
+def test_cholesky(torch, dtype, n, k):
+    """a symmetric positive definite matrix takes the Cholesky path (panels
+    of 64, ragged last panel); FP64 data is refined in FP64"""
+    m = synth.matrix(2900 + n, 1, n, n, "f64")
+    a = synth.cast(m @ m.T / n + np.eye(n), dtype)
+    b = synth.matrix(2900 + n, 2, n, k, dtype)
+    assert check_solve(solve_plan(n, k, dtype), a, b, dtype, f"n={n} k={k}") == "cholesky"
+
+
+@pytest.mark.parametrize("tier", ["native", "f64"])
+def test_cholesky_ill_conditioned(torch, tier):
+    """A = Q diag(s) Q^T with condition number 1e6 (the symmetric variant of
+    the solve benchmark's matrix): refined to the general solve's stopping rule
+    (native tier), or factored in FP64 (f64 tier)"""
+    n, k = 1024, 16
+    a = synth.conditioned_matrix(3000, n, 1e6, symmetric=True)
+    b = synth.matrix(3000, 2, n, k, "f64")
+    g = E.Graph()
+    nodes, outs = g.build(E.solve(g.input(0, n, n), g.input(1, n, k)))
+    plan = ag.Plan(nodes, outs, tier=tier)
+    x = run(plan, a, b)
+    assert plan.solve_path()[0] == "cholesky" and plan.status()[0] == "ok"
+    assert oracle.backward_error(a, x, b) <= 1e-14
+    ref = oracle.matmul(oracle.inv(a), b)
+    assert oracle.rel_err(x, ref) <= 1e-16 * 1e6 * 100
+
+
+def test_symmetric_not_positive_definite(torch):
+    """symmetric with a positive diagonal but indefinite: the Cholesky attempt
+    fails and the general LU solves it; a negative diagonal element skips the
+    attempt"""
+    n, k = 300, 2
+    m = synth.matrix(3100, 1, n, n, "f64")
+    spd = m @ m.T / n + np.eye(n)
+    ind = spd.copy()
+    ind[10, 20] = ind[20, 10] = 50.0
+    neg = spd.copy()
+    neg[5, 5] = -2.0
+    b = synth.matrix(3100, 2, n, k, "f64")
+    for a in (ind, neg):
+        plan = solve_plan(n, k)
+        assert check_solve(plan, a, b, "f64", "indefinite") == "general"
+        assert plan.solve_path()[3] is True

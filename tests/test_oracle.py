@@ -322,3 +322,25 @@ def test_solve_triangular_against_scipy(orc):
     a[2, 2] = 0.0
     with pytest.raises(orc.SingularMatrix):
         orc.solve_triangular(a, np.ones((4, 1)), False)
+
+
+def test_cholesky_against_numpy(orc):
+    rng = np.random.default_rng(34)
+    for n in (1, 5, 40):
+        m = rng.standard_normal((n, n))
+        a = m @ m.T + n * np.eye(n)
+        L = orc.cholesky(a)
+        assert np.allclose(L, np.tril(L)) and np.all(np.diag(L) > 0)
+        assert np.max(np.abs(L - np.linalg.cholesky(a))) < 1e-12 * max(1.0, np.max(np.abs(L)))
+    # symmetric with a positive diagonal, but indefinite
+    with pytest.raises(orc.NotPositiveDefinite):
+        orc.cholesky(np.array([[1.0, 2.0], [2.0, 1.0]]))
+    spd = rng.standard_normal((30, 30))
+    spd = spd @ spd.T + 30 * np.eye(30)
+    assert orc.solve_path(spd) == "cholesky"
+    ind = spd.copy()
+    ind[0, 1] = ind[1, 0] = 1e3
+    assert orc.solve_path(ind) == "general"
+    neg = spd.copy()
+    neg[3, 3] = -1.0
+    assert orc.solve_path(neg) == "general"

@@ -20,6 +20,7 @@ PINS = [
     T.test_inverse, T.test_solve_literal_and_backward_error, T.test_exact_fraction_inverse,
     T.test_submat_against_index_arithmetic, T.test_band_widths_and_symmetry, T.test_solve_path_order,
     T.test_solve_band_against_dense_and_exact, T.test_solve_triangular_against_scipy,
+    T.test_cholesky_against_numpy,
 ]
 
 
@@ -115,6 +116,21 @@ def _mut_triangular_wrong_side(a, b, lower):
     return _orig_solve_triangular(a, b, not lower)
 
 
+def _mut_cholesky_no_sqrt(a):
+    # the pivot itself instead of its square root
+    a = oracle.f64(a)
+    n = a.shape[0]
+    L = np.zeros((n, n))
+    for j in range(n):
+        d = a[j, j] - L[j, :j] @ L[j, :j]
+        if not d > 0:
+            raise oracle.NotPositiveDefinite("pivot")
+        L[j, j] = d
+        for i in range(j + 1, n):
+            L[i, j] = (a[i, j] - L[i, :j] @ L[j, :j]) / L[j, j]
+    return L
+
+
 _orig_band_widths = oracle.band_widths
 _orig_solve_triangular = oracle.solve_triangular
 
@@ -133,6 +149,7 @@ MUTANTS = {
     "band_without_pivoting": ("solve_band", _mut_band_no_pivoting),
     "band_widths_swapped": ("band_widths", _mut_band_widths_swapped),
     "triangular_wrong_side": ("solve_triangular", _mut_triangular_wrong_side),
+    "cholesky_without_sqrt": ("cholesky", _mut_cholesky_no_sqrt),
 }
 
 
@@ -147,6 +164,6 @@ def test_planted_mistake_is_caught(orc, monkeypatch, name):
     for pin in PINS:
         try:
             pin(oracle)
-        except (AssertionError, ValueError, oracle.SingularMatrix, IndexError):
+        except (AssertionError, ValueError, oracle.SingularMatrix, oracle.NotPositiveDefinite, IndexError):
             caught += 1
     assert caught > 0, f"no pin caught the planted mistake {name}"
