@@ -56,12 +56,18 @@ def args():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--workload", default="fused",
-                   choices=["fused", "products", "chain", "solve", "plain", "batched", "planner"],
+                   choices=["fused", "products", "chain", "solve", "plain", "batched", "planner", "structured"],
                    help="fused (default) is the benchmark line; the others measure the remaining "
                         "expression families and print one JSON line each")
     p.add_argument("--tiers", default="bf16,split_bf16")
     p.add_argument("--solve-tiers", default="lu32_ir64,f64,split_bf16,bf16")
     p.add_argument("--no-literal", action="store_true")
+    p.add_argument("--solve-matrix", default="both", choices=["both", "nonsymmetric", "symmetric"],
+                   help="solve workload: the non-symmetric matrix (LU) and/or its symmetric "
+                        "positive definite variant (Cholesky)")
+    p.add_argument("--sizes", default="100,250,500,1000,4096",
+                   help="structured workload: tridiagonal sizes")
+    p.add_argument("--dtype", default="f64", choices=["f64", "f32"], help="structured workload: element type")
     return p.parse_args()
 
 
@@ -403,7 +409,7 @@ def bench_solve(a):
     stream = torch.cuda.current_stream(dev)
     nA = np.linalg.norm(A)
     res = {}
-    for tier in a.solve_tiers.split(","):
+    for tier in (a.solve_tiers.split(",") if a.solve_matrix != "symmetric" else []):
         p_ = ag.Plan(nodes, outs, tier=tier)
         out = p_.alloc_outputs(dev)
         p_(dA, dB, outputs=out)
@@ -416,7 +422,7 @@ def bench_solve(a):
         res[tier] = {"ms": ms, "status": st, "info": info, "backward_err": bwd, "forward_err": fwd,
                      "gflops": (2.0 / 3.0 * n ** 3 + 2.0 * n * n * nrhs) / ms / 1e6}
         p_._ws.clear()
-    if not a.no_literal:
+    if not a.no_literal and a.solve_matrix != "symmetric":
         lit = ag.Plan(nodes, outs, flags=ag.PLAN_LITERAL)
         out = lit.alloc_outputs(dev)
         lit(dA, dB, outputs=out)
@@ -429,13 +435,19 @@ def bench_solve(a):
     # the symmetric variant A = Q diag(s) Q^T: the analysis finds it symmetric
     # with a positive diagonal and the Cholesky path solves it (no pivoting);
     # the same matrix through the general LU for comparison
+    if a.solve_matrix == "nonsymmetric":
+        print(json.dumps({"workload": "inv(A)*B, A 4096x4096 kappa=1e6 (non-symmetric), B 4096x64 FP64",
+                          "results": res}), flush=True)
+        return
     As = synth.conditioned_matrix(20250203 + 3, n, 1e6, symmetric=True)
     Xs = np.linalg.solve(As, B)
     dAs = torch.from_numpy(np.ascontiguousarray(As.T)).to(dev).t()
     nAs = np.linalg.norm(As)
     spd = {}
-    for name, tier, flags in (("cholesky_lu32_ir64", "lu32_ir64", 0),
-                              ("lu_lu32_ir64", "lu32_ir64", ag.PLAN_NO_SOLVE_ANALYSIS)):
+    spd_modes = (("cholesky_lu32_ir64", "lu32_ir64", 0),)
+    if not a.no_literal:
+        spd_modes += (("lu_lu32_ir64", "lu32_ir64", ag.PLAN_NO_SOLVE_ANALYSIS),)
+    for name, tier, flags in spd_modes:
         p_ = ag.Plan(nodes, outs, tier=tier, flags=flags)
         out = p_.alloc_outputs(dev)
         p_(dAs, dB, outputs=out)
@@ -514,31 +526,48 @@ def bench_plain(a):
                            "err_vs_oracle": oracle.rel_err(got, ref)}
             r["vs_literal"] = r["literal"]["us"] / r["optimised"]["us"]
             nxt[f"{name}_n{nn}"] = r
-    # solve(A, b) with A tridiagonal (Sec. III (10)) at the paper's sizes:
-    # the analysed solve (band LU) against the literal dense LU.  A has
-    # uniform [-1, 1) off-diagonals and diagonal uniform [-1, 1) + 3.
-    for nn in (100, 250, 500, 1000, 4096):
-        a_h = synth.band_matrix(20250203 + 10, 1, nn, 1, 1, "f64", diag_shift=3.0)
-        b_h = synth.matrix(20250203 + 10, 2, nn, 1, "f64")
+    print(json.dumps({"workload": "six expressions over 256x256 FP64 A,B,C,D and v", "results": res,
+                      "graph_replay_us_all_six": gms * 1e3, "next_rows": nxt}), flush=True)
+
+
+def bench_structured(a):
+    """solve(A, b) with A tridiagonal (Sec. III (10)) at the paper's sizes:
+    the analysed solve (the tridiagonal band LU) against the literal dense
+    LU.  A has uniform [-1, 1) off-diagonals and diagonal uniform [-1, 1) + 3."""
+    import torch
+    import oracle
+    import paper_2502_03000_gb300 as ag
+    from paper_2502_03000_gb300 import expr as E
+    import synth
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    dt = a.dtype
+    nxt = {}
+    for nn in [int(x) for x in a.sizes.split(",")]:
+        a_h = synth.band_matrix(20250203 + 10, 1, nn, 1, 1, dt, diag_shift=3.0)
+        b_h = synth.matrix(20250203 + 10, 2, nn, 1, dt)
         g = E.Graph()
-        nodes, outs = g.build(E.solve(g.input(0, nn, nn), g.input(1, nn, 1)))
+        nodes, outs = g.build(E.solve(g.input(0, nn, nn, dt), g.input(1, nn, 1, dt)))
         a_d = torch.from_numpy(a_h.T.copy()).to(dev).t()
         b_d = torch.from_numpy(b_h.T.copy()).to(dev).t()
         ref = oracle.solve_band(a_h, b_h, 1, 1)
         r = {}
-        for mode, flags in (("optimised", 0), ("literal", ag.PLAN_LITERAL)):
+        modes = (("optimised", 0),) if a.no_literal else (("optimised", 0), ("literal", ag.PLAN_LITERAL))
+        for mode, flags in modes:
             p_ = ag.Plan(nodes, outs, flags=flags)
             out = p_.alloc_outputs(dev)
-            p_(a_d, b_d, outputs=out)
+            for _ in range(max(1, a.warmup)):
+                p_(a_d, b_d, outputs=out)
             torch.cuda.synchronize()
-            reps = 50 if mode == "optimised" or nn <= 1000 else 5
+            reps = a.steps if mode == "optimised" or nn <= 1000 else max(1, a.steps // 10)
             ms = time_ms(lambda: p_(a_d, b_d, outputs=out), reps, stream)
-            r[mode] = {"us": ms * 1e3, "path": p_.solve_path()[0],
+            r[mode] = {"us": ms * 1e3, "path": p_.solve_path()[0], "status": p_.status(),
                        "err_vs_oracle": oracle.rel_err(out[0].double().cpu().numpy(), ref)}
-        r["vs_literal"] = r["literal"]["us"] / r["optimised"]["us"]
+        if "literal" in r:
+            r["vs_literal"] = r["literal"]["us"] / r["optimised"]["us"]
         nxt[f"solve_tridiag_n{nn}"] = r
-    print(json.dumps({"workload": "six expressions over 256x256 FP64 A,B,C,D and v", "results": res,
-                      "graph_replay_us_all_six": gms * 1e3, "next_rows": nxt}), flush=True)
+    print(json.dumps({"workload": f"solve(A, b), A tridiagonal n x n ({dt}), b n x 1", "results": nxt}),
+          flush=True)
 
 
 def bench_planner(a):
@@ -587,7 +616,8 @@ def main():
         return
     if a.workload != "fused":
         {"products": bench_products, "batched": bench_batched, "chain": bench_chain,
-         "solve": bench_solve, "plain": bench_plain, "planner": bench_planner}[a.workload](a)
+         "solve": bench_solve, "plain": bench_plain, "planner": bench_planner,
+         "structured": bench_structured}[a.workload](a)
         return
     import numpy as np
     import torch
