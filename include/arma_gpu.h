@@ -184,7 +184,13 @@ arma_status arma_gpu_output_info(const arma_plan* plan, int32_t i, int64_t* rows
  * in_ptrs[slot] are device pointers to the operands described by the INPUT
  * nodes; out_ptrs[i] device pointers for the outputs; workspace a device
  * buffer of workspace_bytes >= arma_gpu_plan_workspace(), 256-byte aligned.
- * Asynchronous: returns after launching; it does not synchronise. */
+ * Asynchronous: returns after launching; it does not synchronise, with one
+ * exception: a plan with an analysed solve (ARMA_OP_SOLVE, or inv(A)*B in an
+ * optimised plan) waits on `stream` for the analysis of its matrix before it
+ * launches the solver (and once more when a Cholesky attempt fails).  While
+ * `stream` is being captured into a CUDA graph no analysis runs and the
+ * general solver is recorded instead; ARMA_PLAN_NO_SOLVE_ANALYSIS gives the
+ * same behaviour always. */
 arma_status arma_gpu_eval(const arma_plan* plan, const void* const* in_ptrs,
                           void* const* out_ptrs, void* workspace, size_t workspace_bytes,
                           void* stream);

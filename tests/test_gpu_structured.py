@@ -241,3 +241,30 @@ def test_symmetric_not_positive_definite(torch):
         plan = solve_plan(n, k)
         assert check_solve(plan, a, b, "f64", "indefinite") == "general"
         assert plan.solve_path()[3] is True
+
+
+def test_analysed_solve_under_graph_capture(torch):
+    """while the stream is captured into a CUDA graph no analysis (and no host
+    wait) runs: the graph holds the general solve, and its replays solve the
+    system"""
+    import torch as T
+    n, k = 300, 2
+    a = synth.band_matrix(3200, 1, n, 1, 1, "f64", diag_shift=3.0)
+    b = synth.matrix(3200, 2, n, k, "f64")
+    plan = solve_plan(n, k)
+    ins = [to_dev(a), to_dev(b)]
+    out = plan.alloc_outputs(ins[0].device)
+    ws = plan.workspace(ins[0].device)
+    s = T.cuda.Stream()
+    s.wait_stream(T.cuda.current_stream())
+    g = T.cuda.CUDAGraph()
+    with T.cuda.stream(s):
+        plan(*ins, outputs=out, workspace=ws, stream=s.cuda_stream)   # warm-up outside capture
+        s.synchronize()
+        with T.cuda.graph(g, stream=s):
+            plan(*ins, outputs=out, workspace=ws, stream=s.cuda_stream)
+    out[0].zero_()
+    g.replay()
+    T.cuda.synchronize()
+    assert plan.solve_path(workspace=ws)[0] == "none"
+    assert oracle.rel_err(to_host(out[0]), oracle.solve_band(a, b, 1, 1)) <= 1e-12
