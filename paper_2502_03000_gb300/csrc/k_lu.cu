@@ -779,12 +779,44 @@ __device__ __forceinline__ void block_solve(T (&y)[16], const T* D, const T* din
   }
 }
 
-// inverses of the diagonal blocks: Linv_i = L_ii^-1 (unit lower) and
-// Uinv_i = U_ii^-1, each 64 x 64 column-major (zero-padded past the last
-// row), by the block solve applied to the identity.  A zero pivot gives a
-// zero row, as in the substitution.  With lower_nonunit the matrix is a
-// lower-triangular system matrix itself: Linv_i inverts its whole lower
-// block, diagonal included (Uinv_i is then not used).
+// Inverses of one diagonal block (w <= 64 rows at src, leading dimension
+// lda): Linv = L^-1 of its lower part (unit diagonal unless lower_nonunit)
+// and, when Uinv is not null, Uinv = U^-1 of its upper part; each 64 x 64
+// column-major, zero-padded past w, by the block solve applied to the
+// identity.  D (NB * NB) and dinv (NB) are shared memory; 256 threads.
+template <typename T>
+__device__ __forceinline__ void invert_block(const T* src, int64_t lda, int w, T* D, T* dinv, T* Linv, T* Uinv,
+                                             bool lower_nonunit) {
+  const int tid = threadIdx.x, lane = tid & 31, col = tid >> 2, q = tid & 3;
+  load_block(D, src, lda, w, w);
+  __syncthreads();
+  if (tid < NB) {
+    const T p = D[tid * NB + tid];
+    dinv[tid] = (tid < w && p != (T)0) ? (T)1 / p : (T)0;
+  }
+  __syncthreads();
+  {
+    T y[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) y[k] = (q * 16 + k == col && col < w) ? (T)1 : (T)0;
+    block_solve<T, true>(y, D, dinv, w, q, lane, !lower_nonunit);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) Linv[col * NB + q * 16 + k] = y[k];
+  }
+  if (Uinv) {
+    T y[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) y[k] = (q * 16 + k == col && col < w) ? (T)1 : (T)0;
+    block_solve<T, false>(y, D, dinv, w, q, lane);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) Uinv[col * NB + q * 16 + k] = y[k];
+  }
+}
+
+// inverses of all diagonal blocks: Linv_i = L_ii^-1 (unit lower) and
+// Uinv_i = U_ii^-1 of an LU factor (a zero pivot gives a zero row, as in the
+// substitution); with lower_nonunit the matrix is a lower-triangular system
+// matrix (or a Cholesky factor) and Linv_i inverts its whole lower block
 template <typename T>
 __global__ void __launch_bounds__(256) inv_diag_kernel(const T* __restrict__ LU, int64_t n, T* Linv, T* Uinv,
                                                        int64_t lda = 0, int lower_nonunit = 0) {
@@ -793,25 +825,8 @@ __global__ void __launch_bounds__(256) inv_diag_kernel(const T* __restrict__ LU,
   if (lda == 0) lda = n;
   const int64_t j = (int64_t)blockIdx.x * NB;
   const int w = (int)(n - j < NB ? n - j : NB);
-  const int tid = threadIdx.x, lane = tid & 31, col = tid >> 2, q = tid & 3;
-  load_block(D, LU + j + j * lda, lda, w, w);
-  __syncthreads();
-  if (tid < NB) {
-    const T p = D[tid * NB + tid];
-    dinv[tid] = (tid < w && p != (T)0) ? (T)1 / p : (T)0;
-  }
-  __syncthreads();
-  T* out[2] = {Linv + (int64_t)blockIdx.x * NB * NB, Uinv + (int64_t)blockIdx.x * NB * NB};
-#pragma unroll
-  for (int which = 0; which < 2; ++which) {
-    T y[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) y[k] = (q * 16 + k == col && col < w) ? (T)1 : (T)0;
-    if (which == 0) block_solve<T, true>(y, D, dinv, w, q, lane, !lower_nonunit);
-    else block_solve<T, false>(y, D, dinv, w, q, lane);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) out[which][col * NB + q * 16 + k] = y[k];
-  }
+  invert_block(LU + j + j * lda, lda, w, D, dinv, Linv + (int64_t)blockIdx.x * NB * NB,
+               Uinv + (int64_t)blockIdx.x * NB * NB, lower_nonunit != 0);
 }
 
 constexpr int CW = 16;          // right-hand sides per CTA of the cooperative substitution
@@ -1445,8 +1460,9 @@ cudaError_t factor(const SolveArgs& a, const Layout& L, char* base, cudaStream_t
 // global memory, so S's column c is only read during the step: one barrier
 // per column.
 template <typename T>
-__global__ void __launch_bounds__(256) chol_diag_kernel(T* W, int64_t ld, int64_t j, int w, Ctl* ctl) {
-  __shared__ T S[NB][NB + 1];   // S[r][c] = block (r, c), lower part
+__global__ void __launch_bounds__(256) chol_diag_kernel(T* W, int64_t ld, int64_t j, int w, Ctl* ctl, T* Linv) {
+  __shared__ __align__(16) T S[NB][NB + 1];   // S[r][c] = block (r, c), lower part
+  __shared__ T dinv[NB];
   if (*(volatile int*)&ctl->chol_fail) return;
   const int tid = threadIdx.x, r = tid & (NB - 1), g = tid >> 6;
   for (int t = tid; t < NB * NB; t += 256) {
@@ -1468,6 +1484,11 @@ __global__ void __launch_bounds__(256) chol_diag_kernel(T* W, int64_t ld, int64_
     }
     if (tid == 0) W[(j + c) + (j + c) * ld] = sq;
   }
+  // L_jj^-1 for the panel below, from the factor just written (the barrier
+  // makes this block's global writes visible to all of its threads)
+  if (!Linv) return;
+  __syncthreads();
+  invert_block(W + j + j * ld, ld, w, &S[0][0], dinv, Linv, (T*)nullptr, true);
 }
 
 __global__ void iota_kernel(int32_t* p, int64_t n) {
@@ -1494,14 +1515,13 @@ cudaError_t factor_cholesky(const SolveArgs& a, const Layout& L, char* base, cud
   const int dt = L.f64 ? ARMA_F64 : ARMA_F32;
   for (int64_t j = 0; j < n; j += NB) {
     const int w = (int)(n - j < NB ? n - j : NB);
-    chol_diag_kernel<T><<<1, 256, 0, s>>>(W, n, j, w, ctl);
-    if (launches) ++*launches;
     const int64_t rest = n - j - w;
-    if (rest <= 0) continue;
-    // L_jj^-1 (non-unit lower), then L_21 = A_21 (L_jj^-1)^T in place
+    // the block's factor and, when rows remain below, its inverse L_jj^-1;
+    // then L_21 = A_21 (L_jj^-1)^T in place
     T* Li = Dinv + (j / NB) * NB * NB;
-    inv_diag_kernel<T><<<1, 256, 0, s>>>(W + j + j * n, (int64_t)w, Li, Dinv + (nb + j / NB) * NB * NB, n, 1);
+    chol_diag_kernel<T><<<1, 256, 0, s>>>(W, n, j, w, ctl, rest > 0 ? Li : nullptr);
     if (launches) ++*launches;
+    if (rest <= 0) continue;
     {
       GemmArgs t;
       memset(&t, 0, sizeof t);
