@@ -33,9 +33,9 @@ struct Bind {
 
 const void* cptr(const Bind& b, const Ref& r) {
   switch (r.kind) {
-    case REF_INPUT: return b.in[r.idx];
-    case REF_OUTPUT: return b.out[r.idx];
-    case REF_WS: return b.ws + r.idx;
+    case REF_INPUT: return static_cast<const char*>(b.in[r.idx]) + r.boff;
+    case REF_OUTPUT: return static_cast<const char*>(b.out[r.idx]) + r.boff;
+    case REF_WS: return b.ws + r.idx + r.boff;
     default: return nullptr;
   }
 }

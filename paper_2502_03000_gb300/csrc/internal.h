@@ -27,8 +27,10 @@ enum RefKind : int32_t { REF_NONE = 0, REF_INPUT = 1, REF_OUTPUT = 2, REF_WS = 3
 struct Ref {
   int32_t kind = REF_NONE;
   int32_t pad = 0;
-  int64_t idx = 0;  // input slot, output index, or workspace byte offset
+  int64_t idx = 0;   // input slot, output index, or workspace byte offset
+  int64_t boff = 0;  // bytes from the buffer's start: a submatrix view read in place
   bool valid() const { return kind != REF_NONE; }
+  bool same(const Ref& o) const { return kind == o.kind && idx == o.idx && boff == o.boff; }
 };
 
 inline Ref ref_input(int64_t slot) { Ref r; r.kind = REF_INPUT; r.idx = slot; return r; }

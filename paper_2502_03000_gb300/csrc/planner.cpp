@@ -791,7 +791,7 @@ void Planner::emit_gemm(int64_t m, int64_t n, int64_t k, const MatOperand& A, co
   // and layout are compared by pointer at evaluation.
   if (!literal_ && !(e_.flags & ARMA_PLAN_NO_SYRK) && m == n && m > 1 && A.trans != B.trans &&
       A.dtype == B.dtype && A.ld == B.ld && !g.C.ref.valid() && !rs && !cs && A.ref.kind == B.ref.kind) {
-    if (A.ref.idx == B.ref.idx) g.sym = 1;
+    if (A.ref.same(B.ref)) g.sym = 1;
     else if (A.ref.kind == REF_INPUT) g.sym = 2;
   }
   g.scratch_bytes = gemm_scratch_bytes(g);
@@ -1159,6 +1159,23 @@ MatOperand Planner::materialize(int x) {
     return m;
   }
   if (err_ != ARMA_OK) return MatOperand();
+  // a submatrix of a matrix (no transpose on the way) is that matrix's
+  // buffer at an offset with the same leading dimension: read in place by
+  // every kernel, no copy (Sec. III (2)); an output still gets its copy
+  if (d.op == ARMA_OP_SUBMAT && out_of_[x] < 0 && !literal_) {
+    int z = d.a;
+    while (!loc_[z].ref.valid() && nd_[z].op == ARMA_OP_SUBMAT) z = nd_[z].a;
+    if (loc_[z].ref.valid() || nd_[z].op != ARMA_OP_TRANS) {
+      MatOperand base = materialize(d.a);
+      if (err_ != ARMA_OK) return MatOperand();
+      if (!base.trans) {
+        MatOperand v = base;
+        v.ref.boff += ((int64_t)d.slot + (int64_t)d.ld * base.ld) * (int64_t)dtype_size(base.dtype);
+        loc_[x] = v;
+        return v;
+      }
+    }
+  }
   MatOperand dest = dest_for(x);
   switch (d.op) {
     case ARMA_OP_MATMUL:
@@ -1672,7 +1689,8 @@ arma_status plan_batched(const arma_expr* exprs, int32_t count, arma_plan* p) {
       const Step& st2 = one.steps[1];
       if (st2.kind != ST_DOT) return ARMA_ERR_UNSUPPORTED;
       const DotStep& d = st2.dot;
-      if (d.A.ref.kind != REF_INPUT || d.B.ref.kind != REF_INPUT || d.A.ref.idx != g.A.ref.idx ||
+      if (d.A.ref.kind != REF_INPUT || d.B.ref.kind != REF_INPUT || d.A.ref.boff || d.B.ref.boff ||
+          d.A.ref.idx != g.A.ref.idx ||
           d.B.ref.idx != g.B.ref.idx || d.A.trans != g.A.trans || d.B.trans != g.B.trans || d.alpha != 1.0 ||
           d.out.kind != REF_OUTPUT)
         return ARMA_ERR_UNSUPPORTED;

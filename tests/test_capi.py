@@ -232,6 +232,21 @@ def test_submatrix_views_in_place():
         assert ei.value.status == "shape"
 
 
+def test_views_feed_kernels_in_place():
+    """a submatrix view (no transpose on the way) is an offset into its
+    matrix: products, trace, solve and the symmetric product read it with no
+    copy; the literal plan copies every view"""
+    g = E.Graph()
+    A, B, Q = g.input(0, 203, 171), g.input(1, 203, 171), g.input(3, 171, 203)
+    va, vb = A.sub(3, 7, 150, 101), B.sub(50, 70, 150, 101)
+    for e, want in ((A.sub(0, 0, 100, 171) * Q.sub(0, 3, 171, 90), ["gemm"]), (va.t() * vb, ["gemm"]),
+                    (E.trace(va.t() * vb), ["diagdot"]), (va * va.t(), ["syrk"]),
+                    (E.solve(A.sub(0, 0, 150, 150), B.sub(0, 0, 150, 3)), ["solve"])):
+        nodes, outs = g.build(e)
+        assert kernels(ag.Plan(nodes, outs)) == want
+        assert "ew" in kernels(ag.Plan(nodes, outs, flags=ag.PLAN_LITERAL))
+
+
 def test_fused_program_contracts_products():
     """A%B + 3*C - D/2: the sum is reordered so that the product becomes one
     fused multiply-add and the power-of-two term an exact exponent load:

@@ -413,3 +413,30 @@ def test_empty_and_whole_views(torch):
     nodes, outs = g.build(v * 2.0, E.accu(v))
     got = run(nodes, outs, host, "f64")
     assert got[0].shape == (10, 0) and to_host(got[1]) == 0.0
+
+
+@pytest.mark.parametrize("layout", [dict(), dict(pad=5, offset=3)])
+def test_views_read_in_place_by_other_kernels(torch, layout):
+    """views passed to the product, trace, symmetric-product and solve
+    kernels as offsets into their matrices (odd offsets, padded and
+    misaligned inputs)"""
+    m, n = 203, 171
+    ld = m + layout.get("pad", 0)
+    g = E.Graph()
+    A, B = g.input(0, m, n, "f64", ld=ld), g.input(1, m, n, "f64", ld=ld)
+    host = inputs(960, [(m, n), (m, n)], "f64")
+    host[0] = host[0] + np.eye(m, n) * 8.0        # the square view below is well conditioned
+    va, vb = A.sub(3, 7, 150, 101), B.sub(50, 70, 150, 101)
+    cases = {
+        "product": va.t() * vb,
+        "trace": E.trace(va.t() * vb),
+        "syrk": 0.5 * (va * va.t()),
+        "view_of_view": A.sub(10, 10, 120, 120).sub(7, 3, 80, 90).t() * B.sub(1, 2, 80, 5),
+        "solve": E.solve(A.sub(0, 0, 150, 150), B.sub(3, 1, 150, 4)),
+    }
+    for name, e in cases.items():
+        nodes, outs = g.build(e)
+        ref = oracle.evaluate(nodes, outs, host)
+        for flags in (0, ag.PLAN_LITERAL):
+            got = run(nodes, outs, host, "f64", flags, **layout)
+            check(got, ref, TOL["f64"] * (100 if name == "solve" else 10), f"{name} flags={flags}")
