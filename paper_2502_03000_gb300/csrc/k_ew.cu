@@ -16,21 +16,29 @@
 
 #include <type_traits>
 
+#include <atomic>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace arma {
 
+// Host-side caches in this library are safe for concurrent evaluations from
+// several threads: values that every thread would compute alike are atomics
+// (a race only repeats the query), lookup tables take a mutex.
 int device_sm_count() {
-  static int cached[64] = {0};
+  static std::atomic<int> cached[64];
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
-  if (!cached[dev]) {
+  int v = cached[dev].load(std::memory_order_relaxed);
+  if (!v) {
     int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    cached[dev] = n > 0 ? n : 1;
+    v = n > 0 ? n : 1;
+    cached[dev].store(v, std::memory_order_relaxed);
   }
-  return cached[dev];
+  return v;
 }
 
 namespace {
@@ -411,9 +419,11 @@ typedef void (*EwKernel)(EwArgs);
 // Resident 256-thread blocks per SM for a kernel (cached): the streaming
 // passes launch exactly one wave and stride through the data.
 int resident_blocks(const void* k) {
+  static std::mutex mu;
   static const void* keys[128];
   static int vals[128];
   static int n = 0;
+  std::lock_guard<std::mutex> lock(mu);
   for (int i = 0; i < n; ++i)
     if (keys[i] == k) return vals[i];
   int occ = 0;

@@ -31,6 +31,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -766,14 +767,14 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   p.sym = sym ? 1 : 0;
   p.skip = a.skip;
 
-  static bool attr_set[64] = {false};
+  static std::atomic<bool> attr_set[64];
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
-  if (!attr_set[dev]) {
+  if (!attr_set[dev].load(std::memory_order_acquire)) {
     e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    attr_set[dev] = true;
+    attr_set[dev].store(true, std::memory_order_release);
   }
   const int64_t per_split = sym ? (g.tiles_m / 2) * (int64_t)(g.tiles_m / 2 + 1) : (int64_t)g.tiles_m * g.tiles_n;
   const int64_t work = per_split * g.splits;

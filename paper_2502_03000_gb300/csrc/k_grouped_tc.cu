@@ -24,6 +24,8 @@
 // MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
 
+#include <atomic>
+
 #include "common.cuh"
 #include "grouped.h"
 #include "tc_ops.cuh"
@@ -252,14 +254,17 @@ __global__ void __launch_bounds__(GTHREADS, S == 1 ? 2 : 1) grouped_tc_kernel(co
 template <typename AT, int S>
 cudaError_t launch_tc(const GroupedArgs& g, cudaStream_t s, int* launches) {
   constexpr int smem = smem_bytes<S>();
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<bool> attr[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!attr[dev].load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(grouped_tc_kernel<AT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     // the whole unified cache as shared memory, so that several CTAs fit
     e = cudaFuncSetAttribute(grouped_tc_kernel<AT, S>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr[dev].store(true, std::memory_order_release);
   }
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grouped_tc_kernel<AT, S>, GTHREADS, smem);

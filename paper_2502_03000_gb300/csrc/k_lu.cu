@@ -31,6 +31,8 @@
 #include <type_traits>
 #include <utility>
 
+#include <atomic>
+
 #include "common.cuh"
 
 namespace arma {
@@ -1296,13 +1298,15 @@ Layout layout(int64_t n, int64_t nrhs, int32_t tier, int32_t analyse = 0) {
 // CTAs when it fits their shared memory, else the cooperative grid kernel
 template <typename T>
 cudaError_t launch_panel(PanelArgs<T>& pa, int64_t rows, int ctas, cudaStream_t s) {
-  static int cluster_max = -1;            // largest usable cluster size, probed once
+  static std::atomic<int> cluster_probe{-1};   // largest usable cluster size, probed once
+  int cluster_max = cluster_probe.load(std::memory_order_acquire);
   if (cluster_max < 0) {
     cluster_max = 8;
     if (cudaFuncSetAttribute(panel_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
         cudaSuccess)
       cluster_max = 16;
     cudaGetLastError();
+    cluster_probe.store(cluster_max, std::memory_order_release);
   }
   auto cluster_cfg = [&](cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int cs, size_t smem) {
     memset(&cfg, 0, sizeof cfg);

@@ -24,6 +24,8 @@
 //                      candidates, the updated band elements and the
 //                      right-hand sides) and the back substitution (lanes
 //                      over right-hand sides).
+#include <atomic>
+
 #include "common.cuh"
 
 namespace arma {
@@ -510,15 +512,15 @@ cudaError_t launch_tridiag(BandArgs a, cudaStream_t s) {
     tridiag_kernel<DT, FT, REFINE, false><<<1, 256, 0, s>>>(a);
     return cudaGetLastError();
   }
-  static bool attr[64] = {false};
+  static std::atomic<bool> attr[64];
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
-  if (!attr[dev]) {
+  if (!attr[dev].load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(tridiag_kernel<DT, FT, REFINE, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_CAP);
     if (e != cudaSuccess) return e;
-    attr[dev] = true;
+    attr[dev].store(true, std::memory_order_release);
   }
   tridiag_kernel<DT, FT, REFINE, true><<<1, 256, (size_t)bytes, s>>>(a);
   return cudaGetLastError();

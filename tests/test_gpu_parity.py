@@ -440,3 +440,47 @@ def test_views_read_in_place_by_other_kernels(torch, layout):
         for flags in (0, ag.PLAN_LITERAL):
             got = run(nodes, outs, host, "f64", flags, **layout)
             check(got, ref, TOL["f64"] * (100 if name == "solve" else 10), f"{name} flags={flags}")
+
+
+def test_concurrent_evaluations_from_threads(torch):
+    """plans evaluated from several host threads at once, each on its own
+    stream with its own workspace, give the same bits as one at a time
+    (the library's host-side caches are shared)"""
+    import threading
+    import torch as T
+    n = 300
+    g = E.Graph()
+    A, B, C, D = (g.input(s, n, n) for s in range(4))
+    exprs = [A % B + 3 * C - D / 2, 2 * A.t() * B + C, A * A.t(), E.trace(A * B), E.accu(A % B)]
+    host = inputs(970, [(n, n)] * 4, "f64")
+    dev_in = [to_dev(h) for h in host]
+    plans = [ag.Plan(*g.build(e)) for e in exprs]
+    ref = []
+    for p in plans:
+        out = p(*dev_in)
+        T.cuda.synchronize()
+        ref.append([to_host(o) for o in out])
+    results, errors = {}, []
+
+    def work(i):
+        try:
+            s = T.cuda.Stream()
+            p = plans[i % len(plans)]
+            ws = T.empty(max(256, p.workspace_bytes), dtype=T.uint8, device="cuda")
+            outs = p.alloc_outputs(T.device("cuda"))
+            for _ in range(5):
+                p(*dev_in, outputs=outs, workspace=ws, stream=s.cuda_stream)
+            s.synchronize()
+            results[i] = [to_host(o) for o in outs]
+        except Exception as e:          # reported below
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(10)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for i, got in results.items():
+        for x, y in zip(got, ref[i % len(plans)]):
+            assert np.array_equal(np.asarray(x), np.asarray(y)), i
