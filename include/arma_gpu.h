@@ -89,7 +89,10 @@ typedef enum {
   ARMA_OP_INV = 15,        /* matrix inverse (square a) */
   ARMA_OP_SUBMAT = 16,     /* view of a: rows [slot, slot + rows), columns [ld, ld + cols)
                               (node fields: slot = first row, ld = first column, rows x
-                              cols = size); elementwise expressions read it in place */
+                              cols = size; Sec. III (2)).  Read in place: by the fused
+                              elementwise pass always, and by products, trace, solves and
+                              reductions when no transpose lies between the view and its
+                              matrix; the literal plan copies it */
   ARMA_OP_SOLVE = 17       /* solve(a, b): X with a X = b, a square (Sec. III (10)).  The
                               optimised plan analyses a when evaluated and picks the solver
                               (arma_solve_path); the literal plan always factors a densely. */

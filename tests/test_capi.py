@@ -247,6 +247,18 @@ def test_views_feed_kernels_in_place():
         assert "ew" in kernels(ag.Plan(nodes, outs, flags=ag.PLAN_LITERAL))
 
 
+def test_symmetric_product_of_views():
+    """the same view on both sides is a symmetric product; two different
+    views of one matrix (different offsets) are not"""
+    g = E.Graph()
+    A = g.input(0, 100, 80)
+    v, w = A.sub(0, 0, 60, 80), A.sub(1, 0, 60, 80)
+    nodes, outs = g.build(v * v.t())
+    assert kernels(ag.Plan(nodes, outs)) == ["syrk"]
+    nodes, outs = g.build(v * w.t())
+    assert kernels(ag.Plan(nodes, outs)) == ["gemm"]
+
+
 def test_fused_program_contracts_products():
     """A%B + 3*C - D/2: the sum is reordered so that the product becomes one
     fused multiply-add and the power-of-two term an exact exponent load:
