@@ -273,10 +273,17 @@ class Plan:
                "arma_gpu_eval_fused_static")
         return outputs
 
+    def _last_workspace(self, workspace):
+        if workspace is not None:
+            return workspace
+        if not self._ws:
+            raise ValueError("no evaluation to report on: evaluate the plan first or pass its workspace")
+        return next(iter(self._ws.values()))
+
     def status(self, workspace=None, stream=None):
         """Device-side status of the last evaluation (synchronises)."""
         import torch
-        ws = workspace if workspace is not None else next(iter(self._ws.values()))
+        ws = self._last_workspace(workspace)
         st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
         info = ctypes.c_int64()
         code = lib().arma_gpu_eval_status(self._h, ctypes.c_void_p(ws.data_ptr()), ctypes.c_void_p(st),
@@ -291,7 +298,7 @@ def _solve_path(self, workspace=None, stream=None):
     """The solver the last evaluation's analysed solve took and what the
     analysis of its matrix found (synchronises): (path, kl, ku, symmetric)."""
     import torch
-    ws = workspace if workspace is not None else next(iter(self._ws.values()))
+    ws = self._last_workspace(workspace)
     st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
     v = [ctypes.c_int32() for _ in range(4)]
     _check(lib().arma_gpu_eval_solve_path(self._h, ctypes.c_void_p(ws.data_ptr()), ctypes.c_void_p(st),

@@ -278,3 +278,13 @@ def test_plan_info_is_json():
     p = ag.Plan(*E.config_products(256))
     info = p.info
     assert info["mode"] == "optimised" and info["steps"][0]["flops"] == 2 * 256 ** 3
+
+
+def test_status_before_any_evaluation_is_an_error():
+    g = E.Graph()
+    nodes, outs = g.build(E.solve(g.input(0, 8, 8), g.input(1, 8, 1)))
+    p = ag.Plan(nodes, outs)
+    with pytest.raises(ValueError):
+        p.status()
+    with pytest.raises(ValueError):
+        p.solve_path()
