@@ -82,17 +82,21 @@ def test_tridiagonal(torch, dtype, n, k):
     assert check_solve(solve_plan(n, k, dtype), a, b, dtype, f"n={n} k={k}") == "band"
 
 
-@pytest.mark.parametrize("kl,ku", [(1, 1), (2, 0), (0, 3), (3, 5), (31, 32), (7, 2)])
-def test_band_with_row_exchanges(torch, kl, ku):
+@pytest.mark.parametrize("kl,ku,k,dtype", [(1, 1, 5, "f64"), (2, 0, 5, "f64"), (0, 3, 5, "f64"), (3, 5, 5, "f64"),
+                                            (31, 32, 5, "f64"), (7, 2, 5, "f64"), (3, 5, 40, "f64"),
+                                            (3, 5, 5, "f32"), (2, 2, 33, "f32")])
+def test_band_with_row_exchanges(torch, kl, ku, k, dtype):
     """no diagonal dominance and zeros on the diagonal: partial pivoting
-    must exchange rows (elimination without it breaks down)"""
+    must exchange rows (elimination without it breaks down); more than 32
+    right-hand sides take the lanes' second pass"""
     n = 4 * (2 * kl + ku + 1) + 37
     both = kl > 0 and ku > 0
     a = synth.band_matrix(2100 + kl, 1, n, kl, ku, "f64", zero_diag_every=5 if both else 0)
     if not both:
         a += 4.0 * np.eye(n)          # a triangular band with a zero diagonal element is singular
-    b = synth.matrix(2100 + kl, 2, n, 5, "f64")
-    assert check_solve(solve_plan(n, 5), a, b, "f64", f"kl={kl} ku={ku}") == "band"
+    a = synth.cast(a, dtype)
+    b = synth.matrix(2100 + kl, 2, n, k, dtype)
+    assert check_solve(solve_plan(n, k, dtype), a, b, dtype, f"kl={kl} ku={ku} k={k}") == "band"
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -268,3 +272,21 @@ def test_analysed_solve_under_graph_capture(torch):
     T.cuda.synchronize()
     assert plan.solve_path(workspace=ws)[0] == "none"
     assert oracle.rel_err(to_host(out[0]), oracle.solve_band(a, b, 1, 1)) <= 1e-12
+
+
+@pytest.mark.parametrize("side", ["upper", "lower"])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_triangular_many_right_hand_sides(torch, side, dtype):
+    """20000 right-hand sides: more (block row, 16-column slice) CTAs than the
+    GPU holds at once, so the triangular substitution takes its per-block
+    launches (forward only for lower, backward only for upper, non-unit
+    diagonal blocks)"""
+    n, k = 256, 20000
+    m = synth.matrix(3300, 1, n, n, "f64") + 4.0 * np.eye(n)
+    a = synth.cast(np.triu(m) if side == "upper" else np.tril(m), dtype)
+    b = synth.matrix(3300, 2, n, k, dtype)
+    plan = solve_plan(n, k, dtype)
+    x = run(plan, a, b, dtype)
+    assert plan.solve_path()[0] == side and plan.status()[0] == "ok"
+    ref = oracle.solve_triangular(a, b, side == "lower")
+    assert oracle.rel_err(x, ref) <= (1e-13 if dtype == "f64" else 1e-5)
