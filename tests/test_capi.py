@@ -288,3 +288,27 @@ def test_status_before_any_evaluation_is_an_error():
         p.status()
     with pytest.raises(ValueError):
         p.solve_path()
+
+
+def test_view_planning_edges():
+    """a view of a transpose feeding a product is copied once (one strided
+    pass); a view that is itself an output gets its own copy; views of views
+    compose without copies"""
+    g = E.Graph()
+    A, Q = g.input(0, 120, 90), g.input(1, 60, 4)
+    nodes, outs = g.build(A.t().sub(5, 7, 60, 60) * Q)
+    assert kernels(ag.Plan(nodes, outs)) == ["ew", "gemm"]
+    nodes, outs = g.build(A.sub(1, 2, 30, 40))
+    assert kernels(ag.Plan(nodes, outs)) == ["ew"]
+    nodes, outs = g.build(A.sub(10, 10, 100, 60).sub(5, 5, 60, 50).t() * A.sub(0, 0, 60, 3))
+    assert kernels(ag.Plan(nodes, outs)) == ["gemm"]
+
+
+def test_analysed_solve_workspace():
+    """the analysed solve reserves the structured solvers' scratch on top of
+    the general solver's"""
+    g = E.Graph()
+    nodes, outs = g.build(E.solve(g.input(0, 500, 500), g.input(1, 500, 8)))
+    full = ag.Plan(nodes, outs).workspace_bytes
+    plain = ag.Plan(nodes, outs, flags=ag.PLAN_NO_SOLVE_ANALYSIS).workspace_bytes
+    assert full > plain > 0
