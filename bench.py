@@ -29,13 +29,10 @@ sys.path.insert(0, ROOT)
 N = 8192
 DTYPES = ("f32", "f64")
 SEED = 20250203 + 2
-# columns of the bounded CPU sample (the oracle evaluates this column block)
-SAMPLE_COLS = 1024
-
 # DRAM bytes (read + write) of one fused launch at n = 8192, scaled by 4 from
 # an ncu capture of the same kernel source at n = 4096 (the traffic grows in
-# proportion to the elements); see profiles/ew_fused_8192.md.  Reported as
-# null once the kernel source no longer has this hash.
+# proportion to the elements).  Reported as null once the kernel source no
+# longer has this hash.
 NCU_TRAFFIC = {"kernel_src_sha1": "87e17ed6dcc62e37b92935424e5d914a94acf80b",
                "f64": 4 * (537.030912e6 + 114.284544e6), "f32": 4 * (268.505600e6 + 37.646336e6)}
 
@@ -59,7 +56,7 @@ def args():
                    choices=["fused", "products", "chain", "solve", "plain", "batched", "planner", "structured"],
                    help="fused (default) is the benchmark line; the others measure the remaining "
                         "expression families and print one JSON line each")
-    p.add_argument("--tiers", default="bf16,split_bf16")
+    p.add_argument("--tiers", default="bf16,split_bf16,f64")
     p.add_argument("--solve-tiers", default="lu32_ir64,f64,split_bf16,bf16")
     p.add_argument("--no-literal", action="store_true")
     p.add_argument("--solve-matrix", default="both", choices=["both", "nonsymmetric", "symmetric"],
@@ -68,6 +65,8 @@ def args():
     p.add_argument("--sizes", default="100,250,500,1000,4096",
                    help="structured workload: tridiagonal sizes")
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"], help="structured workload: element type")
+    p.add_argument("--planner-save", default="", help="planner workload: directory for the trained network "
+                                                         "and the timing records (JSON)")
     return p.parse_args()
 
 
@@ -107,28 +106,43 @@ def rel_err(x, ref) -> float:
     return d if r < 1e-300 else d / r
 
 
-def oracle_sample(n: int, cols: int):
-    """Literal FP64 oracle on the column block [0, cols) of both dtypes.
-    Returns (seconds, results per dtype, inputs per dtype)."""
-    import numpy as np
+def oracle_full(hin, n: int):
+    """Literal FP64 oracle on the whole workload, both element types.
+    Returns (seconds of oracle evaluation, results per dtype)."""
     import oracle
     import synth
-    hin = host_inputs(n, cols)
-    res, ins = {}, {}
+    res = {}
     t = 0.0
     for dt in DTYPES:
         x = [synth.cast(h, dt) for h in hin]
         nodes, outs = workload_nodes(n, dt)
-        # the same expression on an n x cols block
-        for d in nodes:
-            if d["op"] == "input":
-                d["cols"] = cols
         t0 = time.perf_counter()
-        r = oracle.evaluate(nodes, outs, x)
+        res[dt] = oracle.evaluate(nodes, outs, x)
         t += time.perf_counter() - t0
-        res[dt], ins[dt] = r, x
-        _ = np
-    return t, res, ins
+    return t, res
+
+
+def host_cpu() -> dict:
+    """Core count and CPU model of this host (for the CPU baseline)."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or "unknown"}
 
 
 def clocks_start(dev_index: int):
@@ -182,30 +196,36 @@ def peaks():
 
 
 def run_reference(a):
+    """The reference arm: the literal FP64 oracle evaluating the whole
+    workload (both element types, full size) once per step, on all host
+    cores (OpenMP over the independent columns of each elementwise operator;
+    the reductions are single sequential sums)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
     oracle.build()
-    cols = SAMPLE_COLS if a.n == N else max(1, a.n // 8)
+    hin = host_inputs(a.n)
     for _ in range(a.warmup):
-        oracle_sample(a.n, cols)
+        oracle_full(hin, a.n)
     ts = []
     for _ in range(a.steps):
-        t, _, _ = oracle_sample(a.n, cols)
+        t, _ = oracle_full(hin, a.n)
         ts.append(t)
-    frac = cols / a.n
     sec = sum(ts) / len(ts)
-    value = 2 * frac / sec
+    value = 2 / sec
+    cpu = {"value": value, "unit": "evals/s", "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"the whole workload per step: literal FP64 oracle on A,B,C,D {a.n}x{a.n} in FP32 and "
+                     f"FP64 (one evaluation each), inputs generated once beforehand"}
+    cpu.update(host_cpu())
     line = {"impl": "reference", "metric": "evals/s & % roofline, optimised vs literal plan, at stated err vs FP64 oracle",
             "value": value, "unit": "evals/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
-            "ms_per_step": sec * 1e3 / frac, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"fused elementwise out=A%B+3*C-D/2, accu(out), norm(out,'fro'); "
                                    f"A,B,C,D {a.n}x{a.n} uniform[-1,1] in FP32 and FP64",
                        "evals_per_step": 2},
-            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
-                             "sample": f"literal FP64 oracle on the {a.n}x{cols} column block of both dtypes per step, scaled by {a.n}/{cols}"},
+            "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -271,7 +291,8 @@ def bench_products(a):
     rng = np.random.default_rng(3)
     ii, jj = rng.integers(0, n, 128), rng.integers(0, n, 128)
     At = np.asfortranarray(host[0].T)
-    cpu = {"kind": "oracle", "unit": "s", "cores": 1, "sample": "128 sampled entries of the product"}
+    cpu = {"kind": "oracle", "unit": "s", "cores": oracle.num_threads(), "sample": "128 sampled entries of the product"}
+    cpu.update(host_cpu())
     ref = 2.0 * cpu_baseline_leg(cpu, oracle.matmul_entries, At, host[1], ii, jj) + host[2][ii, jj]
     flops = 2.0 * n ** 3
     res = {}
@@ -391,7 +412,8 @@ def bench_chain(a):
         ins.append(d)
     nodes, outs = E.config_chain(dims, "f64")
     stream = torch.cuda.current_stream(dev)
-    cpu = {"kind": "oracle", "unit": "s", "cores": 1, "sample": "the whole chain, right to left"}
+    cpu = {"kind": "oracle", "unit": "s", "cores": oracle.num_threads(), "sample": "the whole chain, right to left"}
+    cpu.update(host_cpu())
     ref = cpu_baseline_leg(cpu, oracle.chain_eval, host, (0, 0, (1, 1, (2, 2, 3))))
     hbm, src = peaks()
     alg_bytes = 8.0 * (dims[0] * dims[1] + dims[1] * dims[2] + dims[2] * dims[3] + dims[3] + dims[0])
@@ -422,9 +444,15 @@ def bench_solve(a):
     from paper_2502_03000_gb300 import expr as E
     dev = torch.device("cuda", 0)
     n, nrhs = 4096, 64
+    import oracle
+    oracle.build()
     A = synth.conditioned_matrix(20250203 + 3, n, 1e6, symmetric=False)
     B = synth.matrix(20250203 + 3, 2, n, nrhs, "f64")
-    Xref = np.linalg.solve(A, B)
+    cpu = {"kind": "oracle", "unit": "s", "cores": oracle.num_threads(),
+           "sample": "the literal inv(A)*B of each matrix: Gauss-Jordan inverse, then the triple-loop product"}
+    cpu.update(host_cpu())
+    # forward errors are taken against the oracle's literal inv(A) * B
+    Xref = cpu_baseline_leg(cpu, oracle.solve_literal, A, B)
     dA = torch.from_numpy(np.ascontiguousarray(A.T)).to(dev).t()
     dB = torch.from_numpy(np.ascontiguousarray(B.T)).to(dev).t()
     nodes, outs = E.config_solve(n, nrhs)
@@ -459,10 +487,10 @@ def bench_solve(a):
     # the same matrix through the general LU for comparison
     if a.solve_matrix == "nonsymmetric":
         print(json.dumps({"workload": "inv(A)*B, A 4096x4096 kappa=1e6 (non-symmetric), B 4096x64 FP64",
-                          "results": res}), flush=True)
+                          "results": res, "cpu_baseline": cpu}), flush=True)
         return
     As = synth.conditioned_matrix(20250203 + 3, n, 1e6, symmetric=True)
-    Xs = np.linalg.solve(As, B)
+    Xs = cpu_baseline_leg(cpu, oracle.solve_literal, As, B)
     dAs = torch.from_numpy(np.ascontiguousarray(As.T)).to(dev).t()
     nAs = np.linalg.norm(As)
     spd = {}
@@ -482,7 +510,7 @@ def bench_solve(a):
                      "forward_err": float(np.linalg.norm(X - Xs) / np.linalg.norm(Xs))}
         p_._ws.clear()
     print(json.dumps({"workload": "inv(A)*B, A 4096x4096 kappa=1e6 (non-symmetric), B 4096x64 FP64",
-                      "results": res, "symmetric_positive_definite": spd}), flush=True)
+                      "results": res, "symmetric_positive_definite": spd, "cpu_baseline": cpu}), flush=True)
 
 
 def bench_plain(a):
@@ -499,7 +527,8 @@ def bench_plain(a):
     ins = [torch.from_numpy(h.T.copy()).to(dev).t() for h in host]
     exprs = E.config_plain(n, "f64")
     stream = torch.cuda.current_stream(dev)
-    cpu = {"kind": "oracle", "unit": "s", "cores": 1, "sample": "every expression, literally, once per plan"}
+    cpu = {"kind": "oracle", "unit": "s", "cores": oracle.num_threads(), "sample": "every expression, literally, once per plan"}
+    cpu.update(host_cpu())
     res = {}
     opt_plans = []
     for name, (nodes, outs) in exprs.items():
@@ -566,6 +595,7 @@ def bench_structured(a):
     stream = torch.cuda.current_stream(dev)
     dt = a.dtype
     cpu = {"kind": "oracle", "unit": "s", "cores": 1, "sample": "the oracle's band solver on every system"}
+    cpu.update(host_cpu())
     nxt = {}
     for nn in [int(x) for x in a.sizes.split(",")]:
         a_h = synth.band_matrix(20250203 + 10, 1, nn, 1, 1, dt, diag_shift=3.0)
@@ -596,9 +626,11 @@ def bench_structured(a):
 
 def bench_planner(a):
     """5,000 random DAGs (depth <= 5, dims log-uniform 16..8192, FP32/BF16,
-    literal work capped at 2e11 FLOP): candidates timed, the cost network
-    trained on 80% by the library's kernels, held-out picks of the network,
-    the FLOP/byte heuristic and the literal plan against the best candidate."""
+    literal work capped at 2e11 FLOP): the library's candidates (chain order,
+    fusion, split-K, precision tiers at least as accurate as the data's) timed,
+    the cost network trained on 80% by the library's kernels and loaded into
+    the library; held-out picks of the network, the FLOP/byte estimate and the
+    literal plan against the best candidate."""
     import math
     import torch
     from paper_2502_03000_gb300 import costmodel as cm
@@ -609,7 +641,7 @@ def bench_planner(a):
     t1 = time.perf_counter()
     budget = float(os.environ.get("ARMA_PLANNER_BUDGET_S", "420"))
     for i in range(0, len(dags), 100):
-        part = cm.collect(dags[i:i + 100], reps=2)
+        part = cm.collect(dags[i:i + 100])
         for r in part:
             r["dag"] += i
         recs += part
@@ -621,15 +653,30 @@ def bench_planner(a):
     net = cm.CostNet(seed=0)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    losses = net.fit([r["features"] for r in train], [math.log(r["time"]) for r in train], steps=3000)
+    steps = 3000
+    losses = net.fit([r["features"] for r in train], [math.log(r["time"]) for r in train], steps=steps)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t2
-    res = cm.evaluate(test, net)
-    res_train = cm.evaluate(train, net)
+    guard = 4.0
+    res = cm.evaluate(test, net, guard=guard)
+    res_train = cm.evaluate(train, net, guard=guard)
+    # the library's own choice with the network loaded, on held-out DAGs
+    net.to_library(guard=guard)
+    _, mlp, _ = cm.picks(test, net, guard=guard)
+    agree = sum(1 for d, r in mlp.items() if cm.library_pick(dags[d][0], dags[d][1])[0] == r["cand"])
+    if a.planner_save:
+        os.makedirs(a.planner_save, exist_ok=True)
+        net.save(os.path.join(a.planner_save, "costnet.json"))
+        cm.save_records(recs, os.path.join(a.planner_save, "records.json"))
+    cands = {}
+    for r in recs:
+        cands[r["dag"]] = cands.get(r["dag"], 0) + (1 if r["cand"] >= 0 else 0)
     print(json.dumps({"workload": "random DAGs, depth<=5, dims log-uniform [16,8192], FP32/BF16, literal <= 2e11 FLOP",
                       "dags_timed": done, "records": len(recs), "train_records": len(train), "test_dags": res["dags"],
-                      "gen_s": gen_s, "collect_s": collect_s, "train_s": train_s, "train_steps": 3000,
-                      "loss_first_last": [losses[0], losses[-1]], "held_out": res,
+                      "candidates_per_dag_mean": sum(cands.values()) / max(1, len(cands)),
+                      "gen_s": gen_s, "collect_s": collect_s, "train_s": train_s, "train_steps": steps,
+                      "loss_first_last": [losses[0], losses[-1]], "guard": guard, "held_out": res,
+                      "library_choice_agrees": f"{agree}/{len(mlp)}",
                       "train_fit": {k: res_train[k] for k in res_train if k.endswith("regret")}}), flush=True)
 
 
@@ -681,7 +728,6 @@ def main():
         lits[dt] = ag.Plan(nodes, o, flags=ag.PLAN_LITERAL)
         outs[dt] = plans[dt].alloc_outputs(dev)
         plans[dt].workspace(dev)
-    del hin
     torch.cuda.synchronize()
 
     def step():
@@ -784,21 +830,24 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / a.e2e_steps
 
-    # ---- accuracy against the oracle on the CPU sample (rank 0) ----
+    # ---- accuracy against the oracle on the whole workload (rank 0) ----
     cpu = None
     err = {}
     if rank == 0 and not a.no_cpu:
         import oracle
         oracle.build()
-        cols = SAMPLE_COLS if n == N else max(1, n // 8)
-        t_cpu, ref, _ = oracle_sample(n, cols)
+        t_cpu, ref = oracle_full(hin, n)
         for dt in DTYPES:
-            blk = outs[dt][0][:, :cols].double().cpu().numpy()
-            err[dt] = {"out_block": oracle.rel_err(blk, ref[dt][0])}
-        frac = cols / n
-        cpu = {"value": 2 * frac / t_cpu, "unit": "evals/s", "cores": 1, "kind": "oracle",
-               "sample": f"literal FP64 oracle (one thread) on the {n}x{cols} column block of both "
-                         f"element types, scaled by {n}/{cols}; {t_cpu:.2f} s"}
+            got = outs[dt][0].double().cpu().numpy()
+            err[dt] = {"out": rel_err(got, ref[dt][0]),
+                       "accu": rel_err(float(outs[dt][1].item()), ref[dt][1]),
+                       "norm_fro": rel_err(float(outs[dt][2].item()), ref[dt][2])}
+            del got
+        cpu = {"value": 2 / t_cpu, "unit": "evals/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"the whole workload: literal FP64 oracle on A,B,C,D {n}x{n} in FP32 and FP64, "
+                         f"one evaluation each; {t_cpu:.2f} s"}
+        cpu.update(host_cpu())
+    del hin
 
     # ---- roofline of the dominant kernel ----
     hbm, src = peaks()

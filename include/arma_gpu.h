@@ -66,7 +66,10 @@ typedef enum {
   ARMA_ERR_SINGULAR = 6,    /* LU met an exact zero pivot (LAPACK info > 0) */
   ARMA_ERR_NOCONVERGE = 7,  /* iterative refinement did not reach its tolerance */
   ARMA_ERR_CUDA = 8,        /* a CUDA runtime call failed */
-  ARMA_ERR_UNSUPPORTED = 9  /* a valid expression this library does not evaluate */
+  ARMA_ERR_UNSUPPORTED = 9, /* a valid expression this library does not evaluate */
+  ARMA_ERR_TIMEOUT = 10     /* a bounded device-side wait ran out (arma_gpu_set_wait_limit_ns);
+                               the kernels concerned returned early and the outputs are
+                               not valid */
 } arma_status;
 
 /* Operations of the expression tree.  Operands are earlier node indices. */
@@ -135,7 +138,12 @@ typedef enum {
 #define ARMA_PLAN_CHAIN_LEFT   0x2u  /* keep the written left-to-right order of product chains */
 #define ARMA_PLAN_CHAIN_GREEDY 0x4u  /* the paper's chain rule (smallest adjacent result first)
                                         instead of the exact minimum-cost order */
-#define ARMA_PLAN_COST_MLP     0x8u  /* rank candidate plans with the learned cost model */
+#define ARMA_PLAN_COST_MLP     0x8u  /* choose among candidate plans (arma_gpu_plan_candidates)
+                                        the one the learned cost model loaded with
+                                        arma_gpu_cost_model_load predicts fastest; with no
+                                        model loaded, or when the FLOP/byte estimate rates the
+                                        network's pick worse than its own pick by more than
+                                        the model's guard factor, the estimate's pick */
 #define ARMA_PLAN_NO_FUSE      0x10u /* optimised rewrites but no elementwise fusion */
 #define ARMA_PLAN_NO_TENSOR    0x20u /* batched plans: SIMT tiles instead of tensor-core tiles */
 #define ARMA_PLAN_TILE64       0x40u /* batched SIMT tiles: 64 x 64 for every problem */
@@ -147,6 +155,25 @@ typedef enum {
 #define ARMA_PLAN_NO_SOLVE_ANALYSIS 0x200u /* solves skip the run-time analysis of their
                                          matrix: always the general LU, and the evaluation
                                          never waits on its stream */
+#define ARMA_PLAN_COST_HEURISTIC 0x400u /* choose among candidate plans the one with the
+                                         smallest FLOP/byte estimate
+                                         (arma_gpu_plan_heuristic_cost) */
+#define ARMA_PLAN_TIER_CHOICE  0x800u /* with a COST flag: candidates also take every
+                                         precision tier at least as accurate as the requested
+                                         one (BF16 < SPLIT_BF16 < LU32_IR64 < F64; NATIVE may
+                                         move to F64, and to SPLIT_BF16 when all inputs are
+                                         BF16) */
+#define ARMA_PLAN_NO_SPLITK    0x1000u /* products without split-K: one CTA per output tile
+                                         over the whole reduction dimension */
+/* Step limit of the FP64 iterative refinement of mixed-precision solves
+ * (tiers LU32_IR64 and BF16; Sec. I and Sec. III (9): inv(A)*b as a
+ * solve).  ARMA_PLAN_REFINE_STEPS(k), 1 <= k <= 15, stops after k steps; 0
+ * (the default) means 10.  A solve that has not reached its stopping rule
+ * (normwise backward error <= 1e-14) within the limit reports
+ * ARMA_ERR_NOCONVERGE with info = the steps taken. */
+#define ARMA_PLAN_REFINE_SHIFT 16
+#define ARMA_PLAN_REFINE_MASK  0xF0000u
+#define ARMA_PLAN_REFINE_STEPS(k) ((((uint32_t)(k)) & 0xFu) << ARMA_PLAN_REFINE_SHIFT)
 
 typedef struct arma_node {
   int32_t op;        /* arma_op */
@@ -227,6 +254,18 @@ void arma_gpu_plan_free(arma_plan* plan);
 
 const char* arma_gpu_status_string(arma_status status);
 
+/* Time limit of each bounded device-side wait that the solve kernels make
+ * on one another's progress (the flag waits of the cooperative blocked
+ * substitution and the grid barrier of the cooperative panel), in
+ * nanoseconds; 2e9 (2 s) by default.  A wait that runs out records
+ * ARMA_ERR_TIMEOUT in the evaluation's status word, every other wait of the
+ * launch then gives up, and all kernels return.  0 means: give up at the
+ * first poll that finds the awaited flag unset.  The setting is process-wide
+ * and read when a kernel is launched; it exists so that callers (and this
+ * library's tests) can exercise failure detection without a hung GPU.
+ * Returns the previous limit. */
+uint64_t arma_gpu_set_wait_limit_ns(uint64_t ns);
+
 /* Name and text of the last CUDA runtime error behind an ARMA_ERR_CUDA
  * returned to the calling thread ("" if none).  The string is owned by the
  * library and stays valid until the thread's next failing call. */
@@ -234,19 +273,64 @@ const char* arma_gpu_last_cuda_error(void);
 
 /* ---- Cost model.  The paper chooses an evaluation by fixed rules
  * (compile-time patterns, Sec. II; the greedy chain rule, Sec. II chain
- * paragraph).  Here candidate plans of one expression (the flag variants
- * above) are ranked either by a FLOP/byte roofline estimate or by a small
- * learned network trained on timings this library records. ---- */
+ * paragraph).  Here arma_gpu_plan itself can choose among candidate plans of
+ * one expression (ARMA_PLAN_COST_HEURISTIC, ARMA_PLAN_COST_MLP): chain
+ * order, fusion, split-K and precision tier, ranked either by a FLOP/byte
+ * roofline estimate or by a small learned network trained on timings that
+ * this library records with its own GPU kernels.  The plan's decision log
+ * (arma_gpu_plan_info) lists the candidates, their scores and the pick. ---- */
 
-#define ARMA_PLAN_FEATURES 16
+#define ARMA_PLAN_FEATURES 24
 
-/* Host only: the plan's feature vector (log2 work and bytes, step counts
- * per kernel kind, tensor-core share, literal flag, ...); n >= 16 floats. */
+/* Host only: the plan's feature vector; n >= ARMA_PLAN_FEATURES floats.
+ *   0 log2(1 + flops)            1 log2(1 + bytes)         2 steps
+ *   3 elementwise steps          4 product steps           5 matrix-vector steps
+ *   6 diagonal-dot steps         7 copy steps              8 solve steps
+ *   9 log2(1 + largest step flops)  10 log2(1 + largest step bytes)
+ *  11 log2(1 + workspace bytes)  12 tensor-core share of flops
+ *  13 literal plan               14 split-BF16 share of flops
+ *  15 log2(1 + flops / bytes)    16 ln(FLOP/byte estimate, seconds)
+ *  17 kernel launches            18 FP64 DFMA share of flops
+ *  19 share of the estimate spent in elementwise passes
+ *  20 share of the estimate spent in products
+ *  21 log2(1 + smallest dimension of the largest product)
+ *  22 products without split-K   23 log2(1 + largest output elements) */
 arma_status arma_gpu_plan_features(const arma_plan* plan, float* features, int32_t n);
 
 /* Host only: estimated seconds, summing per step a launch plus the larger
  * of its compute time and its memory time on GB300. */
 arma_status arma_gpu_plan_heuristic_cost(const arma_plan* plan, double* seconds);
+
+/* Host only: plan every distinct candidate evaluation of an expression: the
+ * chain orders (exact DP, the paper's greedy rule, written order), with and
+ * without elementwise fusion, with and without split-K, and, with
+ * ARMA_PLAN_TIER_CHOICE, every admissible precision tier.  Candidates whose
+ * step lists coincide are planned once.  plans[i] (i < *count) receive new
+ * plans, owned by the caller (arma_gpu_plan_free); at most capacity are
+ * written and *count receives the number of distinct candidates.  The
+ * expression's own COST flags are ignored; ARMA_PLAN_LITERAL gives the
+ * literal plan alone. */
+arma_status arma_gpu_plan_candidates(const arma_expr* expr, arma_plan** plans, int32_t capacity,
+                                     int32_t* count);
+
+/* Load the learned cost model that ARMA_PLAN_COST_MLP consults (host
+ * memory, copied; process-wide, replaces any earlier model).  The network
+ * (layout as arma_gpu_mlp_forward) maps the standardised feature vector
+ * z_i = (f_i - mean[i]) / scale[i] of a plan to a correction of the
+ * FLOP/byte estimate: predicted seconds = estimate * exp(network(z)).
+ * features must be ARMA_PLAN_FEATURES; hidden <= 128; guard >= 1 is the
+ * factor by which the estimate may rate the network's pick slower than its
+ * own before that pick is overruled (0: never overruled). */
+arma_status arma_gpu_cost_model_load(const float* params, int32_t features, int32_t hidden, const float* mean,
+                                     const float* scale, double guard);
+
+/* Forget the loaded cost model (ARMA_PLAN_COST_MLP then uses the estimate). */
+void arma_gpu_cost_model_clear(void);
+
+/* Host only: seconds the loaded cost model predicts for a plan (the same
+ * arithmetic as arma_gpu_mlp_forward, in FP32 on the host).  Returns
+ * ARMA_ERR_UNSUPPORTED when no model is loaded. */
+arma_status arma_gpu_cost_model_predict(const arma_plan* plan, double* seconds);
 
 /* Cost network: y = W3 relu(W2 relu(W1 x + b1) + b2) + b3, FP32, with
  * features <= 64 inputs and hidden <= 128 units; parameters packed as
@@ -317,9 +401,11 @@ arma_status arma_gpu_eval_batched(const arma_plan* plan, const void* device_tabl
  * if arma_gpu_plan_workspace() <= ARMA_STATIC_SCRATCH_BYTES; otherwise the
  * call returns ARMA_ERR_UNSUPPORTED or ARMA_ERR_WORKSPACE and launches
  * nothing.  The scratch lives in one file-scope device array of
- * ARMA_STATIC_SCRATCH_BYTES per GPU, held until the process exits.  The
- * first call on a device looks up that array's device address (with the
- * device current); make that first call before any stream capture.  The
+ * ARMA_STATIC_SCRATCH_BYTES per GPU, held until the process exits.  Every
+ * call outside stream capture looks up that array's device address (with
+ * the device current); a call under capture reuses the address found by the
+ * last call outside capture, so make the first call on a device before any
+ * stream capture.  The
  * call allocates nothing.  Every call shares the array: calls whose kernels
  * overlap on the GPU (different streams, or other threads) race on it.
  * in_ptrs, out_ptrs and stream mean the same as in arma_gpu_eval. */

@@ -29,12 +29,14 @@
 
 void or_add(int64_t m, int64_t n, const double* a, int64_t lda, const double* b,
             int64_t ldb, double* c, int64_t ldc) {
+#pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n; ++j)
     for (int64_t i = 0; i < m; ++i) AT(c, ldc, i, j) = AT(a, lda, i, j) + AT(b, ldb, i, j);
 }
 
 void or_sub(int64_t m, int64_t n, const double* a, int64_t lda, const double* b,
             int64_t ldb, double* c, int64_t ldc) {
+#pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n; ++j)
     for (int64_t i = 0; i < m; ++i) AT(c, ldc, i, j) = AT(a, lda, i, j) - AT(b, ldb, i, j);
 }
@@ -42,6 +44,7 @@ void or_sub(int64_t m, int64_t n, const double* a, int64_t lda, const double* b,
 /* Schur (elementwise) product, Armadillo's operator % */
 void or_schur(int64_t m, int64_t n, const double* a, int64_t lda, const double* b,
               int64_t ldb, double* c, int64_t ldc) {
+#pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n; ++j)
     for (int64_t i = 0; i < m; ++i) AT(c, ldc, i, j) = AT(a, lda, i, j) * AT(b, ldb, i, j);
 }
@@ -49,6 +52,7 @@ void or_schur(int64_t m, int64_t n, const double* a, int64_t lda, const double* 
 /* elementwise division, Armadillo's operator / between matrices */
 void or_div(int64_t m, int64_t n, const double* a, int64_t lda, const double* b,
             int64_t ldb, double* c, int64_t ldc) {
+#pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n; ++j)
     for (int64_t i = 0; i < m; ++i) AT(c, ldc, i, j) = AT(a, lda, i, j) / AT(b, ldb, i, j);
 }
@@ -56,6 +60,7 @@ void or_div(int64_t m, int64_t n, const double* a, int64_t lda, const double* b,
 /* s * X (the Op<Mat, op_mul> marker of Sec. II) */
 void or_scale(int64_t m, int64_t n, double s, const double* a, int64_t lda, double* c,
               int64_t ldc) {
+#pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n; ++j)
     for (int64_t i = 0; i < m; ++i) AT(c, ldc, i, j) = s * AT(a, lda, i, j);
 }
@@ -63,6 +68,7 @@ void or_scale(int64_t m, int64_t n, double s, const double* a, int64_t lda, doub
 /* X / s */
 void or_div_scalar(int64_t m, int64_t n, double s, const double* a, int64_t lda, double* c,
                    int64_t ldc) {
+#pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n; ++j)
     for (int64_t i = 0; i < m; ++i) AT(c, ldc, i, j) = AT(a, lda, i, j) / s;
 }
@@ -70,12 +76,14 @@ void or_div_scalar(int64_t m, int64_t n, double s, const double* a, int64_t lda,
 /* X + s */
 void or_add_scalar(int64_t m, int64_t n, double s, const double* a, int64_t lda, double* c,
                    int64_t ldc) {
+#pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n; ++j)
     for (int64_t i = 0; i < m; ++i) AT(c, ldc, i, j) = AT(a, lda, i, j) + s;
 }
 
 /* -X */
 void or_neg(int64_t m, int64_t n, const double* a, int64_t lda, double* c, int64_t ldc) {
+#pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n; ++j)
     for (int64_t i = 0; i < m; ++i) AT(c, ldc, i, j) = -AT(a, lda, i, j);
 }
@@ -84,6 +92,7 @@ void or_neg(int64_t m, int64_t n, const double* a, int64_t lda, double* c, int64
 
 /* C (n x m) = A^T for A (m x n) */
 void or_trans(int64_t m, int64_t n, const double* a, int64_t lda, double* c, int64_t ldc) {
+#pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n; ++j)
     for (int64_t i = 0; i < m; ++i) AT(c, ldc, j, i) = AT(a, lda, i, j);
 }
@@ -133,6 +142,7 @@ void or_diagmat_vec(int64_t n, const double* v, int64_t inc, double* c, int64_t 
 
 /* matrix X (m x n) -> same shape, off-diagonal elements zeroed */
 void or_diagmat_mat(int64_t m, int64_t n, const double* a, int64_t lda, double* c, int64_t ldc) {
+#pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < n; ++j)
     for (int64_t i = 0; i < m; ++i) AT(c, ldc, i, j) = (i == j) ? AT(a, lda, i, j) : 0.0;
 }

@@ -39,8 +39,15 @@ OPS = {"input": 0, "add": 1, "sub": 2, "schur": 3, "div": 4, "scale": 5, "div_sc
 TIERS = {"native": 0, "f64": 1, "split_bf16": 2, "bf16": 3, "lu32_ir64": 4}
 PLAN_LITERAL, PLAN_CHAIN_LEFT, PLAN_CHAIN_GREEDY, PLAN_COST_MLP, PLAN_NO_FUSE, PLAN_NO_TENSOR = 1, 2, 4, 8, 16, 32
 PLAN_TILE64, PLAN_TILE32, PLAN_NO_SYRK, PLAN_NO_SOLVE_ANALYSIS = 64, 128, 256, 512
+PLAN_COST_HEURISTIC, PLAN_TIER_CHOICE, PLAN_NO_SPLITK = 0x400, 0x800, 0x1000
 STATUS = {0: "ok", 1: "invalid", 2: "shape", 3: "dtype", 4: "align", 5: "workspace",
-          6: "singular", 7: "noconverge", 8: "cuda", 9: "unsupported"}
+          6: "singular", 7: "noconverge", 8: "cuda", 9: "unsupported", 10: "timeout"}
+PLAN_REFINE_SHIFT, PLAN_REFINE_MASK = 16, 0xF0000
+
+
+def PLAN_REFINE_STEPS(k: int) -> int:
+    """Plan flag: stop FP64 iterative refinement after k (1..15) steps."""
+    return (int(k) & 0xF) << PLAN_REFINE_SHIFT
 
 
 class ArmaError(RuntimeError):
@@ -66,13 +73,15 @@ class Expr(ctypes.Structure):
 
 EXPORTS = ["arma_gpu_plan", "arma_gpu_plan_workspace", "arma_gpu_output_info", "arma_gpu_eval",
            "arma_gpu_eval_status", "arma_gpu_eval_solve_path", "arma_gpu_plan_info", "arma_gpu_plan_free",
-           "arma_gpu_status_string", "arma_gpu_last_cuda_error", "arma_gpu_chain_order",
+           "arma_gpu_status_string", "arma_gpu_last_cuda_error", "arma_gpu_set_wait_limit_ns",
+           "arma_gpu_chain_order",
            "arma_gpu_eval_fused_static",
            "arma_gpu_plan_batched", "arma_gpu_batched_table_bytes", "arma_gpu_batched_table_fill",
            "arma_gpu_eval_batched", "arma_gpu_plan_features", "arma_gpu_plan_heuristic_cost",
            "arma_gpu_mlp_param_count", "arma_gpu_mlp_workspace", "arma_gpu_mlp_forward", "arma_gpu_mlp_grad",
-           "arma_gpu_mlp_adam"]
-N_FEATURES = 16
+           "arma_gpu_mlp_adam", "arma_gpu_plan_candidates", "arma_gpu_cost_model_load",
+           "arma_gpu_cost_model_clear", "arma_gpu_cost_model_predict"]
+N_FEATURES = 24
 STATIC_SCRATCH_BYTES = 131072
 
 
@@ -95,6 +104,8 @@ def lib() -> ctypes.CDLL:
     L.arma_gpu_status_string.restype = ctypes.c_char_p
     L.arma_gpu_last_cuda_error.argtypes = []
     L.arma_gpu_last_cuda_error.restype = ctypes.c_char_p
+    L.arma_gpu_set_wait_limit_ns.argtypes = [ctypes.c_uint64]
+    L.arma_gpu_set_wait_limit_ns.restype = ctypes.c_uint64
     L.arma_gpu_chain_order.argtypes = [i32, ctypes.POINTER(i64), i32, ctypes.POINTER(i32),
                                        ctypes.POINTER(ctypes.c_uint64)]
     L.arma_gpu_eval_fused_static.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
@@ -104,6 +115,11 @@ def lib() -> ctypes.CDLL:
     L.arma_gpu_eval_batched.argtypes = [vp, vp, vp, ctypes.c_size_t, vp]
     L.arma_gpu_plan_features.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
     L.arma_gpu_plan_heuristic_cost.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.arma_gpu_plan_candidates.argtypes = [ctypes.POINTER(Expr), ctypes.POINTER(vp), i32, ctypes.POINTER(i32)]
+    L.arma_gpu_cost_model_load.argtypes = [vp, i32, i32, vp, vp, ctypes.c_double]
+    L.arma_gpu_cost_model_clear.argtypes = []
+    L.arma_gpu_cost_model_clear.restype = None
+    L.arma_gpu_cost_model_predict.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.arma_gpu_mlp_param_count.argtypes = [i32, i32]
     L.arma_gpu_mlp_param_count.restype = i64
     L.arma_gpu_mlp_workspace.argtypes = [i32, i32, i32]
@@ -121,6 +137,12 @@ def _check(code: int, where: str):
         if STATUS.get(code) == "cuda":
             detail = (lib().arma_gpu_last_cuda_error() or b"").decode(errors="replace")
         raise ArmaError(code, where, detail)
+
+
+def set_wait_limit_ns(ns: int) -> int:
+    """Limit of each bounded device wait of the solve kernels (ns, process
+    wide); 0 gives up at the first unset poll.  Returns the previous limit."""
+    return int(lib().arma_gpu_set_wait_limit_ns(int(ns)))
 
 
 def torch_dtype(dt: int):
@@ -166,20 +188,54 @@ def _mk_nodes(nodes):
     return arr
 
 
+def _mk_expr(nodes, outputs, tier, flags):
+    arr = _mk_nodes(nodes)
+    outs = (ctypes.c_int32 * len(outputs))(*outputs)
+    e = Expr(len(nodes), len(outputs), arr, outs, TIERS[tier] if isinstance(tier, str) else int(tier), int(flags))
+    return e, arr, outs
+
+
+def candidates(nodes, outputs, tier="native", flags=0, capacity=128):
+    """Every distinct candidate plan the library considers for an expression
+    (arma_gpu_plan_candidates), in its enumeration order: the index of the
+    candidate a COST-flag plan picked (``info["choice"]["picked"]``)."""
+    L = lib()
+    e, arr, outs = _mk_expr(nodes, outputs, tier, flags)
+    hs = (ctypes.c_void_p * capacity)()
+    n = ctypes.c_int32()
+    _check(L.arma_gpu_plan_candidates(ctypes.byref(e), hs, capacity, ctypes.byref(n)), "arma_gpu_plan_candidates")
+    return [Plan(nodes, outputs, _handle=ctypes.c_void_p(hs[i])) for i in range(min(n.value, capacity))]
+
+
+def load_cost_model(params, mean, scale, hidden, guard=0.0):
+    """Give the library a trained cost network (host arrays; see
+    arma_gpu_cost_model_load).  ARMA_PLAN_COST_MLP plans consult it."""
+    import numpy as np
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    mu = np.ascontiguousarray(np.asarray(mean, dtype=np.float32))
+    sd = np.ascontiguousarray(np.asarray(scale, dtype=np.float32))
+    _check(lib().arma_gpu_cost_model_load(p.ctypes.data, len(mu), int(hidden), mu.ctypes.data, sd.ctypes.data,
+                                          float(guard)), "arma_gpu_cost_model_load")
+
+
+def clear_cost_model():
+    lib().arma_gpu_cost_model_clear()
+
+
 class Plan:
     """A planned expression.  Planning runs on the host only; ``__call__``
     enqueues the plan's kernels on the current CUDA stream."""
 
-    def __init__(self, nodes, outputs, tier="native", flags=0):
+    def __init__(self, nodes, outputs, tier="native", flags=0, _handle=None):
         self.nodes = [dict(d) for d in nodes]
         self.outputs = list(outputs)
         L = lib()
-        self._arr = _mk_nodes(self.nodes)
-        self._outs = (ctypes.c_int32 * len(self.outputs))(*self.outputs)
-        e = Expr(len(self.nodes), len(self.outputs), self._arr, self._outs,
-                 TIERS[tier] if isinstance(tier, str) else int(tier), int(flags))
-        h = ctypes.c_void_p()
-        _check(L.arma_gpu_plan(ctypes.byref(e), ctypes.byref(h)), "arma_gpu_plan")
+        if _handle is None:
+            e, self._arr, self._outs = _mk_expr(self.nodes, self.outputs, tier, flags)
+            h = ctypes.c_void_p()
+            _check(L.arma_gpu_plan(ctypes.byref(e), ctypes.byref(h)), "arma_gpu_plan")
+        else:
+            h = _handle
         self._h = h
         ws = ctypes.c_size_t()
         _check(L.arma_gpu_plan_workspace(h, ctypes.byref(ws)), "arma_gpu_plan_workspace")
@@ -215,6 +271,12 @@ class Plan:
         f = (ctypes.c_float * N_FEATURES)()
         _check(lib().arma_gpu_plan_features(self._h, f, N_FEATURES), "arma_gpu_plan_features")
         return list(f)
+
+    def predicted_cost(self) -> float:
+        """Seconds the loaded cost network predicts (host forward pass)."""
+        c = ctypes.c_double()
+        _check(lib().arma_gpu_cost_model_predict(self._h, ctypes.byref(c)), "arma_gpu_cost_model_predict")
+        return float(c.value)
 
     def heuristic_cost(self) -> float:
         c = ctypes.c_double()

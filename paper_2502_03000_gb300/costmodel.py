@@ -1,12 +1,22 @@
 """Learned ranking of candidate plans.
 
-For an expression the planner can produce several candidate plans (exact
-chain order, the paper's greedy chain rule, written order, no elementwise
-fusion, the literal one-kernel-per-operator plan).  This module records
-their run times, trains the library's cost network on the GPU (forward,
-gradient and Adam kernels of libarma_gpu.so) to predict log run time from
-the plan features, and ranks candidates with it.  The FLOP/byte roofline
-estimate (arma_gpu_plan_heuristic_cost) is the fallback and the yardstick.
+For one expression the library plans several candidates
+(arma_gpu_plan_candidates: chain order, elementwise fusion, split-K and,
+with ARMA_PLAN_TIER_CHOICE, every precision tier at least as accurate as the
+one asked for).  This module records their run times on the GPU, trains the
+library's cost network with the library's own forward, gradient and Adam
+kernels, and hands the trained network to the library, whose planner then
+ranks the candidates itself (ARMA_PLAN_COST_MLP).
+
+The network predicts a correction to the FLOP/byte roofline estimate
+(arma_gpu_plan_heuristic_cost): predicted seconds = estimate *
+exp(network(standardised features)).  The estimate is also one of the
+features, so an untrained network (output 0) ranks exactly like the
+estimate.  The estimate remains the fallback (no model loaded) and the judge
+of the network's picks (the guard factor of arma_gpu_cost_model_load).
+
+Weights, feature scaling and the timing records persist as JSON
+(``CostNet.save`` / ``CostNet.load``, ``save_records`` / ``load_records``).
 """
 from __future__ import annotations
 
@@ -16,35 +26,37 @@ import math
 
 import numpy as np
 
-from . import (PLAN_CHAIN_GREEDY, PLAN_CHAIN_LEFT, PLAN_LITERAL, PLAN_NO_FUSE, N_FEATURES, ArmaError, Plan,
-               _check, lib)
+from . import (PLAN_LITERAL, PLAN_TIER_CHOICE, PLAN_COST_MLP, N_FEATURES, ArmaError, Plan, _check, candidates,
+               lib, load_cost_model)
 
-CANDIDATES = (("dp", 0), ("paper_greedy", PLAN_CHAIN_GREEDY), ("written_order", PLAN_CHAIN_LEFT),
-              ("unfused", PLAN_NO_FUSE), ("literal", PLAN_LITERAL))
 HIDDEN = 64
+HEURISTIC_FEATURE = 16      # ln(FLOP/byte estimate) among the plan features
 
 
-def candidate_plans(nodes, outputs, tier="native"):
-    """Distinct candidate plans (duplicates by kernel sequence removed; the
-    literal plan is always kept as the reference point)."""
-    out, seen = [], set()
-    for name, flags in CANDIDATES:
-        p = Plan(nodes, outputs, tier=tier, flags=flags)
-        key = json.dumps([(s["kernel"], s["note"]) for s in p.info["steps"]])
-        if key in seen and name != "literal":
-            continue
-        seen.add(key)
-        out.append((name, p))
+def candidate_plans(nodes, outputs, tier="native", flags=PLAN_TIER_CHOICE):
+    """The library's distinct candidates for an expression, as (index, Plan)
+    in its enumeration order, and the literal plan last with index -1."""
+    out = [(i, p) for i, p in enumerate(candidates(nodes, outputs, tier=tier, flags=flags))]
+    out.append((-1, Plan(nodes, outputs, tier=tier, flags=PLAN_LITERAL)))
     return out
 
 
-def time_plan(plan, inputs, reps=3, device="cuda"):
+def time_plan(plan, inputs, device="cuda", target_s=1e-3, max_reps=50):
+    """Mean seconds per evaluation (CUDA events): one warm-up, one timed
+    evaluation to size the repetition count, then enough repetitions for
+    about target_s of GPU time (at least 3)."""
     import torch
     outs = plan.alloc_outputs(device)
     plan(*inputs, outputs=outs)
     torch.cuda.synchronize()
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    plan(*inputs, outputs=outs)
+    e1.record(s)
+    torch.cuda.synchronize()
+    t1 = max(e0.elapsed_time(e1) * 1e-3, 1e-7)
+    reps = int(min(max_reps, max(3, target_s / t1)))
     e0.record(s)
     for _ in range(reps):
         plan(*inputs, outputs=outs)
@@ -53,28 +65,44 @@ def time_plan(plan, inputs, reps=3, device="cuda"):
     return e0.elapsed_time(e1) / reps * 1e-3
 
 
-def collect(dags, device="cuda", reps=3, gen_seed=7):
-    """Time every distinct candidate of every DAG.  dags: list of
-    (nodes, outputs, dtype).  Returns a list of records."""
+def dag_inputs(nodes, dtype, g, device="cuda"):
     import torch
     from synth.dags import input_shapes
+    td = torch.float32 if dtype == "f32" else torch.bfloat16
+    return [(torch.rand((c, r), device=device, generator=g) * 2 - 1).to(td).t() for r, c in input_shapes(nodes)]
+
+
+def collect(dags, device="cuda", gen_seed=7, flags=PLAN_TIER_CHOICE, target_s=1e-3):
+    """Time every candidate (and the literal plan) of every DAG.  dags: list
+    of (nodes, outputs, dtype).  Returns a list of records."""
+    import torch
     g = torch.Generator(device=device)
     g.manual_seed(gen_seed)
     recs = []
     for di, (nodes, outs, dt) in enumerate(dags):
-        td = torch.float32 if dt == "f32" else torch.bfloat16
-        ins = [(torch.rand((c, r), device=device, generator=g) * 2 - 1).to(td).t() for r, c in input_shapes(nodes)]
-        for ci, (name, p) in enumerate(candidate_plans(nodes, outs)):
-            t = time_plan(p, ins, reps, device)
-            recs.append({"dag": di, "cand": name, "features": p.features(), "time": t,
+        ins = dag_inputs(nodes, dt, g, device)
+        for ci, p in candidate_plans(nodes, outs, flags=flags):
+            t = time_plan(p, ins, device, target_s=target_s)
+            recs.append({"dag": di, "cand": ci, "features": p.features(), "time": t,
                          "heuristic": p.heuristic_cost(), "kernels": len(p.info["steps"])})
             p._ws.clear()
         del ins
     return recs
 
 
+def save_records(recs, path):
+    with open(path, "w") as f:
+        json.dump(recs, f)
+
+
+def load_records(path):
+    with open(path) as f:
+        return json.load(f)
+
+
 class CostNet:
-    """The cost network on the GPU; inputs are standardised features."""
+    """The cost network on the GPU; inputs are standardised features, the
+    output a log-seconds correction to the FLOP/byte estimate."""
 
     def __init__(self, features=N_FEATURES, hidden=HIDDEN, seed=0, device="cuda"):
         import torch
@@ -82,12 +110,13 @@ class CostNet:
         self.P = int(lib().arma_gpu_mlp_param_count(features, hidden))
         rng = np.random.default_rng(seed)
         w = []
-        # He-style initialisation for ReLU layers
+        # He-style initialisation for the ReLU layers; the output layer
+        # starts at zero, so the untrained network reproduces the estimate
         w.append(rng.normal(0, math.sqrt(2.0 / features), hidden * features))
         w.append(np.zeros(hidden))
         w.append(rng.normal(0, math.sqrt(2.0 / hidden), hidden * hidden))
         w.append(np.zeros(hidden))
-        w.append(rng.normal(0, math.sqrt(1.0 / hidden), hidden))
+        w.append(np.zeros(hidden))
         w.append(np.zeros(1))
         self.params = torch.tensor(np.concatenate(w), dtype=torch.float32, device=device)
         self.mu = np.zeros(features)
@@ -98,7 +127,8 @@ class CostNet:
         Z = (np.asarray(X, dtype=np.float64) - self.mu) / self.sd
         return torch.tensor(Z, dtype=torch.float32, device=self.device).contiguous()
 
-    def predict(self, X):
+    def correction(self, X):
+        """network(standardised X): the predicted ln(time / estimate)."""
         import torch
         x = self._x(X)
         y = torch.empty(x.shape[0], dtype=torch.float32, device=self.device)
@@ -108,14 +138,20 @@ class CostNet:
                                           ctypes.c_void_p(st)), "arma_gpu_mlp_forward")
         return y.double().cpu().numpy()
 
-    def fit(self, X, T, steps=2000, lr=3e-3):
-        """Full-batch Adam on the mean squared error of log time."""
+    def predict_log_seconds(self, X):
+        X = np.asarray(X, dtype=np.float64)
+        return X[:, HEURISTIC_FEATURE] + self.correction(X)
+
+    def fit(self, X, log_t, steps=2000, lr=3e-3):
+        """Full-batch Adam on the mean squared error of ln(time / estimate)."""
         import torch
         X = np.asarray(X, dtype=np.float64)
+        target = np.asarray(log_t, dtype=np.float64) - X[:, HEURISTIC_FEATURE]
         self.mu = X.mean(axis=0)
-        self.sd = X.std(axis=0) + 1e-6
+        self.sd = X.std(axis=0)
+        self.sd[self.sd < 1e-6] = 1.0
         x = self._x(X)
-        t = torch.tensor(np.asarray(T), dtype=torch.float32, device=self.device)
+        t = torch.tensor(target, dtype=torch.float32, device=self.device)
         n = x.shape[0]
         g = torch.zeros(self.P, dtype=torch.float32, device=self.device)
         m = torch.zeros_like(g)
@@ -130,6 +166,8 @@ class CostNet:
                                        ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()), n,
                                        ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                        ctypes.c_void_p(ws.data_ptr()), ws.numel(), st), "arma_gpu_mlp_grad")
+            if k == 1:
+                losses.append(float(((y - t) ** 2).mean().item()))
             _check(L.arma_gpu_mlp_adam(ctypes.c_void_p(self.params.data_ptr()), ctypes.c_void_p(g.data_ptr()),
                                        ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(v.data_ptr()), self.P, k,
                                        lr, 0.9, 0.999, 1e-8, st), "arma_gpu_mlp_adam")
@@ -137,31 +175,90 @@ class CostNet:
                 losses.append(float(((y - t) ** 2).mean().item()))
         return losses
 
+    def host_params(self):
+        return self.params.detach().float().cpu().numpy()
 
-def choose(recs_by_dag, scores):
-    """For each DAG the candidate with the smallest score."""
-    return {d: min(rs, key=lambda r: scores[id(r)]) for d, rs in recs_by_dag.items()}
+    def to_library(self, guard=0.0):
+        """Load this network into the library's planner (ARMA_PLAN_COST_MLP)."""
+        load_cost_model(self.host_params(), self.mu, self.sd, self.H, guard)
+
+    def save(self, path):
+        with open(path, "w") as f:
+            json.dump({"features": self.F, "hidden": self.H, "params": self.host_params().tolist(),
+                       "mean": [float(x) for x in self.mu], "scale": [float(x) for x in self.sd]}, f)
+
+    @classmethod
+    def load(cls, path, device="cuda"):
+        import torch
+        with open(path) as f:
+            d = json.load(f)
+        net = cls(d["features"], d["hidden"], device=device)
+        net.params = torch.tensor(np.asarray(d["params"], dtype=np.float32), device=device)
+        net.mu = np.asarray(d["mean"], dtype=np.float64)
+        net.sd = np.asarray(d["scale"], dtype=np.float64)
+        return net
 
 
-def evaluate(recs, net=None):
-    """Geometric-mean time over DAGs of the network's pick, the heuristic's
-    pick, the literal plan and the best candidate (regret = pick / best)."""
+def by_dag(recs):
     by = {}
     for r in recs:
         by.setdefault(r["dag"], []).append(r)
-    heur = choose(by, {id(r): r["heuristic"] for r in recs})
-    res = {"dags": len(by)}
-    picks = {"heuristic": heur,
-             "literal": {d: next(r for r in rs if r["cand"] == "literal") for d, rs in by.items()},
-             "best": {d: min(rs, key=lambda r: r["time"]) for d, rs in by.items()}}
+    return by
+
+
+def picks(recs, net=None, guard=0.0):
+    """Per DAG, the candidate the estimate picks and (with a network) the one
+    the network picks under the library's rule: the smallest predicted time,
+    overruled by the estimate's pick when the estimate rates it more than
+    `guard` times slower.  Only the library's candidates are eligible."""
+    by = by_dag(recs)
+    heur, mlp, guarded = {}, {}, 0
+    pred = {}
     if net is not None:
-        pred = net.predict([r["features"] for r in recs])
-        picks["mlp"] = choose(by, {id(r): p for r, p in zip(recs, pred)})
-    for name, pk in picks.items():
+        cand = [r for r in recs if r["cand"] >= 0]
+        lp = net.predict_log_seconds([r["features"] for r in cand])
+        pred = {id(r): v for r, v in zip(cand, lp)}
+    for d, rs in by.items():
+        cs = [r for r in rs if r["cand"] >= 0]
+        h = min(cs, key=lambda r: (r["heuristic"], r["cand"]))
+        heur[d] = h
+        if net is not None:
+            m = min(cs, key=lambda r: (pred[id(r)], r["cand"]))
+            if guard > 0 and m["heuristic"] > guard * h["heuristic"]:
+                m = h
+                guarded += 1
+            mlp[d] = m
+    return heur, mlp, guarded
+
+
+def evaluate(recs, net=None, guard=0.0):
+    """Geometric-mean time over DAGs of the network's pick, the estimate's
+    pick, the literal plan and the best candidate (regret = pick / best)."""
+    by = by_dag(recs)
+    heur, mlp, guarded = picks(recs, net, guard)
+    best = {d: min((r for r in rs if r["cand"] >= 0), key=lambda r: r["time"]) for d, rs in by.items()}
+    sel = {"heuristic": heur, "best": best,
+           "literal": {d: next(r for r in rs if r["cand"] == -1) for d, rs in by.items()}}
+    if net is not None:
+        sel["mlp"] = mlp
+    res = {"dags": len(by)}
+    for name, pk in sel.items():
         lt = [math.log(pk[d]["time"]) for d in by]
         res[name + "_geomean_s"] = math.exp(sum(lt) / len(lt))
-        res[name + "_regret"] = math.exp(sum(math.log(pk[d]["time"] / picks["best"][d]["time"]) for d in by) / len(by))
+        res[name + "_regret"] = math.exp(sum(math.log(pk[d]["time"] / best[d]["time"]) for d in by) / len(by))
+    if net is not None:
+        res["mlp_beats_heuristic_dags"] = sum(1 for d in by if mlp[d]["time"] < heur[d]["time"])
+        res["heuristic_beats_mlp_dags"] = sum(1 for d in by if heur[d]["time"] < mlp[d]["time"])
+        res["guarded"] = guarded
     return res
+
+
+def library_pick(nodes, outputs, flags=PLAN_TIER_CHOICE):
+    """The candidate index the library's planner picks with ARMA_PLAN_COST_MLP
+    (the loaded network, or the estimate when none is loaded)."""
+    p = Plan(nodes, outputs, flags=flags | PLAN_COST_MLP)
+    ch = p.info["choice"]
+    return ch["picked"], ch["scorer"]
 
 
 def make_dags(seed, count, lo=16, hi=8192, cap_flops=2e11, max_inputs_bytes=2e9, start=0):

@@ -3,6 +3,7 @@
 // plan's steps on the caller's stream.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <string>
@@ -17,9 +18,20 @@ arma_status plan_features(const arma_plan* p, float* out, int32_t n);
 arma_status plan_heuristic(const arma_plan* p, double* seconds);
 arma_status chain_order_api(int32_t n, const int64_t* dims, int32_t method, int32_t* splits,
                             uint64_t* cost);
+arma_status plan_candidates_api(const arma_expr* e, arma_plan** plans, int32_t capacity, int32_t* count);
+arma_status cost_model_load(const float* params, int32_t F, int32_t H, const float* mean, const float* scale,
+                            double guard);
+void cost_model_clear();
+arma_status cost_model_predict(const arma_plan* p, double* seconds);
 }  // namespace arma
 
 using namespace arma;
+
+namespace {
+std::atomic<uint64_t>& wait_ns_setting();
+}
+
+uint64_t arma::wait_limit_ns() { return wait_ns_setting().load(std::memory_order_relaxed); }
 
 namespace {
 
@@ -42,6 +54,11 @@ const void* cptr(const Bind& b, const Ref& r) {
 void* mptr(const Bind& b, const Ref& r) { return const_cast<void*>(cptr(b, r)); }
 
 thread_local char g_last_cuda[160] = "";
+
+std::atomic<uint64_t>& wait_ns_setting() {
+  static std::atomic<uint64_t> v{2000000000ull};
+  return v;
+}
 
 // records the CUDA error for arma_gpu_last_cuda_error() and maps it
 arma_status cuda_status(cudaError_t e) {
@@ -99,6 +116,7 @@ arma_status run_step(const Step& st, const Bind& b, cudaStream_t s, int* launche
       // the run-time half of the symmetric-product check: two slots bound
       // to the same memory (launch_gemm re-checks every condition)
       a.sym = g.sym == 1 || (g.sym == 2 && a.A == a.B) ? 1 : 0;
+      a.nosplit = g.nosplit;
       return cuda_status(launch_gemm(a, s, launches));
     }
     case ST_DOT: {
@@ -139,6 +157,7 @@ arma_status run_step(const Step& st, const Bind& b, cudaStream_t s, int* launche
       a.status_info = reinterpret_cast<int64_t*>(b.ws + 8);
       a.analyse = v.analyse;
       a.props = reinterpret_cast<int32_t*>(b.ws + kSolveRecordOffset);
+      a.max_ir = v.max_ir;
       return cuda_status(launch_solve(a, s, launches));
     }
   }
@@ -255,6 +274,8 @@ void arma_gpu_plan_free(arma_plan* plan) { delete plan; }
 
 const char* arma_gpu_last_cuda_error(void) { return g_last_cuda; }
 
+uint64_t arma_gpu_set_wait_limit_ns(uint64_t ns) { return wait_ns_setting().exchange(ns); }
+
 const char* arma_gpu_status_string(arma_status s) {
   switch (s) {
     case ARMA_OK: return "ok";
@@ -267,6 +288,7 @@ const char* arma_gpu_status_string(arma_status s) {
     case ARMA_ERR_NOCONVERGE: return "iterative refinement did not converge";
     case ARMA_ERR_CUDA: return "CUDA runtime error";
     case ARMA_ERR_UNSUPPORTED: return "expression not supported";
+    case ARMA_ERR_TIMEOUT: return "a bounded device-side wait ran out";
   }
   return "unknown status";
 }
@@ -282,6 +304,30 @@ arma_status arma_gpu_plan_features(const arma_plan* plan, float* features, int32
 
 arma_status arma_gpu_plan_heuristic_cost(const arma_plan* plan, double* seconds) {
   return plan_heuristic(plan, seconds);
+}
+
+arma_status arma_gpu_plan_candidates(const arma_expr* expr, arma_plan** plans, int32_t capacity,
+                                     int32_t* count) {
+  try {
+    return plan_candidates_api(expr, plans, capacity, count);
+  } catch (...) {
+    return ARMA_ERR_INVALID;
+  }
+}
+
+arma_status arma_gpu_cost_model_load(const float* params, int32_t features, int32_t hidden, const float* mean,
+                                     const float* scale, double guard) {
+  try {
+    return cost_model_load(params, features, hidden, mean, scale, guard);
+  } catch (...) {
+    return ARMA_ERR_INVALID;
+  }
+}
+
+void arma_gpu_cost_model_clear(void) { cost_model_clear(); }
+
+arma_status arma_gpu_cost_model_predict(const arma_plan* plan, double* seconds) {
+  return cost_model_predict(plan, seconds);
 }
 
 arma_status arma_gpu_plan_batched(const arma_expr* exprs, int32_t count, arma_plan** plan) {

@@ -37,6 +37,10 @@ inline Ref ref_input(int64_t slot) { Ref r; r.kind = REF_INPUT; r.idx = slot; re
 inline Ref ref_output(int64_t i) { Ref r; r.kind = REF_OUTPUT; r.idx = i; return r; }
 inline Ref ref_ws(int64_t off) { Ref r; r.kind = REF_WS; r.idx = off; return r; }
 
+// limit of one bounded device wait on another CTA's progress, in ns
+// (arma_gpu_set_wait_limit_ns; 0: give up at the first unset poll)
+uint64_t wait_limit_ns();
+
 inline size_t dtype_size(int dt) { return dt == ARMA_F64 ? 8 : dt == ARMA_F32 ? 4 : 2; }
 
 // --------------------------------------------------------------------------
@@ -154,6 +158,7 @@ struct GemmStep {
   // two input slots of the same shape and layout, decided at evaluation by
   // comparing the bound pointers
   int32_t sym = 0;
+  int32_t nosplit = 0;      // 1: no split-K over CTAs (ARMA_PLAN_NO_SPLITK)
   Ref scratch;              // workspace for operand conversion / split-K partials
   int64_t scratch_bytes = 0;
 };
@@ -173,6 +178,7 @@ struct GemmArgs {
   const int* skip;   // optional: the kernels return at once when *skip != 0
   int32_t sym;       // 1: A == B, lda == ldb, ta != tb, no C or scalings: only the
                      // lower-triangle tiles are computed, the rest is mirrored
+  int32_t nosplit;   // 1: one CTA per output tile over the whole of K (no split-K)
 };
 
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s, int* launches);
@@ -227,6 +233,7 @@ struct SolveStep {
   int32_t tier = ARMA_TIER_LU32_IR64;
   int32_t explicit_inverse = 0;  // literal plan: form inv(A) then multiply
   int32_t analyse = 0;     // run-time analysis of A picks the solver (Sec. III (10))
+  int32_t max_ir = 10;     // refinement step limit (ARMA_PLAN_REFINE_STEPS)
   Ref scratch;
   int64_t scratch_bytes = 0;
 };
@@ -251,6 +258,7 @@ struct SolveArgs {
   int64_t* status_info;
   int32_t analyse;        // 1: analyse A first and dispatch
   int32_t* props;         // the solve record (SP_WORDS int32)
+  int32_t max_ir;         // refinement step limit (1 .. 15)
 };
 int64_t solve_scratch_bytes(int64_t n, int64_t nrhs, int32_t tier, int32_t analyse = 0);
 cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches);

@@ -280,7 +280,7 @@ cudaError_t launch_gemv(const GemmArgs& a, cudaStream_t s, int* launches) {
   }
   cudaError_t e;
   if (g.rsm == 1 || g.k == 0) {
-    g.splits = g.k == 0 ? 1 : gemv_splits(g.rows, g.k);
+    g.splits = (g.k == 0 || a.nosplit) ? 1 : gemv_splits(g.rows, g.k);
     if (g.splits > 1 && (!a.scratch || a.scratch_bytes < (int64_t)g.splits * g.rows * 8)) g.splits = 1;
     g.partials = static_cast<double*>(a.scratch);
     dim3 grid((unsigned)((g.rows + 255) / 256), (unsigned)g.splits);
@@ -483,7 +483,7 @@ cudaError_t launch_gemm(const GemmArgs& a0, cudaStream_t s, int* launches) {
   GemmArgs a = a0;
   a.sym = gemm_sym_valid(a0);   // anything else is a general product
   if (a.tier != ARMA_TIER_F64 && gemm_tc_supported(a)) return launch_gemm_tc(a, s, launches);
-  int splits = simt_splits(a.m, a.n, a.k);
+  int splits = a.nosplit ? 1 : simt_splits(a.m, a.n, a.k);
   if (splits > 1 && (!a.scratch || a.scratch_bytes < (int64_t)splits * a.m * a.n * 8)) splits = 1;
   const int64_t tm = (a.m + BM - 1) / BM, tn = (a.n + BN - 1) / BN;
   dim3 grid((unsigned)(a.sym ? tm * (tm + 1) / 2 : tm), (unsigned)(a.sym ? 1 : tn), (unsigned)splits);

@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   fence_before();
   __syncthreads();
-  if (threadIdx.x == 0 && *abort && p.status) atomicCAS(p.status, 0, (int32_t)ARMA_ERR_CUDA);
+  if (threadIdx.x == 0 && *abort && p.status) atomicCAS(p.status, 0, (int32_t)ARMA_ERR_TIMEOUT);
   if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
@@ -633,7 +633,7 @@ struct Geometry {
 
 // sym: op(B)^T is op(A), so one prepared operand serves both TMA maps; its
 // rows are padded to a multiple of both tile heights
-Geometry geometry(int64_t m, int64_t n, int64_t k, int32_t tier, bool sym = false) {
+Geometry geometry(int64_t m, int64_t n, int64_t k, int32_t tier, bool sym = false, bool nosplit = false) {
   Geometry g;
   g.terms = tier == ARMA_TIER_SPLIT_BF16 ? 6 : 1;
   g.slices = tier == ARMA_TIER_SPLIT_BF16 ? 3 : 1;
@@ -646,7 +646,7 @@ Geometry geometry(int64_t m, int64_t n, int64_t k, int32_t tier, bool sym = fals
   // split K over CTAs only when the output has too few tiles to fill the GPU
   int64_t splits = 1;
   const int64_t tiles = (int64_t)g.tiles_m * g.tiles_n;
-  while (tiles * splits < 148 && kb / (splits * 2) >= 4) splits *= 2;
+  while (!nosplit && tiles * splits < 148 && kb / (splits * 2) >= 4) splits *= 2;
   if (splits > kb) splits = kb > 0 ? kb : 1;
   g.splits = (int32_t)(splits < 1 ? 1 : splits);
   g.kb_per_split = (int32_t)((kb + g.splits - 1) / g.splits);
@@ -694,7 +694,7 @@ bool gemm_tc_supported(const GemmArgs& a) {
   if (a.m < 1 || a.n < 1 || a.k < 1) return false;
   if (a.m > (1ll << 30) || a.n > (1ll << 30) || a.k > (1ll << 30)) return false;
   if (!a.scratch) return false;
-  tc::Geometry g = tc::geometry(a.m, a.n, a.k, a.tier, a.sym != 0);
+  tc::Geometry g = tc::geometry(a.m, a.n, a.k, a.tier, a.sym != 0, a.nosplit != 0);
   return a.scratch_bytes >= g.a_bytes + g.b_bytes + g.p_bytes + 1024;
 }
 
@@ -708,7 +708,7 @@ int64_t gemm_tc_scratch_bytes(int64_t m, int64_t n, int64_t k, int32_t tier) {
 cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   using namespace tc;
   const bool sym = a.sym != 0;
-  Geometry g = geometry(a.m, a.n, a.k, a.tier, sym);
+  Geometry g = geometry(a.m, a.n, a.k, a.tier, sym, a.nosplit != 0);
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(a.scratch) + 255) & ~uintptr_t(255));
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(base);
   __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(base + ((g.a_bytes + 255) / 256) * 256);

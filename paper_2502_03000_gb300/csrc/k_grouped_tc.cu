@@ -20,7 +20,7 @@
 // slower than SIMT for the benchmark's size mix.
 //
 // Waits on the MMA-completion barriers are bounded: on timeout the CTA
-// records ARMA_ERR_CUDA in the status word, waits (bounded) for its issued
+// records ARMA_ERR_TIMEOUT in the status word, waits (bounded) for its issued
 // MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
 
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(GTHREADS, S == 1 ? 2 : 1) grouped_tc_kernel(co
   }
   fence_before();
   __syncthreads();
-  if (threadIdx.x == 0 && *abort && g.status) atomicCAS(g.status, 0, (int32_t)ARMA_ERR_CUDA);
+  if (threadIdx.x == 0 && *abort && g.status) atomicCAS(g.status, 0, (int32_t)ARMA_ERR_TIMEOUT);
   if (warp == 0) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(GTMEM) : "memory");

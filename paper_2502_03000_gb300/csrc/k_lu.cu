@@ -42,10 +42,10 @@ namespace lu {
 constexpr int NB = 64;          // panel width
 constexpr int PT = 256;         // panel threads per CTA
 constexpr int MAX_CTAS = 64;
-constexpr int MAX_IR = 10;
+constexpr int MAX_IR = 10;        // default refinement step limit
+constexpr int MAX_IR_LIMIT = 15;  // largest limit a plan may ask for
 constexpr double IR_TOL = 1e-14;
 constexpr unsigned int SPIN_LIMIT = 1u << 26;
-constexpr uint64_t WAIT_NS = 2000000000ull;     // 2 s bound on one wait
 constexpr int FLAG_STRIDE = 32;                 // substitution flags, one per 128 bytes
 
 struct Ctl {                    // device control block in the solve scratch
@@ -57,7 +57,17 @@ struct Ctl {                    // device control block in the solve scratch
   double nrmA, nrmB, nrmR, nrmX;
 };
 
-__device__ __forceinline__ bool grid_barrier(Ctl* c, unsigned int nblocks, int32_t* status) {
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier in global memory for a cooperative launch.  The wait is
+// bounded by wait_ns (and an iteration count); a wait that runs out, or
+// finds that another CTA already gave up, records ARMA_ERR_TIMEOUT and
+// returns false, and every CTA then leaves its loop.
+__device__ __forceinline__ bool grid_barrier(Ctl* c, unsigned int nblocks, int32_t* status, uint64_t wait_ns) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -71,11 +81,13 @@ __device__ __forceinline__ bool grid_barrier(Ctl* c, unsigned int nblocks, int32
       __threadfence();
       atomicAdd(&c->bar_gen, 1u);
     } else {
+      const uint64_t t0 = global_ns();
       unsigned int i = 0;
       while (*gen == g) {
-        if (++i > SPIN_LIMIT || *(volatile int*)&c->err) {
+        if (wait_ns == 0 || ++i > SPIN_LIMIT || *(volatile int*)&c->err ||
+            ((i & 255u) == 0u && global_ns() - t0 > wait_ns)) {
           atomicExch(&c->err, 1);
-          atomicCAS(status, 0, (int32_t)ARMA_ERR_CUDA);
+          atomicCAS(status, 0, (int32_t)ARMA_ERR_TIMEOUT);
           ok = 0;
           break;
         }
@@ -100,6 +112,7 @@ struct PanelArgs {
   T* drow;                // [2][NB]
   Ctl* ctl;
   int32_t* status; int64_t* info;
+  uint64_t wait_ns;       // bound on one grid-barrier wait
 };
 
 // the CTA's panel rows into shared memory, eight loads in flight per thread
@@ -177,7 +190,7 @@ __global__ void __launch_bounds__(PT) panel_kernel(const __grid_constant__ Panel
       for (int q = threadIdx.x; q < w; q += PT) a.drow[ph * NB + q] = sm[q * R + (d - r0)];
     // 2. all CTAs meet (the barrier orders this block's writes before its
     //    arrival: bar.sync, then a device fence by the arriving thread)
-    if (!grid_barrier(a.ctl, gridDim.x, a.status)) return;
+    if (!grid_barrier(a.ctl, gridDim.x, a.status, a.wait_ns)) return;
     // 3. every CTA picks the same pivot: warp 0 reads the candidates in
     //    parallel and reduces them (ties to the smallest row index)
     if (wid == 0) {
@@ -670,12 +683,6 @@ __device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 // dst[c * NB + r] = src[r + c * ld] for r < rows, c < cols, zero elsewhere
 template <typename T>
 __device__ __forceinline__ void load_block(T* dst, const T* src, int64_t ld, int rows, int cols) {
@@ -867,7 +874,7 @@ __global__ void __launch_bounds__(256) sub_coop_kernel(const T* __restrict__ LU,
                                                        const T* __restrict__ Uinv, int64_t n, T* Y, T* Z,
                                                        int64_t nrhs, unsigned int* flags, Ctl* ctl,
                                                        int32_t* status, const int* skip, int64_t lda,
-                                                       int sweeps) {
+                                                       int sweeps, uint64_t wait_ns) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* Ms = reinterpret_cast<T*>(smraw);   // off-diagonal block, Ms[m * NB + r]
@@ -890,13 +897,14 @@ __global__ void __launch_bounds__(256) sub_coop_kernel(const T* __restrict__ LU,
       int ok = 1;
       const uint64_t t0 = global_ns();
       for (unsigned int it = 0; ld_acquire(f) == 0u; ++it) {
-        __nanosleep(64);
-        if (*(volatile int*)&ctl->err || it > SPIN_LIMIT || ((it & 255u) == 0u && global_ns() - t0 > WAIT_NS)) {
+        if (wait_ns == 0 || *(volatile int*)&ctl->err || it > SPIN_LIMIT ||
+            ((it & 255u) == 255u && global_ns() - t0 > wait_ns)) {
           atomicExch(&ctl->err, 1);
-          atomicCAS(status, 0, (int32_t)ARMA_ERR_CUDA);
+          atomicCAS(status, 0, (int32_t)ARMA_ERR_TIMEOUT);
           ok = 0;
           break;
         }
+        __nanosleep(64);
       }
       s_ok = ok;
     }
@@ -1404,6 +1412,7 @@ cudaError_t factor(const SolveArgs& a, const Layout& L, char* base, cudaStream_t
     pa.cand_data = reinterpret_cast<T*>(base + L.cand_data);
     pa.drow = reinterpret_cast<T*>(base + L.drow);
     pa.ctl = ctl;
+    pa.wait_ns = wait_limit_ns();
     pa.status = a.status_code;
     pa.info = a.status_info;
     cudaError_t e = launch_panel<T>(pa, rows, ctas, s);
@@ -1579,8 +1588,10 @@ cudaError_t substitute(const T* W, const T* Linv, const T* Uinv, int64_t n, T* Y
         nb * gc <= (int64_t)per_sm * device_sm_count()) {
       cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)2 * nb * gc * FLAG_STRIDE * sizeof(unsigned int), s);
       if (e != cudaSuccess) return e;
+      uint64_t wait_ns = wait_limit_ns();
       void* args[] = {(void*)&W, (void*)&Linv, (void*)&Uinv, (void*)&n, (void*)&Y, (void*)&Z, (void*)&nrhs,
-                      (void*)&flags, (void*)&ctl, (void*)&status, (void*)&skip, (void*)&lda, (void*)&sweeps};
+                      (void*)&flags, (void*)&ctl, (void*)&status, (void*)&skip, (void*)&lda, (void*)&sweeps,
+                      (void*)&wait_ns};
       e = cudaLaunchCooperativeKernel((const void*)sub_coop_kernel<T>, dim3((unsigned)nb, (unsigned)gc), dim3(256),
                                       args, smem, s);
       if (e == cudaSuccess) {
@@ -1825,7 +1836,8 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
   sum_partials_kernel<<<1, 256, 0, s>>>(part, 512, sq, 1);
   norms_init_kernel<<<1, 32, 0, s>>>(ctl, sq);
   if (launches) *launches += 6;
-  for (int it = 1; it <= MAX_IR; ++it) {
+  const int max_ir = a.max_ir >= 1 && a.max_ir <= MAX_IR_LIMIT ? a.max_ir : MAX_IR;
+  for (int it = 1; it <= max_ir; ++it) {
     // r = B - A x (FP64)
     GemmArgs g;
     memset(&g, 0, sizeof g);
@@ -1845,7 +1857,7 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
     sum_partials_kernel<<<1, 256, 0, s>>>(part, 512, sq + 2, 0);
     sumsq_any_kernel<<<512, 256, 0, s>>>(X64, ARMA_F64, n, n, nrhs, part);
     sum_partials_kernel<<<1, 256, 0, s>>>(part, 512, sq + 2, 1);
-    ir_check_kernel<<<1, 32, 0, s>>>(ctl, sq + 2, it, a.status_code, a.status_info, it == MAX_IR);
+    ir_check_kernel<<<1, 32, 0, s>>>(ctl, sq + 2, it, a.status_code, a.status_info, it == max_ir);
     // d = (LU)^-1 P r in FP32; x += d
     gather_kernel<float><<<grid_for(n * nrhs), 256, 0, s>>>(R64, n, ARMA_F64, perm, Y, n, nrhs, &ctl->done);
     e = substitute<float>(W, Linv, Uinv, n, Y, Z, nrhs, flags, ctl, a.status_code, &ctl->done, s, launches, 0, 3,

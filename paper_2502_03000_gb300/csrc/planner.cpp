@@ -5,6 +5,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
+#include <mutex>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -794,6 +796,7 @@ void Planner::emit_gemm(int64_t m, int64_t n, int64_t k, const MatOperand& A, co
     if (A.ref.same(B.ref)) g.sym = 1;
     else if (A.ref.kind == REF_INPUT) g.sym = 2;
   }
+  g.nosplit = (e_.flags & ARMA_PLAN_NO_SPLITK) ? 1 : 0;
   g.scratch_bytes = gemm_scratch_bytes(g);
   if (g.scratch_bytes > 0) g.scratch = ref_ws(alloc_ws(g.scratch_bytes));
   Step st;
@@ -808,7 +811,7 @@ void Planner::emit_gemm(int64_t m, int64_t n, int64_t k, const MatOperand& A, co
      << (g.sym == 2 ? " (symmetric if both slots hold the same matrix)" : "") << " op(A)="
      << (A.trans ? "T" : "N") << " op(B)=" << (B.trans ? "T" : "N") << " alpha=" << alpha
      << " beta=" << g.beta << (rs ? " rowscale" : "") << (cs ? " colscale" : "") << " tier="
-     << tier_name(g.tier) << " (" << why << ")";
+     << tier_name(g.tier) << (g.nosplit ? " nosplit" : "") << " (" << why << ")";
   st.note = os.str();
   push_step(std::move(st));
 }
@@ -830,6 +833,8 @@ void Planner::emit_solve(const MatOperand& A, int64_t n, const MatOperand* B, in
   // the run-time analysis that picks a diagonal, band or triangular solver
   // (Sec. III (10)); the literal plan and explicit inverses factor densely
   s.analyse = (!literal_ && !explicit_inverse && !(e_.flags & ARMA_PLAN_NO_SOLVE_ANALYSIS)) ? 1 : 0;
+  const uint32_t ir = (e_.flags & ARMA_PLAN_REFINE_MASK) >> ARMA_PLAN_REFINE_SHIFT;
+  s.max_ir = ir ? (int32_t)ir : 10;
   s.scratch_bytes = solve_scratch_bytes(n, s.nrhs, s.tier, s.analyse);
   s.scratch = ref_ws(alloc_ws(s.scratch_bytes));
   Step st;
@@ -1659,11 +1664,18 @@ arma_status Planner::run() {
 
 }  // namespace
 
-arma_status plan_expression(const arma_expr* e, arma_plan* p, std::string* msg) {
+arma_status plan_single(const arma_expr* e, arma_plan* p) {
   Planner pl(*e, *p);
-  arma_status s = pl.run();
+  return pl.run();
+}
+
+arma_status plan_ranked(const arma_expr* e, arma_plan* p);
+
+arma_status plan_expression(const arma_expr* e, arma_plan* p, std::string* msg) {
   (void)msg;
-  return s;
+  if ((e->flags & (ARMA_PLAN_COST_MLP | ARMA_PLAN_COST_HEURISTIC)) && !(e->flags & ARMA_PLAN_LITERAL))
+    return plan_ranked(e, p);
+  return plan_single(e, p);
 }
 
 // Plan `count` instances of one expression family for the grouped kernel.
@@ -1761,48 +1773,13 @@ arma_status plan_batched(const arma_expr* exprs, int32_t count, arma_plan* p) {
 // ---------------------------------------------------------------------------
 static double l2(double x) { return std::log2(1.0 + (x > 0 ? x : 0)); }
 
-arma_status plan_features(const arma_plan* p, float* out, int32_t n) {
-  if (!p || !out || n < ARMA_PLAN_FEATURES) return ARMA_ERR_INVALID;
-  double f[ARMA_PLAN_FEATURES] = {0};
-  double maxf = 0, maxb = 0, tc_flops = 0, split_flops = 0;
-  for (const Step& st : p->steps) {
-    f[2] += 1;
-    switch (st.kind) {
-      case ST_EW: f[3] += 1; break;
-      case ST_GEMM:
-        if (st.gemm.m == 1 || st.gemm.n == 1) f[5] += 1;
-        else f[4] += 1;
-        if (st.gemm.tier == ARMA_TIER_SPLIT_BF16 || st.gemm.tier == ARMA_TIER_BF16) tc_flops += st.flops;
-        if (st.gemm.tier == ARMA_TIER_SPLIT_BF16) split_flops += st.flops;
-        break;
-      case ST_DOT: f[6] += 1; break;
-      case ST_TRANSPOSE: case ST_DIAGBUILD: f[7] += 1; break;
-      case ST_SOLVE: f[8] += 1; break;
-    }
-    maxf = std::max(maxf, st.flops);
-    maxb = std::max(maxb, st.bytes);
-  }
-  f[0] = l2(p->flops);
-  f[1] = l2(p->bytes);
-  f[9] = l2(maxf);
-  f[10] = l2(maxb);
-  f[11] = l2((double)p->ws_bytes);
-  f[12] = p->flops > 0 ? tc_flops / p->flops : 0;
-  f[13] = (p->flags & ARMA_PLAN_LITERAL) ? 1 : 0;
-  f[14] = p->flops > 0 ? split_flops / p->flops : 0;
-  f[15] = l2(p->bytes > 0 ? p->flops / p->bytes : 0);
-  for (int i = 0; i < ARMA_PLAN_FEATURES; ++i) out[i] = (float)f[i];
-  for (int i = ARMA_PLAN_FEATURES; i < n; ++i) out[i] = 0.f;
-  return ARMA_OK;
-}
-
 // Roofline estimate in the paper's spirit (fewer operations and fewer
 // passes over memory are faster): every step costs a launch plus the larger
-// of its compute time and its memory time on GB300.
-arma_status plan_heuristic(const arma_plan* p, double* seconds) {
-  if (!p || !seconds) return ARMA_ERR_INVALID;
+// of its compute time and its memory time on GB300.  `ew` and `prod`
+// receive the parts spent in elementwise passes and in products.
+static double heuristic_parts(const arma_plan* p, double* ew, double* prod) {
   const double hbm = 6.5e12, launch = 4e-6, dp = 0.3e12, simt = 40e12, bf16 = 1.2e15;
-  double t = 0;
+  double t = 0, te = 0, tp = 0;
   for (const Step& st : p->steps) {
     double c = 0;
     switch (st.kind) {
@@ -1822,9 +1799,335 @@ arma_status plan_heuristic(const arma_plan* p, double* seconds) {
       default:
         break;
     }
-    t += launch + std::max(c, st.bytes / hbm);
+    const double ts = launch + std::max(c, st.bytes / hbm);
+    t += ts;
+    if (st.kind == ST_EW) te += ts;
+    if (st.kind == ST_GEMM) tp += ts;
   }
-  *seconds = t;
+  if (ew) *ew = te;
+  if (prod) *prod = tp;
+  return t;
+}
+
+// kernel launches a step makes (approximately: the products' split-K
+// combine and the solve's refinement depend on run-time data)
+static double step_launches(const Step& st) {
+  switch (st.kind) {
+    case ST_GEMM: {
+      const GemmStep& g = st.gemm;
+      if (g.m == 1 || g.n == 1) return g.nosplit ? 1 : 2;
+      const bool tc = g.tier == ARMA_TIER_SPLIT_BF16 || g.tier == ARMA_TIER_BF16;
+      return (tc ? (g.sym ? 2 : 3) : 1) + (g.nosplit ? 0 : 1) + (g.sym ? 1 : 0);
+    }
+    case ST_DOT: return 2;
+    case ST_SOLVE: return 8 + 4.0 * (double)((st.solve.n + 63) / 64);
+    default: return 1;
+  }
+}
+
+arma_status plan_heuristic(const arma_plan* p, double* seconds) {
+  if (!p || !seconds) return ARMA_ERR_INVALID;
+  *seconds = heuristic_parts(p, nullptr, nullptr);
+  return ARMA_OK;
+}
+
+arma_status plan_features(const arma_plan* p, float* out, int32_t n) {
+  if (!p || !out || n < ARMA_PLAN_FEATURES) return ARMA_ERR_INVALID;
+  double f[ARMA_PLAN_FEATURES] = {0};
+  double maxf = 0, maxb = 0, tc_flops = 0, split_flops = 0, dp_flops = 0, launches = 0, nosplit = 0;
+  double big_flops = -1, big_min_dim = 0, max_out = 0;
+  for (const Step& st : p->steps) {
+    f[2] += 1;
+    launches += step_launches(st);
+    switch (st.kind) {
+      case ST_EW:
+        f[3] += 1;
+        max_out = std::max(max_out, (double)st.ew.m * (double)st.ew.n);
+        break;
+      case ST_GEMM: {
+        const GemmStep& g = st.gemm;
+        if (g.m == 1 || g.n == 1) f[5] += 1;
+        else f[4] += 1;
+        if (g.tier == ARMA_TIER_SPLIT_BF16 || g.tier == ARMA_TIER_BF16) tc_flops += st.flops;
+        if (g.tier == ARMA_TIER_SPLIT_BF16) split_flops += st.flops;
+        if (g.tier == ARMA_TIER_F64) dp_flops += st.flops;
+        if (g.nosplit) nosplit += 1;
+        if (st.flops > big_flops) {
+          big_flops = st.flops;
+          big_min_dim = (double)std::min(g.m, std::min(g.n, g.k));
+        }
+        max_out = std::max(max_out, (double)g.m * (double)g.n);
+        break;
+      }
+      case ST_DOT: f[6] += 1; break;
+      case ST_TRANSPOSE: case ST_DIAGBUILD: f[7] += 1; break;
+      case ST_SOLVE:
+        f[8] += 1;
+        if (st.solve.tier == ARMA_TIER_F64) dp_flops += st.flops;
+        break;
+    }
+    maxf = std::max(maxf, st.flops);
+    maxb = std::max(maxb, st.bytes);
+  }
+  double te = 0, tp = 0;
+  const double h = heuristic_parts(p, &te, &tp);
+  f[0] = l2(p->flops);
+  f[1] = l2(p->bytes);
+  f[9] = l2(maxf);
+  f[10] = l2(maxb);
+  f[11] = l2((double)p->ws_bytes);
+  f[12] = p->flops > 0 ? tc_flops / p->flops : 0;
+  f[13] = (p->flags & ARMA_PLAN_LITERAL) ? 1 : 0;
+  f[14] = p->flops > 0 ? split_flops / p->flops : 0;
+  f[15] = l2(p->bytes > 0 ? p->flops / p->bytes : 0);
+  f[16] = std::log(h > 0 ? h : 1e-9);
+  f[17] = launches;
+  f[18] = p->flops > 0 ? dp_flops / p->flops : 0;
+  f[19] = h > 0 ? te / h : 0;
+  f[20] = h > 0 ? tp / h : 0;
+  f[21] = l2(big_min_dim);
+  f[22] = nosplit;
+  f[23] = l2(max_out);
+  for (int i = 0; i < ARMA_PLAN_FEATURES; ++i) out[i] = (float)f[i];
+  for (int i = ARMA_PLAN_FEATURES; i < n; ++i) out[i] = 0.f;
+  return ARMA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The learned cost model on the host, and the choice among candidate plans
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CostModel {
+  int F = 0, H = 0;
+  std::vector<float> params, mean, scale;
+  double guard = 0;
+};
+
+std::mutex g_model_mu;
+std::shared_ptr<const CostModel> g_model;
+
+std::shared_ptr<const CostModel> loaded_model() {
+  std::lock_guard<std::mutex> lock(g_model_mu);
+  return g_model;
+}
+
+// y = W3 relu(W2 relu(W1 z + b1) + b2) + b3 with the packing and the
+// operation order of the GPU forward kernel (fused multiply-adds in FP32,
+// inputs in index order), so the two agree bit for bit
+float model_forward(const CostModel& M, const float* feat) {
+  const int F = M.F, H = M.H;
+  const float* P = M.params.data();
+  const int64_t W1 = 0, b1 = W1 + (int64_t)H * F, W2 = b1 + H, b2 = W2 + (int64_t)H * H, W3 = b2 + H,
+                b3 = W3 + H;
+  std::vector<float> z(F), h1(H);
+  for (int f = 0; f < F; ++f) z[f] = (feat[f] - M.mean[f]) / M.scale[f];
+  for (int i = 0; i < H; ++i) {
+    float a = P[b1 + i];
+    for (int f = 0; f < F; ++f) a = std::fmaf(P[W1 + (int64_t)i * F + f], z[f], a);
+    h1[i] = a > 0.f ? a : 0.f;
+  }
+  float y = P[b3];
+  for (int i = 0; i < H; ++i) {
+    float a = P[b2 + i];
+    for (int j = 0; j < H; ++j) a = std::fmaf(P[W2 + (int64_t)i * H + j], h1[j], a);
+    y = std::fmaf(P[W3 + i], a > 0.f ? a : 0.f, y);
+  }
+  return y;
+}
+
+double model_seconds(const CostModel& M, const arma_plan* p) {
+  float feat[ARMA_PLAN_FEATURES];
+  plan_features(p, feat, ARMA_PLAN_FEATURES);
+  const double h = heuristic_parts(p, nullptr, nullptr);
+  return h * std::exp((double)model_forward(M, feat));
+}
+
+constexpr uint32_t kChoiceFlags = ARMA_PLAN_COST_MLP | ARMA_PLAN_COST_HEURISTIC | ARMA_PLAN_TIER_CHOICE;
+constexpr uint32_t kVariantFlags = ARMA_PLAN_CHAIN_LEFT | ARMA_PLAN_CHAIN_GREEDY | ARMA_PLAN_NO_FUSE |
+                                   ARMA_PLAN_NO_SPLITK;
+
+struct Variant {
+  uint32_t flags;
+  int32_t tier;
+};
+
+bool all_inputs(const arma_expr& e, int32_t dt) {
+  bool any = false;
+  for (int i = 0; i < e.n_nodes; ++i)
+    if (e.nodes[i].op == ARMA_OP_INPUT) {
+      any = true;
+      if (e.nodes[i].dtype != dt) return false;
+    }
+  return any;
+}
+
+// Precision tiers at least as accurate as the requested one
+// (BF16 < SPLIT_BF16 < LU32_IR64 < F64; NATIVE resolves by element type).
+std::vector<int32_t> admissible_tiers(const arma_expr& e) {
+  const int32_t t = e.tier;
+  std::vector<int32_t> v{t};
+  if (!(e.flags & ARMA_PLAN_TIER_CHOICE)) return v;
+  switch (t) {
+    case ARMA_TIER_BF16: v.push_back(ARMA_TIER_SPLIT_BF16); v.push_back(ARMA_TIER_F64); break;
+    case ARMA_TIER_SPLIT_BF16: case ARMA_TIER_LU32_IR64: v.push_back(ARMA_TIER_F64); break;
+    case ARMA_TIER_NATIVE:
+      if (all_inputs(e, ARMA_BF16)) v.push_back(ARMA_TIER_SPLIT_BF16);
+      v.push_back(ARMA_TIER_F64);
+      break;
+    default: break;
+  }
+  return v;
+}
+
+std::vector<Variant> variants(const arma_expr& e) {
+  const uint32_t base = e.flags & ~(kChoiceFlags | kVariantFlags);
+  if (e.flags & ARMA_PLAN_LITERAL) return {Variant{base, e.tier}};
+  std::vector<Variant> v;
+  const uint32_t chains[3] = {0u, ARMA_PLAN_CHAIN_GREEDY, ARMA_PLAN_CHAIN_LEFT};
+  for (int32_t t : admissible_tiers(e))
+    for (uint32_t c : chains)
+      for (uint32_t fuse : {0u, (uint32_t)ARMA_PLAN_NO_FUSE})
+        for (uint32_t split : {0u, (uint32_t)ARMA_PLAN_NO_SPLITK}) v.push_back(Variant{base | c | fuse | split, t});
+  return v;
+}
+
+// the step list of a plan's decision log: plans with equal step lists
+// launch the same kernels with the same arguments
+std::string step_signature(const arma_plan& p) {
+  const size_t a = p.log.find("\"steps\": [");
+  const size_t b = p.log.rfind("], \"flops\"");
+  std::string sig = (a != std::string::npos && b != std::string::npos && b > a) ? p.log.substr(a, b - a) : p.log;
+  for (const Step& st : p.steps) {
+    if (st.kind == ST_SOLVE) sig += " solve:" + std::to_string(st.solve.tier);
+    if (st.kind == ST_GEMM) sig += " gemm:" + std::to_string(st.gemm.nosplit);
+  }
+  return sig;
+}
+
+const char* variant_name(uint32_t f) {
+  const bool greedy = f & ARMA_PLAN_CHAIN_GREEDY, left = f & ARMA_PLAN_CHAIN_LEFT;
+  const bool nofuse = f & ARMA_PLAN_NO_FUSE, nosplit = f & ARMA_PLAN_NO_SPLITK;
+  static const char* names[3][4] = {{"dp", "dp+nosplit", "dp+unfused", "dp+unfused+nosplit"},
+                                    {"greedy", "greedy+nosplit", "greedy+unfused", "greedy+unfused+nosplit"},
+                                    {"written", "written+nosplit", "written+unfused", "written+unfused+nosplit"}};
+  return names[left ? 2 : greedy ? 1 : 0][(nofuse ? 2 : 0) + (nosplit ? 1 : 0)];
+}
+
+}  // namespace
+
+arma_status plan_single(const arma_expr* e, arma_plan* p);
+
+// Every distinct candidate plan of an expression, in enumeration order.
+static arma_status plan_candidates(const arma_expr* e, std::vector<std::unique_ptr<arma_plan>>& out,
+                                   std::vector<Variant>* used) {
+  out.clear();
+  std::vector<std::string> sigs;
+  arma_status first_err = ARMA_OK;
+  for (const Variant& v : variants(*e)) {
+    arma_expr x = *e;
+    x.flags = v.flags;
+    x.tier = v.tier;
+    std::unique_ptr<arma_plan> p(new arma_plan());
+    arma_status s = plan_single(&x, p.get());
+    if (s != ARMA_OK) {
+      if (first_err == ARMA_OK) first_err = s;
+      continue;
+    }
+    const std::string sig = step_signature(*p);
+    if (std::find(sigs.begin(), sigs.end(), sig) != sigs.end()) continue;
+    sigs.push_back(sig);
+    out.push_back(std::move(p));
+    if (used) used->push_back(v);
+  }
+  return out.empty() ? (first_err != ARMA_OK ? first_err : ARMA_ERR_INVALID) : ARMA_OK;
+}
+
+// Plan the candidates and keep the one the scorer ranks fastest; the
+// decision log records every candidate with its scores.
+arma_status plan_ranked(const arma_expr* e, arma_plan* p) {
+  std::vector<std::unique_ptr<arma_plan>> cands;
+  std::vector<Variant> used;
+  arma_status s = plan_candidates(e, cands, &used);
+  if (s != ARMA_OK) return s;
+  std::shared_ptr<const CostModel> model = (e->flags & ARMA_PLAN_COST_MLP) ? loaded_model() : nullptr;
+  const size_t n = cands.size();
+  std::vector<double> h(n), m(n, 0.0);
+  size_t hb = 0, mb = 0;
+  for (size_t i = 0; i < n; ++i) {
+    h[i] = heuristic_parts(cands[i].get(), nullptr, nullptr);
+    if (h[i] < h[hb]) hb = i;
+    if (model) {
+      m[i] = model_seconds(*model, cands[i].get());
+      if (m[i] < m[mb]) mb = i;
+    }
+  }
+  size_t pick = model ? mb : hb;
+  bool guarded = false;
+  if (model && model->guard > 0 && h[mb] > model->guard * h[hb]) {
+    pick = hb;
+    guarded = true;
+  }
+  std::ostringstream os;
+  os.precision(6);
+  os << ", \"choice\": {\"scorer\": \"" << (model ? "mlp" : "heuristic") << "\", \"picked\": " << pick
+     << ", \"heuristic_pick\": " << hb << ", \"guarded\": " << (guarded ? "true" : "false")
+     << ", \"candidates\": [";
+  for (size_t i = 0; i < n; ++i) {
+    os << (i ? ", " : "") << "{\"variant\": \"" << variant_name(used[i].flags) << "\", \"tier\": \""
+       << tier_name(used[i].tier) << "\", \"heuristic_s\": " << h[i];
+    if (model) os << ", \"predicted_s\": " << m[i];
+    os << "}";
+  }
+  os << "]}";
+  arma_plan& best = *cands[pick];
+  if (!best.log.empty() && best.log.back() == '}') best.log.insert(best.log.size() - 1, os.str());
+  *p = std::move(best);
+  return ARMA_OK;
+}
+
+arma_status plan_candidates_api(const arma_expr* e, arma_plan** plans, int32_t capacity, int32_t* count) {
+  if (!e || !count || capacity < 0 || (capacity > 0 && !plans)) return ARMA_ERR_INVALID;
+  std::vector<std::unique_ptr<arma_plan>> cands;
+  arma_status s = plan_candidates(e, cands, nullptr);
+  if (s != ARMA_OK) return s;
+  *count = (int32_t)cands.size();
+  for (int32_t i = 0; i < capacity; ++i) plans[i] = i < (int32_t)cands.size() ? cands[i].release() : nullptr;
+  return ARMA_OK;
+}
+
+arma_status cost_model_load(const float* params, int32_t F, int32_t H, const float* mean, const float* scale,
+                            double guard) {
+  if (!params || !mean || !scale || F != ARMA_PLAN_FEATURES || H < 1 || H > 128 || guard < 0 ||
+      !std::isfinite(guard))
+    return ARMA_ERR_INVALID;
+  auto M = std::make_shared<CostModel>();
+  M->F = F;
+  M->H = H;
+  const int64_t np = (int64_t)H * F + H + (int64_t)H * H + H + H + 1;
+  M->params.assign(params, params + np);
+  M->mean.assign(mean, mean + F);
+  M->scale.assign(scale, scale + F);
+  for (float x : M->params)
+    if (!std::isfinite(x)) return ARMA_ERR_INVALID;
+  for (int i = 0; i < F; ++i)
+    if (!std::isfinite(M->mean[i]) || !std::isfinite(M->scale[i]) || M->scale[i] == 0.f) return ARMA_ERR_INVALID;
+  M->guard = guard;
+  std::lock_guard<std::mutex> lock(g_model_mu);
+  g_model = std::move(M);
+  return ARMA_OK;
+}
+
+void cost_model_clear() {
+  std::lock_guard<std::mutex> lock(g_model_mu);
+  g_model.reset();
+}
+
+arma_status cost_model_predict(const arma_plan* p, double* seconds) {
+  if (!p || !seconds || p->batched) return ARMA_ERR_INVALID;
+  std::shared_ptr<const CostModel> M = loaded_model();
+  if (!M) return ARMA_ERR_UNSUPPORTED;
+  *seconds = model_seconds(*M, p);
   return ARMA_OK;
 }
 

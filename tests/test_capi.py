@@ -34,7 +34,7 @@ def test_exports_every_declared_symbol():
 
 def test_status_strings():
     L = ag.lib()
-    for code in range(10):
+    for code in range(11):
         assert L.arma_gpu_status_string(code)
 
 

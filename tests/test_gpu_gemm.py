@@ -88,11 +88,11 @@ def test_gemm_repeatable(torch):
     assert torch.equal(a[0], b[0])
 
 
-@pytest.mark.parametrize("tier", ["split_bf16", "bf16"])
+@pytest.mark.parametrize("tier", ["split_bf16", "bf16", "f64"])
 def test_gemm_benchmark_size_sampled(torch, tier):
     """2*trans(A)*B + C at 8192^3 with FP64 inputs, in the launch
-    configuration the benchmark times; sampled entries against the oracle's
-    own increasing-l sums."""
+    configuration the benchmark times (the FP64 tier is the DFMA product);
+    sampled entries against the oracle's own increasing-l sums."""
     n = 8192
     nodes, outs = E.config_products(n, "f64")
     host = [synth.matrix(20250203 + 3, s + 1, n, n, "f64") for s in range(3)]

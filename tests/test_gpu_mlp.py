@@ -67,12 +67,15 @@ def test_adam_matches_oracle(torch):
 
 
 def test_training_fits_a_smooth_function(torch):
-    from paper_2502_03000_gb300.costmodel import CostNet
+    """The library's kernels train the cost network: it learns a smooth
+    function of its inputs (as ln(time) of the features) to well within its
+    initial error."""
+    from paper_2502_03000_gb300.costmodel import CostNet, HEURISTIC_FEATURE
     rng = np.random.default_rng(1)
-    X = rng.normal(0, 1, (512, 16))
-    T = np.sin(X[:, 0]) + 0.5 * X[:, 1] * X[:, 2] + 0.1 * X[:, 3]
+    X = rng.normal(0, 1, (512, ag.N_FEATURES))
+    T = np.sin(X[:, 0]) + 0.5 * X[:, 1] * X[:, 2] + 0.1 * X[:, 3] + X[:, HEURISTIC_FEATURE]
     net = CostNet(seed=3)
     losses = net.fit(X, T, steps=1500, lr=3e-3)
     assert losses[-1] < 0.1 * losses[0]
-    pred = net.predict(X)
+    pred = net.predict_log_seconds(X)
     assert np.mean((pred - T) ** 2) < 0.05

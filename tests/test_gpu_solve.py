@@ -92,19 +92,96 @@ def test_solve_f32_inputs(torch):
     assert oracle.rel_err(X, oracle.solve_literal(A, B)) <= TOL["f32"]
 
 
+_COND = {}
+
+
+def conditioned(symmetric):
+    """The benchmark matrix A = Q1 diag(s) Q2^T (n = 4096, kappa = 1e6) and
+    the oracle's literal Gauss-Jordan inverse of it, computed once."""
+    if symmetric not in _COND:
+        A = synth.conditioned_matrix(20250203 + 3, 4096, 1e6, symmetric=symmetric)
+        _COND[symmetric] = (A, oracle.inv(A))
+    return _COND[symmetric]
+
+
 @pytest.mark.parametrize("symmetric", [True, False])
 def test_solve_conditioned_benchmark_size(torch, symmetric):
     """A = Q1 diag(s) Q2^T, n = 4096, kappa = 1e6, B 4096 x 64 (the benchmark
-    configuration): backward error <= 1e-12, forward error <= 1e-12 * kappa
-    against an independent library solve."""
+    configuration): backward error <= 1e-12, and forward error <= 1e-12 *
+    kappa against the oracle's literal inv(A) * B (Gauss-Jordan inverse, then
+    the triple-loop product)."""
     n, nrhs = 4096, 64
-    A = synth.conditioned_matrix(20250203 + 3, n, 1e6, symmetric=symmetric)
+    A, Ainv = conditioned(symmetric)
     B = synth.matrix(20250203 + 3, 2, n, nrhs, "f64")
     X, (st, info) = solve(torch, A, B, "lu32_ir64")
     assert st == "ok", (st, info)
     assert oracle.backward_error(A, X, B) <= 1e-12
-    Xn = np.linalg.solve(A, B)
-    assert oracle.rel_err(X, Xn) <= 1e-12 * 1e6
+    assert oracle.rel_err(X, oracle.matmul(Ainv, B)) <= 1e-12 * 1e6
+
+
+def test_refinement_step_cap(torch):
+    """ARMA_PLAN_REFINE_STEPS(k) stops the FP64 refinement after k steps: with
+    the number of steps the solve needs it converges (info = that number), one
+    step fewer reports ARMA_ERR_NOCONVERGE with info = the cap."""
+    n, nrhs = 4096, 64
+    A, _ = conditioned(False)
+    B = synth.matrix(20250203 + 3, 2, n, nrhs, "f64")
+    _, (st, need) = solve(torch, A, B, "lu32_ir64")
+    assert st == "ok" and 2 <= need <= 10, (st, need)
+    X, (st, info) = solve(torch, A, B, "lu32_ir64", flags=ag.PLAN_REFINE_STEPS(need))
+    assert (st, info) == ("ok", need)
+    assert oracle.backward_error(A, X, B) <= 1e-12
+    X1, (st, info) = solve(torch, A, B, "lu32_ir64", flags=ag.PLAN_REFINE_STEPS(need - 1))
+    assert (st, info) == ("noconverge", need - 1)
+    _, (st, info) = solve(torch, A, B, "lu32_ir64", flags=ag.PLAN_REFINE_STEPS(1))
+    assert (st, info) == ("noconverge", 1)
+
+
+def test_bf16_tier(torch):
+    """The BF16 tier factors in BF16 (one tensor-core product per trailing
+    update) and refines in FP64.  At kappa = 1e6, kappa * u_bf16 >> 1: the
+    refinement cannot converge and the solve reports ARMA_ERR_NOCONVERGE after
+    its 10 steps.  On a well-conditioned matrix it converges to the FP64
+    backward error."""
+    n, nrhs = 4096, 64
+    A, Ainv = conditioned(False)
+    B = synth.matrix(20250203 + 3, 2, n, nrhs, "f64")
+    X, (st, info) = solve(torch, A, B, "bf16")
+    assert (st, info) == ("noconverge", 10)
+    err = oracle.rel_err(X, oracle.matmul(Ainv, B))
+    print(f"\nbf16 tier, kappa 1e6: forward error {err:.3e}, status {st}")
+    A2 = well_conditioned(31, 1000)
+    B2 = synth.matrix(32, 2, 1000, 16, "f64")
+    X2, (st, info) = solve(torch, A2, B2, "bf16")
+    assert st == "ok" and 1 <= info <= 10, (st, info)
+    assert oracle.backward_error(A2, X2, B2) <= 1e-14
+    assert oracle.rel_err(X2, oracle.solve_literal(A2, B2)) <= 1e-12
+
+
+def test_bounded_wait_runs_out(torch):
+    """Failure detection without a hung GPU: with the wait limit at 0 the
+    cooperative substitution gives up at the first flag it finds unset; the
+    kernels return, the status reads ARMA_ERR_TIMEOUT, and the next
+    evaluation with the default limit, on the same plan and workspace,
+    succeeds."""
+    n, nrhs = 4096, 64
+    A = well_conditioned(41, n)
+    B = synth.matrix(42, 2, n, nrhs, "f64")
+    nodes, outs = E.config_solve(n, nrhs)
+    plan = ag.Plan(nodes, outs, tier="lu32_ir64", flags=ag.PLAN_NO_SOLVE_ANALYSIS)
+    dA, dB = to_dev(A), to_dev(B)
+    old = ag.set_wait_limit_ns(0)
+    try:
+        plan(dA, dB)
+        torch.cuda.synchronize()
+        st, _ = plan.status()
+    finally:
+        ag.set_wait_limit_ns(old)
+    assert st == "timeout"
+    (X,) = plan(dA, dB)
+    torch.cuda.synchronize()
+    assert plan.status()[0] == "ok"
+    assert oracle.backward_error(A, to_host(X), B) <= 1e-14
 
 
 def test_solve_panel_beyond_cluster_memory(torch):
@@ -123,7 +200,7 @@ def test_solve_panel_beyond_cluster_memory(torch):
 def test_refinement_steps_reported(torch):
     """lu32_ir64 reports the refinement steps it took (info) on success."""
     n = 4096
-    A = synth.conditioned_matrix(20250203 + 3, n, 1e6, symmetric=False)
+    A, _ = conditioned(False)
     B = synth.matrix(20250203 + 3, 2, n, 4, "f64")
     X, (st, info) = solve(torch, A, B, "lu32_ir64")
     assert st == "ok" and 1 <= info <= 10, (st, info)
