@@ -139,11 +139,13 @@ typedef enum {
 #define ARMA_PLAN_CHAIN_GREEDY 0x4u  /* the paper's chain rule (smallest adjacent result first)
                                         instead of the exact minimum-cost order */
 #define ARMA_PLAN_COST_MLP     0x8u  /* choose among candidate plans (arma_gpu_plan_candidates)
-                                        the one the learned cost model loaded with
-                                        arma_gpu_cost_model_load predicts fastest; with no
-                                        model loaded, or when the FLOP/byte estimate rates the
-                                        network's pick worse than its own pick by more than
-                                        the model's guard factor, the estimate's pick */
+                                        with the learned cost model loaded by
+                                        arma_gpu_cost_model_load: the network's fastest
+                                        candidate replaces the FLOP/byte estimate's pick when
+                                        the network predicts it faster by the model's margin
+                                        and the estimate does not rate it slower than its own
+                                        pick by more than the model's guard factor; with no
+                                        model loaded, the estimate's pick */
 #define ARMA_PLAN_NO_FUSE      0x10u /* optimised rewrites but no elementwise fusion */
 #define ARMA_PLAN_NO_TENSOR    0x20u /* batched plans: SIMT tiles instead of tensor-core tiles */
 #define ARMA_PLAN_TILE64       0x40u /* batched SIMT tiles: 64 x 64 for every problem */
@@ -280,7 +282,7 @@ const char* arma_gpu_last_cuda_error(void);
  * this library records with its own GPU kernels.  The plan's decision log
  * (arma_gpu_plan_info) lists the candidates, their scores and the pick. ---- */
 
-#define ARMA_PLAN_FEATURES 24
+#define ARMA_PLAN_FEATURES 32
 
 /* Host only: the plan's feature vector; n >= ARMA_PLAN_FEATURES floats.
  *   0 log2(1 + flops)            1 log2(1 + bytes)         2 steps
@@ -294,7 +296,15 @@ const char* arma_gpu_last_cuda_error(void);
  *  19 share of the estimate spent in elementwise passes
  *  20 share of the estimate spent in products
  *  21 log2(1 + smallest dimension of the largest product)
- *  22 products without split-K   23 log2(1 + largest output elements) */
+ *  22 products without split-K   23 log2(1 + largest output elements)
+ *  24 products whose K is split over CTAs (a combine launch each)
+ *  25 log2(1 + elements read with a stride by fused passes)
+ *  26 share of the estimate in FP64 (DFMA) products
+ *  27 useful / padded output of the tensor-core products (1 if none)
+ *  28 log2(1 + work items of the largest product / 152 SMs)
+ *  29 operand preparation passes of the tensor-core products
+ *  30 log2(1 + K of the largest product)
+ *  31 share of the estimate in kernel launches */
 arma_status arma_gpu_plan_features(const arma_plan* plan, float* features, int32_t n);
 
 /* Host only: estimated seconds, summing per step a launch plus the larger
@@ -318,11 +328,13 @@ arma_status arma_gpu_plan_candidates(const arma_expr* expr, arma_plan** plans, i
  * (layout as arma_gpu_mlp_forward) maps the standardised feature vector
  * z_i = (f_i - mean[i]) / scale[i] of a plan to a correction of the
  * FLOP/byte estimate: predicted seconds = estimate * exp(network(z)).
- * features must be ARMA_PLAN_FEATURES; hidden <= 128; guard >= 1 is the
- * factor by which the estimate may rate the network's pick slower than its
- * own before that pick is overruled (0: never overruled). */
+ * features must be ARMA_PLAN_FEATURES; hidden <= 128.  The network's
+ * fastest candidate replaces the estimate's pick only when the network
+ * predicts it at least a fraction `margin` (0 <= margin < 1) faster than the
+ * estimate's pick, and only when the estimate rates it at most `guard`
+ * times slower than its own pick (guard >= 1; 0: no such check). */
 arma_status arma_gpu_cost_model_load(const float* params, int32_t features, int32_t hidden, const float* mean,
-                                     const float* scale, double guard);
+                                     const float* scale, double guard, double margin);
 
 /* Forget the loaded cost model (ARMA_PLAN_COST_MLP then uses the estimate). */
 void arma_gpu_cost_model_clear(void);

@@ -81,7 +81,7 @@ EXPORTS = ["arma_gpu_plan", "arma_gpu_plan_workspace", "arma_gpu_output_info", "
            "arma_gpu_mlp_param_count", "arma_gpu_mlp_workspace", "arma_gpu_mlp_forward", "arma_gpu_mlp_grad",
            "arma_gpu_mlp_adam", "arma_gpu_plan_candidates", "arma_gpu_cost_model_load",
            "arma_gpu_cost_model_clear", "arma_gpu_cost_model_predict"]
-N_FEATURES = 24
+N_FEATURES = 32
 STATIC_SCRATCH_BYTES = 131072
 
 
@@ -116,7 +116,7 @@ def lib() -> ctypes.CDLL:
     L.arma_gpu_plan_features.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
     L.arma_gpu_plan_heuristic_cost.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.arma_gpu_plan_candidates.argtypes = [ctypes.POINTER(Expr), ctypes.POINTER(vp), i32, ctypes.POINTER(i32)]
-    L.arma_gpu_cost_model_load.argtypes = [vp, i32, i32, vp, vp, ctypes.c_double]
+    L.arma_gpu_cost_model_load.argtypes = [vp, i32, i32, vp, vp, ctypes.c_double, ctypes.c_double]
     L.arma_gpu_cost_model_clear.argtypes = []
     L.arma_gpu_cost_model_clear.restype = None
     L.arma_gpu_cost_model_predict.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
@@ -207,7 +207,7 @@ def candidates(nodes, outputs, tier="native", flags=0, capacity=128):
     return [Plan(nodes, outputs, _handle=ctypes.c_void_p(hs[i])) for i in range(min(n.value, capacity))]
 
 
-def load_cost_model(params, mean, scale, hidden, guard=0.0):
+def load_cost_model(params, mean, scale, hidden, guard=0.0, margin=0.0):
     """Give the library a trained cost network (host arrays; see
     arma_gpu_cost_model_load).  ARMA_PLAN_COST_MLP plans consult it."""
     import numpy as np
@@ -215,7 +215,7 @@ def load_cost_model(params, mean, scale, hidden, guard=0.0):
     mu = np.ascontiguousarray(np.asarray(mean, dtype=np.float32))
     sd = np.ascontiguousarray(np.asarray(scale, dtype=np.float32))
     _check(lib().arma_gpu_cost_model_load(p.ctypes.data, len(mu), int(hidden), mu.ctypes.data, sd.ctypes.data,
-                                          float(guard)), "arma_gpu_cost_model_load")
+                                          float(guard), float(margin)), "arma_gpu_cost_model_load")
 
 
 def clear_cost_model():

@@ -41,12 +41,14 @@ def candidate_plans(nodes, outputs, tier="native", flags=PLAN_TIER_CHOICE):
     return out
 
 
-def time_plan(plan, inputs, device="cuda", target_s=1e-3, max_reps=50):
+def time_plan(plan, inputs, device="cuda", target_s=1e-3, max_reps=50, outputs=None, slow_above=None):
     """Mean seconds per evaluation (CUDA events): one warm-up, one timed
     evaluation to size the repetition count, then enough repetitions for
-    about target_s of GPU time (at least 3)."""
+    about target_s of GPU time (at least 3).  A candidate whose single timed
+    evaluation exceeds `slow_above` seconds is clearly not the fastest: its
+    single time is returned without repetitions."""
     import torch
-    outs = plan.alloc_outputs(device)
+    outs = outputs if outputs is not None else plan.alloc_outputs(device)
     plan(*inputs, outputs=outs)
     torch.cuda.synchronize()
     s = torch.cuda.current_stream()
@@ -56,6 +58,8 @@ def time_plan(plan, inputs, device="cuda", target_s=1e-3, max_reps=50):
     e1.record(s)
     torch.cuda.synchronize()
     t1 = max(e0.elapsed_time(e1) * 1e-3, 1e-7)
+    if slow_above is not None and t1 > slow_above:
+        return t1
     reps = int(min(max_reps, max(3, target_s / t1)))
     e0.record(s)
     for _ in range(reps):
@@ -72,21 +76,29 @@ def dag_inputs(nodes, dtype, g, device="cuda"):
     return [(torch.rand((c, r), device=device, generator=g) * 2 - 1).to(td).t() for r, c in input_shapes(nodes)]
 
 
-def collect(dags, device="cuda", gen_seed=7, flags=PLAN_TIER_CHOICE, target_s=1e-3):
+def collect(dags, device="cuda", gen_seed=7, flags=PLAN_TIER_CHOICE, target_s=1e-3, slow_factor=4.0):
     """Time every candidate (and the literal plan) of every DAG.  dags: list
-    of (nodes, outputs, dtype).  Returns a list of records."""
+    of (nodes, outputs, dtype).  All candidates of a DAG share its inputs and
+    outputs; a candidate more than slow_factor times slower than the fastest
+    one so far is timed once.  Returns a list of records."""
     import torch
     g = torch.Generator(device=device)
     g.manual_seed(gen_seed)
     recs = []
     for di, (nodes, outs, dt) in enumerate(dags):
         ins = dag_inputs(nodes, dt, g, device)
-        for ci, p in candidate_plans(nodes, outs, flags=flags):
-            t = time_plan(p, ins, device, target_s=target_s)
+        cands = candidate_plans(nodes, outs, flags=flags)
+        out_bufs = cands[0][1].alloc_outputs(device)
+        best = None
+        for ci, p in cands:
+            t = time_plan(p, ins, device, target_s=target_s, outputs=out_bufs,
+                          slow_above=None if best is None else slow_factor * best)
+            if ci >= 0:
+                best = t if best is None else min(best, t)
             recs.append({"dag": di, "cand": ci, "features": p.features(), "time": t,
                          "heuristic": p.heuristic_cost(), "kernels": len(p.info["steps"])})
             p._ws.clear()
-        del ins
+        del ins, out_bufs
     return recs
 
 
@@ -123,9 +135,11 @@ class CostNet:
         self.sd = np.ones(features)
 
     def _x(self, X):
+        """Standardised features, in FP32 exactly as the library's planner
+        forms them: (f - mean) / scale with FP32 operands."""
         import torch
-        Z = (np.asarray(X, dtype=np.float64) - self.mu) / self.sd
-        return torch.tensor(Z, dtype=torch.float32, device=self.device).contiguous()
+        Z = (np.asarray(X, dtype=np.float32) - self.mu.astype(np.float32)) / self.sd.astype(np.float32)
+        return torch.tensor(Z.astype(np.float32), dtype=torch.float32, device=self.device).contiguous()
 
     def correction(self, X):
         """network(standardised X): the predicted ln(time / estimate)."""
@@ -142,11 +156,20 @@ class CostNet:
         X = np.asarray(X, dtype=np.float64)
         return X[:, HEURISTIC_FEATURE] + self.correction(X)
 
-    def fit(self, X, log_t, steps=2000, lr=3e-3):
-        """Full-batch Adam on the mean squared error of ln(time / estimate)."""
+    def fit(self, X, log_t, steps=2000, lr=3e-3, groups=None):
+        """Full-batch Adam on the mean squared error of ln(time / estimate).
+        With `groups` (the expression each record belongs to), the target is
+        centred per expression: only differences between the candidates of
+        one expression decide a pick, so an expression-wide offset is not
+        learned."""
         import torch
         X = np.asarray(X, dtype=np.float64)
         target = np.asarray(log_t, dtype=np.float64) - X[:, HEURISTIC_FEATURE]
+        if groups is not None:
+            groups = np.asarray(groups)
+            for gid in np.unique(groups):
+                sel = groups == gid
+                target[sel] -= target[sel].mean()
         self.mu = X.mean(axis=0)
         self.sd = X.std(axis=0)
         self.sd[self.sd < 1e-6] = 1.0
@@ -178,9 +201,9 @@ class CostNet:
     def host_params(self):
         return self.params.detach().float().cpu().numpy()
 
-    def to_library(self, guard=0.0):
+    def to_library(self, guard=0.0, margin=0.0):
         """Load this network into the library's planner (ARMA_PLAN_COST_MLP)."""
-        load_cost_model(self.host_params(), self.mu, self.sd, self.H, guard)
+        load_cost_model(self.host_params(), self.mu, self.sd, self.H, guard, margin)
 
     def save(self, path):
         with open(path, "w") as f:
@@ -206,11 +229,12 @@ def by_dag(recs):
     return by
 
 
-def picks(recs, net=None, guard=0.0):
+def picks(recs, net=None, guard=0.0, margin=0.0):
     """Per DAG, the candidate the estimate picks and (with a network) the one
-    the network picks under the library's rule: the smallest predicted time,
-    overruled by the estimate's pick when the estimate rates it more than
-    `guard` times slower.  Only the library's candidates are eligible."""
+    the library's rule picks: the network's fastest candidate replaces the
+    estimate's pick when the network predicts it at least `margin` faster and
+    the estimate rates it at most `guard` times slower than its own pick.
+    Only the library's candidates are eligible."""
     by = by_dag(recs)
     heur, mlp, guarded = {}, {}, 0
     pred = {}
@@ -224,18 +248,21 @@ def picks(recs, net=None, guard=0.0):
         heur[d] = h
         if net is not None:
             m = min(cs, key=lambda r: (pred[id(r)], r["cand"]))
-            if guard > 0 and m["heuristic"] > guard * h["heuristic"]:
-                m = h
-                guarded += 1
-            mlp[d] = m
+            pick = h
+            if m is not h and pred[id(m)] < math.log(1.0 - margin) + pred[id(h)]:
+                if guard > 0 and m["heuristic"] > guard * h["heuristic"]:
+                    guarded += 1
+                else:
+                    pick = m
+            mlp[d] = pick
     return heur, mlp, guarded
 
 
-def evaluate(recs, net=None, guard=0.0):
+def evaluate(recs, net=None, guard=0.0, margin=0.0):
     """Geometric-mean time over DAGs of the network's pick, the estimate's
     pick, the literal plan and the best candidate (regret = pick / best)."""
     by = by_dag(recs)
-    heur, mlp, guarded = picks(recs, net, guard)
+    heur, mlp, guarded = picks(recs, net, guard, margin)
     best = {d: min((r for r in rs if r["cand"] >= 0), key=lambda r: r["time"]) for d, rs in by.items()}
     sel = {"heuristic": heur, "best": best,
            "literal": {d: next(r for r in rs if r["cand"] == -1) for d, rs in by.items()}}
@@ -249,6 +276,7 @@ def evaluate(recs, net=None, guard=0.0):
     if net is not None:
         res["mlp_beats_heuristic_dags"] = sum(1 for d in by if mlp[d]["time"] < heur[d]["time"])
         res["heuristic_beats_mlp_dags"] = sum(1 for d in by if heur[d]["time"] < mlp[d]["time"])
+        res["overrides"] = sum(1 for d in by if mlp[d] is not heur[d])
         res["guarded"] = guarded
     return res
 

@@ -20,7 +20,7 @@ arma_status chain_order_api(int32_t n, const int64_t* dims, int32_t method, int3
                             uint64_t* cost);
 arma_status plan_candidates_api(const arma_expr* e, arma_plan** plans, int32_t capacity, int32_t* count);
 arma_status cost_model_load(const float* params, int32_t F, int32_t H, const float* mean, const float* scale,
-                            double guard);
+                            double guard, double margin);
 void cost_model_clear();
 arma_status cost_model_predict(const arma_plan* p, double* seconds);
 }  // namespace arma
@@ -316,9 +316,9 @@ arma_status arma_gpu_plan_candidates(const arma_expr* expr, arma_plan** plans, i
 }
 
 arma_status arma_gpu_cost_model_load(const float* params, int32_t features, int32_t hidden, const float* mean,
-                                     const float* scale, double guard) {
+                                     const float* scale, double guard, double margin) {
   try {
-    return cost_model_load(params, features, hidden, mean, scale, guard);
+    return cost_model_load(params, features, hidden, mean, scale, guard, margin);
   } catch (...) {
     return ARMA_ERR_INVALID;
   }
@@ -349,7 +349,8 @@ arma_status arma_gpu_plan_batched(const arma_expr* exprs, int32_t count, arma_pl
   return ARMA_OK;
 }
 
-static size_t table_layout(const BatchedInfo& b, size_t* probs_off, size_t* prob_off, size_t* code_off) {
+static size_t table_layout(const BatchedInfo& b, size_t* probs_off, size_t* prob_off, size_t* code_off,
+                           size_t* order_off) {
   size_t off = 0;
   *probs_off = off;
   off += (size_t)b.count * sizeof(GroupedProblem);
@@ -359,13 +360,16 @@ static size_t table_layout(const BatchedInfo& b, size_t* probs_off, size_t* prob
   off = (off + 255) / 256 * 256;
   *code_off = off;
   off += (size_t)b.tiles * sizeof(uint32_t);
+  off = (off + 255) / 256 * 256;
+  *order_off = off;
+  off += (size_t)b.tiles * sizeof(int32_t);
   return (off + 255) / 256 * 256;
 }
 
 arma_status arma_gpu_batched_table_bytes(const arma_plan* plan, size_t* bytes) {
   if (!plan || !bytes || !plan->batched) return ARMA_ERR_INVALID;
-  size_t a, b, c;
-  *bytes = table_layout(plan->bi, &a, &b, &c);
+  size_t a, b, c, d;
+  *bytes = table_layout(plan->bi, &a, &b, &c, &d);
   return ARMA_OK;
 }
 
@@ -373,8 +377,8 @@ arma_status arma_gpu_batched_table_fill(const arma_plan* plan, const void* const
                                         void* const* out_ptrs, void* host_table) {
   if (!plan || !plan->batched || !in_ptrs || !out_ptrs || !host_table) return ARMA_ERR_INVALID;
   const BatchedInfo& b = plan->bi;
-  size_t po, pr, pc;
-  table_layout(b, &po, &pr, &pc);
+  size_t po, pr, pc, pd;
+  table_layout(b, &po, &pr, &pc, &pd);
   char* base = static_cast<char*>(host_table);
   GroupedProblem* probs = reinterpret_cast<GroupedProblem*>(base + po);
   for (int32_t i = 0; i < b.count; ++i) {
@@ -394,6 +398,7 @@ arma_status arma_gpu_batched_table_fill(const arma_plan* plan, const void* const
   }
   std::memcpy(base + pr, b.tile_prob.data(), b.tile_prob.size() * sizeof(int32_t));
   std::memcpy(base + pc, b.tile_code.data(), b.tile_code.size() * sizeof(uint32_t));
+  std::memcpy(base + pd, b.tile_order.data(), b.tile_order.size() * sizeof(int32_t));
   return ARMA_OK;
 }
 
@@ -402,8 +407,8 @@ arma_status arma_gpu_eval_batched(const arma_plan* plan, const void* device_tabl
   if (!plan || !plan->batched || !device_table) return ARMA_ERR_INVALID;
   if (!workspace || workspace_bytes < plan->ws_bytes) return ARMA_ERR_WORKSPACE;
   const BatchedInfo& b = plan->bi;
-  size_t po, pr, pc;
-  table_layout(b, &po, &pr, &pc);
+  size_t po, pr, pc, pd;
+  table_layout(b, &po, &pr, &pc, &pd);
   const char* base = static_cast<const char*>(device_table);
   GroupedArgs g;
   std::memset(&g, 0, sizeof g);
@@ -411,6 +416,8 @@ arma_status arma_gpu_eval_batched(const arma_plan* plan, const void* device_tabl
   g.probs = reinterpret_cast<const GroupedProblem*>(base + po);
   g.tile_prob = reinterpret_cast<const int32_t*>(base + pr);
   g.tile_code = reinterpret_cast<const uint32_t*>(base + pc);
+  g.tile_order = reinterpret_cast<const int32_t*>(base + pd);
+  g.next_tile = reinterpret_cast<unsigned int*>(static_cast<char*>(workspace) + 16);
   g.ta = b.ta; g.tb = b.tb; g.abdt = b.abdt; g.cdt = b.cdt; g.ddt = b.ddt;
   g.alpha = b.alpha; g.beta = b.beta;
   g.alpha_f = (float)b.alpha; g.beta_f = (float)b.beta;
@@ -418,7 +425,8 @@ arma_status arma_gpu_eval_batched(const arma_plan* plan, const void* device_tabl
   g.tc = b.tc;
   g.status = static_cast<int32_t*>(workspace);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaError_t e = cudaMemsetAsync(workspace, 0, 16, s)) return cuda_status(e);
+  // status, info and the tile counter start at zero
+  if (cudaError_t e = cudaMemsetAsync(workspace, 0, 32, s)) return cuda_status(e);
   int launches = 0;
   return cuda_status(launch_grouped(g, s, &launches));
 }

@@ -22,6 +22,8 @@ struct GroupedArgs {
   const GroupedProblem* probs;
   const int32_t* tile_prob;     // tile -> problem
   const uint32_t* tile_code;    // tile -> (tm << 16) | tn
+  const int32_t* tile_order;    // processing order: tiles by decreasing work
+  unsigned int* next_tile;      // work counter (zeroed before the launch)
   int32_t ta, tb, abdt, cdt, ddt, pad;
   double alpha, beta;
   float alpha_f, beta_f;

@@ -184,6 +184,8 @@ struct GemmArgs {
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s, int* launches);
 int64_t gemm_scratch_bytes(const GemmStep& g);
 int64_t gemm_tc_scratch_bytes(int64_t m, int64_t n, int64_t k, int32_t tier);
+int gemm_tc_splits(int64_t m, int64_t n, int64_t k, int32_t tier, bool sym, bool nosplit);
+void gemm_step_shape(const GemmStep& g, int* splits, double* tiles);
 int64_t gemm_simt_scratch_bytes(int64_t m, int64_t n, int64_t k);
 
 // trace(op(A) * op(B)) -> FP64 scalar.  op(A) is m x k, op(B) is k x n;
@@ -323,6 +325,7 @@ struct BatchedInfo {
   std::vector<int64_t> first_tile;
   std::vector<int32_t> tile_prob;
   std::vector<uint32_t> tile_code;
+  std::vector<int32_t> tile_order;   // tiles by decreasing work (longest first)
   int64_t tiles = 0;
 };
 

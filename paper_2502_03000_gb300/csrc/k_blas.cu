@@ -457,6 +457,31 @@ int64_t gemm_simt_scratch_bytes(int64_t m, int64_t n, int64_t k) {
   return s > 1 ? (int64_t)s * m * n * 8 : 0;
 }
 
+// K splits (CTAs per output tile) the product kernels will use for a step,
+// and the tiles of its output; host only (152 SMs assumed for the
+// matrix-vector rule, whose launch reads the device)
+void gemm_step_shape(const GemmStep& g, int* splits, double* tiles) {
+  if (g.m == 1 || g.n == 1) {
+    const int64_t rows = g.n == 1 ? g.m : g.n;
+    const int64_t blocks = (rows + 255) / 256;
+    int64_t s = (152 * 4 + blocks - 1) / blocks;
+    const int64_t smax = (g.k + 31) / 32;
+    if (s > smax) s = smax;
+    if (s > 64) s = 64;
+    *splits = g.nosplit || s < 1 ? 1 : (int)s;
+    *tiles = (double)blocks;
+    return;
+  }
+  const bool tc = g.tier == ARMA_TIER_SPLIT_BF16 || g.tier == ARMA_TIER_BF16;
+  if (tc) {
+    *splits = gemm_tc_splits(g.m, g.n, g.k, g.tier, g.sym != 0, g.nosplit != 0);
+    *tiles = (double)((g.m + 127) / 128) * (double)((g.n + 255) / 256);
+  } else {
+    *splits = g.nosplit ? 1 : simt_splits(g.m, g.n, g.k);
+    *tiles = (double)((g.m + BM - 1) / BM) * (double)((g.n + BN - 1) / BN);
+  }
+}
+
 int64_t gemm_scratch_bytes(const GemmStep& g) {
   if (g.n == 1 || g.m == 1) {
     int64_t rows = g.n == 1 ? g.m : g.n;

@@ -687,6 +687,30 @@ bool make_map(CUtensorMap* map, const void* base, int64_t kp, int64_t rows, int 
   return r == CUDA_SUCCESS;
 }
 
+// A map straight over the caller's BF16 operand when it is already K-major
+// (element (row r, k) at base[k + r * ld]): no preparation pass.  Rows past
+// `rows` and K past `kdim` are outside the tensor and read as zero.
+bool make_map_direct(CUtensorMap* map, const void* base, int64_t kdim, int64_t rows, int64_t ld, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kdim, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// a BF16 operand the kernel can read in place: one slice (BF16 tier), K-major,
+// 16-byte aligned base and a leading dimension of a multiple of 8 elements
+// (TMA strides are multiples of 16 bytes)
+bool direct_operand(const void* X, int32_t dt, int64_t ld, bool kmajor, int32_t slices) {
+  return slices == 1 && dt == ARMA_BF16 && kmajor && ld % 8 == 0 && ld >= 8 &&
+         (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
+}
+
 }  // namespace tc
 
 bool gemm_tc_supported(const GemmArgs& a) {
@@ -696,6 +720,11 @@ bool gemm_tc_supported(const GemmArgs& a) {
   if (!a.scratch) return false;
   tc::Geometry g = tc::geometry(a.m, a.n, a.k, a.tier, a.sym != 0, a.nosplit != 0);
   return a.scratch_bytes >= g.a_bytes + g.b_bytes + g.p_bytes + 1024;
+}
+
+int gemm_tc_splits(int64_t m, int64_t n, int64_t k, int32_t tier, bool sym, bool nosplit) {
+  if (m < 1 || n < 1 || k < 1) return 1;
+  return tc::geometry(m, n, k, tier, sym, nosplit).splits;
 }
 
 int64_t gemm_tc_scratch_bytes(int64_t m, int64_t n, int64_t k, int32_t tier) {
@@ -730,20 +759,33 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
       prep_kernel<<<gg, 256, 0, s>>>(pp);
     }
   };
-  prep(pa);
+  // BF16 operands that are already K-major (op(A) = A^T, op(B) = B) feed
+  // TMA in place: no preparation pass over them
+  const bool directA = !sym && direct_operand(a.A, a.adt, a.lda, a.ta != 0, g.slices);
+  const bool directB = !sym && direct_operand(a.B, a.bdt, a.ldb, a.tb == 0, g.slices);
+  if (!directA) {
+    prep(pa);
+    if (launches) ++*launches;
+  }
   // op(B)^T (n x k): element (j, l) = op(B)(l, j) = tb ? B[j + l*ldb] : B[l + j*ldb]
   PrepArgs pb;
   pb.X = a.B; pb.ldx = a.ldb; pb.xdt = a.bdt; pb.trans = a.tb ? 0 : 1;
   pb.R = a.n; pb.K = a.k; pb.rpad = g.npad; pb.kp = g.kp; pb.slices = g.slices; pb.out = Bs;
   pb.skip = a.skip;
-  if (!sym) prep(pb);
-  if (launches) *launches += sym ? 1 : 2;
+  if (!sym && !directB) {
+    prep(pb);
+    if (launches) ++*launches;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
 
   CUtensorMap mapA, mapB;
-  if (!make_map(&mapA, As, g.kp, (int64_t)g.slices * g.mpad, BM)) return cudaErrorInvalidValue;
-  if (!make_map(&mapB, sym ? As : Bs, g.kp, (int64_t)g.slices * g.npad, BN)) return cudaErrorInvalidValue;
+  if (directA ? !make_map_direct(&mapA, a.A, a.k, a.m, a.lda, BM)
+              : !make_map(&mapA, As, g.kp, (int64_t)g.slices * g.mpad, BM))
+    return cudaErrorInvalidValue;
+  if (directB ? !make_map_direct(&mapB, a.B, a.k, a.n, a.ldb, BN)
+              : !make_map(&mapB, sym ? As : Bs, g.kp, (int64_t)g.slices * g.npad, BN))
+    return cudaErrorInvalidValue;
 
   Params p;
   memset(&p, 0, sizeof p);

@@ -3,8 +3,9 @@
 //     D_g = alpha * op(A_g) * op(B_g) + beta * C_g,   t_g = trace(op(A_g) op(B_g))
 // (the batched form of the paper's folded product and diagonal-only trace,
 // Sec. II xGEMM paragraph, Sec. III (5)).  A host-built tile list spans all
-// problems; each CTA walks it with a fixed stride, so there is one launch for
-// the whole batch (plus a small trace finalisation) instead of one or more
+// problems, ordered by decreasing work; the CTAs of one resident wave take
+// tiles from a shared counter (longest first), so there is one launch for the
+// whole batch (plus a small trace finalisation) instead of one or more
 // launches per problem, and the pair of launches can be captured in a CUDA
 // graph.  Per problem the tile shape is 32 x 32 or 64 x 64, picked on the host
 // by a padded-work cost model.  Accumulation is FP32 (BF16 inputs are
@@ -139,12 +140,23 @@ __device__ __forceinline__ void grouped_tile(const GroupedProblem& pb, int tm, i
   }
 }
 
+// the next tile of the work list for this CTA (thread 0 takes it from the
+// shared counter; the list is ordered longest first)
+__device__ __forceinline__ int64_t next_tile(const GroupedArgs& g, int* slot) {
+  __syncthreads();
+  if (threadIdx.x == 0) *slot = (int)atomicAdd(g.next_tile, 1u);
+  __syncthreads();
+  return *slot;
+}
+
 template <typename AT>
 __global__ void __launch_bounds__(256, 2) grouped_kernel(const __grid_constant__ GroupedArgs g) {
   __shared__ __align__(16) float As[GBK][SROW];
   __shared__ __align__(16) float Bs[GBK][SROW];
+  __shared__ int s_next;
   const GroupedProblem* probs = g.probs;
-  for (int64_t t = blockIdx.x; t < g.tiles; t += gridDim.x) {
+  for (int64_t i = next_tile(g, &s_next); i < g.tiles; i = next_tile(g, &s_next)) {
+    const int64_t t = g.tile_order[i];
     const uint32_t code = g.tile_code[t];
     const int32_t p = g.tile_prob[t];
     const GroupedProblem pb = probs[p];
@@ -179,8 +191,10 @@ cudaError_t launch_grouped(const GroupedArgs& g, cudaStream_t s, int* launches) 
     if (launches) ++*launches;
     return cudaGetLastError();
   }
+  // one resident wave (2 CTAs per SM by the register bound); CTAs take
+  // tiles from the shared counter until the list is done
   const int sms = device_sm_count();
-  int64_t grid = (int64_t)sms * 8;
+  int64_t grid = (int64_t)sms * 2;
   if (grid > g.tiles) grid = g.tiles;
   if (g.abdt == ARMA_BF16) grouped_kernel<__nv_bfloat16><<<(unsigned)grid, 256, 0, s>>>(g);
   else if (g.abdt == ARMA_F32) grouped_kernel<float><<<(unsigned)grid, 256, 0, s>>>(g);

@@ -4,7 +4,8 @@
 // Sec. III (5)), for thousands of problems of uneven sizes in one persistent
 // launch.
 //
-// Each CTA walks the host-built list of 128 x 128 output tiles.  Per K block
+// The CTAs (three per SM) take 128 x 128 output tiles from a shared counter
+// over the host-built list, longest first.  Per K block
 // of 64 every thread loads its share of the two operand tiles from global
 // memory (both operands K-contiguous: op(A) = A^T, op(B) = B), converts them
 // to BF16 and stores them in the 128-byte-swizzled K-major layout that the
@@ -67,6 +68,20 @@ __device__ __forceinline__ void tile_load(TileRegs<__nv_bfloat16>& t, const __nv
   const int l = (int)l0 + 2 * lane;
   const unsigned short* p = reinterpret_cast<const unsigned short*>(X) + (row0 + warp) * ld + l;
   const int nr = (int)(rows - row0), kk = (int)k, step = 8 * (int)ld;
+  // an even leading dimension and an aligned base make every pair a 4-byte
+  // aligned word (l is even): one load per pair instead of two
+  const bool words = ((ld & 1) == 0) && ((reinterpret_cast<uintptr_t>(X) & 3u) == 0);
+  if (words) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i, p += step) {
+      const int r = warp + 8 * i;
+      uint32_t w = 0u;
+      if (r < nr && l + 1 < kk) w = *reinterpret_cast<const uint32_t*>(p);
+      else if (r < nr && l < kk) w = p[0];
+      t.v[i] = w;
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 16; ++i, p += step) {
     const int r = warp + 8 * i;
@@ -82,9 +97,10 @@ __device__ __forceinline__ void tile_store(const TileRegs<__nv_bfloat16>& t, uns
   for (int i = 0; i < 16; ++i) *reinterpret_cast<uint32_t*>(dst + sw_off(warp + 8 * i, 2 * lane)) = t.v[i];
 }
 
-// 2 CTAs per SM (64 KiB of stages each, <= 128 registers)
+constexpr int GCTAS = 3;   // CTAs per SM: 3 x 64 KiB of stages, 3 x 128 TMEM columns
+
 template <typename AT, int S>
-__global__ void __launch_bounds__(GTHREADS, S == 1 ? 2 : 1) grouped_tc_kernel(const __grid_constant__ GroupedArgs g) {
+__global__ void __launch_bounds__(GTHREADS, S == 1 ? GCTAS : 1) grouped_tc_kernel(const __grid_constant__ GroupedArgs g) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -114,7 +130,11 @@ __global__ void __launch_bounds__(GTHREADS, S == 1 ? 2 : 1) grouped_tc_kernel(co
   int64_t issued = 0;   // K blocks issued by this CTA: stage = issued & 1
   bool ok = true;
   TileRegs<AT> ra, rb;
-  for (int64_t t = blockIdx.x; t < g.tiles && ok; t += gridDim.x) {
+  __shared__ int s_next;
+  if (threadIdx.x == 0) s_next = (int)atomicAdd(g.next_tile, 1u);
+  __syncthreads();
+  for (int64_t i = s_next; i < g.tiles && ok;) {
+    const int64_t t = g.tile_order[i];
     const uint32_t code = g.tile_code[t];
     const GroupedProblem pb = g.probs[g.tile_prob[t]];
     const int tm = (int)(code >> 16), tn = (int)(code & 0xFFFFu);
@@ -206,24 +226,24 @@ __global__ void __launch_bounds__(GTHREADS, S == 1 ? 2 : 1) grouped_tc_kernel(co
         for (int j = 0; j < 16; ++j) v[j] = 0.f;
       }
       if (!row_ok) continue;
-      float cv[16];
+      // C is read as each D element is formed (few live registers: three
+      // CTAs share the SM's register file); the storage type is uniform
       if (has_c && g.cdt == ARMA_F32) {
         const float* Cr = static_cast<const float*>(pb.C) + row + (j0 + 64 * h + c0) * pb.ldc;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) cv[j] = c0 + j < ncol ? Cr[j * ldc] : 0.f;
-      } else if (has_c) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          cv[j] = c0 + j < ncol ? load_as<float>(pb.C, row + (j0 + 64 * h + c0 + j) * pb.ldc, g.cdt) : 0.f;
+        for (int j = 0; j < 16; ++j) {
+          if (c0 + j >= ncol) continue;
+          if (c0 + j == diag) dsum += (double)v[j];
+          Dr[(c0 + j) * ldd] = fmaf(g.beta_f, Cr[j * ldc], g.alpha_f * v[j]);
+        }
       } else {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) cv[j] = 0.f;
-      }
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        if (c0 + j >= ncol) continue;
-        if (c0 + j == diag) dsum += (double)v[j];
-        Dr[(c0 + j) * ldd] = fmaf(g.beta_f, cv[j], g.alpha_f * v[j]);
+        for (int j = 0; j < 16; ++j) {
+          if (c0 + j >= ncol) continue;
+          if (c0 + j == diag) dsum += (double)v[j];
+          const float cv = has_c ? load_as<float>(pb.C, row + (j0 + 64 * h + c0 + j) * pb.ldc, g.cdt) : 0.f;
+          Dr[(c0 + j) * ldd] = fmaf(g.beta_f, cv, g.alpha_f * v[j]);
+        }
       }
     }
     if (g.trace_partials && tm == tn) {   // diagonal tile: its share of the trace
@@ -231,10 +251,13 @@ __global__ void __launch_bounds__(GTHREADS, S == 1 ? 2 : 1) grouped_tc_kernel(co
       block_sum2(dsum, qq);
       if (threadIdx.x == 0) g.trace_partials[t] = dsum;
     }
-    // TMEM reads finish before the next tile's MMAs overwrite the accumulator
+    // TMEM reads finish before the next tile's MMAs overwrite the accumulator;
+    // the next tile comes from the shared counter (longest first)
     fence_before();
+    if (threadIdx.x == 0) s_next = (int)atomicAdd(g.next_tile, 1u);
     __syncthreads();
     fence_after();
+    i = s_next;
   }
   // every issued MMA completes before TMEM is released
   if (issued > 0 && threadIdx.x == 0) {
@@ -266,12 +289,10 @@ cudaError_t launch_tc(const GroupedArgs& g, cudaStream_t s, int* launches) {
     if (e != cudaSuccess) return e;
     attr[dev].store(true, std::memory_order_release);
   }
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grouped_tc_kernel<AT, S>, GTHREADS, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  if (per_sm > 4) per_sm = 4;   // TMEM: 4 x 128 columns per SM
-  int64_t grid = (int64_t)device_sm_count() * per_sm;
+  // one wave of GCTAS CTAs per SM (the register bound of the launch and
+  // the shared-memory carveout allow it; TMEM holds 4 x 128 columns); the
+  // CTAs take tiles from the shared counter
+  int64_t grid = (int64_t)device_sm_count() * (S == 1 ? GCTAS : 1);
   if (grid > g.tiles) grid = g.tiles;
   grouped_tc_kernel<AT, S><<<(unsigned)grid, GTHREADS, smem, s>>>(g);
   if (launches) ++*launches;

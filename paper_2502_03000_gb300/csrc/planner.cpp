@@ -1754,6 +1754,21 @@ arma_status plan_batched(const arma_expr* exprs, int32_t count, arma_plan* p) {
     b.tiles += ntm * ntn;
     p->flops += 2.0 * (double)g.m * (double)g.n * (double)g.k;
   }
+  // CTAs take tiles from a shared counter, longest first (the longest-
+  // processing-time rule): a tile's work is its area times the problem's K
+  {
+    std::vector<double> work((size_t)b.tiles);
+    for (int64_t t = 0; t < b.tiles; ++t) {
+      const int32_t i = b.tile_prob[(size_t)t];
+      const double T = (double)b.tile[(size_t)i];
+      work[(size_t)t] = T * T * (double)std::max<int64_t>(b.k[(size_t)i], 1);
+    }
+    b.tile_order.resize((size_t)b.tiles);
+    for (int64_t t = 0; t < b.tiles; ++t) b.tile_order[(size_t)t] = (int32_t)t;
+    std::stable_sort(b.tile_order.begin(), b.tile_order.end(),
+                     [&](int32_t x, int32_t y) { return work[(size_t)x] > work[(size_t)y]; });
+  }
+  if (b.tiles > INT32_MAX) return ARMA_ERR_UNSUPPORTED;
   p->batched = true;
   p->ws_bytes = kHeaderBytes + (size_t)((b.tiles * 8 + 255) / 256 * 256);
   std::ostringstream os;
@@ -1869,6 +1884,35 @@ arma_status plan_features(const arma_plan* p, float* out, int32_t n) {
     maxf = std::max(maxf, st.flops);
     maxb = std::max(maxb, st.bytes);
   }
+  // what the estimate leaves out: split-K combine launches, strided reads
+  // in fused passes, FP64 (DFMA) product time, tile padding and parallelism
+  // of the tensor-core products, operand preparation passes
+  double combines = 0, strided = 0, dp_time = 0, tc_useful = 0, tc_padded = 0, big_tiles = 0, big_k = 0,
+         preps = 0, big_f = -1;
+  for (const Step& st : p->steps) {
+    if (st.kind == ST_EW) {
+      for (int k = 0; k < st.ew.nin; ++k)
+        if (st.ew.in[k].rs != 1 || st.ew.in[k].flags) strided += (double)st.ew.m * (double)st.ew.n;
+    } else if (st.kind == ST_GEMM) {
+      const GemmStep& g = st.gemm;
+      int splits = 1;
+      double tiles = 0;
+      gemm_step_shape(g, &splits, &tiles);
+      if (splits > 1) combines += 1;
+      const bool tc = g.tier == ARMA_TIER_SPLIT_BF16 || g.tier == ARMA_TIER_BF16;
+      if (g.tier == ARMA_TIER_F64 && g.m > 1 && g.n > 1) dp_time += st.flops / 0.3e12;
+      if (tc && g.m > 1 && g.n > 1) {
+        tc_useful += (double)g.m * (double)g.n;
+        tc_padded += (double)((g.m + 127) / 128 * 128) * (double)((g.n + 255) / 256 * 256);
+        preps += (g.A.dtype == ARMA_BF16 && g.A.trans ? 0 : 1) + (g.B.dtype == ARMA_BF16 && !g.B.trans ? 0 : 1);
+      }
+      if (st.flops > big_f) {
+        big_f = st.flops;
+        big_tiles = tiles * splits;
+        big_k = (double)g.k;
+      }
+    }
+  }
   double te = 0, tp = 0;
   const double h = heuristic_parts(p, &te, &tp);
   f[0] = l2(p->flops);
@@ -1888,6 +1932,14 @@ arma_status plan_features(const arma_plan* p, float* out, int32_t n) {
   f[21] = l2(big_min_dim);
   f[22] = nosplit;
   f[23] = l2(max_out);
+  f[24] = combines;
+  f[25] = l2(strided);
+  f[26] = h > 0 ? dp_time / h : 0;
+  f[27] = tc_padded > 0 ? tc_useful / tc_padded : 1;
+  f[28] = l2(big_tiles / 152.0);
+  f[29] = preps;
+  f[30] = l2(big_k);
+  f[31] = h > 0 ? launches * 4e-6 / h : 0;
   for (int i = 0; i < ARMA_PLAN_FEATURES; ++i) out[i] = (float)f[i];
   for (int i = ARMA_PLAN_FEATURES; i < n; ++i) out[i] = 0.f;
   return ARMA_OK;
@@ -1901,7 +1953,8 @@ namespace {
 struct CostModel {
   int F = 0, H = 0;
   std::vector<float> params, mean, scale;
-  double guard = 0;
+  double guard = 0;    // the estimate overrules picks it rates > guard x its own pick
+  double margin = 0;   // the network must predict its pick this much faster than the estimate's
 };
 
 std::mutex g_model_mu;
@@ -2062,11 +2115,14 @@ arma_status plan_ranked(const arma_expr* e, arma_plan* p) {
       if (m[i] < m[mb]) mb = i;
     }
   }
-  size_t pick = model ? mb : hb;
+  // the network's pick replaces the estimate's only when the network
+  // predicts it at least `margin` faster, and the estimate does not rate it
+  // more than `guard` times slower than its own pick
+  size_t pick = hb;
   bool guarded = false;
-  if (model && model->guard > 0 && h[mb] > model->guard * h[hb]) {
-    pick = hb;
-    guarded = true;
+  if (model && mb != hb && m[mb] < (1.0 - model->margin) * m[hb]) {
+    if (model->guard > 0 && h[mb] > model->guard * h[hb]) guarded = true;
+    else pick = mb;
   }
   std::ostringstream os;
   os.precision(6);
@@ -2097,9 +2153,9 @@ arma_status plan_candidates_api(const arma_expr* e, arma_plan** plans, int32_t c
 }
 
 arma_status cost_model_load(const float* params, int32_t F, int32_t H, const float* mean, const float* scale,
-                            double guard) {
+                            double guard, double margin) {
   if (!params || !mean || !scale || F != ARMA_PLAN_FEATURES || H < 1 || H > 128 || guard < 0 ||
-      !std::isfinite(guard))
+      !std::isfinite(guard) || !(margin >= 0 && margin < 1))
     return ARMA_ERR_INVALID;
   auto M = std::make_shared<CostModel>();
   M->F = F;
@@ -2113,6 +2169,7 @@ arma_status cost_model_load(const float* params, int32_t F, int32_t H, const flo
   for (int i = 0; i < F; ++i)
     if (!std::isfinite(M->mean[i]) || !std::isfinite(M->scale[i]) || M->scale[i] == 0.f) return ARMA_ERR_INVALID;
   M->guard = guard;
+  M->margin = margin;
   std::lock_guard<std::mutex> lock(g_model_mu);
   g_model = std::move(M);
   return ARMA_OK;
