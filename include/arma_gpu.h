@@ -129,7 +129,15 @@ typedef enum {
   ARMA_TIER_SPLIT_BF16 = 2,  /* operands split into 3 BF16 terms, 6 tensor-core products
                                 with FP32 accumulation (about FP32 accuracy) */
   ARMA_TIER_BF16 = 3,        /* operands rounded to BF16, one tensor-core product, FP32 accumulate */
-  ARMA_TIER_LU32_IR64 = 4    /* solves: FP32-accurate LU on tensor cores, FP64 iterative refinement */
+  ARMA_TIER_LU32_IR64 = 4,   /* solves: FP32-accurate LU on tensor cores, FP64 iterative refinement */
+  ARMA_TIER_F64_SLICED = 5   /* products: FP64-accurate from exact BF16 slices on the tensor cores
+                                (FP64 operands scaled per row / column, cut into 8 integer
+                                slices of 7 bits, the 36 slice products of weight >= 2^-63
+                                accumulated exactly in K chunks of 1024 and combined in FP64;
+                                the error-free splitting of Ozaki et al. 2012).  Needs finite
+                                FP64 operands whose row and column maxima multiply within FP64
+                                range; other operands take the FP64 (DFMA) product.  Solves:
+                                as LU32_IR64 */
 } arma_tier;
 
 /* Plan flags. */
@@ -162,11 +170,16 @@ typedef enum {
                                          (arma_gpu_plan_heuristic_cost) */
 #define ARMA_PLAN_TIER_CHOICE  0x800u /* with a COST flag: candidates also take every
                                          precision tier at least as accurate as the requested
-                                         one (BF16 < SPLIT_BF16 < LU32_IR64 < F64; NATIVE may
-                                         move to F64, and to SPLIT_BF16 when all inputs are
-                                         BF16) */
+                                         one (BF16 < SPLIT_BF16 < LU32_IR64 < F64 = F64_SLICED;
+                                         NATIVE may move to F64 or F64_SLICED, and to
+                                         SPLIT_BF16 when all inputs are BF16) */
 #define ARMA_PLAN_NO_SPLITK    0x1000u /* products without split-K: one CTA per output tile
                                          over the whole reduction dimension */
+#define ARMA_PLAN_DFMA_RESIDUAL 0x2000u /* iterative refinement forms r = B - A X with the
+                                         FP64 (DFMA) product; by default systems of n >= 1024
+                                         with >= 8 right-hand sides use the sliced FP64
+                                         product of tier ARMA_TIER_F64_SLICED, A sliced once
+                                         per solve */
 /* Step limit of the FP64 iterative refinement of mixed-precision solves
  * (tiers LU32_IR64 and BF16; Sec. I and Sec. III (9): inv(A)*b as a
  * solve).  ARMA_PLAN_REFINE_STEPS(k), 1 <= k <= 15, stops after k steps; 0

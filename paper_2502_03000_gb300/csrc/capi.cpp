@@ -158,6 +158,7 @@ arma_status run_step(const Step& st, const Bind& b, cudaStream_t s, int* launche
       a.analyse = v.analyse;
       a.props = reinterpret_cast<int32_t*>(b.ws + kSolveRecordOffset);
       a.max_ir = v.max_ir;
+      a.dfma_residual = v.dfma_residual;
       return cuda_status(launch_solve(a, s, launches));
     }
   }

@@ -179,6 +179,8 @@ struct GemmArgs {
   int32_t sym;       // 1: A == B, lda == ldb, ta != tb, no C or scalings: only the
                      // lower-triangle tiles are computed, the rest is mirrored
   int32_t nosplit;   // 1: one CTA per output tile over the whole of K (no split-K)
+  int32_t reuse_a;   // F64_SLICED: op(A)'s slices are already in scratch (an earlier call
+                     // with the same A and scratch)
 };
 
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s, int* launches);
@@ -187,6 +189,10 @@ int64_t gemm_tc_scratch_bytes(int64_t m, int64_t n, int64_t k, int32_t tier);
 int gemm_tc_splits(int64_t m, int64_t n, int64_t k, int32_t tier, bool sym, bool nosplit);
 void gemm_step_shape(const GemmStep& g, int* splits, double* tiles);
 int64_t gemm_simt_scratch_bytes(int64_t m, int64_t n, int64_t k);
+// FP64-accurate products from exact BF16 slices (tier ARMA_TIER_F64_SLICED)
+int64_t gemm_ozaki_scratch_bytes(int64_t m, int64_t n, int64_t k);
+bool gemm_ozaki_supported(const GemmArgs& a);
+cudaError_t launch_gemm_ozaki(const GemmArgs& a, cudaStream_t s, int* launches);
 
 // trace(op(A) * op(B)) -> FP64 scalar.  op(A) is m x k, op(B) is k x n;
 // the sum runs over i < min(m, n), l < k.
@@ -236,6 +242,7 @@ struct SolveStep {
   int32_t explicit_inverse = 0;  // literal plan: form inv(A) then multiply
   int32_t analyse = 0;     // run-time analysis of A picks the solver (Sec. III (10))
   int32_t max_ir = 10;     // refinement step limit (ARMA_PLAN_REFINE_STEPS)
+  int32_t dfma_residual = 0;   // 1: the refinement residual by the DFMA product always
   Ref scratch;
   int64_t scratch_bytes = 0;
 };
@@ -261,8 +268,10 @@ struct SolveArgs {
   int32_t analyse;        // 1: analyse A first and dispatch
   int32_t* props;         // the solve record (SP_WORDS int32)
   int32_t max_ir;         // refinement step limit (1 .. 15)
+  int32_t dfma_residual;  // 1: the refinement residual by the DFMA product always
 };
-int64_t solve_scratch_bytes(int64_t n, int64_t nrhs, int32_t tier, int32_t analyse = 0);
+int64_t solve_scratch_bytes(int64_t n, int64_t nrhs, int32_t tier, int32_t analyse = 0,
+                            int32_t dfma_residual = 0);
 cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches);
 
 struct BandArgs {

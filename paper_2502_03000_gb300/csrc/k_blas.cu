@@ -489,7 +489,12 @@ int64_t gemm_scratch_bytes(const GemmStep& g) {
   }
   const int64_t tc = gemm_tc_scratch_bytes(g.m, g.n, g.k, g.tier);
   const int64_t simt = gemm_simt_scratch_bytes(g.m, g.n, g.k);
-  return tc > simt ? tc : simt;
+  int64_t b = tc > simt ? tc : simt;
+  if (g.tier == ARMA_TIER_F64_SLICED) {
+    const int64_t oz = gemm_ozaki_scratch_bytes(g.m, g.n, g.k);
+    if (oz > b) b = oz;
+  }
+  return b;
 }
 
 // sym 1: a symmetric product (no beta*C), mirrored; sym 2: only the lower
@@ -507,6 +512,7 @@ cudaError_t launch_gemm(const GemmArgs& a0, cudaStream_t s, int* launches) {
   if (a0.n == 1 || a0.m == 1) return launch_gemv(a0, s, launches);
   GemmArgs a = a0;
   a.sym = gemm_sym_valid(a0);   // anything else is a general product
+  if (a.tier == ARMA_TIER_F64_SLICED && gemm_ozaki_supported(a)) return launch_gemm_ozaki(a, s, launches);
   if (a.tier != ARMA_TIER_F64 && gemm_tc_supported(a)) return launch_gemm_tc(a, s, launches);
   int splits = a.nosplit ? 1 : simt_splits(a.m, a.n, a.k);
   if (splits > 1 && (!a.scratch || a.scratch_bytes < (int64_t)splits * a.m * a.n * 8)) splits = 1;

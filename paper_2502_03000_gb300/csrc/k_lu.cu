@@ -1255,7 +1255,13 @@ struct Layout {
   bool refine;
 };
 
-Layout layout(int64_t n, int64_t nrhs, int32_t tier, int32_t analyse = 0) {
+// the refinement residual r = B - A X by the sliced FP64 product (A sliced
+// once per solve) rather than DFMA: large systems with several right-hand sides
+bool sliced_residual(int64_t n, int64_t nrhs, int32_t dfma_residual) {
+  return !dfma_residual && n >= 1024 && nrhs >= 8;
+}
+
+Layout layout(int64_t n, int64_t nrhs, int32_t tier, int32_t analyse = 0, int32_t dfma_residual = 0) {
   Layout L;
   L.f64 = tier == ARMA_TIER_F64;
   L.refine = tier == ARMA_TIER_LU32_IR64 || tier == ARMA_TIER_BF16;
@@ -1280,7 +1286,11 @@ Layout layout(int64_t n, int64_t nrhs, int32_t tier, int32_t analyse = 0) {
     if (gb < sb) gb = sb;
   }
   if (L.refine) {
-    const int64_t rb = gemm_simt_scratch_bytes(n, nrhs, n);   // FP64 residual
+    int64_t rb = gemm_simt_scratch_bytes(n, nrhs, n);   // FP64 residual
+    if (sliced_residual(n, nrhs, dfma_residual)) {
+      const int64_t ob = gemm_ozaki_scratch_bytes(n, nrhs, n);
+      if (rb < ob) rb = ob;
+    }
     if (gb < rb) gb = rb;
   }
   L.gemm_bytes = gb;
@@ -1736,15 +1746,15 @@ bool solve_structured(const SolveArgs& a, const Layout& L, char* base, Ctl* ctl,
 
 }  // namespace lu
 
-int64_t solve_scratch_bytes(int64_t n, int64_t nrhs, int32_t tier, int32_t analyse) {
-  return lu::layout(n, nrhs, tier, analyse).total;
+int64_t solve_scratch_bytes(int64_t n, int64_t nrhs, int32_t tier, int32_t analyse, int32_t dfma_residual) {
+  return lu::layout(n, nrhs, tier, analyse, dfma_residual).total;
 }
 
 cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
   using namespace lu;
   const int64_t n = a.n, nrhs = a.nrhs;
   if (n == 0 || nrhs == 0) return cudaSuccess;
-  Layout L = layout(n, nrhs, a.tier, a.analyse);
+  Layout L = layout(n, nrhs, a.tier, a.analyse, a.dfma_residual);
   if (a.scratch_bytes < L.total) return cudaErrorInvalidValue;
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(a.scratch) + 255) & ~uintptr_t(255));
   Ctl* ctl = reinterpret_cast<Ctl*>(base + L.ctl);
@@ -1837,6 +1847,8 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
   norms_init_kernel<<<1, 32, 0, s>>>(ctl, sq);
   if (launches) *launches += 6;
   const int max_ir = a.max_ir >= 1 && a.max_ir <= MAX_IR_LIMIT ? a.max_ir : MAX_IR;
+  const bool resid_sliced = sliced_residual(n, nrhs, a.dfma_residual) && a.adt == ARMA_F64 &&
+                            a.A != nullptr;
   for (int it = 1; it <= max_ir; ++it) {
     // r = B - A x (FP64)
     GemmArgs g;
@@ -1847,7 +1859,10 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
     g.C = a.B; g.ldc = a.ldb; g.cdt = a.bdt;
     g.D = R64; g.ldd = n; g.ddt = ARMA_F64;
     g.alpha = -1.0; g.beta = 1.0;
-    g.tier = ARMA_TIER_F64;
+    // FP64-accurate either way: the sliced product on the tensor cores, with
+    // A's slices made by the first step and reused, or DFMA
+    g.tier = resid_sliced ? ARMA_TIER_F64_SLICED : ARMA_TIER_F64;
+    g.reuse_a = resid_sliced && it > 1 ? 1 : 0;
     g.scratch = base + L.gemm; g.scratch_bytes = L.gemm_bytes;
     g.status = a.status_code;
     g.skip = &ctl->done;

@@ -156,6 +156,7 @@ const char* op_name(int op) {
   return (op >= 0 && op <= ARMA_OP_SOLVE) ? names[op] : "?";
 }
 const char* tier_name(int t) {
+  if (t == ARMA_TIER_F64_SLICED) return "f64_sliced";
   static const char* names[] = {"native", "f64", "split_bf16", "bf16", "lu32_ir64"};
   return (t >= 0 && t <= 4) ? names[t] : "?";
 }
@@ -225,12 +226,15 @@ class Planner {
     int t = e_.tier;
     if (t == ARMA_TIER_NATIVE || t == ARMA_TIER_LU32_IR64)
       return dt == ARMA_F64 ? ARMA_TIER_F64 : dt == ARMA_F32 ? ARMA_TIER_SPLIT_BF16 : ARMA_TIER_BF16;
+    // the sliced product takes FP64 operands; FP64 accuracy on others is DFMA
+    if (t == ARMA_TIER_F64_SLICED && dt != ARMA_F64) return ARMA_TIER_F64;
     return t;
   }
   int32_t solve_tier(int32_t dt) const {
     int t = e_.tier;
     if (t == ARMA_TIER_NATIVE)
       return dt == ARMA_F64 ? ARMA_TIER_LU32_IR64 : dt == ARMA_F32 ? ARMA_TIER_SPLIT_BF16 : ARMA_TIER_BF16;
+    if (t == ARMA_TIER_F64_SLICED) return ARMA_TIER_LU32_IR64;
     return t;
   }
 
@@ -287,7 +291,7 @@ arma_status Planner::validate() {
     return fail(ARMA_ERR_INVALID, "n_nodes must be 1..256 with a node array");
   if (e_.n_outputs < 1 || e_.n_outputs > 32 || !e_.outputs)
     return fail(ARMA_ERR_INVALID, "n_outputs must be 1..32 with an output array");
-  if (e_.tier < 0 || e_.tier > ARMA_TIER_LU32_IR64) return fail(ARMA_ERR_INVALID, "bad tier");
+  if (e_.tier < 0 || e_.tier > ARMA_TIER_F64_SLICED) return fail(ARMA_ERR_INVALID, "bad tier");
   int n = e_.n_nodes;
   nd_.assign(e_.nodes, e_.nodes + n);
   info_.assign(n, NInfo());
@@ -827,7 +831,7 @@ void Planner::emit_solve(const MatOperand& A, int64_t n, const MatOperand* B, in
   // an explicit inverse has no right-hand side to refine against: FP64 data
   // is factored in FP64 (the paper's naive GETRF + GETRI in the data's type)
   if (explicit_inverse && dt == ARMA_F64 &&
-      (e_.tier == ARMA_TIER_NATIVE || e_.tier == ARMA_TIER_LU32_IR64))
+      (e_.tier == ARMA_TIER_NATIVE || e_.tier == ARMA_TIER_LU32_IR64 || e_.tier == ARMA_TIER_F64_SLICED))
     s.tier = ARMA_TIER_F64;
   s.explicit_inverse = explicit_inverse ? 1 : 0;
   // the run-time analysis that picks a diagonal, band or triangular solver
@@ -835,7 +839,8 @@ void Planner::emit_solve(const MatOperand& A, int64_t n, const MatOperand* B, in
   s.analyse = (!literal_ && !explicit_inverse && !(e_.flags & ARMA_PLAN_NO_SOLVE_ANALYSIS)) ? 1 : 0;
   const uint32_t ir = (e_.flags & ARMA_PLAN_REFINE_MASK) >> ARMA_PLAN_REFINE_SHIFT;
   s.max_ir = ir ? (int32_t)ir : 10;
-  s.scratch_bytes = solve_scratch_bytes(n, s.nrhs, s.tier, s.analyse);
+  s.dfma_residual = (e_.flags & ARMA_PLAN_DFMA_RESIDUAL) ? 1 : 0;
+  s.scratch_bytes = solve_scratch_bytes(n, s.nrhs, s.tier, s.analyse, s.dfma_residual);
   s.scratch = ref_ws(alloc_ws(s.scratch_bytes));
   Step st;
   st.kind = ST_SOLVE;
@@ -1806,6 +1811,7 @@ static double heuristic_parts(const arma_plan* p, double* ew, double* prod) {
         else if (st.gemm.tier == ARMA_TIER_SPLIT_BF16) c = 6 * st.flops / bf16 + 2e-6;
         else if (st.gemm.tier == ARMA_TIER_BF16) c = st.flops / bf16 + 2e-6;
         else if (st.gemm.tier == ARMA_TIER_F64) c = st.flops / dp;
+        else if (st.gemm.tier == ARMA_TIER_F64_SLICED) c = 36 * st.flops / bf16 + 8e-6 + st.bytes * 3 / hbm;
         else c = st.flops / simt;
         break;
       case ST_SOLVE:
@@ -2022,11 +2028,17 @@ std::vector<int32_t> admissible_tiers(const arma_expr& e) {
   std::vector<int32_t> v{t};
   if (!(e.flags & ARMA_PLAN_TIER_CHOICE)) return v;
   switch (t) {
-    case ARMA_TIER_BF16: v.push_back(ARMA_TIER_SPLIT_BF16); v.push_back(ARMA_TIER_F64); break;
-    case ARMA_TIER_SPLIT_BF16: case ARMA_TIER_LU32_IR64: v.push_back(ARMA_TIER_F64); break;
+    case ARMA_TIER_BF16:
+      v.push_back(ARMA_TIER_SPLIT_BF16); v.push_back(ARMA_TIER_F64); v.push_back(ARMA_TIER_F64_SLICED);
+      break;
+    case ARMA_TIER_SPLIT_BF16: case ARMA_TIER_LU32_IR64:
+      v.push_back(ARMA_TIER_F64); v.push_back(ARMA_TIER_F64_SLICED);
+      break;
+    case ARMA_TIER_F64: v.push_back(ARMA_TIER_F64_SLICED); break;
     case ARMA_TIER_NATIVE:
       if (all_inputs(e, ARMA_BF16)) v.push_back(ARMA_TIER_SPLIT_BF16);
       v.push_back(ARMA_TIER_F64);
+      v.push_back(ARMA_TIER_F64_SLICED);
       break;
     default: break;
   }

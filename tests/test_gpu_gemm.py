@@ -136,3 +136,86 @@ def test_gemm_benchmark_size_sampled(torch, tier):
     got = D[torch.as_tensor(ii), torch.as_tensor(jj)].double().cpu().numpy()
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert err <= TOL[tier], err
+
+
+# ---- FP64 products from exact BF16 slices (tier f64_sliced) ----
+
+@pytest.mark.parametrize("ta,tb", [(1, 0), (0, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("mnk", [(129, 300, 77), (257, 513, 2100), (64, 1000, 1024), (300, 2, 129), (2, 2, 1)])
+def test_sliced_f64_folded(torch, ta, tb, mnk):
+    """every transpose combination, ragged tiles, K across several 1024-chunks
+    and split-K, alpha / beta*C / diagonal scalings: FP64 accuracy"""
+    m, n, k = mnk
+    nodes, outs, shapes = product_case(m, n, k, ta, tb, "f64", extra=True)
+    got, ref = run_case(torch, nodes, outs, shapes, "f64", "f64_sliced", seed=m + n + 3 * k)
+    check(got, ref, TOL["f64"], f"{mnk} {ta}{tb} f64_sliced")
+
+
+def test_sliced_f64_exact_on_integers(torch):
+    """integer operands (|x| < 2^20): every slice product and every FP64 sum
+    is exact, so the result equals the integer product bit for bit"""
+    rng = np.random.default_rng(5)
+    m, n, k = 300, 200, 3000
+    A = rng.integers(-(1 << 20) + 1, 1 << 20, size=(k, m)).astype(np.float64)
+    B = rng.integers(-(1 << 20) + 1, 1 << 20, size=(k, n)).astype(np.float64)
+    g = E.Graph()
+    a, b = g.input(0, k, m), g.input(1, k, n)
+    nodes, outs = g.build(a.t() * b)
+    (D,) = ag.Plan(nodes, outs, tier="f64_sliced")(to_dev(A), to_dev(B))
+    torch.cuda.synchronize()
+    ref = A.T.astype(object) @ B.astype(object)       # exact integers
+    got = to_host(D)
+    assert np.array_equal(got, np.asarray(ref, dtype=np.float64))
+
+
+def test_sliced_f64_scaling_and_specials(torch):
+    """rows and columns scaled over 2^+-300 (each scaled by its own maximum),
+    a zero row, a zero column; a NaN in a row of A makes that output row NaN
+    and nothing else"""
+    m, n, k = 150, 140, 700
+    A = synth.matrix(91, 1, k, m, "f64") * (2.0 ** np.linspace(-300, 300, m))[None, :]
+    B = synth.matrix(91, 2, k, n, "f64") * (2.0 ** np.linspace(200, -200, n))[None, :]
+    A[:, 7] = 0.0
+    B[:, 11] = 0.0
+    g = E.Graph()
+    a, b = g.input(0, k, m), g.input(1, k, n)
+    nodes, outs = g.build(a.t() * b)
+    plan = ag.Plan(nodes, outs, tier="f64_sliced")
+    (D,) = plan(to_dev(A), to_dev(B))
+    torch.cuda.synchronize()
+    ref = oracle.matmul(np.asfortranarray(A.T), B)
+    got = to_host(D)
+    # relative to each entry's own scale 2^(e_i + f_j): row-column scaled error
+    scale = np.abs(A).max(axis=0)[:, None] * np.abs(B).max(axis=0)[None, :] * k
+    scale[scale == 0] = 1.0
+    assert np.max(np.abs(got - ref) / scale) <= 1e-14
+    assert np.all(got[7, :] == 0.0) and np.all(got[:, 11] == 0.0)
+    A2 = A.copy()
+    A2[3, 20] = np.nan
+    (D2,) = plan(to_dev(A2), to_dev(B))
+    torch.cuda.synchronize()
+    got2 = to_host(D2)
+    assert np.all(np.isnan(got2[20, :]))
+    mask = np.ones(m, bool)
+    mask[20] = False
+    assert np.array_equal(got2[mask], got[mask])
+
+
+def test_sliced_f64_benchmark_size_sampled(torch):
+    """2*trans(A)*B + C at 8192^3 with tier f64_sliced, in the benchmark's
+    launch configuration; sampled entries against the oracle's sums"""
+    n = 8192
+    nodes, outs = E.config_products(n, "f64")
+    host = [synth.matrix(20250203 + 3, s + 1, n, n, "f64") for s in range(3)]
+    plan = ag.Plan(nodes, outs, tier="f64_sliced")
+    (D,) = plan(*[to_dev(h) for h in host])
+    torch.cuda.synchronize()
+    assert plan.status()[0] == "ok"
+    rng = np.random.default_rng(3)
+    ii = rng.integers(0, n, 256)
+    jj = rng.integers(0, n, 256)
+    At = np.asfortranarray(host[0].T)
+    ref = 2.0 * oracle.matmul_entries(At, host[1], ii, jj) + host[2][ii, jj]
+    got = D[torch.as_tensor(ii), torch.as_tensor(jj)].double().cpu().numpy()
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= TOL["f64"], err

@@ -137,6 +137,20 @@ def test_refinement_step_cap(torch):
     assert (st, info) == ("noconverge", 1)
 
 
+@pytest.mark.parametrize("flags", [0, ag.PLAN_DFMA_RESIDUAL])
+def test_residual_sliced_or_dfma(torch, flags):
+    """The FP64 refinement residual by the sliced tensor-core product
+    (default at this size) or by DFMA: both reach the backward error bound and
+    agree with the oracle's literal inverse times B."""
+    n, nrhs = 4096, 64
+    A, Ainv = conditioned(False)
+    B = synth.matrix(20250203 + 3, 2, n, nrhs, "f64")
+    X, (st, info) = solve(torch, A, B, "lu32_ir64", flags=flags)
+    assert st == "ok", (st, info)
+    assert oracle.backward_error(A, X, B) <= 1e-12
+    assert oracle.rel_err(X, oracle.matmul(Ainv, B)) <= 1e-12 * 1e6
+
+
 def test_bf16_tier(torch):
     """The BF16 tier factors in BF16 (one tensor-core product per trailing
     update) and refines in FP64.  At kappa = 1e6, kappa * u_bf16 >> 1: the
