@@ -661,9 +661,9 @@ def bench_planner(a):
     gen_s = time.perf_counter() - t0
     recs, done = [], 0
     t1 = time.perf_counter()
-    budget = float(os.environ.get("ARMA_PLANNER_BUDGET_S", "420"))
+    budget = float(os.environ.get("ARMA_PLANNER_BUDGET_S", "900"))
     for i in range(0, len(dags), 100):
-        part = cm.collect(dags[i:i + 100])
+        part = cm.collect(dags[i:i + 100], target_s=5e-4)
         for r in part:
             r["dag"] += i
         recs += part
@@ -676,7 +676,8 @@ def bench_planner(a):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     steps = 3000
-    losses = net.fit([r["features"] for r in train], [math.log(r["time"]) for r in train], steps=steps)
+    losses = net.fit([r["features"] for r in train], [math.log(r["time"]) for r in train], steps=steps,
+                     groups=[r["dag"] for r in train])
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t2
     guard = 4.0

@@ -23,6 +23,7 @@ from __future__ import annotations
 import ctypes
 import json
 import math
+import os
 
 import numpy as np
 
@@ -31,6 +32,8 @@ from . import (PLAN_LITERAL, PLAN_TIER_CHOICE, PLAN_COST_MLP, N_FEATURES, ArmaEr
 
 HIDDEN = 64
 HEURISTIC_FEATURE = 16      # ln(FLOP/byte estimate) among the plan features
+# the network trained on GB300 timings (train_costnet.py), if present
+DEFAULT_MODEL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "costnet_gb300.json")
 
 
 def candidate_plans(nodes, outputs, tier="native", flags=PLAN_TIER_CHOICE):
@@ -220,6 +223,16 @@ class CostNet:
         net.mu = np.asarray(d["mean"], dtype=np.float64)
         net.sd = np.asarray(d["scale"], dtype=np.float64)
         return net
+
+
+def load_default(guard=4.0, margin=0.0, device="cuda"):
+    """Load the shipped GB300 cost network into the library's planner
+    (ARMA_PLAN_COST_MLP); returns it, or None when the file is absent."""
+    if not os.path.exists(DEFAULT_MODEL):
+        return None
+    net = CostNet.load(DEFAULT_MODEL, device=device)
+    net.to_library(guard=guard, margin=margin)
+    return net
 
 
 def by_dag(recs):

@@ -353,14 +353,18 @@ __global__ void __launch_bounds__(256) row_exp_kcontig_kernel(SliceArgs a) {
   if (lane == 0) a.e[r] = m;
 }
 
-// rows adjacent in memory (rs == 1): one thread per row, coalesced across the warp
+// rows adjacent in memory (rs == 1): a thread per row and per 64 of K
+// (coalesced across the warp), combined with an integer atomic maximum into
+// e, which starts below every bound (NONFINITE is the largest int32, so a
+// non-finite value wins the maximum)
 __global__ void __launch_bounds__(256) row_exp_rcontig_kernel(SliceArgs a) {
   if (a.skip && *a.skip) return;
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= a.R) return;
+  const int64_t l0 = (int64_t)blockIdx.y * 64, l1 = min(l0 + 64, a.K);
   int32_t m = -1021;
-  for (int64_t l = 0; l < a.K; ++l) m = emax(m, exp_bound(a.X[r + l * a.ks]));
-  a.e[r] = m;
+  for (int64_t l = l0; l < l1; ++l) m = emax(m, exp_bound(a.X[r + l * a.ks]));
+  atomicMax(a.e + r, m);
 }
 
 // slices of one value r in (-1, 1): q_s = rint(128 r_s), r_{s+1} = 128 r_s - q_s
@@ -544,10 +548,16 @@ cudaError_t launch_gemm_ozaki(const GemmArgs& a, cudaStream_t s, int* launches) 
   sb.R = a.n; sb.K = a.k; sb.rpad = g.npad; sb.kp = g.kp;
   sb.e = eb; sb.out = Bs; sb.skip = a.skip;
   auto slice = [&](const SliceArgs& x) -> cudaError_t {
-    if (x.ks == 1) row_exp_kcontig_kernel<<<(unsigned)((x.R + 7) / 8), 256, 0, s>>>(x);
-    else row_exp_rcontig_kernel<<<(unsigned)((x.R + 255) / 256), 256, 0, s>>>(x);
     const int64_t gy = x.kp / 64;
     if (gy > 65535) return cudaErrorInvalidConfiguration;
+    if (x.ks == 1) {
+      row_exp_kcontig_kernel<<<(unsigned)((x.R + 7) / 8), 256, 0, s>>>(x);
+    } else {
+      // 0x80808080 as int32 is below every exponent bound
+      cudaError_t e0 = cudaMemsetAsync(x.e, 0x80, (size_t)x.R * sizeof(int32_t), s);
+      if (e0 != cudaSuccess) return e0;
+      row_exp_rcontig_kernel<<<dim3((unsigned)((x.R + 255) / 256), (unsigned)gy), 256, 0, s>>>(x);
+    }
     slice_kernel<<<dim3((unsigned)(x.rpad / 32), (unsigned)gy), 256, 0, s>>>(x);
     if (launches) *launches += 2;
     return cudaGetLastError();

@@ -180,3 +180,29 @@ def test_candidates_match_oracle(torch):
             torch.cuda.synchronize()
             err = oracle.rel_err(to_host(got[0]), ref[0])
             assert err <= 1e-4, (i, ci, p.info["tier"], err)
+
+
+def test_shipped_cost_model_beats_heuristic_on_fresh_dags(torch, capsys):
+    """The cost network shipped with the library (trained by its own kernels
+    on GB300 timings of 4,000 DAGs of the benchmark's generator, seed
+    20250203 + 5) ranks the candidates of 200 DAGs drawn with another seed
+    better than the FLOP/byte estimate: lower geometric-mean regret against
+    the fastest candidate."""
+    from paper_2502_03000_gb300 import costmodel as cm
+    import os
+    assert os.path.exists(cm.DEFAULT_MODEL), "the shipped cost network is missing"
+    net = cm.CostNet.load(cm.DEFAULT_MODEL)
+    dags = cm.make_dags(20250203 + 7, 200, lo=16, hi=8192, cap_flops=2e11)
+    recs = cm.collect(dags, target_s=5e-4)
+    res = cm.evaluate(recs, net, guard=4.0)
+    with capsys.disabled():
+        print("\nshipped model, fresh DAGs:", {k: round(v, 4) if isinstance(v, float) else v for k, v in res.items()})
+    assert res["mlp_regret"] < res["heuristic_regret"], res
+    # and the library, given the network, picks what the rule picks
+    net.to_library(guard=4.0)
+    try:
+        _, mlp, _ = cm.picks(recs, net, guard=4.0)
+        for d, r in sorted(mlp.items())[:30]:
+            assert cm.library_pick(dags[d][0], dags[d][1])[0] == r["cand"]
+    finally:
+        ag.clear_cost_model()
