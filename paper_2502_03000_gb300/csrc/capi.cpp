@@ -351,7 +351,7 @@ arma_status arma_gpu_plan_batched(const arma_expr* exprs, int32_t count, arma_pl
 }
 
 static size_t table_layout(const BatchedInfo& b, size_t* probs_off, size_t* prob_off, size_t* code_off,
-                           size_t* order_off) {
+                           size_t* order_off, size_t* rec_off = nullptr) {
   size_t off = 0;
   *probs_off = off;
   off += (size_t)b.count * sizeof(GroupedProblem);
@@ -364,6 +364,9 @@ static size_t table_layout(const BatchedInfo& b, size_t* probs_off, size_t* prob
   off = (off + 255) / 256 * 256;
   *order_off = off;
   off += (size_t)b.tiles * sizeof(int32_t);
+  off = (off + 255) / 256 * 256;
+  if (rec_off) *rec_off = off;
+  if (b.tc) off += (size_t)b.tiles * sizeof(GroupedTile);
   return (off + 255) / 256 * 256;
 }
 
@@ -378,8 +381,8 @@ arma_status arma_gpu_batched_table_fill(const arma_plan* plan, const void* const
                                         void* const* out_ptrs, void* host_table) {
   if (!plan || !plan->batched || !in_ptrs || !out_ptrs || !host_table) return ARMA_ERR_INVALID;
   const BatchedInfo& b = plan->bi;
-  size_t po, pr, pc, pd;
-  table_layout(b, &po, &pr, &pc, &pd);
+  size_t po, pr, pc, pd, pt;
+  table_layout(b, &po, &pr, &pc, &pd, &pt);
   char* base = static_cast<char*>(host_table);
   GroupedProblem* probs = reinterpret_cast<GroupedProblem*>(base + po);
   for (int32_t i = 0; i < b.count; ++i) {
@@ -400,6 +403,23 @@ arma_status arma_gpu_batched_table_fill(const arma_plan* plan, const void* const
   std::memcpy(base + pr, b.tile_prob.data(), b.tile_prob.size() * sizeof(int32_t));
   std::memcpy(base + pc, b.tile_code.data(), b.tile_code.size() * sizeof(uint32_t));
   std::memcpy(base + pd, b.tile_order.data(), b.tile_order.size() * sizeof(int32_t));
+  if (b.tc) {
+    GroupedTile* recs = reinterpret_cast<GroupedTile*>(base + pt);
+    for (int64_t pos = 0; pos < b.tiles; ++pos) {
+      const int32_t t = b.tile_order[(size_t)pos];
+      const GroupedProblem& g = probs[b.tile_prob[(size_t)t]];
+      if (g.m > INT32_MAX || g.n > INT32_MAX || g.k > INT32_MAX || g.lda > INT32_MAX || g.ldb > INT32_MAX ||
+          g.ldc > INT32_MAX)
+        return ARMA_ERR_UNSUPPORTED;
+      GroupedTile& r = recs[pos];
+      r.A = g.A; r.B = g.B; r.C = g.C; r.D = g.D;
+      r.m = (int32_t)g.m; r.n = (int32_t)g.n; r.k = (int32_t)g.k;
+      r.lda = (int32_t)g.lda; r.ldb = (int32_t)g.ldb; r.ldc = (int32_t)g.ldc;
+      r.tm = (uint16_t)(b.tile_code[(size_t)t] >> 16);
+      r.tn = (uint16_t)(b.tile_code[(size_t)t] & 0xFFFFu);
+      r.t = t;
+    }
+  }
   return ARMA_OK;
 }
 
@@ -408,8 +428,8 @@ arma_status arma_gpu_eval_batched(const arma_plan* plan, const void* device_tabl
   if (!plan || !plan->batched || !device_table) return ARMA_ERR_INVALID;
   if (!workspace || workspace_bytes < plan->ws_bytes) return ARMA_ERR_WORKSPACE;
   const BatchedInfo& b = plan->bi;
-  size_t po, pr, pc, pd;
-  table_layout(b, &po, &pr, &pc, &pd);
+  size_t po, pr, pc, pd, pt;
+  table_layout(b, &po, &pr, &pc, &pd, &pt);
   const char* base = static_cast<const char*>(device_table);
   GroupedArgs g;
   std::memset(&g, 0, sizeof g);
@@ -418,6 +438,7 @@ arma_status arma_gpu_eval_batched(const arma_plan* plan, const void* device_tabl
   g.tile_prob = reinterpret_cast<const int32_t*>(base + pr);
   g.tile_code = reinterpret_cast<const uint32_t*>(base + pc);
   g.tile_order = reinterpret_cast<const int32_t*>(base + pd);
+  g.recs = b.tc ? reinterpret_cast<const GroupedTile*>(base + pt) : nullptr;
   g.next_tile = reinterpret_cast<unsigned int*>(static_cast<char*>(workspace) + 16);
   g.ta = b.ta; g.tb = b.tb; g.abdt = b.abdt; g.cdt = b.cdt; g.ddt = b.ddt;
   g.alpha = b.alpha; g.beta = b.beta;

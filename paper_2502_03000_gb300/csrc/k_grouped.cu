@@ -133,10 +133,13 @@ __device__ __forceinline__ void grouped_tile(const GroupedProblem& pb, int tm, i
     const double* C = static_cast<const double*>(pb.C);
     store([&](int64_t x) { return (float)C[x]; });
   }
-  if (diag_out) {   // diagonal tile: this tile's share of the trace
+  if (diag_out) {   // diagonal tile: this tile's share of the trace (slot 0 of its kTraceSlots)
     double q = 0.0;
     block_sum2(dsum, q);
-    if (threadIdx.x == 0) *diag_out = dsum;
+    if (threadIdx.x == 0) {
+      diag_out[0] = dsum;
+      for (int k = 1; k < kTraceSlots; ++k) diag_out[k] = 0.0;
+    }
   }
 }
 
@@ -161,7 +164,7 @@ __global__ void __launch_bounds__(256, 2) grouped_kernel(const __grid_constant__
     const int32_t p = g.tile_prob[t];
     const GroupedProblem pb = probs[p];
     const int tm = (int)(code >> 16), tn = (int)(code & 0xFFFFu);
-    double* dout = (g.trace_partials && tm == tn) ? g.trace_partials + t : nullptr;
+    double* dout = (g.trace_partials && tm == tn) ? g.trace_partials + kTraceSlots * t : nullptr;
     if (pb.tile == 32) grouped_tile<AT, 32>(pb, tm, tn, g, As, Bs, dout);
     else grouped_tile<AT, 64>(pb, tm, tn, g, As, Bs, dout);
   }
@@ -176,7 +179,12 @@ __global__ void grouped_trace_kernel(const __grid_constant__ GroupedArgs g) {
   const int64_t d = pb.m < pb.n ? pb.m : pb.n;
   const int64_t ntn = (pb.n + pb.tile - 1) / pb.tile;
   double s = 0.0;
-  for (int64_t q = 0; q * pb.tile < d; ++q) s += g.trace_partials[pb.first_tile + q * ntn + q];
+  for (int64_t q = 0; q * pb.tile < d; ++q) {
+    const double* part = g.trace_partials + kTraceSlots * (pb.first_tile + q * ntn + q);
+    double tile = 0.0;
+    for (int k = 0; k < kTraceSlots; ++k) tile += part[k];
+    s += tile;
+  }
   *pb.trace = s;
 }
 

@@ -1731,17 +1731,17 @@ arma_status plan_batched(const arma_expr* exprs, int32_t count, arma_plan* p) {
     }
     b.m.push_back(g.m); b.n.push_back(g.n); b.k.push_back(g.k);
     b.lda.push_back(g.A.ld); b.ldb.push_back(g.B.ld); b.ldc.push_back(g.C.ref.valid() ? g.C.ld : 0);
-    // tile shape per problem: 128 x 128 on the tensor cores for BF16
-    // operands that are both K-contiguous (op(A) = A^T, op(B) = B); FP32
-    // operands would need the three-slice split there, which measured slower
-    // than the SIMT tiles for this size mix (5.5 against 3.7 ms for 10,000
-    // problems of 8..512).  SIMT tiles: 32 x 32 runs at about half the
-    // efficiency of 64 x 64 per output and wins only when 64-tiles would pad
-    // more than 2x (ARMA_PLAN_TILE64 / ARMA_PLAN_TILE32 force one shape; the
-    // Python autotuner times these candidates).  ARMA_PLAN_NO_TENSOR keeps
-    // BF16 on the SIMT tiles.
+    // tile shape per problem: 128 x 128 on the tensor cores when both
+    // operands are K-contiguous (op(A) = A^T, op(B) = B): BF16 operands as
+    // they are, FP32 operands as three exact BF16 slices (six products).
+    // SIMT tiles otherwise: 32 x 32 runs at about half the efficiency of
+    // 64 x 64 per output and wins only when 64-tiles would pad more than 2x
+    // (ARMA_PLAN_TILE64 / ARMA_PLAN_TILE32 force one shape; the Python
+    // autotuner times these candidates).  ARMA_PLAN_NO_TENSOR keeps every
+    // batch on the SIMT tiles.
     if (i == 0)
-      b.tc = (g.A.trans == 1 && g.B.trans == 0 && g.A.dtype == ARMA_BF16 && !(exprs[0].flags & ARMA_PLAN_NO_TENSOR))
+      b.tc = (g.A.trans == 1 && g.B.trans == 0 && (g.A.dtype == ARMA_BF16 || g.A.dtype == ARMA_F32) &&
+              !(exprs[0].flags & ARMA_PLAN_NO_TENSOR))
                  ? 1 : 0;
     const int64_t t32 = ((g.m + 31) / 32) * ((g.n + 31) / 32);
     const int64_t t64 = ((g.m + 63) / 64) * ((g.n + 63) / 64);
@@ -1775,7 +1775,7 @@ arma_status plan_batched(const arma_expr* exprs, int32_t count, arma_plan* p) {
   }
   if (b.tiles > INT32_MAX) return ARMA_ERR_UNSUPPORTED;
   p->batched = true;
-  p->ws_bytes = kHeaderBytes + (size_t)((b.tiles * 8 + 255) / 256 * 256);
+  p->ws_bytes = kHeaderBytes + (size_t)((b.tiles * 8 * 8 + 255) / 256 * 256);   // 8 trace partials per tile
   std::ostringstream os;
   os.precision(17);
   os << "{\"mode\": \"batched\", \"count\": " << count << ", \"tiles\": " << b.tiles

@@ -156,15 +156,16 @@ def batch_of(torch, shapes, dtype, seed):
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 def test_batched_tensor_core_tiles(torch, dtype):
-    """128 x 128 tcgen05 tiles (BF16 operands; FP32 operands take the SIMT
-    tiles): exact tile, ragged edges in m, n and K, several K blocks, K
-    longer than the 512 of the benchmark, one element"""
+    """128 x 128 tcgen05 tiles (BF16 operands as they are, FP32 operands as
+    three exact BF16 slices): exact tile, ragged edges in m, n and K, several
+    K blocks, K longer than the 512 of the benchmark, one element, more tiles
+    than CTAs"""
     shapes = [(128, 128, 64), (129, 127, 65), (300, 257, 1000), (1, 1, 1), (8, 300, 3), (256, 5, 130),
-              (640, 384, 16)]
+              (640, 384, 16), (1100, 1030, 70)]
     inst, host, ins, outs = batch_of(torch, shapes, dtype, 900)
     bp = ag.BatchedPlan(inst)
-    assert bp.info["tensor_cores"] is (dtype == "bf16")
-    assert bp.info["steps"][0]["kernel"] == ("grouped_tc" if dtype == "bf16" else "grouped")
+    assert bp.info["tensor_cores"] is True
+    assert bp.info["steps"][0]["kernel"] == "grouped_tc"
     bp.bind(ins, outs, "cuda")
     bp()
     torch.cuda.synchronize()
@@ -180,7 +181,7 @@ def test_batched_tensor_and_simt_paths_agree(torch, dtype):
     inst, host, ins, outs = build_batch(torch, 303, 40, dtype)
     for flags in (0, ag.PLAN_NO_TENSOR):
         bp = ag.BatchedPlan(inst, flags=flags)
-        assert bp.info["tensor_cores"] is (flags == 0 and dtype == "bf16")
+        assert bp.info["tensor_cores"] is (flags == 0)
         bp.bind(ins, outs, "cuda")
         for o in outs:
             o[0].fill_(float("nan"))
