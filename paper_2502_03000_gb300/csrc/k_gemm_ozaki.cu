@@ -12,9 +12,8 @@
 //
 // Slicing.  A scaled value r in (-1, 1) is written exactly as
 //     r = sum_{s<8} q_s 2^(-7(s+1)) + rest,   |rest| <= 2^-57,
-// with integers q_0 = rint(128 r), q_s = rint(128 r_s) for the remainders
-// r_s (|q_0| <= 128, |q_s| <= 64): every q_s is exact in BF16, and every step
-// is exact in FP64 (a remainder x - rint(x) needs no rounding).
+// with integers |q_0| <= 128, |q_s| <= 64 (balanced base-128 digits of the
+// 56-bit fixed-point value of r): every q_s is exact in BF16.
 //
 // Products.  op(A) op(B) = 2^(e_i + f_j) sum_{s,t} 2^(-7(s+t+2)) Q_s P_t
 // keeps the 36 slice products with s + t <= 7; the dropped ones are below
@@ -367,15 +366,33 @@ __global__ void __launch_bounds__(256) row_exp_rcontig_kernel(SliceArgs a) {
   atomicMax(a.e + r, m);
 }
 
-// slices of one value r in (-1, 1): q_s = rint(128 r_s), r_{s+1} = 128 r_s - q_s
-__device__ __forceinline__ void slice8(double r, uint16_t (&q)[S]) {
+// Slices of one value x of a row with exponent bound e (|x| < 2^e): the
+// fixed-point integer M = rint(x 2^(56 - e)), |M| <= 2^56 (the rounding is
+// the rest, <= 2^-57 of 2^e), written in balanced base-128 digits
+//     M = sum_{s<8} q_s 128^(7 - s),  q_7 .. q_1 in [-64, 63],  |q_0| <= 128,
+// taken from the least significant end: q = M mod 128 in [-64, 63], then
+// M = (M - q) / 128 exactly.  The scaling is two exact power-of-two products;
+// the digits use 32-bit integer operations on the two halves of M (64-bit
+// integer operations would run on the FP64 pipe).
+__device__ __forceinline__ void slice8(double x, int e, uint16_t (&q)[S]) {
+  const int sh = 56 - e, a = sh / 2, b = sh - a;
+  const long long M = __double2ll_rn(x * pow2_half(a) * pow2_half(b));
+  uint32_t lo = (uint32_t)(unsigned long long)M;
+  uint32_t hi = (uint32_t)((unsigned long long)M >> 32);
+  int d[S];
 #pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const double t = r * 128.0;
-    const double qi = rint(t);
-    r = t - qi;
-    q[s] = __bfloat16_as_ushort(__float2bfloat16_rn((float)qi));   // |qi| <= 128: exact
+  for (int s = S - 1; s >= 1; --s) {
+    int v = (int)(lo & 127u);
+    v -= (v & 64) << 1;                                // balanced digit in [-64, 63]
+    const uint32_t vl = (uint32_t)v, vh = (uint32_t)(v >> 31);
+    asm("sub.cc.u32 %0, %0, %2;\n\tsubc.u32 %1, %1, %3;" : "+r"(lo), "+r"(hi) : "r"(vl), "r"(vh));
+    lo = __funnelshift_r(lo, hi, 7);                   // (hi:lo) >>= 7, arithmetic
+    hi = (uint32_t)((int32_t)hi >> 7);
+    d[s] = v;
   }
+  d[0] = (int)lo;                                      // |q_0| <= 128
+#pragma unroll
+  for (int s = 0; s < S; ++s) q[s] = __bfloat16_as_ushort(__float2bfloat16_rn((float)d[s]));   // exact
 }
 
 // A 32-row x 64-K tile per block through shared memory (so that the global
@@ -405,12 +422,10 @@ __global__ void __launch_bounds__(256) slice_kernel(SliceArgs a) {
   if (r >= a.rpad || l >= a.kp) return;
   const int32_t e = r < a.R ? a.e[r] : 0;
   __align__(16) uint16_t q[S][8];
-  // r * 2^-e in two exact steps
-  const double f1 = e == NONFINITE ? 0.0 : pow2_half(-(e / 2)), f2 = e == NONFINITE ? 0.0 : pow2_half(-(e - e / 2));
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     uint16_t qs[S];
-    slice8(e == NONFINITE ? 0.0 : tile[rr][8 * g + j] * f1 * f2, qs);
+    slice8(e == NONFINITE ? 0.0 : tile[rr][8 * g + j], e == NONFINITE ? 0 : e, qs);
 #pragma unroll
     for (int s = 0; s < S; ++s) q[s][j] = qs[s];
   }
