@@ -180,6 +180,12 @@ typedef enum {
                                          with >= 8 right-hand sides use the sliced FP64
                                          product of tier ARMA_TIER_F64_SLICED, A sliced once
                                          per solve */
+#define ARMA_PLAN_NO_LOOKAHEAD 0x4000u /* the FP32 LU factorisation on one stream.  By default
+                                         systems of 192 <= n <= 4096 overlap the trailing
+                                         update of each panel with the factorisation of the
+                                         next (look-ahead) on a high-priority stream of the
+                                         calling host thread (created on first use and kept);
+                                         the results are the same bit for bit */
 /* Step limit of the FP64 iterative refinement of mixed-precision solves
  * (tiers LU32_IR64 and BF16; Sec. I and Sec. III (9): inv(A)*b as a
  * solve).  ARMA_PLAN_REFINE_STEPS(k), 1 <= k <= 15, stops after k steps; 0

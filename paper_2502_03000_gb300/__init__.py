@@ -40,6 +40,7 @@ TIERS = {"native": 0, "f64": 1, "split_bf16": 2, "bf16": 3, "lu32_ir64": 4, "f64
 PLAN_LITERAL, PLAN_CHAIN_LEFT, PLAN_CHAIN_GREEDY, PLAN_COST_MLP, PLAN_NO_FUSE, PLAN_NO_TENSOR = 1, 2, 4, 8, 16, 32
 PLAN_TILE64, PLAN_TILE32, PLAN_NO_SYRK, PLAN_NO_SOLVE_ANALYSIS = 64, 128, 256, 512
 PLAN_COST_HEURISTIC, PLAN_TIER_CHOICE, PLAN_NO_SPLITK, PLAN_DFMA_RESIDUAL = 0x400, 0x800, 0x1000, 0x2000
+PLAN_NO_LOOKAHEAD = 0x4000
 STATUS = {0: "ok", 1: "invalid", 2: "shape", 3: "dtype", 4: "align", 5: "workspace",
           6: "singular", 7: "noconverge", 8: "cuda", 9: "unsupported", 10: "timeout"}
 PLAN_REFINE_SHIFT, PLAN_REFINE_MASK = 16, 0xF0000

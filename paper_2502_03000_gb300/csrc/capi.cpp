@@ -159,6 +159,7 @@ arma_status run_step(const Step& st, const Bind& b, cudaStream_t s, int* launche
       a.props = reinterpret_cast<int32_t*>(b.ws + kSolveRecordOffset);
       a.max_ir = v.max_ir;
       a.dfma_residual = v.dfma_residual;
+      a.no_lookahead = v.no_lookahead;
       return cuda_status(launch_solve(a, s, launches));
     }
   }

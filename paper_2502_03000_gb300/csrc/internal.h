@@ -181,6 +181,9 @@ struct GemmArgs {
   int32_t nosplit;   // 1: one CTA per output tile over the whole of K (no split-K)
   int32_t reuse_a;   // F64_SLICED: op(A)'s slices are already in scratch (an earlier call
                      // with the same A and scratch)
+  int32_t max_ctas;  // tensor-core products: at most this many CTAs (0: one per SM), leaving
+                     // SMs to a kernel that runs beside the product
+  int32_t no_gemv;   // 1: one-row or one-column products take the product kernels too
 };
 
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s, int* launches);
@@ -243,6 +246,7 @@ struct SolveStep {
   int32_t analyse = 0;     // run-time analysis of A picks the solver (Sec. III (10))
   int32_t max_ir = 10;     // refinement step limit (ARMA_PLAN_REFINE_STEPS)
   int32_t dfma_residual = 0;   // 1: the refinement residual by the DFMA product always
+  int32_t no_lookahead = 0;    // 1: the LU factorisation on one stream
   Ref scratch;
   int64_t scratch_bytes = 0;
 };
@@ -269,6 +273,7 @@ struct SolveArgs {
   int32_t* props;         // the solve record (SP_WORDS int32)
   int32_t max_ir;         // refinement step limit (1 .. 15)
   int32_t dfma_residual;  // 1: the refinement residual by the DFMA product always
+  int32_t no_lookahead;   // 1: the LU factorisation on one stream
 };
 int64_t solve_scratch_bytes(int64_t n, int64_t nrhs, int32_t tier, int32_t analyse = 0,
                             int32_t dfma_residual = 0);

@@ -509,7 +509,7 @@ int gemm_sym_valid(const GemmArgs& a) {
 
 cudaError_t launch_gemm(const GemmArgs& a0, cudaStream_t s, int* launches) {
   if (a0.m == 0 || a0.n == 0) return cudaSuccess;
-  if (a0.n == 1 || a0.m == 1) return launch_gemv(a0, s, launches);
+  if ((a0.n == 1 || a0.m == 1) && !a0.no_gemv) return launch_gemv(a0, s, launches);
   GemmArgs a = a0;
   a.sym = gemm_sym_valid(a0);   // anything else is a general product
   if (a.tier == ARMA_TIER_F64_SLICED && gemm_ozaki_supported(a)) return launch_gemm_ozaki(a, s, launches);

@@ -821,7 +821,9 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   const int64_t per_split = sym ? (g.tiles_m / 2) * (int64_t)(g.tiles_m / 2 + 1) : (int64_t)g.tiles_m * g.tiles_n;
   const int64_t work = per_split * g.splits;
   const int sms = device_sm_count();
-  const int grid = (int)(work < sms ? work : sms);
+  int ctas = sms;
+  if (a.max_ctas > 0 && a.max_ctas < ctas) ctas = a.max_ctas;
+  const int grid = (int)(work < ctas ? work : ctas);
   gemm_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(mapA, mapB, p);
   if (launches) ++*launches;
   e = cudaGetLastError();

@@ -27,6 +27,7 @@
 // Numerical failures never trap: a zero pivot records ARMA_ERR_SINGULAR and
 // its 1-based column in the workspace status; refinement that does not reach
 // its tolerance records ARMA_ERR_NOCONVERGE.
+#include <algorithm>
 #include <cooperative_groups.h>
 #include <type_traits>
 #include <utility>
@@ -646,10 +647,27 @@ __global__ void laswp_kernel(T* A, int64_t ld, int64_t n, int64_t j, int w, cons
   }
 }
 
+// the panel's row swaps (rows j .. j + w - 1 with piv[]) applied to the
+// columns [c0, c1)
+template <typename T>
+__global__ void laswp_range_kernel(T* A, int64_t ld, int64_t j, int w, const int32_t* piv, int64_t c0, int64_t c1) {
+  const int64_t col = c0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= c1) return;
+  for (int c = 0; c < w; ++c) {
+    const int64_t d = j + c, p = piv[d];
+    if (p != d) {
+      const T t = A[d + col * ld];
+      A[d + col * ld] = A[p + col * ld];
+      A[p + col * ld] = t;
+    }
+  }
+}
+
 // U12 = L11^-1 A12 (L11 unit lower w x w): one warp per column of A12, lane
 // l holding rows l and l + 32; the column is read and written coalesced
+// (columns [c0, n) of the block row; c0 = 0 means j + w)
 template <typename T>
-__global__ void __launch_bounds__(256) trsm_kernel(T* A, int64_t ld, int64_t n, int64_t j, int w) {
+__global__ void __launch_bounds__(256) trsm_kernel(T* A, int64_t ld, int64_t n, int64_t j, int w, int64_t c0 = 0) {
   __shared__ T L[NB * NB];
   for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
     const int r = t % w, c = t / w;
@@ -657,7 +675,7 @@ __global__ void __launch_bounds__(256) trsm_kernel(T* A, int64_t ld, int64_t n, 
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int64_t col = j + w + (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int64_t col = (c0 ? c0 : j + w) + (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (col >= n) return;
   T* x = A + j + col * ld;
   T x0 = lane < w ? x[lane] : (T)0;
@@ -1251,6 +1269,7 @@ struct Layout {
       total;
   int64_t tri_dinv, tri_y, tri_z, band;   // structured solvers (analysed solves only)
   int64_t gemm_bytes;
+  int64_t gemm2, gemm2_bytes;              // the look-ahead's next-panel update (FP32 LU)
   bool f64;
   bool refine;
 };
@@ -1295,6 +1314,8 @@ Layout layout(int64_t n, int64_t nrhs, int32_t tier, int32_t analyse = 0, int32_
   }
   L.gemm_bytes = gb;
   L.gemm = take(gb);
+  L.gemm2_bytes = L.f64 ? 0 : std::max<int64_t>(gemm_tc_scratch_bytes(n, NB, NB, gt) + 1024, 64 * n * 8);
+  L.gemm2 = L.f64 ? 0 : take(L.gemm2_bytes);
   L.y = take(n * nrhs * es);
   L.z = take(n * nrhs * es);
   L.x64 = L.refine ? take(n * nrhs * 8) : 0;
@@ -1391,6 +1412,139 @@ cudaError_t launch_panel(PanelArgs<T>& pa, int64_t rows, int ctas, cudaStream_t 
   return cudaLaunchCooperativeKernel((const void*)panel_kernel<T>, dim3(ctas), dim3(PT), kargs, smem, s);
 }
 
+// The look-ahead FP32 factorisation (panels that all fit one register
+// cluster, n <= 16 * 256 rows).  The update after panel j is cut in two:
+// the next panel's 64 columns N, and the rest R.  A high-priority side
+// stream carries the critical path: panel j, the swaps of the columns left of
+// it and of N, N's triangular solve and its product update; the caller's
+// stream then updates R (swaps, triangular solve, product limited to the SMs
+// the panel cluster leaves) while the side stream already factors panel
+// j + 1 from N.  Events order the two: the side stream touches N of panel
+// j + 1 (part of R of panel j) only after R's update, and R's update starts
+// only after panel j's pivots and L21 are final.
+int side_stream(cudaStream_t* out) {
+  thread_local cudaStream_t streams[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+  if (!streams[dev]) {
+    int lo = 0, hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) return -1;
+    if (cudaStreamCreateWithPriority(&streams[dev], cudaStreamNonBlocking, hi) != cudaSuccess) {
+      streams[dev] = nullptr;
+      return -1;
+    }
+  }
+  *out = streams[dev];
+  return 0;
+}
+
+bool lookahead_ok(int64_t n) { return n >= 3 * NB && n <= 16 * CSLOTS * RPT; }
+
+cudaError_t factor_lookahead(const SolveArgs& a, const Layout& L, char* base, cudaStream_t s, int* launches,
+                             bool* done) {
+  using T = float;
+  *done = false;
+  const int64_t n = a.n;
+  cudaStream_t h = nullptr;
+  if (side_stream(&h) != 0) return cudaSuccess;   // fall back to the one-stream factorisation
+  cudaEvent_t ev[4] = {};
+  for (int i = 0; i < 4; ++i)
+    if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) {
+      for (int k = 0; k < i; ++k) cudaEventDestroy(ev[k]);
+      cudaGetLastError();
+      return cudaSuccess;
+    }
+  cudaEvent_t ev_start = ev[0], ev_next = ev[1], ev_rest = ev[2], ev_end = ev[3];
+  *done = true;
+  T* W = reinterpret_cast<T*>(base + L.lu);
+  int32_t* piv = reinterpret_cast<int32_t*>(base + L.piv);
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + L.ctl);
+  const int sms = device_sm_count();
+  const int32_t gt = a.tier == ARMA_TIER_BF16 ? ARMA_TIER_BF16 : ARMA_TIER_SPLIT_BF16;
+  cudaError_t e = cudaSuccess;
+  auto gemm = [&](int64_t m, int64_t nc, int64_t k, int64_t j, int64_t c0, char* scratch, int64_t sb, int max_ctas,
+                  cudaStream_t st) -> cudaError_t {
+    GemmArgs g;
+    memset(&g, 0, sizeof g);
+    g.m = m; g.n = nc; g.k = k;
+    g.A = W + (j + k) + j * n; g.lda = n; g.ta = 0; g.adt = ARMA_F32;
+    g.B = W + j + c0 * n; g.ldb = n; g.tb = 0; g.bdt = ARMA_F32;
+    g.C = W + (j + k) + c0 * n; g.ldc = n; g.cdt = ARMA_F32;
+    g.D = W + (j + k) + c0 * n; g.ldd = n; g.ddt = ARMA_F32;
+    g.alpha = -1.0; g.beta = 1.0;
+    g.tier = gt;
+    g.scratch = scratch; g.scratch_bytes = sb;
+    g.status = a.status_code;
+    g.max_ctas = max_ctas;
+    g.no_gemv = 1;     // the same product kernel for every block width
+    return launch_gemm(g, st, launches);
+  };
+  {
+    int64_t blocks = (n * n + 255) / 256, cap = (int64_t)sms * 8;
+    copy_kernel<T><<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(a.A, a.lda, a.adt, W, n);
+    if (launches) ++*launches;
+  }
+  if ((e = cudaEventRecord(ev_start, s)) != cudaSuccess) goto out;
+  if ((e = cudaStreamWaitEvent(h, ev_start, 0)) != cudaSuccess) goto out;
+  for (int64_t j = 0; j < n; j += NB) {
+    const int w = (int)(n - j < NB ? n - j : NB);
+    PanelArgs<T> pa;
+    pa.A = W; pa.ld = n; pa.n = n; pa.j = j; pa.w = w;
+    const int64_t rows = n - j;
+    int ctas = (int)((rows + PT - 1) / PT);
+    if (ctas < 1) ctas = 1;
+    if (ctas > MAX_CTAS) ctas = MAX_CTAS;
+    if (ctas > sms) ctas = sms;
+    pa.rows_per_cta = (rows + ctas - 1) / ctas;
+    ctas = (int)((rows + pa.rows_per_cta - 1) / pa.rows_per_cta);
+    pa.piv = piv;
+    pa.cand_val = reinterpret_cast<double*>(base + L.cand_val);
+    pa.cand_row = reinterpret_cast<int64_t*>(base + L.cand_row);
+    pa.cand_data = reinterpret_cast<T*>(base + L.cand_data);
+    pa.drow = reinterpret_cast<T*>(base + L.drow);
+    pa.ctl = ctl;
+    pa.wait_ns = wait_limit_ns();
+    pa.status = a.status_code;
+    pa.info = a.status_info;
+    if ((e = launch_panel<T>(pa, rows, ctas, h)) != cudaSuccess) goto out;
+    if (launches) ++*launches;
+    const int64_t rest = n - j - w;
+    const int w2 = (int)(rest < NB ? rest : NB);     // the next panel's width
+    // R of the previous panel is updated (it holds this panel's N)
+    if (j > 0 && (e = cudaStreamWaitEvent(h, ev_rest, 0)) != cudaSuccess) goto out;
+    if (j > 0) {
+      laswp_range_kernel<T><<<(unsigned)((j + 255) / 256), 256, 0, h>>>(W, n, j, w, piv, 0, j);
+      if (launches) ++*launches;
+    }
+    if (w2 > 0) {
+      laswp_range_kernel<T><<<1, 256, 0, h>>>(W, n, j, w, piv, j + w, j + w + w2);
+      trsm_kernel<T><<<(unsigned)((w2 + 7) / 8), 256, 0, h>>>(W, n, j + w + w2, j, w, j + w);
+      if (launches) *launches += 2;
+      if ((e = gemm(rest, w2, w, j, j + w, base + L.gemm2, L.gemm2_bytes, 0, h)) != cudaSuccess) goto out;
+    }
+    if ((e = cudaEventRecord(ev_next, h)) != cudaSuccess) goto out;
+    const int64_t r0 = j + w + w2, rn = n - r0;       // R: columns [r0, n)
+    if (rn > 0) {
+      if ((e = cudaStreamWaitEvent(s, ev_next, 0)) != cudaSuccess) goto out;
+      laswp_range_kernel<T><<<(unsigned)((rn + 255) / 256), 256, 0, s>>>(W, n, j, w, piv, r0, n);
+      trsm_kernel<T><<<(unsigned)((rn + 7) / 8), 256, 0, s>>>(W, n, n, j, w, r0);
+      if (launches) *launches += 2;
+      if ((e = gemm(rest, rn, w, j, r0, base + L.gemm, L.gemm_bytes, sms - 16 > 1 ? sms - 16 : 1, s)) != cudaSuccess)
+        goto out;
+      if ((e = cudaEventRecord(ev_rest, s)) != cudaSuccess) goto out;
+    } else if (j + w < n) {
+      if ((e = cudaEventRecord(ev_rest, h)) != cudaSuccess) goto out;   // nothing left of R
+    }
+  }
+  // the caller's stream continues after the side stream's last work
+  if ((e = cudaEventRecord(ev_end, h)) != cudaSuccess) goto out;
+  e = cudaStreamWaitEvent(s, ev_end, 0);
+out:
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e;
+}
+
 template <typename T>
 cudaError_t factor(const SolveArgs& a, const Layout& L, char* base, cudaStream_t s, int* launches) {
   const int64_t n = a.n;
@@ -1449,6 +1603,7 @@ cudaError_t factor(const SolveArgs& a, const Layout& L, char* base, cudaStream_t
       g.tier = gt;
       g.scratch = base + L.gemm; g.scratch_bytes = L.gemm_bytes;
       g.status = a.status_code;
+      g.no_gemv = 1;   // as the look-ahead factorisation does: the same kernel for every width
       e = launch_gemm(g, s, launches);
       if (e != cudaSuccess) return e;
     }
@@ -1812,7 +1967,12 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s, int* launches) {
     if (launches) *launches += 4;
     return cudaGetLastError();
   }
-  e = chol ? try_cholesky(0.0f) : factor<float>(a, L, base, s, launches);
+  bool la = false;
+  if (!chol && !a.no_lookahead && lookahead_ok(n)) {
+    e = factor_lookahead(a, L, base, s, launches, &la);
+    if (e != cudaSuccess) return e;
+  }
+  if (!la) e = chol ? try_cholesky(0.0f) : factor<float>(a, L, base, s, launches);
   if (e != cudaSuccess) return e;
   const float* W = reinterpret_cast<const float*>(base + L.lu);
   float* Linv = reinterpret_cast<float*>(base + L.dinv);

@@ -840,6 +840,7 @@ void Planner::emit_solve(const MatOperand& A, int64_t n, const MatOperand* B, in
   const uint32_t ir = (e_.flags & ARMA_PLAN_REFINE_MASK) >> ARMA_PLAN_REFINE_SHIFT;
   s.max_ir = ir ? (int32_t)ir : 10;
   s.dfma_residual = (e_.flags & ARMA_PLAN_DFMA_RESIDUAL) ? 1 : 0;
+  s.no_lookahead = (e_.flags & ARMA_PLAN_NO_LOOKAHEAD) ? 1 : 0;
   s.scratch_bytes = solve_scratch_bytes(n, s.nrhs, s.tier, s.analyse, s.dfma_residual);
   s.scratch = ref_ws(alloc_ws(s.scratch_bytes));
   Step st;

@@ -151,6 +151,19 @@ def test_residual_sliced_or_dfma(torch, flags):
     assert oracle.rel_err(X, oracle.matmul(Ainv, B)) <= 1e-12 * 1e6
 
 
+@pytest.mark.parametrize("n,nrhs", [(4096, 64), (1000, 5), (257, 3), (2100, 17)])
+def test_lookahead_equals_one_stream(torch, n, nrhs):
+    """The look-ahead factorisation (next panel beside the trailing update,
+    two streams) gives the one-stream factorisation's result bit for bit."""
+    A = synth.conditioned_matrix(20250203 + 3, n, 1e6, symmetric=False) if n == 4096 else well_conditioned(n + 7, n)
+    B = synth.matrix(n + 8, 2, n, nrhs, "f64")
+    X1, (st1, i1) = solve(torch, A, B, "lu32_ir64")
+    X2, (st2, i2) = solve(torch, A, B, "lu32_ir64", flags=ag.PLAN_NO_LOOKAHEAD)
+    assert (st1, i1) == (st2, i2) and st1 == "ok"
+    assert np.array_equal(X1, X2)
+    assert oracle.backward_error(A, X1, B) <= 1e-14
+
+
 def test_bf16_tier(torch):
     """The BF16 tier factors in BF16 (one tensor-core product per trailing
     update) and refines in FP64.  At kappa = 1e6, kappa * u_bf16 >> 1: the
