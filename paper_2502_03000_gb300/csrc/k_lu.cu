@@ -416,35 +416,19 @@ __global__ void __launch_bounds__(CPT) panel_cluster_kernel(const __grid_constan
   }
 }
 
-// The cluster panel with the panel held in registers: thread (slot, seg)
-// keeps rows slot and slot + 128 of its CTA, panel columns 16 seg ..
-// 16 seg + 15, so the rank-1 update touches no shared memory.  The column
-// loop is unrolled by 16 so that register indices are static.  Pivot
-// candidates are compared as monotone integer keys of |value| (warp
-// max/min reductions); ties go to the smallest row.  Rows per CTA <= 256
-// and >= w (the diagonal block lies in CTA 0).
-constexpr int RPT = 2;
-
-// row i of a thread's register rows, as selects (never an indexed access,
-// which would move the rows to local memory)
-template <typename T>
-__device__ __forceinline__ T pick(const T (&x)[RPT][16], int i, int kk) {
-  T v = x[0][kk];
-#pragma unroll
-  for (int q = 1; q < RPT; ++q) v = i == q ? x[q][kk] : v;
-  return v;
-}
-template <typename T>
-__device__ __forceinline__ void blend(T (&x)[RPT][16], int i, int kk, T v) {
-#pragma unroll
-  for (int q = 0; q < RPT; ++q) x[q][kk] = i == q ? v : x[q][kk];
-}
-
-// f(integral_constant<int, I>) for each I of the sequence, in order
-template <typename F, int... Is>
-__device__ __forceinline__ void static_for(F& f, std::integer_sequence<int, Is...>) {
-  (f(std::integral_constant<int, Is>{}), ...);
-}
+// The cluster panel with the panel held in registers, one row per thread:
+// thread t of a CTA keeps row t of the CTA's rows, all 64 panel columns, so
+// a row's multiplier never leaves its thread and the rank-1 update touches
+// no shared memory.  Per column: warp candidates -> CTA barrier -> the CTA's
+// candidate and its row published -> cluster barrier -> warp 0 reads the
+// CTAs' candidates, then (one more round trip) the winning row and, in the
+// CTA that holds the pivot row, row d -> CTA barrier -> swap, multiplier,
+// update.  The column loop is unrolled by 16 (static register index within a
+// group of 16 columns, the group at run time).  Pivot candidates are compared
+// as monotone integer keys of |value| (warp max/min reductions); ties go to
+// the smallest row.  Pivots are kept in shared memory and stored once at the
+// end.  Rows per CTA <= RT and >= w (the diagonal block lies in CTA 0).
+constexpr int RT = 256;
 
 __device__ __forceinline__ uint32_t abs_key(float v) { return (__float_as_uint(v) & 0x7fffffffu) + 1u; }
 __device__ __forceinline__ uint64_t abs_key(double v) {
@@ -465,19 +449,35 @@ __device__ __forceinline__ void warp_argmax(uint64_t& key, uint32_t& row) {
   key = m;
 }
 
+// f(integral_constant<int, I>) for each I of the sequence, in order
+template <typename F, int... Is>
+__device__ __forceinline__ void static_for(F& f, std::integer_sequence<int, Is...>) {
+  (f(std::integral_constant<int, Is>{}), ...);
+}
+
+// x[cb][k], the group cb at run time
+template <typename T, int k>
+__device__ __forceinline__ T group_col(const T (&x)[4][16], int cb) {
+  T v = x[0][k];
+#pragma unroll
+  for (int g = 1; g < 4; ++g) v = cb == g ? x[g][k] : v;
+  return v;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(CPT, 1) panel_reg_kernel(const __grid_constant__ PanelArgs<T> a) {
+__global__ void __launch_bounds__(RT, 1) panel_reg_kernel(const __grid_constant__ PanelArgs<T> a) {
   using K = typename std::conditional<sizeof(T) == 8, uint64_t, uint32_t>::type;
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
-  __shared__ K wkey[4];                   // per warp of the column's segment
-  __shared__ uint32_t wrow[4];
+  __shared__ K wkey[RT / 32];             // per warp
+  __shared__ uint32_t wrow[RT / 32];
   __shared__ K c_key[2];                  // this CTA's candidate, per phase
   __shared__ uint32_t c_row[2];
   __shared__ __align__(16) T c_data[2][NB];   // its candidate row
   __shared__ __align__(16) T c_drow[2][NB];   // row d (CTA 0)
-  __shared__ T lbuf[CSLOTS * RPT];        // multipliers of column c
   __shared__ __align__(16) T s_u[NB];     // the pivot row
+  __shared__ __align__(16) T s_d[NB];     // row d, in the CTA that holds the pivot row
+  __shared__ int32_t s_piv[NB];           // pivot rows, stored once at the end
   __shared__ int64_t s_p;
   __shared__ int s_win;
   const unsigned int nranks = cl.num_blocks();
@@ -488,66 +488,55 @@ __global__ void __launch_bounds__(CPT, 1) panel_reg_kernel(const __grid_constant
   const int nown = r1 > r0 ? (int)(r1 - r0) : 0;
   const int w = a.w;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int slot = tid & (CSLOTS - 1), seg = tid / CSLOTS;
-  T x[RPT][16];
+  const bool own = tid < nown;
+  const int64_t grow = r0 + tid;          // this thread's row
+  T x[4][16];
 #pragma unroll
-  for (int i = 0; i < RPT; ++i)
+  for (int g = 0; g < 4; ++g)
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      const int rr = slot + CSLOTS * i, col = 16 * seg + kk;
-      x[i][kk] = (rr < nown && col < w) ? a.A[(r0 + rr) + (a.j + col) * a.ld] : (T)0;
+      const int col = 16 * g + kk;
+      x[g][kk] = (own && col < w) ? a.A[grow + (a.j + col) * a.ld] : (T)0;
     }
+  for (int q = tid; q < NB; q += RT) s_u[q] = s_d[q] = (T)0;   // columns >= w stay zero
+  __syncthreads();
   for (int cb = 0; cb < 4 && 16 * cb < w; ++cb) {
     auto column = [&](auto kc) {
       constexpr int k = decltype(kc)::value;
       const int c = 16 * cb + k;
-      if (c < w) {
+      if (c >= w) return;
       const int64_t d = a.j + c;
-      const int ph = k & 1;
-      const int dl = (int)(d - r0);       // row d in this CTA's numbering
-      // A. per-warp candidates of column c (the warps of segment cb)
-      if (seg == cb) {
-        K key = 0;
-        uint32_t row = 0xffffffffu;
+      const int ph = c & 1;
+      // A. warp candidates of column c (rows >= d)
+      K key = 0;
+      uint32_t row = 0xffffffffu;
+      if (own && grow >= d) { key = abs_key(group_col<T, k>(x, cb)); row = (uint32_t)grow; }
+      warp_argmax(key, row);
+      if (lane == 0) { wkey[wid] = key; wrow[wid] = row; }
+      if (rank == 0 && grow == d) {
 #pragma unroll
-        for (int i = 0; i < RPT; ++i) {
-          const int rr = slot + CSLOTS * i;
-          if (rr < nown && r0 + rr >= d) {
-            const K kv = abs_key(x[i][k]);
-            if (kv > key) { key = kv; row = (uint32_t)(r0 + rr); }
-          }
-        }
-        warp_argmax(key, row);
-        if (lane == 0) { wkey[wid & 3] = key; wrow[wid & 3] = row; }
-      }
-      if (rank == 0 && dl >= 0 && dl < nown && (dl & (CSLOTS - 1)) == slot) {
-        const int i = dl / CSLOTS;
+        for (int g = 0; g < 4; ++g)
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk)
-          if (16 * seg + kk < w) c_drow[ph][16 * seg + kk] = pick(x, i, kk);
+          for (int kk = 0; kk < 16; ++kk) c_drow[ph][16 * g + kk] = x[g][kk];
       }
       __syncthreads();
-      // B. the CTA's candidate; its owner threads publish the row
+      // B. the CTA's candidate; its owner publishes the row
       K ck = wkey[0];
       uint32_t cr = wrow[0];
 #pragma unroll
-      for (int q = 1; q < 4; ++q)
+      for (int q = 1; q < RT / 32; ++q)
         if (wkey[q] > ck || (wkey[q] == ck && wrow[q] < cr)) { ck = wkey[q]; cr = wrow[q]; }
       if (tid == 0) { c_key[ph] = ck; c_row[ph] = cr; }
-      if (ck != 0) {
-        const int cl_ = (int)((int64_t)cr - r0);
-        if ((cl_ & (CSLOTS - 1)) == slot) {
-          const int i = cl_ / CSLOTS;
+      if (ck != 0 && (uint32_t)grow == cr && own) {
 #pragma unroll
-          for (int kk = 0; kk < 16; ++kk)
-            if (16 * seg + kk < w) c_data[ph][16 * seg + kk] = pick(x, i, kk);
-        }
+        for (int g = 0; g < 4; ++g)
+#pragma unroll
+          for (int kk = 0; kk < 16; ++kk) c_data[ph][16 * g + kk] = x[g][kk];
       }
       cl.sync();
-      // C. warp 0 selects the pivot among the CTAs' candidates and copies
-      //    the pivot row into this CTA's shared memory (one remote read per
-      //    value and CTA; every thread reading it remotely would queue the
-      //    whole cluster on the winner's shared memory)
+      // C. warp 0 selects the pivot among the CTAs' candidates and copies the
+      //    pivot row (and, where the pivot row lies in this CTA, row d) into
+      //    this CTA's shared memory: one remote read per value and CTA
       if (wid == 0) {
         K gk = 0;
         uint32_t gr = 0xffffffffu, mine = 0xffffffffu;
@@ -558,75 +547,69 @@ __global__ void __launch_bounds__(CPT, 1) panel_reg_kernel(const __grid_constant
         warp_argmax(gk, gr);
         const bool sing = gk <= (K)1;     // |value| = 0 everywhere below d
         const int wn = sing ? -1 : __ffs(__ballot_sync(0xffffffffu, mine == gr)) - 1;
+        const int64_t p = sing ? d : (int64_t)gr;
         const T* src = wn >= 0 ? cl.map_shared_rank(&c_data[ph][0], (unsigned int)wn)
                                : cl.map_shared_rank(&c_drow[ph][0], 0u);
-        for (int q = lane; q < w; q += 32) s_u[q] = src[q];
+        const bool here = p != d && p >= r0 && p < r0 + nown;
+        const T* drow = cl.map_shared_rank(&c_drow[ph][0], 0u);
+        for (int q = lane; q < w; q += 32) {
+          const T uq = src[q];
+          const T dq = here ? drow[q] : (T)0;
+          s_u[q] = uq;
+          if (here) s_d[q] = dq;
+        }
         if (lane == 0) {
-          s_p = sing ? d : (int64_t)gr;
+          s_p = p;
           s_win = wn;
-          if (rank == 0) {
-            if (sing && atomicCAS(a.status, 0, (int32_t)ARMA_ERR_SINGULAR) == 0) *a.info = d + 1;
-            a.piv[d] = (int32_t)(sing ? d : (int64_t)gr);
-          }
+          s_piv[c] = (int32_t)p;
+          if (rank == 0 && sing && atomicCAS(a.status, 0, (int32_t)ARMA_ERR_SINGULAR) == 0) *a.info = d + 1;
         }
       }
       __syncthreads();
       const int64_t p = s_p;
-      const bool singular = s_win < 0;
-      T u[16];
-#pragma unroll
-      for (int kk = 0; kk < 16; ++kk) u[kk] = 16 * seg + kk < w ? s_u[16 * seg + kk] : (T)0;
+      if (s_win < 0) return;              // singular column: nothing to eliminate
       const T pv = s_u[c];
       // D. swap rows d and p
       if (p != d) {
-        if (dl >= 0 && dl < nown && (dl & (CSLOTS - 1)) == slot) {
-          const int i = dl / CSLOTS;
+        if (grow == d) {
 #pragma unroll
-          for (int kk = 0; kk < 16; ++kk) blend(x, i, kk, u[kk]);
-        }
-        const int pl = (int)(p - r0);
-        if (pl >= 0 && pl < nown && (pl & (CSLOTS - 1)) == slot) {
-          const T* dr = cl.map_shared_rank(&c_drow[ph][0], 0u);
-          const int i = pl / CSLOTS;
+          for (int g = 0; g < 4; ++g)
 #pragma unroll
-          for (int kk = 0; kk < 16; ++kk)
-            if (16 * seg + kk < w) blend(x, i, kk, dr[16 * seg + kk]);
+            for (int kk = 0; kk < 16; ++kk) x[g][kk] = s_u[16 * g + kk];
+        } else if (grow == p) {
+#pragma unroll
+          for (int g = 0; g < 4; ++g)
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) x[g][kk] = s_d[16 * g + kk];
         }
       }
-      // E. multipliers of column c, then the rank-1 update
-      if (seg == cb) {
+      // E. the multiplier of this row, then the update of the columns right of c
+      if (own && grow > d) {
+        const T l = group_col<T, k>(x, cb) / pv;
 #pragma unroll
-        for (int i = 0; i < RPT; ++i) {
-          const int rr = slot + CSLOTS * i;
-          T l = (T)0;
-          if (!singular && rr < nown && r0 + rr > d) {
-            l = x[i][k] / pv;
-            x[i][k] = l;
+        for (int g = 0; g < 4; ++g) {
+          if (g == cb) {
+            x[g][k] = l;
+#pragma unroll
+            for (int kk = k + 1; kk < 16; ++kk) x[g][kk] -= l * s_u[16 * g + kk];
+          } else if (g > cb) {
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) x[g][kk] -= l * s_u[16 * g + kk];
           }
-          lbuf[rr] = l;
         }
-      }
-      __syncthreads();
-      if (!singular && 16 * seg + 15 > c) {
-#pragma unroll
-        for (int i = 0; i < RPT; ++i) {
-          const T l = lbuf[slot + CSLOTS * i];
-#pragma unroll
-          for (int kk = 0; kk < 16; ++kk)
-            if (16 * seg + kk > c) x[i][kk] -= l * u[kk];
-        }
-      }
       }
     };
     static_for(column, std::make_integer_sequence<int, 16>{});
   }
   cl.sync();                              // peers may still read this CTA's buffers
+  if (rank == 0)
+    for (int q = tid; q < w; q += RT) a.piv[a.j + q] = s_piv[q];
 #pragma unroll
-  for (int i = 0; i < RPT; ++i)
+  for (int g = 0; g < 4; ++g)
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      const int rr = slot + CSLOTS * i, col = 16 * seg + kk;
-      if (rr < nown && col < w) a.A[(r0 + rr) + (a.j + col) * a.ld] = x[i][kk];
+      const int col = 16 * g + kk;
+      if (own && col < w) a.A[grow + (a.j + col) * a.ld] = x[g][kk];
     }
 }
 
@@ -1347,10 +1330,10 @@ cudaError_t launch_panel(PanelArgs<T>& pa, int64_t rows, int ctas, cudaStream_t 
     cudaGetLastError();
     cluster_probe.store(cluster_max, std::memory_order_release);
   }
-  auto cluster_cfg = [&](cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int cs, size_t smem) {
+  auto cluster_cfg = [&](cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int cs, size_t smem, int threads) {
     memset(&cfg, 0, sizeof cfg);
     cfg.gridDim = dim3((unsigned)cs);
-    cfg.blockDim = dim3(CPT);
+    cfg.blockDim = dim3((unsigned)threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1360,10 +1343,10 @@ cudaError_t launch_panel(PanelArgs<T>& pa, int64_t rows, int ctas, cudaStream_t 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
   };
-  // registers: the smallest cluster with <= 128 * RPT rows per CTA
+  // registers: the smallest cluster with <= RT rows per CTA
   for (int cs = 1; cs <= cluster_max; cs *= 2) {
     const int64_t R = (rows + cs - 1) / cs;
-    if (R > CSLOTS * RPT) continue;
+    if (R > RT) continue;
     if (R < pa.w) break;
     if (cs > 8 && cudaFuncSetAttribute(panel_reg_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                       cudaSuccess) {
@@ -1372,7 +1355,7 @@ cudaError_t launch_panel(PanelArgs<T>& pa, int64_t rows, int ctas, cudaStream_t 
     }
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    cluster_cfg(cfg, attr, cs, 0);
+    cluster_cfg(cfg, attr, cs, 0, RT);
     int nclusters = 0;
     if (cudaOccupancyMaxActiveClusters(&nclusters, panel_reg_kernel<T>, &cfg) != cudaSuccess || nclusters < 1) {
       cudaGetLastError();
@@ -1393,7 +1376,7 @@ cudaError_t launch_panel(PanelArgs<T>& pa, int64_t rows, int ctas, cudaStream_t 
       break;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    cluster_cfg(cfg, attr, cs, smem);
+    cluster_cfg(cfg, attr, cs, smem, CPT);
     int nclusters = 0;
     if (cudaOccupancyMaxActiveClusters(&nclusters, panel_cluster_kernel<T>, &cfg) != cudaSuccess || nclusters < 1) {
       cudaGetLastError();
@@ -1438,7 +1421,7 @@ int side_stream(cudaStream_t* out) {
   return 0;
 }
 
-bool lookahead_ok(int64_t n) { return n >= 3 * NB && n <= 16 * CSLOTS * RPT; }
+bool lookahead_ok(int64_t n) { return n >= 3 * NB && n <= 16 * RT; }
 
 cudaError_t factor_lookahead(const SolveArgs& a, const Layout& L, char* base, cudaStream_t s, int* launches,
                              bool* done) {
@@ -1688,8 +1671,7 @@ cudaError_t factor_cholesky(const SolveArgs& a, const Layout& L, char* base, cud
     if (launches) ++*launches;
   }
   const int32_t gt = L.f64 ? ARMA_TIER_F64 : a.tier == ARMA_TIER_BF16 ? ARMA_TIER_BF16 : ARMA_TIER_SPLIT_BF16;
-  const int64_t nb = (n + NB - 1) / NB;
-  T* Dinv = reinterpret_cast<T*>(base + L.dinv);   // [2 nb][NB][NB]; rewritten after the factorisation
+  T* Dinv = reinterpret_cast<T*>(base + L.dinv);   // [2 ceil(n / NB)][NB][NB]; rewritten after the factorisation
   const int dt = L.f64 ? ARMA_F64 : ARMA_F32;
   for (int64_t j = 0; j < n; j += NB) {
     const int w = (int)(n - j < NB ? n - j : NB);
