@@ -399,6 +399,8 @@ arma_status arma_gpu_batched_table_fill(const arma_plan* plan, const void* const
     g.first_tile = b.first_tile[i];
     g.tile = b.tile[i];
     g.pad = 0;
+    g.pa = b.tc ? b.pa[i] : 0;
+    g.pb = b.tc ? b.pb[i] : 0;
     if ((!g.A || !g.B || !g.D) && g.m * g.n > 0) return ARMA_ERR_INVALID;
   }
   std::memcpy(base + pr, b.tile_prob.data(), b.tile_prob.size() * sizeof(int32_t));
@@ -409,16 +411,26 @@ arma_status arma_gpu_batched_table_fill(const arma_plan* plan, const void* const
     for (int64_t pos = 0; pos < b.tiles; ++pos) {
       const int32_t t = b.tile_order[(size_t)pos];
       const GroupedProblem& g = probs[b.tile_prob[(size_t)t]];
-      if (g.m > INT32_MAX || g.n > INT32_MAX || g.k > INT32_MAX || g.lda > INT32_MAX || g.ldb > INT32_MAX ||
-          g.ldc > INT32_MAX)
+      if (g.m > INT32_MAX || g.n > INT32_MAX || g.k > INT32_MAX || g.ldc > INT32_MAX)
         return ARMA_ERR_UNSUPPORTED;
       GroupedTile& r = recs[pos];
-      r.A = g.A; r.B = g.B; r.C = g.C; r.D = g.D;
+      std::memset(&r, 0, sizeof r);
+      r.C = g.C; r.D = g.D;
       r.m = (int32_t)g.m; r.n = (int32_t)g.n; r.k = (int32_t)g.k;
-      r.lda = (int32_t)g.lda; r.ldb = (int32_t)g.ldb; r.ldc = (int32_t)g.ldc;
+      r.ldc = (int32_t)g.ldc;
       r.tm = (uint16_t)(b.tile_code[(size_t)t] >> 16);
       r.tn = (uint16_t)(b.tile_code[(size_t)t] & 0xFFFFu);
       r.t = t;
+      // the tile's rows in the packed arrays, and the smallest box that
+      // covers the rows it has (rows past them only feed outputs that are
+      // never stored)
+      r.ya = (int32_t)(g.pa + 128 * (int64_t)r.tm);
+      r.yb = (int32_t)(g.pb + 128 * (int64_t)r.tn);
+      r.sa = r.m;
+      r.sb = r.n;
+      auto box = [](int64_t rows) -> uint16_t { return rows <= 16 ? 16 : rows <= 32 ? 32 : rows <= 64 ? 64 : 128; };
+      r.ha = box(g.m - 128 * (int64_t)r.tm);
+      r.hb = box(g.n - 128 * (int64_t)r.tn);
     }
   }
   return ARMA_OK;
@@ -447,6 +459,13 @@ arma_status arma_gpu_eval_batched(const arma_plan* plan, const void* device_tabl
   g.trace_partials = b.out_t >= 0 ? reinterpret_cast<double*>(static_cast<char*>(workspace) + kHeaderBytes) : nullptr;
   g.tc = b.tc;
   g.status = static_cast<int32_t*>(workspace);
+  if (b.tc) {
+    g.pack_a = static_cast<char*>(workspace) + b.pack_off;
+    g.pack_b = static_cast<char*>(workspace) + b.pack_off + (size_t)b.slices * (size_t)b.rows_a * 128;
+    g.rows_a = b.rows_a;
+    g.rows_b = b.rows_b;
+    g.slices = b.slices;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // status, info and the tile counter start at zero
   if (cudaError_t e = cudaMemsetAsync(workspace, 0, 32, s)) return cuda_status(e);

@@ -341,6 +341,11 @@ struct BatchedInfo {
   std::vector<uint32_t> tile_code;
   std::vector<int32_t> tile_order;   // tiles by decreasing work (longest first)
   int64_t tiles = 0;
+  // tensor cores: packed operand rows (K-block-major, 64 BF16 per row)
+  std::vector<int64_t> pa, pb;       // per problem: first packed row of op(A), op(B)^T
+  int64_t rows_a = 0, rows_b = 0;    // packed rows per slice
+  int32_t slices = 1;                // 1 (BF16) or 3 (FP32 as exact BF16 slices)
+  size_t pack_off = 0, pack_bytes = 0;   // the packed arrays in the workspace
 };
 
 }  // namespace arma

@@ -1,32 +1,41 @@
 // Grouped products on the tensor cores (tcgen05, sm_103a): the batched form
 // of the folded product D_g = alpha * op(A_g) op(B_g) + beta * C_g with the
 // diagonal-only trace t_g = trace(op(A_g) op(B_g)) (Sec. II xGEMM paragraph,
-// Sec. III (5)), for thousands of problems of uneven sizes in one persistent
-// launch.
+// Sec. III (5)), for thousands of problems of uneven sizes in two launches.
 //
-// One CTA per SM walks its share of the host-built list of 128 x 128 output
-// tiles (ordered by decreasing work; CTA c takes positions c, 2G-1-c, 2G+c,
-// ... so that the long tiles spread evenly).  Every role walks the same
-// sequence, so they need no tile queue:
-//   warps 0..15  producers, two groups of eight warps taking alternate K
-//                blocks: per K block of 64 a group loads the two operand
-//                tiles from global memory (both operands
-//                K-contiguous: op(A) = A^T, op(B) = B; leading dimensions of
-//                any value, so no tensor map fits them), convert to BF16
-//                (S = 1) or split FP32 exactly into three BF16 slices (S = 3,
-//                Henry et al. 2019, the BF16 work the paper cites), and store
-//                them 128-byte-swizzled into a ring of shared-memory stages;
-//                the next block is prefetched into L2 meanwhile
-//   warp 16      TMEM owner (two 128-column FP32 accumulators) and MMA issuer:
-//                one tcgen05.mma per 16 of K and slice product (6 products of
-//                order <= 2 for S = 3, smallest first)
-//   warps 17..20 epilogue: tcgen05.ld of a finished accumulator while the next
-//                tile's MMAs run into the other; alpha, beta*C, D, and the
-//                diagonal of diagonal tiles for the traces
-// Every mbarrier wait is bounded: on timeout the CTA records ARMA_ERR_TIMEOUT
-// in the status word, waits (bounded) for its issued MMAs, frees TMEM and
-// returns.
+// 1. pack   one CTA per (problem, operand) copies op(A_g) and op(B_g)^T (both
+//           K-contiguous, leading dimensions of any value) into one packed
+//           array per operand: K-block-major BF16 rows of 64 (K block kb of a
+//           problem's R rows at rows p_g + kb R .. + R - 1, K past k_g zero).
+//           FP32 operands are split exactly into three BF16 slices (Henry et
+//           al. 2019, the BF16 work the paper cites), one array per slice.
+//           Every row of 64 is one 128-byte line, so the product kernel
+//           reads the operands with TMA whatever the caller's strides.
+// 2. product  one persistent CTA per SM walks its share of the host-built
+//           list of 128 x 128 output tiles (ordered by decreasing work; CTA c
+//           takes positions c, 2G-1-c, 2G+c, ... so that the long tiles
+//           spread evenly).  Every role walks the same sequence:
+//   warp 0     TMA producer: per K block one box of op(A) rows and one of
+//              op(B)^T rows per slice into a ring of shared-memory stages
+//              (128-byte swizzle); the box is the smallest of 16, 32, 64 and
+//              128 rows that covers the tile's rows
+//   warp 1     TMEM owner (four 128-column FP32 accumulators, all of TMEM)
+//              and MMA issuer: tile i of the CTA's sequence into accumulator
+//              i % 4; one tcgen05.mma per 16 of K and slice product (6
+//              products of order <= 2 for three slices, smallest first)
+//   warps 2..17 four epilogue groups of four warps (one per TMEM lane
+//              quarter); group e drains the tiles i = e (mod 4), so four
+//              tiles' epilogues are in flight: the tile's C lines into L2
+//              while its MMAs run, then per 16 columns tcgen05.ld, C, alpha,
+//              beta*C, D, and the diagonal of diagonal tiles for the traces
+// Rows of a box past the problem's rows (and stale shared memory past a
+// short box) only reach output rows and columns that are never stored: each
+// output element depends on its own row of op(A) and column of op(B) alone.
+// Every mbarrier wait is bounded: on timeout the CTA records
+// ARMA_ERR_TIMEOUT in the status word, waits (bounded) for its issued copies
+// and MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <atomic>
 
@@ -35,76 +44,41 @@
 #include "tc_ops.cuh"
 
 namespace arma {
+namespace tc {
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn();   // k_gemm_tc.cu
+}
+
 namespace {
 
 using namespace tc;
 
-constexpr int GM = 128, GN = 128, GK = 64;   // output tile and K block
-constexpr int NPROD = 256;                   // producer threads of one group (8 warps)
-constexpr int NGROUP = 2;                    // producer groups, alternate K blocks
-constexpr int MMA_WARP = 8 * NGROUP;         // warp 16
-constexpr int NEPI = 256;                    // warps 17..24: lane quarters 1, 2, 3, 0, twice
-constexpr int GTHREADS = (8 * NGROUP + 9) * 32;
-constexpr int GSLICE = GM * GK * 2;          // one BF16 operand slice (GN == GM): 16 KiB
-constexpr int GTMEM = 256;                   // two 128 x 128 FP32 accumulators
+constexpr int GM = 128, GN = 128, GK = kPackK;   // output tile and K block
+constexpr int GBOX = GM * GK * 2;               // one 128-row BF16 operand box: 16 KiB
+constexpr int NACC = 4;                         // accumulators = epilogue groups
+constexpr int NEPI = 128;                       // threads of one epilogue group (4 warps)
+constexpr int GTHREADS = 64 + NACC * NEPI;      // 18 warps
+constexpr int GTMEM = NACC * GN;                // four 128 x 128 FP32 accumulators: all 512 columns
 
 template <int S>
-__host__ __device__ constexpr int gstages() { return S == 1 ? 4 : 2; }
+__host__ __device__ constexpr int gstages() { return S == 1 ? 6 : 2; }
 template <int S>
-__host__ __device__ constexpr int stage_bytes() { return 2 * S * GSLICE; }   // A slices, then B slices
+__host__ __device__ constexpr int stage_bytes() { return 2 * S * GBOX; }   // A slices, then B slices
 template <int S>
 __host__ __device__ constexpr int smem_bytes() { return gstages<S>() * stage_bytes<S>() + 1024 + 256; }
 
-// byte offset of (row r, K index c) in a 128-byte-swizzled K-major tile
-// (rows of 64 BF16; the 16-byte chunk index is XORed with r mod 8)
-__device__ __forceinline__ uint32_t sw_off(int r, int c) {
-  return (uint32_t)(r * 128 + ((((c >> 3) ^ (r & 7)) << 4)) + ((c & 7) << 1));
-}
+// box heights and the tensor map of each
+constexpr int kBoxes = 4;
+__host__ __device__ constexpr int box_index(int rows) { return rows <= 16 ? 0 : rows <= 32 ? 1 : rows <= 64 ? 2 : 3; }
+
+struct PackedMaps {
+  CUtensorMap a[kBoxes];
+  CUtensorMap b[kBoxes];
+};
 
 // position of CTA c's walk over the ordered tile list (G CTAs) in round
 // `round`: rounds of G tiles, alternate rounds reversed
 __device__ __forceinline__ int64_t walk(int64_t round, int c, int G) {
   return round * G + ((round & 1) ? (G - 1 - c) : c);
-}
-
-// this thread's 16 rows (pw + 8 i) x 2 K columns (2 lane, 2 lane + 1) of a
-// K-contiguous operand tile: rows [row0, row0 + 128) of op(X), K [l0, l0 + 64)
-__device__ __forceinline__ void load_pairs(uint32_t (&v)[16], const __nv_bfloat16* X, int64_t ld, int64_t rows,
-                                           int64_t row0, int64_t k, int64_t l0, int pw, int lane) {
-  const int l = (int)l0 + 2 * lane;
-  const unsigned short* p = reinterpret_cast<const unsigned short*>(X) + (row0 + pw) * ld + l;
-  const int nr = (int)(rows - row0), kk = (int)k, step = 8 * (int)ld;
-  // an even leading dimension and an aligned base make each pair one
-  // aligned 32-bit word (l is even)
-  const bool words = ((ld & 1) == 0) && ((reinterpret_cast<uintptr_t>(X) & 3u) == 0);
-#pragma unroll
-  for (int i = 0; i < 16; ++i, p += step) {
-    const int r = pw + 8 * i;
-    uint32_t w = 0u;
-    if (r < nr && l < kk) {
-      if (words && l + 1 < kk) w = *reinterpret_cast<const uint32_t*>(p);
-      else w = (uint32_t)p[0] | ((l + 1 < kk) ? (uint32_t)p[1] << 16 : 0u);
-    }
-    v[i] = w;
-  }
-}
-
-__device__ __forceinline__ void load_pairs(float2 (&v)[16], const float* X, int64_t ld, int64_t rows, int64_t row0,
-                                           int64_t k, int64_t l0, int pw, int lane) {
-  const int l = (int)l0 + 2 * lane;
-  const float* p = X + (row0 + pw) * ld + l;
-  const int nr = (int)(rows - row0), kk = (int)k, step = 8 * (int)ld;
-  const bool pairs = ((ld & 1) == 0) && ((reinterpret_cast<uintptr_t>(X) & 7u) == 0);
-#pragma unroll
-  for (int i = 0; i < 16; ++i, p += step) {
-    const int r = pw + 8 * i;
-    float2 w = make_float2(0.f, 0.f);
-    if (r < nr && l < kk) {
-      if (pairs && l + 1 < kk) w = *reinterpret_cast<const float2*>(p);
-      else { w.x = p[0]; w.y = (l + 1 < kk) ? p[1] : 0.f; }
-    }
-    v[i] = w;
-  }
 }
 
 // x = s0 + s1 + s2 exactly, each a BF16: s0 = RN(x), s1 = RN(x - s0), s2 =
@@ -120,29 +94,96 @@ __device__ __forceinline__ void split3_rn(float x, uint16_t (&sl)[3]) {
   sl[2] = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
 }
 
-// the row lines of the next K block into L2 (lanes 0..15: the 16 rows of this warp)
-__device__ __forceinline__ void prefetch_rows(const void* X, int64_t ld, int64_t es, int64_t rows, int64_t row0,
-                                              int64_t k, int64_t l0, int pw, int lane) {
-  if (lane >= 16 || l0 >= k) return;
-  const int r = pw + 8 * lane;
-  if (r >= rows - row0) return;
-  const char* a = static_cast<const char*>(X) + ((row0 + r) * ld + l0) * es;
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
-}
+// ---------------------------------------------------------------------------
+// pack: block 2 g + op packs operand op (0: op(A), 1: op(B)^T) of problem g.
+// Its packed rows f = kb R + r (K block kb, row r) lie at p_g + f: warp w
+// takes the runs of PU consecutive f starting at PU (w + 8 i), PU loads in
+// flight per lane; lane l holds K columns 2 l and 2 l + 1 of the row.
+// ---------------------------------------------------------------------------
+constexpr int PU = 8;
 
 template <typename AT, int S>
-__global__ void __launch_bounds__(GTHREADS, 1) grouped_tc_kernel(const __grid_constant__ GroupedArgs g) {
+__global__ void __launch_bounds__(256) grouped_pack_kernel(const __grid_constant__ GroupedArgs g) {
+  const int64_t pi = blockIdx.x >> 1;
+  const int op = blockIdx.x & 1;
+  if (pi >= g.count) return;
+  const GroupedProblem& P = g.probs[pi];
+  const int64_t R = op ? P.n : P.m, K = P.k;
+  if (R <= 0 || K <= 0) return;
+  const AT* X = static_cast<const AT*>(op ? P.B : P.A);
+  const int64_t ld = op ? P.ldb : P.lda;
+  const int64_t p0 = op ? P.pb : P.pa;
+  const int64_t rows = op ? g.rows_b : g.rows_a;
+  uint32_t* out = static_cast<uint32_t*>(op ? g.pack_b : g.pack_a);   // pairs of BF16
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t total = R * ((K + GK - 1) / GK);
+  // element pairs (2 l, 2 l + 1) in one aligned load when every row start is even
+  const bool words = sizeof(AT) == 2 && (ld & 1) == 0 && (reinterpret_cast<uintptr_t>(X) & 3u) == 0;
+  const bool pairs = sizeof(AT) == 4 && (ld & 1) == 0 && (reinterpret_cast<uintptr_t>(X) & 7u) == 0;
+  for (int64_t f0 = (int64_t)PU * warp; f0 < total; f0 += (int64_t)PU * 8) {
+    int64_t kb = f0 / R, r = f0 - kb * R;
+    float x0[PU], x1[PU];
+    uint32_t wv[PU];
+#pragma unroll
+    for (int u = 0; u < PU; ++u) {
+      x0[u] = x1[u] = 0.f;
+      wv[u] = 0u;
+      const int64_t c = kb * GK + 2 * lane;
+      if (f0 + u < total && c < K) {
+        const bool v1 = c + 1 < K;
+        const AT* src = X + r * ld + c;
+        if constexpr (sizeof(AT) == 2) {
+          if (words && v1) {
+            wv[u] = __ldg(reinterpret_cast<const unsigned int*>(src));
+          } else {
+            const unsigned short* h = reinterpret_cast<const unsigned short*>(src);
+            wv[u] = (uint32_t)__ldg(h) | (v1 ? (uint32_t)__ldg(h + 1) << 16 : 0u);
+          }
+        } else {
+          if (pairs && v1) {
+            const float2 f = __ldg(reinterpret_cast<const float2*>(src));
+            x0[u] = f.x;
+            x1[u] = f.y;
+          } else {
+            x0[u] = __ldg(reinterpret_cast<const float*>(src));
+            x1[u] = v1 ? __ldg(reinterpret_cast<const float*>(src) + 1) : 0.f;
+          }
+        }
+      }
+      if (++r == R) { r = 0; ++kb; }
+    }
+#pragma unroll
+    for (int u = 0; u < PU; ++u) {
+      if (f0 + u >= total) break;
+      const int64_t row = p0 + f0 + u;
+      if constexpr (S == 1) {
+        out[row * (GK / 2) + lane] = wv[u];
+      } else {
+        uint16_t s0[3], s1[3];
+        split3_rn(x0[u], s0);
+        split3_rn(x1[u], s1);
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl)
+          out[((int64_t)sl * rows + row) * (GK / 2) + lane] = (uint32_t)s0[sl] | ((uint32_t)s1[sl] << 16);
+      }
+    }
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(GTHREADS, 1)
+    grouped_packed_kernel(const __grid_constant__ GroupedArgs g, const __grid_constant__ PackedMaps maps) {
   constexpr int STAGES = gstages<S>();
   constexpr int SB = stage_bytes<S>();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * SB);
-  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], done
+  // bars: full[STAGES], empty[STAGES], tfull[NACC], tempty[NACC], done
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
-  const uint32_t tfull0 = smem_u32(bars + 2 * STAGES), tempty0 = smem_u32(bars + 2 * STAGES + 2);
-  const uint32_t done_bar = smem_u32(bars + 2 * STAGES + 4);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  const uint32_t tfull0 = smem_u32(bars + 2 * STAGES), tempty0 = smem_u32(bars + 2 * STAGES + NACC);
+  const uint32_t done_bar = smem_u32(bars + 2 * STAGES + 2 * NACC);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2 * NACC + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = gridDim.x, c = blockIdx.x;
@@ -150,10 +191,10 @@ __global__ void __launch_bounds__(GTHREADS, 1) grouped_tc_kernel(const __grid_co
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(full0 + 8 * s, NPROD);
+      mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < NACC; ++a) {
       mbar_init(tfull0 + 8 * a, 1);
       mbar_init(tempty0 + 8 * a, NEPI);
     }
@@ -161,7 +202,7 @@ __global__ void __launch_bounds__(GTHREADS, 1) grouped_tc_kernel(const __grid_co
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == MMA_WARP) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(GTMEM)
                  : "memory");
@@ -172,69 +213,50 @@ __global__ void __launch_bounds__(GTHREADS, 1) grouped_tc_kernel(const __grid_co
   fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  if (warp < MMA_WARP) {
-    // ------------------------------------------------------------ producers
-    // group grp takes the K blocks q = grp, grp + NGROUP, ... of this CTA's
-    // sequence; block q uses stage q % STAGES in its (q / STAGES)-th round
-    const int pw = warp & 7, grp = warp >> 3;
-    int64_t q = 0;
-    bool ok = true;
-    for (int64_t rd = 0; rd < rounds && ok; ++rd) {
-      const int64_t pos = walk(rd, c, G);
-      if (pos >= g.tiles) continue;
-      const GroupedTile pb = g.recs[pos];
-      const int64_t i0 = (int64_t)pb.tm * GM, j0 = (int64_t)pb.tn * GN;
-      const AT* A = static_cast<const AT*>(pb.A);
-      const AT* B = static_cast<const AT*>(pb.B);
-      const int64_t nkb = (pb.k + GK - 1) / GK;
-      for (int64_t kb = 0; kb < nkb; ++kb, ++q) {
-        if ((int)(q % NGROUP) != grp) continue;
-        if (kb + NGROUP < nkb) {
-          prefetch_rows(A, pb.lda, (int64_t)sizeof(AT), pb.m, i0, pb.k, (kb + NGROUP) * GK, pw, lane);
-          prefetch_rows(B, pb.ldb, (int64_t)sizeof(AT), pb.n, j0, pb.k, (kb + NGROUP) * GK, pw, lane);
-        }
-        const int stage = (int)(q % STAGES);
-        const uint32_t phase = (uint32_t)((q / STAGES) & 1);
-        // the stage's previous MMAs have finished reading it
-        ok = __all_sync(0xffffffffu, mbar_wait(empty0 + 8 * stage, phase ^ 1u, abort));
-        if (!ok) break;
-        unsigned char* sA = smem + stage * SB;
-        unsigned char* sB = sA + S * GSLICE;
-        if constexpr (S == 1) {
-          uint32_t va[16], vb[16];
-          load_pairs(va, A, pb.lda, pb.m, i0, pb.k, kb * GK, pw, lane);
-          load_pairs(vb, B, pb.ldb, pb.n, j0, pb.k, kb * GK, pw, lane);
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      for (int i = 0; i < kBoxes; ++i) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a[i])) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b[i])) : "memory");
+      }
+      int64_t q = 0;   // K blocks issued: stage q % STAGES in round q / STAGES
+      bool ok = true;
+      for (int64_t rd = 0; rd < rounds && ok; ++rd) {
+        const int64_t pos = walk(rd, c, G);
+        if (pos >= g.tiles) continue;
+        const GroupedTile& pb = g.recs[pos];
+        const int32_t ya = pb.ya, yb = pb.yb, sa = pb.sa, sb = pb.sb, kk = pb.k;
+        const int ha = pb.ha, hb = pb.hb;
+        const int ia = box_index(ha), ib = box_index(hb);
+        const uint32_t bytes = (uint32_t)(S * (ha + hb) * GK * 2);
+        const int64_t nkb = (kk + GK - 1) / GK;
+        for (int64_t kb = 0; kb < nkb; ++kb, ++q) {
+          const int stage = (int)(q % STAGES);
+          const uint32_t phase = (uint32_t)((q / STAGES) & 1);
+          if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, abort)) { ok = false; break; }
+          const uint32_t sA = smem_u32(smem + stage * SB), sBb = sA + S * GBOX;
+          mbar_expect_tx(full0 + 8 * stage, bytes);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            *reinterpret_cast<uint32_t*>(sA + sw_off(pw + 8 * i, 2 * lane)) = va[i];
-            *reinterpret_cast<uint32_t*>(sB + sw_off(pw + 8 * i, 2 * lane)) = vb[i];
-          }
-        } else {
-          // FP32: exact three-slice split
-#pragma unroll
-          for (int op = 0; op < 2; ++op) {
-            float2 v[16];
-            if (op == 0) load_pairs(v, reinterpret_cast<const float*>(A), pb.lda, pb.m, i0, pb.k, kb * GK, pw, lane);
-            else load_pairs(v, reinterpret_cast<const float*>(B), pb.ldb, pb.n, j0, pb.k, kb * GK, pw, lane);
-            unsigned char* dst = op == 0 ? sA : sB;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              uint16_t x0[3], x1[3];
-              split3_rn(v[i].x, x0);
-              split3_rn(v[i].y, x1);
-              const uint32_t off = sw_off(pw + 8 * i, 2 * lane);
-#pragma unroll
-              for (int sl = 0; sl < 3; ++sl)
-                *reinterpret_cast<uint32_t*>(dst + sl * GSLICE + off) = (uint32_t)x0[sl] | ((uint32_t)x1[sl] << 16);
-            }
+          for (int sl = 0; sl < S; ++sl) {
+            tma_load_2d(sA + sl * GBOX, &maps.a[ia], full0 + 8 * stage, 0,
+                        (int32_t)(ya + kb * sa + (int64_t)sl * g.rows_a));
+            tma_load_2d(sBb + sl * GBOX, &maps.b[ib], full0 + 8 * stage, 0,
+                        (int32_t)(yb + kb * sb + (int64_t)sl * g.rows_b));
           }
         }
-        // generic-proxy stores become visible to the tensor core, then arrive
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(full0 + 8 * stage);
+      }
+      // copies still in flight land before the CTA leaves: the last use of
+      // each stage has completed (bounded)
+      for (int64_t u = q - 1; u >= 0 && u >= q - STAGES; --u) {
+        const int stage = (int)(u % STAGES);
+        const uint32_t phase = (uint32_t)((u / STAGES) & 1);
+        for (uint32_t i = 0; i < WAIT_LIMIT && !mbar_try(full0 + 8 * stage, phase); ++i) {
+        }
       }
     }
-  } else if (warp == MMA_WARP) {
+    __syncwarp();
+  } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(GM, GN);
@@ -254,18 +276,18 @@ __global__ void __launch_bounds__(GTHREADS, 1) grouped_tc_kernel(const __grid_co
           if (!mbar_wait(full0 + 8 * stage, phase, abort)) { ok = false; break; }
           fence_after();
           const uint64_t ad = sw128_desc(smem_u32(smem + stage * SB));
-          const uint64_t bd = sw128_desc(smem_u32(smem + stage * SB + S * GSLICE));
+          const uint64_t bd = sw128_desc(smem_u32(smem + stage * SB + S * GBOX));
           constexpr int NT = S == 1 ? 1 : 6;
 #pragma unroll
           for (int term = 0; term < NT; ++term) {
             // split products smallest first: (2,0) (1,1) (0,2) (1,0) (0,1) (0,0)
             const int sa = S == 1 ? 0 : (term == 0 ? 2 : term == 1 ? 1 : term == 2 ? 0 : term == 3 ? 1 : 0);
             const int sb = S == 1 ? 0 : (term == 0 ? 0 : term == 1 ? 1 : term == 2 ? 2 : term == 3 ? 0 : term == 4 ? 1 : 0);
-            const uint64_t a0 = ad + (uint64_t)((sa * GSLICE) >> 4), b0 = bd + (uint64_t)((sb * GSLICE) >> 4);
+            const uint64_t a0 = ad + (uint64_t)((sa * GBOX) >> 4), b0 = bd + (uint64_t)((sb * GBOX) >> 4);
 #pragma unroll
-            for (int kk = 0; kk < GK / 16; ++kk)
-              mma_bf16(dcol, a0 + (uint64_t)(2 * kk), b0 + (uint64_t)(2 * kk), idesc,
-                       (kb > 0 || term > 0 || kk > 0) ? 1u : 0u);
+            for (int k16 = 0; k16 < GK / 16; ++k16)
+              mma_bf16(dcol, a0 + (uint64_t)(2 * k16), b0 + (uint64_t)(2 * k16), idesc,
+                       (kb > 0 || term > 0 || k16 > 0) ? 1u : 0u);
           }
           mma_commit(empty0 + 8 * stage);    // frees the stage when these MMAs finish
           issued = true;
@@ -273,7 +295,7 @@ __global__ void __launch_bounds__(GTHREADS, 1) grouped_tc_kernel(const __grid_co
         }
         if (!ok) break;
         mma_commit(tfull0 + 8 * acc);         // the tile's accumulator is complete
-        if (++acc == 2) { acc = 0; aphase ^= 1u; }
+        if (++acc == NACC) { acc = 0; aphase ^= 1u; }
       }
       if (issued) {
         mma_commit(done_bar);
@@ -284,79 +306,86 @@ __global__ void __launch_bounds__(GTHREADS, 1) grouped_tc_kernel(const __grid_co
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
-    // warp w: TMEM lane quarter w % 4 (tile rows 32 (w % 4) ..) and column
-    // half (w - 17) / 4; each thread owns one row and 64 columns
+    // group e = (w - 2) / 4 drains accumulator e, i.e. the tiles i = e
+    // (mod NACC) of this CTA's sequence; warp w reads TMEM lane quarter
+    // w % 4 (tile rows 32 (w % 4) ..): each thread owns one row, 128 columns
     const int q = warp & 3;
-    const int half = (warp - (MMA_WARP + 1)) >> 2;
+    const int e = (warp - 2) >> 2;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    int acc = 0;
+    const uint32_t acc_col = (uint32_t)(e * GN);
     uint32_t aphase = 0;
-    bool ok = true;
-    for (int64_t rd = 0; rd < rounds && ok; ++rd) {
+    int64_t i = -1;   // index of the tile in this CTA's sequence
+    for (int64_t rd = 0; rd < rounds; ++rd) {
       const int64_t pos = walk(rd, c, G);
       if (pos >= g.tiles) continue;
+      if ((++i) % NACC != e) continue;
       const GroupedTile pb = g.recs[pos];
       const int64_t t = pb.t;
       const int tm = pb.tm, tn = pb.tn;
-      const int64_t i0 = (int64_t)tm * GM, j0 = (int64_t)tn * GN + 64 * half;
+      const int64_t i0 = (int64_t)tm * GM, j0 = (int64_t)tn * GN;
       const int64_t row = i0 + 32 * q + lane;
       const bool row_ok = row < pb.m;
       const bool has_c = pb.C && g.beta != 0.0;
-      const int ncol = (int)(pb.n - j0 < 64 ? pb.n - j0 : 64);   // may be <= 0
-      // this warp's block of C into L2 while the tile's MMAs run: lane j,
-      // columns j and j + 32
+      const int ncol = (int)(pb.n - j0 < GN ? pb.n - j0 : GN);
+      // the C lines of this warp's 32 rows into L2 while the tile's MMAs run
+      // (lane l: columns l, l + 32, l + 64, l + 96)
       if (has_c && i0 + 32 * q < pb.m) {
         const int64_t es = g.cdt == ARMA_F64 ? 8 : g.cdt == ARMA_F32 ? 4 : 2;
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
+        for (int u = 0; u < 4; ++u)
           if (lane + 32 * u < ncol)
             asm volatile("prefetch.global.L2 [%0];" ::"l"(static_cast<const char*>(pb.C) +
-                                                          ((i0 + 32 * q) + (j0 + lane + 32 * u) * pb.ldc) * es));
+                                                          ((i0 + 32 * q) + (j0 + lane + 32 * u) * (int64_t)pb.ldc) * es));
       }
-      ok = __all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * acc, aphase, abort));
-      if (!ok) break;
+      if (!__all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * e, aphase, abort))) break;
+      aphase ^= 1u;
       fence_after();
-      const bool any_k = pb.k > 0;
-      float* Dr = static_cast<float*>(pb.D) + row + j0 * (int64_t)pb.m;
-      const int ldc = pb.ldc, ldd = pb.m;
-      const int diag = (int)(row - j0);
       double dsum = 0.0;
-      // 16 columns at a time: the TMEM load, then all 16 C loads, then D
-      // (D may be C itself, so C is read before D is written)
+      float* Dr = static_cast<float*>(pb.D) + row + j0 * (int64_t)pb.m;
+      const int diag = (int)(row - j0);
 #pragma unroll 1
-      for (int c0 = 0; c0 < 64 && c0 < ncol; c0 += 16) {
+      for (int c0 = 0; c0 < ncol; c0 += 16) {
         float v[16];
-        if (any_k) {
-          tmem_ld16(tmem_base + lane_base + (uint32_t)(acc * GN + 64 * half + c0), v);
+        if (pb.k > 0) {
+          tmem_ld16(tmem_base + lane_base + acc_col + (uint32_t)c0, v);
         } else {
 #pragma unroll
           for (int j = 0; j < 16; ++j) v[j] = 0.f;
         }
         if (!row_ok) continue;
-        float cv[16];
         if (has_c && g.cdt == ARMA_F32) {
-          const float* Cr = static_cast<const float*>(pb.C) + row + (j0 + c0) * pb.ldc;
+          // all 16 C values before any D (D may be C itself)
+          const float* Cr = static_cast<const float*>(pb.C) + row + (j0 + c0) * (int64_t)pb.ldc;
+          float cv[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) cv[j] = c0 + j < ncol ? Cr[j * ldc] : 0.f;
+          for (int j = 0; j < 16; ++j) cv[j] = c0 + j < ncol ? __ldg(Cr + (int64_t)j * pb.ldc) : 0.f;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if (c0 + j >= ncol) break;
+            if (c0 + j == diag) dsum += (double)v[j];
+            Dr[(int64_t)(c0 + j) * pb.m] = fmaf(g.beta_f, cv[j], g.alpha_f * v[j]);
+          }
         } else {
+          // no C, or C of another type: element by element (D is FP32, so
+          // it is never C itself here)
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            cv[j] = (has_c && c0 + j < ncol) ? load_as<float>(pb.C, row + (j0 + c0 + j) * pb.ldc, g.cdt) : 0.f;
-        }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          if (c0 + j >= ncol) continue;
-          if (c0 + j == diag) dsum += (double)v[j];
-          Dr[(c0 + j) * ldd] = fmaf(g.beta_f, cv[j], g.alpha_f * v[j]);
+          for (int j = 0; j < 16; ++j) {
+            if (c0 + j >= ncol) break;
+            if (c0 + j == diag) dsum += (double)v[j];
+            const float cj = has_c ? load_as<float>(pb.C, row + (j0 + c0 + j) * (int64_t)pb.ldc, g.cdt) : 0.f;
+            Dr[(int64_t)(c0 + j) * pb.m] = fmaf(g.beta_f, cj, g.alpha_f * v[j]);
+          }
         }
       }
       // the accumulator is free for the MMA issuer again
       fence_before();
-      mbar_arrive(tempty0 + 8 * acc);
-      if (++acc == 2) { acc = 0; aphase ^= 1u; }
+      mbar_arrive(tempty0 + 8 * e);
       if (g.trace_partials && tm == tn) {     // diagonal tile: each warp's share of the trace
         dsum = warp_sum(dsum);
-        if (lane == 0) g.trace_partials[kTraceSlots * t + 4 * half + q] = dsum;
+        if (lane == 0) {
+          g.trace_partials[kTraceSlots * t + q] = dsum;
+          g.trace_partials[kTraceSlots * t + 4 + q] = 0.0;
+        }
       }
     }
   }
@@ -364,244 +393,61 @@ __global__ void __launch_bounds__(GTHREADS, 1) grouped_tc_kernel(const __grid_co
   fence_before();
   __syncthreads();
   if (threadIdx.x == 0 && *abort && g.status) atomicCAS(g.status, 0, (int32_t)ARMA_ERR_TIMEOUT);
-  if (warp == MMA_WARP) {
+  if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(GTMEM) : "memory");
   }
 }
 
-// ---------------------------------------------------------------------------
-// BF16 operands: every warp of the CTA loads, one thread issues the MMAs and
-// every warp drains the accumulator; two CTAs per SM, each with two stages
-// so that the loads of K block k + 1 overlap the MMAs of block k.  CTAs take
-// tiles from a shared counter over the ordered list (longest first); the
-// next tile's position and record are fetched while the current tile runs.
-// ---------------------------------------------------------------------------
-constexpr int STHREADS = 256;
-constexpr int SCTAS = 2;                       // CTAs per SM (<= 128 registers per thread)
-constexpr int STMEM = 128;                     // one 128 x 128 FP32 accumulator
-constexpr int SSTAGE = 2 * GSLICE;             // A tile, then B tile
-constexpr int SSMEM = 2 * SSTAGE + 1024 + 256;
-
-__global__ void __launch_bounds__(STHREADS, SCTAS) grouped_tc_serial_kernel(const __grid_constant__ GroupedArgs g) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* smem =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * SSTAGE);   // MMA done, per stage
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
-  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  int* s_pos = reinterpret_cast<int*>(tmem_slot + 2);                // the current tile's position
-  uint4* s_rec = reinterpret_cast<uint4*>(bars + 4);                 // and its record
-  const uint32_t done0 = smem_u32(bars);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint4* recs = reinterpret_cast<const uint4*>(g.recs);
-  if (threadIdx.x == 0) {
-    mbar_init(done0, 1);
-    mbar_init(done0 + 8, 1);
-    *abort = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    int p0 = 0;
-    if (lane == 0) p0 = (int)atomicAdd(g.next_tile, 1u);
-    p0 = __shfl_sync(0xffffffffu, p0, 0);
-    if (lane == 0) *s_pos = p0;
-    if (lane < 4 && p0 < g.tiles) s_rec[lane] = recs[4 * (int64_t)p0 + lane];
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(STMEM)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem_base = *tmem_slot;
-  const uint32_t idesc = idesc_bf16(GM, GN);
-  int64_t issued = 0;   // K blocks issued by this CTA: stage = issued & 1
-  bool ok = true;
-  while (ok) {
-    const int64_t pos = *s_pos;
-    if (pos >= g.tiles) break;
-    GroupedTile pb;
-    *reinterpret_cast<uint4*>(&pb) = s_rec[0];
-    reinterpret_cast<uint4*>(&pb)[1] = s_rec[1];
-    reinterpret_cast<uint4*>(&pb)[2] = s_rec[2];
-    reinterpret_cast<uint4*>(&pb)[3] = s_rec[3];
-    const int64_t i0 = (int64_t)pb.tm * GM, j0 = (int64_t)pb.tn * GN;
-    const __nv_bfloat16* A = static_cast<const __nv_bfloat16*>(pb.A);
-    const __nv_bfloat16* B = static_cast<const __nv_bfloat16*>(pb.B);
-    const int64_t nkb = (pb.k + GK - 1) / GK;
-    uint32_t ra[16], rb[16];
-    if (nkb > 0) {
-      load_pairs(ra, A, pb.lda, pb.m, i0, pb.k, 0, warp, lane);
-      load_pairs(rb, B, pb.ldb, pb.n, j0, pb.k, 0, warp, lane);
-    }
-    // the next tile's position and record, in flight during this tile
-    // (after this warp's first loads, so that they overlap)
-    int npos = 0;
-    uint4 nrec = make_uint4(0u, 0u, 0u, 0u);
-    if (warp == 0) {
-      if (lane == 0) npos = (int)atomicAdd(g.next_tile, 1u);
-      npos = __shfl_sync(0xffffffffu, npos, 0);
-      if (lane < 4 && npos < g.tiles) nrec = recs[4 * (int64_t)npos + lane];
-    }
-    for (int64_t kb = 0; kb < nkb; ++kb, ++issued) {
-      const int st = (int)(issued & 1);
-      unsigned char* sA = smem + st * SSTAGE;
-      unsigned char* sB = sA + GSLICE;
-      // the stage's previous MMAs (two K blocks ago) must have finished
-      if (issued >= 2 && !mbar_wait(done0 + 8 * st, (uint32_t)(((issued >> 1) - 1) & 1), abort)) *abort = 1;
-      if (!*abort) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          *reinterpret_cast<uint32_t*>(sA + sw_off(warp + 8 * i, 2 * lane)) = ra[i];
-          *reinterpret_cast<uint32_t*>(sB + sw_off(warp + 8 * i, 2 * lane)) = rb[i];
-        }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic stores -> tensor core
-      if (__syncthreads_or(*abort != 0)) { ok = false; break; }
-      if (threadIdx.x == 0) {
-        fence_after();
-        const uint64_t ad = sw128_desc(smem_u32(sA)), bd = sw128_desc(smem_u32(sB));
-#pragma unroll
-        for (int kk = 0; kk < GK / 16; ++kk)
-          mma_bf16(tmem_base, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-        mma_commit(done0 + 8 * st);
-      }
-      // the next block's loads overlap these MMAs
-      if (kb + 1 < nkb) {
-        load_pairs(ra, A, pb.lda, pb.m, i0, pb.k, (kb + 1) * GK, warp, lane);
-        load_pairs(rb, B, pb.ldb, pb.n, j0, pb.k, (kb + 1) * GK, warp, lane);
-      }
-    }
-    if (!ok) break;
-    // while the last MMAs run: this warp's block of C (32 rows x 64 columns)
-    // into L2
-    const bool has_c = pb.C && g.beta != 0.0;
-    {
-      const int q = warp & 3, h = warp >> 2;
-      if (has_c && i0 + 32 * q < pb.m) {
-        const int64_t es = g.cdt == ARMA_F64 ? 8 : g.cdt == ARMA_F32 ? 4 : 2;
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int64_t col = j0 + 64 * h + 32 * u + lane;
-          if (col < pb.n)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(static_cast<const char*>(pb.C) +
-                                                          ((i0 + 32 * q) + col * pb.ldc) * es));
-        }
-      }
-    }
-    // accumulator complete: the last commit covers every earlier MMA
-    if (nkb > 0) {
-      const int64_t last = issued - 1;
-      if (!mbar_wait(done0 + 8 * (int)(last & 1), (uint32_t)((last >> 1) & 1), abort)) *abort = 1;
-      if (__syncthreads_or(*abort != 0)) { ok = false; break; }
-      fence_after();
-    }
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows) and
-    // columns 64 (w / 4) .. +63
-    const int q = warp & 3, h = warp >> 2;
-    const int64_t row = i0 + 32 * q + lane;
-    const bool row_ok = row < pb.m;
-    float* Dr = static_cast<float*>(pb.D) + row + (j0 + 64 * h) * (int64_t)pb.m;
-    const int ncol = (int)(pb.n - (j0 + 64 * h));
-    const int diag = (int)(row - (j0 + 64 * h));
-    double dsum = 0.0;
-#pragma unroll 1
-    for (int c0 = 0; c0 < 64 && c0 < ncol; c0 += 16) {
-      float v[16];
-      if (nkb > 0) {
-        tmem_ld16(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * h + c0), v);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = 0.f;
-      }
-      if (!row_ok) continue;
-      // all 16 C values before any D (D may be C itself)
-      float cv[16];
-      if (has_c && g.cdt == ARMA_F32) {
-        const float* Cr = static_cast<const float*>(pb.C) + row + (j0 + 64 * h + c0) * (int64_t)pb.ldc;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) cv[j] = c0 + j < ncol ? Cr[j * pb.ldc] : 0.f;
-      } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          cv[j] = (has_c && c0 + j < ncol) ? load_as<float>(pb.C, row + (j0 + 64 * h + c0 + j) * pb.ldc, g.cdt) : 0.f;
-      }
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        if (c0 + j >= ncol) continue;
-        if (c0 + j == diag) dsum += (double)v[j];
-        Dr[(c0 + j) * pb.m] = fmaf(g.beta_f, cv[j], g.alpha_f * v[j]);
-      }
-    }
-    if (g.trace_partials && pb.tm == pb.tn) {   // diagonal tile: its share of the trace
-      double qq = 0.0;
-      block_sum2(dsum, qq);
-      if (threadIdx.x == 0) {
-        g.trace_partials[(int64_t)kTraceSlots * pb.t] = dsum;
-        for (int k = 1; k < kTraceSlots; ++k) g.trace_partials[(int64_t)kTraceSlots * pb.t + k] = 0.0;
-      }
-    }
-    // TMEM reads finish before the next tile's MMAs overwrite the
-    // accumulator; the next record replaces the current one
-    fence_before();
-    __syncthreads();
-    if (threadIdx.x < 4) s_rec[threadIdx.x] = nrec;
-    if (threadIdx.x == 0) *s_pos = npos;
-    __syncthreads();
-    fence_after();
-  }
-  // every issued MMA completes before TMEM is released
-  if (issued > 0 && threadIdx.x == 0) {
-    const int64_t last = issued - 1;
-    for (uint32_t i = 0; i < WAIT_LIMIT && !mbar_try(done0 + 8 * (int)(last & 1), (uint32_t)((last >> 1) & 1)); ++i) {
-    }
-  }
-  fence_before();
-  __syncthreads();
-  if (threadIdx.x == 0 && *abort && g.status) atomicCAS(g.status, 0, (int32_t)ARMA_ERR_TIMEOUT);
-  if (warp == 0) {
-    fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(STMEM) : "memory");
-  }
-}
-
-cudaError_t launch_tc_serial(const GroupedArgs& g, cudaStream_t s, int* launches) {
-  static std::atomic<bool> attr[64];
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (!attr[dev].load(std::memory_order_acquire)) {
-    cudaError_t e = cudaFuncSetAttribute(grouped_tc_serial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SSMEM);
-    if (e != cudaSuccess) return e;
-    attr[dev].store(true, std::memory_order_release);
-  }
-  int64_t grid = (int64_t)device_sm_count() * SCTAS;
-  if (grid > g.tiles) grid = g.tiles;
-  grouped_tc_serial_kernel<<<(unsigned)grid, STHREADS, SSMEM, s>>>(g);
-  if (launches) ++*launches;
-  return cudaGetLastError();
+// a packed array as a 2-D BF16 tensor of `rows` rows of 64, read in boxes of
+// box_rows x 64 with the 128-byte swizzle the MMA descriptors expect
+bool make_packed_map(CUtensorMap* map, const void* base, int64_t rows, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn || rows < 1) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)GK, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(GK * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)GK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 template <typename AT, int S>
-cudaError_t launch_tc(const GroupedArgs& g, cudaStream_t s, int* launches) {
+cudaError_t launch_packed(const GroupedArgs& g, cudaStream_t s, int* launches) {
+  if (g.slices != S) return cudaErrorInvalidValue;
+  const bool any = g.rows_a > 0 && g.rows_b > 0;   // some problem has K > 0
+  if (any && (!g.pack_a || !g.pack_b)) return cudaErrorInvalidValue;
+  // 1. pack
+  if (any) {
+    if (2 * g.count > (int64_t)INT32_MAX) return cudaErrorInvalidConfiguration;
+    grouped_pack_kernel<AT, S><<<(unsigned)(2 * g.count), 256, 0, s>>>(g);
+    if (launches) ++*launches;
+  }
+  // 2. the products (with no K anywhere no box is ever loaded)
+  PackedMaps maps;
+  memset(&maps, 0, sizeof maps);
+  if (any) {
+    for (int i = 0; i < kBoxes; ++i) {
+      if (!make_packed_map(&maps.a[i], g.pack_a, (int64_t)S * g.rows_a, 16 << i)) return cudaErrorInvalidValue;
+      if (!make_packed_map(&maps.b[i], g.pack_b, (int64_t)S * g.rows_b, 16 << i)) return cudaErrorInvalidValue;
+    }
+  }
   constexpr int smem = smem_bytes<S>();
   static std::atomic<bool> attr[64];
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
   if (!attr[dev].load(std::memory_order_acquire)) {
-    cudaError_t e = cudaFuncSetAttribute(grouped_tc_kernel<AT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(grouped_packed_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr[dev].store(true, std::memory_order_release);
   }
   // one CTA per SM, each walking its share of the tile list
   int64_t grid = (int64_t)device_sm_count();
   if (grid > g.tiles) grid = g.tiles;
-  grouped_tc_kernel<AT, S><<<(unsigned)grid, GTHREADS, smem, s>>>(g);
+  grouped_packed_kernel<S><<<(unsigned)grid, GTHREADS, smem, s>>>(g, maps);
   if (launches) ++*launches;
   return cudaGetLastError();
 }
@@ -611,8 +457,8 @@ cudaError_t launch_tc(const GroupedArgs& g, cudaStream_t s, int* launches) {
 cudaError_t launch_grouped_tc(const GroupedArgs& g, cudaStream_t s, int* launches) {
   if (g.tiles == 0) return cudaSuccess;
   if (!g.recs) return cudaErrorInvalidValue;
-  if (g.abdt == ARMA_BF16) return launch_tc_serial(g, s, launches);
-  if (g.abdt == ARMA_F32) return launch_tc<float, 3>(g, s, launches);
+  if (g.abdt == ARMA_BF16) return launch_packed<__nv_bfloat16, 1>(g, s, launches);
+  if (g.abdt == ARMA_F32) return launch_packed<float, 3>(g, s, launches);
   return cudaErrorInvalidValue;
 }
 

@@ -1750,6 +1750,13 @@ arma_status plan_batched(const arma_expr* exprs, int32_t count, arma_plan* p) {
     const int32_t T = b.tc ? 128 : (fl & ARMA_PLAN_TILE64) ? 64 : (fl & ARMA_PLAN_TILE32) ? 32 : (t32 < 2 * t64) ? 32 : 64;
     b.tile.push_back(T);
     b.first_tile.push_back(b.tiles);
+    if (b.tc) {   // packed rows: K blocks of 64, each holding the problem's op(A) / op(B)^T rows
+      const int64_t nkb = (g.k + 63) / 64;
+      b.pa.push_back(b.rows_a);
+      b.pb.push_back(b.rows_b);
+      b.rows_a += g.m * nkb;
+      b.rows_b += g.n * nkb;
+    }
     const int64_t ntm = (g.m + T - 1) / T, ntn = (g.n + T - 1) / T;
     if (ntm > 65535 || ntn > 65535) return ARMA_ERR_UNSUPPORTED;
     for (int64_t tm = 0; tm < ntm; ++tm)
@@ -1777,6 +1784,14 @@ arma_status plan_batched(const arma_expr* exprs, int32_t count, arma_plan* p) {
   if (b.tiles > INT32_MAX) return ARMA_ERR_UNSUPPORTED;
   p->batched = true;
   p->ws_bytes = kHeaderBytes + (size_t)((b.tiles * 8 * 8 + 255) / 256 * 256);   // 8 trace partials per tile
+  if (b.tc) {
+    // the packed operands (TMA reads them with 32-bit row coordinates)
+    b.slices = b.abdt == ARMA_BF16 ? 1 : 3;
+    if ((int64_t)b.slices * std::max(b.rows_a, b.rows_b) + 128 > INT32_MAX) return ARMA_ERR_UNSUPPORTED;
+    b.pack_off = (p->ws_bytes + 1023) / 1024 * 1024;
+    b.pack_bytes = (size_t)b.slices * (size_t)(b.rows_a + b.rows_b) * 128;
+    p->ws_bytes = b.pack_off + b.pack_bytes;
+  }
   std::ostringstream os;
   os.precision(17);
   os << "{\"mode\": \"batched\", \"count\": " << count << ", \"tiles\": " << b.tiles

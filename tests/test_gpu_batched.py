@@ -207,3 +207,36 @@ def test_batched_autotune(torch, dtype):
         check_instance(*inst[i], host[i], outs[i], dtype)
     bp2, times2 = autotune.tune(inst, ins, outs, "cuda", reps=2)
     assert len(times2) == 1 and list(times2)[0] == min(times, key=times.get)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_batched_strided_unaligned_operands(torch, dtype):
+    """operands as views with leading dimensions larger than K (even and
+    odd) and bases one element off alignment: the tensor-core path packs
+    them whatever their strides, and meets the oracle"""
+    shapes = [(37, 45, 70), (130, 20, 129), (5, 200, 64), (64, 64, 1), (200, 150, 300), (17, 130, 66)]
+    inst, host, ins, outs = [], [], [], []
+    for i, (m, n, k) in enumerate(shapes):
+        pa, pb = (1, 3, 8, 0, 5, 2)[i], (2, 0, 1, 7, 4, 9)[i]
+        g = E.Graph()
+        A = g.input(0, k, m, dtype, ld=k + pa)
+        B = g.input(1, k, n, dtype, ld=k + pb)
+        C = g.input(2, m, n, "f32")
+        nodes, o = g.build(2 * A.t() * B + C, E.trace(A.t() * B))
+        inst.append((nodes, o))
+        Ah = synth.matrix(1200 + i, 1, k, m, dtype)
+        Bh = synth.matrix(1200 + i, 2, k, n, dtype)
+        Ch = synth.matrix(1200 + i, 3, m, n, "f32")
+        host.append([Ah, Bh, Ch])
+        ins.append([to_dev(Ah, dtype, pad=pa, offset=1), to_dev(Bh, dtype, pad=pb, offset=i % 2),
+                    to_dev(Ch, "f32")])
+        outs.append([ag.empty_colmajor(m, n, torch.float32, "cuda"),
+                     torch.zeros(1, dtype=torch.float64, device="cuda")])
+    bp = ag.BatchedPlan(inst)
+    assert bp.info["tensor_cores"] is True
+    bp.bind(ins, outs, "cuda")
+    bp()
+    torch.cuda.synchronize()
+    assert bp.status()[0] == "ok"
+    for i in range(len(inst)):
+        check_instance(*inst[i], host[i], outs[i], dtype)
