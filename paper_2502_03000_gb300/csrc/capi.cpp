@@ -352,7 +352,7 @@ arma_status arma_gpu_plan_batched(const arma_expr* exprs, int32_t count, arma_pl
 }
 
 static size_t table_layout(const BatchedInfo& b, size_t* probs_off, size_t* prob_off, size_t* code_off,
-                           size_t* order_off, size_t* rec_off = nullptr) {
+                           size_t* order_off, size_t* rec_off = nullptr, size_t* item_off = nullptr) {
   size_t off = 0;
   *probs_off = off;
   off += (size_t)b.count * sizeof(GroupedProblem);
@@ -368,6 +368,9 @@ static size_t table_layout(const BatchedInfo& b, size_t* probs_off, size_t* prob
   off = (off + 255) / 256 * 256;
   if (rec_off) *rec_off = off;
   if (b.tc) off += (size_t)b.tiles * sizeof(GroupedTile);
+  off = (off + 255) / 256 * 256;
+  if (item_off) *item_off = off;
+  if (b.tc) off += b.pack_items.size() * sizeof(int32_t);
   return (off + 255) / 256 * 256;
 }
 
@@ -382,8 +385,8 @@ arma_status arma_gpu_batched_table_fill(const arma_plan* plan, const void* const
                                         void* const* out_ptrs, void* host_table) {
   if (!plan || !plan->batched || !in_ptrs || !out_ptrs || !host_table) return ARMA_ERR_INVALID;
   const BatchedInfo& b = plan->bi;
-  size_t po, pr, pc, pd, pt;
-  table_layout(b, &po, &pr, &pc, &pd, &pt);
+  size_t po, pr, pc, pd, pt, pi;
+  table_layout(b, &po, &pr, &pc, &pd, &pt, &pi);
   char* base = static_cast<char*>(host_table);
   GroupedProblem* probs = reinterpret_cast<GroupedProblem*>(base + po);
   for (int32_t i = 0; i < b.count; ++i) {
@@ -432,6 +435,7 @@ arma_status arma_gpu_batched_table_fill(const arma_plan* plan, const void* const
       r.ha = box(g.m - 128 * (int64_t)r.tm);
       r.hb = box(g.n - 128 * (int64_t)r.tn);
     }
+    std::memcpy(base + pi, b.pack_items.data(), b.pack_items.size() * sizeof(int32_t));
   }
   return ARMA_OK;
 }
@@ -441,8 +445,8 @@ arma_status arma_gpu_eval_batched(const arma_plan* plan, const void* device_tabl
   if (!plan || !plan->batched || !device_table) return ARMA_ERR_INVALID;
   if (!workspace || workspace_bytes < plan->ws_bytes) return ARMA_ERR_WORKSPACE;
   const BatchedInfo& b = plan->bi;
-  size_t po, pr, pc, pd, pt;
-  table_layout(b, &po, &pr, &pc, &pd, &pt);
+  size_t po, pr, pc, pd, pt, pi;
+  table_layout(b, &po, &pr, &pc, &pd, &pt, &pi);
   const char* base = static_cast<const char*>(device_table);
   GroupedArgs g;
   std::memset(&g, 0, sizeof g);
@@ -465,6 +469,8 @@ arma_status arma_gpu_eval_batched(const arma_plan* plan, const void* device_tabl
     g.rows_a = b.rows_a;
     g.rows_b = b.rows_b;
     g.slices = b.slices;
+    g.pack_items = reinterpret_cast<const int32_t*>(base + pi);
+    g.n_items = (int64_t)(b.pack_items.size() / 2);
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // status, info and the tile counter start at zero

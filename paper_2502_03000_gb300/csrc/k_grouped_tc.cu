@@ -95,78 +95,95 @@ __device__ __forceinline__ void split3_rn(float x, uint16_t (&sl)[3]) {
 }
 
 // ---------------------------------------------------------------------------
-// pack: block 2 g + op packs operand op (0: op(A), 1: op(B)^T) of problem g.
-// Its packed rows f = kb R + r (K block kb, row r) lie at p_g + f: warp w
-// takes the runs of PU consecutive f starting at PU (w + 8 i), PU loads in
-// flight per lane; lane l holds K columns 2 l and 2 l + 1 of the row.
+// pack: the work is the host-built list of runs of kPackRun packed rows of
+// one operand (0: op(A), 1: op(B)^T) of one problem; warp w of the grid takes
+// runs w, w + W, ...  Packed row f = kb R + r (K block kb, row r) of a problem
+// lies at p_g + f; PU rows per pass, PU loads in flight per lane; lane l
+// holds K columns 2 l and 2 l + 1 of a row.
 // ---------------------------------------------------------------------------
-constexpr int PU = 8;
+constexpr int PU = 16;
 
 template <typename AT, int S>
-__global__ void __launch_bounds__(256) grouped_pack_kernel(const __grid_constant__ GroupedArgs g) {
-  const int64_t pi = blockIdx.x >> 1;
-  const int op = blockIdx.x & 1;
-  if (pi >= g.count) return;
-  const GroupedProblem& P = g.probs[pi];
-  const int64_t R = op ? P.n : P.m, K = P.k;
-  if (R <= 0 || K <= 0) return;
-  const AT* X = static_cast<const AT*>(op ? P.B : P.A);
-  const int64_t ld = op ? P.ldb : P.lda;
-  const int64_t p0 = op ? P.pb : P.pa;
-  const int64_t rows = op ? g.rows_b : g.rows_a;
-  uint32_t* out = static_cast<uint32_t*>(op ? g.pack_b : g.pack_a);   // pairs of BF16
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t total = R * ((K + GK - 1) / GK);
-  // element pairs (2 l, 2 l + 1) in one aligned load when every row start is even
-  const bool words = sizeof(AT) == 2 && (ld & 1) == 0 && (reinterpret_cast<uintptr_t>(X) & 3u) == 0;
-  const bool pairs = sizeof(AT) == 4 && (ld & 1) == 0 && (reinterpret_cast<uintptr_t>(X) & 7u) == 0;
-  for (int64_t f0 = (int64_t)PU * warp; f0 < total; f0 += (int64_t)PU * 8) {
-    int64_t kb = f0 / R, r = f0 - kb * R;
-    float x0[PU], x1[PU];
-    uint32_t wv[PU];
+__global__ void __launch_bounds__(256, 3) grouped_pack_kernel(const __grid_constant__ GroupedArgs g) {
+  const int lane = threadIdx.x & 31;
+  const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < g.n_items; it += W) {
+    const int32_t code = g.pack_items[2 * it], first = g.pack_items[2 * it + 1];
+    const int64_t pi = code >> 1;
+    const int op = code & 1;
+    const GroupedProblem& P = g.probs[pi];
+    const int64_t R = op ? P.n : P.m, K = P.k;
+    const AT* X = static_cast<const AT*>(op ? P.B : P.A);
+    const int64_t ld = op ? P.ldb : P.lda;
+    const int64_t p0 = op ? P.pb : P.pa;
+    const int64_t rows = op ? g.rows_b : g.rows_a;
+    uint32_t* out = static_cast<uint32_t*>(op ? g.pack_b : g.pack_a);   // pairs of BF16
+    const int64_t total = min(R * ((K + GK - 1) / GK), (int64_t)first + kPackRun);
+    // element pairs (2 l, 2 l + 1) in one aligned load when every row start is even
+    const bool words = sizeof(AT) == 2 && (ld & 1) == 0 && (reinterpret_cast<uintptr_t>(X) & 3u) == 0;
+    const bool pairs = sizeof(AT) == 4 && (ld & 1) == 0 && (reinterpret_cast<uintptr_t>(X) & 7u) == 0;
+    for (int64_t f0 = first; f0 < total; f0 += PU) {
+      int64_t kb = f0 / R, r = f0 - kb * R;
+      int64_t c = kb * GK + 2 * lane;
+      const AT* src = X + r * ld + c;
+      float x0[PU], x1[PU];
+      uint32_t wv[PU];
 #pragma unroll
-    for (int u = 0; u < PU; ++u) {
-      x0[u] = x1[u] = 0.f;
-      wv[u] = 0u;
-      const int64_t c = kb * GK + 2 * lane;
-      if (f0 + u < total && c < K) {
-        const bool v1 = c + 1 < K;
-        const AT* src = X + r * ld + c;
-        if constexpr (sizeof(AT) == 2) {
-          if (words && v1) {
-            wv[u] = __ldg(reinterpret_cast<const unsigned int*>(src));
+      for (int u = 0; u < PU; ++u) {
+        x0[u] = x1[u] = 0.f;
+        wv[u] = 0u;
+        if (f0 + u < total && c < K) {
+          const bool v1 = c + 1 < K;
+          if constexpr (sizeof(AT) == 2) {
+            if (words && v1) {
+              wv[u] = __ldg(reinterpret_cast<const unsigned int*>(src));
+            } else {
+              const unsigned short* h = reinterpret_cast<const unsigned short*>(src);
+              wv[u] = (uint32_t)__ldg(h) | (v1 ? (uint32_t)__ldg(h + 1) << 16 : 0u);
+            }
           } else {
-            const unsigned short* h = reinterpret_cast<const unsigned short*>(src);
-            wv[u] = (uint32_t)__ldg(h) | (v1 ? (uint32_t)__ldg(h + 1) << 16 : 0u);
-          }
-        } else {
-          if (pairs && v1) {
-            const float2 f = __ldg(reinterpret_cast<const float2*>(src));
-            x0[u] = f.x;
-            x1[u] = f.y;
-          } else {
-            x0[u] = __ldg(reinterpret_cast<const float*>(src));
-            x1[u] = v1 ? __ldg(reinterpret_cast<const float*>(src) + 1) : 0.f;
+            if (pairs && v1) {
+              const float2 f = __ldg(reinterpret_cast<const float2*>(src));
+              x0[u] = f.x;
+              x1[u] = f.y;
+            } else {
+              x0[u] = __ldg(reinterpret_cast<const float*>(src));
+              x1[u] = v1 ? __ldg(reinterpret_cast<const float*>(src) + 1) : 0.f;
+            }
           }
         }
+        // the next packed row: the next row of this K block, or row 0 of the next
+        src += ld;
+        if (++r == R) { r = 0; c += GK; src = X + c; }
       }
-      if (++r == R) { r = 0; ++kb; }
-    }
 #pragma unroll
-    for (int u = 0; u < PU; ++u) {
-      if (f0 + u >= total) break;
-      const int64_t row = p0 + f0 + u;
-      if constexpr (S == 1) {
-        out[row * (GK / 2) + lane] = wv[u];
-      } else {
-        uint16_t s0[3], s1[3];
-        split3_rn(x0[u], s0);
-        split3_rn(x1[u], s1);
+      for (int u = 0; u < PU; ++u) {
+        if (f0 + u >= total) break;
+        const int64_t row = p0 + f0 + u;
+        if constexpr (S == 1) {
+          out[row * (GK / 2) + lane] = wv[u];
+        } else {
+          uint16_t s0[3], s1[3];
+          split3_rn(x0[u], s0);
+          split3_rn(x1[u], s1);
 #pragma unroll
-        for (int sl = 0; sl < S; ++sl)
-          out[((int64_t)sl * rows + row) * (GK / 2) + lane] = (uint32_t)s0[sl] | ((uint32_t)s1[sl] << 16);
+          for (int sl = 0; sl < S; ++sl)
+            out[((int64_t)sl * rows + row) * (GK / 2) + lane] = (uint32_t)s0[sl] | ((uint32_t)s1[sl] << 16);
+        }
       }
     }
+  }
+}
+
+// 16 FP32 values of C along a row: x[j] = C[j * ldc] for j < n (0 past n
+// or when !ok); no predicates when all 16 are wanted
+__device__ __forceinline__ void load_c16(float (&x)[16], const float* C, int64_t ldc, bool ok, int n) {
+  if (ok && n >= 16) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) x[j] = __ldg(C + j * ldc);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) x[j] = (ok && j < n) ? __ldg(C + j * ldc) : 0.f;
   }
 }
 
@@ -337,14 +354,28 @@ __global__ void __launch_bounds__(GTHREADS, 1)
             asm volatile("prefetch.global.L2 [%0];" ::"l"(static_cast<const char*>(pb.C) +
                                                           ((i0 + 32 * q) + (j0 + lane + 32 * u) * (int64_t)pb.ldc) * es));
       }
+      // FP32 C: the first 16 columns are loaded before the accumulator is
+      // complete, and then the loads of the next 16 columns are in flight
+      // while a chunk's D is written (all of a chunk's C is read before its
+      // D, and D columns are written in order, so D may be C itself)
+      const bool c32 = has_c && g.cdt == ARMA_F32;
+      const int64_t ldc = pb.ldc, ldd = pb.m;
+      const float* Cr = c32 ? static_cast<const float*>(pb.C) + row + j0 * ldc : nullptr;
+      float cn[16];
+      load_c16(cn, Cr, ldc, c32 && row_ok, ncol);
       if (!__all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * e, aphase, abort))) break;
       aphase ^= 1u;
       fence_after();
       double dsum = 0.0;
-      float* Dr = static_cast<float*>(pb.D) + row + j0 * (int64_t)pb.m;
-      const int diag = (int)(row - j0);
+      float* Dr = static_cast<float*>(pb.D) + row + j0 * ldd;
+      // this row's diagonal column, if the trace runs through it (i < min(m, n))
+      const int diag = (tm == tn && row - j0 < ncol) ? (int)(row - j0) : -1;
 #pragma unroll 1
       for (int c0 = 0; c0 < ncol; c0 += 16) {
+        float cv[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) cv[j] = cn[j];
+        load_c16(cn, Cr + (int64_t)(c0 + 16) * ldc, ldc, c32 && row_ok, ncol - (c0 + 16));
         float v[16];
         if (pb.k > 0) {
           tmem_ld16(tmem_base + lane_base + acc_col + (uint32_t)c0, v);
@@ -353,28 +384,28 @@ __global__ void __launch_bounds__(GTHREADS, 1)
           for (int j = 0; j < 16; ++j) v[j] = 0.f;
         }
         if (!row_ok) continue;
-        if (has_c && g.cdt == ARMA_F32) {
-          // all 16 C values before any D (D may be C itself)
-          const float* Cr = static_cast<const float*>(pb.C) + row + (j0 + c0) * (int64_t)pb.ldc;
-          float cv[16];
+        float* dp = Dr + (int64_t)c0 * ldd;
+        if (diag >= c0 && diag < c0 + 16) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) cv[j] = c0 + j < ncol ? __ldg(Cr + (int64_t)j * pb.ldc) : 0.f;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            if (c0 + j >= ncol) break;
+          for (int j = 0; j < 16; ++j)
             if (c0 + j == diag) dsum += (double)v[j];
-            Dr[(int64_t)(c0 + j) * pb.m] = fmaf(g.beta_f, cv[j], g.alpha_f * v[j]);
+        }
+        if (c32 || !has_c) {
+          if (c0 + 16 <= ncol) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) dp[j * ldd] = fmaf(g.beta_f, cv[j], g.alpha_f * v[j]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (c0 + j < ncol) dp[j * ldd] = fmaf(g.beta_f, cv[j], g.alpha_f * v[j]);
           }
         } else {
-          // no C, or C of another type: element by element (D is FP32, so
-          // it is never C itself here)
+          // C of another type, element by element (D is FP32, so it is
+          // never C itself here)
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            if (c0 + j >= ncol) break;
-            if (c0 + j == diag) dsum += (double)v[j];
-            const float cj = has_c ? load_as<float>(pb.C, row + (j0 + c0 + j) * (int64_t)pb.ldc, g.cdt) : 0.f;
-            Dr[(int64_t)(c0 + j) * pb.m] = fmaf(g.beta_f, cj, g.alpha_f * v[j]);
-          }
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < ncol)
+              dp[j * ldd] = fmaf(g.beta_f, load_as<float>(pb.C, row + (j0 + c0 + j) * ldc, g.cdt), g.alpha_f * v[j]);
         }
       }
       // the accumulator is free for the MMA issuer again
@@ -420,9 +451,20 @@ cudaError_t launch_packed(const GroupedArgs& g, cudaStream_t s, int* launches) {
   const bool any = g.rows_a > 0 && g.rows_b > 0;   // some problem has K > 0
   if (any && (!g.pack_a || !g.pack_b)) return cudaErrorInvalidValue;
   // 1. pack
-  if (any) {
-    if (2 * g.count > (int64_t)INT32_MAX) return cudaErrorInvalidConfiguration;
-    grouped_pack_kernel<AT, S><<<(unsigned)(2 * g.count), 256, 0, s>>>(g);
+  if (any && g.n_items > 0) {
+    if (!g.pack_items) return cudaErrorInvalidValue;
+    // a persistent grid: as many CTAs of 8 warps as fit on the GPU at once,
+    // or fewer for a short list
+    static std::atomic<int> per_sm{0};
+    int fit = per_sm.load(std::memory_order_relaxed);
+    if (fit <= 0) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, grouped_pack_kernel<AT, S>, 256, 0) != cudaSuccess ||
+          fit < 1)
+        fit = 1;
+      per_sm.store(fit, std::memory_order_relaxed);
+    }
+    int64_t blocks = (g.n_items + 7) / 8, cap = (int64_t)device_sm_count() * fit;
+    grouped_pack_kernel<AT, S><<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(g);
     if (launches) ++*launches;
   }
   // 2. the products (with no K anywhere no box is ever loaded)

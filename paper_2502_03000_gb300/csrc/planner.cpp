@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "grouped.h"
 #include "internal.h"
 
 namespace arma {
@@ -1756,6 +1757,15 @@ arma_status plan_batched(const arma_expr* exprs, int32_t count, arma_plan* p) {
       b.pb.push_back(b.rows_b);
       b.rows_a += g.m * nkb;
       b.rows_b += g.n * nkb;
+      // the pack kernel's work: runs of kPackRun packed rows within one operand
+      for (int op = 0; op < 2; ++op) {
+        const int64_t total = (op ? g.n : g.m) * nkb;
+        if (total > INT32_MAX) return ARMA_ERR_UNSUPPORTED;
+        for (int64_t f = 0; f < total; f += kPackRun) {
+          b.pack_items.push_back(2 * i + op);
+          b.pack_items.push_back((int32_t)f);
+        }
+      }
     }
     const int64_t ntm = (g.m + T - 1) / T, ntn = (g.n + T - 1) / T;
     if (ntm > 65535 || ntn > 65535) return ARMA_ERR_UNSUPPORTED;
