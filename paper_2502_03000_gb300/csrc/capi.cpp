@@ -470,7 +470,7 @@ arma_status arma_gpu_eval_batched(const arma_plan* plan, const void* device_tabl
     g.rows_b = b.rows_b;
     g.slices = b.slices;
     g.pack_items = reinterpret_cast<const int32_t*>(base + pi);
-    g.n_items = (int64_t)(b.pack_items.size() / 2);
+    g.n_items = (int64_t)(b.pack_items.size() / 3);
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // status, info and the tile counter start at zero

@@ -59,11 +59,11 @@ struct GroupedArgs {
   int64_t rows_a, rows_b;       // packed rows per slice
   int32_t slices;               // 1 (BF16 operands) or 3 (FP32 operands, exact BF16 slices)
   int32_t pad2;
-  const int32_t* pack_items;    // pack work items: (2 problem + operand, first row) pairs
+  const int32_t* pack_items;    // pack work items: (2 problem + operand, first row, rows) triplets
   int64_t n_items;
 };
 
-// packed rows per pack work item
+// packed rows per pack work item (about: whole rows with all their K blocks)
 constexpr int kPackRun = 64;
 
 // K elements per packed row (one K block)

@@ -345,7 +345,7 @@ struct BatchedInfo {
   std::vector<int64_t> pa, pb;       // per problem: first packed row of op(A), op(B)^T
   int64_t rows_a = 0, rows_b = 0;    // packed rows per slice
   int32_t slices = 1;                // 1 (BF16) or 3 (FP32 as exact BF16 slices)
-  std::vector<int32_t> pack_items;   // pack work: (2 problem + operand, first packed row) pairs, runs of 64
+  std::vector<int32_t> pack_items;   // pack work: (2 problem + operand, first row, rows) triplets
   size_t pack_off = 0, pack_bytes = 0;   // the packed arrays in the workspace
 };
 

@@ -95,80 +95,119 @@ __device__ __forceinline__ void split3_rn(float x, uint16_t (&sl)[3]) {
 }
 
 // ---------------------------------------------------------------------------
-// pack: the work is the host-built list of runs of kPackRun packed rows of
-// one operand (0: op(A), 1: op(B)^T) of one problem; warp w of the grid takes
-// runs w, w + W, ...  Packed row f = kb R + r (K block kb, row r) of a problem
-// lies at p_g + f; PU rows per pass, PU loads in flight per lane; lane l
-// holds K columns 2 l and 2 l + 1 of a row.
+// pack: the work is the host-built list of runs of whole rows of one operand
+// (0: op(A), 1: op(B)^T) of one problem, with all their K blocks; warp w of
+// the grid takes runs w, w + W, ...  Pair t of a run is (row t / nkb, K
+// block t % nkb), K block fastest, so a warp reads consecutive source
+// memory.  A lane group copies one pair per step: 8 lanes of 16 bytes (BF16)
+// or 16 lanes of 16 bytes (FP32, then split) from aligned 16-byte loads of
+// the source row, each lane joining its chunk with the next lane's (rows may
+// start at any element).  Only chunks that hold an element of the row are
+// loaded, and elements past K are zero.  All loads of a step are issued
+// before their data is used.  Packed row (kb, r) of a problem lies at
+// p_g + kb R + r.
 // ---------------------------------------------------------------------------
-constexpr int PU = 16;
+constexpr int PU = 2;   // pairs per lane group and step
+
+// bytes sh .. sh + 15 of the 32 bytes c (sh even): shift by 2 words, by one
+// word, then by 16 bits
+__device__ __forceinline__ uint4 window16(const uint32_t (&c)[8], uint32_t sh) {
+  uint32_t d[6], e[5];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) d[i] = (sh & 8u) ? c[i + 2] : c[i];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) e[i] = (sh & 4u) ? d[i + 1] : d[i];
+  const uint32_t fs = (sh & 2u) * 8u;
+  return make_uint4(__funnelshift_r(e[0], e[1], fs), __funnelshift_r(e[1], e[2], fs),
+                    __funnelshift_r(e[2], e[3], fs), __funnelshift_r(e[3], e[4], fs));
+}
 
 template <typename AT, int S>
-__global__ void __launch_bounds__(256, 3) grouped_pack_kernel(const __grid_constant__ GroupedArgs g) {
+__global__ void __launch_bounds__(256, sizeof(AT) == 2 ? 4 : 3) grouped_pack_kernel(const __grid_constant__ GroupedArgs g) {
+  constexpr int LPR = sizeof(AT) == 2 ? 8 : 16;       // lanes per packed row
+  constexpr int GPW = 32 / LPR;                        // pairs per warp and unrolled step
+  constexpr int EPL = 16 / (int)sizeof(AT);            // source elements per lane
   const int lane = threadIdx.x & 31;
+  const int gsub = lane / LPR, j = lane % LPR;
   const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < g.n_items; it += W) {
-    const int32_t code = g.pack_items[2 * it], first = g.pack_items[2 * it + 1];
+    const int32_t code = g.pack_items[3 * it], r0 = g.pack_items[3 * it + 1], nr = g.pack_items[3 * it + 2];
     const int64_t pi = code >> 1;
     const int op = code & 1;
     const GroupedProblem& P = g.probs[pi];
     const int64_t R = op ? P.n : P.m, K = P.k;
-    const AT* X = static_cast<const AT*>(op ? P.B : P.A);
+    const char* X = static_cast<const char*>(op ? P.B : P.A);
     const int64_t ld = op ? P.ldb : P.lda;
     const int64_t p0 = op ? P.pb : P.pa;
     const int64_t rows = op ? g.rows_b : g.rows_a;
-    uint32_t* out = static_cast<uint32_t*>(op ? g.pack_b : g.pack_a);   // pairs of BF16
-    const int64_t total = min(R * ((K + GK - 1) / GK), (int64_t)first + kPackRun);
-    // element pairs (2 l, 2 l + 1) in one aligned load when every row start is even
-    const bool words = sizeof(AT) == 2 && (ld & 1) == 0 && (reinterpret_cast<uintptr_t>(X) & 3u) == 0;
-    const bool pairs = sizeof(AT) == 4 && (ld & 1) == 0 && (reinterpret_cast<uintptr_t>(X) & 7u) == 0;
-    for (int64_t f0 = first; f0 < total; f0 += PU) {
-      int64_t kb = f0 / R, r = f0 - kb * R;
-      int64_t c = kb * GK + 2 * lane;
-      const AT* src = X + r * ld + c;
-      float x0[PU], x1[PU];
-      uint32_t wv[PU];
+    const uint32_t nkb = (uint32_t)((K + GK - 1) / GK);
+    const int64_t T = (int64_t)nr * nkb;
+    for (int64_t t0 = 0; t0 < T; t0 += GPW * PU) {
+      uint4 q[PU], qx[PU];
+      int64_t dst[PU];
+      uint32_t shv[PU];
+      int nvv[PU];
 #pragma unroll
       for (int u = 0; u < PU; ++u) {
-        x0[u] = x1[u] = 0.f;
-        wv[u] = 0u;
-        if (f0 + u < total && c < K) {
-          const bool v1 = c + 1 < K;
-          if constexpr (sizeof(AT) == 2) {
-            if (words && v1) {
-              wv[u] = __ldg(reinterpret_cast<const unsigned int*>(src));
-            } else {
-              const unsigned short* h = reinterpret_cast<const unsigned short*>(src);
-              wv[u] = (uint32_t)__ldg(h) | (v1 ? (uint32_t)__ldg(h + 1) << 16 : 0u);
-            }
-          } else {
-            if (pairs && v1) {
-              const float2 f = __ldg(reinterpret_cast<const float2*>(src));
-              x0[u] = f.x;
-              x1[u] = f.y;
-            } else {
-              x0[u] = __ldg(reinterpret_cast<const float*>(src));
-              x1[u] = v1 ? __ldg(reinterpret_cast<const float*>(src) + 1) : 0.f;
-            }
-          }
-        }
-        // the next packed row: the next row of this K block, or row 0 of the next
-        src += ld;
-        if (++r == R) { r = 0; c += GK; src = X + c; }
+        const int64_t t = t0 + GPW * u + gsub;
+        const bool rv = t < T;
+        const uint32_t tu = (uint32_t)(rv ? t : 0);
+        const uint32_t rl = tu / nkb, kb = tu - rl * nkb;
+        const int64_t r = r0 + rl;
+        dst[u] = rv ? p0 + (int64_t)kb * R + r : -1;
+        const int nv = rv ? (int)min((int64_t)GK, K - (int64_t)GK * kb) : 0;   // elements of this pair
+        nvv[u] = nv;
+        const char* A = X + (int64_t)sizeof(AT) * (r * ld + (int64_t)GK * kb);
+        const uint32_t sh = (uint32_t)(reinterpret_cast<uintptr_t>(A) & 15u);
+        shv[u] = sh;
+        const char* a0 = A - sh;
+        const char* last = A + (int64_t)sizeof(AT) * nv - 1;
+        q[u] = make_uint4(0u, 0u, 0u, 0u);
+        qx[u] = q[u];
+        if (nv > 0 && a0 + 16 * j <= last) q[u] = __ldg(reinterpret_cast<const uint4*>(a0 + 16 * j));
+        if (nv > 0 && j == LPR - 1 && a0 + 16 * LPR <= last)
+          qx[u] = __ldg(reinterpret_cast<const uint4*>(a0 + 16 * LPR));
       }
 #pragma unroll
       for (int u = 0; u < PU; ++u) {
-        if (f0 + u >= total) break;
-        const int64_t row = p0 + f0 + u;
+        uint4 nx;
+        nx.x = __shfl_down_sync(0xffffffffu, q[u].x, 1, LPR);
+        nx.y = __shfl_down_sync(0xffffffffu, q[u].y, 1, LPR);
+        nx.z = __shfl_down_sync(0xffffffffu, q[u].z, 1, LPR);
+        nx.w = __shfl_down_sync(0xffffffffu, q[u].w, 1, LPR);
+        if (j == LPR - 1) nx = qx[u];
+        const uint32_t c[8] = {q[u].x, q[u].y, q[u].z, q[u].w, nx.x, nx.y, nx.z, nx.w};
+        uint4 w = window16(c, shv[u]);
+        const int e0 = EPL * j;   // first source element of this lane
+        if (e0 + EPL > nvv[u]) {  // past the pair's valid elements: zero
+          uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int tt = 0; tt < 4; ++tt) {
+            if constexpr (sizeof(AT) == 2) {
+              const int e = e0 + 2 * tt;
+              if (e >= nvv[u]) ww[tt] = 0u;
+              else if (e + 1 >= nvv[u]) ww[tt] &= 0xFFFFu;
+            } else {
+              if (e0 + tt >= nvv[u]) ww[tt] = 0u;
+            }
+          }
+          w = make_uint4(ww[0], ww[1], ww[2], ww[3]);
+        }
+        if (dst[u] < 0) continue;
         if constexpr (S == 1) {
-          out[row * (GK / 2) + lane] = wv[u];
+          static_cast<uint4*>(op ? g.pack_b : g.pack_a)[dst[u] * 8 + j] = w;
         } else {
-          uint16_t s0[3], s1[3];
-          split3_rn(x0[u], s0);
-          split3_rn(x1[u], s1);
+          // four FP32 values -> four BF16 of each slice (8 bytes a slice)
+          uint16_t s0[3], s1[3], s2[3], s3[3];
+          split3_rn(__uint_as_float(w.x), s0);
+          split3_rn(__uint_as_float(w.y), s1);
+          split3_rn(__uint_as_float(w.z), s2);
+          split3_rn(__uint_as_float(w.w), s3);
+          uint2* out = static_cast<uint2*>(op ? g.pack_b : g.pack_a);
 #pragma unroll
           for (int sl = 0; sl < S; ++sl)
-            out[((int64_t)sl * rows + row) * (GK / 2) + lane] = (uint32_t)s0[sl] | ((uint32_t)s1[sl] << 16);
+            out[((int64_t)sl * rows + dst[u]) * 16 + j] =
+                make_uint2((uint32_t)s0[sl] | ((uint32_t)s1[sl] << 16), (uint32_t)s2[sl] | ((uint32_t)s3[sl] << 16));
         }
       }
     }

@@ -1757,13 +1757,16 @@ arma_status plan_batched(const arma_expr* exprs, int32_t count, arma_plan* p) {
       b.pb.push_back(b.rows_b);
       b.rows_a += g.m * nkb;
       b.rows_b += g.n * nkb;
-      // the pack kernel's work: runs of kPackRun packed rows within one operand
+      // the pack kernel's work: runs of whole rows of one operand (all their
+      // K blocks, about kPackRun packed rows a run), in source order
       for (int op = 0; op < 2; ++op) {
-        const int64_t total = (op ? g.n : g.m) * nkb;
-        if (total > INT32_MAX) return ARMA_ERR_UNSUPPORTED;
-        for (int64_t f = 0; f < total; f += kPackRun) {
+        const int64_t R = op ? g.n : g.m;
+        if (R * nkb > INT32_MAX) return ARMA_ERR_UNSUPPORTED;
+        const int64_t run = std::max<int64_t>(1, kPackRun / std::max<int64_t>(nkb, 1));
+        for (int64_t r = 0; r < R && nkb > 0; r += run) {
           b.pack_items.push_back(2 * i + op);
-          b.pack_items.push_back((int32_t)f);
+          b.pack_items.push_back((int32_t)r);
+          b.pack_items.push_back((int32_t)std::min<int64_t>(run, R - r));
         }
       }
     }
