@@ -65,6 +65,7 @@ def args():
     p.add_argument("--sizes", default="100,250,500,1000,4096",
                    help="structured workload: tridiagonal sizes")
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"], help="structured workload: element type")
+    p.add_argument("--batched-dtypes", default="f32,bf16", help="batched workload: operand types")
     p.add_argument("--planner-save", default="", help="planner workload: directory for the trained network "
                                                          "and the timing records (JSON)")
     return p.parse_args()
@@ -347,11 +348,6 @@ def bench_products(a):
                       "bf16_peak_tflops": peak, "peak_source": src, "tiers": res, "cpu_baseline": cpu}), flush=True)
 
 
-def fp32_simt_peak_tflops():
-    # 152 SMs x 128 FP32 FMA lanes x 2 flops x 2.07 GHz (nominal unit counts and clock)
-    return 152 * 128 * 2 * 2.07e9 / 1e12
-
-
 def bench_batched(a):
     """10,000 instances of 2*trans(A_i)*B_i + C_i and trace(A_i^T B_i), m, n, k
     log-uniform in [8, 512]: one grouped launch (CUDA-graph replay) against
@@ -368,11 +364,12 @@ def bench_batched(a):
     n = synth.log_uniform_ints(seed, 2, count, 8, 512)
     k = synth.log_uniform_ints(seed, 3, count, 8, 512)
     flops = float(np.sum(2.0 * m * n * k))
+    hbm, hbm_src = peaks()
     gen = torch.Generator(device=dev)
     gen.manual_seed(seed)
     stream = torch.cuda.current_stream(dev)
     res = {}
-    for dt in ("f32", "bf16"):
+    for dt in a.batched_dtypes.split(","):
         td = torch.float32 if dt == "f32" else torch.bfloat16
 
         def uni(r, c, t):
@@ -397,24 +394,32 @@ def bench_batched(a):
         g.replay()
         torch.cuda.synchronize()
         ms = time_ms(g.replay, a.steps, stream)
-        # baseline: one evaluation (and its launches) per instance
-        plans = [ag.Plan(nd, o) for nd, o in inst]
-        for p_, x, y in zip(plans, ins, outs):
-            p_(*x, outputs=y)
-        torch.cuda.synchronize()
-        base_ms = time_ms(lambda: [p_(*x, outputs=y) for p_, x, y in zip(plans, ins, outs)], 1, stream)
-        launches = sum(len(p_.info["steps"]) for p_ in plans)
+        # baseline: one evaluation (and its launches) per instance (--no-literal: none)
+        base_ms, launches = None, None
+        if not a.no_literal:
+            plans = [ag.Plan(nd, o) for nd, o in inst]
+            for p_, x, y in zip(plans, ins, outs):
+                p_(*x, outputs=y)
+            torch.cuda.synchronize()
+            base_ms = time_ms(lambda: [p_(*x, outputs=y) for p_, x, y in zip(plans, ins, outs)], 1, stream)
+            launches = sum(len(p_.info["steps"]) for p_ in plans)
+            del plans
+        # algorithmic bytes of one batch: op(A), op(B) and C read once, D
+        # written once (the traces are 8 bytes a problem)
+        es = 4 if dt == "f32" else 2
+        nbytes = float(np.sum((m * k + k * n) * es + 2 * m * n * 4 + 8))
+        achieved = nbytes / (ms * 1e-3) / 1e9
         res[dt] = {"ms_per_batch": ms, "instances_per_s": count / (ms * 1e-3), "tflops": flops / ms / 1e9,
-                   "frac_of_fp32_simt_peak": flops / ms / 1e9 / fp32_simt_peak_tflops(),
-                   "per_instance_ms": base_ms, "vs_per_instance": base_ms / ms,
+                   "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                                "frac": achieved / hbm, "peak_source": hbm_src, "algorithmic_bytes": nbytes},
+                   "per_instance_ms": base_ms, "vs_per_instance": None if base_ms is None else base_ms / ms,
                    "per_instance_planned_steps": launches, "tiles": bp.info["tiles"],
                    "kernel": bp.info["steps"][0]["kernel"], "tile": bp.info["tile"],
                    "autotune_ms": tuned, "plan_and_tune_s": plan_s}
-        del plans, bp, g, ins, outs
+        del bp, g, ins, outs
         torch.cuda.empty_cache()
     print(json.dumps({"workload": "10000 x (2*trans(A_i)*B_i+C_i, trace(A_i^T B_i)), m,n,k log-uniform [8,512]",
-                      "flops_per_batch": flops, "fp32_simt_peak_tflops": fp32_simt_peak_tflops(),
-                      "results": res}), flush=True)
+                      "flops_per_batch": flops, "results": res}), flush=True)
 
 
 def bench_chain(a):
