@@ -544,8 +544,38 @@ __device__ __forceinline__ void prep_group(const PrepArgs& a, int64_t r, int64_t
                                            uint16_t (&s1)[8], uint16_t (&s2)[8]) {
   const XT* X = static_cast<const XT*>(a.X) + r * a.ldx;
   XT x[8];
+  // a whole aligned group inside the matrix: 16-byte loads (the same values)
+  const bool whole = r < a.R && l0 + 8 <= a.K && (reinterpret_cast<uintptr_t>(X + l0) & 15u) == 0;
+  bool done = false;
+  if constexpr (sizeof(XT) == 8) {
+    if (whole) {
+      const double2* p = reinterpret_cast<const double2*>(X + l0);
 #pragma unroll
-  for (int e = 0; e < 8; ++e) x[e] = (r < a.R && l0 + e < a.K) ? X[l0 + e] : XT(0);
+      for (int h = 0; h < 4; ++h) {
+        const double2 v = __ldg(p + h);
+        x[2 * h] = v.x;
+        x[2 * h + 1] = v.y;
+      }
+      done = true;
+    }
+  } else if constexpr (sizeof(XT) == 4) {
+    if (whole) {
+      const float4* p = reinterpret_cast<const float4*>(X + l0);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float4 v = __ldg(p + h);
+        x[4 * h] = v.x;
+        x[4 * h + 1] = v.y;
+        x[4 * h + 2] = v.z;
+        x[4 * h + 3] = v.w;
+      }
+      done = true;
+    }
+  }
+  if (!done) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) x[e] = (r < a.R && l0 + e < a.K) ? X[l0 + e] : XT(0);
+  }
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     uint16_t sl[3] = {0, 0, 0};
