@@ -53,7 +53,8 @@ def args():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--workload", default="fused",
-                   choices=["fused", "products", "chain", "solve", "plain", "batched", "planner", "structured"],
+                   choices=["fused", "products", "chain", "solve", "plain", "batched", "planner", "structured",
+                            "hostlink"],
                    help="fused (default) is the benchmark line; the others measure the remaining "
                         "expression families and print one JSON line each")
     p.add_argument("--tiers", default="bf16,split_bf16,f64")
@@ -712,6 +713,58 @@ def bench_planner(a):
                       "train_fit": {k: res_train[k] for k in res_train if k.endswith("regret")}}), flush=True)
 
 
+def bench_hostlink(a):
+    """The host link: the fused FP32 pass over 8192^2 inputs held in pinned
+    host memory. Route 1: the kernel reads them over the link at the address
+    arma_gpu_device_address gives (no staging copy). Route 2: the copy
+    engines bring them into device memory first, then the pass runs there.
+    Reported as GB/s of input bytes, beside the pass on resident inputs."""
+    import ctypes
+    import torch
+    import paper_2502_03000_gb300 as ag
+    from paper_2502_03000_gb300 import expr as E
+    dev = torch.device("cuda", 0)
+    n = a.n
+    stream = torch.cuda.current_stream(dev)
+    nodes, outs = E.config_fused(n, "f32")
+    plan = ag.Plan(nodes, outs)
+    gen = torch.Generator().manual_seed(20250203 + 2)
+    host = [(torch.rand((n, n), generator=gen) * 2 - 1).pin_memory() for _ in range(4)]
+    devc = [torch.empty((n, n), device=dev) for _ in range(4)]
+    try:
+        addr = [ag.device_address(h.data_ptr()) for h in host]
+    except ag.ArmaError as e:
+        print(json.dumps({"workload": "hostlink", "unavailable": f"pinned host memory not addressable: {e}"}))
+        return
+    out = plan.alloc_outputs(dev)
+    ws = plan.workspace(dev)
+    ins = (ctypes.c_void_p * max(1, plan.n_slots))(*addr)
+    outp = (ctypes.c_void_p * len(out))(*[o.data_ptr() for o in out])
+
+    def zero_copy():
+        assert ag.lib().arma_gpu_eval(plan._h, ins, outp, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                      ctypes.c_void_p(stream.cuda_stream)) == 0
+
+    def copy_then_eval():
+        for d_, h_ in zip(devc, host):
+            d_.copy_(h_, non_blocking=True)
+        plan(*[d_.t() for d_ in devc], outputs=out, workspace=ws)
+
+    for f in (zero_copy, copy_then_eval):
+        for _ in range(max(3, a.warmup)):
+            f()
+    torch.cuda.synchronize()
+    steps = max(3, a.steps // 4)
+    zc = time_ms(zero_copy, steps, stream)
+    ce = time_ms(copy_then_eval, steps, stream)
+    resident = time_ms(lambda: plan(*[d_.t() for d_ in devc], outputs=out, workspace=ws), steps, stream)
+    nbytes = 4 * n * n * 4
+    print(json.dumps({"workload": f"fused FP32 pass, A,B,C,D {n}x{n} in pinned host memory", "input_bytes": nbytes,
+                      "zero_copy": {"ms": zc, "gbs": nbytes / zc / 1e6},
+                      "copy_engines_then_pass": {"ms": ce, "gbs": nbytes / ce / 1e6},
+                      "resident_pass_ms": resident}), flush=True)
+
+
 def main():
     a = args()
     if a.impl == "reference":
@@ -720,7 +773,7 @@ def main():
     if a.workload != "fused":
         {"products": bench_products, "batched": bench_batched, "chain": bench_chain,
          "solve": bench_solve, "plain": bench_plain, "planner": bench_planner,
-         "structured": bench_structured}[a.workload](a)
+         "structured": bench_structured, "hostlink": bench_hostlink}[a.workload](a)
         return
     import numpy as np
     import torch
@@ -860,7 +913,44 @@ def main():
     stream.wait_stream(d2h_s)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / a.e2e_steps
+    e2e_copy_ms = e0.elapsed_time(e1) / a.e2e_steps
+
+    # The same step without staging copies: the kernels read the pinned host
+    # inputs and write the pinned host results over the host link, at the
+    # addresses arma_gpu_device_address gives.  Both routes are bound by the
+    # link; the faster one is the e2e figure.
+    import ctypes
+    e2e_zc_ms = None
+    try:
+        zc_args = {}
+        for dt in DTYPES:
+            ins = (ctypes.c_void_p * max(1, plans[dt].n_slots))(
+                *[ag.device_address(hp.data_ptr()) for hp in host_pinned[dt]])
+            outp = (ctypes.c_void_p * len(outs[dt]))(*[ag.device_address(ho.data_ptr()) for ho in host_out[dt]])
+            zc_args[dt] = (ins, outp, plans[dt].workspace(dev))
+    except ag.ArmaError:
+        zc_args = None
+    if zc_args is not None:
+        def zc_step():
+            for dt in DTYPES:
+                ins, outp, ws = zc_args[dt]
+                rc = ag.lib().arma_gpu_eval(plans[dt]._h, ins, outp, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                            ctypes.c_void_p(stream.cuda_stream))
+                if rc != 0:
+                    raise RuntimeError(f"arma_gpu_eval: {ag.STATUS.get(rc, rc)}")
+        zc_step()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(a.e2e_steps):
+            zc_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_zc_ms = e0.elapsed_time(e1) / a.e2e_steps
+    routes = {"copy_engines": e2e_copy_ms}
+    if e2e_zc_ms is not None:
+        routes["zero_copy"] = e2e_zc_ms
+    e2e_route = min(routes, key=routes.get)
+    e2e_ms = routes[e2e_route]
 
     # ---- accuracy against the oracle on the whole workload (rank 0) ----
     cpu = None
@@ -915,7 +1005,8 @@ def main():
                      "alg_bytes_per_launch": alg[dom]},
         "cpu_baseline": cpu,
         "e2e": {"value": 2 / (e2e_ms * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "route": e2e_route,
+                "routes_evals_per_s": {k: 2 / (v * 1e-3) for k, v in routes.items()}},
         "gpu_launches": launches_per_step * a.steps,
         "clocks": clocks,
     }

@@ -287,6 +287,17 @@ const char* arma_gpu_status_string(arma_status status);
  * Returns the previous limit. */
 uint64_t arma_gpu_set_wait_limit_ns(uint64_t ns);
 
+/* The address at which this library's kernels reach the memory at p (the
+ * paper has no counterpart: it runs on the host).  Device and managed
+ * memory: p itself.  Pinned host memory that the current device maps
+ * (cudaHostAlloc, cudaHostRegister; with unified addressing the same
+ * pointer): the mapped address, so arma_gpu_eval can take inputs and
+ * outputs in host memory and its kernels read and write them over the host
+ * link, with no staging copy.  Memory the device cannot address (plain
+ * pageable host memory included) gives ARMA_ERR_INVALID and *dptr = NULL.
+ * Host-only; it allocates nothing. */
+arma_status arma_gpu_device_address(const void* p, void** dptr);
+
 /* Name and text of the last CUDA runtime error behind an ARMA_ERR_CUDA
  * returned to the calling thread ("" if none).  The string is owned by the
  * library and stays valid until the thread's next failing call. */

@@ -81,7 +81,7 @@ EXPORTS = ["arma_gpu_plan", "arma_gpu_plan_workspace", "arma_gpu_output_info", "
            "arma_gpu_eval_batched", "arma_gpu_plan_features", "arma_gpu_plan_heuristic_cost",
            "arma_gpu_mlp_param_count", "arma_gpu_mlp_workspace", "arma_gpu_mlp_forward", "arma_gpu_mlp_grad",
            "arma_gpu_mlp_adam", "arma_gpu_plan_candidates", "arma_gpu_cost_model_load",
-           "arma_gpu_cost_model_clear", "arma_gpu_cost_model_predict"]
+           "arma_gpu_cost_model_clear", "arma_gpu_cost_model_predict", "arma_gpu_device_address"]
 N_FEATURES = 32
 STATIC_SCRATCH_BYTES = 131072
 
@@ -107,6 +107,7 @@ def lib() -> ctypes.CDLL:
     L.arma_gpu_last_cuda_error.restype = ctypes.c_char_p
     L.arma_gpu_set_wait_limit_ns.argtypes = [ctypes.c_uint64]
     L.arma_gpu_set_wait_limit_ns.restype = ctypes.c_uint64
+    L.arma_gpu_device_address.argtypes = [vp, ctypes.POINTER(vp)]
     L.arma_gpu_chain_order.argtypes = [i32, ctypes.POINTER(i64), i32, ctypes.POINTER(i32),
                                        ctypes.POINTER(ctypes.c_uint64)]
     L.arma_gpu_eval_fused_static.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
@@ -144,6 +145,15 @@ def set_wait_limit_ns(ns: int) -> int:
     """Limit of each bounded device wait of the solve kernels (ns, process
     wide); 0 gives up at the first unset poll.  Returns the previous limit."""
     return int(lib().arma_gpu_set_wait_limit_ns(int(ns)))
+
+
+def device_address(ptr: int) -> int:
+    """The address at which the library's kernels reach memory at ``ptr``
+    (device memory: ``ptr``; pinned host memory the GPU maps: its mapped
+    address).  Raises ArmaError for memory the device cannot address."""
+    out = ctypes.c_void_p()
+    _check(lib().arma_gpu_device_address(ctypes.c_void_p(ptr), ctypes.byref(out)), "arma_gpu_device_address")
+    return int(out.value)
 
 
 def torch_dtype(dt: int):

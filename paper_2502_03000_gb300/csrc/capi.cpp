@@ -278,6 +278,27 @@ const char* arma_gpu_last_cuda_error(void) { return g_last_cuda; }
 
 uint64_t arma_gpu_set_wait_limit_ns(uint64_t ns) { return wait_ns_setting().exchange(ns); }
 
+arma_status arma_gpu_device_address(const void* p, void** dptr) {
+  if (!dptr) return ARMA_ERR_INVALID;
+  *dptr = nullptr;
+  if (!p) return ARMA_ERR_INVALID;
+  cudaPointerAttributes at;
+  std::memset(&at, 0, sizeof at);
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return ARMA_ERR_INVALID;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+    *dptr = const_cast<void*>(p);
+    return ARMA_OK;
+  }
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+    *dptr = at.devicePointer;
+    return ARMA_OK;
+  }
+  return ARMA_ERR_INVALID;
+}
+
 const char* arma_gpu_status_string(arma_status s) {
   switch (s) {
     case ARMA_OK: return "ok";
