@@ -99,15 +99,19 @@ __device__ __forceinline__ void split3_rn(float x, uint16_t (&sl)[3]) {
 // (0: op(A), 1: op(B)^T) of one problem, with all their K blocks; warp w of
 // the grid takes runs w, w + W, ...  Pair t of a run is (row t / nkb, K
 // block t % nkb), K block fastest, so a warp reads consecutive source
-// memory.  A lane group copies one pair per step: 8 lanes of 16 bytes (BF16)
-// or 16 lanes of 16 bytes (FP32, then split) from aligned 16-byte loads of
-// the source row, each lane joining its chunk with the next lane's (rows may
-// start at any element).  Only chunks that hold an element of the row are
-// loaded, and elements past K are zero.  All loads of a step are issued
-// before their data is used.  Packed row (kb, r) of a problem lies at
-// p_g + kb R + r.
+// memory.  Packed row (kb, r) of a problem lies at p_g + kb R + r.  Elements
+// past K are zero.  All loads of a step are issued before their data is used.
+//   BF16: a group of 8 lanes copies one pair per step, 16 bytes a lane, from
+//         aligned 16-byte loads of the source row, each lane joining its
+//         chunk with the next lane's (rows may start at any element).  Only
+//         chunks that hold an element of the row are loaded.
+//   FP32: a warp per pair, a float pair per lane (one 8-byte load when the
+//         row starts are even), then the exact three-way split; pairs taken
+//         K block by K block, so consecutive pairs write consecutive rows of
+//         the three slice arrays.
 // ---------------------------------------------------------------------------
-constexpr int PU = 2;   // pairs per lane group and step
+constexpr int PU = 2;     // BF16: pairs per lane group and step
+constexpr int PU32 = 16;  // FP32: pairs per warp and step
 
 // bytes sh .. sh + 15 of the 32 bytes c (sh even): shift by 2 words, by one
 // word, then by 16 bits
@@ -122,13 +126,119 @@ __device__ __forceinline__ uint4 window16(const uint32_t (&c)[8], uint32_t sh) {
                     __funnelshift_r(e[2], e[3], fs), __funnelshift_r(e[3], e[4], fs));
 }
 
+// one run of BF16 pairs
+__device__ __forceinline__ void pack_run_bf16(const char* X, int64_t ld, int64_t R, int64_t K, int64_t p0,
+                                              int32_t r0, int64_t T, uint32_t nkb, uint4* out, int lane) {
+  const int gsub = lane >> 3, j = lane & 7;
+  for (int64_t t0 = 0; t0 < T; t0 += 4 * PU) {
+    uint4 q[PU], qx[PU];
+    int64_t dst[PU];
+    uint32_t shv[PU];
+    int nvv[PU];
+#pragma unroll
+    for (int u = 0; u < PU; ++u) {
+      const int64_t t = t0 + 4 * u + gsub;
+      const bool rv = t < T;
+      const uint32_t tu = (uint32_t)(rv ? t : 0);
+      const uint32_t rl = tu / nkb, kb = tu - rl * nkb;
+      const int64_t r = r0 + rl;
+      dst[u] = rv ? p0 + (int64_t)kb * R + r : -1;
+      const int nv = rv ? (int)min((int64_t)GK, K - (int64_t)GK * kb) : 0;   // elements of this pair
+      nvv[u] = nv;
+      const char* A = X + 2 * (r * ld + (int64_t)GK * kb);
+      const uint32_t sh = (uint32_t)(reinterpret_cast<uintptr_t>(A) & 15u);
+      shv[u] = sh;
+      const char* a0 = A - sh;
+      const char* last = A + 2 * nv - 1;
+      q[u] = make_uint4(0u, 0u, 0u, 0u);
+      qx[u] = q[u];
+      if (nv > 0 && a0 + 16 * j <= last) q[u] = __ldg(reinterpret_cast<const uint4*>(a0 + 16 * j));
+      if (nv > 0 && j == 7 && a0 + 128 <= last) qx[u] = __ldg(reinterpret_cast<const uint4*>(a0 + 128));
+    }
+#pragma unroll
+    for (int u = 0; u < PU; ++u) {
+      uint4 nx;
+      nx.x = __shfl_down_sync(0xffffffffu, q[u].x, 1, 8);
+      nx.y = __shfl_down_sync(0xffffffffu, q[u].y, 1, 8);
+      nx.z = __shfl_down_sync(0xffffffffu, q[u].z, 1, 8);
+      nx.w = __shfl_down_sync(0xffffffffu, q[u].w, 1, 8);
+      if (j == 7) nx = qx[u];
+      const uint32_t c[8] = {q[u].x, q[u].y, q[u].z, q[u].w, nx.x, nx.y, nx.z, nx.w};
+      uint4 w = window16(c, shv[u]);
+      if (8 * j + 8 > nvv[u]) {   // past the pair's valid elements: zero
+        uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt) {
+          const int e = 8 * j + 2 * tt;
+          if (e >= nvv[u]) ww[tt] = 0u;
+          else if (e + 1 >= nvv[u]) ww[tt] &= 0xFFFFu;
+        }
+        w = make_uint4(ww[0], ww[1], ww[2], ww[3]);
+      }
+      if (dst[u] >= 0) out[dst[u] * 8 + j] = w;
+    }
+  }
+}
+
+// one run of FP32 pairs, split into S slices: K block by K block, rows r0 ..
+// r0 + nr - 1 within each, a source pointer walked from pair to pair
+template <int S>
+__device__ __forceinline__ void pack_run_f32(const float* X, int64_t ld, int64_t R, int64_t K, int64_t p0,
+                                             int32_t r0, int32_t nr, int64_t T, int64_t rows, uint32_t* out,
+                                             int lane) {
+  const bool pairs = (ld & 1) == 0 && (reinterpret_cast<uintptr_t>(X) & 7u) == 0;
+  int32_t rl = 0;
+  int64_t c = 2 * lane, base = p0 + r0;   // base: packed row of (this K block, row r0)
+  const float* src = X + (int64_t)r0 * ld + c;
+  for (int64_t t0 = 0; t0 < T; t0 += PU32) {
+    float x0[PU32], x1[PU32];
+    const int32_t rl0 = rl;        // the walk's state at the step's first pair,
+    const int64_t base0 = base;    // replayed for the stores
+#pragma unroll
+    for (int u = 0; u < PU32; ++u) {
+      x0[u] = x1[u] = 0.f;
+      if (t0 + u < T && c < K) {
+        if (pairs && c + 1 < K) {
+          const float2 f = __ldg(reinterpret_cast<const float2*>(src));
+          x0[u] = f.x;
+          x1[u] = f.y;
+        } else {
+          x0[u] = __ldg(src);
+          x1[u] = c + 1 < K ? __ldg(src + 1) : 0.f;
+        }
+      }
+      // the next pair: the next row of this K block, or row r0 of the next
+      src += ld;
+      if (++rl == nr) {
+        rl = 0;
+        c += GK;
+        base += R;
+        src = X + (int64_t)r0 * ld + c;
+      }
+    }
+    int32_t rs = rl0;
+    int64_t bs = base0;
+#pragma unroll
+    for (int u = 0; u < PU32; ++u) {
+      if (t0 + u >= T) break;
+      uint16_t a0[3], a1[3];
+      split3_rn(x0[u], a0);
+      split3_rn(x1[u], a1);
+      const int64_t dst = bs + rs;
+#pragma unroll
+      for (int sl = 0; sl < S; ++sl)
+        out[((int64_t)sl * rows + dst) * (GK / 2) + lane] = (uint32_t)a0[sl] | ((uint32_t)a1[sl] << 16);
+      if (++rs == nr) {
+        rs = 0;
+        bs += R;
+      }
+    }
+  }
+}
+
 template <typename AT, int S>
 __global__ void __launch_bounds__(256, sizeof(AT) == 2 ? 4 : 3) grouped_pack_kernel(const __grid_constant__ GroupedArgs g) {
-  constexpr int LPR = sizeof(AT) == 2 ? 8 : 16;       // lanes per packed row
-  constexpr int GPW = 32 / LPR;                        // pairs per warp and unrolled step
-  constexpr int EPL = 16 / (int)sizeof(AT);            // source elements per lane
   const int lane = threadIdx.x & 31;
-  const int gsub = lane / LPR, j = lane % LPR;
   const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < g.n_items; it += W) {
     const int32_t code = g.pack_items[3 * it], r0 = g.pack_items[3 * it + 1], nr = g.pack_items[3 * it + 2];
@@ -136,81 +246,17 @@ __global__ void __launch_bounds__(256, sizeof(AT) == 2 ? 4 : 3) grouped_pack_ker
     const int op = code & 1;
     const GroupedProblem& P = g.probs[pi];
     const int64_t R = op ? P.n : P.m, K = P.k;
-    const char* X = static_cast<const char*>(op ? P.B : P.A);
+    const void* X = op ? P.B : P.A;
     const int64_t ld = op ? P.ldb : P.lda;
     const int64_t p0 = op ? P.pb : P.pa;
-    const int64_t rows = op ? g.rows_b : g.rows_a;
     const uint32_t nkb = (uint32_t)((K + GK - 1) / GK);
     const int64_t T = (int64_t)nr * nkb;
-    for (int64_t t0 = 0; t0 < T; t0 += GPW * PU) {
-      uint4 q[PU], qx[PU];
-      int64_t dst[PU];
-      uint32_t shv[PU];
-      int nvv[PU];
-#pragma unroll
-      for (int u = 0; u < PU; ++u) {
-        const int64_t t = t0 + GPW * u + gsub;
-        const bool rv = t < T;
-        const uint32_t tu = (uint32_t)(rv ? t : 0);
-        const uint32_t rl = tu / nkb, kb = tu - rl * nkb;
-        const int64_t r = r0 + rl;
-        dst[u] = rv ? p0 + (int64_t)kb * R + r : -1;
-        const int nv = rv ? (int)min((int64_t)GK, K - (int64_t)GK * kb) : 0;   // elements of this pair
-        nvv[u] = nv;
-        const char* A = X + (int64_t)sizeof(AT) * (r * ld + (int64_t)GK * kb);
-        const uint32_t sh = (uint32_t)(reinterpret_cast<uintptr_t>(A) & 15u);
-        shv[u] = sh;
-        const char* a0 = A - sh;
-        const char* last = A + (int64_t)sizeof(AT) * nv - 1;
-        q[u] = make_uint4(0u, 0u, 0u, 0u);
-        qx[u] = q[u];
-        if (nv > 0 && a0 + 16 * j <= last) q[u] = __ldg(reinterpret_cast<const uint4*>(a0 + 16 * j));
-        if (nv > 0 && j == LPR - 1 && a0 + 16 * LPR <= last)
-          qx[u] = __ldg(reinterpret_cast<const uint4*>(a0 + 16 * LPR));
-      }
-#pragma unroll
-      for (int u = 0; u < PU; ++u) {
-        uint4 nx;
-        nx.x = __shfl_down_sync(0xffffffffu, q[u].x, 1, LPR);
-        nx.y = __shfl_down_sync(0xffffffffu, q[u].y, 1, LPR);
-        nx.z = __shfl_down_sync(0xffffffffu, q[u].z, 1, LPR);
-        nx.w = __shfl_down_sync(0xffffffffu, q[u].w, 1, LPR);
-        if (j == LPR - 1) nx = qx[u];
-        const uint32_t c[8] = {q[u].x, q[u].y, q[u].z, q[u].w, nx.x, nx.y, nx.z, nx.w};
-        uint4 w = window16(c, shv[u]);
-        const int e0 = EPL * j;   // first source element of this lane
-        if (e0 + EPL > nvv[u]) {  // past the pair's valid elements: zero
-          uint32_t ww[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-          for (int tt = 0; tt < 4; ++tt) {
-            if constexpr (sizeof(AT) == 2) {
-              const int e = e0 + 2 * tt;
-              if (e >= nvv[u]) ww[tt] = 0u;
-              else if (e + 1 >= nvv[u]) ww[tt] &= 0xFFFFu;
-            } else {
-              if (e0 + tt >= nvv[u]) ww[tt] = 0u;
-            }
-          }
-          w = make_uint4(ww[0], ww[1], ww[2], ww[3]);
-        }
-        if (dst[u] < 0) continue;
-        if constexpr (S == 1) {
-          static_cast<uint4*>(op ? g.pack_b : g.pack_a)[dst[u] * 8 + j] = w;
-        } else {
-          // four FP32 values -> four BF16 of each slice (8 bytes a slice)
-          uint16_t s0[3], s1[3], s2[3], s3[3];
-          split3_rn(__uint_as_float(w.x), s0);
-          split3_rn(__uint_as_float(w.y), s1);
-          split3_rn(__uint_as_float(w.z), s2);
-          split3_rn(__uint_as_float(w.w), s3);
-          uint2* out = static_cast<uint2*>(op ? g.pack_b : g.pack_a);
-#pragma unroll
-          for (int sl = 0; sl < S; ++sl)
-            out[((int64_t)sl * rows + dst[u]) * 16 + j] =
-                make_uint2((uint32_t)s0[sl] | ((uint32_t)s1[sl] << 16), (uint32_t)s2[sl] | ((uint32_t)s3[sl] << 16));
-        }
-      }
-    }
+    if constexpr (sizeof(AT) == 2)
+      pack_run_bf16(static_cast<const char*>(X), ld, R, K, p0, r0, T, nkb,
+                    static_cast<uint4*>(op ? g.pack_b : g.pack_a), lane);
+    else
+      pack_run_f32<S>(static_cast<const float*>(X), ld, R, K, p0, r0, nr, T, op ? g.rows_b : g.rows_a,
+                      static_cast<uint32_t*>(op ? g.pack_b : g.pack_a), lane);
   }
 }
 

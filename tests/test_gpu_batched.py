@@ -240,3 +240,43 @@ def test_batched_strided_unaligned_operands(torch, dtype):
     assert bp.status()[0] == "ok"
     for i in range(len(inst)):
         check_instance(*inst[i], host[i], outs[i], dtype)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("form", ["no_c", "alpha_beta"])
+def test_batched_box_heights_and_forms(torch, dtype, form):
+    """m and n on both sides of every operand box height (16, 32, 64, 128)
+    and of the tile edge, one-element K and several K blocks; the family
+    without C (alpha*op(A)*op(B)) and with other alpha and beta"""
+    shapes = [(16, 17, 64), (17, 16, 65), (32, 33, 1), (33, 32, 127), (64, 65, 128), (65, 64, 129),
+              (128, 129, 200), (129, 128, 8), (255, 257, 2), (1, 300, 70)]
+    inst, host, ins, outs = [], [], [], []
+    for i, (m, n, k) in enumerate(shapes):
+        g = E.Graph()
+        A = g.input(0, k, m, dtype)
+        B = g.input(1, k, n, dtype)
+        Ah = synth.matrix(1500 + i, 1, k, m, dtype)
+        Bh = synth.matrix(1500 + i, 2, k, n, dtype)
+        if form == "no_c":
+            nodes, o = g.build(A.t() * B, E.trace(A.t() * B))
+            host.append([Ah, Bh])
+            ins.append([to_dev(Ah, dtype), to_dev(Bh, dtype)])
+        else:
+            C = g.input(2, m, n, "f32")
+            nodes, o = g.build(0.5 * A.t() * B - 1.5 * C, E.trace(A.t() * B))
+            Ch = synth.matrix(1500 + i, 3, m, n, "f32")
+            host.append([Ah, Bh, Ch])
+            ins.append([to_dev(Ah, dtype), to_dev(Bh, dtype), to_dev(Ch, "f32")])
+        inst.append((nodes, o))
+        outs.append([ag.empty_colmajor(m, n, torch.float32, "cuda"),
+                     torch.zeros(1, dtype=torch.float64, device="cuda")])
+    bp = ag.BatchedPlan(inst)
+    assert bp.info["tensor_cores"] is True
+    bp.bind(ins, outs, "cuda")
+    for o in outs:
+        o[0].fill_(float("nan"))
+    bp()
+    torch.cuda.synchronize()
+    assert bp.status()[0] == "ok"
+    for i in range(len(inst)):
+        check_instance(*inst[i], host[i], outs[i], dtype)
