@@ -195,6 +195,17 @@ typedef enum {
 #define ARMA_PLAN_REFINE_SHIFT 16
 #define ARMA_PLAN_REFINE_MASK  0xF0000u
 #define ARMA_PLAN_REFINE_STEPS(k) ((((uint32_t)(k)) & 0xFu) << ARMA_PLAN_REFINE_SHIFT)
+/* K splits of every product (the CTAs that share one output tile, their
+ * partial sums added by a combine pass): ARMA_PLAN_SPLITS(k), 1 <= k <= 15,
+ * asks for k (fewer when K has fewer blocks of the kernel's K step, or when
+ * the partial sums would pass 256 MB in the DFMA kernel); 0 (the default)
+ * keeps the library's per-SM work model.  ARMA_PLAN_NO_SPLITK is k = 1.  The
+ * products on the FP64-accurate sliced tier and matrix-vector products keep
+ * their own rule.  This is what an autotuner varies to time split counts on
+ * the caller's own operands. */
+#define ARMA_PLAN_SPLITS_SHIFT 20
+#define ARMA_PLAN_SPLITS_MASK  0xF00000u
+#define ARMA_PLAN_SPLITS(k)    ((((uint32_t)(k)) & 0xFu) << ARMA_PLAN_SPLITS_SHIFT)
 
 typedef struct arma_node {
   int32_t op;        /* arma_op */

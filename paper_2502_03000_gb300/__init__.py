@@ -51,6 +51,14 @@ def PLAN_REFINE_STEPS(k: int) -> int:
     return (int(k) & 0xF) << PLAN_REFINE_SHIFT
 
 
+def PLAN_SPLITS(k: int) -> int:
+    """Flag bits asking every product for k K splits (1..15); 0 keeps the
+    library's per-SM model (ARMA_PLAN_SPLITS)."""
+    if not 0 <= int(k) <= 15:
+        raise ValueError("split count must be in 0..15")
+    return (int(k) & 0xF) << 20
+
+
 class ArmaError(RuntimeError):
     def __init__(self, code: int, where: str, detail: str = ""):
         self.code = code

@@ -117,6 +117,7 @@ arma_status run_step(const Step& st, const Bind& b, cudaStream_t s, int* launche
       // to the same memory (launch_gemm re-checks every condition)
       a.sym = g.sym == 1 || (g.sym == 2 && a.A == a.B) ? 1 : 0;
       a.nosplit = g.nosplit;
+      a.split_req = g.split_req;
       return cuda_status(launch_gemm(a, s, launches));
     }
     case ST_DOT: {

@@ -159,6 +159,7 @@ struct GemmStep {
   // comparing the bound pointers
   int32_t sym = 0;
   int32_t nosplit = 0;      // 1: no split-K over CTAs (ARMA_PLAN_NO_SPLITK)
+  int32_t split_req = 0;    // K splits asked for (ARMA_PLAN_SPLITS), 0: the library's model
   Ref scratch;              // workspace for operand conversion / split-K partials
   int64_t scratch_bytes = 0;
 };
@@ -179,6 +180,7 @@ struct GemmArgs {
   int32_t sym;       // 1: A == B, lda == ldb, ta != tb, no C or scalings: only the
                      // lower-triangle tiles are computed, the rest is mirrored
   int32_t nosplit;   // 1: one CTA per output tile over the whole of K (no split-K)
+  int32_t split_req; // K splits asked for, 0: the library's model (nosplit wins)
   int32_t reuse_a;   // F64_SLICED: op(A)'s slices are already in scratch (an earlier call
                      // with the same A and scratch)
   int32_t max_ctas;  // tensor-core products: at most this many CTAs (0: one per SM), leaving
@@ -188,10 +190,10 @@ struct GemmArgs {
 
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t s, int* launches);
 int64_t gemm_scratch_bytes(const GemmStep& g);
-int64_t gemm_tc_scratch_bytes(int64_t m, int64_t n, int64_t k, int32_t tier);
-int gemm_tc_splits(int64_t m, int64_t n, int64_t k, int32_t tier, bool sym, bool nosplit);
+int64_t gemm_tc_scratch_bytes(int64_t m, int64_t n, int64_t k, int32_t tier, int32_t split_req = 0);
+int gemm_tc_splits(int64_t m, int64_t n, int64_t k, int32_t tier, bool sym, bool nosplit, int32_t split_req = 0);
 void gemm_step_shape(const GemmStep& g, int* splits, double* tiles);
-int64_t gemm_simt_scratch_bytes(int64_t m, int64_t n, int64_t k);
+int64_t gemm_simt_scratch_bytes(int64_t m, int64_t n, int64_t k, int32_t split_req = 0);
 // FP64-accurate products from exact BF16 slices (tier ARMA_TIER_F64_SLICED)
 int64_t gemm_ozaki_scratch_bytes(int64_t m, int64_t n, int64_t k);
 bool gemm_ozaki_supported(const GemmArgs& a);

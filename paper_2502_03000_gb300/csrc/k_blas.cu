@@ -452,8 +452,20 @@ cudaError_t launch_mirror_lower(void* D, int64_t n, int64_t ldd, int32_t ddt, cu
   return cudaGetLastError();
 }
 
-int64_t gemm_simt_scratch_bytes(int64_t m, int64_t n, int64_t k) {
-  const int s = simt_splits(m, n, k);
+// the DFMA kernel's K splits: the model's, or as many as asked for (at most
+// one per BK block of K, partial sums within 256 MB)
+int simt_split_count(int64_t m, int64_t n, int64_t k, bool nosplit, int32_t req) {
+  if (nosplit) return 1;
+  if (req <= 0) return simt_splits(m, n, k);
+  int s = req;
+  const int64_t kb = (k + BK - 1) / BK;
+  if (s > kb) s = kb > 0 ? (int)kb : 1;
+  while (s > 1 && (double)s * (double)m * (double)n * 8.0 > 256e6) --s;
+  return s < 1 ? 1 : s;
+}
+
+int64_t gemm_simt_scratch_bytes(int64_t m, int64_t n, int64_t k, int32_t split_req) {
+  const int s = simt_split_count(m, n, k, false, split_req);
   return s > 1 ? (int64_t)s * m * n * 8 : 0;
 }
 
@@ -474,10 +486,10 @@ void gemm_step_shape(const GemmStep& g, int* splits, double* tiles) {
   }
   const bool tc = g.tier == ARMA_TIER_SPLIT_BF16 || g.tier == ARMA_TIER_BF16;
   if (tc) {
-    *splits = gemm_tc_splits(g.m, g.n, g.k, g.tier, g.sym != 0, g.nosplit != 0);
+    *splits = gemm_tc_splits(g.m, g.n, g.k, g.tier, g.sym != 0, g.nosplit != 0, g.split_req);
     *tiles = (double)((g.m + 127) / 128) * (double)((g.n + 255) / 256);
   } else {
-    *splits = g.nosplit ? 1 : simt_splits(g.m, g.n, g.k);
+    *splits = simt_split_count(g.m, g.n, g.k, g.nosplit != 0, g.split_req);
     *tiles = (double)((g.m + BM - 1) / BM) * (double)((g.n + BN - 1) / BN);
   }
 }
@@ -487,8 +499,8 @@ int64_t gemm_scratch_bytes(const GemmStep& g) {
     int64_t rows = g.n == 1 ? g.m : g.n;
     return 64 * rows * 8;
   }
-  const int64_t tc = gemm_tc_scratch_bytes(g.m, g.n, g.k, g.tier);
-  const int64_t simt = gemm_simt_scratch_bytes(g.m, g.n, g.k);
+  const int64_t tc = gemm_tc_scratch_bytes(g.m, g.n, g.k, g.tier, g.split_req);
+  const int64_t simt = gemm_simt_scratch_bytes(g.m, g.n, g.k, g.split_req);
   int64_t b = tc > simt ? tc : simt;
   if (g.tier == ARMA_TIER_F64_SLICED) {
     const int64_t oz = gemm_ozaki_scratch_bytes(g.m, g.n, g.k);
@@ -514,7 +526,7 @@ cudaError_t launch_gemm(const GemmArgs& a0, cudaStream_t s, int* launches) {
   a.sym = gemm_sym_valid(a0);   // anything else is a general product
   if (a.tier == ARMA_TIER_F64_SLICED && gemm_ozaki_supported(a)) return launch_gemm_ozaki(a, s, launches);
   if (a.tier != ARMA_TIER_F64 && gemm_tc_supported(a)) return launch_gemm_tc(a, s, launches);
-  int splits = a.nosplit ? 1 : simt_splits(a.m, a.n, a.k);
+  int splits = simt_split_count(a.m, a.n, a.k, a.nosplit != 0, a.split_req);
   if (splits > 1 && (!a.scratch || a.scratch_bytes < (int64_t)splits * a.m * a.n * 8)) splits = 1;
   const int64_t tm = (a.m + BM - 1) / BM, tn = (a.n + BN - 1) / BN;
   dim3 grid((unsigned)(a.sym ? tm * (tm + 1) / 2 : tm), (unsigned)(a.sym ? 1 : tn), (unsigned)splits);

@@ -663,7 +663,8 @@ struct Geometry {
 
 // sym: op(B)^T is op(A), so one prepared operand serves both TMA maps; its
 // rows are padded to a multiple of both tile heights
-Geometry geometry(int64_t m, int64_t n, int64_t k, int32_t tier, bool sym = false, bool nosplit = false) {
+Geometry geometry(int64_t m, int64_t n, int64_t k, int32_t tier, bool sym = false, bool nosplit = false,
+                  int32_t req = 0) {
   Geometry g;
   g.terms = tier == ARMA_TIER_SPLIT_BF16 ? 6 : 1;
   g.slices = tier == ARMA_TIER_SPLIT_BF16 ? 3 : 1;
@@ -674,9 +675,12 @@ Geometry geometry(int64_t m, int64_t n, int64_t k, int32_t tier, bool sym = fals
   g.tiles_n = (int32_t)(g.npad / BN);
   const int64_t kb = (k + BK - 1) / BK;
   // split K over CTAs only when the output has too few tiles to fill the GPU
+  // (or as many splits as asked for)
   int64_t splits = 1;
   const int64_t tiles = (int64_t)g.tiles_m * g.tiles_n;
-  while (!nosplit && tiles * splits < 148 && kb / (splits * 2) >= 4) splits *= 2;
+  if (!nosplit && req > 0) splits = req;
+  else
+    while (!nosplit && tiles * splits < 148 && kb / (splits * 2) >= 4) splits *= 2;
   if (splits > kb) splits = kb > 0 ? kb : 1;
   g.splits = (int32_t)(splits < 1 ? 1 : splits);
   g.kb_per_split = (int32_t)((kb + g.splits - 1) / g.splits);
@@ -748,26 +752,26 @@ bool gemm_tc_supported(const GemmArgs& a) {
   if (a.m < 1 || a.n < 1 || a.k < 1) return false;
   if (a.m > (1ll << 30) || a.n > (1ll << 30) || a.k > (1ll << 30)) return false;
   if (!a.scratch) return false;
-  tc::Geometry g = tc::geometry(a.m, a.n, a.k, a.tier, a.sym != 0, a.nosplit != 0);
+  tc::Geometry g = tc::geometry(a.m, a.n, a.k, a.tier, a.sym != 0, a.nosplit != 0, a.split_req);
   return a.scratch_bytes >= g.a_bytes + g.b_bytes + g.p_bytes + 1024;
 }
 
-int gemm_tc_splits(int64_t m, int64_t n, int64_t k, int32_t tier, bool sym, bool nosplit) {
+int gemm_tc_splits(int64_t m, int64_t n, int64_t k, int32_t tier, bool sym, bool nosplit, int32_t split_req) {
   if (m < 1 || n < 1 || k < 1) return 1;
-  return tc::geometry(m, n, k, tier, sym, nosplit).splits;
+  return tc::geometry(m, n, k, tier, sym, nosplit, split_req).splits;
 }
 
-int64_t gemm_tc_scratch_bytes(int64_t m, int64_t n, int64_t k, int32_t tier) {
+int64_t gemm_tc_scratch_bytes(int64_t m, int64_t n, int64_t k, int32_t tier, int32_t split_req) {
   if (tier != ARMA_TIER_SPLIT_BF16 && tier != ARMA_TIER_BF16) return 0;
   if (m < 1 || n < 1 || k < 1) return 0;
-  tc::Geometry g = tc::geometry(m, n, k, tier);
+  tc::Geometry g = tc::geometry(m, n, k, tier, false, false, split_req);
   return g.a_bytes + g.b_bytes + g.p_bytes + 1024;
 }
 
 cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* launches) {
   using namespace tc;
   const bool sym = a.sym != 0;
-  Geometry g = geometry(a.m, a.n, a.k, a.tier, sym, a.nosplit != 0);
+  Geometry g = geometry(a.m, a.n, a.k, a.tier, sym, a.nosplit != 0, a.split_req);
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(a.scratch) + 255) & ~uintptr_t(255));
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(base);
   __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(base + ((g.a_bytes + 255) / 256) * 256);

@@ -802,6 +802,7 @@ void Planner::emit_gemm(int64_t m, int64_t n, int64_t k, const MatOperand& A, co
     else if (A.ref.kind == REF_INPUT) g.sym = 2;
   }
   g.nosplit = (e_.flags & ARMA_PLAN_NO_SPLITK) ? 1 : 0;
+  g.split_req = (int32_t)((e_.flags & ARMA_PLAN_SPLITS_MASK) >> ARMA_PLAN_SPLITS_SHIFT);
   g.scratch_bytes = gemm_scratch_bytes(g);
   if (g.scratch_bytes > 0) g.scratch = ref_ws(alloc_ws(g.scratch_bytes));
   Step st;
@@ -816,7 +817,8 @@ void Planner::emit_gemm(int64_t m, int64_t n, int64_t k, const MatOperand& A, co
      << (g.sym == 2 ? " (symmetric if both slots hold the same matrix)" : "") << " op(A)="
      << (A.trans ? "T" : "N") << " op(B)=" << (B.trans ? "T" : "N") << " alpha=" << alpha
      << " beta=" << g.beta << (rs ? " rowscale" : "") << (cs ? " colscale" : "") << " tier="
-     << tier_name(g.tier) << (g.nosplit ? " nosplit" : "") << " (" << why << ")";
+     << tier_name(g.tier) << (g.nosplit ? " nosplit" : "")
+     << (g.split_req > 0 && !g.nosplit ? " splits=" + std::to_string(g.split_req) : std::string()) << " (" << why << ")";
   st.note = os.str();
   push_step(std::move(st));
 }
@@ -1662,7 +1664,14 @@ arma_status Planner::run() {
     for (auto& ch : note) if (ch == '"') ch = '\'';
     const char* kname = (s.kind == ST_GEMM && s.gemm.sym == 1 && s.gemm.m > 1) ? "syrk" : kn[s.kind];
     os << (i ? ", " : "") << "{\"kernel\": \"" << kname << "\", \"flops\": " << s.flops
-       << ", \"bytes\": " << s.bytes << ", \"note\": \"" << note << "\"}";
+       << ", \"bytes\": " << s.bytes << ", \"note\": \"" << note << "\"";
+    if (s.kind == ST_GEMM) {   // the K splits the product kernels will use
+      int sp = 1;
+      double tiles = 0;
+      gemm_step_shape(s.gemm, &sp, &tiles);
+      os << ", \"splits\": " << sp;
+    }
+    os << "}";
   }
   os << "], \"flops\": " << p_.flops << ", \"bytes\": " << p_.bytes << "}";
   p_.log = os.str();

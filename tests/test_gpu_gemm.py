@@ -219,3 +219,46 @@ def test_sliced_f64_benchmark_size_sampled(torch):
     got = D[torch.as_tensor(ii), torch.as_tensor(jj)].double().cpu().numpy()
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert err <= TOL["f64"], err
+
+
+@pytest.mark.parametrize("tier", ["split_bf16", "bf16", "f64"])
+def test_requested_split_counts(torch, tier):
+    """every K split count a plan may ask for (ARMA_PLAN_SPLITS) gives the
+    oracle's product at the tier's tolerance, tensor-core and DFMA kernels"""
+    m, n, k = 300, 200, 2500
+    nodes, outs, shapes = product_case(m, n, k, 1, 0, "f64", extra=True)
+    host = [synth.matrix(31, s + 1, r, c, "f64") for s, (r, c) in enumerate(shapes)]
+    ref = oracle.evaluate(nodes, outs, host)
+    ins = [to_dev(h, "f64") for h in host]
+    seen = set()
+    for kreq in (1, 2, 3, 4, 8, 15):
+        plan = ag.Plan(nodes, outs, tier=tier, flags=ag.PLAN_SPLITS(kreq))
+        sp = [st["splits"] for st in plan.info["steps"] if st["kernel"] == "gemm"]
+        assert all(1 <= x <= kreq for x in sp)
+        seen.add(tuple(sp))
+        got = plan(*ins)
+        torch.cuda.synchronize()
+        assert plan.status()[0] == "ok"
+        check(got, ref, TOL[tier if tier != "f64" else "f64"], f"{tier} splits={kreq}")
+    assert len(seen) >= 4
+
+
+def test_autotuner_times_split_counts(torch, tmp_path, monkeypatch):
+    """the autotuner times the distinct split counts of a product on the
+    caller's operands, keeps the fastest, persists the choice, and reuses it"""
+    from paper_2502_03000_gb300 import autotune
+    m, n, k = 512, 384, 6000
+    nodes, outs, shapes = product_case(m, n, k, 1, 0, "f32", extra=True)
+    host = [synth.matrix(32, s + 1, r, c, "f32") for s, (r, c) in enumerate(shapes)]
+    ins = [to_dev(h, "f32") for h in host]
+    cache = str(tmp_path / "tune.json")
+    monkeypatch.setenv("ARMA_AUTOTUNE_CACHE", cache)
+    best, times = autotune.tune_plan(nodes, outs, ins, tier="split_bf16", reps=2)
+    assert len(times) >= 3 and all(t > 0 for t in times.values())
+    got = best(*ins)
+    torch.cuda.synchronize()
+    check(got, oracle.evaluate(nodes, outs, host), TOL["split_bf16"], "tuned")
+    import os
+    assert os.path.exists(cache)
+    best2, times2 = autotune.tune_plan(nodes, outs, ins, tier="split_bf16", reps=2)
+    assert list(times2) == [min(times, key=times.get)]

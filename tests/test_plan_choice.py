@@ -129,3 +129,30 @@ def test_wait_limit_roundtrip():
     old = ag.set_wait_limit_ns(12345)
     assert ag.set_wait_limit_ns(old) == 12345
     assert ag.lib().arma_gpu_status_string(10) == b"a bounded device-side wait ran out"
+
+
+def test_split_count_flag():
+    """ARMA_PLAN_SPLITS(k): the plan's products report the split count they
+    will use, k or fewer (K blocks), and NO_SPLITK is one split"""
+    assert ag.PLAN_SPLITS(3) == 3 << 20
+    with pytest.raises(ValueError):
+        ag.PLAN_SPLITS(16)
+    nodes, outs = E.config_products(1024, "f64")
+    for tier in ("bf16", "split_bf16", "f64"):
+        for k in (1, 2, 4, 8, 15):
+            p = ag.Plan(nodes, outs, tier=tier, flags=ag.PLAN_SPLITS(k))
+            sp = [s["splits"] for s in p.info["steps"] if s["kernel"] == "gemm"]
+            assert sp and all(1 <= x <= k for x in sp), (tier, k, sp)
+        p = ag.Plan(nodes, outs, tier=tier, flags=ag.PLAN_NO_SPLITK | ag.PLAN_SPLITS(8))
+        assert [s["splits"] for s in p.info["steps"] if s["kernel"] == "gemm"] == [1]
+
+
+def test_autotune_table_keeps_split_choices(tmp_path):
+    from paper_2502_03000_gb300 import autotune
+    nodes, outs = E.config_products(256, "f32")
+    sig = autotune.plan_signature(nodes, outs, "split_bf16", 0)
+    autotune._cache[sig] = "splits4"
+    path = str(tmp_path / "t.json")
+    autotune.save(path)
+    del autotune._cache[sig]
+    assert autotune.load(path) >= 1 and autotune._cache[sig] == "splits4"
