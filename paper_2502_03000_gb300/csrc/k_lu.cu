@@ -1445,8 +1445,11 @@ cudaError_t factor_lookahead(const SolveArgs& a, const Layout& L, char* base, cu
   const int sms = device_sm_count();
   const int32_t gt = a.tier == ARMA_TIER_BF16 ? ARMA_TIER_BF16 : ARMA_TIER_SPLIT_BF16;
   cudaError_t e = cudaSuccess;
+  // the trailing update of columns [c0, c0 + nc): the next panel's columns
+  // (tier NATIVE with FP32 data: the FP32 SIMT product, one CTA per output
+  // tile, no preparation pass) or the rest (the tensor-core product)
   auto gemm = [&](int64_t m, int64_t nc, int64_t k, int64_t j, int64_t c0, char* scratch, int64_t sb, int max_ctas,
-                  cudaStream_t st) -> cudaError_t {
+                  cudaStream_t st, int32_t tier, int32_t nosplit) -> cudaError_t {
     GemmArgs g;
     memset(&g, 0, sizeof g);
     g.m = m; g.n = nc; g.k = k;
@@ -1455,7 +1458,8 @@ cudaError_t factor_lookahead(const SolveArgs& a, const Layout& L, char* base, cu
     g.C = W + (j + k) + c0 * n; g.ldc = n; g.cdt = ARMA_F32;
     g.D = W + (j + k) + c0 * n; g.ldd = n; g.ddt = ARMA_F32;
     g.alpha = -1.0; g.beta = 1.0;
-    g.tier = gt;
+    g.tier = tier;
+    g.nosplit = nosplit;
     g.scratch = scratch; g.scratch_bytes = sb;
     g.status = a.status_code;
     g.max_ctas = max_ctas;
@@ -1495,28 +1499,32 @@ cudaError_t factor_lookahead(const SolveArgs& a, const Layout& L, char* base, cu
     const int w2 = (int)(rest < NB ? rest : NB);     // the next panel's width
     // R of the previous panel is updated (it holds this panel's N)
     if (j > 0 && (e = cudaStreamWaitEvent(h, ev_rest, 0)) != cudaSuccess) goto out;
-    if (j > 0) {
-      laswp_range_kernel<T><<<(unsigned)((j + 255) / 256), 256, 0, h>>>(W, n, j, w, piv, 0, j);
-      if (launches) ++*launches;
-    }
     if (w2 > 0) {
       laswp_range_kernel<T><<<1, 256, 0, h>>>(W, n, j, w, piv, j + w, j + w + w2);
       trsm_kernel<T><<<(unsigned)((w2 + 7) / 8), 256, 0, h>>>(W, n, j + w + w2, j, w, j + w);
       if (launches) *launches += 2;
-      if ((e = gemm(rest, w2, w, j, j + w, base + L.gemm2, L.gemm2_bytes, 0, h)) != cudaSuccess) goto out;
+      if ((e = gemm(rest, w2, w, j, j + w, base + L.gemm2, L.gemm2_bytes, 0, h, ARMA_TIER_NATIVE, 1)) != cudaSuccess)
+        goto out;
     }
     if ((e = cudaEventRecord(ev_next, h)) != cudaSuccess) goto out;
+    // the caller's stream: R, then this panel's swaps of the factored columns
+    // on the left (nothing on the side stream reads them again)
+    if ((e = cudaStreamWaitEvent(s, ev_next, 0)) != cudaSuccess) goto out;
     const int64_t r0 = j + w + w2, rn = n - r0;       // R: columns [r0, n)
     if (rn > 0) {
-      if ((e = cudaStreamWaitEvent(s, ev_next, 0)) != cudaSuccess) goto out;
       laswp_range_kernel<T><<<(unsigned)((rn + 255) / 256), 256, 0, s>>>(W, n, j, w, piv, r0, n);
       trsm_kernel<T><<<(unsigned)((rn + 7) / 8), 256, 0, s>>>(W, n, n, j, w, r0);
       if (launches) *launches += 2;
-      if ((e = gemm(rest, rn, w, j, r0, base + L.gemm, L.gemm_bytes, sms - 16 > 1 ? sms - 16 : 1, s)) != cudaSuccess)
+      if ((e = gemm(rest, rn, w, j, r0, base + L.gemm, L.gemm_bytes, sms - 16 > 1 ? sms - 16 : 1, s, gt, 0)) !=
+          cudaSuccess)
         goto out;
       if ((e = cudaEventRecord(ev_rest, s)) != cudaSuccess) goto out;
     } else if (j + w < n) {
       if ((e = cudaEventRecord(ev_rest, h)) != cudaSuccess) goto out;   // nothing left of R
+    }
+    if (j > 0) {
+      laswp_range_kernel<T><<<(unsigned)((j + 255) / 256), 256, 0, s>>>(W, n, j, w, piv, 0, j);
+      if (launches) ++*launches;
     }
   }
   // the caller's stream continues after the side stream's last work
@@ -1574,21 +1582,30 @@ cudaError_t factor(const SolveArgs& a, const Layout& L, char* base, cudaStream_t
     if (rest > 0) {
       trsm_kernel<T><<<(unsigned)((rest + 7) / 8), 256, 0, s>>>(W, n, n, j, w);
       if (launches) ++*launches;
-      GemmArgs g;
-      memset(&g, 0, sizeof g);
+      // FP32 factors: the next panel's columns through the FP32 SIMT product
+      // and the rest through the tensor-core product, as the look-ahead
+      // factorisation splits them, so both give the same factors bit for bit
       const int dt = L.f64 ? ARMA_F64 : ARMA_F32;
-      g.m = rest; g.n = rest; g.k = w;
-      g.A = W + (j + w) + j * n; g.lda = n; g.ta = 0; g.adt = dt;
-      g.B = W + j + (j + w) * n; g.ldb = n; g.tb = 0; g.bdt = dt;
-      g.C = W + (j + w) + (j + w) * n; g.ldc = n; g.cdt = dt;
-      g.D = W + (j + w) + (j + w) * n; g.ldd = n; g.ddt = dt;
-      g.alpha = -1.0; g.beta = 1.0;
-      g.tier = gt;
-      g.scratch = base + L.gemm; g.scratch_bytes = L.gemm_bytes;
-      g.status = a.status_code;
-      g.no_gemv = 1;   // as the look-ahead factorisation does: the same kernel for every width
-      e = launch_gemm(g, s, launches);
-      if (e != cudaSuccess) return e;
+      const int64_t w2 = L.f64 ? rest : (rest < NB ? rest : NB);
+      for (int part = 0; part < 2; ++part) {
+        const int64_t c0 = part == 0 ? j + w : j + w + w2, nc = part == 0 ? w2 : rest - w2;
+        if (nc <= 0) continue;
+        GemmArgs g;
+        memset(&g, 0, sizeof g);
+        g.m = rest; g.n = nc; g.k = w;
+        g.A = W + (j + w) + j * n; g.lda = n; g.ta = 0; g.adt = dt;
+        g.B = W + j + c0 * n; g.ldb = n; g.tb = 0; g.bdt = dt;
+        g.C = W + (j + w) + c0 * n; g.ldc = n; g.cdt = dt;
+        g.D = W + (j + w) + c0 * n; g.ldd = n; g.ddt = dt;
+        g.alpha = -1.0; g.beta = 1.0;
+        g.tier = (part == 0 && !L.f64) ? ARMA_TIER_NATIVE : gt;
+        g.nosplit = (part == 0 && !L.f64) ? 1 : 0;
+        g.scratch = base + L.gemm; g.scratch_bytes = L.gemm_bytes;
+        g.status = a.status_code;
+        g.no_gemv = 1;   // the same product kernel for every block width
+        e = launch_gemm(g, s, launches);
+        if (e != cudaSuccess) return e;
+      }
     }
   }
   return cudaGetLastError();
