@@ -110,7 +110,8 @@ def test_batched_rejects_other_families(torch):
     assert ei.value.status == "unsupported"
 
 
-def test_batched_benchmark_size_sampled(torch):
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_batched_benchmark_size_sampled(torch, dtype):
     """10,000 instances (m, n, k log-uniform in [8, 512]) in one launch;
     sampled instances against the oracle"""
     count = 10000
@@ -121,22 +122,25 @@ def test_batched_benchmark_size_sampled(torch):
     gen = torch.Generator(device="cuda")
     gen.manual_seed(20250203 + 4)
 
-    def uni(r, c):
-        return (torch.rand((c, r), device="cuda", generator=gen) * 2 - 1).t()
+    td = torch.float32 if dtype == "f32" else torch.bfloat16
+
+    def uni(r, c, t=torch.float32):
+        return (torch.rand((c, r), device="cuda", generator=gen) * 2 - 1).to(t).t()
 
     for i in range(count):
-        nodes, o = E.config_batched_instance(int(m[i]), int(n[i]), int(k[i]), "f32")
+        nodes, o = E.config_batched_instance(int(m[i]), int(n[i]), int(k[i]), dtype)
         inst.append((nodes, o))
-        ins.append([uni(int(k[i]), int(m[i])), uni(int(k[i]), int(n[i])), uni(int(m[i]), int(n[i]))])
+        ins.append([uni(int(k[i]), int(m[i]), td), uni(int(k[i]), int(n[i]), td), uni(int(m[i]), int(n[i]))])
         outs.append([ag.empty_colmajor(int(m[i]), int(n[i]), torch.float32, "cuda"),
                      torch.zeros(1, dtype=torch.float64, device="cuda")])
     bp = ag.BatchedPlan(inst)
     bp.bind(ins, outs, "cuda")
     bp()
     torch.cuda.synchronize()
+    assert bp.info["tensor_cores"] is True
     for i in sorted(sample):
         h = [to_host(t) for t in ins[i]]
-        check_instance(*inst[i], h, outs[i], "f32")
+        check_instance(*inst[i], h, outs[i], dtype)
 
 
 def batch_of(torch, shapes, dtype, seed):
