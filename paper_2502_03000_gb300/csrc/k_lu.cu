@@ -646,6 +646,45 @@ __global__ void laswp_range_kernel(T* A, int64_t ld, int64_t j, int w, const int
   }
 }
 
+// The next panel's columns of the trailing update, FP32:
+// A(r, c0 + c) -= sum_{k < w} A(r, j + k) A(j + k, c0 + c) for rows r in
+// [j + w, n) and c < nc <= 64.  A CTA takes 32 rows: the w x nc block of U
+// and its 32 x w block of L in shared memory, each thread 8 outputs of one
+// row (K in ascending order).  Both factorisations use it for these columns.
+constexpr int NU_ROWS = 32;
+__global__ void __launch_bounds__(256) next_update_kernel(float* A, int64_t ld, int64_t n, int64_t j, int w,
+                                                          int64_t c0, int nc) {
+  __shared__ float U[NB][NB + 1];          // U[k][c]
+  __shared__ float Lt[NU_ROWS][NB + 1];    // Lt[row][k]
+  const int t = threadIdx.x;
+  const int64_t rb = j + w + (int64_t)blockIdx.x * NU_ROWS;
+  for (int idx = t; idx < NB * NB; idx += 256) {
+    const int k = idx % NB, c = idx / NB;
+    U[k][c] = (k < w && c < nc) ? A[(j + k) + (c0 + c) * ld] : 0.f;
+  }
+  for (int idx = t; idx < NU_ROWS * NB; idx += 256) {
+    const int row = idx % NU_ROWS, k = idx / NU_ROWS;
+    Lt[row][k] = (rb + row < n && k < w) ? A[(rb + row) + (j + k) * ld] : 0.f;
+  }
+  __syncthreads();
+  const int row = t >> 3, cg = t & 7;
+  const int64_t r = rb + row;
+  if (r >= n) return;
+  float acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+  for (int k = 0; k < w; ++k) {
+    const float l = Lt[row][k];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = fmaf(l, U[k][8 * cg + q], acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int c = 8 * cg + q;
+    if (c < nc) A[r + (c0 + c) * ld] -= acc[q];
+  }
+}
+
 // U12 = L11^-1 A12 (L11 unit lower w x w): one warp per column of A12, lane
 // l holding rows l and l + 32; the column is read and written coalesced
 // (columns [c0, n) of the block row; c0 = 0 means j + w)
@@ -1445,9 +1484,8 @@ cudaError_t factor_lookahead(const SolveArgs& a, const Layout& L, char* base, cu
   const int sms = device_sm_count();
   const int32_t gt = a.tier == ARMA_TIER_BF16 ? ARMA_TIER_BF16 : ARMA_TIER_SPLIT_BF16;
   cudaError_t e = cudaSuccess;
-  // the trailing update of columns [c0, c0 + nc): the next panel's columns
-  // (tier NATIVE with FP32 data: the FP32 SIMT product, one CTA per output
-  // tile, no preparation pass) or the rest (the tensor-core product)
+  // the trailing update of columns [c0, c0 + nc) past the next panel's (the
+  // tensor-core product; the next panel's columns take next_update_kernel)
   auto gemm = [&](int64_t m, int64_t nc, int64_t k, int64_t j, int64_t c0, char* scratch, int64_t sb, int max_ctas,
                   cudaStream_t st, int32_t tier, int32_t nosplit) -> cudaError_t {
     GemmArgs g;
@@ -1503,8 +1541,8 @@ cudaError_t factor_lookahead(const SolveArgs& a, const Layout& L, char* base, cu
       laswp_range_kernel<T><<<1, 256, 0, h>>>(W, n, j, w, piv, j + w, j + w + w2);
       trsm_kernel<T><<<(unsigned)((w2 + 7) / 8), 256, 0, h>>>(W, n, j + w + w2, j, w, j + w);
       if (launches) *launches += 2;
-      if ((e = gemm(rest, w2, w, j, j + w, base + L.gemm2, L.gemm2_bytes, 0, h, ARMA_TIER_NATIVE, 1)) != cudaSuccess)
-        goto out;
+      next_update_kernel<<<(unsigned)((rest + NU_ROWS - 1) / NU_ROWS), 256, 0, h>>>(W, n, n, j, w, j + w, w2);
+      if (launches) ++*launches;
     }
     if ((e = cudaEventRecord(ev_next, h)) != cudaSuccess) goto out;
     // the caller's stream: R, then this panel's swaps of the factored columns
@@ -1582,14 +1620,20 @@ cudaError_t factor(const SolveArgs& a, const Layout& L, char* base, cudaStream_t
     if (rest > 0) {
       trsm_kernel<T><<<(unsigned)((rest + 7) / 8), 256, 0, s>>>(W, n, n, j, w);
       if (launches) ++*launches;
-      // FP32 factors: the next panel's columns through the FP32 SIMT product
-      // and the rest through the tensor-core product, as the look-ahead
+      // FP32 factors: the next panel's columns through next_update_kernel and
+      // the rest through the tensor-core product, as the look-ahead
       // factorisation splits them, so both give the same factors bit for bit
       const int dt = L.f64 ? ARMA_F64 : ARMA_F32;
-      const int64_t w2 = L.f64 ? rest : (rest < NB ? rest : NB);
-      for (int part = 0; part < 2; ++part) {
-        const int64_t c0 = part == 0 ? j + w : j + w + w2, nc = part == 0 ? w2 : rest - w2;
-        if (nc <= 0) continue;
+      const int64_t w2 = L.f64 ? 0 : (rest < NB ? rest : NB);
+      if constexpr (std::is_same<T, float>::value) {
+        if (w2 > 0) {
+          next_update_kernel<<<(unsigned)((rest + NU_ROWS - 1) / NU_ROWS), 256, 0, s>>>(W, n, n, j, w, j + w,
+                                                                                        (int)w2);
+          if (launches) ++*launches;
+        }
+      }
+      const int64_t c0 = j + w + w2, nc = rest - w2;
+      if (nc > 0) {
         GemmArgs g;
         memset(&g, 0, sizeof g);
         g.m = rest; g.n = nc; g.k = w;
@@ -1598,8 +1642,7 @@ cudaError_t factor(const SolveArgs& a, const Layout& L, char* base, cudaStream_t
         g.C = W + (j + w) + c0 * n; g.ldc = n; g.cdt = dt;
         g.D = W + (j + w) + c0 * n; g.ldd = n; g.ddt = dt;
         g.alpha = -1.0; g.beta = 1.0;
-        g.tier = (part == 0 && !L.f64) ? ARMA_TIER_NATIVE : gt;
-        g.nosplit = (part == 0 && !L.f64) ? 1 : 0;
+        g.tier = gt;
         g.scratch = base + L.gemm; g.scratch_bytes = L.gemm_bytes;
         g.status = a.status_code;
         g.no_gemv = 1;   // the same product kernel for every block width
