@@ -8,7 +8,7 @@
  * It is the literal, eager evaluation that the paper uses as its "naive"
  * reference (Sec. II, the discussion of Z = 0.4*X + 0.6*Y before delayed
  * evaluation is introduced): every operator runs on its own and writes a
- * fresh temporary.  The Python driver (oracle/__init__.py) allocates those
+ * fresh temporary.  The Python side (oracle/__init__.py) allocates those
  * temporaries and walks the expression in written order; this file holds
  * one plain loop per operator.
  *

@@ -68,7 +68,7 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
     cmd = [nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-cudart", "static", "-lcuda"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        # the driver library is only needed for its entry-point lookup; link without it
+        # the CUDA driver library is only needed for its entry-point lookup; link without it
         cmd = cmd[:-1]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

@@ -12,8 +12,8 @@ The network predicts a correction to the FLOP/byte roofline estimate
 (arma_gpu_plan_heuristic_cost): predicted seconds = estimate *
 exp(network(standardised features)).  The estimate is also one of the
 features, so an untrained network (output 0) ranks exactly like the
-estimate.  The estimate remains the fallback (no model loaded) and the judge
-of the network's picks (the guard factor of arma_gpu_cost_model_load).
+estimate.  The estimate remains the fallback (no model loaded) and the check
+on the network's picks (the guard factor of arma_gpu_cost_model_load).
 
 Weights, feature scaling and the timing records persist as JSON
 (``CostNet.save`` / ``CostNet.load``, ``save_records`` / ``load_records``).
