@@ -433,10 +433,16 @@ arma_status arma_gpu_batched_table_bytes(const arma_plan* plan, size_t* bytes);
 arma_status arma_gpu_batched_table_fill(const arma_plan* plan, const void* const* in_ptrs,
                                         void* const* out_ptrs, void* host_table);
 
-/* Evaluate every instance of the batch: one persistent grouped kernel over
- * a tile list spanning all instances (plus one small kernel for traces).
- * device_table is the filled table in device memory; workspace as in
- * arma_gpu_eval.  Asynchronous on stream; capturable in a CUDA graph. */
+/* Evaluate every instance of the batch.  On the tensor cores (both
+ * operands K-contiguous, BF16 or FP32; the plan log's "tensor_cores") a pack
+ * kernel first copies every instance's op(A) and op(B)^T into packed
+ * K-block-major BF16 arrays in the workspace (FP32 as three exact BF16
+ * slices), then one persistent tcgen05 kernel reads them with TMA; the
+ * workspace (arma_gpu_plan_workspace) therefore holds about
+ * slices * 128 bytes per row of 64 of K of every operand.  Otherwise one
+ * persistent SIMT grouped kernel runs.  A small kernel adds the traces.
+ * device_table is the filled table in device memory.  Asynchronous on
+ * stream; capturable in a CUDA graph. */
 arma_status arma_gpu_eval_batched(const arma_plan* plan, const void* device_table, void* workspace,
                                   size_t workspace_bytes, void* stream);
 
