@@ -376,6 +376,15 @@ __global__ void __launch_bounds__(256, std::is_same<T, double>::value ? 4 : 3)
         ff.add_f32(ps, pq);
       }
     }
+    if constexpr (kFF && 4 * NIN <= 32) {
+      // this warp's chunks two grid-stride steps ahead into L2, one 128-byte
+      // line (8 chunks of 16 bytes) per lane: those reads are in flight while
+      // the FP64 pipe works on the next step
+      const int lane = threadIdx.x & 31;
+      const int64_t nx = c - lane + 2 * stride + (int64_t)(lane & 3) * 8;
+      if (lane < 4 * NIN && nx < nchunk)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(static_cast<const T*>(a.in[lane >> 2]) + nx * V));
+    }
   }
   rs += ff.sum();
   rq += ff.sumsq();
