@@ -147,9 +147,6 @@ bool is_binary(int op) {
   return op == ARMA_OP_ADD || op == ARMA_OP_SUB || op == ARMA_OP_SCHUR || op == ARMA_OP_DIV ||
          op == ARMA_OP_MATMUL || op == ARMA_OP_SOLVE;
 }
-bool is_reduction(int op) {
-  return op == ARMA_OP_TRACE || op == ARMA_OP_ACCU || op == ARMA_OP_NORM_FRO;
-}
 const char* op_name(int op) {
   static const char* names[] = {"input", "add", "sub", "schur", "div", "scale", "div_scalar",
                                 "add_scalar", "neg", "trans", "matmul", "diagmat", "trace",
@@ -161,7 +158,6 @@ const char* tier_name(int t) {
   static const char* names[] = {"native", "f64", "split_bf16", "bf16", "lu32_ir64"};
   return (t >= 0 && t <= 4) ? names[t] : "?";
 }
-const char* dtype_name(int d) { return d == ARMA_F64 ? "f64" : d == ARMA_F32 ? "f32" : "bf16"; }
 
 struct Factor {
   enum Kind { DENSE, DIAG, INV } kind = DENSE;
