@@ -2,7 +2,6 @@
 symbol the header declares, validates descriptors (the paper's conformance
 checks, Sec. II), orders matrix chains exactly like exhaustive search, and
 plans the paper's rewrites onto the expected kernels."""
-import ctypes
 import os
 import random
 import re

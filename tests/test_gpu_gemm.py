@@ -9,7 +9,7 @@ import oracle
 import paper_2502_03000_gb300 as ag
 import synth
 from paper_2502_03000_gb300 import expr as E
-from tests.gpu_util import TOL, check, inputs, need_gpu, to_dev, to_host
+from tests.gpu_util import TOL, check, need_gpu, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 

@@ -4,7 +4,6 @@ counts the work of every rank.  Two gloo ranks on 127.0.0.1."""
 import os
 import socket
 
-import pytest
 import torch.multiprocessing as mp
 
 
