@@ -129,6 +129,22 @@ def test_matmul_vs_numpy_and_transpose_identity(orc):
     np.testing.assert_array_equal(orc.matmul(P, A), A[::-1, :])
 
 
+def test_transpose_moves_entries(orc):
+    # element (i, j) of trans(X) is element (j, i) of X, square or not
+    for m, n in ((1, 1), (5, 5), (16, 16), (3, 7), (7, 3)):
+        X = np.arange(m * n, dtype=np.float64).reshape(m, n, order="F") + 1.0
+        T = orc.trans(X)
+        assert T.shape == (n, m)
+        for i in range(n):
+            for j in range(m):
+                assert T[i, j] == X[j, i]
+    # (S R)^T = R^T S^T for square factors too
+    S, R = _rand(4, 3, 12, 12), _rand(4, 4, 12, 12)
+    np.testing.assert_allclose(orc.trans(orc.matmul(S, R)), orc.matmul(orc.trans(R), orc.trans(S)),
+                               rtol=0, atol=1e-13)
+    assert not np.array_equal(orc.trans(S), S)
+
+
 def test_matmul_entries_match_full_product(orc):
     A, B = _rand(5, 1, 40, 31), _rand(5, 2, 31, 23)
     C = orc.matmul(A, B)
@@ -198,6 +214,18 @@ def test_solve_literal_and_backward_error(orc):
     assert orc.backward_error(A, X, B) < 1e-12
     Xn = np.linalg.solve(A, B)
     assert orc.rel_err(X, Xn) < 1e6 * 1e-13
+
+
+def test_backward_error_closed_form(orc):
+    # A = 2I, X = I, B = I (n = 4): B - AX = -I, so the error is
+    # ||I||_F / (||2I||_F ||I||_F + ||I||_F) = 2 / (4 * 2 + 2) = 0.2
+    I4 = np.eye(4)
+    assert orc.backward_error(2 * I4, I4, I4) == 0.2
+    # an exact solution has no backward error; X = 0 has the largest, 1
+    A = np.array([[2.0, 1.0], [1.0, 3.0]])
+    B = np.array([[3.0], [4.0]])
+    assert orc.backward_error(A, np.array([[1.0], [1.0]]), B) == 0.0
+    assert orc.backward_error(A, np.zeros((2, 1)), B) == 1.0
 
 
 def test_rel_err_definition(orc):
