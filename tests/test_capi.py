@@ -31,6 +31,23 @@ def test_exports_every_declared_symbol():
     assert set(ag.EXPORTS) <= declared
 
 
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without the compiled library, loading it and planning
+    through it raise instead of computing anything elsewhere."""
+    monkeypatch.setattr(ag, "LIB_PATH", str(tmp_path / "libarma_gpu.so"))
+    ag.lib.cache_clear()
+    try:
+        with pytest.raises(ImportError):
+            ag.lib()
+        nodes, outs = E.config_fused(8, "f64")
+        with pytest.raises(ImportError):
+            ag.Plan(nodes, outs)
+    finally:
+        monkeypatch.undo()
+        ag.lib.cache_clear()
+    assert ag.lib() is not None
+
+
 def test_status_strings():
     L = ag.lib()
     for code in range(11):
