@@ -231,14 +231,28 @@ typedef struct arma_expr {
 
 typedef struct arma_plan arma_plan;
 
-/* Validate and plan an expression (host only; no CUDA call).
- * On success *plan is a new plan; on error *plan is set to NULL. */
+/* Validate and plan an expression (host only; no CUDA call).  This is the
+ * point where the delayed expression of Sec. II is looked at as a whole and
+ * mapped onto kernels: the conformance checks, the rewrites of Sec. III
+ * (1)-(10), the chain order and, with ARMA_PLAN_COST_*, the choice among
+ * candidate plans.  expr and the arrays it points to are read only during
+ * the call.  Errors: ARMA_ERR_INVALID (null pointers, counts out of range,
+ * an operand index not below its node's, one input slot described twice
+ * differently), ARMA_ERR_SHAPE (non-conforming sizes, negative sizes,
+ * ld < max(1, rows)), ARMA_ERR_DTYPE (an unknown element type, or mixed
+ * element types where the operation needs equal ones), ARMA_ERR_UNSUPPORTED
+ * (a valid expression outside what this library evaluates).  On success
+ * *plan is a new plan, owned by the caller until arma_gpu_plan_free(); on
+ * error *plan is set to NULL. */
 arma_status arma_gpu_plan(const arma_expr* expr, arma_plan** plan);
 
-/* Workspace bytes arma_gpu_eval needs for this plan (256-byte aligned). */
+/* Workspace bytes arma_gpu_eval needs for this plan (the buffer itself must
+ * be 256-byte aligned).  ARMA_ERR_INVALID for a null argument. */
 arma_status arma_gpu_plan_workspace(const arma_plan* plan, size_t* bytes);
 
-/* Shape and element type of output i (scalars: 1 x 1, ARMA_F64). */
+/* Shape and element type of output i (scalars: 1 x 1, ARMA_F64), so that
+ * the caller can allocate out_ptrs[i].  ARMA_ERR_INVALID for a null plan or
+ * an i outside 0 .. n_outputs - 1; null output pointers are skipped. */
 arma_status arma_gpu_output_info(const arma_plan* plan, int32_t i, int64_t* rows,
                                  int64_t* cols, int32_t* dtype);
 
@@ -282,8 +296,12 @@ arma_status arma_gpu_eval_solve_path(const arma_plan* plan, const void* workspac
  * receives the full length + 1. */
 arma_status arma_gpu_plan_info(const arma_plan* plan, char* buf, size_t len, size_t* needed);
 
+/* Release a plan (NULL is ignored).  No evaluation of it may still be
+ * running on a stream; the caller's buffers are not touched. */
 void arma_gpu_plan_free(arma_plan* plan);
 
+/* A static, NUL-terminated name for a status code ("unknown status" for
+ * values outside arma_status). */
 const char* arma_gpu_status_string(arma_status status);
 
 /* Time limit of each bounded device-side wait that the solve kernels make
