@@ -403,16 +403,20 @@ void arma_gpu_cost_model_clear(void);
  * ARMA_ERR_UNSUPPORTED when no model is loaded. */
 arma_status arma_gpu_cost_model_predict(const arma_plan* plan, double* seconds);
 
-/* Cost network: y = W3 relu(W2 relu(W1 x + b1) + b2) + b3, FP32, with
- * features <= 64 inputs and hidden <= 128 units; parameters packed as
- * W1 (hidden x features, row-major), b1, W2 (hidden x hidden), b2, W3, b3.
- * All pointers are device pointers; calls are asynchronous on stream. */
+/* Cost network (this library's learned plan choice; the paper has none):
+ * y = W3 relu(W2 relu(W1 x + b1) + b2) + b3, FP32, with 1 <= features <= 64
+ * inputs and 1 <= hidden <= 128 units; parameters packed as W1 (hidden x
+ * features, row-major), b1, W2 (hidden x hidden), b2, W3, b3.  Samples are
+ * rows of x (n x features, row-major).  All pointers are device pointers
+ * owned by the caller; calls are asynchronous on stream.  Sizes out of range
+ * or null pointers give ARMA_ERR_INVALID, a failed launch ARMA_ERR_CUDA. */
 int64_t arma_gpu_mlp_param_count(int32_t features, int32_t hidden);
 
-/* Workspace bytes for arma_gpu_mlp_grad with n samples. */
+/* Workspace bytes for arma_gpu_mlp_grad with n samples (per-sample
+ * activations and deltas, plus 1 KiB). */
 size_t arma_gpu_mlp_workspace(int32_t features, int32_t hidden, int32_t n);
 
-/* y[i] = network(x[i * features ...]) for i < n. */
+/* y[i] = network(x[i * features ...]) for i < n (n = 0: nothing). */
 arma_status arma_gpu_mlp_forward(const float* params, int32_t features, int32_t hidden, const float* x,
                                  int32_t n, float* y, void* stream);
 
@@ -423,7 +427,9 @@ arma_status arma_gpu_mlp_grad(const float* params, int32_t features, int32_t hid
                               const float* target, int32_t n, float* grad, float* y_out, void* workspace,
                               size_t workspace_bytes, void* stream);
 
-/* One Adam step (Kingma and Ba, 2015) with bias correction for step >= 1. */
+/* One Adam step (Kingma and Ba, 2015) over count parameters, in place on
+ * params and the moment vectors m and v, with bias correction for step >= 1
+ * (ARMA_ERR_INVALID for step < 1, count < 1 or a null pointer). */
 arma_status arma_gpu_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t count,
                               int32_t step, float lr, float beta1, float beta2, float eps, void* stream);
 
