@@ -1,0 +1,87 @@
+"""Pins for the seeded input generators that both the CUDA path and the
+oracle receive their inputs from: the counter-based splitmix64 against the
+published outputs of the generator, BF16 rounding against torch's
+conversion, and the properties the tests rely on (the same values whatever
+the chunking or storage order, the stated ranges, the stated spectra)."""
+import numpy as np
+import pytest
+
+import synth
+
+
+def test_splitmix64_published_outputs():
+    # the first outputs of splitmix64 from state 0 (Vigna's splitmix64.c):
+    # seed 0, stream 0 starts from that state
+    got = [int(x) for x in synth.raw_u64(0, 0, 0, 4)]
+    assert got == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC]
+    # a counter window is a slice of the same sequence
+    assert [int(x) for x in synth.raw_u64(0, 0, 2, 2)] == got[2:]
+
+
+def test_streams_and_seeds_differ():
+    a = synth.raw_u64(1, 1, 0, 1000)
+    assert len(np.unique(a)) == 1000
+    assert not np.array_equal(a, synth.raw_u64(1, 2, 0, 1000))
+    assert not np.array_equal(a, synth.raw_u64(2, 1, 0, 1000))
+
+
+def test_uniform_range_moments_and_chunking():
+    v = synth.uniform_flat(7, 3, 1 << 16)
+    assert v.min() >= -1.0 and v.max() < 1.0
+    # uniform on [-1, 1): mean 0, variance 1/3 (65536 draws: standard errors 0.0023 and 0.0012)
+    assert abs(v.mean()) < 0.01 and abs(v.var() - 1.0 / 3.0) < 0.006
+    np.testing.assert_array_equal(v, synth.uniform_flat(7, 3, 1 << 16, chunk=1000))
+    np.testing.assert_array_equal(v[500:700], synth.uniform_flat(7, 3, 200, start=500))
+
+
+def test_matrix_is_column_major_over_the_stream():
+    M = synth.matrix(5, "B", 13, 7)
+    flat = synth.uniform_flat(5, synth.STREAMS["B"], 13 * 7)
+    for j in range(7):
+        np.testing.assert_array_equal(M[:, j], flat[13 * j:13 * (j + 1)])
+    assert M.flags.f_contiguous
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    x = np.concatenate([
+        synth.uniform_flat(9, 1, 4096).astype(np.float32),
+        # halfway cases: ties go to the even BF16 mantissa
+        np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, -(1 + 2.0 ** -8), 2.0 ** -130 * 3], dtype=np.float32),
+    ])
+    ours = synth.round_bf16(x)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    np.testing.assert_array_equal(ours, ref)
+    assert ours[4096] == 1.0 and ours[4097] == np.float32(1 + 2.0 ** -6)
+
+
+def test_cast_to_storage_types():
+    x = synth.uniform_flat(4, 2, 1000).reshape(40, 25, order="F")
+    np.testing.assert_array_equal(synth.cast(x, "f32"), x.astype(np.float32))
+    b = synth.cast(x, "bf16")
+    assert b.dtype == np.float32 and np.all((b.view(np.uint32) & 0xFFFF) == 0)
+    with pytest.raises(ValueError):
+        synth.cast(x, "f16")
+
+
+def test_small_ints_range():
+    s = synth.small_ints(3, 1, 30, 30)
+    assert set(np.unique(s)) <= set(range(-4, 5)) and len(np.unique(s)) == 9
+
+
+def test_conditioned_matrix_spectrum():
+    n = 96
+    for symmetric in (True, False):
+        A = synth.conditioned_matrix(11, n, cond=1e6, symmetric=symmetric)
+        s = np.linalg.svd(A, compute_uv=False)
+        np.testing.assert_allclose(np.sort(s), synth.geometric_spectrum(n, 1e6), rtol=1e-9)
+        if symmetric:
+            assert np.array_equal(A, A.T)
+            assert np.all(np.linalg.eigvalsh(A) > 0)
+
+
+def test_log_uniform_ints_range_and_spread():
+    v = synth.log_uniform_ints(20250203, 4, 20000, 8, 512)
+    assert v.min() == 8 and v.max() == 512
+    # log-uniform: the median is near the geometric mean sqrt(8 * 512) = 64
+    assert 58 <= np.median(v) <= 70
