@@ -85,3 +85,34 @@ def test_log_uniform_ints_range_and_spread():
     assert v.min() == 8 and v.max() == 512
     # log-uniform: the median is near the geometric mean sqrt(8 * 512) = 64
     assert 58 <= np.median(v) <= 70
+
+
+def test_random_dags_follow_the_recipe():
+    from synth.dags import random_dag
+
+    allowed = {"input", "add", "sub", "schur", "scale", "trans", "matmul", "diagmat", "trace"}
+
+    def levels(nodes, i):
+        # generator levels: diagmat(v) goes with the product it scales, a
+        # root trace with its argument
+        nd = nodes[i]
+        if nd["op"] == "input":
+            return 0
+        if nd["op"] in ("diagmat", "trace"):
+            return levels(nodes, nd["a"])
+        kids = [nd[k] for k in ("a", "b") if k in nd]
+        return 1 + max(levels(nodes, c) for c in kids)
+
+    dts = set()
+    for i in range(300):
+        nodes, outs, dt = random_dag(20250203 + 5, i)
+        assert (nodes, outs, dt) == random_dag(20250203 + 5, i)      # the same DAG every time
+        dts.add(dt)
+        assert {nd["op"] for nd in nodes} <= allowed
+        assert nodes[outs[0]]["op"] != "input"
+        assert levels(nodes, outs[0]) <= 5
+        for nd in nodes:
+            if nd["op"] == "input":
+                assert 1 <= nd["rows"] <= 8192 and 1 <= nd["cols"] <= 8192
+                assert nd["dtype"] == dt
+    assert dts == {"f32", "bf16"}
