@@ -3,7 +3,8 @@
 Expressions of depth <= 5 over +, -, % (Schur), scalar *, trans, * (matrix
 product), diagmat and trace, with dimensions drawn log-uniform in
 [lo, hi].  Shapes are chosen first and operands generated to conform, so
-every expression is valid.  Uniforms come from the counter-based generator
+every expression conforms in shape; element types may not (see the end
+of ``random_dag``).  Uniforms come from the counter-based generator
 in ``synth`` (stream 1000 + index), so DAG i is the same on every machine.
 """
 from __future__ import annotations
@@ -85,8 +86,9 @@ def random_dag(seed: int, index: int, lo: int = 16, hi: int = 8192, max_depth: i
         e = add({"op": "scale", "a": e, "s": 2.0})
     if r == c and d.u() < 0.3:
         e = add({"op": "trace", "a": e})
-    # products of BF16 operands return FP32; an elementwise op mixing a
-    # product with a BF16 leaf would not conform, so such DAGs use FP32
+    # products of BF16 operands return FP32, so an elementwise op that mixes
+    # a product with a BF16 leaf does not conform: the caller draws such a
+    # DAG again with dtype="f32"
     return nodes, [e], dt
 
 

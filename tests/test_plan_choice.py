@@ -156,3 +156,20 @@ def test_autotune_table_keeps_split_choices(tmp_path):
     autotune.save(path)
     del autotune._cache[sig]
     assert autotune.load(path) >= 1 and autotune._cache[sig] == "splits4"
+
+
+def test_planner_workload_dags_all_plan():
+    """The cost-model workload keeps only DAGs the library plans: BF16 DAGs
+    that do not conform are drawn again in FP32, and every kept DAG plans
+    both literally and optimised."""
+    from paper_2502_03000_gb300 import costmodel as cm
+    dags = cm.make_dags(20250203 + 5, 150)
+    assert len(dags) == 150
+    kinds = {dt for _, _, dt in dags}
+    assert kinds == {"f32", "bf16"}
+    for nodes, outs, dt in dags:
+        lit = ag.Plan(nodes, outs, flags=ag.PLAN_LITERAL)
+        opt = ag.Plan(nodes, outs)
+        assert lit.info["flops"] <= 2e11
+        # fusion and folding only remove launches
+        assert len(opt.info["steps"]) <= len(lit.info["steps"])
