@@ -157,6 +157,50 @@ def test_rewrites_config_plain():
     assert lit["accuAoB"] == ["ew", "ew"]
 
 
+def test_trace_looks_through_transposes():
+    """trace(X^T) = trace(X): a transpose that only the trace uses is not
+    materialised, and the plan is step for step the plan of trace(X) (the
+    fused diagonal pass, the diagonal-only product, or a reduction)."""
+    import re
+
+    def N(op, **k):
+        d = {"op": op}
+        d.update(k)
+        return d
+
+    def steps(nodes, outs, **kw):
+        p = ag.Plan(nodes, outs, **kw)
+        return ([(s["kernel"], s["flops"], s["bytes"], re.sub(r"node \d+", "node", s["note"]))
+                 for s in p.info["steps"]], p.info["workspace"])
+
+    A = N("input", slot=0, rows=97, cols=97, dtype="f32", ld=97)
+    R = N("input", slot=0, rows=40, cols=70, dtype="f64", ld=41)
+    S = N("input", slot=1, rows=40, cols=70, dtype="f64", ld=40)
+    B = N("input", slot=1, rows=97, cols=60, dtype="f32", ld=97)
+    C = N("input", slot=2, rows=60, cols=97, dtype="f32", ld=60)
+    cases = [
+        ([A, N("scale", a=0, s=0.91), N("trans", a=1), N("trace", a=2)],
+         [A, N("scale", a=0, s=0.91), N("trace", a=1)]),
+        ([R, S, N("add", a=0, b=1), N("trans", a=2), N("trace", a=3)],          # non-square
+         [R, S, N("add", a=0, b=1), N("trace", a=2)]),
+        ([A, B, C, N("matmul", a=1, b=2), N("trans", a=3), N("trace", a=4)],
+         [A, B, C, N("matmul", a=1, b=2), N("trace", a=3)]),
+        ([A, N("trans", a=0), N("trace", a=1)], [A, N("trace", a=0)]),
+        ([A, N("scale", a=0, s=2.0), N("trans", a=1), N("trans", a=2), N("trace", a=3)],
+         [A, N("scale", a=0, s=2.0), N("trace", a=1)]),
+    ]
+    for with_t, without in cases:
+        got, ref = steps(with_t, [len(with_t) - 1]), steps(without, [len(without) - 1])
+        assert got == ref, (got, ref)
+        assert "transpose" not in [k for k, *_ in got[0]]
+    # a transpose that is also an output is materialised once; the trace reads it
+    nodes = [A, N("scale", a=0, s=0.91), N("trans", a=1), N("trace", a=2)]
+    k = kernels(ag.Plan(nodes, [2, 3]))
+    assert k.count("transpose") == 1
+    # the literal plan keeps the written order
+    assert "transpose" in kernels(ag.Plan(cases[0][0], [3], flags=ag.PLAN_LITERAL))
+
+
 def test_rewrites_fused_and_chain_and_solve():
     p = ag.Plan(*E.config_fused(128))
     assert kernels(p) == ["ew"]
