@@ -1418,11 +1418,12 @@ void Planner::plan_scalar(int r) {
   scalar_done_[r] = 1;
   const arma_node& d = nd_[r];
   int x = d.a;
-  // trace(X^T) = trace(X): the same diagonal elements, summed in the same
-  // order.  A transpose that only this trace uses is looked through, so the
-  // rewrites below see X itself and no transpose is materialised.
-  if (d.op == ARMA_OP_TRACE)
-    while (nd_[x].op == ARMA_OP_TRANS && !loc_[x].ref.valid() && uses_[x] <= 1 && out_of_[x] < 0) x = nd_[x].a;
+  // trace(X^T) = trace(X) (the same diagonal elements, summed in the same
+  // order); accu and the Frobenius norm sum every element, so they too are
+  // those of X up to the order of the sum.  A transpose that only this
+  // reduction uses is looked through, so the rewrites below see X itself and
+  // no transpose is materialised.
+  while (nd_[x].op == ARMA_OP_TRANS && !loc_[x].ref.valid() && uses_[x] <= 1 && out_of_[x] < 0) x = nd_[x].a;
   Ref out = ref_output(out_of_[r]);
   const arma_node& xd = nd_[x];
   bool x_inner = !loc_[x].ref.valid() && uses_[x] <= 1 && out_of_[x] < 0;

@@ -157,10 +157,12 @@ def test_rewrites_config_plain():
     assert lit["accuAoB"] == ["ew", "ew"]
 
 
-def test_trace_looks_through_transposes():
-    """trace(X^T) = trace(X): a transpose that only the trace uses is not
-    materialised, and the plan is step for step the plan of trace(X) (the
-    fused diagonal pass, the diagonal-only product, or a reduction)."""
+def test_reductions_look_through_transposes():
+    """trace(X^T) = trace(X), and accu and the Frobenius norm sum every
+    element: a transpose that only the reduction uses is not materialised,
+    and the plan is step for step the plan of the reduction of X (the fused
+    diagonal or reducing pass, the diagonal-only product, or a reduction of
+    a materialised matrix)."""
     import re
 
     def N(op, **k):
@@ -193,6 +195,13 @@ def test_trace_looks_through_transposes():
         got, ref = steps(with_t, [len(with_t) - 1]), steps(without, [len(without) - 1])
         assert got == ref, (got, ref)
         assert "transpose" not in [k for k, *_ in got[0]]
+    # accu and the Frobenius norm of a transpose: the plans of accu(X) and norm(X)
+    for red in ("accu", "norm_fro"):
+        got = steps([A, N("scale", a=0, s=0.91), N("trans", a=1), N(red, a=2)], [3])
+        ref = steps([A, N("scale", a=0, s=0.91), N(red, a=1)], [2])
+        assert got == ref, (red, got, ref)
+        got = steps([R, N("trans", a=0), N(red, a=1)], [2])
+        assert got == steps([R, N(red, a=0)], [1]) and "transpose" not in [k for k, *_ in got[0]]
     # a transpose that is also an output is materialised once; the trace reads it
     nodes = [A, N("scale", a=0, s=0.91), N("trans", a=1), N("trace", a=2)]
     k = kernels(ag.Plan(nodes, [2, 3]))
