@@ -381,3 +381,24 @@ def test_analysed_solve_workspace():
     full = ag.Plan(nodes, outs).workspace_bytes
     plain = ag.Plan(nodes, outs, flags=ag.PLAN_NO_SOLVE_ANALYSIS).workspace_bytes
     assert full > plain > 0
+
+
+def test_c_program_uses_the_abi(tmp_path):
+    """A plain C99 program compiled against include/arma_gpu.h and linked to
+    the library plans the fused benchmark expression, reads the decision
+    log, meets the conformance check and orders the benchmark chain through
+    the C ABI alone (host calls, no GPU)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(ag.LIB_PATH)
+    exe = str(tmp_path / "plan_from_c")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "c", "plan_from_c.c"),
+                        "-o", exe, "-L", libdir, "-larma_gpu", "-Wl,-rpath," + libdir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.strip().endswith("OK"), r.stdout + r.stderr
