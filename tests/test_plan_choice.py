@@ -173,3 +173,31 @@ def test_planner_workload_dags_all_plan():
         assert lit.info["flops"] <= 2e11
         # fusion and folding only remove launches
         assert len(opt.info["steps"]) <= len(lit.info["steps"])
+
+
+def test_concurrent_planning_matches_sequential():
+    """arma_gpu_plan from 8 host threads at once (ctypes drops the GIL
+    around each call) gives the same decision logs as one thread, with and
+    without the cost-model choice."""
+    import json
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2502_03000_gb300 import costmodel as cm
+    dags = cm.make_dags(20250203 + 9, 64)
+    flag_sets = [0, ag.PLAN_LITERAL, ag.PLAN_TIER_CHOICE | ag.PLAN_COST_HEURISTIC]
+
+    def plan_all(order):
+        out = {}
+        for i in order:
+            nodes, outs, _ = dags[i % len(dags)]
+            f = flag_sets[i % len(flag_sets)]
+            out[i] = json.dumps(ag.Plan(nodes, outs, flags=f).info, sort_keys=True)
+        return out
+
+    work = list(range(3 * len(dags)))
+    ref = plan_all(work)
+    with ThreadPoolExecutor(8) as ex:
+        parts = list(ex.map(plan_all, [work[t::8][::-1] for t in range(8)]))
+    got = {}
+    for p in parts:
+        got.update(p)
+    assert got == ref
