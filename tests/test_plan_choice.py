@@ -201,3 +201,53 @@ def test_concurrent_planning_matches_sequential():
     for p in parts:
         got.update(p)
     assert got == ref
+
+
+def test_model_swaps_during_concurrent_planning():
+    """While host threads plan with ARMA_PLAN_COST_MLP, another thread loads
+    and clears the shipped network over and over.  Every plan sees one
+    consistent state: its pick is the network's pick when its log says the
+    network scored it, and the estimate's otherwise."""
+    import json
+    import threading
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2502_03000_gb300 import costmodel as cm
+    with open(cm.DEFAULT_MODEL) as f:
+        d = json.load(f)
+    model = dict(params=d["params"], mean=d["mean"], scale=d["scale"], hidden=d["hidden"], guard=4.0)
+    dags = cm.make_dags(20250203 + 10, 48)
+    flags = ag.PLAN_TIER_CHOICE | ag.PLAN_COST_MLP
+
+    def picks():
+        return [ag.Plan(n, o, flags=flags).info["choice"] for n, o, _ in dags]
+
+    ag.clear_cost_model()
+    heur = [c["picked"] for c in picks()]
+    ag.load_cost_model(**model)
+    try:
+        first = picks()
+        assert all(c["scorer"] == "mlp" for c in first)
+        mlp = [c["picked"] for c in first]
+        stop = threading.Event()
+
+        def swap():
+            while not stop.is_set():
+                ag.clear_cost_model()
+                ag.load_cost_model(**model)
+
+        t = threading.Thread(target=swap)
+        t.start()
+        try:
+            with ThreadPoolExecutor(6) as ex:
+                runs = list(ex.map(lambda _: picks(), range(12)))
+        finally:
+            stop.set()
+            t.join()
+        seen = set()
+        for run in runs:
+            for i, c in enumerate(run):
+                seen.add(c["scorer"])
+                assert c["picked"] == (mlp[i] if c["scorer"] == "mlp" else heur[i]), (i, c)
+        assert seen <= {"mlp", "heuristic"}
+    finally:
+        ag.clear_cost_model()
