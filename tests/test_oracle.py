@@ -372,3 +372,34 @@ def test_cholesky_against_numpy(orc):
     neg = spd.copy()
     neg[3, 3] = -1.0
     assert orc.solve_path(neg) == "general"
+
+
+def test_threads_do_not_change_results(tmp_path):
+    """The oracle's OpenMP loops run over independent output columns and
+    leave every summation order as written, so one thread and several give
+    bit-identical results."""
+    import subprocess
+    import sys
+    script = (
+        "import sys, numpy as np, oracle, synth\n"
+        "from paper_2502_03000_gb300 import expr as E\n"
+        "nodes, outs = E.config_fused(300, 'f64')\n"
+        "ins = [synth.matrix(3, s + 1, 300, 300, 'f64') for s in range(4)]\n"
+        "r = oracle.evaluate(nodes, outs, ins)\n"
+        "A, B = synth.matrix(4, 1, 120, 90, 'f64'), synth.matrix(4, 2, 90, 70, 'f64')\n"
+        "M = synth.matrix(4, 3, 50, 50, 'f64') + 50 * np.eye(50)\n"
+        "np.savez(sys.argv[1], out=r[0], accu=r[1], norm=r[2], prod=oracle.matmul(A, B),\n"
+        "         inv=oracle.inv(M), t=oracle.trans(A), acc=oracle.accu(A), nf=oracle.norm_fro(A),\n"
+        "         threads=oracle.num_threads())\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = {}
+    for t in (1, 4):
+        env = dict(os.environ, OMP_NUM_THREADS=str(t), PYTHONPATH=root)
+        path = str(tmp_path / f"r{t}.npz")
+        r = subprocess.run([sys.executable, "-c", script, path], env=env, cwd=root,
+                           capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr[-2000:]
+        res[t] = np.load(path)
+    assert int(res[1]["threads"]) == 1 and int(res[4]["threads"]) == 4
+    for k in ("out", "accu", "norm", "prod", "inv", "t", "acc", "nf"):
+        np.testing.assert_array_equal(res[1][k], res[4][k], err_msg=k)
