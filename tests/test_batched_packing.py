@@ -113,3 +113,37 @@ def test_tile_records_rows_and_boxes():
         assert u16(row, 58) == box(n - 128 * tn)              # hb
         counted += 1
     assert counted == sum(((m + 127) // 128) * ((n + 127) // 128) for m, n, _ in shapes)
+
+
+def test_batched_planning_checks():
+    """arma_gpu_plan_batched: the conformance check per instance, one
+    expression family per batch (same nodes and scalars, sizes free), FP32 or
+    BF16 operands; operands that are not K-contiguous take the SIMT kernel."""
+    import copy
+
+    def status(inst):
+        try:
+            bp = ag.BatchedPlan(inst)
+        except ag.ArmaError as e:
+            return e.status
+        return "tc" if bp.info["tensor_cores"] else "simt"
+
+    n, o = E.config_batched_instance(20, 30, 40, "f32")
+    assert status([(n, o), E.config_batched_instance(64, 8, 512, "f32")]) == "tc"
+    assert status([E.config_batched_instance(20, 30, 40, "bf16")]) == "tc"
+    bad = copy.deepcopy(n)
+    bad[1]["rows"] = bad[1]["ld"] = 41                      # B's K differs from A's
+    assert status([(bad, o)]) == "shape"
+    assert status([]) == "invalid"
+    assert status([E.config_batched_instance(20, 30, 40, "f64")]) == "dtype"
+    assert status([E.config_fused(16, "f32")]) == "unsupported"
+    assert status([(n, o), E.config_fused(16, "f32")]) == "unsupported"
+    other = copy.deepcopy(n)
+    other[4]["s"] = 3.0                                     # another alpha: another family
+    assert status([(n, o), (other, o)]) == "unsupported"
+    # A stored m x k (op(A) = A, K along its rows): planned, on the SIMT kernel
+    nt = copy.deepcopy(n)
+    nt[0] = {"op": "input", "slot": 0, "rows": 20, "cols": 40, "dtype": "f32", "ld": 20}
+    nt[3] = {"op": "scale", "a": 0, "s": 1.0}
+    nt[7] = {"op": "scale", "a": 0, "s": 1.0}
+    assert status([(nt, o)]) == "simt"
