@@ -443,7 +443,15 @@ arma_status arma_gpu_mlp_adam(float* params, const float* grad, float* m, float*
  * A, B are FP32 or BF16, D FP32, traces FP64; accumulation is FP32.
  * Otherwise arma_gpu_plan_batched returns ARMA_ERR_UNSUPPORTED. ---- */
 
-/* Plan count instances (exprs[i] describes instance i). */
+/* Plan count >= 1 instances (exprs[i] describes instance i; read only
+ * during the call).  All instances share one family: the same nodes, scalars
+ * and outputs, with their own sizes.  Errors: ARMA_ERR_INVALID (count < 1,
+ * null pointers), ARMA_ERR_SHAPE (an instance does not conform),
+ * ARMA_ERR_DTYPE (operands that are not FP32 or BF16), ARMA_ERR_UNSUPPORTED
+ * (another form, or instances of different families).  Operands that are
+ * K-contiguous (op(A) = trans of a k x m matrix, B k x n) run on the tensor
+ * cores; others on the SIMT grouped kernel (the plan log's "tensor_cores").
+ * On success *plan is owned by the caller until arma_gpu_plan_free(). */
 arma_status arma_gpu_plan_batched(const arma_expr* exprs, int32_t count, arma_plan** plan);
 
 /* Bytes of the problem table that describes one batch of pointers. */
