@@ -3,7 +3,7 @@
     g = Graph()
     A = g.input(0, m, n); B = g.input(1, m, n)
     Z = 0.4 * A + 0.6 * B              # elementwise (Sec. II example)
-    k = trace(A @ B.t())                 # '@' is the matrix product, '%' Schur
+    k = trace(A * B.t())                 # '*' (or '@') is the matrix product, '%' Schur
     nodes, outputs = g.build(Z, k)
 
 The result is the plain node-dict list that ``Plan`` (and the tests'
@@ -67,6 +67,10 @@ class X:
         if isinstance(o, X):
             return self._bin("sub", o)
         return self.g._add({"op": "add_scalar", "a": self.i, "s": -float(o)})
+
+    def __rsub__(self, s):
+        # s - X = (-X) + s
+        return (-self) + float(s)
 
     def __neg__(self):
         return self.g._add({"op": "neg", "a": self.i})

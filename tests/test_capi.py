@@ -402,3 +402,27 @@ def test_c_program_uses_the_abi(tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0 and r.stdout.strip().endswith("OK"), r.stdout + r.stderr
+
+
+def test_builder_operators_follow_armadillo():
+    """The Python expression builder writes Armadillo's operators as nodes:
+    '*' between matrices is the product ('@' too), '%' the Schur product,
+    scalars scale, shift and divide, and s - X is -X + s.  The literal
+    oracle evaluates what was built as numpy does, and every elementwise
+    result plans into one fused pass."""
+    import numpy as np
+    import oracle
+    import synth
+    g = E.Graph()
+    A, B = g.input(0, 6, 5), g.input(1, 6, 5)
+    C = g.input(2, 5, 3)
+    outs = [1 - A, A + 1, -A, A / 4, 0.5 * A % B, A - B, A * C, A @ C, E.trans(A)]
+    nodes, o = g.build(*outs)
+    a, b, c = synth.matrix(2, 1, 6, 5), synth.matrix(2, 2, 6, 5), synth.matrix(2, 3, 5, 3)
+    got = oracle.evaluate(nodes, o, [a, b, c])
+    want = [1 - a, a + 1, -a, a / 4, 0.5 * a * b, a - b, a @ c, a @ c, a.T]
+    for x, y in zip(got, want):
+        np.testing.assert_allclose(x, y, rtol=0, atol=1e-15)
+    for out in outs[:6]:
+        nodes, o = g.build(out)
+        assert kernels(ag.Plan(nodes, o)) == ["ew"]
