@@ -2,6 +2,7 @@
 // C-ABI entry points (include/arma_gpu.h) and the executor that enqueues a
 // plan's steps on the caller's stream.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 #include <cstring>
@@ -225,12 +226,23 @@ arma_status arma_gpu_eval(const arma_plan* plan, const void* const* in_ptrs, voi
          (int32_t)plan->outs.size()};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cudaError_t e = cudaMemsetAsync(workspace, 0, kHeaderBytes, s)) return cuda_status(e);
+  // NVTX ranges name the evaluation and each of its steps on a profiler's
+  // timeline (the GPU-side counterpart of the plan's decision log); with no
+  // profiler attached the calls return at once
+  static const char* const kStepRange[] = {"arma:ew", "arma:gemm", "arma:diagdot",
+                                           "arma:transpose", "arma:diagbuild", "arma:solve"};
+  nvtxRangePushA("arma_gpu_eval");
   int launches = 0;
+  arma_status r = ARMA_OK;
   for (const Step& st : plan->steps) {
-    arma_status r = run_step(st, b, s, &launches);
-    if (r != ARMA_OK) return r;
+    const int k = (int)st.kind;
+    nvtxRangePushA(k >= 0 && k <= ST_SOLVE ? kStepRange[k] : "arma:step");
+    r = run_step(st, b, s, &launches);
+    nvtxRangePop();
+    if (r != ARMA_OK) break;
   }
-  return ARMA_OK;
+  nvtxRangePop();
+  return r;
 }
 
 arma_status arma_gpu_eval_status(const arma_plan* plan, const void* workspace, void* stream,
