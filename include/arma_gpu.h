@@ -243,7 +243,9 @@ typedef struct arma_plan arma_plan;
  * element types where the operation needs equal ones), ARMA_ERR_UNSUPPORTED
  * (a valid expression outside what this library evaluates).  On success
  * *plan is a new plan, owned by the caller until arma_gpu_plan_free(); on
- * error *plan is set to NULL. */
+ * error *plan is set to NULL.  With the environment variable ARMA_PLAN_LOG
+ * set (to anything but "" or "0") every call also writes one line to stderr:
+ * the decision log of arma_gpu_plan_info, or the status it failed with. */
 arma_status arma_gpu_plan(const arma_expr* expr, arma_plan** plan);
 
 /* Workspace bytes arma_gpu_eval needs for this plan (the buffer itself must

@@ -5,6 +5,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -174,6 +175,17 @@ bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) %
 
 extern "C" {
 
+// ARMA_PLAN_LOG set to anything but "" or "0": every arma_gpu_plan call
+// writes one line to stderr, the plan's decision log or the status it failed
+// with (read once per process).
+static bool plan_log_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("ARMA_PLAN_LOG");
+    return v != nullptr && *v != 0 && std::strcmp(v, "0") != 0;
+  }();
+  return on;
+}
+
 arma_status arma_gpu_plan(const arma_expr* expr, arma_plan** plan) {
   if (!plan) return ARMA_ERR_INVALID;
   *plan = nullptr;
@@ -185,6 +197,10 @@ arma_status arma_gpu_plan(const arma_expr* expr, arma_plan** plan) {
     s = plan_expression(expr, p, nullptr);
   } catch (...) {
     s = ARMA_ERR_INVALID;
+  }
+  if (plan_log_enabled()) {
+    if (s == ARMA_OK) std::fprintf(stderr, "arma_gpu_plan: %s\n", p->log.c_str());
+    else std::fprintf(stderr, "arma_gpu_plan: failed: %s\n", arma_gpu_status_string(s));
   }
   if (s != ARMA_OK) {
     delete p;

@@ -426,3 +426,29 @@ def test_builder_operators_follow_armadillo():
     for out in outs[:6]:
         nodes, o = g.build(out)
         assert kernels(ag.Plan(nodes, o)) == ["ew"]
+
+
+def test_plan_log_environment_variable():
+    """ARMA_PLAN_LOG=1 makes every arma_gpu_plan call write its decision log
+    (or the status it failed with) to stderr; unset, planning is silent."""
+    import json
+    import subprocess
+    import sys
+    script = ("import paper_2502_03000_gb300 as ag\n"
+              "from paper_2502_03000_gb300 import expr as E\n"
+              "ag.Plan(*E.config_fused(64, 'f64'))\n"
+              "g = E.Graph(); A = g.input(0, 4, 5); B = g.input(1, 4, 6)\n"
+              "try:\n    ag.Plan(*g.build(A + B))\nexcept ag.ArmaError:\n    pass\n")
+    for value, lines in (("1", 2), ("0", 0), (None, 0)):
+        env = dict(os.environ, PYTHONPATH=ROOT)
+        env.pop("ARMA_PLAN_LOG", None)
+        if value is not None:
+            env["ARMA_PLAN_LOG"] = value
+        r = subprocess.run([sys.executable, "-c", script], env=env, cwd=ROOT, capture_output=True, text=True,
+                           timeout=120)
+        assert r.returncode == 0, r.stderr
+        logged = [ln for ln in r.stderr.splitlines() if ln.startswith("arma_gpu_plan: ")]
+        assert len(logged) == lines, r.stderr
+        if lines:
+            assert json.loads(logged[0][len("arma_gpu_plan: "):])["steps"][0]["kernel"] == "ew"
+            assert logged[1] == "arma_gpu_plan: failed: non-conforming operand sizes"
